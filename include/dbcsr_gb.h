@@ -1,0 +1,208 @@
+/*
+ * dbcsr_gb.h -- C ABI of the GB300 block-sparse sign-matrix library.
+ *
+ * The library implements, for one GPU, the block-sparse matrix operations and
+ * the density-matrix sign iteration of the CP2K/Quickstep review
+ * (Kuehne et al. 2020):
+ *   - DBCSR block-CSR matrices of atom blocks (section "DBCSR library": blocks
+ *     whose sizes follow the basis of each atom, stored in a blocked CSR format);
+ *   - the local block-sparse product C = beta*C + alpha*A*B as batches of small
+ *     dense block products (section "Local multiplication") followed by the
+ *     eps_filter truncation (section "Sign-Method");
+ *   - trace and the trace of a product (DBCSR's single-matrix operations);
+ *   - the sign iteration X <- X (3 - X^2) / 2 and the density matrix
+ *     P = (1 - sign(H - mu 1)) / 2 (section "Sign-Method", Eq. signdef and the
+ *     density-matrix relation with S = 1).
+ *
+ * Conventions shared by every entry point:
+ *   - Every function returns a dbcsr_status; no C++ exception crosses the ABI.
+ *     On failure dbcsr_last_error() returns a message (per host thread), and
+ *     the output arguments are left unchanged unless stated otherwise.
+ *   - Handles are created and destroyed by the caller.  The library owns all
+ *     device memory of a matrix (stream-ordered allocations on the matrix's
+ *     stream); input buffers are copied, never retained.
+ *   - Matrices are square block grids: block row and block column I both have
+ *     edge blk_size[I].  Blocks are dense, row-major, FP64 unless a function
+ *     says otherwise.  Both triangles of symmetric matrices are stored.
+ *   - Work is queued on the matrix's CUDA stream.  Functions that return host
+ *     values (traces, reports, statistics, get_block, export) synchronise that
+ *     stream before returning.
+ *   - "on_device" arguments: 0 = the pointer is host memory, 1 = it is device
+ *     memory of the current device.  Index arrays are always host memory.
+ */
+#ifndef DBCSR_GB_H
+#define DBCSR_GB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dbcsr_matrix_* dbcsr_matrix;
+
+typedef enum {
+    DBCSR_OK = 0,
+    DBCSR_EINVAL = 1,     /* bad argument: null handle, index out of range, size mismatch, duplicate block */
+    DBCSR_ENOMEM = 2,     /* a device or host allocation failed */
+    DBCSR_ECAPACITY = 3,  /* a size exceeds a fixed limit of the library */
+    DBCSR_ECUDA = 4,      /* a CUDA runtime call failed (message holds cudaGetErrorString) */
+    DBCSR_ENAN = 5,       /* a NaN or Inf appeared in a result */
+    DBCSR_ENOTCONV = 6,   /* the sign iteration stopped without reaching the tolerance */
+    DBCSR_ETIMEOUT = 7,   /* a bounded device-side wait ran out */
+    DBCSR_ESTATE = 8      /* the call is not allowed in the matrix's current state (e.g. not finalized) */
+} dbcsr_status;
+
+typedef enum {
+    DBCSR_FP64 = 0,       /* FP64 operands, FP64 accumulation */
+    DBCSR_BF16 = 2,       /* BF16 operands (round to nearest even), FP32 accumulation, FP64 result */
+    DBCSR_MIXED = 3       /* sign iteration only: BF16 tier while the residual >= switch, then FP64 */
+} dbcsr_prec;
+
+/* Work counters of one product.  Counts refer to the blocks the product
+ * actually formed, after the exact norm-bound prescreen (a candidate C block
+ * whose bound |alpha| sum_K ||A_IK||_F ||B_KJ||_F + |beta| ||C_IJ||_F is below
+ * eps_filter can only be filtered, so it is not formed). */
+typedef struct {
+    int64_t n_candidates;      /* blocks of the full pattern of A*B (union C when beta != 0) */
+    int64_t n_formed;          /* candidate blocks that passed the prescreen and were computed */
+    int64_t n_kept;            /* blocks left after the eps_filter truncation */
+    int64_t n_products;        /* block products A_IK * B_KJ executed */
+    double flops;              /* sum of 2*m*k*n over the executed products (unpadded) */
+    double dev2_filtered;      /* ||C_filtered - 1||_F^2 (meaningful for X*X in the sign iteration) */
+    double ms_symbolic;        /* device time of the stack builder, ms */
+    double ms_numeric;         /* device time of the block-product kernel, ms */
+    double ms_filter;          /* device time of norm-filter-compaction, ms */
+} dbcsr_mult_stats;
+
+/* Options of the sign iteration. */
+typedef struct {
+    double eps_filter;         /* block Frobenius-norm threshold applied after every product */
+    double tol;                /* stop when ||X^2 - 1||_F / N < tol */
+    int32_t max_iter;          /* at most this many steps (default 100 when <= 0) */
+    int32_t prec;              /* dbcsr_prec: DBCSR_FP64 or DBCSR_MIXED */
+    double switch_tol;         /* DBCSR_MIXED: residual below which FP64 takes over (e.g. 1e-4) */
+    double stall_after;        /* stall test active once r < stall_after (default 1e-2 when <= 0) */
+    int32_t verbose;           /* 1: print one line per step to stderr */
+    int32_t reserved;
+} dbcsr_sign_opts;
+
+#define DBCSR_MAX_HISTORY 128
+
+/* Outcome of dbcsr_sign_iterate. */
+typedef struct {
+    int32_t iterations;        /* steps taken (products X*X formed) */
+    int32_t converged;         /* 1 if r < tol was reached */
+    int32_t stalled;           /* 1 if the stall test stopped the iteration */
+    int32_t fp64_from;         /* first step computed in FP64 (DBCSR_MIXED), else 0 */
+    double alpha;              /* Gershgorin scale: X_0 = (H - mu 1) / alpha */
+    double residual;           /* last r = ||X^2 - 1||_F / N */
+    double trace_p;            /* Tr(P) */
+    double e_band;             /* Tr(P H) */
+    double flops;              /* sum over every product of the executed 2*m*k*n */
+    int64_t n_products;        /* executed block products */
+    double ms_total;           /* wall time of the call (device-synchronised), ms */
+    double ms_multiply;        /* device time spent in block-product kernels, ms */
+    int64_t nnzb_x;            /* blocks of the converged X */
+    double residual_history[DBCSR_MAX_HISTORY];
+    int64_t nnzb_history[DBCSR_MAX_HISTORY];
+} dbcsr_sign_report;
+
+/* Last error message of the calling host thread ("" if none). */
+const char* dbcsr_last_error(void);
+
+/* Library version string. */
+const char* dbcsr_version(void);
+
+/*
+ * Creates an empty matrix with nblk block rows/columns of edges blk_size[0..nblk-1]
+ * (host array, each in [1, 64]).  stream: a cudaStream_t (NULL = the legacy
+ * default stream); all work on the matrix is queued there.  The matrix starts
+ * in the "building" state: blocks are added with put_block(s), then finalize().
+ */
+dbcsr_status dbcsr_create(dbcsr_matrix* out, int32_t nblk, const int32_t* blk_size, void* stream);
+
+/* Frees the matrix and its device memory (stream-ordered).  NULL is accepted. */
+dbcsr_status dbcsr_destroy(dbcsr_matrix m);
+
+/*
+ * Stages block (row, col): blk_size[row] x blk_size[col] doubles, row-major, at
+ * data (host or device per on_device).  The data is copied before return.
+ * Allowed in the building state only; a duplicate (row, col) makes finalize fail.
+ */
+dbcsr_status dbcsr_put_block(dbcsr_matrix m, int32_t row, int32_t col, const double* data, int on_device);
+
+/*
+ * Stages n blocks at once: rows[i], cols[i] (host arrays); their data packed one
+ * after the other, each row-major, in the order given (host or device).
+ */
+dbcsr_status dbcsr_put_blocks(dbcsr_matrix m, int64_t n, const int32_t* rows, const int32_t* cols,
+                              const double* packed, int on_device);
+
+/* Sorts the staged blocks into block-CSR order and moves them to the device.
+ * Fails with DBCSR_EINVAL on a duplicate block (the matrix stays building). */
+dbcsr_status dbcsr_finalize(dbcsr_matrix m);
+
+/* Block count and stored element count of a finalized matrix. */
+dbcsr_status dbcsr_get_info(dbcsr_matrix m, int32_t* nblk, int64_t* nnzb, int64_t* nelem);
+
+/* Copies block (row, col) to out_host (row-major) and sets *present; absent
+ * blocks set *present = 0 and leave out_host untouched. */
+dbcsr_status dbcsr_get_block(dbcsr_matrix m, int32_t row, int32_t col, double* out_host, int* present);
+
+/*
+ * Copies the whole matrix to host arrays: row_ptr[nblk+1], col[nnzb] and the
+ * packed FP64 data[nelem] in block-CSR order (each may be NULL to skip it).
+ */
+dbcsr_status dbcsr_export(dbcsr_matrix m, int64_t* row_ptr, int32_t* col, double* data);
+
+/* dst = src (pattern and values); dst must have the same block sizes. */
+dbcsr_status dbcsr_copy(dbcsr_matrix dst, dbcsr_matrix src);
+
+/* m = scale * m + shift * 1.  Every diagonal block must be present. */
+dbcsr_status dbcsr_scale_shift(dbcsr_matrix m, double scale, double shift);
+
+/*
+ * C = beta * C + alpha * A * B, then every block of C with Frobenius norm
+ * strictly below eps_filter is removed (diagonal blocks are always kept).
+ * The sum over K of each C_IJ is taken in ascending K.  C may be the same
+ * handle as A and/or B.  The result is formed on the pattern of A*B (union C's
+ * pattern when beta != 0) less the candidates that the exact norm-bound
+ * prescreen proves would be filtered.  prec: DBCSR_FP64 or DBCSR_BF16.
+ * stats may be NULL; when given, the call synchronises and fills it.
+ */
+dbcsr_status dbcsr_multiply(double alpha, dbcsr_matrix A, dbcsr_matrix B, double beta, dbcsr_matrix C,
+                            double eps_filter, int32_t prec, dbcsr_mult_stats* stats);
+
+/* Removes the blocks of m with Frobenius norm strictly below eps (diagonal blocks kept). */
+dbcsr_status dbcsr_filter(dbcsr_matrix m, double eps);
+
+/* *out = Tr(A) (synchronises). */
+dbcsr_status dbcsr_trace(dbcsr_matrix A, double* out);
+
+/* *out = Tr(A * B) = sum_IJ <A_IJ, B_JI^T>, without forming the product (synchronises). */
+dbcsr_status dbcsr_trace_product(dbcsr_matrix A, dbcsr_matrix B, double* out);
+
+/* *out = max_i sum_j |(A - mu 1)_ij| (Gershgorin bound of the spectral radius; synchronises). */
+dbcsr_status dbcsr_gershgorin(dbcsr_matrix A, double mu, double* out);
+
+/*
+ * Density matrix by the second-order Newton-Schulz sign iteration
+ * (section "Sign-Method"; S = 1):
+ *   X_0 = (H - mu 1) / alpha, alpha = dbcsr_gershgorin(H, mu);
+ *   repeat: X2 = filter(X X); r = ||X2 - 1||_F / N; stop if r < tol;
+ *           X <- filter(1.5 X - 0.5 X X2)          (= X (3 - X^2) / 2);
+ *   P_out = (1 - X) / 2.
+ * H must be symmetric with every diagonal block present.  P_out receives the
+ * result (its previous content is replaced).  rep may be NULL.  Returns
+ * DBCSR_ENOTCONV (P_out and rep still filled) when max_iter or the stall test
+ * ended the iteration before r < tol.
+ */
+dbcsr_status dbcsr_sign_iterate(dbcsr_matrix H, double mu, const dbcsr_sign_opts* opts, dbcsr_matrix P_out,
+                                dbcsr_sign_report* rep);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DBCSR_GB_H */
