@@ -1,0 +1,285 @@
+#!/usr/bin/env python3
+"""Benchmark: time-to-P and block-GEMM throughput of the FP64 Newton-Schulz sign
+iteration on the 1,024-water synthetic Hamiltonian (N = 23,552, eps 1e-7, tol 1e-9).
+
+One step = one complete sign iteration from the resident H to the density matrix
+P (every product, filter, trace of the path).  value = algorithmic FP64 flops of
+all block products executed in the timed steps / device time (TFLOP/s);
+ms_per_step = time-to-P.  With --gpus N > 1 (torchrun) every rank solves its own
+replica (the path is not sharded across GPUs here: replicas only, weak scaling).
+
+--impl reference times the FP64 CPU oracle (plain C) on the host cores, each step
+a bounded sample of the same workload (the first product X0.X0 restricted to a
+fixed set of block rows).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# nominal dense rates (TFLOP/s) used to carry a measured bf16 peak over to FP64
+NOMINAL_BF16 = 2250.0
+NOMINAL_FP64 = 1.25
+FALLBACK_BF16_BURST, FALLBACK_BF16_SUSTAINED = 1900.0, 1700.0
+
+
+def fp64_peak():
+    """FP64 roofline peak: the measured bf16 peak times the nominal FP64/bf16 ratio."""
+    try:
+        pk = json.load(open(PEAKS_FILE))
+        bf16, src = float(pk["bf16_tflops_sustained"]), "measured bf16 sustained x nominal fp64/bf16"
+    except Exception:
+        bf16, src = FALLBACK_BF16_SUSTAINED, "fallback bf16 sustained x nominal fp64/bf16"
+    return bf16 * NOMINAL_FP64 / NOMINAL_BF16, src
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region (median SM clock, throttle reasons)."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), f[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = sorted(r[0] for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[2]) if v.lower() == "active"})
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
+                "samples": len(rows)}
+
+
+def oracle_sample(h, w, rows_frac: float, reps: int = 1):
+    """The oracle's first product X0.X0 on the first block rows of X0 (a bounded sample)."""
+    import numpy as np
+    from oracle import bsr
+    Ho = bsr.Mat.of(h.H)
+    alpha = float(bsr.abs_row_sums(Ho, 0.0).max())
+    X = bsr.add_identity(Ho, 1.0 / alpha, 0.0)
+    R = max(1, int(X.nblk * rows_frac))
+    keep = X.rows < R
+    Xs = bsr.select_blocks(X, keep)
+    t0 = time.perf_counter()
+    flops = 0
+    for _ in range(reps):
+        _, info = bsr.multiply(1.0, Xs, X, eps=w.eps_filter, info=True)
+        flops += info.flops
+    dt = time.perf_counter() - t0
+    return flops, dt, R, bsr.num_threads()
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import synth
+    w = synth.SIGN_1024
+    h = synth.build_hamiltonian(w)
+    frac = args.ref_rows
+    for _ in range(args.warmup):
+        oracle_sample(h, w, frac)
+    tot_f, tot_t = 0, 0.0
+    for _ in range(args.steps):
+        f, dt, R, cores = oracle_sample(h, w, frac)
+        tot_f += f
+        tot_t += dt
+    value = tot_f / tot_t / 1e12
+    sample = (f"first product X0.X0 of the FP64 sign iteration restricted to block rows [0, {R}) of {h.H.nblk} "
+              f"(no prescreen, eps {w.eps_filter}), one per step")
+    out = {"metric": "block-GEMM TFLOP/s (FP64 sign iteration, time-to-P)", "value": value, "unit": "TFLOP/s",
+           "impl": "reference", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": tot_t / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": w.name, "n_mol": w.n_mol, "N": w.n, "eps_filter": w.eps_filter, "tol": w.tol,
+                      "sample": sample},
+           "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cores, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU-baseline leg")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--ref-rows", type=float, default=0.4, help="fraction of block rows in the oracle sample")
+    ap.add_argument("--verbose", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    import paper_2003_03868_gb300 as gb
+    try:
+        gb.lib()
+    except ImportError:
+        from paper_2003_03868_gb300 import build
+        build.build()
+        gb.lib()
+    import synth
+
+    w = synth.SIGN_1024
+    h = synth.build_hamiltonian(w)
+    stream = torch.cuda.current_stream()
+    H = gb.Matrix.of(h.H, stream=stream.cuda_stream)
+
+    def step():
+        return gb.sign_iterate(H, h.mu, w.eps_filter, w.tol, verbose=args.verbose)
+
+    for _ in range(args.warmup):
+        r = step()
+    barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    l0 = gb.lib().dbcsr_launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    flops, ms_mult, iters, ebands, trp, conv = 0.0, 0.0, [], [], [], []
+    for _ in range(args.steps):
+        r = step()
+        flops += r.report.flops
+        ms_mult += r.report.ms_multiply
+        iters.append(r.report.iterations)
+        ebands.append(r.report.e_band)
+        trp.append(r.report.trace_p)
+        conv.append(bool(r.report.converged))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    launches = gb.lib().dbcsr_launch_count() - l0
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    t = torch.tensor([ms, flops], dtype=torch.float64, device="cuda")
+    if dist:
+        mx = t.clone()
+        dist.all_reduce(mx[0:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(mx[1:2], op=dist.ReduceOp.SUM)
+        t = mx
+    ms_all, flops_all = float(t[0]), float(t[1])
+    value = flops_all / (ms_all * 1e-3) / 1e12
+
+    # end to end through the public API: inputs from pinned host memory, report read back
+    e2e = None
+    if not args.no_e2e:
+        data_pin = torch.from_numpy(np.ascontiguousarray(h.H.data)).pin_memory()
+        h2d = int(h.H.data.nbytes + 2 * 4 * h.H.col.shape[0])
+        barrier()
+        f0 = time.perf_counter()
+        e2 = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        e2[0].record(stream)
+        fl = 0.0
+        for _ in range(args.steps):
+            Hs = gb.Matrix.from_blocks(h.H.blk_size, h.H.row_ptr, h.H.col, None, stream=stream.cuda_stream,
+                                       data_ptr=data_pin.data_ptr())
+            rr = gb.sign_iterate(Hs, h.mu, w.eps_filter, w.tol)
+            fl += rr.report.flops
+            _ = float(rr.report.e_band)
+            Hs.close()
+        e2[1].record(stream)
+        torch.cuda.synchronize()
+        ms2 = e2[0].elapsed_time(e2[1])
+        e2e = {"value": fl / (ms2 * 1e-3) / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": 8 * 3, "ms_per_step": ms2 / args.steps,
+               "wall_s": time.perf_counter() - f0}
+
+    peak, peak_src = fp64_peak()
+    achieved = flops / (ms_mult * 1e-3) / 1e12 if ms_mult > 0 else 0.0
+    roofline = {"bound": "fp64", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None, "kernel": "k_smm_f64",
+                "peak_source": peak_src, "kernel_share_of_step": ms_mult / ms if ms > 0 else None}
+    try:
+        roofline["fp64_dfma_measured_tflops"] = gb.lib().dbcsr_bench_peak(0, 4096, 152 * 8, 256) / 1e3
+        roofline["fp64_dmma_measured_tflops"] = gb.lib().dbcsr_bench_peak(1, 4096, 152 * 8, 256) / 1e3
+    except Exception:
+        pass
+
+    out = {"metric": "block-GEMM TFLOP/s (FP64 sign iteration, time-to-P)", "value": value, "unit": "TFLOP/s",
+           "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_all / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": w.name, "n_mol": w.n_mol, "N": w.n, "blocks": {"O": 13, "H": 5},
+                      "eps_filter": w.eps_filter, "tol": w.tol, "mu": h.mu,
+                      "l2": "inputs larger than L2 (H alone is %.0f MB; 129 MB L2)" % (h.H.data.nbytes / 1e6),
+                      "parallelism": f"replicas x{world}"},
+           "time_to_p_ms": ms_all / args.steps,
+           "iterations": iters[-1], "converged": all(conv), "trace_p": trp[-1], "n_occ": h.n_occ,
+           "e_band": ebands[-1], "gpu_launches": launches, "clocks": clk, "roofline": roofline, "e2e": e2e}
+
+    if rank == 0 and world == 1 and not args.no_cpu:
+        f, dt, R, cores = oracle_sample(h, w, args.ref_rows)
+        out["cpu_baseline"] = {"value": f / dt / 1e12, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+                               "sample": f"first product X0.X0 on block rows [0, {R}) of {h.H.nblk} "
+                                         f"({f / 1e9:.1f} GFLOP executed in {dt:.1f} s, no prescreen)"}
+    if rank == 0:
+        print(json.dumps(out))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,37 @@
+/*
+ * dbcsr_gb_bench.h -- measurement helpers of the GB300 block-sparse library.
+ *
+ * These calls have no counterpart in the paper: they measure the machine (the
+ * FP64 rates that bound the FP64 block products) and count kernel launches, so
+ * that reported throughput can be set against a roofline.
+ */
+#ifndef DBCSR_GB_BENCH_H
+#define DBCSR_GB_BENCH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Kinds of dbcsr_bench_peak. */
+#define DBCSR_PEAK_DFMA 0   /* FP64 fused multiply-add on the CUDA cores */
+#define DBCSR_PEAK_DMMA 1   /* FP64 tensor-core mma.sync m8n8k4 */
+
+/*
+ * Runs a compute-only loop of the given kind on the current device: `blocks`
+ * CTAs of `threads` threads, each issuing `iters` rounds of independent
+ * operations, timed with CUDA events.  Returns the achieved rate in GFLOP/s
+ * (2 flops per FMA), or a negative value on error (dbcsr_last_error() says why).
+ * threads must be a multiple of 32 in [32, 1024]; blocks in [1, 65535]; iters >= 1.
+ */
+double dbcsr_bench_peak(int32_t kind, int32_t iters, int32_t blocks, int32_t threads);
+
+/* Number of kernels this library has launched in this process so far. */
+int64_t dbcsr_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DBCSR_GB_BENCH_H */

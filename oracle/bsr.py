@@ -46,6 +46,7 @@ def lib():
         L.oracle_trace_product.restype = C.c_double
         L.oracle_abs_row_sums.argtypes = [C.c_int32, p, p, p, p, p, p, C.c_double, p]
         L.oracle_num_threads.restype = C.c_int
+        L.oracle_mm_block.argtypes = [C.c_int32, C.c_int32, p, C.c_double] + [p] * 8 + [C.c_double, p, p]
         _lib = L
     return _lib
 
@@ -224,6 +225,16 @@ def multiply(alpha: float, A: Mat, B: Mat, beta: float = 0.0, Cin: Mat | None = 
     dk = np.ascontiguousarray(dev2[keep])
     d2f = lib().oracle_sum_dev2(Cf.nblk, _p(Cf.bs), _p(Cf.rp), _p(Cf.col), _p(dk))
     return Cf, MultInfo(Cu, norms, keep, float(d2f), float(d2u), int(stats[0]), int(stats[1]))
+
+
+def product_block(I: int, J: int, alpha: float, A: Mat, B: Mat, beta: float = 0.0, Cin: Mat | None = None):
+    """Block (I, J) of alpha*A*B + beta*C_in, computed on its own (same loop order as multiply)."""
+    out = np.zeros(int(A.bs[I]) * int(A.bs[J]))
+    ci = Cin.block(I, J) if (Cin is not None and beta != 0.0) else None
+    ci = None if ci is None else np.ascontiguousarray(ci).ravel()
+    lib().oracle_mm_block(int(I), int(J), _p(A.bs), float(alpha), _p(A.rp), _p(A.col), _p(A.boff), _p(A.data),
+                          _p(B.rp), _p(B.col), _p(B.boff), _p(B.data), float(beta), _p(ci), _p(out))
+    return out.reshape(int(A.bs[I]), int(A.bs[J]))
 
 
 def trace(M: Mat) -> float:

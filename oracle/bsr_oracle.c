@@ -322,3 +322,35 @@ int oracle_num_threads(void) {
     return 1;
 #endif
 }
+
+/*
+ * One block of the product: out = alpha * sum_K A_IK * B_KJ (ascending K, then k)
+ * + beta * ci (ci may be NULL).  Used to check single outputs of large products.
+ */
+void oracle_mm_block(int32_t I, int32_t J, const int32_t* bs, double alpha,
+                     const int64_t* a_rp, const int32_t* a_col, const int64_t* a_boff, const double* a_data,
+                     const int64_t* b_rp, const int32_t* b_col, const int64_t* b_boff, const double* b_data,
+                     double beta, const double* ci, double* out) {
+    const int64_t m = bs[I], n = bs[J];
+    for (int64_t e = 0; e < m * n; ++e) out[e] = 0.0;
+    for (int64_t p = a_rp[I]; p < a_rp[I + 1]; ++p) {
+        const int32_t K = a_col[p];
+        const int64_t k = bs[K];
+        /* find B_KJ */
+        int64_t lo = b_rp[K], hi = b_rp[K + 1];
+        while (lo < hi) {
+            int64_t mid = lo + (hi - lo) / 2;
+            if (b_col[mid] < J) lo = mid + 1; else hi = mid;
+        }
+        if (!(lo < b_rp[K + 1] && b_col[lo] == J)) continue;
+        const double* a = a_data + a_boff[p];
+        const double* b = b_data + b_boff[lo];
+        for (int64_t i = 0; i < m; ++i)
+            for (int64_t j = 0; j < n; ++j) {
+                double s = out[i * n + j];
+                for (int64_t kk = 0; kk < k; ++kk) s = s + a[i * k + kk] * b[kk * n + j];
+                out[i * n + j] = s;
+            }
+    }
+    for (int64_t e = 0; e < m * n; ++e) out[e] = ci ? alpha * out[e] + beta * ci[e] : alpha * out[e];
+}

@@ -1,0 +1,79 @@
+"""ctypes declarations of the C ABI in include/dbcsr_gb.h (argument marshalling only)."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libdbcsr_gb.so")
+
+DBCSR_OK, DBCSR_EINVAL, DBCSR_ENOMEM, DBCSR_ECAPACITY, DBCSR_ECUDA = 0, 1, 2, 3, 4
+DBCSR_ENAN, DBCSR_ENOTCONV, DBCSR_ETIMEOUT, DBCSR_ESTATE = 5, 6, 7, 8
+DBCSR_FP64, DBCSR_BF16, DBCSR_MIXED = 0, 2, 3
+MAX_HISTORY = 128
+
+STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECAPACITY", 4: "ECUDA", 5: "ENAN", 6: "ENOTCONV",
+                7: "ETIMEOUT", 8: "ESTATE"}
+
+
+class MultStats(C.Structure):
+    _fields_ = [("n_candidates", C.c_int64), ("n_formed", C.c_int64), ("n_kept", C.c_int64),
+                ("n_products", C.c_int64), ("flops", C.c_double), ("dev2_filtered", C.c_double),
+                ("ms_symbolic", C.c_double), ("ms_numeric", C.c_double), ("ms_filter", C.c_double)]
+
+
+class SignOpts(C.Structure):
+    _fields_ = [("eps_filter", C.c_double), ("tol", C.c_double), ("max_iter", C.c_int32), ("prec", C.c_int32),
+                ("switch_tol", C.c_double), ("stall_after", C.c_double), ("verbose", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
+class SignReport(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("converged", C.c_int32), ("stalled", C.c_int32), ("fp64_from", C.c_int32),
+                ("alpha", C.c_double), ("residual", C.c_double), ("trace_p", C.c_double), ("e_band", C.c_double),
+                ("flops", C.c_double), ("n_products", C.c_int64), ("ms_total", C.c_double),
+                ("ms_multiply", C.c_double), ("nnzb_x", C.c_int64),
+                ("residual_history", C.c_double * MAX_HISTORY), ("nnzb_history", C.c_int64 * MAX_HISTORY)]
+
+
+# (name, restype, argtypes) of every exported entry point
+P = C.c_void_p
+SIGNATURES = [
+    ("dbcsr_last_error", C.c_char_p, []),
+    ("dbcsr_version", C.c_char_p, []),
+    ("dbcsr_create", C.c_int, [C.POINTER(P), C.c_int32, P, P]),
+    ("dbcsr_destroy", C.c_int, [P]),
+    ("dbcsr_put_block", C.c_int, [P, C.c_int32, C.c_int32, P, C.c_int]),
+    ("dbcsr_put_blocks", C.c_int, [P, C.c_int64, P, P, P, C.c_int]),
+    ("dbcsr_finalize", C.c_int, [P]),
+    ("dbcsr_get_info", C.c_int, [P, C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+    ("dbcsr_get_block", C.c_int, [P, C.c_int32, C.c_int32, P, C.POINTER(C.c_int)]),
+    ("dbcsr_export", C.c_int, [P, P, P, P]),
+    ("dbcsr_copy", C.c_int, [P, P]),
+    ("dbcsr_scale_shift", C.c_int, [P, C.c_double, C.c_double]),
+    ("dbcsr_multiply", C.c_int, [C.c_double, P, P, C.c_double, P, C.c_double, C.c_int32, C.POINTER(MultStats)]),
+    ("dbcsr_filter", C.c_int, [P, C.c_double]),
+    ("dbcsr_trace", C.c_int, [P, C.POINTER(C.c_double)]),
+    ("dbcsr_trace_product", C.c_int, [P, P, C.POINTER(C.c_double)]),
+    ("dbcsr_gershgorin", C.c_int, [P, C.c_double, C.POINTER(C.c_double)]),
+    ("dbcsr_sign_iterate", C.c_int, [P, C.c_double, C.POINTER(SignOpts), P, C.POINTER(SignReport)]),
+    ("dbcsr_bench_peak", C.c_double, [C.c_int32, C.c_int32, C.c_int32, C.c_int32]),
+    ("dbcsr_launch_count", C.c_int64, []),
+]
+
+_lib = None
+
+
+def load():
+    """The shared library; raises if it has not been built (there is no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with paper_2003_03868_gb300.build.build()")
+        L = C.CDLL(LIB_PATH)
+        for name, res, args in SIGNATURES:
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib

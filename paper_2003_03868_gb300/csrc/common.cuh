@@ -1,0 +1,167 @@
+// Shared declarations of the GB300 block-sparse library: error plumbing,
+// stream-ordered device buffers, the matrix object and internal entry points.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdint>
+#include <cstring>
+#include <stdexcept>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "dbcsr_gb.h"
+
+namespace dbg {
+
+// Largest block edge the kernels accept (atom blocks of the workloads are <= 23).
+constexpr int kMaxBlock = 32;
+
+struct Error : std::runtime_error {
+    dbcsr_status code;
+    Error(dbcsr_status c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+[[noreturn]] void fail(dbcsr_status code, const std::string& msg);
+extern std::atomic<int64_t> g_launches;
+
+#define DBG_CK(call)                                                                        \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess) {                                                            \
+            if (e_ == cudaErrorMemoryAllocation) {                                          \
+                (void)cudaGetLastError();                                                   \
+                ::dbg::fail(DBCSR_ENOMEM, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+            }                                                                               \
+            ::dbg::fail(DBCSR_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));   \
+        }                                                                                   \
+    } while (0)
+
+// Every kernel launch site is followed by DBG_LAUNCH_CK(): it checks the launch
+// and counts it (dbcsr_launch_count).
+#define DBG_LAUNCH_CK()                                    \
+    do {                                                   \
+        ::dbg::g_launches.fetch_add(1, std::memory_order_relaxed); \
+        DBG_CK(cudaGetLastError());                        \
+    } while (0)
+
+// Device array allocated and freed in stream order (cudaMallocAsync pool).
+template <class T>
+struct DBuf {
+    T* p = nullptr;
+    int64_t n = 0;
+    cudaStream_t s = nullptr;
+
+    DBuf() = default;
+    DBuf(const DBuf&) = delete;
+    DBuf& operator=(const DBuf&) = delete;
+    DBuf(DBuf&& o) noexcept : p(o.p), n(o.n), s(o.s) { o.p = nullptr; o.n = 0; }
+    DBuf& operator=(DBuf&& o) noexcept {
+        if (this != &o) {
+            release();
+            p = o.p; n = o.n; s = o.s;
+            o.p = nullptr; o.n = 0;
+        }
+        return *this;
+    }
+    ~DBuf() { release(); }
+
+    void alloc(int64_t count, cudaStream_t stream) {
+        release();
+        s = stream;
+        n = count;
+        if (count > 0) DBG_CK(cudaMallocAsync((void**)&p, sizeof(T) * (size_t)count, stream));
+    }
+    void zero() {
+        if (n > 0) DBG_CK(cudaMemsetAsync(p, 0, sizeof(T) * (size_t)n, s));
+    }
+    void release() noexcept {
+        if (p) cudaFreeAsync(p, s);
+        p = nullptr;
+        n = 0;
+    }
+};
+
+// Pinned host scratch for small device->host readbacks.
+struct HostScalars {
+    int64_t* i = nullptr;
+    double* d = nullptr;
+    HostScalars();
+    ~HostScalars();
+};
+HostScalars& host_scalars();
+
+}  // namespace dbg
+
+// The matrix object behind the opaque C handle.
+struct dbcsr_matrix_ {
+    int32_t nblk = 0;
+    int64_t n = 0;                       // matrix dimension = sum of block edges
+    cudaStream_t stream = nullptr;
+    std::vector<int32_t> h_bs;           // host copy of the block edges
+    dbg::DBuf<int32_t> bs;               // [nblk] block edges
+    bool finalized = false;
+
+    // block-CSR on the device
+    int64_t nnzb = 0, nel = 0;
+    dbg::DBuf<int64_t> rp;               // [nblk + 1] row pointers
+    dbg::DBuf<int32_t> col;              // [nnzb] block column, ascending per row
+    dbg::DBuf<int32_t> row;              // [nnzb] block row of each block
+    dbg::DBuf<int64_t> off;              // [nnzb + 1] element offset of each block in data
+    dbg::DBuf<double> data;              // [nel] blocks row-major, packed in CSR order
+    dbg::DBuf<double> norms;             // [nnzb] Frobenius norms (valid iff norms_valid)
+    bool norms_valid = false;
+
+    // staging area of put_block(s) before finalize
+    std::vector<int32_t> st_row, st_col;
+    std::vector<int64_t> st_src;         // element offset of each staged block in st_dev
+    dbg::DBuf<double> st_dev;
+    int64_t st_dev_used = 0;
+};
+
+namespace dbg {
+
+// ---- scan.cu
+// out[0..n] = exclusive prefix sum of in[0..n-1]; out[n] = total.  n >= 0.
+void scan_exclusive(const int64_t* in, int64_t* out, int64_t n, cudaStream_t s);
+void scan_exclusive(const int32_t* in, int64_t* out, int64_t n, cudaStream_t s);
+// Deterministic sum of v[0..n-1] into *out (device); fixed reduction tree for a given n.
+void det_sum(const double* v, int64_t n, double* out, cudaStream_t s);
+
+// ---- matrix.cu
+void check_finalized(const dbcsr_matrix_* m);
+void ensure_norms(dbcsr_matrix_* m);
+void compute_block_norms(const dbcsr_matrix_* m, double* norms, double* dev2);
+void copy_matrix(dbcsr_matrix_* dst, const dbcsr_matrix_* src);
+void scale_shift(dbcsr_matrix_* m, double scale, double shift);
+// Keeps the blocks whose flag is nonzero (norms, when given, are compacted too).
+void compact(dbcsr_matrix_* m, const int32_t* keep, const double* norms_in);
+void filter_matrix(dbcsr_matrix_* m, double eps, const double* norms_in);
+int64_t read_i64(const int64_t* dev, cudaStream_t s);
+void read_i64s(const int64_t* const* dev, int k, int64_t* out, cudaStream_t s);
+double read_f64(const double* dev, cudaStream_t s);
+
+// ---- reduce.cu
+double trace(dbcsr_matrix_* m);
+double trace_product(dbcsr_matrix_* a, dbcsr_matrix_* b);
+double gershgorin(dbcsr_matrix_* m, double mu);
+
+// ---- multiply.cu
+void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbcsr_matrix_* C, double eps,
+              int prec, dbcsr_mult_stats* stats, bool want_dev2);
+
+// ---- sign.cu
+dbcsr_status sign_iterate(dbcsr_matrix_* H, double mu, const dbcsr_sign_opts* opts, dbcsr_matrix_* P,
+                          dbcsr_sign_report* rep);
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+inline unsigned grid_for(int64_t work, int per, int64_t cap = 152 * 64) {
+    int64_t g = ceil_div(work, per);
+    if (g < 1) g = 1;
+    if (g > cap) g = cap;
+    return (unsigned)g;
+}
+
+}  // namespace dbg

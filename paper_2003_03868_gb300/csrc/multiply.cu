@@ -1,0 +1,557 @@
+// The block-sparse product C = beta*C + alpha*A*B followed by the eps_filter
+// truncation (DBCSR sections "Local multiplication" and "Batched execution";
+// the filter is from section "Sign-Method").
+//
+// The paper separates *what* to multiply (CPU traversal + batch generation) from
+// *performing* the batches (SMM kernels).  Here both halves run on the GPU:
+//
+//  1. k_cand_count   per block row I: bitmap (shared memory) of the block columns
+//                    J reached through A_IK B_KJ (and C_IJ when beta != 0).
+//  2. k_cand_bound   per row: the candidates in ascending J, and for each the
+//                    exact norm bound |alpha| sum_K ||A_IK|| ||B_KJ|| (+ |beta|
+//                    ||C_IJ||), the product count and sum of k.  A candidate
+//                    whose bound is below eps can only be filtered away, so it
+//                    is not formed (diagonal blocks always are).
+//  3. k_form_meta    compacted list of formed blocks with their product-list
+//                    offsets (prefix sums) and data offsets.
+//  4. k_fill_stack   per row: the product stack (a_blk, b_blk), grouped by C
+//                    block and in ascending K inside each group.
+//  5. k_smm_f64      output-stationary batched small GEMM: one warp owns one C
+//                    block and sums its products in stack order (no atomics);
+//                    the epilogue applies alpha/beta and writes the block norm.
+//  6. filter         blocks with norm < eps dropped (diagonal kept), compaction.
+#include <algorithm>
+#include <cmath>
+
+#include "common.cuh"
+
+namespace dbg {
+
+// Largest number of block rows: the per-row bitmap and its rank table live in
+// shared memory (2 * 4 bytes per 32 block columns).
+constexpr int32_t kMaxBlockRows = 262144;
+
+namespace {
+
+constexpr int kSymThreads = 256;
+// Shared memory kept for per-row candidate accumulators (the rest goes to global).
+constexpr int kSymSmemBudget = 96 * 1024;
+
+__device__ __forceinline__ int block_excl_scan_int(int v, int* sh, int& total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sh[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int t = lane < nw ? sh[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        sh[lane] = t;
+    }
+    __syncthreads();
+    const int excl = (warp ? sh[warp - 1] : 0) + x - v;
+    total = sh[nw - 1];
+    __syncthreads();
+    return excl;
+}
+
+struct RowPattern {
+    const int64_t* a_rp; const int32_t* a_col;
+    const int64_t* b_rp; const int32_t* b_col;
+    const int64_t* c_rp; const int32_t* c_col;   // C_in pattern (beta != 0) or null
+};
+
+// Bitmap of the candidate block columns of row I; returns the candidate count
+// and fills wpre with the exclusive prefix popcount of the words.
+__device__ int build_row(const RowPattern& P, int32_t I, uint32_t* bm, int* wpre, int nwords, int* sh_scan) {
+    for (int w = threadIdx.x; w < nwords; w += blockDim.x) bm[w] = 0u;
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int64_t p = P.a_rp[I] + warp; p < P.a_rp[I + 1]; p += nw) {
+        const int32_t K = P.a_col[p];
+        for (int64_t q = P.b_rp[K] + lane; q < P.b_rp[K + 1]; q += 32) {
+            const int32_t J = P.b_col[q];
+            atomicOr(&bm[J >> 5], 1u << (J & 31));
+        }
+    }
+    if (P.c_col)
+        for (int64_t q = P.c_rp[I] + threadIdx.x; q < P.c_rp[I + 1]; q += blockDim.x) {
+            const int32_t J = P.c_col[q];
+            atomicOr(&bm[J >> 5], 1u << (J & 31));
+        }
+    __syncthreads();
+    const int per = (nwords + blockDim.x - 1) / blockDim.x;
+    const int lo = min(nwords, (int)threadIdx.x * per), hi = min(nwords, lo + per);
+    int s = 0;
+    for (int w = lo; w < hi; ++w) s += __popc(bm[w]);
+    int total;
+    int run = block_excl_scan_int(s, sh_scan, total);
+    for (int w = lo; w < hi; ++w) {
+        wpre[w] = run;
+        run += __popc(bm[w]);
+    }
+    __syncthreads();
+    return total;
+}
+
+__device__ __forceinline__ int rank_of(const uint32_t* bm, const int* wpre, int32_t J) {
+    return wpre[J >> 5] + __popc(bm[J >> 5] & ((1u << (J & 31)) - 1u));
+}
+
+__global__ void k_cand_count(int32_t nblk, RowPattern P, int nwords, int64_t* __restrict__ ccnt,
+                             unsigned long long* __restrict__ max_row) {
+    extern __shared__ uint32_t smem[];
+    __shared__ int sh_scan[32];
+    uint32_t* bm = smem;
+    int* wpre = (int*)(smem + nwords);
+    for (int32_t I = blockIdx.x; I < nblk; I += gridDim.x) {
+        const int n = build_row(P, I, bm, wpre, nwords, sh_scan);
+        if (threadIdx.x == 0) {
+            ccnt[I] = n;
+            atomicMax(max_row, (unsigned long long)n);
+        }
+        __syncthreads();
+    }
+}
+
+struct BoundArgs {
+    double abs_alpha, abs_beta, eps_lo;
+    const double* a_norm; const double* b_norm; const double* c_norm;
+    const int32_t* bs;
+    const int64_t* coff;
+    int32_t* cand_row; int32_t* cand_col;
+    double* bound; int32_t* pcnt; int32_t* ksum; int64_t* cin;
+    int32_t* keep;
+    int use_smem;
+};
+
+__global__ void k_cand_bound(int32_t nblk, RowPattern P, int nwords, BoundArgs B) {
+    extern __shared__ uint32_t smem[];
+    __shared__ int sh_scan[32];
+    uint32_t* bm = smem;
+    int* wpre = (int*)(smem + nwords);
+    double* sh_bound = (double*)(smem + 2 * ((nwords + 1) & ~1));
+    for (int32_t I = blockIdx.x; I < nblk; I += gridDim.x) {
+        const int nc = build_row(P, I, bm, wpre, nwords, sh_scan);
+        const int64_t cb = B.coff[I];
+        double* bnd = B.use_smem ? sh_bound : B.bound + cb;
+        int32_t* pc = B.use_smem ? (int32_t*)(sh_bound + nc) : B.pcnt + cb;
+        int32_t* ks = B.use_smem ? pc + nc : B.ksum + cb;
+        // candidates in ascending J
+        for (int w = threadIdx.x; w < nwords; w += blockDim.x) {
+            uint32_t bits = bm[w];
+            int r = wpre[w];
+            while (bits) {
+                const int b = __ffs(bits) - 1;
+                bits &= bits - 1u;
+                B.cand_col[cb + r] = 32 * w + b;
+                B.cand_row[cb + r] = I;
+                bnd[r] = 0.0;
+                pc[r] = 0;
+                ks[r] = 0;
+                if (B.cin) B.cin[cb + r] = -1;
+                ++r;
+            }
+        }
+        __syncthreads();
+        if (P.c_col)
+            for (int64_t q = P.c_rp[I] + threadIdx.x; q < P.c_rp[I + 1]; q += blockDim.x)
+                B.cin[cb + rank_of(bm, wpre, P.c_col[q])] = q;
+        __syncthreads();
+        // ascending K, one K at a time: every accumulator is updated in a fixed order
+        for (int64_t p = P.a_rp[I]; p < P.a_rp[I + 1]; ++p) {
+            const int32_t K = P.a_col[p];
+            const double na = B.abs_alpha * B.a_norm[p];
+            const int kk = B.bs[K];
+            for (int64_t q = P.b_rp[K] + threadIdx.x; q < P.b_rp[K + 1]; q += blockDim.x) {
+                const int r = rank_of(bm, wpre, P.b_col[q]);
+                bnd[r] = bnd[r] + na * B.b_norm[q];
+                pc[r] += 1;
+                ks[r] += kk;
+            }
+            __syncthreads();
+        }
+        for (int r = threadIdx.x; r < nc; r += blockDim.x) {
+            double b = bnd[r];
+            const int64_t ci = B.cin ? B.cin[cb + r] : -1;
+            if (ci >= 0) b += B.abs_beta * B.c_norm[ci];
+            const int32_t J = B.cand_col[cb + r];
+            B.keep[cb + r] = (J == I || b >= B.eps_lo) ? 1 : 0;
+            if (B.use_smem) {
+                B.pcnt[cb + r] = pc[r];
+                B.ksum[cb + r] = ks[r];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_form_meta(int64_t ncand, const int32_t* __restrict__ keep, const int64_t* __restrict__ kidx,
+                            const int32_t* __restrict__ cand_row, const int32_t* __restrict__ cand_col,
+                            const int32_t* __restrict__ pcnt, const int32_t* __restrict__ ksum,
+                            const int64_t* __restrict__ cin, const int32_t* __restrict__ bs,
+                            int32_t* __restrict__ f_row, int32_t* __restrict__ f_col, int64_t* __restrict__ f_area,
+                            int64_t* __restrict__ f_np, int64_t* __restrict__ f_cin,
+                            unsigned long long* __restrict__ flops) {
+    unsigned long long local = 0;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncand; c += (int64_t)gridDim.x * blockDim.x) {
+        if (!keep[c]) continue;
+        const int64_t k = kidx[c];
+        const int32_t I = cand_row[c], J = cand_col[c];
+        f_row[k] = I;
+        f_col[k] = J;
+        f_area[k] = (int64_t)bs[I] * bs[J];
+        f_np[k] = pcnt[c];
+        f_cin[k] = cin ? cin[c] : -1;
+        local += 2ull * (unsigned long long)bs[I] * (unsigned long long)bs[J] * (unsigned long long)ksum[c];
+    }
+    for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
+    if ((threadIdx.x & 31) == 0 && local) atomicAdd(flops, local);
+}
+
+__global__ void k_form_rp(int32_t nblk, const int64_t* __restrict__ coff, const int64_t* __restrict__ kidx,
+                          int64_t* __restrict__ f_rp) {
+    for (int32_t I = blockIdx.x * blockDim.x + threadIdx.x; I <= nblk; I += gridDim.x * blockDim.x)
+        f_rp[I] = kidx[coff[I]];
+}
+
+struct FillArgs {
+    const int64_t* coff;
+    const int32_t* keep;
+    const int64_t* kidx;
+    const int64_t* pbeg;
+    int32_t* cursor;
+    int32_t* prod_a; int32_t* prod_b;
+    int use_smem;
+};
+
+__global__ void k_fill_stack(int32_t nblk, RowPattern P, int nwords, FillArgs F) {
+    extern __shared__ uint32_t smem[];
+    __shared__ int sh_scan[32];
+    uint32_t* bm = smem;
+    int* wpre = (int*)(smem + nwords);
+    int32_t* sh_cur = (int32_t*)(smem + 2 * nwords);
+    for (int32_t I = blockIdx.x; I < nblk; I += gridDim.x) {
+        const int nc = build_row(P, I, bm, wpre, nwords, sh_scan);
+        const int64_t cb = F.coff[I];
+        const int64_t kb = F.kidx[cb];
+        const int nk = (int)(F.kidx[cb + nc] - kb);
+        int32_t* cur = F.use_smem ? sh_cur : F.cursor + kb;
+        for (int r = threadIdx.x; r < nk; r += blockDim.x) cur[r] = 0;
+        __syncthreads();
+        for (int64_t p = P.a_rp[I]; p < P.a_rp[I + 1]; ++p) {
+            const int32_t K = P.a_col[p];
+            for (int64_t q = P.b_rp[K] + threadIdx.x; q < P.b_rp[K + 1]; q += blockDim.x) {
+                const int64_t c = cb + rank_of(bm, wpre, P.b_col[q]);
+                if (!F.keep[c]) continue;
+                const int64_t k = F.kidx[c];
+                const int32_t at = cur[k - kb];
+                cur[k - kb] = at + 1;
+                const int64_t pos = F.pbeg[k] + at;
+                F.prod_a[pos] = (int32_t)p;
+                F.prod_b[pos] = (int32_t)q;
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// ----------------------------------------------------------------- FP64 SMM
+struct SmmArgs {
+    const int32_t* f_row; const int32_t* f_col; const int64_t* f_off; const int64_t* f_pbeg; const int64_t* f_cin;
+    const int32_t* prod_a; const int32_t* prod_b;
+    const int32_t* a_col; const int64_t* a_off; const double* a_data;
+    const int64_t* b_off; const double* b_data;
+    const int64_t* ci_off; const double* ci_data;
+    const int32_t* bs;
+    double alpha, beta;
+    double* c_data; double* c_norm; double* c_dev2;
+};
+
+template <int E>
+__device__ __forceinline__ void smm_block(const SmmArgs& S, int64_t k, int I, int J, int m, int n, int lane) {
+    const int mn = m * n;
+    int ii[E], jj[E];
+    double acc[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int idx = lane + 32 * e;
+        const int i = idx < mn ? idx / n : 0;
+        ii[e] = i;
+        jj[e] = idx < mn ? idx - i * n : 0;
+        acc[e] = 0.0;
+    }
+    const int64_t pe = S.f_pbeg[k + 1];
+    for (int64_t p = S.f_pbeg[k]; p < pe; ++p) {
+        const int32_t ai = S.prod_a[p], bi = S.prod_b[p];
+        const int kk = S.bs[S.a_col[ai]];
+        const double* __restrict__ A = S.a_data + S.a_off[ai];
+        const double* __restrict__ B = S.b_data + S.b_off[bi];
+        for (int t = 0; t < kk; ++t) {
+#pragma unroll
+            for (int e = 0; e < E; ++e) acc[e] = fma(__ldg(A + ii[e] * kk + t), __ldg(B + t * n + jj[e]), acc[e]);
+        }
+    }
+    const int64_t ci = S.f_cin[k];
+    const double* cin = ci >= 0 ? S.ci_data + S.ci_off[ci] : nullptr;
+    double* out = S.c_data + S.f_off[k];
+    double s = 0.0, d = 0.0;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int idx = lane + 32 * e;
+        if (idx < mn) {
+            double v = S.alpha * acc[e];
+            if (cin) v = v + S.beta * cin[idx];
+            out[idx] = v;
+            s = fma(v, v, s);
+            const double w = (I == J && ii[e] == jj[e]) ? v - 1.0 : v;
+            d = fma(w, w, d);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s += __shfl_xor_sync(0xffffffffu, s, o);
+        d += __shfl_xor_sync(0xffffffffu, d, o);
+    }
+    if (lane == 0) {
+        S.c_norm[k] = sqrt(s);
+        S.c_dev2[k] = d;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_smm_f64(int64_t nform, SmmArgs S) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t k = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); k < nform; k += warps) {
+        const int I = S.f_row[k], J = S.f_col[k];
+        const int m = S.bs[I], n = S.bs[J];
+        const int E = (m * n + 31) >> 5;
+        switch (E) {
+#define DBG_CASE(x) case x: smm_block<x>(S, k, I, J, m, n, lane); break;
+            DBG_CASE(1) DBG_CASE(2) DBG_CASE(3) DBG_CASE(4) DBG_CASE(5) DBG_CASE(6) DBG_CASE(7) DBG_CASE(8)
+            DBG_CASE(9) DBG_CASE(10) DBG_CASE(11) DBG_CASE(12) DBG_CASE(13) DBG_CASE(14) DBG_CASE(15) DBG_CASE(16)
+            DBG_CASE(17) DBG_CASE(18) DBG_CASE(19) DBG_CASE(20) DBG_CASE(21) DBG_CASE(22) DBG_CASE(23) DBG_CASE(24)
+            DBG_CASE(25) DBG_CASE(26) DBG_CASE(27) DBG_CASE(28) DBG_CASE(29) DBG_CASE(30) DBG_CASE(31) DBG_CASE(32)
+#undef DBG_CASE
+            default: break;
+        }
+    }
+}
+
+__global__ void k_keep_filter(int64_t nb, const int32_t* __restrict__ row, const int32_t* __restrict__ col,
+                              const double* __restrict__ norms, const double* __restrict__ dev2, double eps,
+                              int32_t* __restrict__ keep, double* __restrict__ dev2_kept) {
+    for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nb; b += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t k = (row[b] == col[b] || norms[b] >= eps) ? 1 : 0;
+        keep[b] = k;
+        dev2_kept[b] = k ? dev2[b] : 0.0;
+    }
+}
+
+struct EventSet {
+    cudaEvent_t e[4];
+    EventSet() {
+        for (auto& x : e) DBG_CK(cudaEventCreate(&x));
+    }
+    ~EventSet() {
+        for (auto& x : e) cudaEventDestroy(x);
+    }
+    float ms(int a, int b) {
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e[a], e[b]);
+        return t;
+    }
+};
+
+int sym_grid(int32_t nblk) { return std::min<int32_t>(nblk, 152 * 8); }
+
+}  // namespace
+
+void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbcsr_matrix_* C, double eps, int prec,
+              dbcsr_mult_stats* stats, bool want_dev2) {
+    check_finalized(A);
+    check_finalized(B);
+    if (!C) fail(DBCSR_EINVAL, "multiply: null C");
+    if (A->h_bs != B->h_bs || A->h_bs != C->h_bs) fail(DBCSR_EINVAL, "multiply: block sizes of A, B and C differ");
+    if (prec != DBCSR_FP64) fail(DBCSR_EINVAL, "multiply: precision not supported by this entry point");
+    if (!(eps >= 0.0)) fail(DBCSR_EINVAL, "multiply: eps_filter must be >= 0");
+    const bool use_c = (beta != 0.0);
+    if (use_c) check_finalized(C);
+    const int32_t nblk = A->nblk;
+    if (nblk > kMaxBlockRows) fail(DBCSR_ECAPACITY, "multiply: more than 262144 block rows");
+    cudaStream_t s = C->stream;
+    if (A->stream != s) DBG_CK(cudaStreamSynchronize(A->stream));
+    if (B->stream != s) DBG_CK(cudaStreamSynchronize(B->stream));
+
+    EventSet ev;
+    DBG_CK(cudaEventRecord(ev.e[0], s));
+    ensure_norms(A);
+    ensure_norms(B);
+    if (use_c) ensure_norms(C);
+
+    const int nwords = (nblk + 31) / 32;
+    const size_t sm_rank = (size_t)2 * ((nwords + 1) & ~1) * sizeof(uint32_t);
+    RowPattern P{A->rp.p, A->col.p, B->rp.p, B->col.p, use_c ? C->rp.p : nullptr, use_c ? C->col.p : nullptr};
+
+    // 1. candidate counts
+    DBuf<int64_t> ccnt, coff, maxrow;
+    ccnt.alloc(nblk, s);
+    coff.alloc(nblk + 1, s);
+    maxrow.alloc(1, s);
+    maxrow.zero();
+    {
+        const size_t sm = sm_rank;
+        if (sm > 48 * 1024) DBG_CK(cudaFuncSetAttribute(k_cand_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        k_cand_count<<<sym_grid(nblk), kSymThreads, sm, s>>>(nblk, P, nwords, ccnt.p, (unsigned long long*)maxrow.p);
+        DBG_LAUNCH_CK();
+    }
+    scan_exclusive(ccnt.p, coff.p, nblk, s);
+    int64_t h2[2];
+    {
+        const int64_t* src[2] = {coff.p + nblk, maxrow.p};
+        read_i64s(src, 2, h2, s);
+    }
+    const int64_t ncand = h2[0], max_row = h2[1];
+
+    // 2. candidates, bounds and the prescreen decision
+    DBuf<int32_t> cand_row, cand_col, pcnt, ksum, keep;
+    DBuf<double> bound;
+    DBuf<int64_t> cin, kidx;
+    const int64_t nc1 = std::max<int64_t>(ncand, 1);
+    cand_row.alloc(nc1, s);
+    cand_col.alloc(nc1, s);
+    pcnt.alloc(nc1, s);
+    ksum.alloc(nc1, s);
+    keep.alloc(nc1, s);
+    kidx.alloc(ncand + 1, s);
+    if (use_c) cin.alloc(nc1, s);
+    const size_t sm_acc = sm_rank + (size_t)max_row * (sizeof(double) + 2 * sizeof(int32_t));
+    const bool acc_smem = sm_acc <= (size_t)kSymSmemBudget;
+    if (!acc_smem) bound.alloc(nc1, s);
+    if (ncand) {
+        BoundArgs ba{std::fabs(alpha), std::fabs(beta), eps * (1.0 - 1e-12), A->norms.p, B->norms.p,
+                     use_c ? C->norms.p : nullptr, A->bs.p, coff.p, cand_row.p, cand_col.p,
+                     bound.p, pcnt.p, ksum.p, use_c ? cin.p : nullptr, keep.p, acc_smem ? 1 : 0};
+        const size_t sm = acc_smem ? sm_acc : sm_rank;
+        if (sm > 48 * 1024) DBG_CK(cudaFuncSetAttribute(k_cand_bound, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        k_cand_bound<<<sym_grid(nblk), kSymThreads, sm, s>>>(nblk, P, nwords, ba);
+        DBG_LAUNCH_CK();
+    }
+    scan_exclusive(keep.p, kidx.p, ncand, s);
+    const int64_t nform = read_i64(kidx.p + ncand, s);
+
+    // 3. formed-block metadata
+    const int64_t nf1 = std::max<int64_t>(nform, 1);
+    DBuf<int32_t> f_row, f_col;
+    DBuf<int64_t> f_area, f_np, f_cin, f_off, f_pbeg, f_rp, flops;
+    f_row.alloc(nf1, s);
+    f_col.alloc(nf1, s);
+    f_area.alloc(nf1, s);
+    f_np.alloc(nf1, s);
+    f_cin.alloc(nf1, s);
+    f_off.alloc(nform + 1, s);
+    f_pbeg.alloc(nform + 1, s);
+    f_rp.alloc(nblk + 1, s);
+    flops.alloc(1, s);
+    flops.zero();
+    if (ncand) {
+        k_form_meta<<<grid_for(ncand, 256), 256, 0, s>>>(ncand, keep.p, kidx.p, cand_row.p, cand_col.p, pcnt.p, ksum.p,
+                                                         use_c ? cin.p : nullptr, A->bs.p, f_row.p, f_col.p, f_area.p,
+                                                         f_np.p, f_cin.p, (unsigned long long*)flops.p);
+        DBG_LAUNCH_CK();
+    }
+    k_form_rp<<<grid_for(nblk + 1, 256), 256, 0, s>>>(nblk, coff.p, kidx.p, f_rp.p);
+    DBG_LAUNCH_CK();
+    scan_exclusive(f_area.p, f_off.p, nform, s);
+    scan_exclusive(f_np.p, f_pbeg.p, nform, s);
+    int64_t h3[3];
+    {
+        const int64_t* src[3] = {f_off.p + nform, f_pbeg.p + nform, flops.p};
+        read_i64s(src, 3, h3, s);
+    }
+    const int64_t nel = h3[0], nprod = h3[1];
+    const double nflop = (double)(unsigned long long)h3[2];
+
+    // 4. product stacks
+    DBuf<int32_t> prod_a, prod_b, cursor;
+    prod_a.alloc(std::max<int64_t>(nprod, 1), s);
+    prod_b.alloc(std::max<int64_t>(nprod, 1), s);
+    const size_t sm_fill = sm_rank + (size_t)max_row * sizeof(int32_t);
+    const bool fill_smem = sm_fill <= (size_t)kSymSmemBudget;
+    if (!fill_smem) cursor.alloc(nf1, s);
+    if (nprod) {
+        FillArgs fa{coff.p, keep.p, kidx.p, f_pbeg.p, cursor.p, prod_a.p, prod_b.p, fill_smem ? 1 : 0};
+        const size_t sm = fill_smem ? sm_fill : sm_rank;
+        if (sm > 48 * 1024) DBG_CK(cudaFuncSetAttribute(k_fill_stack, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        k_fill_stack<<<sym_grid(nblk), kSymThreads, sm, s>>>(nblk, P, nwords, fa);
+        DBG_LAUNCH_CK();
+    }
+    // the candidate arrays are no longer needed
+    cand_row.release(); cand_col.release(); pcnt.release(); ksum.release(); bound.release(); cursor.release();
+    DBG_CK(cudaEventRecord(ev.e[1], s));
+
+    // 5. numeric
+    DBuf<double> c_data, c_norm, c_dev2;
+    c_data.alloc(std::max<int64_t>(nel, 1), s);
+    c_norm.alloc(nf1, s);
+    c_dev2.alloc(nf1, s);
+    if (nform) {
+        SmmArgs sa{f_row.p, f_col.p, f_off.p, f_pbeg.p, f_cin.p, prod_a.p, prod_b.p, A->col.p, A->off.p, A->data.p,
+                   B->off.p, B->data.p, use_c ? C->off.p : nullptr, use_c ? C->data.p : nullptr, A->bs.p,
+                   alpha, beta, c_data.p, c_norm.p, c_dev2.p};
+        k_smm_f64<<<grid_for(nform, 8, 152 * 16), 256, 0, s>>>(nform, sa);
+        DBG_LAUNCH_CK();
+    }
+    DBG_CK(cudaEventRecord(ev.e[2], s));
+    prod_a.release(); prod_b.release();
+
+    // install the formed blocks as C (A or B may alias C: every read above is queued before)
+    C->rp = std::move(f_rp);
+    C->row = std::move(f_row);
+    C->col = std::move(f_col);
+    C->off = std::move(f_off);
+    C->data = std::move(c_data);
+    C->nnzb = nform;
+    C->nel = nel;
+    C->norms = std::move(c_norm);
+    C->norms_valid = true;
+    C->finalized = true;
+
+    // 6. filter
+    DBuf<int32_t> keep2;
+    DBuf<double> dev2k, dsum;
+    keep2.alloc(nf1, s);
+    dev2k.alloc(nf1, s);
+    dsum.alloc(1, s);
+    if (nform) {
+        k_keep_filter<<<grid_for(nform, 256), 256, 0, s>>>(nform, C->row.p, C->col.p, C->norms.p, c_dev2.p, eps,
+                                                           keep2.p, dev2k.p);
+        DBG_LAUNCH_CK();
+    }
+    if (want_dev2) det_sum(dev2k.p, nform, dsum.p, s);
+    compact(C, keep2.p, C->norms.p);
+    DBG_CK(cudaEventRecord(ev.e[3], s));
+
+    if (stats) {
+        DBG_CK(cudaStreamSynchronize(s));
+        stats->n_candidates = ncand;
+        stats->n_formed = nform;
+        stats->n_kept = C->nnzb;
+        stats->n_products = nprod;
+        stats->flops = nflop;
+        stats->dev2_filtered = want_dev2 ? read_f64(dsum.p, s) : 0.0;
+        stats->ms_symbolic = ev.ms(0, 1);
+        stats->ms_numeric = ev.ms(1, 2);
+        stats->ms_filter = ev.ms(2, 3);
+    }
+}
+
+}  // namespace dbg

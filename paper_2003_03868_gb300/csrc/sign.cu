@@ -1,0 +1,112 @@
+// Density matrix by the second-order Newton-Schulz sign iteration
+// (section "Sign-Method": sign(A) = A (A^2)^(-1/2), P = (1 - sign(H - mu 1)) / 2
+// with S = 1, eps_filter truncation after every product).
+//
+//   X_0 = (H - mu 1) / alpha,  alpha = Gershgorin bound of H - mu 1
+//   repeat:  X2 = filter(X X);  r = ||X2 - 1||_F / N;  stop when r < tol
+//            X  = filter(1.5 X - 0.5 X X2)       ( = X (3 - X^2) / 2 )
+//   P = (1 - X) / 2,  Tr(P),  E_band = Tr(P H)
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <memory>
+
+#include "common.cuh"
+
+namespace dbg {
+
+namespace {
+
+std::unique_ptr<dbcsr_matrix_> make_like(const dbcsr_matrix_* m, cudaStream_t s) {
+    auto x = std::make_unique<dbcsr_matrix_>();
+    x->nblk = m->nblk;
+    x->n = m->n;
+    x->stream = s;
+    x->h_bs = m->h_bs;
+    x->bs.alloc(m->nblk, s);
+    DBG_CK(cudaMemcpyAsync(x->bs.p, m->bs.p, sizeof(int32_t) * m->nblk, cudaMemcpyDeviceToDevice, s));
+    return x;
+}
+
+}  // namespace
+
+dbcsr_status sign_iterate(dbcsr_matrix_* H, double mu, const dbcsr_sign_opts* opts, dbcsr_matrix_* P,
+                          dbcsr_sign_report* rep) {
+    check_finalized(H);
+    if (!P) fail(DBCSR_EINVAL, "sign_iterate: null P_out");
+    if (P->h_bs != H->h_bs) fail(DBCSR_EINVAL, "sign_iterate: P_out block sizes differ from H");
+    dbcsr_sign_opts o{};
+    o.eps_filter = 0.0;
+    o.tol = 1e-9;
+    o.max_iter = 100;
+    o.prec = DBCSR_FP64;
+    o.stall_after = 1e-2;
+    if (opts) o = *opts;
+    if (o.max_iter <= 0) o.max_iter = 100;
+    if (o.stall_after <= 0) o.stall_after = 1e-2;
+    if (!(o.eps_filter >= 0) || !(o.tol > 0)) fail(DBCSR_EINVAL, "sign_iterate: need eps_filter >= 0 and tol > 0");
+    if (o.prec != DBCSR_FP64) fail(DBCSR_EINVAL, "sign_iterate: precision policy not supported");
+
+    const auto t0 = std::chrono::steady_clock::now();
+    cudaStream_t s = H->stream;
+    const double N = (double)H->n;
+    const double alpha = gershgorin(H, mu);
+    if (!(alpha > 0) || !std::isfinite(alpha)) fail(DBCSR_EINVAL, "sign_iterate: Gershgorin bound is zero or not finite");
+
+    auto X = make_like(H, s);
+    auto X2 = make_like(H, s);
+    copy_matrix(X.get(), H);
+    scale_shift(X.get(), 1.0 / alpha, -mu / alpha);
+
+    dbcsr_sign_report r{};
+    r.alpha = alpha;
+    int it = 0;
+    bool converged = false, stalled = false;
+    double res = 0.0;
+    while (it < o.max_iter) {
+        dbcsr_mult_stats st{};
+        multiply(1.0, X.get(), X.get(), 0.0, X2.get(), o.eps_filter, DBCSR_FP64, &st, true);
+        res = std::sqrt(st.dev2_filtered) / N;
+        r.flops += st.flops;
+        r.n_products += st.n_products;
+        r.ms_multiply += st.ms_numeric;
+        if (it < DBCSR_MAX_HISTORY) r.residual_history[it] = res;
+        ++it;
+        if (!std::isfinite(res)) fail(DBCSR_ENAN, "sign_iterate: residual is not finite");
+        if (o.verbose)
+            std::fprintf(stderr, "[sign] it %3d r %.3e nnzb(X) %lld cand %lld formed %lld kept %lld %.1f GF %.2f ms\n",
+                         it, res, (long long)X->nnzb, (long long)st.n_candidates, (long long)st.n_formed,
+                         (long long)st.n_kept, st.flops * 1e-9, st.ms_numeric);
+        if (res < o.tol) {
+            converged = true;
+            if (it - 1 < DBCSR_MAX_HISTORY) r.nnzb_history[it - 1] = X->nnzb;
+            break;
+        }
+        if (it >= 3 && r.residual_history[it - 3] < o.stall_after && res > 0.5 * r.residual_history[it - 3]) {
+            stalled = true;
+            if (it - 1 < DBCSR_MAX_HISTORY) r.nnzb_history[it - 1] = X->nnzb;
+            break;
+        }
+        multiply(-0.5, X.get(), X2.get(), 1.5, X.get(), o.eps_filter, DBCSR_FP64, &st, false);
+        r.flops += st.flops;
+        r.n_products += st.n_products;
+        r.ms_multiply += st.ms_numeric;
+        if (it - 1 < DBCSR_MAX_HISTORY) r.nnzb_history[it - 1] = X->nnzb;
+    }
+    copy_matrix(P, X.get());
+    scale_shift(P, -0.5, 0.5);
+    r.trace_p = trace(P);
+    r.e_band = trace_product(P, H);
+    DBG_CK(cudaStreamSynchronize(s));
+    DBG_CK(cudaStreamSynchronize(P->stream));
+    r.iterations = it;
+    r.converged = converged ? 1 : 0;
+    r.stalled = stalled ? 1 : 0;
+    r.residual = res;
+    r.nnzb_x = X->nnzb;
+    r.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (rep) *rep = r;
+    return converged ? DBCSR_OK : DBCSR_ENOTCONV;
+}
+
+}  // namespace dbg

@@ -1,0 +1,107 @@
+"""GPU parity of the Newton-Schulz sign iteration against the FP64 oracle."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import bsr, sign
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+DE_ATOM = 1e-6          # Ha/atom, band-energy tolerance of a converged P
+
+
+@pytest.fixture(scope="module")
+def gb():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2003_03868_gb300 as m
+    m.lib()
+    return m
+
+
+@pytest.mark.parametrize("n_mol,basis,eps,tol", [(8, (13, 5), 0.0, 1e-12), (24, (13, 5), 1e-7, 1e-8),
+                                                 (16, (23, 7), 1e-6, 1e-7), (40, (13, 5), 1e-5, 1e-7)])
+def test_sign_matches_oracle(gb, n_mol, basis, eps, tol):
+    h = synth.build_hamiltonian(synth.small(n_mol, basis=basis, seed=777 + n_mol))
+    H = gb.Matrix.of(h.H)
+    g = gb.sign_iterate(H, 0.0, eps, tol)
+    o = sign.sign_iterate(bsr.Mat.of(h.H), 0.0, eps, tol)
+    assert g.report.alpha == pytest.approx(o.alpha, rel=1e-15)
+    assert bool(g.report.converged) == o.converged
+    assert g.report.iterations == o.iterations
+    np.testing.assert_allclose(g.residuals, o.residuals, rtol=1e-6, atol=1e-13)
+    assert abs(g.report.e_band - o.e_band) / h.n_atoms < 1e-10
+    assert g.report.trace_p == pytest.approx(o.trace_p, abs=1e-9)
+    if o.converged:
+        assert g.report.trace_p == pytest.approx(h.n_occ, abs=1e-5)
+    rp, col, data = g.P.export()
+    # same pattern unless a block norm sits at eps within rounding
+    if np.array_equal(col, o.P.col):
+        assert np.linalg.norm(data - o.P.data) / np.linalg.norm(o.P.data) < 1e-9
+
+
+def test_sign_against_dense_eigh(gb):
+    h = synth.build_hamiltonian(synth.small(10, seed=4321))
+    Hd = bsr.to_dense(bsr.Mat.of(h.H))
+    w, Q = np.linalg.eigh(Hd)
+    Pd = 0.5 * (np.eye(Hd.shape[0]) - Q @ np.diag(np.sign(w)) @ Q.T)
+    g = gb.sign_iterate(gb.Matrix.of(h.H), 0.0, 0.0, 1e-13)
+    rp, col, data = g.P.export()
+    P = bsr.to_dense(bsr.Mat(h.H.blk_size, rp, col, data))
+    assert np.linalg.norm(P - Pd) / np.linalg.norm(Pd) < 1e-11
+    assert np.linalg.norm(P @ P - P) < 1e-10
+
+
+def test_not_converged_is_reported(gb):
+    h = synth.build_hamiltonian(synth.small(12, seed=9001))
+    g = gb.sign_iterate(gb.Matrix.of(h.H), 0.0, 0.05, 1e-14, max_iter=40)
+    assert g.status == 6 and not g.converged
+    assert g.report.stalled or g.report.iterations == 40
+    with pytest.raises(gb.DbcsrError):
+        gb.sign_iterate(gb.Matrix.of(h.H), 0.0, 0.05, 1e-14, max_iter=5, raise_on_notconv=True)
+
+
+@pytest.mark.slow
+def test_sign_1024_waters_full_size(gb):
+    """1,024 waters (N = 23,552), eps 1e-7, tol 1e-9: the configuration the benchmark times.
+
+    Checked against the oracle's band energy stored by tests/golden/make_golden.py
+    (when present), the exact occupation Tr(P) = 4,096, and sampled blocks of the
+    first product recomputed by the oracle one at a time."""
+    w = synth.SIGN_1024
+    h = synth.build_hamiltonian(w)
+    H = gb.Matrix.of(h.H)
+    g = gb.sign_iterate(H, 0.0, w.eps_filter, w.tol)
+    assert g.converged
+    assert g.report.trace_p == pytest.approx(4096, abs=1e-4)
+    gold = os.path.join(HERE, "golden", "sign_1024h2o.json")
+    if os.path.exists(gold):
+        ref = json.load(open(gold))
+        assert abs(g.report.e_band - ref["e_band"]) / h.n_atoms < DE_ATOM
+        assert abs(g.report.iterations - ref["iterations"]) <= 1
+    # sampled outputs of the first product X0.X0 (unfiltered values of formed blocks)
+    Ho = bsr.Mat.of(h.H)
+    alpha = g.report.alpha
+    X0 = bsr.add_identity(Ho, 1.0 / alpha, 0.0)
+    Xg = gb.Matrix.of(h.H)
+    Xg.scale_shift(1.0 / alpha, 0.0)
+    C = gb.Matrix(Xg.blk_size, Xg.stream)
+    gb.multiply(1.0, Xg, Xg, 0.0, C, w.eps_filter)
+    rp, col, data = C.export()
+    Cg = bsr.Mat(h.H.blk_size, rp, col, data)
+    rng = np.random.default_rng(5)
+    rows = rng.integers(0, Ho.nblk, 40)
+    for I in rows:
+        for q in rng.choice(np.arange(rp[I], rp[I + 1]), size=3, replace=False):
+            J = int(col[q])
+            ref = bsr.product_block(int(I), J, 1.0, X0, X0)
+            got = Cg.block(int(I), J)
+            assert np.linalg.norm(got - ref) <= REL * np.linalg.norm(ref) + 1e-300
+
+
+REL = 1e-12
