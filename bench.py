@@ -91,23 +91,21 @@ class Clocks:
                 "samples": len(rows)}
 
 
-def oracle_sample(h, w, rows_frac: float, reps: int = 1):
-    """The oracle's first product X0.X0 on the first block rows of X0 (a bounded sample)."""
-    import numpy as np
-    from oracle import bsr
+def oracle_sample(h, w, steps: int):
+    """The oracle's FP64 sign iteration on the same H, stopped after ``steps``
+    Newton-Schulz steps (2 products each): a bounded sample of the workload."""
+    from oracle import bsr, sign
     Ho = bsr.Mat.of(h.H)
-    alpha = float(bsr.abs_row_sums(Ho, 0.0).max())
-    X = bsr.add_identity(Ho, 1.0 / alpha, 0.0)
-    R = max(1, int(X.nblk * rows_frac))
-    keep = X.rows < R
-    Xs = bsr.select_blocks(X, keep)
     t0 = time.perf_counter()
-    flops = 0
-    for _ in range(reps):
-        _, info = bsr.multiply(1.0, Xs, X, eps=w.eps_filter, info=True)
-        flops += info.flops
+    r = sign.sign_iterate(Ho, h.mu, w.eps_filter, w.tol, max_iter=steps)
     dt = time.perf_counter() - t0
-    return flops, dt, R, bsr.num_threads()
+    return r.flops, dt, bsr.num_threads()
+
+
+def sample_text(steps, flops, dt):
+    return (f"first {steps} Newton-Schulz steps ({2 * steps} products) of the oracle's FP64 sign iteration "
+            f"on the full H ({flops / 1e9:.0f} GFLOP executed in {dt:.1f} s; the oracle forms every candidate "
+            f"block, no prescreen)")
 
 
 def run_reference(args):
@@ -117,17 +115,15 @@ def run_reference(args):
     import synth
     w = synth.SIGN_1024
     h = synth.build_hamiltonian(w)
-    frac = args.ref_rows
     for _ in range(args.warmup):
-        oracle_sample(h, w, frac)
+        oracle_sample(h, w, args.ref_steps)
     tot_f, tot_t = 0, 0.0
     for _ in range(args.steps):
-        f, dt, R, cores = oracle_sample(h, w, frac)
+        f, dt, cores = oracle_sample(h, w, args.ref_steps)
         tot_f += f
         tot_t += dt
     value = tot_f / tot_t / 1e12
-    sample = (f"first product X0.X0 of the FP64 sign iteration restricted to block rows [0, {R}) of {h.H.nblk} "
-              f"(no prescreen, eps {w.eps_filter}), one per step")
+    sample = sample_text(args.ref_steps, f, dt) + ", one per step"
     out = {"metric": "block-GEMM TFLOP/s (FP64 sign iteration, time-to-P)", "value": value, "unit": "TFLOP/s",
            "impl": "reference", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": tot_t / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
@@ -148,7 +144,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU-baseline leg")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--ref-rows", type=float, default=0.4, help="fraction of block rows in the oracle sample")
+    ap.add_argument("--ref-steps", type=int, default=1, help="Newton-Schulz steps per oracle sample (reference arm)")
+    ap.add_argument("--cpu-steps", type=int, default=2, help="Newton-Schulz steps in the oracle CPU baseline")
+    ap.add_argument("--workload", default="sign-1024h2o", choices=["sign-1024h2o", "sign-512h2o"],
+                    help="sign-512h2o: a smaller case for profiler captures")
     ap.add_argument("--verbose", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -182,7 +181,8 @@ def main():
         gb.lib()
     import synth
 
-    w = synth.SIGN_1024
+    w = synth.SIGN_1024 if args.workload == "sign-1024h2o" else synth.Workload(
+        "sign-512h2o-dzvp-fp64", 512, (13, 5), synth.configs.BASE_SEED + 12, 1e-7, 1e-9)
     h = synth.build_hamiltonian(w)
     stream = torch.cuda.current_stream()
     H = gb.Matrix.of(h.H, stream=stream.cuda_stream)
@@ -270,10 +270,9 @@ def main():
            "e_band": ebands[-1], "gpu_launches": launches, "clocks": clk, "roofline": roofline, "e2e": e2e}
 
     if rank == 0 and world == 1 and not args.no_cpu:
-        f, dt, R, cores = oracle_sample(h, w, args.ref_rows)
+        f, dt, cores = oracle_sample(h, w, args.cpu_steps)
         out["cpu_baseline"] = {"value": f / dt / 1e12, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
-                               "sample": f"first product X0.X0 on block rows [0, {R}) of {h.H.nblk} "
-                                         f"({f / 1e9:.1f} GFLOP executed in {dt:.1f} s, no prescreen)"}
+                               "sample": sample_text(args.cpu_steps, f, dt)}
     if rank == 0:
         print(json.dumps(out))
     if dist:

@@ -82,7 +82,7 @@ typedef struct {
     int32_t max_iter;          /* at most this many steps (default 100 when <= 0) */
     int32_t prec;              /* dbcsr_prec: DBCSR_FP64 or DBCSR_MIXED */
     double switch_tol;         /* DBCSR_MIXED: residual below which FP64 takes over (e.g. 1e-4) */
-    double stall_after;        /* stall test active once r < stall_after (default 1e-2 when <= 0) */
+    double stall_ratio;        /* stall test: r_k > ratio*r_{k-1} after r_{k-1} < ratio*r_{k-2} (default 0.5 when <= 0) */
     int32_t verbose;           /* 1: print one line per step to stderr */
     int32_t reserved;
 } dbcsr_sign_opts;
@@ -116,7 +116,7 @@ const char* dbcsr_version(void);
 
 /*
  * Creates an empty matrix with nblk block rows/columns of edges blk_size[0..nblk-1]
- * (host array, each in [1, 64]).  stream: a cudaStream_t (NULL = the legacy
+ * (host array, each in [1, 32]).  stream: a cudaStream_t (NULL = the legacy
  * default stream); all work on the matrix is queued there.  The matrix starts
  * in the "building" state: blocks are added with put_block(s), then finalize().
  */

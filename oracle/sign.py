@@ -19,9 +19,11 @@ Readings taken where the paper is silent:
   filtered product (the paper flushes small elements after every product, so
   X2 is the square the method holds), stops when r < tol, and otherwise sets
   T = 3 1 - X2 and X <- filter(X T / 2) (product on the right);
-* at most ``max_iter`` steps; once r < 1e-2, a step whose residual exceeds half
-  of the residual two steps earlier means filtering has stalled the iteration
-  (reported, not raised);
+* at most ``max_iter`` steps.  Without filtering every eigenvalue moves toward
+  +-1 monotonically and the residual ratio r_k / r_{k-1} only falls, so once a
+  step has cut the residual by more than half, the next one must too; a step
+  that does not (r_k > r_{k-1} / 2 after r_{k-1} < r_{k-2} / 2) means filtering
+  has stalled the iteration (reported, not raised);
 * Tr(P) = (N - Tr X) / 2 and the band energy is E = Tr(P H), with no spin factor.
 """
 from __future__ import annotations
@@ -57,7 +59,7 @@ def gershgorin(H: bsr.Mat, mu: float) -> float:
 
 
 def sign_iterate(H: bsr.Mat, mu: float, eps: float, tol: float, max_iter: int = 100,
-                 stall_after: float = 1e-2) -> SignResult:
+                 stall_ratio: float = 0.5) -> SignResult:
     t0 = time.perf_counter()
     n = H.n
     alpha = gershgorin(H, mu)
@@ -75,7 +77,7 @@ def sign_iterate(H: bsr.Mat, mu: float, eps: float, tol: float, max_iter: int = 
         if r < tol:
             converged = True
             break
-        if len(res) >= 3 and res[-3] < stall_after and r > 0.5 * res[-3]:
+        if len(res) >= 3 and res[-2] < stall_ratio * res[-3] and r > stall_ratio * res[-2]:
             stalled = True
             break
         T = bsr.add_identity(X2, -1.0, 3.0)                        # 3 1 - X^2

@@ -192,11 +192,11 @@ class SignResult:
 
 
 def sign_iterate(H: Matrix, mu: float, eps_filter: float, tol: float, max_iter: int = 100,
-                 prec: int = DBCSR_FP64, switch_tol: float = 1e-4, stall_after: float = 1e-2,
+                 prec: int = DBCSR_FP64, switch_tol: float = 1e-4, stall_ratio: float = 0.5,
                  P: Matrix | None = None, verbose: bool = False, raise_on_notconv: bool = False) -> SignResult:
     """Density matrix P = (1 - sign(H - mu 1)) / 2 by the Newton-Schulz iteration."""
     P = Matrix(H.blk_size, H.stream) if P is None else P
-    o = SignOpts(float(eps_filter), float(tol), int(max_iter), int(prec), float(switch_tol), float(stall_after),
+    o = SignOpts(float(eps_filter), float(tol), int(max_iter), int(prec), float(switch_tol), float(stall_ratio),
                  1 if verbose else 0, 0)
     rep = SignReport()
     st = lib().dbcsr_sign_iterate(H.handle, float(mu), C.byref(o), P.handle, C.byref(rep))

@@ -24,7 +24,7 @@ class MultStats(C.Structure):
 
 class SignOpts(C.Structure):
     _fields_ = [("eps_filter", C.c_double), ("tol", C.c_double), ("max_iter", C.c_int32), ("prec", C.c_int32),
-                ("switch_tol", C.c_double), ("stall_after", C.c_double), ("verbose", C.c_int32),
+                ("switch_tol", C.c_double), ("stall_ratio", C.c_double), ("verbose", C.c_int32),
                 ("reserved", C.c_int32)]
 
 

@@ -40,10 +40,10 @@ dbcsr_status sign_iterate(dbcsr_matrix_* H, double mu, const dbcsr_sign_opts* op
     o.tol = 1e-9;
     o.max_iter = 100;
     o.prec = DBCSR_FP64;
-    o.stall_after = 1e-2;
+    o.stall_ratio = 0.5;
     if (opts) o = *opts;
     if (o.max_iter <= 0) o.max_iter = 100;
-    if (o.stall_after <= 0) o.stall_after = 1e-2;
+    if (o.stall_ratio <= 0) o.stall_ratio = 0.5;
     if (!(o.eps_filter >= 0) || !(o.tol > 0)) fail(DBCSR_EINVAL, "sign_iterate: need eps_filter >= 0 and tol > 0");
     if (o.prec != DBCSR_FP64) fail(DBCSR_EINVAL, "sign_iterate: precision policy not supported");
 
@@ -82,7 +82,10 @@ dbcsr_status sign_iterate(dbcsr_matrix_* H, double mu, const dbcsr_sign_opts* op
             if (it - 1 < DBCSR_MAX_HISTORY) r.nnzb_history[it - 1] = X->nnzb;
             break;
         }
-        if (it >= 3 && r.residual_history[it - 3] < o.stall_after && res > 0.5 * r.residual_history[it - 3]) {
+        // without filtering r_k / r_{k-1} only falls: a fast step followed by a slow one is a stall
+        if (it >= 3 && it - 1 < DBCSR_MAX_HISTORY &&
+            r.residual_history[it - 2] < o.stall_ratio * r.residual_history[it - 3] &&
+            res > o.stall_ratio * r.residual_history[it - 2]) {
             stalled = true;
             if (it - 1 < DBCSR_MAX_HISTORY) r.nnzb_history[it - 1] = X->nnzb;
             break;
