@@ -22,6 +22,8 @@
 //  6. filter         blocks with norm < eps dropped (diagonal kept), compaction.
 #include <algorithm>
 #include <cmath>
+#include <utility>
+#include <vector>
 
 #include "common.cuh"
 
@@ -200,7 +202,7 @@ __global__ void k_form_meta(int64_t ncand, const int32_t* __restrict__ keep, con
                             const int64_t* __restrict__ cin, const int32_t* __restrict__ bs,
                             int32_t* __restrict__ f_row, int32_t* __restrict__ f_col, int64_t* __restrict__ f_area,
                             int64_t* __restrict__ f_np, int64_t* __restrict__ f_cin,
-                            unsigned long long* __restrict__ flops) {
+                            unsigned long long* __restrict__ flops, unsigned long long* __restrict__ class_cnt) {
     unsigned long long local = 0;
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncand; c += (int64_t)gridDim.x * blockDim.x) {
         if (!keep[c]) continue;
@@ -212,6 +214,7 @@ __global__ void k_form_meta(int64_t ncand, const int32_t* __restrict__ keep, con
         f_np[k] = pcnt[c];
         f_cin[k] = cin ? cin[c] : -1;
         local += 2ull * (unsigned long long)bs[I] * (unsigned long long)bs[J] * (unsigned long long)ksum[c];
+        atomicAdd(class_cnt + ((bs[I] * bs[J] + 31) >> 5), 1ull);
     }
     for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
     if ((threadIdx.x & 31) == 0 && local) atomicAdd(flops, local);
@@ -276,75 +279,110 @@ struct SmmArgs {
     double* c_data; double* c_norm; double* c_dev2;
 };
 
+// Shape class of a C block: E = ceil(m*n / 32) accumulators per lane.
+__device__ __forceinline__ int shape_class(int m, int n) { return (m * n + 31) >> 5; }
+
+// One warp per C block of class E (m*n <= 32*E): lane l owns elements l, l+32,
+// ..., sums its products in stack order (ascending K, then k) with FMA, and
+// writes alpha*sum + beta*C_in plus the block's norm and distance to 1.  The
+// lanes first fetch the metadata of 32 products at once (one product each:
+// block offsets and inner size) and broadcast it with shuffles, so the
+// dependent index loads are not paid product by product.
 template <int E>
-__device__ __forceinline__ void smm_block(const SmmArgs& S, int64_t k, int I, int J, int m, int n, int lane) {
-    const int mn = m * n;
-    int ii[E], jj[E];
-    double acc[E];
+__global__ void __launch_bounds__(256) k_smm_f64(int64_t nlist, const int64_t* __restrict__ list, SmmArgs S) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < nlist; w += warps) {
+        const int64_t k = list[w];
+        const int I = S.f_row[k], J = S.f_col[k];
+        const int m = S.bs[I], n = S.bs[J];
+        const int mn = m * n;
+        int ii[E], jj[E];
+        double acc[E];
 #pragma unroll
-    for (int e = 0; e < E; ++e) {
-        const int idx = lane + 32 * e;
-        const int i = idx < mn ? idx / n : 0;
-        ii[e] = i;
-        jj[e] = idx < mn ? idx - i * n : 0;
-        acc[e] = 0.0;
-    }
-    const int64_t pe = S.f_pbeg[k + 1];
-    for (int64_t p = S.f_pbeg[k]; p < pe; ++p) {
-        const int32_t ai = S.prod_a[p], bi = S.prod_b[p];
-        const int kk = S.bs[S.a_col[ai]];
-        const double* __restrict__ A = S.a_data + S.a_off[ai];
-        const double* __restrict__ B = S.b_data + S.b_off[bi];
-        for (int t = 0; t < kk; ++t) {
-#pragma unroll
-            for (int e = 0; e < E; ++e) acc[e] = fma(__ldg(A + ii[e] * kk + t), __ldg(B + t * n + jj[e]), acc[e]);
+        for (int e = 0; e < E; ++e) {
+            const int idx = lane + 32 * e;
+            const int i = idx < mn ? idx / n : 0;
+            ii[e] = i;
+            jj[e] = idx < mn ? idx - i * n : 0;
+            acc[e] = 0.0;
         }
-    }
-    const int64_t ci = S.f_cin[k];
-    const double* cin = ci >= 0 ? S.ci_data + S.ci_off[ci] : nullptr;
-    double* out = S.c_data + S.f_off[k];
-    double s = 0.0, d = 0.0;
+        const int64_t pb = S.f_pbeg[k], pe = S.f_pbeg[k + 1];
+        for (int64_t base = pb; base < pe; base += 32) {
+            const int cnt = (int)min((int64_t)32, pe - base);
+            int64_t ao = 0, bo = 0;
+            int kq = 0;
+            if (lane < cnt) {
+                const int32_t ai = S.prod_a[base + lane], bi = S.prod_b[base + lane];
+                ao = S.a_off[ai];
+                bo = S.b_off[bi];
+                kq = S.bs[S.a_col[ai]];
+            }
+            for (int q = 0; q < cnt; ++q) {
+                const int64_t aoq = __shfl_sync(0xffffffffu, ao, q);
+                const int64_t boq = __shfl_sync(0xffffffffu, bo, q);
+                const int kk = __shfl_sync(0xffffffffu, kq, q);
+                const double* __restrict__ A = S.a_data + aoq;
+                const double* __restrict__ B = S.b_data + boq;
+                for (int t = 0; t < kk; ++t) {
 #pragma unroll
-    for (int e = 0; e < E; ++e) {
-        const int idx = lane + 32 * e;
-        if (idx < mn) {
-            double v = S.alpha * acc[e];
-            if (cin) v = v + S.beta * cin[idx];
-            out[idx] = v;
-            s = fma(v, v, s);
-            const double w = (I == J && ii[e] == jj[e]) ? v - 1.0 : v;
-            d = fma(w, w, d);
+                    for (int e = 0; e < E; ++e)
+                        acc[e] = fma(__ldg(A + ii[e] * kk + t), __ldg(B + t * n + jj[e]), acc[e]);
+                }
+            }
         }
-    }
+        const int64_t ci = S.f_cin[k];
+        const double* cin = ci >= 0 ? S.ci_data + S.ci_off[ci] : nullptr;
+        double* out = S.c_data + S.f_off[k];
+        double sq = 0.0, d = 0.0;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        s += __shfl_xor_sync(0xffffffffu, s, o);
-        d += __shfl_xor_sync(0xffffffffu, d, o);
-    }
-    if (lane == 0) {
-        S.c_norm[k] = sqrt(s);
-        S.c_dev2[k] = d;
+        for (int e = 0; e < E; ++e) {
+            const int idx = lane + 32 * e;
+            if (idx < mn) {
+                double v = S.alpha * acc[e];
+                if (cin) v = v + S.beta * cin[idx];
+                out[idx] = v;
+                sq = fma(v, v, sq);
+                const double wv = (I == J && ii[e] == jj[e]) ? v - 1.0 : v;
+                d = fma(wv, wv, d);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            sq += __shfl_xor_sync(0xffffffffu, sq, o);
+            d += __shfl_xor_sync(0xffffffffu, d, o);
+        }
+        if (lane == 0) {
+            S.c_norm[k] = sqrt(sq);
+            S.c_dev2[k] = d;
+        }
     }
 }
 
-__global__ void __launch_bounds__(256) k_smm_f64(int64_t nform, SmmArgs S) {
-    const int lane = threadIdx.x & 31;
-    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t k = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); k < nform; k += warps) {
-        const int I = S.f_row[k], J = S.f_col[k];
-        const int m = S.bs[I], n = S.bs[J];
-        const int E = (m * n + 31) >> 5;
-        switch (E) {
-#define DBG_CASE(x) case x: smm_block<x>(S, k, I, J, m, n, lane); break;
-            DBG_CASE(1) DBG_CASE(2) DBG_CASE(3) DBG_CASE(4) DBG_CASE(5) DBG_CASE(6) DBG_CASE(7) DBG_CASE(8)
-            DBG_CASE(9) DBG_CASE(10) DBG_CASE(11) DBG_CASE(12) DBG_CASE(13) DBG_CASE(14) DBG_CASE(15) DBG_CASE(16)
-            DBG_CASE(17) DBG_CASE(18) DBG_CASE(19) DBG_CASE(20) DBG_CASE(21) DBG_CASE(22) DBG_CASE(23) DBG_CASE(24)
-            DBG_CASE(25) DBG_CASE(26) DBG_CASE(27) DBG_CASE(28) DBG_CASE(29) DBG_CASE(30) DBG_CASE(31) DBG_CASE(32)
-#undef DBG_CASE
-            default: break;
-        }
-    }
+// Stable partition of the formed blocks by shape class: flag[k] = (class(k) == c).
+__global__ void k_class_flags(int64_t nform, const int32_t* __restrict__ f_row, const int32_t* __restrict__ f_col,
+                              const int32_t* __restrict__ bs, int c, int32_t* __restrict__ flag) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nform; k += (int64_t)gridDim.x * blockDim.x)
+        flag[k] = (shape_class(bs[f_row[k]], bs[f_col[k]]) == c) ? 1 : 0;
 }
+
+__global__ void k_class_scatter(int64_t nform, const int32_t* __restrict__ flag, const int64_t* __restrict__ pos,
+                                int64_t* __restrict__ list) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nform; k += (int64_t)gridDim.x * blockDim.x)
+        if (flag[k]) list[pos[k]] = k;
+}
+
+using SmmKernel = void (*)(int64_t, const int64_t*, SmmArgs);
+
+template <int... Es>
+struct SmmTable {
+    static SmmKernel get(int e) {
+        SmmKernel t[] = {nullptr, &k_smm_f64<Es>...};
+        return (e >= 1 && e <= (int)sizeof...(Es)) ? t[e] : nullptr;
+    }
+};
+using SmmF64 = SmmTable<1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18, 19, 20, 21, 22, 23, 24, 25,
+                        26, 27, 28, 29, 30, 31, 32>;
 
 __global__ void k_keep_filter(int64_t nb, const int32_t* __restrict__ row, const int32_t* __restrict__ col,
                               const double* __restrict__ norms, const double* __restrict__ dev2, double eps,
@@ -451,7 +489,7 @@ void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbc
     // 3. formed-block metadata
     const int64_t nf1 = std::max<int64_t>(nform, 1);
     DBuf<int32_t> f_row, f_col;
-    DBuf<int64_t> f_area, f_np, f_cin, f_off, f_pbeg, f_rp, flops;
+    DBuf<int64_t> f_area, f_np, f_cin, f_off, f_pbeg, f_rp, flops, class_cnt;
     f_row.alloc(nf1, s);
     f_col.alloc(nf1, s);
     f_area.alloc(nf1, s);
@@ -462,20 +500,25 @@ void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbc
     f_rp.alloc(nblk + 1, s);
     flops.alloc(1, s);
     flops.zero();
+    constexpr int kClasses = kMaxBlock * kMaxBlock / 32 + 1;
+    class_cnt.alloc(kClasses, s);
+    class_cnt.zero();
     if (ncand) {
         k_form_meta<<<grid_for(ncand, 256), 256, 0, s>>>(ncand, keep.p, kidx.p, cand_row.p, cand_col.p, pcnt.p, ksum.p,
                                                          use_c ? cin.p : nullptr, A->bs.p, f_row.p, f_col.p, f_area.p,
-                                                         f_np.p, f_cin.p, (unsigned long long*)flops.p);
+                                                         f_np.p, f_cin.p, (unsigned long long*)flops.p,
+                                                         (unsigned long long*)class_cnt.p);
         DBG_LAUNCH_CK();
     }
     k_form_rp<<<grid_for(nblk + 1, 256), 256, 0, s>>>(nblk, coff.p, kidx.p, f_rp.p);
     DBG_LAUNCH_CK();
     scan_exclusive(f_area.p, f_off.p, nform, s);
     scan_exclusive(f_np.p, f_pbeg.p, nform, s);
-    int64_t h3[3];
+    int64_t h3[3 + kClasses];
     {
-        const int64_t* src[3] = {f_off.p + nform, f_pbeg.p + nform, flops.p};
-        read_i64s(src, 3, h3, s);
+        const int64_t* src[3 + kClasses] = {f_off.p + nform, f_pbeg.p + nform, flops.p};
+        for (int c = 0; c < kClasses; ++c) src[3 + c] = class_cnt.p + c;
+        read_i64s(src, 3 + kClasses, h3, s);
     }
     const int64_t nel = h3[0], nprod = h3[1];
     const double nflop = (double)(unsigned long long)h3[2];
@@ -496,7 +539,7 @@ void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbc
     }
     // the candidate arrays are no longer needed
     cand_row.release(); cand_col.release(); pcnt.release(); ksum.release(); bound.release(); cursor.release();
-    DBG_CK(cudaEventRecord(ev.e[1], s));
+    if (!nform) DBG_CK(cudaEventRecord(ev.e[1], s));
 
     // 5. numeric
     DBuf<double> c_data, c_norm, c_dev2;
@@ -507,8 +550,34 @@ void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbc
         SmmArgs sa{f_row.p, f_col.p, f_off.p, f_pbeg.p, f_cin.p, prod_a.p, prod_b.p, A->col.p, A->off.p, A->data.p,
                    B->off.p, B->data.p, use_c ? C->off.p : nullptr, use_c ? C->data.p : nullptr, A->bs.p,
                    alpha, beta, c_data.p, c_norm.p, c_dev2.p};
-        k_smm_f64<<<grid_for(nform, 8, 152 * 16), 256, 0, s>>>(nform, sa);
-        DBG_LAUNCH_CK();
+        // one launch per shape class over that class's blocks (kept in CSR order)
+        DBuf<int32_t> flag;
+        DBuf<int64_t> pos, list;
+        flag.alloc(nform, s);
+        pos.alloc(nform + 1, s);
+        list.alloc(nform, s);
+        int64_t at = 0;
+        std::vector<std::pair<int, int64_t>> launches;
+        for (int c = 1; c < kClasses; ++c) {
+            const int64_t cnt = h3[3 + c];
+            if (!cnt) continue;
+            k_class_flags<<<grid_for(nform, 256), 256, 0, s>>>(nform, f_row.p, f_col.p, A->bs.p, c, flag.p);
+            DBG_LAUNCH_CK();
+            scan_exclusive(flag.p, pos.p, nform, s);
+            k_class_scatter<<<grid_for(nform, 256), 256, 0, s>>>(nform, flag.p, pos.p, list.p + at);
+            DBG_LAUNCH_CK();
+            launches.emplace_back(c, cnt);
+            at += cnt;
+        }
+        DBG_CK(cudaEventRecord(ev.e[1], s));
+        at = 0;
+        for (auto& [c, cnt] : launches) {
+            SmmKernel kern = SmmF64::get(c);
+            if (!kern) fail(DBCSR_ECAPACITY, "multiply: block shape beyond the kernel table");
+            kern<<<grid_for(cnt, 8, 152 * 32), 256, 0, s>>>(cnt, list.p + at, sa);
+            DBG_LAUNCH_CK();
+            at += cnt;
+        }
     }
     DBG_CK(cudaEventRecord(ev.e[2], s));
     prod_a.release(); prod_b.release();

@@ -70,20 +70,27 @@ def test_not_converged_is_reported(gb):
 def test_sign_1024_waters_full_size(gb):
     """1,024 waters (N = 23,552), eps 1e-7, tol 1e-9: the configuration the benchmark times.
 
-    Checked against the oracle's band energy stored by tests/golden/make_golden.py
-    (when present), the exact occupation Tr(P) = 4,096, and sampled blocks of the
-    first product recomputed by the oracle one at a time."""
+    With eps 1e-7 the residual floors near 1.24e-9 (the oracle's own run stalls
+    there too), so the run ends on the stall test.  Checked against the oracle's
+    run stored by tests/golden/make_golden.py (same steps, residuals, band
+    energy), the exact dense-eigendecomposition energy stored by
+    tests/golden/make_golden_exact.py (when present), the occupation
+    Tr(P) = 4,096, and sampled blocks of the first product recomputed by the
+    oracle one at a time."""
     w = synth.SIGN_1024
     h = synth.build_hamiltonian(w)
     H = gb.Matrix.of(h.H)
     g = gb.sign_iterate(H, 0.0, w.eps_filter, w.tol)
-    assert g.converged
+    assert g.converged or (g.report.stalled and g.report.residual < 2 * w.tol)
     assert g.report.trace_p == pytest.approx(4096, abs=1e-4)
-    gold = os.path.join(HERE, "golden", "sign_1024h2o.json")
-    if os.path.exists(gold):
-        ref = json.load(open(gold))
-        assert abs(g.report.e_band - ref["e_band"]) / h.n_atoms < DE_ATOM
-        assert abs(g.report.iterations - ref["iterations"]) <= 1
+    ref = json.load(open(os.path.join(HERE, "golden", "sign_1024h2o.json")))
+    assert abs(g.report.e_band - ref["e_band"]) / h.n_atoms < DE_ATOM
+    assert g.report.iterations == ref["iterations"]
+    np.testing.assert_allclose(g.residuals, ref["residuals"], rtol=1e-3)
+    exact = os.path.join(HERE, "golden", "exact_1024h2o.json")
+    if os.path.exists(exact):
+        ex = json.load(open(exact))
+        assert abs(g.report.e_band - ex["e_band"]) / h.n_atoms < DE_ATOM
     # sampled outputs of the first product X0.X0 (unfiltered values of formed blocks)
     Ho = bsr.Mat.of(h.H)
     alpha = g.report.alpha
