@@ -144,6 +144,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU-baseline leg")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision leg")
     ap.add_argument("--ref-steps", type=int, default=1, help="Newton-Schulz steps per oracle sample (reference arm)")
     ap.add_argument("--cpu-steps", type=int, default=2, help="Newton-Schulz steps in the oracle CPU baseline")
     ap.add_argument("--workload", default="sign-1024h2o", choices=["sign-1024h2o", "sign-512h2o"],
@@ -222,6 +223,33 @@ def main():
     ms_all, flops_all = float(t[0]), float(t[1])
     value = flops_all / (ms_all * 1e-3) / 1e12
 
+    # the same workload with the precision ladder: BF16 tensor-core products while r >= 1e-4, then FP64
+    mixed = None
+    if not args.no_mixed:
+        def step_mixed():
+            return gb.sign_iterate(H, h.mu, w.eps_filter, w.tol, prec=gb.DBCSR_MIXED, switch_tol=1e-4,
+                                   verbose=args.verbose)
+        for _ in range(args.warmup):
+            rm = step_mixed()
+        barrier()
+        m0, m1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        m0.record(stream)
+        mfl = 0.0
+        for _ in range(args.steps):
+            rm = step_mixed()
+            mfl += rm.report.flops
+        m1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        mms = m0.elapsed_time(m1)
+        mixed = {"time_to_p_ms": mms / args.steps, "value": mfl / (mms * 1e-3) / 1e12, "unit": "TFLOP/s",
+                 "speedup_vs_fp64": (ms_all / args.steps) / (mms / args.steps),
+                 "iterations": rm.report.iterations, "fp64_from_step": rm.report.fp64_from,
+                 "converged": bool(rm.report.converged), "stalled": bool(rm.report.stalled),
+                 "residual": rm.report.residual, "trace_p": rm.report.trace_p, "e_band": rm.report.e_band,
+                 "de_band_per_atom_vs_fp64": abs(rm.report.e_band - ebands[-1]) / h.n_atoms,
+                 "switch": 1e-4, "dtype": "bf16 operands / fp32 accumulate, then f64"}
+
     # end to end through the public API: inputs from pinned host memory, report read back
     e2e = None
     if not args.no_e2e:
@@ -267,7 +295,8 @@ def main():
                       "parallelism": f"replicas x{world}"},
            "time_to_p_ms": ms_all / args.steps,
            "iterations": iters[-1], "converged": all(conv), "trace_p": trp[-1], "n_occ": h.n_occ,
-           "e_band": ebands[-1], "gpu_launches": launches, "clocks": clk, "roofline": roofline, "e2e": e2e}
+           "e_band": ebands[-1], "residual": r.report.residual, "stalled": bool(r.report.stalled),
+           "gpu_launches": launches, "clocks": clk, "roofline": roofline, "e2e": e2e, "mixed": mixed}
 
     if rank == 0 and world == 1 and not args.no_cpu:
         f, dt, cores = oracle_sample(h, w, args.cpu_steps)

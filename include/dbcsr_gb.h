@@ -94,7 +94,7 @@ typedef struct {
     int32_t iterations;        /* steps taken (products X*X formed) */
     int32_t converged;         /* 1 if r < tol was reached */
     int32_t stalled;           /* 1 if the stall test stopped the iteration */
-    int32_t fp64_from;         /* first step computed in FP64 (DBCSR_MIXED), else 0 */
+    int32_t fp64_from;         /* first step whose X*X was formed in FP64 (1 for DBCSR_FP64) */
     double alpha;              /* Gershgorin scale: X_0 = (H - mu 1) / alpha */
     double residual;           /* last r = ||X^2 - 1||_F / N */
     double trace_p;            /* Tr(P) */

@@ -1,0 +1,18 @@
+"""Rounding to bfloat16 for the oracle's low-precision pins (TEST INFRASTRUCTURE ONLY).
+
+bfloat16 keeps the sign, the 8 exponent bits of binary32 and 8 significant bits
+(7 stored).  Rounding a double to it (round to nearest, ties to even) is, for
+values in the normal range of binary32, rounding the significand to 8 bits:
+x = f * 2^e with f in [0.5, 1); f * 2^8 rounded half-to-even; times 2^(e-8).
+Values below the binary32 normal range (|x| < 2^-126) become signed zero.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def round_bf16(x: np.ndarray) -> np.ndarray:
+    x = np.asarray(x, dtype=np.float64)
+    f, e = np.frexp(x)
+    r = np.ldexp(np.rint(f * 256.0), e - 8)
+    return np.where(np.abs(x) < 2.0 ** -126, 0.0 * x, r)

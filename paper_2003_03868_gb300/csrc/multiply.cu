@@ -20,6 +20,8 @@
 //                    block and sums its products in stack order (no atomics);
 //                    the epilogue applies alpha/beta and writes the block norm.
 //  6. filter         blocks with norm < eps dropped (diagonal kept), compaction.
+#include <cuda_bf16.h>
+
 #include <algorithm>
 #include <cmath>
 #include <utility>
@@ -215,6 +217,7 @@ __global__ void k_form_meta(int64_t ncand, const int32_t* __restrict__ keep, con
         f_cin[k] = cin ? cin[c] : -1;
         local += 2ull * (unsigned long long)bs[I] * (unsigned long long)bs[J] * (unsigned long long)ksum[c];
         atomicAdd(class_cnt + ((bs[I] * bs[J] + 31) >> 5), 1ull);
+        atomicAdd(class_cnt + (kMaxBlock * kMaxBlock / 32 + 1) + ((bs[I] + 15) / 16 - 1) * 4 + (bs[J] + 7) / 8, 1ull);
     }
     for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
     if ((threadIdx.x & 31) == 0 && local) atomicAdd(flops, local);
@@ -278,9 +281,6 @@ struct SmmArgs {
     double alpha, beta;
     double* c_data; double* c_norm; double* c_dev2;
 };
-
-// Shape class of a C block: E = ceil(m*n / 32) accumulators per lane.
-__device__ __forceinline__ int shape_class(int m, int n) { return (m * n + 31) >> 5; }
 
 // One warp per C block of class E (m*n <= 32*E): lane l owns elements l, l+32,
 // ..., sums its products in stack order (ascending K, then k) with FMA, and
@@ -361,9 +361,12 @@ __global__ void __launch_bounds__(256) k_smm_f64(int64_t nlist, const int64_t* _
 
 // Stable partition of the formed blocks by shape class: flag[k] = (class(k) == c).
 __global__ void k_class_flags(int64_t nform, const int32_t* __restrict__ f_row, const int32_t* __restrict__ f_col,
-                              const int32_t* __restrict__ bs, int c, int32_t* __restrict__ flag) {
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nform; k += (int64_t)gridDim.x * blockDim.x)
-        flag[k] = (shape_class(bs[f_row[k]], bs[f_col[k]]) == c) ? 1 : 0;
+                              const int32_t* __restrict__ bs, int c, int bf16, int32_t* __restrict__ flag) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nform; k += (int64_t)gridDim.x * blockDim.x) {
+        const int m = bs[f_row[k]], n = bs[f_col[k]];
+        // FP64 class: E = ceil(m n / 32) accumulators per lane; BF16 class: (m, n) tile counts (MT, NT)
+        flag[k] = ((bf16 ? ((m + 15) / 16 - 1) * 4 + (n + 7) / 8 : (m * n + 31) >> 5) == c) ? 1 : 0;
+    }
 }
 
 __global__ void k_class_scatter(int64_t nform, const int32_t* __restrict__ flag, const int64_t* __restrict__ pos,
@@ -383,6 +386,217 @@ struct SmmTable {
 };
 using SmmF64 = SmmTable<1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18, 19, 20, 21, 22, 23, 24, 25,
                         26, 27, 28, 29, 30, 31, 32>;
+
+// ------------------------------------------------------------ BF16 tensor-core SMM
+// BF16 operands (rounded to nearest even from FP64), FP32 accumulation on the
+// tensor cores (mma.sync m16n8k16), FP64 epilogue.  One warp owns one C block
+// (m <= 16*MT, n <= 8*NT).  Its products are concatenated along K,
+// C_IJ = [A_IK1 A_IK2 ...] [B_K1J; B_K2J; ...], in shared-memory panels of up to
+// kPanelK columns (ascending K; a panel is padded with zeros to a multiple of 16).
+constexpr int kPanelK = 128;
+constexpr int kPanelLd = kPanelK + 8;      // row stride (bf16): 68 words, conflict-free fragment loads
+constexpr int kBf16Warps = 4;
+
+__device__ __forceinline__ void mma_bf16(float* c, uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t b0,
+                                         uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+struct SmmBf16Args {
+    SmmArgs base;
+    const __nv_bfloat16* a16;
+    const __nv_bfloat16* b16;
+};
+
+template <int MT, int NT>
+__device__ __forceinline__ void bf16_panel_mma(const __nv_bfloat16* sA, const __nv_bfloat16* sB, int kc, int lane,
+                                               float (&acc)[MT][NT][4]) {
+    const int gid = lane >> 2, tig = lane & 3;
+    for (int ks = 0; ks < kc; ks += 16) {
+        uint32_t bf[NT][2];
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt) {
+            const __nv_bfloat16* b = sB + (nt * 8 + gid) * kPanelLd + ks + tig * 2;
+            bf[nt][0] = *reinterpret_cast<const uint32_t*>(b);
+            bf[nt][1] = *reinterpret_cast<const uint32_t*>(b + 8);
+        }
+#pragma unroll
+        for (int mt = 0; mt < MT; ++mt) {
+            const __nv_bfloat16* a = sA + (mt * 16 + gid) * kPanelLd + ks + tig * 2;
+            const uint32_t a0 = *reinterpret_cast<const uint32_t*>(a);
+            const uint32_t a1 = *reinterpret_cast<const uint32_t*>(a + 8 * kPanelLd);
+            const uint32_t a2 = *reinterpret_cast<const uint32_t*>(a + 8);
+            const uint32_t a3 = *reinterpret_cast<const uint32_t*>(a + 8 * kPanelLd + 8);
+#pragma unroll
+            for (int nt = 0; nt < NT; ++nt) mma_bf16(acc[mt][nt], a0, a1, a2, a3, bf[nt][0], bf[nt][1]);
+        }
+    }
+}
+
+template <int MT, int NT>
+__global__ void __launch_bounds__(32 * kBf16Warps) k_smm_bf16(int64_t nlist, const int64_t* __restrict__ list,
+                                                             SmmBf16Args G) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const SmmArgs& S = G.base;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    constexpr int kRowsA = 16 * MT, kRowsB = 8 * NT;
+    __nv_bfloat16* sA = reinterpret_cast<__nv_bfloat16*>(smem_raw) + (size_t)wib * (kRowsA + kRowsB) * kPanelLd;
+    __nv_bfloat16* sB = sA + kRowsA * kPanelLd;
+    const __nv_bfloat16 zero = __float2bfloat16(0.0f);
+    const int64_t warps = (int64_t)gridDim.x * kBf16Warps;
+    for (int64_t w = (int64_t)blockIdx.x * kBf16Warps + wib; w < nlist; w += warps) {
+        const int64_t k = list[w];
+        const int I = S.f_row[k], J = S.f_col[k];
+        const int m = S.bs[I], n = S.bs[J];
+        float acc[MT][NT][4];
+#pragma unroll
+        for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+            for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+                for (int i = 0; i < 4; ++i) acc[mt][nt][i] = 0.f;
+        // rows of A beyond m and columns of B beyond n only feed discarded outputs,
+        // but must hold finite values: clear the panels once per block
+        for (int e = lane; e < (kRowsA + kRowsB) * kPanelLd; e += 32) sA[e] = zero;
+        __syncwarp();
+        int koff = 0;
+        const int64_t pb = S.f_pbeg[k], pe = S.f_pbeg[k + 1];
+        for (int64_t base = pb; base < pe; base += 32) {
+            const int cnt = (int)min((int64_t)32, pe - base);
+            int64_t ao = 0, bo = 0;
+            int kq = 0;
+            if (lane < cnt) {
+                const int32_t ai = S.prod_a[base + lane], bi = S.prod_b[base + lane];
+                ao = S.a_off[ai];
+                bo = S.b_off[bi];
+                kq = S.bs[S.a_col[ai]];
+            }
+            for (int q = 0; q < cnt; ++q) {
+                const int64_t aoq = __shfl_sync(0xffffffffu, ao, q);
+                const int64_t boq = __shfl_sync(0xffffffffu, bo, q);
+                const int kk = __shfl_sync(0xffffffffu, kq, q);
+                if (koff + kk > kPanelK) {
+                    const int kc = (koff + 15) & ~15;
+                    for (int e = lane; e < kRowsA * (kc - koff); e += 32)
+                        sA[(e / (kc - koff)) * kPanelLd + koff + e % (kc - koff)] = zero;
+                    for (int e = lane; e < kRowsB * (kc - koff); e += 32)
+                        sB[(e / (kc - koff)) * kPanelLd + koff + e % (kc - koff)] = zero;
+                    __syncwarp();
+                    bf16_panel_mma<MT, NT>(sA, sB, kc, lane, acc);
+                    __syncwarp();
+                    koff = 0;
+                }
+                const __nv_bfloat16* A = G.a16 + aoq;
+                const __nv_bfloat16* B = G.b16 + boq;
+                for (int e = lane; e < m * kk; e += 32) {
+                    const int r = e / kk, t = e - r * kk;
+                    sA[r * kPanelLd + koff + t] = A[e];
+                }
+                for (int e = lane; e < kk * n; e += 32) {
+                    const int t = e / n, c = e - t * n;
+                    sB[c * kPanelLd + koff + t] = B[e];
+                }
+                koff += kk;
+            }
+        }
+        if (koff > 0) {
+            const int kc = (koff + 15) & ~15;
+            if (kc > koff) {
+                for (int e = lane; e < kRowsA * (kc - koff); e += 32)
+                    sA[(e / (kc - koff)) * kPanelLd + koff + e % (kc - koff)] = zero;
+                for (int e = lane; e < kRowsB * (kc - koff); e += 32)
+                    sB[(e / (kc - koff)) * kPanelLd + koff + e % (kc - koff)] = zero;
+            }
+            __syncwarp();
+            bf16_panel_mma<MT, NT>(sA, sB, kc, lane, acc);
+        }
+        __syncwarp();
+        // epilogue in FP64
+        const int gid = lane >> 2, tig = lane & 3;
+        const int64_t ci = S.f_cin[k];
+        const double* cin = ci >= 0 ? S.ci_data + S.ci_off[ci] : nullptr;
+        double* out = S.c_data + S.f_off[k];
+        double sq = 0.0, d = 0.0;
+#pragma unroll
+        for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+            for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int r = mt * 16 + gid + (i >= 2 ? 8 : 0), c = nt * 8 + tig * 2 + (i & 1);
+                    if (r < m && c < n) {
+                        double v = S.alpha * (double)acc[mt][nt][i];
+                        if (cin) v = v + S.beta * cin[r * n + c];
+                        out[r * n + c] = v;
+                        sq = fma(v, v, sq);
+                        const double wv = (I == J && r == c) ? v - 1.0 : v;
+                        d = fma(wv, wv, d);
+                    }
+                }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            sq += __shfl_xor_sync(0xffffffffu, sq, o);
+            d += __shfl_xor_sync(0xffffffffu, d, o);
+        }
+        if (lane == 0) {
+            S.c_norm[k] = sqrt(sq);
+            S.c_dev2[k] = d;
+        }
+    }
+}
+
+using SmmBf16Kernel = void (*)(int64_t, const int64_t*, SmmBf16Args);
+
+SmmBf16Kernel bf16_kernel(int cls, size_t* smem) {
+    const int mt = (cls - 1) / 4 + 1, nt = (cls - 1) % 4 + 1;
+    *smem = (size_t)kBf16Warps * (16 * mt + 8 * nt) * kPanelLd * sizeof(__nv_bfloat16);
+    switch (cls) {
+        case 1: return &k_smm_bf16<1, 1>;
+        case 2: return &k_smm_bf16<1, 2>;
+        case 3: return &k_smm_bf16<1, 3>;
+        case 4: return &k_smm_bf16<1, 4>;
+        case 5: return &k_smm_bf16<2, 1>;
+        case 6: return &k_smm_bf16<2, 2>;
+        case 7: return &k_smm_bf16<2, 3>;
+        case 8: return &k_smm_bf16<2, 4>;
+        default: return nullptr;
+    }
+}
+
+// FP64 -> BF16, one rounding to nearest (ties to even) of the 52-bit significand to
+// 7 stored bits, from the IEEE-754 encodings.  Values below the binary32 normal
+// range become signed zero, values above it infinity.
+__device__ __forceinline__ __nv_bfloat16 f64_to_bf16_rne(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned short sign = (unsigned short)((b >> 48) & 0x8000u);
+    const int e = (int)((b >> 52) & 0x7ff);
+    const unsigned long long mant = b & 0xFFFFFFFFFFFFFull;
+    unsigned short out;
+    if (e == 0x7ff) {
+        out = sign | 0x7f80u | (mant ? 0x40u : 0u);
+    } else {
+        const int eb = e - 1023 + 127;
+        if (eb >= 0xff) {
+            out = sign | 0x7f80u;
+        } else if (eb <= 0) {
+            out = sign;
+        } else {
+            unsigned long long top = ((unsigned long long)eb << 7) | (mant >> 45);
+            const unsigned long long rem = mant & ((1ull << 45) - 1), half = 1ull << 44;
+            if (rem > half || (rem == half && (top & 1ull))) top += 1;   // a carry moves into the exponent
+            out = (top >= (0xffull << 7)) ? (unsigned short)(sign | 0x7f80u) : (unsigned short)(sign | top);
+        }
+    }
+    return __ushort_as_bfloat16(out);
+}
+
+__global__ void k_to_bf16(int64_t n, const double* __restrict__ in, __nv_bfloat16* __restrict__ out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = f64_to_bf16_rne(in[i]);
+}
 
 __global__ void k_keep_filter(int64_t nb, const int32_t* __restrict__ row, const int32_t* __restrict__ col,
                               const double* __restrict__ norms, const double* __restrict__ dev2, double eps,
@@ -419,7 +633,7 @@ void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbc
     check_finalized(B);
     if (!C) fail(DBCSR_EINVAL, "multiply: null C");
     if (A->h_bs != B->h_bs || A->h_bs != C->h_bs) fail(DBCSR_EINVAL, "multiply: block sizes of A, B and C differ");
-    if (prec != DBCSR_FP64) fail(DBCSR_EINVAL, "multiply: precision not supported by this entry point");
+    if (prec != DBCSR_FP64 && prec != DBCSR_BF16) fail(DBCSR_EINVAL, "multiply: prec must be DBCSR_FP64 or DBCSR_BF16");
     if (!(eps >= 0.0)) fail(DBCSR_EINVAL, "multiply: eps_filter must be >= 0");
     const bool use_c = (beta != 0.0);
     if (use_c) check_finalized(C);
@@ -500,8 +714,9 @@ void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbc
     f_rp.alloc(nblk + 1, s);
     flops.alloc(1, s);
     flops.zero();
-    constexpr int kClasses = kMaxBlock * kMaxBlock / 32 + 1;
-    class_cnt.alloc(kClasses, s);
+    constexpr int kClasses = kMaxBlock * kMaxBlock / 32 + 1;      // FP64 classes E = 1..32
+    constexpr int kClassesBf16 = 9;                                 // BF16 classes (MT, NT) = 1..8
+    class_cnt.alloc(kClasses + kClassesBf16, s);
     class_cnt.zero();
     if (ncand) {
         k_form_meta<<<grid_for(ncand, 256), 256, 0, s>>>(ncand, keep.p, kidx.p, cand_row.p, cand_col.p, pcnt.p, ksum.p,
@@ -514,11 +729,11 @@ void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbc
     DBG_LAUNCH_CK();
     scan_exclusive(f_area.p, f_off.p, nform, s);
     scan_exclusive(f_np.p, f_pbeg.p, nform, s);
-    int64_t h3[3 + kClasses];
+    int64_t h3[3 + kClasses + kClassesBf16];
     {
-        const int64_t* src[3 + kClasses] = {f_off.p + nform, f_pbeg.p + nform, flops.p};
-        for (int c = 0; c < kClasses; ++c) src[3 + c] = class_cnt.p + c;
-        read_i64s(src, 3 + kClasses, h3, s);
+        const int64_t* src[3 + kClasses + kClassesBf16] = {f_off.p + nform, f_pbeg.p + nform, flops.p};
+        for (int c = 0; c < kClasses + kClassesBf16; ++c) src[3 + c] = class_cnt.p + c;
+        read_i64s(src, 3 + kClasses + kClassesBf16, h3, s);
     }
     const int64_t nel = h3[0], nprod = h3[1];
     const double nflop = (double)(unsigned long long)h3[2];
@@ -551,6 +766,9 @@ void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbc
                    B->off.p, B->data.p, use_c ? C->off.p : nullptr, use_c ? C->data.p : nullptr, A->bs.p,
                    alpha, beta, c_data.p, c_norm.p, c_dev2.p};
         // one launch per shape class over that class's blocks (kept in CSR order)
+        const bool bf16 = (prec == DBCSR_BF16);
+        const int ncls = bf16 ? kClassesBf16 : kClasses;
+        const int64_t* cnts = h3 + 3 + (bf16 ? kClasses : 0);
         DBuf<int32_t> flag;
         DBuf<int64_t> pos, list;
         flag.alloc(nform, s);
@@ -558,10 +776,11 @@ void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbc
         list.alloc(nform, s);
         int64_t at = 0;
         std::vector<std::pair<int, int64_t>> launches;
-        for (int c = 1; c < kClasses; ++c) {
-            const int64_t cnt = h3[3 + c];
+        for (int c = 1; c < ncls; ++c) {
+            const int64_t cnt = cnts[c];
             if (!cnt) continue;
-            k_class_flags<<<grid_for(nform, 256), 256, 0, s>>>(nform, f_row.p, f_col.p, A->bs.p, c, flag.p);
+            k_class_flags<<<grid_for(nform, 256), 256, 0, s>>>(nform, f_row.p, f_col.p, A->bs.p, c, bf16 ? 1 : 0,
+                                                               flag.p);
             DBG_LAUNCH_CK();
             scan_exclusive(flag.p, pos.p, nform, s);
             k_class_scatter<<<grid_for(nform, 256), 256, 0, s>>>(nform, flag.p, pos.p, list.p + at);
@@ -569,12 +788,33 @@ void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbc
             launches.emplace_back(c, cnt);
             at += cnt;
         }
+        DBuf<__nv_bfloat16> a16, b16;
+        if (bf16) {
+            // operands rounded to BF16 (nearest even) once per product
+            a16.alloc(std::max<int64_t>(A->nel, 1), s);
+            k_to_bf16<<<grid_for(A->nel, 256, 152 * 32), 256, 0, s>>>(A->nel, A->data.p, a16.p);
+            DBG_LAUNCH_CK();
+            if (B != A) {
+                b16.alloc(std::max<int64_t>(B->nel, 1), s);
+                k_to_bf16<<<grid_for(B->nel, 256, 152 * 32), 256, 0, s>>>(B->nel, B->data.p, b16.p);
+                DBG_LAUNCH_CK();
+            }
+        }
         DBG_CK(cudaEventRecord(ev.e[1], s));
         at = 0;
         for (auto& [c, cnt] : launches) {
-            SmmKernel kern = SmmF64::get(c);
-            if (!kern) fail(DBCSR_ECAPACITY, "multiply: block shape beyond the kernel table");
-            kern<<<grid_for(cnt, 8, 152 * 32), 256, 0, s>>>(cnt, list.p + at, sa);
+            if (bf16) {
+                size_t sm = 0;
+                SmmBf16Kernel kern = bf16_kernel(c, &sm);
+                if (!kern) fail(DBCSR_ECAPACITY, "multiply: block shape beyond the BF16 kernel table");
+                if (sm > 48 * 1024) DBG_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+                SmmBf16Args ga{sa, a16.p, B != A ? b16.p : a16.p};
+                kern<<<grid_for(cnt, kBf16Warps, 152 * 64), 32 * kBf16Warps, sm, s>>>(cnt, list.p + at, ga);
+            } else {
+                SmmKernel kern = SmmF64::get(c);
+                if (!kern) fail(DBCSR_ECAPACITY, "multiply: block shape beyond the kernel table");
+                kern<<<grid_for(cnt, 8, 152 * 32), 256, 0, s>>>(cnt, list.p + at, sa);
+            }
             DBG_LAUNCH_CK();
             at += cnt;
         }

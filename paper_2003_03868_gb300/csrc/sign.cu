@@ -45,7 +45,8 @@ dbcsr_status sign_iterate(dbcsr_matrix_* H, double mu, const dbcsr_sign_opts* op
     if (o.max_iter <= 0) o.max_iter = 100;
     if (o.stall_ratio <= 0) o.stall_ratio = 0.5;
     if (!(o.eps_filter >= 0) || !(o.tol > 0)) fail(DBCSR_EINVAL, "sign_iterate: need eps_filter >= 0 and tol > 0");
-    if (o.prec != DBCSR_FP64) fail(DBCSR_EINVAL, "sign_iterate: precision policy not supported");
+    if (o.prec != DBCSR_FP64 && o.prec != DBCSR_MIXED) fail(DBCSR_EINVAL, "sign_iterate: prec must be FP64 or MIXED");
+    if (o.prec == DBCSR_MIXED && !(o.switch_tol > 0)) o.switch_tol = 1e-4;
 
     const auto t0 = std::chrono::steady_clock::now();
     cudaStream_t s = H->stream;
@@ -63,9 +64,12 @@ dbcsr_status sign_iterate(dbcsr_matrix_* H, double mu, const dbcsr_sign_opts* op
     int it = 0;
     bool converged = false, stalled = false;
     double res = 0.0;
+    // precision ladder: BF16 operands / FP32 accumulation while r >= switch_tol, then FP64
+    int tier = (o.prec == DBCSR_MIXED) ? DBCSR_BF16 : DBCSR_FP64;
+    int first_fp64 = (tier == DBCSR_FP64) ? 1 : 0;
     while (it < o.max_iter) {
         dbcsr_mult_stats st{};
-        multiply(1.0, X.get(), X.get(), 0.0, X2.get(), o.eps_filter, DBCSR_FP64, &st, true);
+        multiply(1.0, X.get(), X.get(), 0.0, X2.get(), o.eps_filter, tier, &st, true);
         res = std::sqrt(st.dev2_filtered) / N;
         r.flops += st.flops;
         r.n_products += st.n_products;
@@ -74,23 +78,34 @@ dbcsr_status sign_iterate(dbcsr_matrix_* H, double mu, const dbcsr_sign_opts* op
         ++it;
         if (!std::isfinite(res)) fail(DBCSR_ENAN, "sign_iterate: residual is not finite");
         if (o.verbose)
-            std::fprintf(stderr, "[sign] it %3d r %.3e nnzb(X) %lld cand %lld formed %lld kept %lld %.1f GF %.2f ms\n",
-                         it, res, (long long)X->nnzb, (long long)st.n_candidates, (long long)st.n_formed,
-                         (long long)st.n_kept, st.flops * 1e-9, st.ms_numeric);
-        if (res < o.tol) {
-            converged = true;
-            if (it - 1 < DBCSR_MAX_HISTORY) r.nnzb_history[it - 1] = X->nnzb;
-            break;
-        }
+            std::fprintf(stderr, "[sign] it %3d %s r %.3e nnzb(X) %lld cand %lld formed %lld kept %lld %.1f GF %.2f ms\n",
+                         it, tier == DBCSR_BF16 ? "bf16" : "fp64", res, (long long)X->nnzb,
+                         (long long)st.n_candidates, (long long)st.n_formed, (long long)st.n_kept, st.flops * 1e-9,
+                         st.ms_numeric);
         // without filtering r_k / r_{k-1} only falls: a fast step followed by a slow one is a stall
-        if (it >= 3 && it - 1 < DBCSR_MAX_HISTORY &&
-            r.residual_history[it - 2] < o.stall_ratio * r.residual_history[it - 3] &&
-            res > o.stall_ratio * r.residual_history[it - 2]) {
-            stalled = true;
-            if (it - 1 < DBCSR_MAX_HISTORY) r.nnzb_history[it - 1] = X->nnzb;
-            break;
+        const bool slow = it >= 3 && it - 1 < DBCSR_MAX_HISTORY &&
+                          r.residual_history[it - 2] < o.stall_ratio * r.residual_history[it - 3] &&
+                          res > o.stall_ratio * r.residual_history[it - 2];
+        if (tier == DBCSR_BF16) {
+            // the low-precision tier ends at the switch residual (or when it stops making progress);
+            // convergence is only ever declared on an FP64 product
+            if (res < o.switch_tol || res < o.tol || slow) {
+                tier = DBCSR_FP64;
+                first_fp64 = it + 1;
+            }
+        } else {
+            if (res < o.tol) {
+                converged = true;
+                if (it - 1 < DBCSR_MAX_HISTORY) r.nnzb_history[it - 1] = X->nnzb;
+                break;
+            }
+            if (slow && it >= first_fp64 + 2) {
+                stalled = true;
+                if (it - 1 < DBCSR_MAX_HISTORY) r.nnzb_history[it - 1] = X->nnzb;
+                break;
+            }
         }
-        multiply(-0.5, X.get(), X2.get(), 1.5, X.get(), o.eps_filter, DBCSR_FP64, &st, false);
+        multiply(-0.5, X.get(), X2.get(), 1.5, X.get(), o.eps_filter, tier, &st, false);
         r.flops += st.flops;
         r.n_products += st.n_products;
         r.ms_multiply += st.ms_numeric;
@@ -103,6 +118,7 @@ dbcsr_status sign_iterate(dbcsr_matrix_* H, double mu, const dbcsr_sign_opts* op
     DBG_CK(cudaStreamSynchronize(s));
     DBG_CK(cudaStreamSynchronize(P->stream));
     r.iterations = it;
+    r.fp64_from = first_fp64;
     r.converged = converged ? 1 : 0;
     r.stalled = stalled ? 1 : 0;
     r.residual = res;
