@@ -86,6 +86,7 @@ struct DBuf {
 
 // Pinned host scratch for small device->host readbacks.
 struct HostScalars {
+    static constexpr int kCap = 256;
     int64_t* i = nullptr;
     double* d = nullptr;
     HostScalars();
@@ -140,7 +141,9 @@ void scale_shift(dbcsr_matrix_* m, double scale, double shift);
 void compact(dbcsr_matrix_* m, const int32_t* keep, const double* norms_in);
 void filter_matrix(dbcsr_matrix_* m, double eps, const double* norms_in);
 int64_t read_i64(const int64_t* dev, cudaStream_t s);
-void read_i64s(const int64_t* const* dev, int k, int64_t* out, cudaStream_t s);
+// Reads k scalars and, optionally, one contiguous array of na values, with one synchronisation.
+void read_i64s(const int64_t* const* dev, int k, int64_t* out, cudaStream_t s, const int64_t* arr = nullptr,
+               int na = 0, int64_t* arr_out = nullptr);
 double read_f64(const double* dev, cudaStream_t s);
 
 // ---- reduce.cu

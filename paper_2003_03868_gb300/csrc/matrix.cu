@@ -13,7 +13,7 @@
 namespace dbg {
 
 HostScalars::HostScalars() {
-    DBG_CK(cudaMallocHost((void**)&i, 64 * sizeof(int64_t)));
+    DBG_CK(cudaMallocHost((void**)&i, kCap * sizeof(int64_t)));
     DBG_CK(cudaMallocHost((void**)&d, 64 * sizeof(double)));
 }
 HostScalars::~HostScalars() {
@@ -32,11 +32,15 @@ int64_t read_i64(const int64_t* dev, cudaStream_t s) {
     return hs.i[0];
 }
 
-void read_i64s(const int64_t* const* dev, int k, int64_t* out, cudaStream_t s) {
+void read_i64s(const int64_t* const* dev, int k, int64_t* out, cudaStream_t s, const int64_t* arr, int na,
+               int64_t* arr_out) {
     HostScalars& hs = host_scalars();
+    if (k + na > HostScalars::kCap) fail(DBCSR_ECAPACITY, "read_i64s: too many values");
     for (int j = 0; j < k; ++j) DBG_CK(cudaMemcpyAsync(hs.i + j, dev[j], sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    if (na > 0) DBG_CK(cudaMemcpyAsync(hs.i + k, arr, sizeof(int64_t) * na, cudaMemcpyDeviceToHost, s));
     DBG_CK(cudaStreamSynchronize(s));
     for (int j = 0; j < k; ++j) out[j] = hs.i[j];
+    for (int j = 0; j < na; ++j) arr_out[j] = hs.i[k + j];
 }
 
 double read_f64(const double* dev, cudaStream_t s) {

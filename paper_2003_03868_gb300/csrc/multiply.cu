@@ -198,6 +198,17 @@ __global__ void k_cand_bound(int32_t nblk, RowPattern P, int nwords, BoundArgs B
     }
 }
 
+// FP64 launch classes: 1..32 padded (E = ceil(m n / 32)); 33 + EF for m n = 32 EF + 1
+// (EF = 1..31, K-split remainder of one element); 65 for 13x13 (EF = 5, R = 9).
+constexpr int kF64ClassKs1 = 33, kF64Class13x13 = 65, kF64Classes = 66;
+
+__device__ __forceinline__ int f64_class(int m, int n) {
+    const int mn = m * n;
+    if (m == 13 && n == 13) return kF64Class13x13;
+    if (mn > 32 && (mn & 31) == 1) return kF64ClassKs1 + (mn >> 5);
+    return (mn + 31) >> 5;
+}
+
 __global__ void k_form_meta(int64_t ncand, const int32_t* __restrict__ keep, const int64_t* __restrict__ kidx,
                             const int32_t* __restrict__ cand_row, const int32_t* __restrict__ cand_col,
                             const int32_t* __restrict__ pcnt, const int32_t* __restrict__ ksum,
@@ -216,8 +227,8 @@ __global__ void k_form_meta(int64_t ncand, const int32_t* __restrict__ keep, con
         f_np[k] = pcnt[c];
         f_cin[k] = cin ? cin[c] : -1;
         local += 2ull * (unsigned long long)bs[I] * (unsigned long long)bs[J] * (unsigned long long)ksum[c];
-        atomicAdd(class_cnt + ((bs[I] * bs[J] + 31) >> 5), 1ull);
-        atomicAdd(class_cnt + (kMaxBlock * kMaxBlock / 32 + 1) + ((bs[I] + 15) / 16 - 1) * 4 + (bs[J] + 7) / 8, 1ull);
+        atomicAdd(class_cnt + f64_class(bs[I], bs[J]), 1ull);
+        atomicAdd(class_cnt + kF64Classes + ((bs[I] + 15) / 16 - 1) * 4 + (bs[J] + 7) / 8, 1ull);
     }
     for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
     if ((threadIdx.x & 31) == 0 && local) atomicAdd(flops, local);
@@ -359,13 +370,116 @@ __global__ void __launch_bounds__(256) k_smm_f64(int64_t nlist, const int64_t* _
     }
 }
 
+// FP64 class with a K-split remainder: the first 32*EF elements of the block are
+// spread over the lanes as in k_smm_f64, and the last R elements are summed along
+// K instead: lane l takes the products l, l+32, ... of the block (the product
+// whose metadata it fetched) for all R elements, and a fixed xor-shuffle tree adds
+// the 32 partial sums.  For m*n = 32*EF + 1 (13x5, 5x13, 23x7, 7x23) this removes
+// a 32-lane pass that would carry one useful element; for 13x13 (EF = 5, R = 9) a
+// pass that would carry nine.
+template <int EF, int R>
+__global__ void __launch_bounds__(256) k_smm_f64_ks(int64_t nlist, const int64_t* __restrict__ list, SmmArgs S) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < nlist; w += warps) {
+        const int64_t k = list[w];
+        const int I = S.f_row[k], J = S.f_col[k];
+        const int n = S.bs[J];
+        int ii[EF], jj[EF], ir[R], jr[R];
+        double acc[EF], rem[R];
+#pragma unroll
+        for (int e = 0; e < EF; ++e) {
+            const int idx = lane + 32 * e;
+            ii[e] = idx / n;
+            jj[e] = idx - ii[e] * n;
+            acc[e] = 0.0;
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int idx = 32 * EF + r;
+            ir[r] = idx / n;
+            jr[r] = idx - ir[r] * n;
+            rem[r] = 0.0;
+        }
+        const int64_t pb = S.f_pbeg[k], pe = S.f_pbeg[k + 1];
+        for (int64_t base = pb; base < pe; base += 32) {
+            const int cnt = (int)min((int64_t)32, pe - base);
+            int64_t ao = 0, bo = 0;
+            int kq = 0;
+            if (lane < cnt) {
+                const int32_t ai = S.prod_a[base + lane], bi = S.prod_b[base + lane];
+                ao = S.a_off[ai];
+                bo = S.b_off[bi];
+                kq = S.bs[S.a_col[ai]];
+            }
+            for (int q = 0; q < cnt; ++q) {
+                const int64_t aoq = __shfl_sync(0xffffffffu, ao, q);
+                const int64_t boq = __shfl_sync(0xffffffffu, bo, q);
+                const int kk = __shfl_sync(0xffffffffu, kq, q);
+                const double* __restrict__ A = S.a_data + aoq;
+                const double* __restrict__ B = S.b_data + boq;
+                for (int t = 0; t < kk; ++t) {
+#pragma unroll
+                    for (int e = 0; e < EF; ++e)
+                        acc[e] = fma(__ldg(A + ii[e] * kk + t), __ldg(B + t * n + jj[e]), acc[e]);
+                }
+            }
+            // remainder: this lane's own product (kq = 0 past the end of the list)
+            const double* __restrict__ A = S.a_data + ao;
+            const double* __restrict__ B = S.b_data + bo;
+            for (int t = 0; t < kq; ++t) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) rem[r] = fma(__ldg(A + ir[r] * kq + t), __ldg(B + t * n + jr[r]), rem[r]);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) rem[r] += __shfl_xor_sync(0xffffffffu, rem[r], o);
+        const int64_t ci = S.f_cin[k];
+        const double* cin = ci >= 0 ? S.ci_data + S.ci_off[ci] : nullptr;
+        double* out = S.c_data + S.f_off[k];
+        double sq = 0.0, d = 0.0;
+#pragma unroll
+        for (int e = 0; e < EF; ++e) {
+            const int idx = lane + 32 * e;
+            double v = S.alpha * acc[e];
+            if (cin) v = v + S.beta * cin[idx];
+            out[idx] = v;
+            sq = fma(v, v, sq);
+            const double wv = (I == J && ii[e] == jj[e]) ? v - 1.0 : v;
+            d = fma(wv, wv, d);
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            if (lane == r) {
+                const int idx = 32 * EF + r;
+                double v = S.alpha * rem[r];
+                if (cin) v = v + S.beta * cin[idx];
+                out[idx] = v;
+                sq = fma(v, v, sq);
+                const double wv = (I == J && ir[r] == jr[r]) ? v - 1.0 : v;
+                d = fma(wv, wv, d);
+            }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            sq += __shfl_xor_sync(0xffffffffu, sq, o);
+            d += __shfl_xor_sync(0xffffffffu, d, o);
+        }
+        if (lane == 0) {
+            S.c_norm[k] = sqrt(sq);
+            S.c_dev2[k] = d;
+        }
+    }
+}
+
 // Stable partition of the formed blocks by shape class: flag[k] = (class(k) == c).
 __global__ void k_class_flags(int64_t nform, const int32_t* __restrict__ f_row, const int32_t* __restrict__ f_col,
                               const int32_t* __restrict__ bs, int c, int bf16, int32_t* __restrict__ flag) {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nform; k += (int64_t)gridDim.x * blockDim.x) {
         const int m = bs[f_row[k]], n = bs[f_col[k]];
         // FP64 class: E = ceil(m n / 32) accumulators per lane; BF16 class: (m, n) tile counts (MT, NT)
-        flag[k] = ((bf16 ? ((m + 15) / 16 - 1) * 4 + (n + 7) / 8 : (m * n + 31) >> 5) == c) ? 1 : 0;
+        flag[k] = ((bf16 ? ((m + 15) / 16 - 1) * 4 + (n + 7) / 8 : f64_class(m, n)) == c) ? 1 : 0;
     }
 }
 
@@ -386,6 +500,23 @@ struct SmmTable {
 };
 using SmmF64 = SmmTable<1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18, 19, 20, 21, 22, 23, 24, 25,
                         26, 27, 28, 29, 30, 31, 32>;
+
+template <int... Es>
+struct SmmKsTable {
+    static SmmKernel get(int ef) {
+        SmmKernel t[] = {nullptr, &k_smm_f64_ks<Es, 1>...};
+        return (ef >= 1 && ef <= (int)sizeof...(Es)) ? t[ef] : nullptr;
+    }
+};
+using SmmF64Ks1 = SmmKsTable<1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18, 19, 20, 21, 22, 23, 24, 25,
+                             26, 27, 28, 29, 30, 31>;
+
+SmmKernel f64_kernel(int cls) {
+    if (cls == kF64Class13x13) return &k_smm_f64_ks<5, 9>;
+    if (cls > kF64ClassKs1 && cls < kF64Class13x13) return SmmF64Ks1::get(cls - kF64ClassKs1);
+    return SmmF64::get(cls);
+}
+
 
 // ------------------------------------------------------------ BF16 tensor-core SMM
 // BF16 operands (rounded to nearest even from FP64), FP32 accumulation on the
@@ -447,6 +578,12 @@ __global__ void __launch_bounds__(32 * kBf16Warps) k_smm_bf16(int64_t nlist, con
     __nv_bfloat16* sB = sA + kRowsA * kPanelLd;
     const __nv_bfloat16 zero = __float2bfloat16(0.0f);
     const int64_t warps = (int64_t)gridDim.x * kBf16Warps;
+    // Rows of A beyond m and columns of B beyond n only feed outputs that are
+    // discarded, but they must hold finite values: clear the panels once.  Later
+    // blocks leave earlier blocks' (finite) values there; the K padding of every
+    // panel is zeroed before its products are issued.
+    for (int e = lane; e < (kRowsA + kRowsB) * kPanelLd; e += 32) sA[e] = zero;
+    __syncwarp();
     for (int64_t w = (int64_t)blockIdx.x * kBf16Warps + wib; w < nlist; w += warps) {
         const int64_t k = list[w];
         const int I = S.f_row[k], J = S.f_col[k];
@@ -458,10 +595,6 @@ __global__ void __launch_bounds__(32 * kBf16Warps) k_smm_bf16(int64_t nlist, con
             for (int nt = 0; nt < NT; ++nt)
 #pragma unroll
                 for (int i = 0; i < 4; ++i) acc[mt][nt][i] = 0.f;
-        // rows of A beyond m and columns of B beyond n only feed discarded outputs,
-        // but must hold finite values: clear the panels once per block
-        for (int e = lane; e < (kRowsA + kRowsB) * kPanelLd; e += 32) sA[e] = zero;
-        __syncwarp();
         int koff = 0;
         const int64_t pb = S.f_pbeg[k], pe = S.f_pbeg[k + 1];
         for (int64_t base = pb; base < pe; base += 32) {
@@ -714,7 +847,7 @@ void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbc
     f_rp.alloc(nblk + 1, s);
     flops.alloc(1, s);
     flops.zero();
-    constexpr int kClasses = kMaxBlock * kMaxBlock / 32 + 1;      // FP64 classes E = 1..32
+    constexpr int kClasses = kF64Classes;                           // FP64 launch classes (f64_class)
     constexpr int kClassesBf16 = 9;                                 // BF16 classes (MT, NT) = 1..8
     class_cnt.alloc(kClasses + kClassesBf16, s);
     class_cnt.zero();
@@ -731,9 +864,8 @@ void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbc
     scan_exclusive(f_np.p, f_pbeg.p, nform, s);
     int64_t h3[3 + kClasses + kClassesBf16];
     {
-        const int64_t* src[3 + kClasses + kClassesBf16] = {f_off.p + nform, f_pbeg.p + nform, flops.p};
-        for (int c = 0; c < kClasses + kClassesBf16; ++c) src[3 + c] = class_cnt.p + c;
-        read_i64s(src, 3 + kClasses + kClassesBf16, h3, s);
+        const int64_t* src[3] = {f_off.p + nform, f_pbeg.p + nform, flops.p};
+        read_i64s(src, 3, h3, s, class_cnt.p, kClasses + kClassesBf16, h3 + 3);
     }
     const int64_t nel = h3[0], nprod = h3[1];
     const double nflop = (double)(unsigned long long)h3[2];
@@ -811,7 +943,7 @@ void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbc
                 SmmBf16Args ga{sa, a16.p, B != A ? b16.p : a16.p};
                 kern<<<grid_for(cnt, kBf16Warps, 152 * 64), 32 * kBf16Warps, sm, s>>>(cnt, list.p + at, ga);
             } else {
-                SmmKernel kern = SmmF64::get(c);
+                SmmKernel kern = f64_kernel(c);
                 if (!kern) fail(DBCSR_ECAPACITY, "multiply: block shape beyond the kernel table");
                 kern<<<grid_for(cnt, 8, 152 * 32), 256, 0, s>>>(cnt, list.p + at, sa);
             }
