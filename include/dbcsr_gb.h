@@ -183,6 +183,27 @@ dbcsr_status dbcsr_trace(dbcsr_matrix A, double* out);
 /* *out = Tr(A * B) = sum_IJ <A_IJ, B_JI^T>, without forming the product (synchronises). */
 dbcsr_status dbcsr_trace_product(dbcsr_matrix A, dbcsr_matrix B, double* out);
 
+/*
+ * *out_dev = Tr(A * B), like dbcsr_trace_product, but allocating nothing.  The
+ * paper has no counterpart: this entry point exists for callers that may not
+ * allocate device memory during the call -- an application whose own arena owns
+ * the GPU memory, code recording a CUDA graph that must not contain allocations,
+ * or a loop that cannot pay for the allocator.
+ *   - out_dev: device pointer to one double, owned by the caller; written in
+ *     stream order on A's stream.  The call does not synchronise; read the value
+ *     after the stream has reached it.  A and B must share that stream.
+ *   - Scratch is a fixed device array inside the library (8 MB + 8 KB on every
+ *     GPU that loads it, kept until the process exits), so A may hold at most
+ *     1,048,576 blocks; larger A fails with DBCSR_ECAPACITY before any work.
+ *   - The first call on each device looks up the array's device address with
+ *     that device current; make that first call before any stream capture.
+ *   - All calls share the one array: calls whose work overlaps on the GPU (on
+ *     different streams, or from several threads) race and give wrong values.
+ *     Each call writes every scratch word before reading it.
+ *   - Same kernels and summation order as dbcsr_trace_product.
+ */
+dbcsr_status dbcsr_trace_product_noalloc(dbcsr_matrix A, dbcsr_matrix B, double* out_dev);
+
 /* *out = max_i sum_j |(A - mu 1)_ij| (Gershgorin bound of the spectral radius; synchronises). */
 dbcsr_status dbcsr_gershgorin(dbcsr_matrix A, double mu, double* out);
 

@@ -169,6 +169,13 @@ def trace_product(A: Matrix, B: Matrix) -> float:
     return out.value
 
 
+def trace_product_noalloc(A: Matrix, B: Matrix, out_dev_ptr: int) -> None:
+    """Queues Tr(A*B) into the caller's device double at ``out_dev_ptr`` without any
+    device allocation (see dbcsr_trace_product_noalloc); does not synchronise."""
+    _check(lib().dbcsr_trace_product_noalloc(A.handle, B.handle, C.c_void_p(int(out_dev_ptr))),
+           "trace_product_noalloc")
+
+
 def gershgorin(M: Matrix, mu: float = 0.0) -> float:
     out = C.c_double()
     _check(lib().dbcsr_gershgorin(M.handle, float(mu), C.byref(out)), "gershgorin")

@@ -55,6 +55,7 @@ SIGNATURES = [
     ("dbcsr_filter", C.c_int, [P, C.c_double]),
     ("dbcsr_trace", C.c_int, [P, C.POINTER(C.c_double)]),
     ("dbcsr_trace_product", C.c_int, [P, P, C.POINTER(C.c_double)]),
+    ("dbcsr_trace_product_noalloc", C.c_int, [P, P, P]),
     ("dbcsr_gershgorin", C.c_int, [P, C.c_double, C.POINTER(C.c_double)]),
     ("dbcsr_sign_iterate", C.c_int, [P, C.c_double, C.POINTER(SignOpts), P, C.POINTER(SignReport)]),
     ("dbcsr_bench_peak", C.c_double, [C.c_int32, C.c_int32, C.c_int32, C.c_int32]),

@@ -25,6 +25,7 @@ struct Error : std::runtime_error {
 };
 
 [[noreturn]] void fail(dbcsr_status code, const std::string& msg);
+void set_last_error(const std::string& msg);
 extern std::atomic<int64_t> g_launches;
 
 #define DBG_CK(call)                                                                        \
@@ -130,6 +131,9 @@ void scan_exclusive(const int64_t* in, int64_t* out, int64_t n, cudaStream_t s);
 void scan_exclusive(const int32_t* in, int64_t* out, int64_t n, cudaStream_t s);
 // Deterministic sum of v[0..n-1] into *out (device); fixed reduction tree for a given n.
 void det_sum(const double* v, int64_t n, double* out, cudaStream_t s);
+// The same sum with a caller-given buffer of kDetSumPartials doubles for the per-CTA partials.
+constexpr int kDetSumPartials = 1024;
+void det_sum_into(const double* v, int64_t n, double* partials, double* out, cudaStream_t s);
 
 // ---- matrix.cu
 void check_finalized(const dbcsr_matrix_* m);
@@ -150,6 +154,8 @@ double read_f64(const double* dev, cudaStream_t s);
 double trace(dbcsr_matrix_* m);
 double trace_product(dbcsr_matrix_* a, dbcsr_matrix_* b);
 double gershgorin(dbcsr_matrix_* m, double mu);
+// part[b] = <A_b, B_JI^T> for every block b = (I, J) of A (the first stage of trace_product).
+void trace_product_parts_into(dbcsr_matrix_* a, dbcsr_matrix_* b, double* part, cudaStream_t s);
 
 // ---- multiply.cu
 void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbcsr_matrix_* C, double eps,

@@ -329,6 +329,7 @@ dbcsr_status guarded(F&& f) {
 
 namespace dbg {
 [[noreturn]] void fail(dbcsr_status code, const std::string& msg) { throw Error(code, msg); }
+void set_last_error(const std::string& msg) { g_last_error = msg; }
 }  // namespace dbg
 
 extern "C" {

@@ -130,4 +130,12 @@ double gershgorin(dbcsr_matrix_* m, double mu) {
     return read_f64(out.p, s);
 }
 
+void trace_product_parts_into(dbcsr_matrix_* a, dbcsr_matrix_* b, double* part, cudaStream_t s) {
+    if (a->nnzb == 0) return;
+    k_trace_product_blocks<<<grid_for(a->nnzb, 8), 256, 0, s>>>(a->nnzb, a->bs.p, a->row.p, a->col.p, a->off.p,
+                                                                a->data.p, b->rp.p, b->col.p, b->off.p, b->data.p,
+                                                                part);
+    DBG_LAUNCH_CK();
+}
+
 }  // namespace dbg

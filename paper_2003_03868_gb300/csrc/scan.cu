@@ -106,6 +106,7 @@ void scan_impl(const T* in, int64_t* out, int64_t n, cudaStream_t s) {
 
 constexpr int kSumThreads = 256;
 constexpr int kSumBlocks = 1024;
+static_assert(kSumBlocks == kDetSumPartials, "det_sum_into partial count");
 
 // Each CTA sums a fixed contiguous chunk (thread-strided, then a fixed tree).
 __global__ void k_sum_partials(const double* __restrict__ v, int64_t n, double* __restrict__ part) {
@@ -150,6 +151,17 @@ void det_sum(const double* v, int64_t n, double* out, cudaStream_t s) {
     k_sum_partials<<<kSumBlocks, kSumThreads, 0, s>>>(v, n, part.p);
     DBG_LAUNCH_CK();
     k_sum_final<<<1, 256, 0, s>>>(part.p, kSumBlocks, out);
+    DBG_LAUNCH_CK();
+}
+
+void det_sum_into(const double* v, int64_t n, double* partials, double* out, cudaStream_t s) {
+    if (n <= 0) {
+        DBG_CK(cudaMemsetAsync(out, 0, sizeof(double), s));
+        return;
+    }
+    k_sum_partials<<<kSumBlocks, kSumThreads, 0, s>>>(v, n, partials);
+    DBG_LAUNCH_CK();
+    k_sum_final<<<1, 256, 0, s>>>(partials, kSumBlocks, out);
     DBG_LAUNCH_CK();
 }
 
