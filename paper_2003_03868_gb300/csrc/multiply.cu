@@ -199,12 +199,13 @@ __global__ void k_cand_bound(int32_t nblk, RowPattern P, int nwords, BoundArgs B
 }
 
 // FP64 launch classes: 1..32 padded (E = ceil(m n / 32)); 33 + EF for m n = 32 EF + 1
-// (EF = 1..31, K-split remainder of one element); 65 for 13x13 (EF = 5, R = 9).
-constexpr int kF64ClassKs1 = 33, kF64Class13x13 = 65, kF64Classes = 66;
+// (EF = 1..31, K-split remainder of one element).  A K-split of more elements
+// (13x13: EF = 5, R = 9) measured slower than the padded class, because the
+// lanes' own products differ in k and the remainder loop diverges.
+constexpr int kF64ClassKs1 = 33, kF64Classes = 65;
 
 __device__ __forceinline__ int f64_class(int m, int n) {
     const int mn = m * n;
-    if (m == 13 && n == 13) return kF64Class13x13;
     if (mn > 32 && (mn & 31) == 1) return kF64ClassKs1 + (mn >> 5);
     return (mn + 31) >> 5;
 }
@@ -375,8 +376,7 @@ __global__ void __launch_bounds__(256) k_smm_f64(int64_t nlist, const int64_t* _
 // K instead: lane l takes the products l, l+32, ... of the block (the product
 // whose metadata it fetched) for all R elements, and a fixed xor-shuffle tree adds
 // the 32 partial sums.  For m*n = 32*EF + 1 (13x5, 5x13, 23x7, 7x23) this removes
-// a 32-lane pass that would carry one useful element; for 13x13 (EF = 5, R = 9) a
-// pass that would carry nine.
+// a 32-lane pass that would carry one useful element.
 template <int EF, int R>
 __global__ void __launch_bounds__(256) k_smm_f64_ks(int64_t nlist, const int64_t* __restrict__ list, SmmArgs S) {
     const int lane = threadIdx.x & 31;
@@ -512,8 +512,7 @@ using SmmF64Ks1 = SmmKsTable<1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 
                              26, 27, 28, 29, 30, 31>;
 
 SmmKernel f64_kernel(int cls) {
-    if (cls == kF64Class13x13) return &k_smm_f64_ks<5, 9>;
-    if (cls > kF64ClassKs1 && cls < kF64Class13x13) return SmmF64Ks1::get(cls - kF64ClassKs1);
+    if (cls > kF64ClassKs1 && cls < kF64Classes) return SmmF64Ks1::get(cls - kF64ClassKs1);
     return SmmF64::get(cls);
 }
 
