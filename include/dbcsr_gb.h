@@ -222,6 +222,27 @@ dbcsr_status dbcsr_gershgorin(dbcsr_matrix A, double mu, double* out);
 dbcsr_status dbcsr_sign_iterate(dbcsr_matrix H, double mu, const dbcsr_sign_opts* opts, dbcsr_matrix P_out,
                                 dbcsr_sign_report* rep);
 
+/*
+ * Solves nsys independent systems H[s] (each symmetric, all diagonal blocks
+ * present, any block sizes) as one batch: the matrices are stacked into one
+ * block-diagonal matrix, so every product forms all systems' blocks in the same
+ * kernel launches (one per block-shape class) -- the paper's batching of block
+ * products into stacks (section "Local multiplication") applied across systems.
+ * Per system: X_0 = (H[s] - mu[s] 1) / alpha_s with its own Gershgorin bound,
+ * its own residual ||X2_s - 1||_F / N_s, convergence and stall tests as in
+ * dbcsr_sign_iterate.  Systems that converge early keep iterating at their fixed
+ * point until all are done.  With DBCSR_MIXED the batch leaves the BF16 tier
+ * once any system's residual is below switch_tol.
+ *   H[nsys], mu[nsys] (host arrays); P_out[nsys]: created by the caller with the
+ *   block sizes of H[s], receive (1 - X_s) / 2; reps[nsys] (may be NULL):
+ *   per-system iterations, residuals, alpha, Tr(P), E_band; flops, products and
+ *   times are the batch totals.  Work runs on H[0]'s stream.  Returns
+ *   DBCSR_ENOTCONV if any system stopped without reaching tol.
+ */
+dbcsr_status dbcsr_sign_iterate_batched(int32_t nsys, const dbcsr_matrix* H, const double* mu,
+                                        const dbcsr_sign_opts* opts, dbcsr_matrix* P_out,
+                                        dbcsr_sign_report* reps);
+
 #ifdef __cplusplus
 }
 #endif

@@ -210,3 +210,22 @@ def sign_iterate(H: Matrix, mu: float, eps_filter: float, tol: float, max_iter: 
     if st != _ffi.DBCSR_OK and (st != _ffi.DBCSR_ENOTCONV or raise_on_notconv):
         _check(st, "sign_iterate")
     return SignResult(P=P, report=rep, status=st)
+
+
+def sign_iterate_batched(Hs, mus, eps_filter: float, tol: float, max_iter: int = 100, prec: int = DBCSR_FP64,
+                         switch_tol: float = 1e-4, stall_ratio: float = 0.5, verbose: bool = False):
+    """Density matrices of many independent systems in one batch (dbcsr_sign_iterate_batched).
+
+    Returns (list of P matrices, list of SignReport, status)."""
+    n = len(Hs)
+    Ps = [Matrix(h.blk_size, Hs[0].stream) for h in Hs]
+    harr = (C.c_void_p * n)(*[h.handle.value for h in Hs])
+    parr = (C.c_void_p * n)(*[p.handle.value for p in Ps])
+    mu = np.ascontiguousarray(mus, dtype=np.float64)
+    o = SignOpts(float(eps_filter), float(tol), int(max_iter), int(prec), float(switch_tol), float(stall_ratio),
+                 1 if verbose else 0, 0)
+    reps = (SignReport * n)()
+    st = lib().dbcsr_sign_iterate_batched(n, harr, _ptr(mu), C.byref(o), parr, reps)
+    if st not in (_ffi.DBCSR_OK, _ffi.DBCSR_ENOTCONV):
+        _check(st, "sign_iterate_batched")
+    return Ps, list(reps), st

@@ -58,6 +58,7 @@ SIGNATURES = [
     ("dbcsr_trace_product_noalloc", C.c_int, [P, P, P]),
     ("dbcsr_gershgorin", C.c_int, [P, C.c_double, C.POINTER(C.c_double)]),
     ("dbcsr_sign_iterate", C.c_int, [P, C.c_double, C.POINTER(SignOpts), P, C.POINTER(SignReport)]),
+    ("dbcsr_sign_iterate_batched", C.c_int, [C.c_int32, P, P, C.POINTER(SignOpts), P, P]),
     ("dbcsr_bench_peak", C.c_double, [C.c_int32, C.c_int32, C.c_int32, C.c_int32]),
     ("dbcsr_launch_count", C.c_int64, []),
 ]

@@ -285,31 +285,48 @@ def decay_matrix(wb: WaterBox, basis: tuple[int, int], seed: int,
     ustart = np.zeros(ui.shape[0], dtype=np.int64)
     np.cumsum(uarea[:-1], out=ustart[1:])
     s_val = splitmix.substream(seed, _TAG_VAL)
-    sizes = np.unique(bs)
-    for bm in sizes:
-        for bn in sizes:
-            shape_sel = np.nonzero((bs[ui] == bm) & (bs[uj] == bn))[0]
-            if shape_sel.size == 0:
-                continue
-            area = int(bm) * int(bn)
-            ar = np.arange(area, dtype=np.int64)
-            for sel in _chunks(shape_sel, area):
-                cnt = (ustart[sel][:, None] + ar[None, :]).astype(np.uint64)
-                u = splitmix.uniform_pm1(s_val, cnt).reshape(-1, bm, bn)
-                dg = ui[sel] == uj[sel]
-                fac = np.exp(-decay * r[sel] * r[sel])
-                vals = u * fac[:, None, None]
-                if dg.any():
-                    d = vals[dg]
-                    d = 0.5 * (d + np.transpose(d, (0, 2, 1)))
-                    d = d + shift * np.eye(bm)[None, :, :]
-                    vals[dg] = d
-                tgt = boff[pos_up[sel]][:, None] + ar[None, :]
-                data[tgt] = vals.reshape(-1, area)
-                nd = ~dg
-                if nd.any():
-                    tgt = boff[pos_lo[sel[nd]]][:, None] + ar[None, :]
-                    data[tgt] = np.transpose(vals[nd], (0, 2, 1)).reshape(-1, area)
+    nnzb = col.shape[0]
+    rows = m.rows()
+    # source upper pair of every CSR block and whether the block is its mirror
+    src = np.empty(nnzb, dtype=np.int64)
+    src[pos_up] = np.arange(ui.shape[0])
+    mirror = np.zeros(nnzb, dtype=bool)
+    offd = ui != uj
+    src[pos_lo[offd]] = np.nonzero(offd)[0]
+    mirror[pos_lo[offd]] = True
+    fac_blk = np.exp(-decay * r * r)[src]
+    mb = bs[rows].astype(np.int64)
+    nb = bs[col].astype(np.int64)
+    # walk the output in CSR order, a chunk of whole blocks at a time: element
+    # (a, c) of block b draws counter ustart[src] + a*nb + c, or, for a mirrored
+    # block, the counter of element (c, a) of its source: ustart[src] + c*mb + a
+    chunk = 1 << 20
+    b0 = 0
+    while b0 < nnzb:
+        b1 = int(np.searchsorted(boff, boff[b0] + chunk, side="right"))
+        b1 = max(b1, b0 + 1)
+        b1 = min(b1, nnzb)
+        e0, e1 = int(boff[b0]), int(boff[b1 - 1] + area_csr[b1 - 1])
+        cnt_b = area_csr[b0:b1]
+        blk = np.repeat(np.arange(b0, b1), cnt_b)
+        local = np.arange(e1 - e0, dtype=np.int64) - np.repeat(boff[b0:b1] - e0, cnt_b)
+        nbe = nb[blk]
+        a_ = local // nbe
+        c_ = local - a_ * nbe
+        ctr = ustart[src[blk]] + np.where(mirror[blk], c_ * mb[blk] + a_, local)
+        data[e0:e1] = splitmix.uniform_pm1(s_val, ctr.astype(np.uint64)) * fac_blk[blk]
+        b0 = b1
+    # diagonal blocks: (U + U^T) / 2 + shift * 1 (U drawn as above, exp(0) = 1)
+    dg = np.nonzero(rows == col)[0]
+    for bm_ in np.unique(bs):
+        sel = dg[bs[rows[dg]] == bm_]
+        if sel.size == 0:
+            continue
+        area = int(bm_) * int(bm_)
+        idx = boff[sel][:, None] + np.arange(area, dtype=np.int64)[None, :]
+        u = data[idx].reshape(-1, bm_, bm_)
+        d = 0.5 * (u + np.transpose(u, (0, 2, 1))) + shift * np.eye(bm_)[None, :, :]
+        data[idx] = d.reshape(-1, area)
     return m, (ui, uj, r, pos_up, pos_lo)
 
 

@@ -1,0 +1,70 @@
+"""Batched sign iteration (many uneven systems in one block-diagonal batch) against
+the FP64 oracle per system and against the single-system GPU path."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import bsr, sign
+
+pytestmark = pytest.mark.gpu
+
+DE_ATOM = 1e-6
+
+
+@pytest.fixture(scope="module")
+def gb():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2003_03868_gb300 as m
+    m.lib()
+    return m
+
+
+def _systems(n, seed):
+    out = []
+    rng = np.random.default_rng(seed)
+    bases = [(13, 5), (23, 7), (13, 7), (23, 5)]
+    for s in range(n):
+        w = synth.small(int(rng.integers(6, 40)), basis=bases[s % 4], seed=seed * 100 + s)
+        out.append(synth.build_hamiltonian(w))
+    return out
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_batch_matches_oracle_per_system(gb, prec):
+    hs = _systems(6, 17)
+    Hs = [gb.Matrix.of(h.H) for h in hs]
+    p = gb.DBCSR_FP64 if prec == "fp64" else gb.DBCSR_MIXED
+    Ps, reps, st = gb.sign_iterate_batched(Hs, [0.0] * len(hs), 1e-7, 1e-8, prec=p)
+    for h, P, r in zip(hs, Ps, reps):
+        o = sign.sign_iterate(bsr.Mat.of(h.H), 0.0, 1e-7, 1e-8)
+        assert r.alpha == pytest.approx(o.alpha, rel=1e-15)
+        assert r.converged or r.stalled
+        assert abs(r.e_band - o.e_band) / h.n_atoms < (1e-7 if prec == "fp64" else DE_ATOM)
+        assert r.trace_p == pytest.approx(h.n_occ, abs=1e-5)
+        if prec == "fp64":
+            assert r.iterations == o.iterations
+            np.testing.assert_allclose([r.residual_history[i] for i in range(r.iterations)], o.residuals,
+                                       rtol=1e-6, atol=1e-13)
+        rp, col, data = P.export()
+        assert rp.shape[0] == h.H.nblk + 1
+
+
+def test_batch_equals_single_system_runs(gb):
+    hs = _systems(5, 23)
+    Hs = [gb.Matrix.of(h.H) for h in hs]
+    Ps, reps, st = gb.sign_iterate_batched(Hs, [0.0] * len(hs), 1e-7, 1e-9)
+    for h, H, r in zip(hs, Hs, reps):
+        g = gb.sign_iterate(H, 0.0, 1e-7, 1e-9)
+        assert abs(r.e_band - g.report.e_band) / h.n_atoms < 1e-9
+        assert r.iterations == g.report.iterations
+
+
+def test_batch_of_one_and_different_mu(gb):
+    h = _systems(1, 29)[0]
+    H = gb.Matrix.of(h.H)
+    Ps, reps, st = gb.sign_iterate_batched([H, H], [0.0, 0.1], 0.0, 1e-11)
+    # mu anywhere in the gap gives the same projector
+    assert abs(reps[0].e_band - reps[1].e_band) < 1e-8
+    assert reps[0].alpha != reps[1].alpha
