@@ -222,6 +222,103 @@ dbcsr_status dbcsr_gershgorin(dbcsr_matrix A, double mu, double* out);
 dbcsr_status dbcsr_sign_iterate(dbcsr_matrix H, double mu, const dbcsr_sign_opts* opts, dbcsr_matrix P_out,
                                 dbcsr_sign_report* rep);
 
+/* Launch configuration of the block-product kernel of one (m, n, k) stack.  No
+ * field changes the arithmetic: every C element is summed in the same order. */
+typedef struct {
+    int32_t tpb;          /* threads per CTA: 64, 128 or 256 */
+    int32_t ctas_per_sm;  /* grid = min(C blocks / warps per CTA, 152 * ctas_per_sm) */
+    int32_t colmajor;     /* FP64: lane-to-element order, 0 row-major, 1 column-major */
+    int32_t prefetch2;    /* FP64: 1 = fetch the next 32 products' metadata ahead */
+} dbcsr_kernel_cfg;
+
+/* One timing of the autotuner. */
+typedef struct {
+    int32_t m, n, k, prec;
+    dbcsr_kernel_cfg cfg;
+    double ms;            /* median time of one launch over the synthetic stack */
+    double gflops;        /* 2 m n k * stack_len / time */
+} dbcsr_tune_record;
+
+/* The configurations the autotuner times for prec (DBCSR_FP64 or DBCSR_BF16):
+ * *n receives their number; up to cap of them are written to out (may be NULL). */
+dbcsr_status dbcsr_tune_space(int32_t prec, dbcsr_kernel_cfg* out, int32_t cap, int32_t* n);
+
+/*
+ * Autotuner (section "Batched execution": kernels are tuned per (m, n, k) over
+ * their parameters and the best parameter set kept).  For each triple
+ * mnk[3t..3t+2] (each in [1, 32]) a synthetic stack of stack_len products is
+ * built on the device (C blocks of ~27 products, A/B blocks drawn from pools of
+ * 20,000), every configuration of dbcsr_tune_space is launched reps times
+ * (median taken) and the fastest becomes the tuned entry (prec, m, n, k) that
+ * dbcsr_multiply uses for its m x n blocks when the largest block edge of the
+ * matrix is k.  Up to cap timings go to recs (may be NULL); *nrec = their total.
+ */
+dbcsr_status dbcsr_autotune(const int32_t* mnk, int32_t ntriples, int32_t prec, int64_t stack_len, int32_t reps,
+                            dbcsr_tune_record* recs, int64_t cap, int64_t* nrec);
+
+/* Times ncfg given configurations on the synthetic (m, n, k) stack: ms_out[i]. */
+dbcsr_status dbcsr_time_config(int32_t prec, int32_t m, int32_t n, int32_t k, int64_t stack_len, int32_t reps,
+                               const dbcsr_kernel_cfg* cfgs, int32_t ncfg, double* ms_out);
+
+/* Tune table: set (cfg NULL removes), get (*found = 0 and the default when absent),
+ * clear, and save/load as text lines "prec m n k tpb ctas_per_sm colmajor prefetch2". */
+dbcsr_status dbcsr_tune_set(int32_t prec, int32_t m, int32_t n, int32_t k, const dbcsr_kernel_cfg* cfg);
+dbcsr_status dbcsr_tune_get(int32_t prec, int32_t m, int32_t n, int32_t k, dbcsr_kernel_cfg* cfg, int* found);
+dbcsr_status dbcsr_tune_clear(void);
+dbcsr_status dbcsr_tune_save(const char* path);
+dbcsr_status dbcsr_tune_load(const char* path);
+
+/*
+ * Performance-prediction MLP (section "Batched execution": the autotuning data
+ * train a model that predicts near-optimal parameters of the untuned kernels).
+ * Model: DBCSR_MLP_FEATURES inputs -> 64 ReLU -> 64 ReLU -> 1, FP32, trained on
+ * the GPU (full-batch mean squared error, Adam); parameters are a flat host
+ * array of dbcsr_mlp_param_count(nfeat) floats:
+ *   W1[64][nfeat], b1[64], W2[64][64], b2[64], W3[64], b3.
+ * Targets are whatever the caller regresses (the tests use standardised log times).
+ */
+#define DBCSR_MLP_FEATURES 10
+
+typedef struct {
+    int32_t epochs;       /* full-batch Adam steps */
+    int32_t reserved;
+    double lr, beta1, beta2, eps;
+} dbcsr_mlp_opts;
+
+typedef struct {
+    float loss_first;     /* mean squared error before the first step */
+    float loss_last;      /* after the last step */
+    double ms;            /* device time of the training */
+    int32_t epochs;
+    int32_t reserved;
+} dbcsr_mlp_report;
+
+int64_t dbcsr_mlp_param_count(int32_t nfeat);
+
+/* Glorot-uniform weights (SplitMix64 stream of seed), zero biases, into params. */
+dbcsr_status dbcsr_mlp_init(int32_t nfeat, uint64_t seed, float* params);
+
+/* Features of samples (m, n, k, cfg): mnk[3i..3i+2], cfgs[i] -> out[i * DBCSR_MLP_FEATURES ...]:
+ * m/32, n/32, k/32, log2(m n k)/15, useful fraction of the lanes (FP64) or tensor tiles (BF16),
+ * K-split flag, tpb/256, log2(ctas_per_sm)/6, colmajor, prefetch2. */
+dbcsr_status dbcsr_mlp_features(int32_t prec, const int32_t* mnk, const dbcsr_kernel_cfg* cfgs, int64_t n, float* out);
+
+/* y_out[b] = model(X[b * nfeat ...]) for B samples (host arrays; runs on the GPU). */
+dbcsr_status dbcsr_mlp_forward(int32_t nfeat, const float* params, const float* X, int64_t B, float* y_out);
+
+/* Mean squared error over B samples and its gradient with respect to every parameter. */
+dbcsr_status dbcsr_mlp_loss_grad(int32_t nfeat, const float* params, const float* X, const float* T, int64_t B,
+                                 float* loss, float* grad);
+
+/* Trains params in place: opts->epochs full-batch Adam steps on the GPU. */
+dbcsr_status dbcsr_mlp_train(int32_t nfeat, float* params, const float* X, const float* T, int64_t B,
+                             const dbcsr_mlp_opts* opts, dbcsr_mlp_report* rep);
+
+/* For each triple, the configuration of dbcsr_tune_space(prec) with the lowest
+ * predicted value (and that value in best_pred, may be NULL). */
+dbcsr_status dbcsr_mlp_predict_best(int32_t prec, const float* params, const int32_t* mnk, int32_t ntriples,
+                                    dbcsr_kernel_cfg* best, float* best_pred);
+
 /*
  * Solves nsys independent systems H[s] (each symmetric, all diagonal blocks
  * present, any block sizes) as one batch: the matrices are stacked into one

@@ -17,6 +17,7 @@ import numpy as np
 
 from . import _ffi
 from ._ffi import DBCSR_FP64, DBCSR_BF16, DBCSR_MIXED, MultStats, SignOpts, SignReport  # noqa: F401
+from ._ffi import KernelCfg, TuneRecord, MlpOpts, MlpReport, MLP_FEATURES  # noqa: F401
 
 
 class DbcsrError(RuntimeError):
@@ -229,3 +230,116 @@ def sign_iterate_batched(Hs, mus, eps_filter: float, tol: float, max_iter: int =
     if st not in (_ffi.DBCSR_OK, _ffi.DBCSR_ENOTCONV):
         _check(st, "sign_iterate_batched")
     return Ps, list(reps), st
+
+
+# ------------------------------------------------------------------ autotuner
+def tune_space(prec: int = DBCSR_FP64):
+    """The launch configurations the autotuner times for ``prec``."""
+    n = C.c_int32()
+    _check(lib().dbcsr_tune_space(int(prec), None, 0, C.byref(n)), "tune_space")
+    arr = (KernelCfg * n.value)()
+    _check(lib().dbcsr_tune_space(int(prec), arr, n.value, C.byref(n)), "tune_space")
+    return list(arr)
+
+
+def autotune(triples, prec: int = DBCSR_FP64, stack_len: int = 100000, reps: int = 5):
+    """Times every configuration on a synthetic stack per (m, n, k); the fastest
+    enters the tune table.  Returns the list of TuneRecord timings."""
+    t = np.ascontiguousarray(np.asarray(triples, dtype=np.int32).reshape(-1, 3))
+    cap = t.shape[0] * len(tune_space(prec))
+    recs = (TuneRecord * cap)()
+    n = C.c_int64()
+    _check(lib().dbcsr_autotune(_ptr(t), int(t.shape[0]), int(prec), int(stack_len), int(reps), recs, cap,
+                                C.byref(n)), "autotune")
+    return list(recs)[:n.value]
+
+
+def time_configs(m: int, n: int, k: int, cfgs, prec: int = DBCSR_FP64, stack_len: int = 100000, reps: int = 5):
+    """Median launch time (ms) of each configuration on the synthetic (m, n, k) stack."""
+    arr = (KernelCfg * len(cfgs))(*cfgs)
+    out = np.zeros(len(cfgs))
+    _check(lib().dbcsr_time_config(int(prec), int(m), int(n), int(k), int(stack_len), int(reps), arr, len(cfgs),
+                                   _ptr(out)), "time_config")
+    return out
+
+
+def tune_set(prec: int, m: int, n: int, k: int, cfg):
+    _check(lib().dbcsr_tune_set(int(prec), int(m), int(n), int(k), C.byref(cfg) if cfg is not None else None),
+           "tune_set")
+
+
+def tune_get(prec: int, m: int, n: int, k: int):
+    """(config, found) of the tune table entry (the default configuration when absent)."""
+    c, f = KernelCfg(), C.c_int()
+    _check(lib().dbcsr_tune_get(int(prec), int(m), int(n), int(k), C.byref(c), C.byref(f)), "tune_get")
+    return c, bool(f.value)
+
+
+def tune_clear():
+    _check(lib().dbcsr_tune_clear(), "tune_clear")
+
+
+def tune_save(path: str):
+    _check(lib().dbcsr_tune_save(path.encode()), "tune_save")
+
+
+def tune_load(path: str):
+    _check(lib().dbcsr_tune_load(path.encode()), "tune_load")
+
+
+# ------------------------------------------------------------------ prediction model
+def mlp_init(nfeat: int = MLP_FEATURES, seed: int = 1):
+    p = np.zeros(lib().dbcsr_mlp_param_count(int(nfeat)), dtype=np.float32)
+    _check(lib().dbcsr_mlp_init(int(nfeat), int(seed), _ptr(p)), "mlp_init")
+    return p
+
+
+def mlp_features(triples, cfgs, prec: int = DBCSR_FP64):
+    """Feature rows of samples (m, n, k, cfg); ``triples`` [n, 3], ``cfgs`` a list of KernelCfg."""
+    t = np.ascontiguousarray(np.asarray(triples, dtype=np.int32).reshape(-1, 3))
+    arr = (KernelCfg * len(cfgs))(*cfgs)
+    out = np.zeros((t.shape[0], MLP_FEATURES), dtype=np.float32)
+    _check(lib().dbcsr_mlp_features(int(prec), _ptr(t), arr, int(t.shape[0]), _ptr(out)), "mlp_features")
+    return out
+
+
+def mlp_forward(params, X):
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    y = np.zeros(X.shape[0], dtype=np.float32)
+    _check(lib().dbcsr_mlp_forward(int(X.shape[1]), _ptr(p), _ptr(X), int(X.shape[0]), _ptr(y)), "mlp_forward")
+    return y
+
+
+def mlp_loss_grad(params, X, T):
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    T = np.ascontiguousarray(T, dtype=np.float32)
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    g = np.zeros_like(p)
+    loss = C.c_float()
+    _check(lib().dbcsr_mlp_loss_grad(int(X.shape[1]), _ptr(p), _ptr(X), _ptr(T), int(X.shape[0]), C.byref(loss),
+                                     _ptr(g)), "mlp_loss_grad")
+    return float(loss.value), g
+
+
+def mlp_train(params, X, T, epochs: int = 2000, lr: float = 1e-3, beta1: float = 0.9, beta2: float = 0.999,
+              eps: float = 1e-8):
+    """Trains a copy of ``params`` on the GPU; returns (params, MlpReport)."""
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    T = np.ascontiguousarray(T, dtype=np.float32)
+    p = np.array(params, dtype=np.float32, copy=True)
+    o = MlpOpts(int(epochs), 0, float(lr), float(beta1), float(beta2), float(eps))
+    r = MlpReport()
+    _check(lib().dbcsr_mlp_train(int(X.shape[1]), _ptr(p), _ptr(X), _ptr(T), int(X.shape[0]), C.byref(o),
+                                 C.byref(r)), "mlp_train")
+    return p, r
+
+
+def mlp_predict_best(params, triples, prec: int = DBCSR_FP64):
+    """Predicted-fastest configuration of every triple (list of KernelCfg)."""
+    t = np.ascontiguousarray(np.asarray(triples, dtype=np.int32).reshape(-1, 3))
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    best = (KernelCfg * t.shape[0])()
+    _check(lib().dbcsr_mlp_predict_best(int(prec), _ptr(p), _ptr(t), int(t.shape[0]), best, None),
+           "mlp_predict_best")
+    return list(best)

@@ -36,6 +36,27 @@ class SignReport(C.Structure):
                 ("residual_history", C.c_double * MAX_HISTORY), ("nnzb_history", C.c_int64 * MAX_HISTORY)]
 
 
+class KernelCfg(C.Structure):
+    _fields_ = [("tpb", C.c_int32), ("ctas_per_sm", C.c_int32), ("colmajor", C.c_int32), ("prefetch2", C.c_int32)]
+
+
+class TuneRecord(C.Structure):
+    _fields_ = [("m", C.c_int32), ("n", C.c_int32), ("k", C.c_int32), ("prec", C.c_int32), ("cfg", KernelCfg),
+                ("ms", C.c_double), ("gflops", C.c_double)]
+
+
+class MlpOpts(C.Structure):
+    _fields_ = [("epochs", C.c_int32), ("reserved", C.c_int32), ("lr", C.c_double), ("beta1", C.c_double),
+                ("beta2", C.c_double), ("eps", C.c_double)]
+
+
+class MlpReport(C.Structure):
+    _fields_ = [("loss_first", C.c_float), ("loss_last", C.c_float), ("ms", C.c_double), ("epochs", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
+MLP_FEATURES = 10
+
 # (name, restype, argtypes) of every exported entry point
 P = C.c_void_p
 SIGNATURES = [
@@ -59,6 +80,21 @@ SIGNATURES = [
     ("dbcsr_gershgorin", C.c_int, [P, C.c_double, C.POINTER(C.c_double)]),
     ("dbcsr_sign_iterate", C.c_int, [P, C.c_double, C.POINTER(SignOpts), P, C.POINTER(SignReport)]),
     ("dbcsr_sign_iterate_batched", C.c_int, [C.c_int32, P, P, C.POINTER(SignOpts), P, P]),
+    ("dbcsr_tune_space", C.c_int, [C.c_int32, P, C.c_int32, C.POINTER(C.c_int32)]),
+    ("dbcsr_autotune", C.c_int, [P, C.c_int32, C.c_int32, C.c_int64, C.c_int32, P, C.c_int64, C.POINTER(C.c_int64)]),
+    ("dbcsr_time_config", C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int64, C.c_int32, P, C.c_int32, P]),
+    ("dbcsr_tune_set", C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_int32, P]),
+    ("dbcsr_tune_get", C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_int32, P, C.POINTER(C.c_int)]),
+    ("dbcsr_tune_clear", C.c_int, []),
+    ("dbcsr_tune_save", C.c_int, [C.c_char_p]),
+    ("dbcsr_tune_load", C.c_int, [C.c_char_p]),
+    ("dbcsr_mlp_param_count", C.c_int64, [C.c_int32]),
+    ("dbcsr_mlp_init", C.c_int, [C.c_int32, C.c_uint64, P]),
+    ("dbcsr_mlp_features", C.c_int, [C.c_int32, P, P, C.c_int64, P]),
+    ("dbcsr_mlp_forward", C.c_int, [C.c_int32, P, P, C.c_int64, P]),
+    ("dbcsr_mlp_loss_grad", C.c_int, [C.c_int32, P, P, P, C.c_int64, C.POINTER(C.c_float), P]),
+    ("dbcsr_mlp_train", C.c_int, [C.c_int32, P, P, P, C.c_int64, C.POINTER(MlpOpts), C.POINTER(MlpReport)]),
+    ("dbcsr_mlp_predict_best", C.c_int, [C.c_int32, P, P, C.c_int32, P, P]),
     ("dbcsr_bench_peak", C.c_double, [C.c_int32, C.c_int32, C.c_int32, C.c_int32]),
     ("dbcsr_launch_count", C.c_int64, []),
 ]

@@ -28,6 +28,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "smm.cuh"
 
 namespace dbg {
 
@@ -204,11 +205,6 @@ __global__ void k_cand_bound(int32_t nblk, RowPattern P, int nwords, BoundArgs B
 // lanes' own products differ in k and the remainder loop diverges.
 constexpr int kF64ClassKs1 = 33, kF64Classes = 65;
 
-__device__ __forceinline__ int f64_class(int m, int n) {
-    const int mn = m * n;
-    if (mn > 32 && (mn & 31) == 1) return kF64ClassKs1 + (mn >> 5);
-    return (mn + 31) >> 5;
-}
 
 __global__ void k_form_meta(int64_t ncand, const int32_t* __restrict__ keep, const int64_t* __restrict__ kidx,
                             const int32_t* __restrict__ cand_row, const int32_t* __restrict__ cand_col,
@@ -216,7 +212,7 @@ __global__ void k_form_meta(int64_t ncand, const int32_t* __restrict__ keep, con
                             const int64_t* __restrict__ cin, const int32_t* __restrict__ bs,
                             int32_t* __restrict__ f_row, int32_t* __restrict__ f_col, int64_t* __restrict__ f_area,
                             int64_t* __restrict__ f_np, int64_t* __restrict__ f_cin,
-                            unsigned long long* __restrict__ flops, unsigned long long* __restrict__ class_cnt) {
+                            unsigned long long* __restrict__ flops, unsigned long long* __restrict__ shape_cnt) {
     unsigned long long local = 0;
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncand; c += (int64_t)gridDim.x * blockDim.x) {
         if (!keep[c]) continue;
@@ -228,8 +224,7 @@ __global__ void k_form_meta(int64_t ncand, const int32_t* __restrict__ keep, con
         f_np[k] = pcnt[c];
         f_cin[k] = cin ? cin[c] : -1;
         local += 2ull * (unsigned long long)bs[I] * (unsigned long long)bs[J] * (unsigned long long)ksum[c];
-        atomicAdd(class_cnt + f64_class(bs[I], bs[J]), 1ull);
-        atomicAdd(class_cnt + kF64Classes + ((bs[I] + 15) / 16 - 1) * 4 + (bs[J] + 7) / 8, 1ull);
+        atomicAdd(shape_cnt + bs[I] * (kMaxBlock + 1) + bs[J], 1ull);
     }
     for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
     if ((threadIdx.x & 31) == 0 && local) atomicAdd(flops, local);
@@ -283,16 +278,31 @@ __global__ void k_fill_stack(int32_t nblk, RowPattern P, int nwords, FillArgs F)
 }
 
 // ----------------------------------------------------------------- FP64 SMM
-struct SmmArgs {
-    const int32_t* f_row; const int32_t* f_col; const int64_t* f_off; const int64_t* f_pbeg; const int64_t* f_cin;
-    const int32_t* prod_a; const int32_t* prod_b;
-    const int32_t* a_col; const int64_t* a_off; const double* a_data;
-    const int64_t* b_off; const double* b_data;
-    const int64_t* ci_off; const double* ci_data;
-    const int32_t* bs;
-    double alpha, beta;
-    double* c_data; double* c_norm; double* c_dev2;
+__device__ __forceinline__ void elem_of(int idx, int m, int n, int colmajor, int& i, int& j) {
+    if (colmajor) {
+        j = idx / m;
+        i = idx - j * m;
+    } else {
+        i = idx / n;
+        j = idx - i * n;
+    }
+}
+
+struct ProdMeta {
+    int64_t ao, bo;
+    int kq;
 };
+
+__device__ __forceinline__ ProdMeta fetch_meta(const SmmArgs& S, int64_t base, int64_t pe, int lane) {
+    ProdMeta m{0, 0, 0};
+    if (base + lane < pe) {
+        const int32_t ai = S.prod_a[base + lane], bi = S.prod_b[base + lane];
+        m.ao = S.a_off[ai];
+        m.bo = S.b_off[bi];
+        m.kq = S.bs[S.a_col[ai]];
+    }
+    return m;
+}
 
 // One warp per C block of class E (m*n <= 32*E): lane l owns elements l, l+32,
 // ..., sums its products in stack order (ascending K, then k) with FMA, and
@@ -314,26 +324,22 @@ __global__ void __launch_bounds__(256) k_smm_f64(int64_t nlist, const int64_t* _
 #pragma unroll
         for (int e = 0; e < E; ++e) {
             const int idx = lane + 32 * e;
-            const int i = idx < mn ? idx / n : 0;
+            int i = 0, j = 0;
+            if (idx < mn) elem_of(idx, m, n, S.colmajor, i, j);
             ii[e] = i;
-            jj[e] = idx < mn ? idx - i * n : 0;
+            jj[e] = j;
             acc[e] = 0.0;
         }
         const int64_t pb = S.f_pbeg[k], pe = S.f_pbeg[k + 1];
+        ProdMeta cur = fetch_meta(S, pb, pe, lane);
         for (int64_t base = pb; base < pe; base += 32) {
             const int cnt = (int)min((int64_t)32, pe - base);
-            int64_t ao = 0, bo = 0;
-            int kq = 0;
-            if (lane < cnt) {
-                const int32_t ai = S.prod_a[base + lane], bi = S.prod_b[base + lane];
-                ao = S.a_off[ai];
-                bo = S.b_off[bi];
-                kq = S.bs[S.a_col[ai]];
-            }
+            ProdMeta nxt{0, 0, 0};
+            if (S.prefetch2) nxt = fetch_meta(S, base + 32, pe, lane);
             for (int q = 0; q < cnt; ++q) {
-                const int64_t aoq = __shfl_sync(0xffffffffu, ao, q);
-                const int64_t boq = __shfl_sync(0xffffffffu, bo, q);
-                const int kk = __shfl_sync(0xffffffffu, kq, q);
+                const int64_t aoq = __shfl_sync(0xffffffffu, cur.ao, q);
+                const int64_t boq = __shfl_sync(0xffffffffu, cur.bo, q);
+                const int kk = __shfl_sync(0xffffffffu, cur.kq, q);
                 const double* __restrict__ A = S.a_data + aoq;
                 const double* __restrict__ B = S.b_data + boq;
                 for (int t = 0; t < kk; ++t) {
@@ -342,6 +348,7 @@ __global__ void __launch_bounds__(256) k_smm_f64(int64_t nlist, const int64_t* _
                         acc[e] = fma(__ldg(A + ii[e] * kk + t), __ldg(B + t * n + jj[e]), acc[e]);
                 }
             }
+            cur = S.prefetch2 ? nxt : fetch_meta(S, base + 32, pe, lane);
         }
         const int64_t ci = S.f_cin[k];
         const double* cin = ci >= 0 ? S.ci_data + S.ci_off[ci] : nullptr;
@@ -351,9 +358,10 @@ __global__ void __launch_bounds__(256) k_smm_f64(int64_t nlist, const int64_t* _
         for (int e = 0; e < E; ++e) {
             const int idx = lane + 32 * e;
             if (idx < mn) {
+                const int pos = ii[e] * n + jj[e];
                 double v = S.alpha * acc[e];
-                if (cin) v = v + S.beta * cin[idx];
-                out[idx] = v;
+                if (cin) v = v + S.beta * cin[pos];
+                out[pos] = v;
                 sq = fma(v, v, sq);
                 const double wv = (I == J && ii[e] == jj[e]) ? v - 1.0 : v;
                 d = fma(wv, wv, d);
@@ -384,38 +392,29 @@ __global__ void __launch_bounds__(256) k_smm_f64_ks(int64_t nlist, const int64_t
     for (int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < nlist; w += warps) {
         const int64_t k = list[w];
         const int I = S.f_row[k], J = S.f_col[k];
-        const int n = S.bs[J];
+        const int m = S.bs[I], n = S.bs[J];
         int ii[EF], jj[EF], ir[R], jr[R];
         double acc[EF], rem[R];
 #pragma unroll
         for (int e = 0; e < EF; ++e) {
-            const int idx = lane + 32 * e;
-            ii[e] = idx / n;
-            jj[e] = idx - ii[e] * n;
+            elem_of(lane + 32 * e, m, n, S.colmajor, ii[e], jj[e]);
             acc[e] = 0.0;
         }
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            const int idx = 32 * EF + r;
-            ir[r] = idx / n;
-            jr[r] = idx - ir[r] * n;
+            elem_of(32 * EF + r, m, n, S.colmajor, ir[r], jr[r]);
             rem[r] = 0.0;
         }
         const int64_t pb = S.f_pbeg[k], pe = S.f_pbeg[k + 1];
+        ProdMeta cur = fetch_meta(S, pb, pe, lane);
         for (int64_t base = pb; base < pe; base += 32) {
             const int cnt = (int)min((int64_t)32, pe - base);
-            int64_t ao = 0, bo = 0;
-            int kq = 0;
-            if (lane < cnt) {
-                const int32_t ai = S.prod_a[base + lane], bi = S.prod_b[base + lane];
-                ao = S.a_off[ai];
-                bo = S.b_off[bi];
-                kq = S.bs[S.a_col[ai]];
-            }
+            ProdMeta nxt{0, 0, 0};
+            if (S.prefetch2) nxt = fetch_meta(S, base + 32, pe, lane);
             for (int q = 0; q < cnt; ++q) {
-                const int64_t aoq = __shfl_sync(0xffffffffu, ao, q);
-                const int64_t boq = __shfl_sync(0xffffffffu, bo, q);
-                const int kk = __shfl_sync(0xffffffffu, kq, q);
+                const int64_t aoq = __shfl_sync(0xffffffffu, cur.ao, q);
+                const int64_t boq = __shfl_sync(0xffffffffu, cur.bo, q);
+                const int kk = __shfl_sync(0xffffffffu, cur.kq, q);
                 const double* __restrict__ A = S.a_data + aoq;
                 const double* __restrict__ B = S.b_data + boq;
                 for (int t = 0; t < kk; ++t) {
@@ -425,12 +424,14 @@ __global__ void __launch_bounds__(256) k_smm_f64_ks(int64_t nlist, const int64_t
                 }
             }
             // remainder: this lane's own product (kq = 0 past the end of the list)
-            const double* __restrict__ A = S.a_data + ao;
-            const double* __restrict__ B = S.b_data + bo;
-            for (int t = 0; t < kq; ++t) {
+            const double* __restrict__ A = S.a_data + cur.ao;
+            const double* __restrict__ B = S.b_data + cur.bo;
+            for (int t = 0; t < cur.kq; ++t) {
 #pragma unroll
-                for (int r = 0; r < R; ++r) rem[r] = fma(__ldg(A + ir[r] * kq + t), __ldg(B + t * n + jr[r]), rem[r]);
+                for (int r = 0; r < R; ++r)
+                    rem[r] = fma(__ldg(A + ir[r] * cur.kq + t), __ldg(B + t * n + jr[r]), rem[r]);
             }
+            cur = S.prefetch2 ? nxt : fetch_meta(S, base + 32, pe, lane);
         }
 #pragma unroll
         for (int r = 0; r < R; ++r)
@@ -442,10 +443,10 @@ __global__ void __launch_bounds__(256) k_smm_f64_ks(int64_t nlist, const int64_t
         double sq = 0.0, d = 0.0;
 #pragma unroll
         for (int e = 0; e < EF; ++e) {
-            const int idx = lane + 32 * e;
+            const int pos = ii[e] * n + jj[e];
             double v = S.alpha * acc[e];
-            if (cin) v = v + S.beta * cin[idx];
-            out[idx] = v;
+            if (cin) v = v + S.beta * cin[pos];
+            out[pos] = v;
             sq = fma(v, v, sq);
             const double wv = (I == J && ii[e] == jj[e]) ? v - 1.0 : v;
             d = fma(wv, wv, d);
@@ -453,10 +454,10 @@ __global__ void __launch_bounds__(256) k_smm_f64_ks(int64_t nlist, const int64_t
 #pragma unroll
         for (int r = 0; r < R; ++r)
             if (lane == r) {
-                const int idx = 32 * EF + r;
+                const int pos = ir[r] * n + jr[r];
                 double v = S.alpha * rem[r];
-                if (cin) v = v + S.beta * cin[idx];
-                out[idx] = v;
+                if (cin) v = v + S.beta * cin[pos];
+                out[pos] = v;
                 sq = fma(v, v, sq);
                 const double wv = (I == J && ir[r] == jr[r]) ? v - 1.0 : v;
                 d = fma(wv, wv, d);
@@ -473,14 +474,11 @@ __global__ void __launch_bounds__(256) k_smm_f64_ks(int64_t nlist, const int64_t
     }
 }
 
-// Stable partition of the formed blocks by shape class: flag[k] = (class(k) == c).
-__global__ void k_class_flags(int64_t nform, const int32_t* __restrict__ f_row, const int32_t* __restrict__ f_col,
-                              const int32_t* __restrict__ bs, int c, int bf16, int32_t* __restrict__ flag) {
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nform; k += (int64_t)gridDim.x * blockDim.x) {
-        const int m = bs[f_row[k]], n = bs[f_col[k]];
-        // FP64 class: E = ceil(m n / 32) accumulators per lane; BF16 class: (m, n) tile counts (MT, NT)
-        flag[k] = ((bf16 ? ((m + 15) / 16 - 1) * 4 + (n + 7) / 8 : f64_class(m, n)) == c) ? 1 : 0;
-    }
+// Stable partition of the formed blocks by shape: flag[k] = (block k is m x n).
+__global__ void k_shape_flags(int64_t nform, const int32_t* __restrict__ f_row, const int32_t* __restrict__ f_col,
+                              const int32_t* __restrict__ bs, int m, int n, int32_t* __restrict__ flag) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nform; k += (int64_t)gridDim.x * blockDim.x)
+        flag[k] = (bs[f_row[k]] == m && bs[f_col[k]] == n) ? 1 : 0;
 }
 
 __global__ void k_class_scatter(int64_t nform, const int32_t* __restrict__ flag, const int64_t* __restrict__ pos,
@@ -525,7 +523,6 @@ SmmKernel f64_kernel(int cls) {
 // kPanelK columns (ascending K; a panel is padded with zeros to a multiple of 16).
 constexpr int kPanelK = 128;
 constexpr int kPanelLd = kPanelK + 8;      // row stride (bf16): 68 words, conflict-free fragment loads
-constexpr int kBf16Warps = 4;
 
 __device__ __forceinline__ void mma_bf16(float* c, uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t b0,
                                          uint32_t b1) {
@@ -567,7 +564,7 @@ __device__ __forceinline__ void bf16_panel_mma(const __nv_bfloat16* sA, const __
 }
 
 template <int MT, int NT>
-__global__ void __launch_bounds__(32 * kBf16Warps) k_smm_bf16(int64_t nlist, const int64_t* __restrict__ list,
+__global__ void __launch_bounds__(256) k_smm_bf16(int64_t nlist, const int64_t* __restrict__ list,
                                                              SmmBf16Args G) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const SmmArgs& S = G.base;
@@ -576,14 +573,15 @@ __global__ void __launch_bounds__(32 * kBf16Warps) k_smm_bf16(int64_t nlist, con
     __nv_bfloat16* sA = reinterpret_cast<__nv_bfloat16*>(smem_raw) + (size_t)wib * (kRowsA + kRowsB) * kPanelLd;
     __nv_bfloat16* sB = sA + kRowsA * kPanelLd;
     const __nv_bfloat16 zero = __float2bfloat16(0.0f);
-    const int64_t warps = (int64_t)gridDim.x * kBf16Warps;
+    const int wpc = blockDim.x >> 5;    // warps per CTA (each has its own panels)
+    const int64_t warps = (int64_t)gridDim.x * wpc;
     // Rows of A beyond m and columns of B beyond n only feed outputs that are
     // discarded, but they must hold finite values: clear the panels once.  Later
     // blocks leave earlier blocks' (finite) values there; the K padding of every
     // panel is zeroed before its products are issued.
     for (int e = lane; e < (kRowsA + kRowsB) * kPanelLd; e += 32) sA[e] = zero;
     __syncwarp();
-    for (int64_t w = (int64_t)blockIdx.x * kBf16Warps + wib; w < nlist; w += warps) {
+    for (int64_t w = (int64_t)blockIdx.x * wpc + wib; w < nlist; w += warps) {
         const int64_t k = list[w];
         const int I = S.f_row[k], J = S.f_col[k];
         const int m = S.bs[I], n = S.bs[J];
@@ -682,9 +680,10 @@ __global__ void __launch_bounds__(32 * kBf16Warps) k_smm_bf16(int64_t nlist, con
 
 using SmmBf16Kernel = void (*)(int64_t, const int64_t*, SmmBf16Args);
 
-SmmBf16Kernel bf16_kernel(int cls, size_t* smem) {
+// Kernel of a BF16 class and the shared memory one warp needs.
+SmmBf16Kernel bf16_kernel(int cls, size_t* smem_per_warp) {
     const int mt = (cls - 1) / 4 + 1, nt = (cls - 1) % 4 + 1;
-    *smem = (size_t)kBf16Warps * (16 * mt + 8 * nt) * kPanelLd * sizeof(__nv_bfloat16);
+    *smem_per_warp = (size_t)(16 * mt + 8 * nt) * kPanelLd * sizeof(__nv_bfloat16);
     switch (cls) {
         case 1: return &k_smm_bf16<1, 1>;
         case 2: return &k_smm_bf16<1, 2>;
@@ -758,6 +757,44 @@ struct EventSet {
 int sym_grid(int32_t nblk) { return std::min<int32_t>(nblk, 152 * 8); }
 
 }  // namespace
+
+TuneCfg default_cfg(int prec) {
+    TuneCfg c;
+    if (prec == DBCSR_BF16) {
+        c.tpb = 128;
+        c.ctas_per_sm = 64;
+    }
+    return c;
+}
+
+void launch_smm_shape(int prec, int m, int n, int64_t cnt, const int64_t* list, const SmmArgs& sa,
+                      const __nv_bfloat16* a16, const __nv_bfloat16* b16, const TuneCfg& cfg, cudaStream_t s) {
+    if (cnt <= 0) return;
+    if (cfg.tpb < 32 || cfg.tpb > 256 || cfg.tpb % 32 || cfg.ctas_per_sm < 1)
+        fail(DBCSR_EINVAL, "launch configuration out of range");
+    const int wpc = cfg.tpb / 32;
+    const int64_t grid = std::min<int64_t>(ceil_div(cnt, wpc), (int64_t)152 * cfg.ctas_per_sm);
+    if (prec == DBCSR_BF16) {
+        size_t per_warp = 0;
+        SmmBf16Kernel kern = bf16_kernel(((m + 15) / 16 - 1) * 4 + (n + 7) / 8, &per_warp);
+        if (!kern) fail(DBCSR_ECAPACITY, "multiply: block shape beyond the BF16 kernel table");
+        const size_t sm = per_warp * wpc;
+        if (sm > 227 * 1024) fail(DBCSR_ECAPACITY, "multiply: BF16 panels exceed shared memory");
+        if (sm > 48 * 1024) DBG_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        SmmBf16Args ga{sa, a16, b16};
+        kern<<<(unsigned)grid, cfg.tpb, sm, s>>>(cnt, list, ga);
+    } else {
+        const int mn = m * n;
+        const int cls = (mn > 32 && (mn & 31) == 1) ? kF64ClassKs1 + (mn >> 5) : (mn + 31) >> 5;
+        SmmKernel kern = f64_kernel(cls);
+        if (!kern) fail(DBCSR_ECAPACITY, "multiply: block shape beyond the kernel table");
+        SmmArgs a = sa;
+        a.colmajor = cfg.colmajor;
+        a.prefetch2 = cfg.prefetch2;
+        kern<<<(unsigned)grid, cfg.tpb, 0, s>>>(cnt, list, a);
+    }
+    DBG_LAUNCH_CK();
+}
 
 void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbcsr_matrix_* C, double eps, int prec,
               dbcsr_mult_stats* stats, bool want_dev2) {
@@ -835,7 +872,7 @@ void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbc
     // 3. formed-block metadata
     const int64_t nf1 = std::max<int64_t>(nform, 1);
     DBuf<int32_t> f_row, f_col;
-    DBuf<int64_t> f_area, f_np, f_cin, f_off, f_pbeg, f_rp, flops, class_cnt;
+    DBuf<int64_t> f_area, f_np, f_cin, f_off, f_pbeg, f_rp, flops, shape_cnt;
     f_row.alloc(nf1, s);
     f_col.alloc(nf1, s);
     f_area.alloc(nf1, s);
@@ -846,25 +883,26 @@ void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbc
     f_rp.alloc(nblk + 1, s);
     flops.alloc(1, s);
     flops.zero();
-    constexpr int kClasses = kF64Classes;                           // FP64 launch classes (f64_class)
-    constexpr int kClassesBf16 = 9;                                 // BF16 classes (MT, NT) = 1..8
-    class_cnt.alloc(kClasses + kClassesBf16, s);
-    class_cnt.zero();
+    constexpr int kShapes = (kMaxBlock + 1) * (kMaxBlock + 1);     // histogram of formed blocks by (m, n)
+    shape_cnt.alloc(kShapes, s);
+    shape_cnt.zero();
     if (ncand) {
         k_form_meta<<<grid_for(ncand, 256), 256, 0, s>>>(ncand, keep.p, kidx.p, cand_row.p, cand_col.p, pcnt.p, ksum.p,
                                                          use_c ? cin.p : nullptr, A->bs.p, f_row.p, f_col.p, f_area.p,
                                                          f_np.p, f_cin.p, (unsigned long long*)flops.p,
-                                                         (unsigned long long*)class_cnt.p);
+                                                         (unsigned long long*)shape_cnt.p);
         DBG_LAUNCH_CK();
     }
     k_form_rp<<<grid_for(nblk + 1, 256), 256, 0, s>>>(nblk, coff.p, kidx.p, f_rp.p);
     DBG_LAUNCH_CK();
     scan_exclusive(f_area.p, f_off.p, nform, s);
     scan_exclusive(f_np.p, f_pbeg.p, nform, s);
-    int64_t h3[3 + kClasses + kClassesBf16];
+    int64_t h3[3];
+    std::vector<int64_t> shapes(kShapes);
     {
         const int64_t* src[3] = {f_off.p + nform, f_pbeg.p + nform, flops.p};
-        read_i64s(src, 3, h3, s, class_cnt.p, kClasses + kClassesBf16, h3 + 3);
+        DBG_CK(cudaMemcpyAsync(shapes.data(), shape_cnt.p, sizeof(int64_t) * kShapes, cudaMemcpyDeviceToHost, s));
+        read_i64s(src, 3, h3, s);
     }
     const int64_t nel = h3[0], nprod = h3[1];
     const double nflop = (double)(unsigned long long)h3[2];
@@ -896,29 +934,28 @@ void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbc
         SmmArgs sa{f_row.p, f_col.p, f_off.p, f_pbeg.p, f_cin.p, prod_a.p, prod_b.p, A->col.p, A->off.p, A->data.p,
                    B->off.p, B->data.p, use_c ? C->off.p : nullptr, use_c ? C->data.p : nullptr, A->bs.p,
                    alpha, beta, c_data.p, c_norm.p, c_dev2.p};
-        // one launch per shape class over that class's blocks (kept in CSR order)
+        // one launch per (m, n) block shape over that shape's blocks (kept in CSR order)
         const bool bf16 = (prec == DBCSR_BF16);
-        const int ncls = bf16 ? kClassesBf16 : kClasses;
-        const int64_t* cnts = h3 + 3 + (bf16 ? kClasses : 0);
         DBuf<int32_t> flag;
         DBuf<int64_t> pos, list;
         flag.alloc(nform, s);
         pos.alloc(nform + 1, s);
         list.alloc(nform, s);
         int64_t at = 0;
-        std::vector<std::pair<int, int64_t>> launches;
-        for (int c = 1; c < ncls; ++c) {
-            const int64_t cnt = cnts[c];
-            if (!cnt) continue;
-            k_class_flags<<<grid_for(nform, 256), 256, 0, s>>>(nform, f_row.p, f_col.p, A->bs.p, c, bf16 ? 1 : 0,
-                                                               flag.p);
-            DBG_LAUNCH_CK();
-            scan_exclusive(flag.p, pos.p, nform, s);
-            k_class_scatter<<<grid_for(nform, 256), 256, 0, s>>>(nform, flag.p, pos.p, list.p + at);
-            DBG_LAUNCH_CK();
-            launches.emplace_back(c, cnt);
-            at += cnt;
-        }
+        struct ShapeLaunch { int m, n; int64_t cnt; };
+        std::vector<ShapeLaunch> launches;
+        for (int m = 1; m <= kMaxBlock; ++m)
+            for (int n = 1; n <= kMaxBlock; ++n) {
+                const int64_t cnt = shapes[m * (kMaxBlock + 1) + n];
+                if (!cnt) continue;
+                k_shape_flags<<<grid_for(nform, 256), 256, 0, s>>>(nform, f_row.p, f_col.p, A->bs.p, m, n, flag.p);
+                DBG_LAUNCH_CK();
+                scan_exclusive(flag.p, pos.p, nform, s);
+                k_class_scatter<<<grid_for(nform, 256), 256, 0, s>>>(nform, flag.p, pos.p, list.p + at);
+                DBG_LAUNCH_CK();
+                launches.push_back({m, n, cnt});
+                at += cnt;
+            }
         DBuf<__nv_bfloat16> a16, b16;
         if (bf16) {
             // operands rounded to BF16 (nearest even) once per product
@@ -931,23 +968,14 @@ void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbc
                 DBG_LAUNCH_CK();
             }
         }
+        // the inner size the tuned configurations are looked up with: the largest block edge
+        const int kmax = *std::max_element(A->h_bs.begin(), A->h_bs.end());
         DBG_CK(cudaEventRecord(ev.e[1], s));
         at = 0;
-        for (auto& [c, cnt] : launches) {
-            if (bf16) {
-                size_t sm = 0;
-                SmmBf16Kernel kern = bf16_kernel(c, &sm);
-                if (!kern) fail(DBCSR_ECAPACITY, "multiply: block shape beyond the BF16 kernel table");
-                if (sm > 48 * 1024) DBG_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-                SmmBf16Args ga{sa, a16.p, B != A ? b16.p : a16.p};
-                kern<<<grid_for(cnt, kBf16Warps, 152 * 64), 32 * kBf16Warps, sm, s>>>(cnt, list.p + at, ga);
-            } else {
-                SmmKernel kern = f64_kernel(c);
-                if (!kern) fail(DBCSR_ECAPACITY, "multiply: block shape beyond the kernel table");
-                kern<<<grid_for(cnt, 8, 152 * 32), 256, 0, s>>>(cnt, list.p + at, sa);
-            }
-            DBG_LAUNCH_CK();
-            at += cnt;
+        for (const ShapeLaunch& L : launches) {
+            launch_smm_shape(prec, L.m, L.n, L.cnt, list.p + at, sa, a16.p, B != A ? b16.p : a16.p,
+                             tune_lookup(prec, L.m, L.n, kmax), s);
+            at += L.cnt;
         }
     }
     DBG_CK(cudaEventRecord(ev.e[2], s));

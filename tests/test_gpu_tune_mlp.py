@@ -1,0 +1,139 @@
+"""Autotuner and performance-prediction MLP on the GPU: tuning records, launch
+configurations leave results bit-identical, MLP forward/gradient/Adam against the
+FP64 oracle, and what the trained model gains over the default configuration."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import mlp as omlp
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gb():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2003_03868_gb300 as m
+    m.lib()
+    m.tune_clear()
+    yield m
+    m.tune_clear()
+
+
+def test_autotune_records_and_table(gb):
+    gb.tune_clear()
+    triples = [(13, 13, 13), (13, 5, 13)]
+    recs = gb.autotune(triples, gb.DBCSR_FP64, stack_len=20000, reps=3)
+    nsp = len(gb.tune_space(gb.DBCSR_FP64))
+    assert len(recs) == len(triples) * nsp
+    assert all(r.ms > 0 and r.gflops > 0 for r in recs)
+    default = gb.tune_get(gb.DBCSR_FP64, 4, 4, 4)[0]
+    for (m, n, k) in triples:
+        cfg, found = gb.tune_get(gb.DBCSR_FP64, m, n, k)
+        assert found
+        rs = [r for r in recs if (r.m, r.n, r.k) == (m, n, k)]
+        best = min(r.ms for r in rs)
+        dflt = [r.ms for r in rs if (r.cfg.tpb, r.cfg.ctas_per_sm, r.cfg.colmajor, r.cfg.prefetch2) ==
+                (default.tpb, default.ctas_per_sm, default.colmajor, default.prefetch2)][0]
+        assert best <= dflt
+    brec = gb.autotune([(13, 5, 13)], gb.DBCSR_BF16, stack_len=20000, reps=3)
+    assert len(brec) == len(gb.tune_space(gb.DBCSR_BF16))
+    gb.tune_clear()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16"])
+def test_configurations_leave_results_bit_identical(gb, prec):
+    p = gb.DBCSR_FP64 if prec == "fp64" else gb.DBCSR_BF16
+    a = synth.build_decay(synth.DECAY_32)
+    gb.tune_clear()
+    A = gb.Matrix.of(a)
+    C = gb.Matrix(A.blk_size, A.stream)
+    gb.multiply(1.0, A, A, 0.0, C, 1e-6, prec=p)
+    ref = C.export()[2].tobytes()
+    space = gb.tune_space(p)
+    for cfg in space[:: max(1, len(space) // 12)]:
+        for (m, n) in [(13, 13), (13, 5), (5, 13), (5, 5)]:
+            gb.tune_set(p, m, n, 13, cfg)
+        C2 = gb.Matrix(A.blk_size, A.stream)
+        gb.multiply(1.0, A, A, 0.0, C2, 1e-6, prec=p)
+        assert C2.export()[2].tobytes() == ref, (cfg.tpb, cfg.ctas_per_sm, cfg.colmajor, cfg.prefetch2)
+    gb.tune_clear()
+
+
+def _mlp_problem(B=300, seed=3):
+    rng = np.random.default_rng(seed)
+    nf = gb_nf = 10
+    p = (rng.standard_normal(omlp.n_params(nf)) * 0.2).astype(np.float32)
+    X = rng.standard_normal((B, nf)).astype(np.float32)
+    T = rng.standard_normal(B).astype(np.float32)
+    return p, X, T
+
+
+def test_mlp_forward_and_gradient_match_oracle(gb):
+    p, X, T = _mlp_problem()
+    y = gb.mlp_forward(p, X)
+    yo, _ = omlp.forward(p.astype(np.float64), X.astype(np.float64))
+    np.testing.assert_allclose(y, yo, rtol=1e-4, atol=1e-4)
+    loss, g = gb.mlp_loss_grad(p, X, T)
+    lo, go = omlp.loss_grad(p.astype(np.float64), X.astype(np.float64), T.astype(np.float64))
+    assert loss == pytest.approx(lo, rel=1e-4)
+    assert np.linalg.norm(g - go) <= 1e-4 * np.linalg.norm(go)
+    np.testing.assert_allclose(g, go, rtol=1e-3, atol=1e-4 * np.abs(go).max())
+
+
+def test_mlp_adam_steps_match_oracle(gb):
+    p, X, T = _mlp_problem(B=128, seed=4)
+    p3, rep = gb.mlp_train(p, X, T, epochs=3, lr=1e-2)
+    q, m, v = p.astype(np.float64), 0.0, 0.0
+    for t in range(1, 4):
+        _, g = omlp.loss_grad(q, X.astype(np.float64), T.astype(np.float64))
+        q, m, v = omlp.adam_step(q, g, m, v, t, lr=1e-2)
+    np.testing.assert_allclose(p3, q, rtol=0, atol=2e-4)
+    assert rep.loss_first == pytest.approx(omlp.loss(p.astype(np.float64), X, T), rel=1e-4)
+
+
+def test_mlp_training_reduces_loss(gb):
+    rng = np.random.default_rng(5)
+    X = rng.uniform(-1, 1, (2000, 10)).astype(np.float32)
+    T = (np.sin(3 * X[:, 0]) + X[:, 1] * X[:, 2]).astype(np.float32)
+    p0 = gb.mlp_init(10, seed=7)
+    p, rep = gb.mlp_train(p0, X, T, epochs=1500, lr=3e-3)
+    assert rep.loss_last < 0.05 * rep.loss_first
+
+
+@pytest.mark.slow
+def test_mlp_predicted_configs_gain_over_default(gb):
+    """Tune a training set of (m, n, k) triples exhaustively, train the MLP on the
+    standardised log times, predict configurations for held-out triples, and time
+    them against the default configuration and the exhaustive best."""
+    rng = np.random.default_rng(11)
+    allt = [(int(m), int(n), int(k)) for m, n, k in rng.integers(4, 33, (40, 3))]
+    train, held = allt[:30], allt[30:]
+    gb.tune_clear()
+    recs = gb.autotune(train, gb.DBCSR_FP64, stack_len=30000, reps=3)
+    cfgs = [r.cfg for r in recs]
+    X = gb.mlp_features([(r.m, r.n, r.k) for r in recs], cfgs)
+    y = np.log(np.array([r.ms for r in recs]))
+    # per-triple centring: the model learns how the configuration changes the time
+    tri = [(r.m, r.n, r.k) for r in recs]
+    mean = {t: np.mean([yy for tt, yy in zip(tri, y) if tt == t]) for t in set(tri)}
+    T = np.array([yy - mean[t] for t, yy in zip(tri, y)])
+    T = (T / T.std()).astype(np.float32)
+    p, rep = gb.mlp_train(gb.mlp_init(10, seed=3), X, T, epochs=3000, lr=2e-3)
+    assert rep.loss_last < rep.loss_first
+    pred = gb.mlp_predict_best(p, held)
+    space = gb.tune_space(gb.DBCSR_FP64)
+    default = gb.tune_get(gb.DBCSR_FP64, 4, 4, 4)[0]
+    r_pred, r_def = [], []
+    for t, c in zip(held, pred):
+        ts = gb.time_configs(*t, space, stack_len=30000, reps=3)
+        tp = gb.time_configs(*t, [c, default], stack_len=30000, reps=3)
+        r_pred.append(tp[0] / ts.min())
+        r_def.append(tp[1] / ts.min())
+    gm_pred = float(np.exp(np.mean(np.log(r_pred))))
+    gm_def = float(np.exp(np.mean(np.log(r_def))))
+    print(f"held-out: predicted/best {gm_pred:.3f} (median {np.median(r_pred):.3f}), default/best {gm_def:.3f}")
+    assert gm_pred <= gm_def * 1.02
+    gb.tune_clear()
