@@ -334,7 +334,7 @@ def main():
            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_all / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic",
-           "config": {"workload": w.name, "n_mol": w.n_mol, "N": w.n, "blocks": {"O": 13, "H": 5},
+           "config": {"workload": w.name, "n_mol": w.n_mol, "N": w.n, "blocks": {"O": w.basis[0], "H": w.basis[1]},
                       "eps_filter": w.eps_filter, "tol": w.tol, "mu": h.mu,
                       "l2": "inputs larger than L2 (H alone is %.0f MB; 129 MB L2)" % (h.H.data.nbytes / 1e6),
                       "parallelism": f"replicas x{world}"},

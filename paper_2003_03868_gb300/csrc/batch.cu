@@ -248,7 +248,7 @@ dbcsr_status sign_iterate_batched(int32_t nsys, dbcsr_matrix_* const* H, const d
     int it = 0;
     while (it < o.max_iter) {
         dbcsr_mult_stats ms{};
-        multiply(1.0, X.get(), X.get(), 0.0, X2.get(), o.eps_filter, tier, &ms, false);
+        multiply(1.0, X.get(), X.get(), 0.0, X2.get(), o.eps_filter, tier, &ms, false, true);
         flops += ms.flops;
         nprod += ms.n_products;
         ms_mult += ms.ms_numeric;
@@ -292,7 +292,7 @@ dbcsr_status sign_iterate_batched(int32_t nsys, dbcsr_matrix_* const* H, const d
             tier = DBCSR_FP64;
             first_fp64 = it + 1;
         }
-        multiply(-0.5, X.get(), X2.get(), 1.5, X.get(), o.eps_filter, tier, &ms, false);
+        multiply(-0.5, X.get(), X2.get(), 1.5, X.get(), o.eps_filter, tier, &ms, false, true);
         flops += ms.flops;
         nprod += ms.n_products;
         ms_mult += ms.ms_numeric;

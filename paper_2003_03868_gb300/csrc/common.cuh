@@ -158,8 +158,11 @@ double gershgorin(dbcsr_matrix_* m, double mu);
 void trace_product_parts_into(dbcsr_matrix_* a, dbcsr_matrix_* b, double* part, cudaStream_t s);
 
 // ---- multiply.cu
+// sym_result: the caller knows alpha*A*B + beta*C is symmetric (as every product of
+// the sign iteration is); blocks (I, J) with I > J whose mirror is formed are then
+// copied as C_JI^T instead of computed.
 void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbcsr_matrix_* C, double eps,
-              int prec, dbcsr_mult_stats* stats, bool want_dev2);
+              int prec, dbcsr_mult_stats* stats, bool want_dev2, bool sym_result = false);
 
 // ---- sign.cu
 dbcsr_status sign_iterate(dbcsr_matrix_* H, double mu, const dbcsr_sign_opts* opts, dbcsr_matrix_* P,

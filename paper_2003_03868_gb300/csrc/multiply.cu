@@ -211,9 +211,7 @@ __global__ void k_form_meta(int64_t ncand, const int32_t* __restrict__ keep, con
                             const int32_t* __restrict__ pcnt, const int32_t* __restrict__ ksum,
                             const int64_t* __restrict__ cin, const int32_t* __restrict__ bs,
                             int32_t* __restrict__ f_row, int32_t* __restrict__ f_col, int64_t* __restrict__ f_area,
-                            int64_t* __restrict__ f_np, int64_t* __restrict__ f_cin,
-                            unsigned long long* __restrict__ flops, unsigned long long* __restrict__ shape_cnt) {
-    unsigned long long local = 0;
+                            int64_t* __restrict__ f_np, int64_t* __restrict__ f_cin, int32_t* __restrict__ f_ksum) {
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncand; c += (int64_t)gridDim.x * blockDim.x) {
         if (!keep[c]) continue;
         const int64_t k = kidx[c];
@@ -223,11 +221,82 @@ __global__ void k_form_meta(int64_t ncand, const int32_t* __restrict__ keep, con
         f_area[k] = (int64_t)bs[I] * bs[J];
         f_np[k] = pcnt[c];
         f_cin[k] = cin ? cin[c] : -1;
-        local += 2ull * (unsigned long long)bs[I] * (unsigned long long)bs[J] * (unsigned long long)ksum[c];
-        atomicAdd(shape_cnt + bs[I] * (kMaxBlock + 1) + bs[J], 1ull);
+        f_ksum[k] = ksum[c];
     }
-    for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
-    if ((threadIdx.x & 31) == 0 && local) atomicAdd(flops, local);
+}
+
+// With a symmetric result, a formed block (I, J) with I > J whose mirror (J, I)
+// is formed too is not computed: mirror[k] = index of (J, I), else -1.
+__global__ void k_find_mirror(int64_t nform, const int32_t* __restrict__ f_row, const int32_t* __restrict__ f_col,
+                              const int64_t* __restrict__ f_rp, int64_t* __restrict__ mirror) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nform; k += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t I = f_row[k], J = f_col[k];
+        int64_t src = -1;
+        if (I > J) {
+            int64_t lo = f_rp[J], hi = f_rp[J + 1];
+            while (lo < hi) {
+                const int64_t mid = (lo + hi) >> 1;
+                if (f_col[mid] < I) lo = mid + 1; else hi = mid;
+            }
+            if (lo < f_rp[J + 1] && f_col[lo] == I) src = lo;
+        }
+        mirror[k] = src;
+    }
+}
+
+// Work of the blocks that are computed (not mirrored): flops, products, and a
+// histogram by block shape (m, n).
+__global__ void k_form_stats(int64_t nform, const int32_t* __restrict__ f_row, const int32_t* __restrict__ f_col,
+                             const int64_t* __restrict__ f_np, const int32_t* __restrict__ f_ksum,
+                             const int64_t* __restrict__ mirror, const int32_t* __restrict__ bs,
+                             unsigned long long* __restrict__ flops, unsigned long long* __restrict__ nprod,
+                             unsigned long long* __restrict__ shape_cnt) {
+    unsigned long long lf = 0, lp = 0;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nform; k += (int64_t)gridDim.x * blockDim.x) {
+        if (mirror[k] >= 0) continue;
+        const int m = bs[f_row[k]], n = bs[f_col[k]];
+        lf += 2ull * (unsigned long long)m * (unsigned long long)n * (unsigned long long)f_ksum[k];
+        lp += (unsigned long long)f_np[k];
+        atomicAdd(shape_cnt + m * (kMaxBlock + 1) + n, 1ull);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        lf += __shfl_xor_sync(0xffffffffu, lf, o);
+        lp += __shfl_xor_sync(0xffffffffu, lp, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (lf) atomicAdd(flops, lf);
+        if (lp) atomicAdd(nprod, lp);
+    }
+}
+
+// Mirrored blocks: C_IJ = C_JI^T (copied after every computed block is written),
+// with their norm and distance to 1 (never diagonal).
+__global__ void k_mirror_copy(int64_t nform, const int64_t* __restrict__ mirror, const int32_t* __restrict__ f_row,
+                              const int32_t* __restrict__ f_col, const int64_t* __restrict__ f_off,
+                              const int32_t* __restrict__ bs, double* __restrict__ c_data, double* __restrict__ c_norm,
+                              double* __restrict__ c_dev2) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t k = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); k < nform; k += warps) {
+        const int64_t src = mirror[k];
+        if (src < 0) continue;
+        const int m = bs[f_row[k]], n = bs[f_col[k]];
+        const double* S = c_data + f_off[src];
+        double* D = c_data + f_off[k];
+        double sq = 0.0;
+        for (int e = lane; e < m * n; e += 32) {
+            const int i = e / n, j = e - i * n;
+            const double v = S[j * m + i];
+            D[e] = v;
+            sq = fma(v, v, sq);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+        if (lane == 0) {
+            c_norm[k] = sqrt(sq);
+            c_dev2[k] = sq;
+        }
+    }
 }
 
 __global__ void k_form_rp(int32_t nblk, const int64_t* __restrict__ coff, const int64_t* __restrict__ kidx,
@@ -476,9 +545,10 @@ __global__ void __launch_bounds__(256) k_smm_f64_ks(int64_t nlist, const int64_t
 
 // Stable partition of the formed blocks by shape: flag[k] = (block k is m x n).
 __global__ void k_shape_flags(int64_t nform, const int32_t* __restrict__ f_row, const int32_t* __restrict__ f_col,
-                              const int32_t* __restrict__ bs, int m, int n, int32_t* __restrict__ flag) {
+                              const int32_t* __restrict__ bs, const int64_t* __restrict__ mirror, int m, int n,
+                              int32_t* __restrict__ flag) {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nform; k += (int64_t)gridDim.x * blockDim.x)
-        flag[k] = (bs[f_row[k]] == m && bs[f_col[k]] == n) ? 1 : 0;
+        flag[k] = (bs[f_row[k]] == m && bs[f_col[k]] == n && mirror[k] < 0) ? 1 : 0;
 }
 
 __global__ void k_class_scatter(int64_t nform, const int32_t* __restrict__ flag, const int64_t* __restrict__ pos,
@@ -797,7 +867,7 @@ void launch_smm_shape(int prec, int m, int n, int64_t cnt, const int64_t* list, 
 }
 
 void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbcsr_matrix_* C, double eps, int prec,
-              dbcsr_mult_stats* stats, bool want_dev2) {
+              dbcsr_mult_stats* stats, bool want_dev2, bool sym_result) {
     check_finalized(A);
     check_finalized(B);
     if (!C) fail(DBCSR_EINVAL, "multiply: null C");
@@ -871,8 +941,12 @@ void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbc
 
     // 3. formed-block metadata
     const int64_t nf1 = std::max<int64_t>(nform, 1);
-    DBuf<int32_t> f_row, f_col;
-    DBuf<int64_t> f_area, f_np, f_cin, f_off, f_pbeg, f_rp, flops, shape_cnt;
+    DBuf<int32_t> f_row, f_col, f_ksum;
+    DBuf<int64_t> f_area, f_np, f_cin, f_off, f_pbeg, f_rp, flops, nprod_exec, shape_cnt, mirror;
+    f_ksum.alloc(nf1, s);
+    mirror.alloc(nf1, s);
+    nprod_exec.alloc(1, s);
+    nprod_exec.zero();
     f_row.alloc(nf1, s);
     f_col.alloc(nf1, s);
     f_area.alloc(nf1, s);
@@ -889,23 +963,36 @@ void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbc
     if (ncand) {
         k_form_meta<<<grid_for(ncand, 256), 256, 0, s>>>(ncand, keep.p, kidx.p, cand_row.p, cand_col.p, pcnt.p, ksum.p,
                                                          use_c ? cin.p : nullptr, A->bs.p, f_row.p, f_col.p, f_area.p,
-                                                         f_np.p, f_cin.p, (unsigned long long*)flops.p,
-                                                         (unsigned long long*)shape_cnt.p);
+                                                         f_np.p, f_cin.p, f_ksum.p);
         DBG_LAUNCH_CK();
     }
     k_form_rp<<<grid_for(nblk + 1, 256), 256, 0, s>>>(nblk, coff.p, kidx.p, f_rp.p);
     DBG_LAUNCH_CK();
+    if (nform) {
+        if (sym_result) {
+            k_find_mirror<<<grid_for(nform, 256), 256, 0, s>>>(nform, f_row.p, f_col.p, f_rp.p, mirror.p);
+            DBG_LAUNCH_CK();
+        } else {
+            DBG_CK(cudaMemsetAsync(mirror.p, 0xff, sizeof(int64_t) * nform, s));   // -1: no block is mirrored
+        }
+        k_form_stats<<<grid_for(nform, 256), 256, 0, s>>>(nform, f_row.p, f_col.p, f_np.p, f_ksum.p, mirror.p, A->bs.p,
+                                                          (unsigned long long*)flops.p,
+                                                          (unsigned long long*)nprod_exec.p,
+                                                          (unsigned long long*)shape_cnt.p);
+        DBG_LAUNCH_CK();
+    }
     scan_exclusive(f_area.p, f_off.p, nform, s);
     scan_exclusive(f_np.p, f_pbeg.p, nform, s);
-    int64_t h3[3];
+    int64_t h3[4];
     std::vector<int64_t> shapes(kShapes);
     {
-        const int64_t* src[3] = {f_off.p + nform, f_pbeg.p + nform, flops.p};
+        const int64_t* src[4] = {f_off.p + nform, f_pbeg.p + nform, flops.p, nprod_exec.p};
         DBG_CK(cudaMemcpyAsync(shapes.data(), shape_cnt.p, sizeof(int64_t) * kShapes, cudaMemcpyDeviceToHost, s));
-        read_i64s(src, 3, h3, s);
+        read_i64s(src, 4, h3, s);
     }
     const int64_t nel = h3[0], nprod = h3[1];
     const double nflop = (double)(unsigned long long)h3[2];
+    const int64_t nprod_done = h3[3];
 
     // 4. product stacks
     DBuf<int32_t> prod_a, prod_b, cursor;
@@ -948,7 +1035,8 @@ void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbc
             for (int n = 1; n <= kMaxBlock; ++n) {
                 const int64_t cnt = shapes[m * (kMaxBlock + 1) + n];
                 if (!cnt) continue;
-                k_shape_flags<<<grid_for(nform, 256), 256, 0, s>>>(nform, f_row.p, f_col.p, A->bs.p, m, n, flag.p);
+                k_shape_flags<<<grid_for(nform, 256), 256, 0, s>>>(nform, f_row.p, f_col.p, A->bs.p, mirror.p, m, n,
+                                                                   flag.p);
                 DBG_LAUNCH_CK();
                 scan_exclusive(flag.p, pos.p, nform, s);
                 k_class_scatter<<<grid_for(nform, 256), 256, 0, s>>>(nform, flag.p, pos.p, list.p + at);
@@ -976,6 +1064,11 @@ void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbc
             launch_smm_shape(prec, L.m, L.n, L.cnt, list.p + at, sa, a16.p, B != A ? b16.p : a16.p,
                              tune_lookup(prec, L.m, L.n, kmax), s);
             at += L.cnt;
+        }
+        if (sym_result) {
+            k_mirror_copy<<<grid_for(nform, 8), 256, 0, s>>>(nform, mirror.p, f_row.p, f_col.p, f_off.p, A->bs.p,
+                                                            c_data.p, c_norm.p, c_dev2.p);
+            DBG_LAUNCH_CK();
         }
     }
     DBG_CK(cudaEventRecord(ev.e[2], s));
@@ -1013,7 +1106,7 @@ void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbc
         stats->n_candidates = ncand;
         stats->n_formed = nform;
         stats->n_kept = C->nnzb;
-        stats->n_products = nprod;
+        stats->n_products = nprod_done;
         stats->flops = nflop;
         stats->dev2_filtered = want_dev2 ? read_f64(dsum.p, s) : 0.0;
         stats->ms_symbolic = ev.ms(0, 1);

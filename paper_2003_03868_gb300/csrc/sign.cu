@@ -69,7 +69,7 @@ dbcsr_status sign_iterate(dbcsr_matrix_* H, double mu, const dbcsr_sign_opts* op
     int first_fp64 = (tier == DBCSR_FP64) ? 1 : 0;
     while (it < o.max_iter) {
         dbcsr_mult_stats st{};
-        multiply(1.0, X.get(), X.get(), 0.0, X2.get(), o.eps_filter, tier, &st, true);
+        multiply(1.0, X.get(), X.get(), 0.0, X2.get(), o.eps_filter, tier, &st, true, true);
         res = std::sqrt(st.dev2_filtered) / N;
         r.flops += st.flops;
         r.n_products += st.n_products;
@@ -105,7 +105,7 @@ dbcsr_status sign_iterate(dbcsr_matrix_* H, double mu, const dbcsr_sign_opts* op
                 break;
             }
         }
-        multiply(-0.5, X.get(), X2.get(), 1.5, X.get(), o.eps_filter, tier, &st, false);
+        multiply(-0.5, X.get(), X2.get(), 1.5, X.get(), o.eps_filter, tier, &st, false, true);
         r.flops += st.flops;
         r.n_products += st.n_products;
         r.ms_multiply += st.ms_numeric;
