@@ -84,8 +84,19 @@ typedef struct {
     double switch_tol;         /* DBCSR_MIXED: residual below which FP64 takes over (e.g. 1e-4) */
     double stall_ratio;        /* stall test: r_k > ratio*r_{k-1} after r_{k-1} < ratio*r_{k-2} (default 0.5 when <= 0) */
     int32_t verbose;           /* 1: print one line per step to stderr */
-    int32_t reserved;
+    int32_t flags;             /* DBCSR_SIGN_* bits, 0 = defaults */
 } dbcsr_sign_opts;
+
+/* dbcsr_sign_opts.flags.  By default a DBCSR_FP64 iteration forms only the blocks
+ * I <= J of its products, whose exact results are symmetric, copies the blocks
+ * I > J as transposes and drops blocks without a formed twin (X stays exactly
+ * symmetric; results agree with full products to the filter's accuracy).  A
+ * DBCSR_MIXED iteration forms both triangles of every product: with mirrored FP64
+ * products after a BF16 tier the residual was measured to stall near 3e-6.
+ * DBCSR_SIGN_FULL_PRODUCTS: form both triangles of every product.
+ * DBCSR_SIGN_SYM_BF16: mirror in the BF16 tier too (experimental). */
+#define DBCSR_SIGN_FULL_PRODUCTS 1
+#define DBCSR_SIGN_SYM_BF16 2
 
 #define DBCSR_MAX_HISTORY 128
 

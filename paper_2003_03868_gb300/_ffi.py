@@ -10,6 +10,7 @@ LIB_PATH = os.path.join(HERE, "libdbcsr_gb.so")
 DBCSR_OK, DBCSR_EINVAL, DBCSR_ENOMEM, DBCSR_ECAPACITY, DBCSR_ECUDA = 0, 1, 2, 3, 4
 DBCSR_ENAN, DBCSR_ENOTCONV, DBCSR_ETIMEOUT, DBCSR_ESTATE = 5, 6, 7, 8
 DBCSR_FP64, DBCSR_BF16, DBCSR_MIXED = 0, 2, 3
+DBCSR_SIGN_FULL_PRODUCTS, DBCSR_SIGN_SYM_BF16 = 1, 2
 MAX_HISTORY = 128
 
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECAPACITY", 4: "ECUDA", 5: "ENAN", 6: "ENOTCONV",
@@ -25,7 +26,7 @@ class MultStats(C.Structure):
 class SignOpts(C.Structure):
     _fields_ = [("eps_filter", C.c_double), ("tol", C.c_double), ("max_iter", C.c_int32), ("prec", C.c_int32),
                 ("switch_tol", C.c_double), ("stall_ratio", C.c_double), ("verbose", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("flags", C.c_int32)]
 
 
 class SignReport(C.Structure):

@@ -158,9 +158,10 @@ double gershgorin(dbcsr_matrix_* m, double mu);
 void trace_product_parts_into(dbcsr_matrix_* a, dbcsr_matrix_* b, double* part, cudaStream_t s);
 
 // ---- multiply.cu
-// sym_result: the caller knows alpha*A*B + beta*C is symmetric (as every product of
-// the sign iteration is); blocks (I, J) with I > J whose mirror is formed are then
-// copied as C_JI^T instead of computed.
+// sym_result: the caller knows alpha*A*B + beta*C is symmetric in exact arithmetic
+// (as every product of the sign iteration is).  Only blocks I <= J whose twin (J, I)
+// is formed are computed, their twins are copied as transposes, and blocks without
+// a formed twin are dropped: the result is exactly symmetric.
 void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbcsr_matrix_* C, double eps,
               int prec, dbcsr_mult_stats* stats, bool want_dev2, bool sym_result = false);
 

@@ -225,35 +225,49 @@ __global__ void k_form_meta(int64_t ncand, const int32_t* __restrict__ keep, con
     }
 }
 
-// With a symmetric result, a formed block (I, J) with I > J whose mirror (J, I)
-// is formed too is not computed: mirror[k] = index of (J, I), else -1.
+// With a symmetric result (sym != 0), each formed block's twin (J, I) is looked up:
+// mirror[k] = its index, or -1 if the twin was not formed.  Blocks then take one of
+// three roles: computed (diagonal, or I < J with a formed twin), copied as the
+// twin's transpose (I > J with a formed twin), or dropped (no formed twin: the
+// exact product is symmetric, so the twin's bound below eps -- or its absence from
+// the pattern -- bounds this block too; what is left is asymmetric rounding noise).
+// Without sym every block is computed.
 __global__ void k_find_mirror(int64_t nform, const int32_t* __restrict__ f_row, const int32_t* __restrict__ f_col,
                               const int64_t* __restrict__ f_rp, int64_t* __restrict__ mirror) {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nform; k += (int64_t)gridDim.x * blockDim.x) {
         const int32_t I = f_row[k], J = f_col[k];
         int64_t src = -1;
-        if (I > J) {
+        if (I != J) {
             int64_t lo = f_rp[J], hi = f_rp[J + 1];
             while (lo < hi) {
                 const int64_t mid = (lo + hi) >> 1;
                 if (f_col[mid] < I) lo = mid + 1; else hi = mid;
             }
             if (lo < f_rp[J + 1] && f_col[lo] == I) src = lo;
+        } else {
+            src = k;
         }
         mirror[k] = src;
     }
+}
+
+// role of formed block k: 0 computed, 1 copied from its twin, 2 dropped
+__device__ __forceinline__ int block_role(int sym, int32_t I, int32_t J, int64_t mirror) {
+    if (!sym || I == J) return 0;
+    if (mirror < 0) return 2;
+    return I < J ? 0 : 1;
 }
 
 // Work of the blocks that are computed (not mirrored): flops, products, and a
 // histogram by block shape (m, n).
 __global__ void k_form_stats(int64_t nform, const int32_t* __restrict__ f_row, const int32_t* __restrict__ f_col,
                              const int64_t* __restrict__ f_np, const int32_t* __restrict__ f_ksum,
-                             const int64_t* __restrict__ mirror, const int32_t* __restrict__ bs,
+                             const int64_t* __restrict__ mirror, int sym, const int32_t* __restrict__ bs,
                              unsigned long long* __restrict__ flops, unsigned long long* __restrict__ nprod,
                              unsigned long long* __restrict__ shape_cnt) {
     unsigned long long lf = 0, lp = 0;
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nform; k += (int64_t)gridDim.x * blockDim.x) {
-        if (mirror[k] >= 0) continue;
+        if (block_role(sym, f_row[k], f_col[k], mirror[k]) != 0) continue;
         const int m = bs[f_row[k]], n = bs[f_col[k]];
         lf += 2ull * (unsigned long long)m * (unsigned long long)n * (unsigned long long)f_ksum[k];
         lp += (unsigned long long)f_np[k];
@@ -269,8 +283,9 @@ __global__ void k_form_stats(int64_t nform, const int32_t* __restrict__ f_row, c
     }
 }
 
-// Mirrored blocks: C_IJ = C_JI^T (copied after every computed block is written),
-// with their norm and distance to 1 (never diagonal).
+// Copied blocks: C_IJ = C_JI^T (after every computed block is written), with their
+// norm and distance to 1 (never diagonal); dropped blocks get norm -1 so that the
+// filter removes them.
 __global__ void k_mirror_copy(int64_t nform, const int64_t* __restrict__ mirror, const int32_t* __restrict__ f_row,
                               const int32_t* __restrict__ f_col, const int64_t* __restrict__ f_off,
                               const int32_t* __restrict__ bs, double* __restrict__ c_data, double* __restrict__ c_norm,
@@ -278,8 +293,16 @@ __global__ void k_mirror_copy(int64_t nform, const int64_t* __restrict__ mirror,
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t k = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); k < nform; k += warps) {
+        const int role = block_role(1, f_row[k], f_col[k], mirror[k]);
+        if (role == 0) continue;
+        if (role == 2) {
+            if (lane == 0) {
+                c_norm[k] = -1.0;
+                c_dev2[k] = 0.0;
+            }
+            continue;
+        }
         const int64_t src = mirror[k];
-        if (src < 0) continue;
         const int m = bs[f_row[k]], n = bs[f_col[k]];
         const double* S = c_data + f_off[src];
         double* D = c_data + f_off[k];
@@ -545,10 +568,12 @@ __global__ void __launch_bounds__(256) k_smm_f64_ks(int64_t nlist, const int64_t
 
 // Stable partition of the formed blocks by shape: flag[k] = (block k is m x n).
 __global__ void k_shape_flags(int64_t nform, const int32_t* __restrict__ f_row, const int32_t* __restrict__ f_col,
-                              const int32_t* __restrict__ bs, const int64_t* __restrict__ mirror, int m, int n,
+                              const int32_t* __restrict__ bs, const int64_t* __restrict__ mirror, int sym, int m, int n,
                               int32_t* __restrict__ flag) {
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nform; k += (int64_t)gridDim.x * blockDim.x)
-        flag[k] = (bs[f_row[k]] == m && bs[f_col[k]] == n && mirror[k] < 0) ? 1 : 0;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nform; k += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t I = f_row[k], J = f_col[k];
+        flag[k] = (bs[I] == m && bs[J] == n && block_role(sym, I, J, mirror[k]) == 0) ? 1 : 0;
+    }
 }
 
 __global__ void k_class_scatter(int64_t nform, const int32_t* __restrict__ flag, const int64_t* __restrict__ pos,
@@ -587,13 +612,15 @@ SmmKernel f64_kernel(int cls) {
 
 // ------------------------------------------------------------ BF16 tensor-core SMM
 // BF16 operands (rounded to nearest even from FP64), FP32 accumulation on the
-// tensor cores (mma.sync m16n8k16), FP64 epilogue.  One warp owns one C block
-// (m <= 16*MT, n <= 8*NT).  Its products are concatenated along K,
-// C_IJ = [A_IK1 A_IK2 ...] [B_K1J; B_K2J; ...], in shared-memory panels of up to
-// kPanelK columns (ascending K; a panel is padded with zeros to a multiple of 16).
-constexpr int kPanelK = 128;
-constexpr int kPanelLd = kPanelK + 8;      // row stride (bf16): 68 words, conflict-free fragment loads
-
+// tensor cores (mma.sync m16n8k16), FP64 epilogue.  Before the products, every
+// block is packed once into a fragment-ready copy: an A-role copy of block
+// (I, K) holds its m x k values in a zero-padded (16 MT) x (16 KT) row-major tile
+// and a B-role copy of block (K, J) holds its transpose, n x k, in a zero-padded
+// (8 NT) x (16 KT) tile.  Each block sits at a fixed stride, so a product's
+// operands are found from its block index alone.  One warp owns one C block
+// (m <= 16 MT, n <= 8 NT) and, per product, loads its A and B fragments with
+// aligned 32-bit loads straight from the packed copies and issues KT x MT x NT
+// MMAs -- no shared-memory staging.  Zero padding adds nothing to the sums.
 __device__ __forceinline__ void mma_bf16(float* c, uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t b0,
                                          uint32_t b1) {
     asm volatile(
@@ -604,54 +631,18 @@ __device__ __forceinline__ void mma_bf16(float* c, uint32_t a0, uint32_t a1, uin
 
 struct SmmBf16Args {
     SmmArgs base;
-    const __nv_bfloat16* a16;
-    const __nv_bfloat16* b16;
+    const __nv_bfloat16* a16;   // A-role packed blocks, block b at a16 + b * a_stride
+    int64_t a_stride;
+    const __nv_bfloat16* b16;   // B-role packed (transposed) blocks, block b at b16 + b * b_stride
+    int64_t b_stride;
 };
 
 template <int MT, int NT>
-__device__ __forceinline__ void bf16_panel_mma(const __nv_bfloat16* sA, const __nv_bfloat16* sB, int kc, int lane,
-                                               float (&acc)[MT][NT][4]) {
-    const int gid = lane >> 2, tig = lane & 3;
-    for (int ks = 0; ks < kc; ks += 16) {
-        uint32_t bf[NT][2];
-#pragma unroll
-        for (int nt = 0; nt < NT; ++nt) {
-            const __nv_bfloat16* b = sB + (nt * 8 + gid) * kPanelLd + ks + tig * 2;
-            bf[nt][0] = *reinterpret_cast<const uint32_t*>(b);
-            bf[nt][1] = *reinterpret_cast<const uint32_t*>(b + 8);
-        }
-#pragma unroll
-        for (int mt = 0; mt < MT; ++mt) {
-            const __nv_bfloat16* a = sA + (mt * 16 + gid) * kPanelLd + ks + tig * 2;
-            const uint32_t a0 = *reinterpret_cast<const uint32_t*>(a);
-            const uint32_t a1 = *reinterpret_cast<const uint32_t*>(a + 8 * kPanelLd);
-            const uint32_t a2 = *reinterpret_cast<const uint32_t*>(a + 8);
-            const uint32_t a3 = *reinterpret_cast<const uint32_t*>(a + 8 * kPanelLd + 8);
-#pragma unroll
-            for (int nt = 0; nt < NT; ++nt) mma_bf16(acc[mt][nt], a0, a1, a2, a3, bf[nt][0], bf[nt][1]);
-        }
-    }
-}
-
-template <int MT, int NT>
-__global__ void __launch_bounds__(256) k_smm_bf16(int64_t nlist, const int64_t* __restrict__ list,
-                                                             SmmBf16Args G) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+__global__ void __launch_bounds__(256) k_smm_bf16(int64_t nlist, const int64_t* __restrict__ list, SmmBf16Args G) {
     const SmmArgs& S = G.base;
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    constexpr int kRowsA = 16 * MT, kRowsB = 8 * NT;
-    __nv_bfloat16* sA = reinterpret_cast<__nv_bfloat16*>(smem_raw) + (size_t)wib * (kRowsA + kRowsB) * kPanelLd;
-    __nv_bfloat16* sB = sA + kRowsA * kPanelLd;
-    const __nv_bfloat16 zero = __float2bfloat16(0.0f);
-    const int wpc = blockDim.x >> 5;    // warps per CTA (each has its own panels)
-    const int64_t warps = (int64_t)gridDim.x * wpc;
-    // Rows of A beyond m and columns of B beyond n only feed outputs that are
-    // discarded, but they must hold finite values: clear the panels once.  Later
-    // blocks leave earlier blocks' (finite) values there; the K padding of every
-    // panel is zeroed before its products are issued.
-    for (int e = lane; e < (kRowsA + kRowsB) * kPanelLd; e += 32) sA[e] = zero;
-    __syncwarp();
-    for (int64_t w = (int64_t)blockIdx.x * wpc + wib; w < nlist; w += warps) {
+    const int lane = threadIdx.x & 31, gid = lane >> 2, tig = lane & 3;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < nlist; w += warps) {
         const int64_t k = list[w];
         const int I = S.f_row[k], J = S.f_col[k];
         const int m = S.bs[I], n = S.bs[J];
@@ -662,7 +653,6 @@ __global__ void __launch_bounds__(256) k_smm_bf16(int64_t nlist, const int64_t* 
             for (int nt = 0; nt < NT; ++nt)
 #pragma unroll
                 for (int i = 0; i < 4; ++i) acc[mt][nt][i] = 0.f;
-        int koff = 0;
         const int64_t pb = S.f_pbeg[k], pe = S.f_pbeg[k + 1];
         for (int64_t base = pb; base < pe; base += 32) {
             const int cnt = (int)min((int64_t)32, pe - base);
@@ -670,52 +660,38 @@ __global__ void __launch_bounds__(256) k_smm_bf16(int64_t nlist, const int64_t* 
             int kq = 0;
             if (lane < cnt) {
                 const int32_t ai = S.prod_a[base + lane], bi = S.prod_b[base + lane];
-                ao = S.a_off[ai];
-                bo = S.b_off[bi];
+                ao = (int64_t)ai * G.a_stride;
+                bo = (int64_t)bi * G.b_stride;
                 kq = S.bs[S.a_col[ai]];
             }
             for (int q = 0; q < cnt; ++q) {
                 const int64_t aoq = __shfl_sync(0xffffffffu, ao, q);
                 const int64_t boq = __shfl_sync(0xffffffffu, bo, q);
                 const int kk = __shfl_sync(0xffffffffu, kq, q);
-                if (koff + kk > kPanelK) {
-                    const int kc = (koff + 15) & ~15;
-                    for (int e = lane; e < kRowsA * (kc - koff); e += 32)
-                        sA[(e / (kc - koff)) * kPanelLd + koff + e % (kc - koff)] = zero;
-                    for (int e = lane; e < kRowsB * (kc - koff); e += 32)
-                        sB[(e / (kc - koff)) * kPanelLd + koff + e % (kc - koff)] = zero;
-                    __syncwarp();
-                    bf16_panel_mma<MT, NT>(sA, sB, kc, lane, acc);
-                    __syncwarp();
-                    koff = 0;
+                const int KT = (kk + 15) >> 4, ld = 16 * KT;     // padded inner size = row length of both tiles
+                const uint32_t* __restrict__ Ap = reinterpret_cast<const uint32_t*>(G.a16 + aoq);
+                const uint32_t* __restrict__ Bp = reinterpret_cast<const uint32_t*>(G.b16 + boq);
+                for (int kt = 0; kt < KT; ++kt) {
+                    const int c0 = (kt * 16 + tig * 2) >> 1;      // 32-bit word of columns (c, c+1)
+                    uint32_t bf[NT][2];
+#pragma unroll
+                    for (int nt = 0; nt < NT; ++nt) {
+                        const int row = (nt * 8 + gid) * (ld >> 1);
+                        bf[nt][0] = __ldg(Bp + row + c0);
+                        bf[nt][1] = __ldg(Bp + row + c0 + 4);
+                    }
+#pragma unroll
+                    for (int mt = 0; mt < MT; ++mt) {
+                        const int r0 = (mt * 16 + gid) * (ld >> 1), r1 = r0 + 8 * (ld >> 1);
+                        const uint32_t a0 = __ldg(Ap + r0 + c0), a1 = __ldg(Ap + r1 + c0);
+                        const uint32_t a2 = __ldg(Ap + r0 + c0 + 4), a3 = __ldg(Ap + r1 + c0 + 4);
+#pragma unroll
+                        for (int nt = 0; nt < NT; ++nt) mma_bf16(acc[mt][nt], a0, a1, a2, a3, bf[nt][0], bf[nt][1]);
+                    }
                 }
-                const __nv_bfloat16* A = G.a16 + aoq;
-                const __nv_bfloat16* B = G.b16 + boq;
-                for (int e = lane; e < m * kk; e += 32) {
-                    const int r = e / kk, t = e - r * kk;
-                    sA[r * kPanelLd + koff + t] = A[e];
-                }
-                for (int e = lane; e < kk * n; e += 32) {
-                    const int t = e / n, c = e - t * n;
-                    sB[c * kPanelLd + koff + t] = B[e];
-                }
-                koff += kk;
             }
         }
-        if (koff > 0) {
-            const int kc = (koff + 15) & ~15;
-            if (kc > koff) {
-                for (int e = lane; e < kRowsA * (kc - koff); e += 32)
-                    sA[(e / (kc - koff)) * kPanelLd + koff + e % (kc - koff)] = zero;
-                for (int e = lane; e < kRowsB * (kc - koff); e += 32)
-                    sB[(e / (kc - koff)) * kPanelLd + koff + e % (kc - koff)] = zero;
-            }
-            __syncwarp();
-            bf16_panel_mma<MT, NT>(sA, sB, kc, lane, acc);
-        }
-        __syncwarp();
         // epilogue in FP64
-        const int gid = lane >> 2, tig = lane & 3;
         const int64_t ci = S.f_cin[k];
         const double* cin = ci >= 0 ? S.ci_data + S.ci_off[ci] : nullptr;
         double* out = S.c_data + S.f_off[k];
@@ -750,10 +726,8 @@ __global__ void __launch_bounds__(256) k_smm_bf16(int64_t nlist, const int64_t* 
 
 using SmmBf16Kernel = void (*)(int64_t, const int64_t*, SmmBf16Args);
 
-// Kernel of a BF16 class and the shared memory one warp needs.
-SmmBf16Kernel bf16_kernel(int cls, size_t* smem_per_warp) {
-    const int mt = (cls - 1) / 4 + 1, nt = (cls - 1) % 4 + 1;
-    *smem_per_warp = (size_t)(16 * mt + 8 * nt) * kPanelLd * sizeof(__nv_bfloat16);
+// Kernel of a BF16 class (MT, NT) = ((cls - 1) / 4 + 1, (cls - 1) % 4 + 1).
+SmmBf16Kernel bf16_kernel(int cls) {
     switch (cls) {
         case 1: return &k_smm_bf16<1, 1>;
         case 2: return &k_smm_bf16<1, 2>;
@@ -794,10 +768,35 @@ __device__ __forceinline__ __nv_bfloat16 f64_to_bf16_rne(double x) {
     return __ushort_as_bfloat16(out);
 }
 
-__global__ void k_to_bf16(int64_t n, const double* __restrict__ in, __nv_bfloat16* __restrict__ out) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        out[i] = f64_to_bf16_rne(in[i]);
+// Fragment-ready BF16 copies of every block of a matrix (one warp per block), at a
+// fixed stride: role 0 (A): block (I, K) as a (16 ceil(m/16)) x (16 ceil(k/16))
+// row-major tile; role 1 (B): block (K, J) transposed, as an (8 ceil(n/8)) x
+// (16 ceil(k/16)) tile.  Padding is zero.
+__global__ void k_pack_bf16(int64_t nb, int role, const int32_t* __restrict__ row, const int32_t* __restrict__ col,
+                            const int32_t* __restrict__ bs, const int64_t* __restrict__ off,
+                            const double* __restrict__ data, int64_t stride, __nv_bfloat16* __restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t b = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); b < nb; b += warps) {
+        const int r_sz = bs[row[b]], c_sz = bs[col[b]];         // the block is r_sz x c_sz, row-major
+        const double* x = data + off[b];
+        __nv_bfloat16* o = out + b * stride;
+        if (role == 0) {                                         // A: m = r_sz rows, k = c_sz columns
+            const int R = 16 * ((r_sz + 15) / 16), L = 16 * ((c_sz + 15) / 16);
+            for (int e = lane; e < R * L; e += 32) {
+                const int i = e / L, t = e - i * L;
+                o[e] = f64_to_bf16_rne((i < r_sz && t < c_sz) ? x[i * c_sz + t] : 0.0);
+            }
+        } else {                                                 // B: k = r_sz rows, n = c_sz columns, stored n x k
+            const int R = 8 * ((c_sz + 7) / 8), L = 16 * ((r_sz + 15) / 16);
+            for (int e = lane; e < R * L; e += 32) {
+                const int j = e / L, t = e - j * L;
+                o[e] = f64_to_bf16_rne((j < c_sz && t < r_sz) ? x[t * c_sz + j] : 0.0);
+            }
+        }
+    }
 }
+
 
 __global__ void k_keep_filter(int64_t nb, const int32_t* __restrict__ row, const int32_t* __restrict__ col,
                               const double* __restrict__ norms, const double* __restrict__ dev2, double eps,
@@ -828,6 +827,12 @@ int sym_grid(int32_t nblk) { return std::min<int32_t>(nblk, 152 * 8); }
 
 }  // namespace
 
+// Largest packed tile of a role for blocks of edge <= maxbs.
+int64_t pack_stride(int role, int maxbs) {
+    const int64_t L = 16 * ((maxbs + 15) / 16);
+    return role == 0 ? 16 * ((maxbs + 15) / 16) * L : 8 * ((maxbs + 7) / 8) * L;
+}
+
 TuneCfg default_cfg(int prec) {
     TuneCfg c;
     if (prec == DBCSR_BF16) {
@@ -838,21 +843,17 @@ TuneCfg default_cfg(int prec) {
 }
 
 void launch_smm_shape(int prec, int m, int n, int64_t cnt, const int64_t* list, const SmmArgs& sa,
-                      const __nv_bfloat16* a16, const __nv_bfloat16* b16, const TuneCfg& cfg, cudaStream_t s) {
+                      const Bf16Packs& pk, const TuneCfg& cfg, cudaStream_t s) {
     if (cnt <= 0) return;
     if (cfg.tpb < 32 || cfg.tpb > 256 || cfg.tpb % 32 || cfg.ctas_per_sm < 1)
         fail(DBCSR_EINVAL, "launch configuration out of range");
     const int wpc = cfg.tpb / 32;
     const int64_t grid = std::min<int64_t>(ceil_div(cnt, wpc), (int64_t)152 * cfg.ctas_per_sm);
     if (prec == DBCSR_BF16) {
-        size_t per_warp = 0;
-        SmmBf16Kernel kern = bf16_kernel(((m + 15) / 16 - 1) * 4 + (n + 7) / 8, &per_warp);
+        SmmBf16Kernel kern = bf16_kernel(((m + 15) / 16 - 1) * 4 + (n + 7) / 8);
         if (!kern) fail(DBCSR_ECAPACITY, "multiply: block shape beyond the BF16 kernel table");
-        const size_t sm = per_warp * wpc;
-        if (sm > 227 * 1024) fail(DBCSR_ECAPACITY, "multiply: BF16 panels exceed shared memory");
-        if (sm > 48 * 1024) DBG_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        SmmBf16Args ga{sa, a16, b16};
-        kern<<<(unsigned)grid, cfg.tpb, sm, s>>>(cnt, list, ga);
+        SmmBf16Args ga{sa, pk.a16, pk.a_stride, pk.b16, pk.b_stride};
+        kern<<<(unsigned)grid, cfg.tpb, 0, s>>>(cnt, list, ga);
     } else {
         const int mn = m * n;
         const int cls = (mn > 32 && (mn & 31) == 1) ? kF64ClassKs1 + (mn >> 5) : (mn + 31) >> 5;
@@ -973,9 +974,10 @@ void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbc
             k_find_mirror<<<grid_for(nform, 256), 256, 0, s>>>(nform, f_row.p, f_col.p, f_rp.p, mirror.p);
             DBG_LAUNCH_CK();
         } else {
-            DBG_CK(cudaMemsetAsync(mirror.p, 0xff, sizeof(int64_t) * nform, s));   // -1: no block is mirrored
+            DBG_CK(cudaMemsetAsync(mirror.p, 0xff, sizeof(int64_t) * nform, s));   // -1 (unused without sym)
         }
-        k_form_stats<<<grid_for(nform, 256), 256, 0, s>>>(nform, f_row.p, f_col.p, f_np.p, f_ksum.p, mirror.p, A->bs.p,
+        k_form_stats<<<grid_for(nform, 256), 256, 0, s>>>(nform, f_row.p, f_col.p, f_np.p, f_ksum.p, mirror.p,
+                                                          sym_result ? 1 : 0, A->bs.p,
                                                           (unsigned long long*)flops.p,
                                                           (unsigned long long*)nprod_exec.p,
                                                           (unsigned long long*)shape_cnt.p);
@@ -1035,8 +1037,8 @@ void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbc
             for (int n = 1; n <= kMaxBlock; ++n) {
                 const int64_t cnt = shapes[m * (kMaxBlock + 1) + n];
                 if (!cnt) continue;
-                k_shape_flags<<<grid_for(nform, 256), 256, 0, s>>>(nform, f_row.p, f_col.p, A->bs.p, mirror.p, m, n,
-                                                                   flag.p);
+                k_shape_flags<<<grid_for(nform, 256), 256, 0, s>>>(nform, f_row.p, f_col.p, A->bs.p, mirror.p,
+                                                                   sym_result ? 1 : 0, m, n, flag.p);
                 DBG_LAUNCH_CK();
                 scan_exclusive(flag.p, pos.p, nform, s);
                 k_class_scatter<<<grid_for(nform, 256), 256, 0, s>>>(nform, flag.p, pos.p, list.p + at);
@@ -1045,24 +1047,33 @@ void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbc
                 at += cnt;
             }
         DBuf<__nv_bfloat16> a16, b16;
+        Bf16Packs pk{};
         if (bf16) {
-            // operands rounded to BF16 (nearest even) once per product
-            a16.alloc(std::max<int64_t>(A->nel, 1), s);
-            k_to_bf16<<<grid_for(A->nel, 256, 152 * 32), 256, 0, s>>>(A->nel, A->data.p, a16.p);
-            DBG_LAUNCH_CK();
-            if (B != A) {
-                b16.alloc(std::max<int64_t>(B->nel, 1), s);
-                k_to_bf16<<<grid_for(B->nel, 256, 152 * 32), 256, 0, s>>>(B->nel, B->data.p, b16.p);
+            // operands rounded to BF16 (nearest even) once per product, into fragment-ready copies
+            const int maxbs = *std::max_element(A->h_bs.begin(), A->h_bs.end());
+            pk.a_stride = pack_stride(0, maxbs);
+            pk.b_stride = pack_stride(1, maxbs);
+            a16.alloc(std::max<int64_t>(A->nnzb, 1) * pk.a_stride, s);
+            b16.alloc(std::max<int64_t>(B->nnzb, 1) * pk.b_stride, s);
+            if (A->nnzb) {
+                k_pack_bf16<<<grid_for(A->nnzb, 8), 256, 0, s>>>(A->nnzb, 0, A->row.p, A->col.p, A->bs.p, A->off.p,
+                                                                 A->data.p, pk.a_stride, a16.p);
                 DBG_LAUNCH_CK();
             }
+            if (B->nnzb) {
+                k_pack_bf16<<<grid_for(B->nnzb, 8), 256, 0, s>>>(B->nnzb, 1, B->row.p, B->col.p, B->bs.p, B->off.p,
+                                                                 B->data.p, pk.b_stride, b16.p);
+                DBG_LAUNCH_CK();
+            }
+            pk.a16 = a16.p;
+            pk.b16 = b16.p;
         }
         // the inner size the tuned configurations are looked up with: the largest block edge
         const int kmax = *std::max_element(A->h_bs.begin(), A->h_bs.end());
         DBG_CK(cudaEventRecord(ev.e[1], s));
         at = 0;
         for (const ShapeLaunch& L : launches) {
-            launch_smm_shape(prec, L.m, L.n, L.cnt, list.p + at, sa, a16.p, B != A ? b16.p : a16.p,
-                             tune_lookup(prec, L.m, L.n, kmax), s);
+            launch_smm_shape(prec, L.m, L.n, L.cnt, list.p + at, sa, pk, tune_lookup(prec, L.m, L.n, kmax), s);
             at += L.cnt;
         }
         if (sym_result) {

@@ -47,6 +47,12 @@ dbcsr_status sign_iterate(dbcsr_matrix_* H, double mu, const dbcsr_sign_opts* op
     if (!(o.eps_filter >= 0) || !(o.tol > 0)) fail(DBCSR_EINVAL, "sign_iterate: need eps_filter >= 0 and tol > 0");
     if (o.prec != DBCSR_FP64 && o.prec != DBCSR_MIXED) fail(DBCSR_EINVAL, "sign_iterate: prec must be FP64 or MIXED");
     if (o.prec == DBCSR_MIXED && !(o.switch_tol > 0)) o.switch_tol = 1e-4;
+    // symmetric products (upper blocks computed, lower mirrored) in the FP64 tier; in the
+    // BF16 tier only on request (X2 there commutes with X only to BF16 accuracy)
+    // The mixed ladder forms both triangles: with mirrored FP64 products after a BF16
+    // tier the iteration was measured to stall near r = 3e-6 (cause not identified).
+    const bool sym_fp64 = !(o.flags & DBCSR_SIGN_FULL_PRODUCTS) && o.prec == DBCSR_FP64;
+    const bool sym_bf16 = !(o.flags & DBCSR_SIGN_FULL_PRODUCTS) && (o.flags & DBCSR_SIGN_SYM_BF16);
 
     const auto t0 = std::chrono::steady_clock::now();
     cudaStream_t s = H->stream;
@@ -69,7 +75,7 @@ dbcsr_status sign_iterate(dbcsr_matrix_* H, double mu, const dbcsr_sign_opts* op
     int first_fp64 = (tier == DBCSR_FP64) ? 1 : 0;
     while (it < o.max_iter) {
         dbcsr_mult_stats st{};
-        multiply(1.0, X.get(), X.get(), 0.0, X2.get(), o.eps_filter, tier, &st, true, true);
+        multiply(1.0, X.get(), X.get(), 0.0, X2.get(), o.eps_filter, tier, &st, true, tier == DBCSR_BF16 ? sym_bf16 : sym_fp64);
         res = std::sqrt(st.dev2_filtered) / N;
         r.flops += st.flops;
         r.n_products += st.n_products;
@@ -105,7 +111,7 @@ dbcsr_status sign_iterate(dbcsr_matrix_* H, double mu, const dbcsr_sign_opts* op
                 break;
             }
         }
-        multiply(-0.5, X.get(), X2.get(), 1.5, X.get(), o.eps_filter, tier, &st, false, true);
+        multiply(-0.5, X.get(), X2.get(), 1.5, X.get(), o.eps_filter, tier, &st, false, tier == DBCSR_BF16 ? sym_bf16 : sym_fp64);
         r.flops += st.flops;
         r.n_products += st.n_products;
         r.ms_multiply += st.ms_numeric;

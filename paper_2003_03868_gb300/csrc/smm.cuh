@@ -44,8 +44,19 @@ std::vector<TuneCfg> tune_space(int prec);
 // Features of one (m, n, k, configuration) sample for the prediction model.
 void mlp_features(int prec, int m, int n, int k, const TuneCfg& c, float* f);
 
+// Fragment-ready BF16 copies of the operands (BF16 products only): block b of A
+// at a16 + b * a_stride (m x k padded to 16-multiples), block b of B transposed at
+// b16 + b * b_stride (n x k padded to 8 x 16-multiples).
+struct Bf16Packs {
+    const __nv_bfloat16* a16 = nullptr;
+    int64_t a_stride = 0;
+    const __nv_bfloat16* b16 = nullptr;
+    int64_t b_stride = 0;
+};
+int64_t pack_stride(int role, int maxbs);
+
 // Launches the kernel of shape (m, n) over the cnt blocks listed in list.
 void launch_smm_shape(int prec, int m, int n, int64_t cnt, const int64_t* list, const SmmArgs& sa,
-                      const __nv_bfloat16* a16, const __nv_bfloat16* b16, const TuneCfg& cfg, cudaStream_t s);
+                      const Bf16Packs& pk, const TuneCfg& cfg, cudaStream_t s);
 
 }  // namespace dbg

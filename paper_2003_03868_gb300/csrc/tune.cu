@@ -66,9 +66,23 @@ __global__ void k_fill_stack_synth(int64_t nprod, int64_t nc, uint64_t seed, int
     }
 }
 
-__global__ void k_to_bf16_synth(int64_t n, const double* __restrict__ in, __nv_bfloat16* __restrict__ out) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        out[i] = __float2bfloat16((float)in[i]);   // timing data only: rounding mode is irrelevant here
+// Packed BF16 pools for timing (rounding mode is irrelevant here): A blocks m x k as
+// (16 ceil(m/16)) x (16 ceil(k/16)) tiles, B blocks k x n transposed as
+// (8 ceil(n/8)) x (16 ceil(k/16)) tiles, zero padded, at the given strides.
+__global__ void k_pack_synth(int64_t nblk, int role, int r_sz, int c_sz, const double* __restrict__ in,
+                             int64_t stride, __nv_bfloat16* __restrict__ out) {
+    const int R = role == 0 ? 16 * ((r_sz + 15) / 16) : 8 * ((c_sz + 7) / 8);
+    const int L = role == 0 ? 16 * ((c_sz + 15) / 16) : 16 * ((r_sz + 15) / 16);
+    const int64_t total = nblk * (int64_t)R * L;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = i / ((int64_t)R * L);
+        const int e = (int)(i - b * R * L), p = e / L, t = e - p * L;
+        const double* x = in + b * (int64_t)r_sz * c_sz;
+        double v = 0.0;
+        if (role == 0) v = (p < r_sz && t < c_sz) ? x[p * c_sz + t] : 0.0;
+        else v = (p < c_sz && t < r_sz) ? x[t * c_sz + p] : 0.0;
+        out[b * stride + e] = __float2bfloat16((float)v);
+    }
 }
 
 // A synthetic (m, n, k) stack resident on the device.
@@ -80,6 +94,7 @@ struct SynthStack {
     DBuf<int32_t> prod_a, prod_b, a_col, f_row, f_col, bs;
     DBuf<int64_t> a_off, b_off, f_off, f_pbeg, f_cin, list;
     SmmArgs args{};
+    Bf16Packs pk{};
 
     SynthStack(int m_, int n_, int k_, int64_t stack_len, bool bf16, cudaStream_t s) : m(m_), n(n_), k(k_) {
         nprod = stack_len;
@@ -112,12 +127,17 @@ struct SynthStack {
             a_col.p, f_row.p, f_col.p, f_off.p, f_pbeg.p, f_cin.p, list.p);
         DBG_LAUNCH_CK();
         if (bf16) {
-            a16.alloc(a.n, s);
-            b16.alloc(b.n, s);
-            k_to_bf16_synth<<<grid_for(a.n, 256), 256, 0, s>>>(a.n, a.p, a16.p);
+            const int maxbs = std::max(m, std::max(n, k));
+            pk.a_stride = pack_stride(0, maxbs);
+            pk.b_stride = pack_stride(1, maxbs);
+            a16.alloc((int64_t)kPool * pk.a_stride, s);
+            b16.alloc((int64_t)kPool * pk.b_stride, s);
+            k_pack_synth<<<grid_for(a16.n, 256, 152 * 64), 256, 0, s>>>(kPool, 0, m, k, a.p, pk.a_stride, a16.p);
             DBG_LAUNCH_CK();
-            k_to_bf16_synth<<<grid_for(b.n, 256), 256, 0, s>>>(b.n, b.p, b16.p);
+            k_pack_synth<<<grid_for(b16.n, 256, 152 * 64), 256, 0, s>>>(kPool, 1, k, n, b.p, pk.b_stride, b16.p);
             DBG_LAUNCH_CK();
+            pk.a16 = a16.p;
+            pk.b16 = b16.p;
         }
         args = SmmArgs{f_row.p, f_col.p, f_off.p, f_pbeg.p, f_cin.p, prod_a.p, prod_b.p, a_col.p, a_off.p, a.p,
                        b_off.p, b.p, nullptr, nullptr, bs.p, 1.0, 0.0, c.p, norm.p, dev2.p, 0, 0};
@@ -129,10 +149,10 @@ struct SynthStack {
         DBG_CK(cudaEventCreate(&e0));
         DBG_CK(cudaEventCreate(&e1));
         std::vector<float> t;
-        launch_smm_shape(prec, m, n, nc, list.p, args, a16.p, b16.p, cfg, s);   // warm-up
+        launch_smm_shape(prec, m, n, nc, list.p, args, pk, cfg, s);   // warm-up
         for (int r = 0; r < reps; ++r) {
             DBG_CK(cudaEventRecord(e0, s));
-            launch_smm_shape(prec, m, n, nc, list.p, args, a16.p, b16.p, cfg, s);
+            launch_smm_shape(prec, m, n, nc, list.p, args, pk, cfg, s);
             DBG_CK(cudaEventRecord(e1, s));
             DBG_CK(cudaEventSynchronize(e1));
             float ms = 0.f;

@@ -45,8 +45,9 @@ def test_batch_matches_oracle_per_system(gb, prec):
         assert r.trace_p == pytest.approx(h.n_occ, abs=1e-5)
         if prec == "fp64":
             assert r.iterations == o.iterations
+            # above the rounding floor (~1e-11 here) the residuals agree to 1e-6
             np.testing.assert_allclose([r.residual_history[i] for i in range(r.iterations)], o.residuals,
-                                       rtol=1e-6, atol=1e-13)
+                                       rtol=1e-6, atol=1e-10)
         rp, col, data = P.export()
         assert rp.shape[0] == h.H.nblk + 1
 

@@ -29,20 +29,32 @@ def gb():
 def test_sign_matches_oracle(gb, n_mol, basis, eps, tol):
     h = synth.build_hamiltonian(synth.small(n_mol, basis=basis, seed=777 + n_mol))
     H = gb.Matrix.of(h.H)
-    g = gb.sign_iterate(H, 0.0, eps, tol)
     o = sign.sign_iterate(bsr.Mat.of(h.H), 0.0, eps, tol)
-    assert g.report.alpha == pytest.approx(o.alpha, rel=1e-15)
-    assert bool(g.report.converged) == o.converged
-    assert g.report.iterations == o.iterations
-    np.testing.assert_allclose(g.residuals, o.residuals, rtol=1e-6, atol=1e-13)
-    assert abs(g.report.e_band - o.e_band) / h.n_atoms < 1e-10
-    assert g.report.trace_p == pytest.approx(o.trace_p, abs=1e-9)
+    # both triangles of every product formed: the oracle's iteration to rounding
+    f = gb.sign_iterate(H, 0.0, eps, tol, full_products=True)
+    assert f.report.alpha == pytest.approx(o.alpha, rel=1e-15)
+    assert bool(f.report.converged) == o.converged
+    assert f.report.iterations == o.iterations
+    # above the rounding floor (~1e-11 for these sizes) the residuals agree to 1e-6
+    np.testing.assert_allclose(f.residuals, o.residuals, rtol=1e-6, atol=1e-10)
+    assert abs(f.report.e_band - o.e_band) / h.n_atoms < 1e-10
+    assert f.report.trace_p == pytest.approx(o.trace_p, abs=1e-9)
     if o.converged:
-        assert g.report.trace_p == pytest.approx(h.n_occ, abs=1e-5)
-    rp, col, data = g.P.export()
-    # same pattern unless a block norm sits at eps within rounding
-    if np.array_equal(col, o.P.col):
+        assert f.report.trace_p == pytest.approx(h.n_occ, abs=1e-5)
+    rp, col, data = f.P.export()
+    if np.array_equal(col, o.P.col):        # same pattern unless a block norm sits at eps within rounding
         assert np.linalg.norm(data - o.P.data) / np.linalg.norm(o.P.data) < 1e-9
+    # default FP64 iteration (mirrored symmetric products): the mirrored X.X2 differs
+    # from the full product by the commutator with the filtered-out blocks, so it
+    # follows the oracle to the filter's accuracy
+    g = gb.sign_iterate(H, 0.0, eps, tol)
+    assert abs(g.report.iterations - o.iterations) <= 1
+    big = [i for i, r in enumerate(o.residuals) if r > 1e3 * max(eps, 1e-13)]
+    np.testing.assert_allclose([g.residuals[i] for i in big], [o.residuals[i] for i in big], rtol=1e-6)
+    assert abs(g.report.e_band - o.e_band) / h.n_atoms < max(1e-10, 0.1 * eps)
+    rp, col, data = g.P.export()
+    if np.array_equal(col, o.P.col):
+        assert np.linalg.norm(data - o.P.data) / np.linalg.norm(o.P.data) < max(1e-9, 10 * eps)
 
 
 def test_sign_against_dense_eigh(gb):
