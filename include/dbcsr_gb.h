@@ -87,16 +87,15 @@ typedef struct {
     int32_t flags;             /* DBCSR_SIGN_* bits, 0 = defaults */
 } dbcsr_sign_opts;
 
-/* dbcsr_sign_opts.flags.  By default a DBCSR_FP64 iteration forms only the blocks
- * I <= J of its products, whose exact results are symmetric, copies the blocks
- * I > J as transposes and drops blocks without a formed twin (X stays exactly
- * symmetric; results agree with full products to the filter's accuracy).  A
- * DBCSR_MIXED iteration forms both triangles of every product: with mirrored FP64
- * products after a BF16 tier the residual was measured to stall near 3e-6.
- * DBCSR_SIGN_FULL_PRODUCTS: form both triangles of every product.
- * DBCSR_SIGN_SYM_BF16: mirror in the BF16 tier too (experimental). */
+/* dbcsr_sign_opts.flags.  Every product of the iteration has a symmetric exact
+ * result.  By default a DBCSR_FP64 iteration forms only the blocks I <= J of its
+ * products and copies the blocks I > J as transposes (blocks without a formed twin
+ * are dropped), so X stays exactly symmetric and the products cost half.  A
+ * DBCSR_MIXED iteration forms both triangles of every product (mirroring after a
+ * BF16 tier measurably degraded the result) and replaces the final X by its
+ * symmetric part.  DBCSR_SIGN_FULL_PRODUCTS: form both triangles of every product
+ * and keep them as computed. */
 #define DBCSR_SIGN_FULL_PRODUCTS 1
-#define DBCSR_SIGN_SYM_BF16 2
 
 #define DBCSR_MAX_HISTORY 128
 

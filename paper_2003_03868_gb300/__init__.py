@@ -202,12 +202,11 @@ class SignResult:
 def sign_iterate(H: Matrix, mu: float, eps_filter: float, tol: float, max_iter: int = 100,
                  prec: int = DBCSR_FP64, switch_tol: float = 1e-4, stall_ratio: float = 0.5,
                  P: Matrix | None = None, verbose: bool = False, raise_on_notconv: bool = False,
-                 full_products: bool = False, sym_bf16: bool = False) -> SignResult:
+                 full_products: bool = False) -> SignResult:
     """Density matrix P = (1 - sign(H - mu 1)) / 2 by the Newton-Schulz iteration."""
     P = Matrix(H.blk_size, H.stream) if P is None else P
     o = SignOpts(float(eps_filter), float(tol), int(max_iter), int(prec), float(switch_tol), float(stall_ratio),
-                 1 if verbose else 0, (_ffi.DBCSR_SIGN_FULL_PRODUCTS if full_products else 0) |
-                 (_ffi.DBCSR_SIGN_SYM_BF16 if sym_bf16 else 0))
+                 1 if verbose else 0, _ffi.DBCSR_SIGN_FULL_PRODUCTS if full_products else 0)
     rep = SignReport()
     st = lib().dbcsr_sign_iterate(H.handle, float(mu), C.byref(o), P.handle, C.byref(rep))
     if st != _ffi.DBCSR_OK and (st != _ffi.DBCSR_ENOTCONV or raise_on_notconv):

@@ -145,10 +145,11 @@ dbcsr_status sign_iterate_batched(int32_t nsys, dbcsr_matrix_* const* H, const d
     if (o.prec == DBCSR_MIXED && !(o.switch_tol > 0)) o.switch_tol = 1e-4;
     // symmetric products (upper blocks computed, lower mirrored) in the FP64 tier; in the
     // BF16 tier only on request (X2 there commutes with X only to BF16 accuracy)
-    // The mixed ladder forms both triangles: with mirrored FP64 products after a BF16
-    // tier the iteration was measured to stall near r = 3e-6 (cause not identified).
-    const bool sym_fp64 = !(o.flags & DBCSR_SIGN_FULL_PRODUCTS) && o.prec == DBCSR_FP64;
-    const bool sym_bf16 = !(o.flags & DBCSR_SIGN_FULL_PRODUCTS) && (o.flags & DBCSR_SIGN_SYM_BF16);
+    // Every product of the iteration is symmetric in exact arithmetic.  FP64 products
+    // compute the blocks I <= J and mirror the rest; BF16 products compute both
+    // triangles and keep their symmetric mean (a BF16 X2 commutes with X only to BF16
+    // accuracy, and the asymmetry would otherwise persist through the FP64 tail).
+    const bool full = (o.flags & DBCSR_SIGN_FULL_PRODUCTS) != 0;
 
     const auto t0 = std::chrono::steady_clock::now();
     cudaStream_t st = H[0]->stream;
@@ -247,6 +248,11 @@ dbcsr_status sign_iterate_batched(int32_t nsys, dbcsr_matrix_* const* H, const d
     }
     int tier = (o.prec == DBCSR_MIXED) ? DBCSR_BF16 : DBCSR_FP64;
     int first_fp64 = (tier == DBCSR_FP64) ? 1 : 0;
+    auto sym_mode = [&](int tier_now, int step) {
+        (void)tier_now;
+        (void)step;
+        return (full || o.prec == DBCSR_MIXED) ? kSymNone : kSymMirror;
+    };
     double flops = 0.0, ms_mult = 0.0;
     int64_t nprod = 0;
     std::vector<double> dev2(nsys);
@@ -254,7 +260,7 @@ dbcsr_status sign_iterate_batched(int32_t nsys, dbcsr_matrix_* const* H, const d
     int it = 0;
     while (it < o.max_iter) {
         dbcsr_mult_stats ms{};
-        multiply(1.0, X.get(), X.get(), 0.0, X2.get(), o.eps_filter, tier, &ms, false, tier == DBCSR_BF16 ? sym_bf16 : sym_fp64);
+        multiply(1.0, X.get(), X.get(), 0.0, X2.get(), o.eps_filter, tier, &ms, false, sym_mode(tier, it + 1));
         flops += ms.flops;
         nprod += ms.n_products;
         ms_mult += ms.ms_numeric;
@@ -298,13 +304,16 @@ dbcsr_status sign_iterate_batched(int32_t nsys, dbcsr_matrix_* const* H, const d
             tier = DBCSR_FP64;
             first_fp64 = it + 1;
         }
-        multiply(-0.5, X.get(), X2.get(), 1.5, X.get(), o.eps_filter, tier, &ms, false, tier == DBCSR_BF16 ? sym_bf16 : sym_fp64);
+        multiply(-0.5, X.get(), X2.get(), 1.5, X.get(), o.eps_filter, tier, &ms, false, sym_mode(tier, it));
         flops += ms.flops;
         nprod += ms.n_products;
         ms_mult += ms.ms_numeric;
     }
     for (int32_t s = 0; s < nsys; ++s)
         if (!done[s]) done[s] = 3;
+
+    // a mixed batch forms both triangles of every product: keep X's symmetric part
+    if (o.prec == DBCSR_MIXED && !full) symmetrize(X.get());
 
     // ---- split X back into the systems: P_s = (1 - X_s) / 2
     std::vector<int64_t> hrp(nblk + 1);

@@ -159,11 +159,16 @@ void trace_product_parts_into(dbcsr_matrix_* a, dbcsr_matrix_* b, double* part, 
 
 // ---- multiply.cu
 // sym_result: the caller knows alpha*A*B + beta*C is symmetric in exact arithmetic
-// (as every product of the sign iteration is).  Only blocks I <= J whose twin (J, I)
-// is formed are computed, their twins are copied as transposes, and blocks without
-// a formed twin are dropped: the result is exactly symmetric.
+// (as every product of the sign iteration is), and the result is made exactly
+// symmetric; blocks without a formed twin (J, I) are dropped.
+//   kSymMirror:  only blocks I <= J are computed, their twins copied as transposes;
+//   kSymAverage: both twins are computed and replaced by their symmetric mean
+//                (for operands that commute only approximately, e.g. BF16 products).
+constexpr int kSymNone = 0, kSymMirror = 1, kSymAverage = 2;
+// m <- (m + m^T) / 2 on the blocks that have a twin; blocks without one are dropped.
+void symmetrize(dbcsr_matrix_* m);
 void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbcsr_matrix_* C, double eps,
-              int prec, dbcsr_mult_stats* stats, bool want_dev2, bool sym_result = false);
+              int prec, dbcsr_mult_stats* stats, bool want_dev2, int sym_result = kSymNone);
 
 // ---- sign.cu
 dbcsr_status sign_iterate(dbcsr_matrix_* H, double mu, const dbcsr_sign_opts* opts, dbcsr_matrix_* P,

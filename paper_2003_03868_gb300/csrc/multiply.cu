@@ -251,11 +251,75 @@ __global__ void k_find_mirror(int64_t nform, const int32_t* __restrict__ f_row, 
     }
 }
 
-// role of formed block k: 0 computed, 1 copied from its twin, 2 dropped
+// role of formed block k: 0 computed, 1 copied from its twin, 2 dropped.
+// sym = 1 (mirror): I < J computed, I > J copied; sym = 2 (average): both twins
+// computed and then replaced by their symmetric mean; blocks without a formed twin
+// are dropped in both modes.
 __device__ __forceinline__ int block_role(int sym, int32_t I, int32_t J, int64_t mirror) {
     if (!sym || I == J) return 0;
     if (mirror < 0) return 2;
-    return I < J ? 0 : 1;
+    return (I < J || sym == 2) ? 0 : 1;
+}
+
+// sym = 2: C_IJ and C_JI become (C_IJ + C_JI^T) / 2 and its transpose, with their
+// norms and distances to 1 (the pair is handled by the warp of its I < J block;
+// diagonal blocks by their own warp).
+__global__ void k_sym_average(int64_t nform, const int64_t* __restrict__ mirror, const int32_t* __restrict__ f_row,
+                              const int32_t* __restrict__ f_col, const int64_t* __restrict__ f_off,
+                              const int32_t* __restrict__ bs, double* __restrict__ c_data,
+                              double* __restrict__ c_norm, double* __restrict__ c_dev2) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t k = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); k < nform; k += warps) {
+        const int32_t I = f_row[k], J = f_col[k];
+        const int64_t t = mirror[k];
+        if (t < 0 || I > J) continue;
+        const int m = bs[I], n = bs[J];
+        double* P = c_data + f_off[k];
+        double* Q = c_data + f_off[t];
+        double sq = 0.0, d = 0.0;
+        if (I == J) {
+            // symmetrise the diagonal block in place: pairs (i, j) and (j, i), i < j
+            for (int e = lane; e < m * m; e += 32) {
+                const int i = e / m, j = e - i * m;
+                if (i < j) {
+                    const double v = 0.5 * (P[i * m + j] + P[j * m + i]);
+                    P[i * m + j] = v;
+                    P[j * m + i] = v;
+                }
+            }
+            __syncwarp();
+            for (int e = lane; e < m * m; e += 32) {
+                const int i = e / m, j = e - i * m;
+                const double v = P[e];
+                sq = fma(v, v, sq);
+                const double w = (i == j) ? v - 1.0 : v;
+                d = fma(w, w, d);
+            }
+        } else {
+            for (int e = lane; e < m * n; e += 32) {
+                const int i = e / n, j = e - i * n;
+                const double v = 0.5 * (P[e] + Q[j * m + i]);
+                P[e] = v;
+                Q[j * m + i] = v;
+                sq = fma(v, v, sq);
+            }
+            d = sq;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            sq += __shfl_xor_sync(0xffffffffu, sq, o);
+            d += __shfl_xor_sync(0xffffffffu, d, o);
+        }
+        if (lane == 0) {
+            c_norm[k] = sqrt(sq);
+            c_dev2[k] = d;
+            if (I != J) {
+                c_norm[t] = sqrt(sq);
+                c_dev2[t] = sq;
+            }
+        }
+    }
 }
 
 // Work of the blocks that are computed (not mirrored): flops, products, and a
@@ -286,14 +350,14 @@ __global__ void k_form_stats(int64_t nform, const int32_t* __restrict__ f_row, c
 // Copied blocks: C_IJ = C_JI^T (after every computed block is written), with their
 // norm and distance to 1 (never diagonal); dropped blocks get norm -1 so that the
 // filter removes them.
-__global__ void k_mirror_copy(int64_t nform, const int64_t* __restrict__ mirror, const int32_t* __restrict__ f_row,
-                              const int32_t* __restrict__ f_col, const int64_t* __restrict__ f_off,
-                              const int32_t* __restrict__ bs, double* __restrict__ c_data, double* __restrict__ c_norm,
-                              double* __restrict__ c_dev2) {
+__global__ void k_mirror_copy(int64_t nform, int sym, const int64_t* __restrict__ mirror,
+                              const int32_t* __restrict__ f_row, const int32_t* __restrict__ f_col,
+                              const int64_t* __restrict__ f_off, const int32_t* __restrict__ bs,
+                              double* __restrict__ c_data, double* __restrict__ c_norm, double* __restrict__ c_dev2) {
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t k = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); k < nform; k += warps) {
-        const int role = block_role(1, f_row[k], f_col[k], mirror[k]);
+        const int role = block_role(sym, f_row[k], f_col[k], mirror[k]);
         if (role == 0) continue;
         if (role == 2) {
             if (lane == 0) {
@@ -825,6 +889,11 @@ struct EventSet {
 
 int sym_grid(int32_t nblk) { return std::min<int32_t>(nblk, 152 * 8); }
 
+__global__ void k_keep_twinned(int64_t nb, const int64_t* __restrict__ mirror, int32_t* __restrict__ keep) {
+    for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nb; b += (int64_t)gridDim.x * blockDim.x)
+        keep[b] = mirror[b] >= 0 ? 1 : 0;
+}
+
 }  // namespace
 
 // Largest packed tile of a role for blocks of edge <= maxbs.
@@ -867,8 +936,30 @@ void launch_smm_shape(int prec, int m, int n, int64_t cnt, const int64_t* list, 
     DBG_LAUNCH_CK();
 }
 
+void symmetrize(dbcsr_matrix_* m) {
+    check_finalized(m);
+    cudaStream_t s = m->stream;
+    const int64_t nb = m->nnzb;
+    if (nb == 0) return;
+    DBuf<int64_t> mirror;
+    DBuf<double> norm, dev2;
+    DBuf<int32_t> keep;
+    mirror.alloc(nb, s);
+    norm.alloc(nb, s);
+    dev2.alloc(nb, s);
+    keep.alloc(nb, s);
+    k_find_mirror<<<grid_for(nb, 256), 256, 0, s>>>(nb, m->row.p, m->col.p, m->rp.p, mirror.p);
+    DBG_LAUNCH_CK();
+    k_sym_average<<<grid_for(nb, 8), 256, 0, s>>>(nb, mirror.p, m->row.p, m->col.p, m->off.p, m->bs.p, m->data.p,
+                                                 norm.p, dev2.p);
+    DBG_LAUNCH_CK();
+    k_keep_twinned<<<grid_for(nb, 256), 256, 0, s>>>(nb, mirror.p, keep.p);
+    DBG_LAUNCH_CK();
+    compact(m, keep.p, nullptr);
+}
+
 void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbcsr_matrix_* C, double eps, int prec,
-              dbcsr_mult_stats* stats, bool want_dev2, bool sym_result) {
+              dbcsr_mult_stats* stats, bool want_dev2, int sym_result) {
     check_finalized(A);
     check_finalized(B);
     if (!C) fail(DBCSR_EINVAL, "multiply: null C");
@@ -977,7 +1068,7 @@ void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbc
             DBG_CK(cudaMemsetAsync(mirror.p, 0xff, sizeof(int64_t) * nform, s));   // -1 (unused without sym)
         }
         k_form_stats<<<grid_for(nform, 256), 256, 0, s>>>(nform, f_row.p, f_col.p, f_np.p, f_ksum.p, mirror.p,
-                                                          sym_result ? 1 : 0, A->bs.p,
+                                                          sym_result, A->bs.p,
                                                           (unsigned long long*)flops.p,
                                                           (unsigned long long*)nprod_exec.p,
                                                           (unsigned long long*)shape_cnt.p);
@@ -1038,7 +1129,7 @@ void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbc
                 const int64_t cnt = shapes[m * (kMaxBlock + 1) + n];
                 if (!cnt) continue;
                 k_shape_flags<<<grid_for(nform, 256), 256, 0, s>>>(nform, f_row.p, f_col.p, A->bs.p, mirror.p,
-                                                                   sym_result ? 1 : 0, m, n, flag.p);
+                                                                   sym_result, m, n, flag.p);
                 DBG_LAUNCH_CK();
                 scan_exclusive(flag.p, pos.p, nform, s);
                 k_class_scatter<<<grid_for(nform, 256), 256, 0, s>>>(nform, flag.p, pos.p, list.p + at);
@@ -1077,12 +1168,18 @@ void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbc
             at += L.cnt;
         }
         if (sym_result) {
-            k_mirror_copy<<<grid_for(nform, 8), 256, 0, s>>>(nform, mirror.p, f_row.p, f_col.p, f_off.p, A->bs.p,
-                                                            c_data.p, c_norm.p, c_dev2.p);
+            DBG_CK(cudaEventRecord(ev.e[2], s));     // the copy / averaging is timed with the filter
+            k_mirror_copy<<<grid_for(nform, 8), 256, 0, s>>>(nform, sym_result, mirror.p, f_row.p, f_col.p, f_off.p,
+                                                            A->bs.p, c_data.p, c_norm.p, c_dev2.p);
             DBG_LAUNCH_CK();
+            if (sym_result == 2) {
+                k_sym_average<<<grid_for(nform, 8), 256, 0, s>>>(nform, mirror.p, f_row.p, f_col.p, f_off.p, A->bs.p,
+                                                                c_data.p, c_norm.p, c_dev2.p);
+                DBG_LAUNCH_CK();
+            }
         }
     }
-    DBG_CK(cudaEventRecord(ev.e[2], s));
+    if (!sym_result || !nform) DBG_CK(cudaEventRecord(ev.e[2], s));
     prod_a.release(); prod_b.release();
 
     // install the formed blocks as C (A or B may alias C: every read above is queued before)

@@ -49,10 +49,13 @@ dbcsr_status sign_iterate(dbcsr_matrix_* H, double mu, const dbcsr_sign_opts* op
     if (o.prec == DBCSR_MIXED && !(o.switch_tol > 0)) o.switch_tol = 1e-4;
     // symmetric products (upper blocks computed, lower mirrored) in the FP64 tier; in the
     // BF16 tier only on request (X2 there commutes with X only to BF16 accuracy)
-    // The mixed ladder forms both triangles: with mirrored FP64 products after a BF16
-    // tier the iteration was measured to stall near r = 3e-6 (cause not identified).
-    const bool sym_fp64 = !(o.flags & DBCSR_SIGN_FULL_PRODUCTS) && o.prec == DBCSR_FP64;
-    const bool sym_bf16 = !(o.flags & DBCSR_SIGN_FULL_PRODUCTS) && (o.flags & DBCSR_SIGN_SYM_BF16);
+    // Every product of the iteration is symmetric in exact arithmetic.  FP64 products
+    // compute the blocks I <= J and mirror the rest.  BF16 products keep both
+    // triangles as computed (a BF16 X2 commutes with X only to BF16 accuracy, so X
+    // leaves the BF16 tier slightly asymmetric); the two products of the first FP64
+    // step keep the symmetric mean of both triangles, which makes X exactly
+    // symmetric again before the mirrored products take over.
+    const bool full = (o.flags & DBCSR_SIGN_FULL_PRODUCTS) != 0;
 
     const auto t0 = std::chrono::steady_clock::now();
     cudaStream_t s = H->stream;
@@ -73,9 +76,14 @@ dbcsr_status sign_iterate(dbcsr_matrix_* H, double mu, const dbcsr_sign_opts* op
     // precision ladder: BF16 operands / FP32 accumulation while r >= switch_tol, then FP64
     int tier = (o.prec == DBCSR_MIXED) ? DBCSR_BF16 : DBCSR_FP64;
     int first_fp64 = (tier == DBCSR_FP64) ? 1 : 0;
+    auto sym_mode = [&](int tier_now, int step) {
+        (void)tier_now;
+        (void)step;
+        return (full || o.prec == DBCSR_MIXED) ? kSymNone : kSymMirror;
+    };
     while (it < o.max_iter) {
         dbcsr_mult_stats st{};
-        multiply(1.0, X.get(), X.get(), 0.0, X2.get(), o.eps_filter, tier, &st, true, tier == DBCSR_BF16 ? sym_bf16 : sym_fp64);
+        multiply(1.0, X.get(), X.get(), 0.0, X2.get(), o.eps_filter, tier, &st, true, sym_mode(tier, it + 1));
         res = std::sqrt(st.dev2_filtered) / N;
         r.flops += st.flops;
         r.n_products += st.n_products;
@@ -111,12 +119,15 @@ dbcsr_status sign_iterate(dbcsr_matrix_* H, double mu, const dbcsr_sign_opts* op
                 break;
             }
         }
-        multiply(-0.5, X.get(), X2.get(), 1.5, X.get(), o.eps_filter, tier, &st, false, tier == DBCSR_BF16 ? sym_bf16 : sym_fp64);
+        multiply(-0.5, X.get(), X2.get(), 1.5, X.get(), o.eps_filter, tier, &st, false, sym_mode(tier, it));
         r.flops += st.flops;
         r.n_products += st.n_products;
         r.ms_multiply += st.ms_numeric;
         if (it - 1 < DBCSR_MAX_HISTORY) r.nnzb_history[it - 1] = X->nnzb;
     }
+    // a mixed run forms both triangles of every product; its X is symmetric only to
+    // BF16 accuracy, so it is replaced by its symmetric part before P is formed
+    if (o.prec == DBCSR_MIXED && !full) symmetrize(X.get());
     copy_matrix(P, X.get());
     scale_shift(P, -0.5, 0.5);
     r.trace_p = trace(P);

@@ -115,3 +115,17 @@ def test_mixed_sign_1024_waters(gb):
     assert g.report.fp64_from > 1
     assert abs(g.report.e_band - ref["e_band"]) / h.n_atoms < DE_ATOM
     assert g.report.trace_p == pytest.approx(4096, abs=1e-4)
+
+
+def test_mixed_density_matrix_is_symmetric(gb):
+    h = synth.build_hamiltonian(synth.small(24, seed=990 + 24))
+    g = gb.sign_iterate(gb.Matrix.of(h.H), 0.0, 1e-7, 1e-8, prec=gb.DBCSR_MIXED)
+    rp, col, data = g.P.export()
+    D = bsr.to_dense(bsr.Mat(h.H.blk_size, rp, col, data))
+    assert np.linalg.norm(D - D.T) <= 1e-14 * np.linalg.norm(D)
+    # the default FP64 iteration mirrors its off-diagonal blocks; its diagonal blocks
+    # are computed, so they are symmetric to rounding
+    f = gb.sign_iterate(gb.Matrix.of(h.H), 0.0, 1e-7, 1e-8)
+    rp, col, data = f.P.export()
+    D = bsr.to_dense(bsr.Mat(h.H.blk_size, rp, col, data))
+    assert np.linalg.norm(D - D.T) <= 1e-14 * np.linalg.norm(D)
