@@ -31,6 +31,21 @@ NOMINAL_BF16 = 2250.0
 NOMINAL_FP64 = 1.25
 FALLBACK_BF16_BURST, FALLBACK_BF16_SUSTAINED = 1900.0, 1700.0
 
+# DRAM traffic of the FP64 block-product kernels (dram__bytes_read.sum + dram__bytes_write.sum),
+# averaged over the 84 k_smm_f64 launches of one sign-1024h2o step, from one ncu capture of
+# the current kernels (profiles/k_smm_f64_traffic_sign1024h2o.md).  Set to None when the
+# kernels change.
+SMM_F64_TRAFFIC = {"sign-1024h2o-dzvp-fp64": 2.8191e9}
+
+
+def bf16_peak():
+    """Measured bf16 tensor peak (sustained: the low tier runs inside a seconds-long step)."""
+    try:
+        pk = json.load(open(PEAKS_FILE))
+        return float(pk["bf16_tflops_sustained"]), "measured bf16 sustained"
+    except Exception:
+        return FALLBACK_BF16_SUSTAINED, "fallback bf16 sustained"
+
 
 def fp64_peak():
     """FP64 roofline peak: the measured bf16 peak times the nominal FP64/bf16 ratio."""
@@ -245,10 +260,13 @@ def main():
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     flops, ms_mult, iters, ebands, trp, conv = 0.0, 0.0, [], [], [], []
+    bytes_min, smm_launches = 0.0, 0
     for _ in range(args.steps):
         r = step()
         flops += r.report.flops
         ms_mult += r.report.ms_multiply
+        bytes_min += r.report.bytes_min_fp64
+        smm_launches += r.report.launches_fp64
         iters.append(r.report.iterations)
         ebands.append(r.report.e_band)
         trp.append(r.report.trace_p)
@@ -268,32 +286,52 @@ def main():
     ms_all, flops_all = float(t[0]), float(t[1])
     value = flops_all / (ms_all * 1e-3) / 1e12
 
-    # the same workload with the precision ladder: BF16 tensor-core products while r >= 1e-4, then FP64
+    # the same workload with the precision ladder: split-BF16 tensor-core products while r >= 1e-4,
+    # then FP64 (and, for comparison, the ladder with plain BF16 products)
     mixed = None
     if not args.no_mixed:
-        def step_mixed():
-            return gb.sign_iterate(H, h.mu, w.eps_filter, w.tol, prec=gb.DBCSR_MIXED, switch_tol=1e-4,
-                                   verbose=args.verbose)
-        for _ in range(args.warmup):
-            rm = step_mixed()
-        barrier()
-        m0, m1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        m0.record(stream)
-        mfl = 0.0
-        for _ in range(args.steps):
-            rm = step_mixed()
-            mfl += rm.report.flops
-        m1.record(stream)
-        torch.cuda.synchronize()
-        barrier()
-        mms = m0.elapsed_time(m1)
-        mixed = {"time_to_p_ms": mms / args.steps, "value": mfl / (mms * 1e-3) / 1e12, "unit": "TFLOP/s",
+        def time_mixed(low):
+            def one():
+                return gb.sign_iterate(H, h.mu, w.eps_filter, w.tol, prec=gb.DBCSR_MIXED, switch_tol=1e-4,
+                                       low=low, verbose=args.verbose)
+            for _ in range(args.warmup):
+                one()
+            barrier()
+            m0, m1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            m0.record(stream)
+            acc = {"flops": 0.0, "flops_low": 0.0, "ms_low": 0.0, "ms_multiply": 0.0, "ms_symbolic": 0.0,
+                   "ms_filter": 0.0}
+            for _ in range(args.steps):
+                rm = one()
+                for k in acc:
+                    acc[k] += getattr(rm.report, k)
+            m1.record(stream)
+            torch.cuda.synchronize()
+            barrier()
+            return rm, m0.elapsed_time(m1), acc
+
+        rm, mms, acc = time_mixed(gb.DBCSR_BF16X3)
+        bpk, bpk_src = bf16_peak()
+        low_alg = acc["flops_low"] / (acc["ms_low"] * 1e-3) / 1e12 if acc["ms_low"] > 0 else 0.0
+        mixed = {"time_to_p_ms": mms / args.steps, "value": acc["flops"] / (mms * 1e-3) / 1e12, "unit": "TFLOP/s",
                  "speedup_vs_fp64": (ms_all / args.steps) / (mms / args.steps),
                  "iterations": rm.report.iterations, "fp64_from_step": rm.report.fp64_from,
                  "converged": bool(rm.report.converged), "stalled": bool(rm.report.stalled),
                  "residual": rm.report.residual, "trace_p": rm.report.trace_p, "e_band": rm.report.e_band,
                  "de_band_per_atom_vs_fp64": abs(rm.report.e_band - ebands[-1]) / h.n_atoms,
-                 "switch": 1e-4, "dtype": "bf16 operands / fp32 accumulate, then f64"}
+                 "switch": 1e-4,
+                 "dtype": "bf16x3 (split bf16 hi+lo operands, fp32 accumulate), then f64",
+                 "ms_per_step": {k: acc[k] / args.steps for k in ("ms_low", "ms_multiply", "ms_symbolic", "ms_filter")},
+                 "low_tier_roofline": {"bound": "tensor", "kernel": "k_smm_bf16<MT,NT,split>",
+                                       "achieved": 3 * low_alg, "unit": "TFLOP/s", "peak": bpk,
+                                       "frac": 3 * low_alg / bpk, "peak_source": bpk_src,
+                                       "algorithmic_tflops": low_alg,
+                                       "note": "achieved counts the three bf16 products (hi*hi, hi*lo, lo*hi) "
+                                               "of every unpadded 2mnk block product"}}
+        rp_, mps, _ = time_mixed(gb.DBCSR_BF16)
+        mixed["plain_bf16"] = {"time_to_p_ms": mps / args.steps, "iterations": rp_.report.iterations,
+                               "fp64_from_step": rp_.report.fp64_from,
+                               "de_band_per_atom_vs_fp64": abs(rp_.report.e_band - ebands[-1]) / h.n_atoms}
 
     # end to end through the public API: inputs from pinned host memory, report read back
     e2e = None
@@ -322,8 +360,10 @@ def main():
     peak, peak_src = fp64_peak()
     achieved = flops / (ms_mult * 1e-3) / 1e12 if ms_mult > 0 else 0.0
     roofline = {"bound": "fp64", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None, "kernel": "k_smm_f64",
-                "peak_source": peak_src, "kernel_share_of_step": ms_mult / ms if ms > 0 else None}
+                "frac": achieved / peak, "traffic": SMM_F64_TRAFFIC.get(w.name), "kernel": "k_smm_f64",
+                "peak_source": peak_src, "kernel_share_of_step": ms_mult / ms if ms > 0 else None,
+                "launches_per_step": smm_launches / args.steps,
+                "compulsory_bytes_per_launch": bytes_min / smm_launches if smm_launches else None}
     try:
         roofline["fp64_dfma_measured_tflops"] = gb.lib().dbcsr_bench_peak(0, 4096, 152 * 8, 256) / 1e3
         roofline["fp64_dmma_measured_tflops"] = gb.lib().dbcsr_bench_peak(1, 4096, 152 * 8, 256) / 1e3

@@ -56,7 +56,9 @@ typedef enum {
 typedef enum {
     DBCSR_FP64 = 0,       /* FP64 operands, FP64 accumulation */
     DBCSR_BF16 = 2,       /* BF16 operands (round to nearest even), FP32 accumulation, FP64 result */
-    DBCSR_MIXED = 3       /* sign iteration only: BF16 tier while the residual >= switch, then FP64 */
+    DBCSR_MIXED = 3,      /* sign iteration only: low-precision tier while the residual >= switch, then FP64 */
+    DBCSR_BF16X3 = 4      /* split BF16 operands a = hi + lo (both BF16), A B ~ Ah Bh + Ah Bl + Al Bh on the
+                             BF16 tensor cores with FP32 accumulation (about 16 significant bits), FP64 result */
 } dbcsr_prec;
 
 /* Work counters of one product.  Counts refer to the blocks the product
@@ -73,6 +75,10 @@ typedef struct {
     double ms_symbolic;        /* device time of the stack builder, ms */
     double ms_numeric;         /* device time of the block-product kernel, ms */
     double ms_filter;          /* device time of norm-filter-compaction, ms */
+    double bytes_min;          /* compulsory bytes of the block-product launches: A and B read once,
+                                  computed C blocks written once (a C input other than A, B read once) */
+    int32_t n_launches;        /* block-product kernel launches (one per block shape) */
+    int32_t reserved;
 } dbcsr_mult_stats;
 
 /* Options of the sign iteration. */
@@ -88,14 +94,19 @@ typedef struct {
 } dbcsr_sign_opts;
 
 /* dbcsr_sign_opts.flags.  Every product of the iteration has a symmetric exact
- * result.  By default a DBCSR_FP64 iteration forms only the blocks I <= J of its
- * products and copies the blocks I > J as transposes (blocks without a formed twin
- * are dropped), so X stays exactly symmetric and the products cost half.  A
- * DBCSR_MIXED iteration forms both triangles of every product (mirroring after a
- * BF16 tier measurably degraded the result) and replaces the final X by its
- * symmetric part.  DBCSR_SIGN_FULL_PRODUCTS: form both triangles of every product
- * and keep them as computed. */
+ * result.  By default every product forms only the blocks I <= J and copies the
+ * blocks I > J as transposes (blocks without a formed twin are dropped), so X stays
+ * symmetric and the products cost half.  The low tier of a DBCSR_MIXED iteration
+ * uses split-BF16 products (DBCSR_BF16X3), which commute with X to about 1e-5;
+ * the final X of a mixed run is replaced by its symmetric part (its diagonal
+ * blocks are summed in FP32).
+ * DBCSR_SIGN_FULL_PRODUCTS: form both triangles of every product and keep them as
+ * computed (no final symmetrisation).
+ * DBCSR_SIGN_PLAIN_BF16: DBCSR_MIXED's low tier uses plain BF16 products.  A BF16
+ * X2 commutes with X only to about 1e-3, so this ladder forms both triangles of
+ * every product and symmetrises the final X. */
 #define DBCSR_SIGN_FULL_PRODUCTS 1
+#define DBCSR_SIGN_PLAIN_BF16 2
 
 #define DBCSR_MAX_HISTORY 128
 
@@ -116,6 +127,12 @@ typedef struct {
     int64_t nnzb_x;            /* blocks of the converged X */
     double residual_history[DBCSR_MAX_HISTORY];
     int64_t nnzb_history[DBCSR_MAX_HISTORY];
+    double ms_symbolic;        /* device time of the stack builders, ms */
+    double ms_filter;          /* device time of norm-filter-compaction (and mirroring), ms */
+    double ms_low;             /* device time of the low tier's block-product kernels, ms */
+    double flops_low;          /* executed 2*m*k*n of the low tier's products */
+    double bytes_min_fp64;     /* sum of dbcsr_mult_stats.bytes_min over the FP64 products */
+    int64_t launches_fp64;     /* sum of dbcsr_mult_stats.n_launches over the FP64 products */
 } dbcsr_sign_report;
 
 /* Last error message of the calling host thread ("" if none). */
@@ -178,7 +195,7 @@ dbcsr_status dbcsr_scale_shift(dbcsr_matrix m, double scale, double shift);
  * The sum over K of each C_IJ is taken in ascending K.  C may be the same
  * handle as A and/or B.  The result is formed on the pattern of A*B (union C's
  * pattern when beta != 0) less the candidates that the exact norm-bound
- * prescreen proves would be filtered.  prec: DBCSR_FP64 or DBCSR_BF16.
+ * prescreen proves would be filtered.  prec: DBCSR_FP64, DBCSR_BF16 or DBCSR_BF16X3.
  * stats may be NULL; when given, the call synchronises and fills it.
  */
 dbcsr_status dbcsr_multiply(double alpha, dbcsr_matrix A, dbcsr_matrix B, double beta, dbcsr_matrix C,

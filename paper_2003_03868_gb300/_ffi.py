@@ -9,8 +9,8 @@ LIB_PATH = os.path.join(HERE, "libdbcsr_gb.so")
 
 DBCSR_OK, DBCSR_EINVAL, DBCSR_ENOMEM, DBCSR_ECAPACITY, DBCSR_ECUDA = 0, 1, 2, 3, 4
 DBCSR_ENAN, DBCSR_ENOTCONV, DBCSR_ETIMEOUT, DBCSR_ESTATE = 5, 6, 7, 8
-DBCSR_FP64, DBCSR_BF16, DBCSR_MIXED = 0, 2, 3
-DBCSR_SIGN_FULL_PRODUCTS = 1
+DBCSR_FP64, DBCSR_BF16, DBCSR_MIXED, DBCSR_BF16X3 = 0, 2, 3, 4
+DBCSR_SIGN_FULL_PRODUCTS, DBCSR_SIGN_PLAIN_BF16 = 1, 2
 MAX_HISTORY = 128
 
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECAPACITY", 4: "ECUDA", 5: "ENAN", 6: "ENOTCONV",
@@ -20,7 +20,8 @@ STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECAPACITY", 4: "ECUDA", 5
 class MultStats(C.Structure):
     _fields_ = [("n_candidates", C.c_int64), ("n_formed", C.c_int64), ("n_kept", C.c_int64),
                 ("n_products", C.c_int64), ("flops", C.c_double), ("dev2_filtered", C.c_double),
-                ("ms_symbolic", C.c_double), ("ms_numeric", C.c_double), ("ms_filter", C.c_double)]
+                ("ms_symbolic", C.c_double), ("ms_numeric", C.c_double), ("ms_filter", C.c_double),
+                ("bytes_min", C.c_double), ("n_launches", C.c_int32), ("reserved", C.c_int32)]
 
 
 class SignOpts(C.Structure):
@@ -34,7 +35,9 @@ class SignReport(C.Structure):
                 ("alpha", C.c_double), ("residual", C.c_double), ("trace_p", C.c_double), ("e_band", C.c_double),
                 ("flops", C.c_double), ("n_products", C.c_int64), ("ms_total", C.c_double),
                 ("ms_multiply", C.c_double), ("nnzb_x", C.c_int64),
-                ("residual_history", C.c_double * MAX_HISTORY), ("nnzb_history", C.c_int64 * MAX_HISTORY)]
+                ("residual_history", C.c_double * MAX_HISTORY), ("nnzb_history", C.c_int64 * MAX_HISTORY),
+                ("ms_symbolic", C.c_double), ("ms_filter", C.c_double), ("ms_low", C.c_double),
+                ("flops_low", C.c_double), ("bytes_min_fp64", C.c_double), ("launches_fp64", C.c_int64)]
 
 
 class KernelCfg(C.Structure):

@@ -143,13 +143,12 @@ dbcsr_status sign_iterate_batched(int32_t nsys, dbcsr_matrix_* const* H, const d
     if (!(o.eps_filter >= 0) || !(o.tol > 0)) fail(DBCSR_EINVAL, "sign_iterate_batched: need eps_filter >= 0 and tol > 0");
     if (o.prec != DBCSR_FP64 && o.prec != DBCSR_MIXED) fail(DBCSR_EINVAL, "sign_iterate_batched: prec must be FP64 or MIXED");
     if (o.prec == DBCSR_MIXED && !(o.switch_tol > 0)) o.switch_tol = 1e-4;
-    // symmetric products (upper blocks computed, lower mirrored) in the FP64 tier; in the
-    // BF16 tier only on request (X2 there commutes with X only to BF16 accuracy)
-    // Every product of the iteration is symmetric in exact arithmetic.  FP64 products
-    // compute the blocks I <= J and mirror the rest; BF16 products compute both
-    // triangles and keep their symmetric mean (a BF16 X2 commutes with X only to BF16
-    // accuracy, and the asymmetry would otherwise persist through the FP64 tail).
+    // Every product of the iteration is symmetric in exact arithmetic.  FP64 and split-BF16
+    // products compute the blocks I <= J and mirror the rest; a plain BF16 tier forms full
+    // products throughout and X's symmetric part is taken at the end.
     const bool full = (o.flags & DBCSR_SIGN_FULL_PRODUCTS) != 0;
+    const int low = (o.flags & DBCSR_SIGN_PLAIN_BF16) ? DBCSR_BF16 : DBCSR_BF16X3;
+    const bool full_mixed = o.prec == DBCSR_MIXED && low == DBCSR_BF16;
 
     const auto t0 = std::chrono::steady_clock::now();
     cudaStream_t st = H[0]->stream;
@@ -246,24 +245,32 @@ dbcsr_status sign_iterate_batched(int32_t nsys, dbcsr_matrix_* const* H, const d
         rep[s] = dbcsr_sign_report{};
         rep[s].alpha = alpha[s];
     }
-    int tier = (o.prec == DBCSR_MIXED) ? DBCSR_BF16 : DBCSR_FP64;
+    int tier = (o.prec == DBCSR_MIXED) ? low : DBCSR_FP64;
     int first_fp64 = (tier == DBCSR_FP64) ? 1 : 0;
-    auto sym_mode = [&](int tier_now, int step) {
-        (void)tier_now;
-        (void)step;
-        return (full || o.prec == DBCSR_MIXED) ? kSymNone : kSymMirror;
+    const int sym = (full || full_mixed) ? kSymNone : kSymMirror;
+    double flops = 0.0, ms_mult = 0.0, ms_sym = 0.0, ms_filt = 0.0, ms_low = 0.0, flops_low = 0.0, bytes_min = 0.0;
+    int64_t nprod = 0, launches_fp64 = 0;
+    auto account = [&](const dbcsr_mult_stats& ms, int tier_of_product) {
+        flops += ms.flops;
+        nprod += ms.n_products;
+        ms_mult += ms.ms_numeric;
+        ms_sym += ms.ms_symbolic;
+        ms_filt += ms.ms_filter;
+        if (tier_of_product != DBCSR_FP64) {
+            ms_low += ms.ms_numeric;
+            flops_low += ms.flops;
+        } else {
+            bytes_min += ms.bytes_min;
+            launches_fp64 += ms.n_launches;
+        }
     };
-    double flops = 0.0, ms_mult = 0.0;
-    int64_t nprod = 0;
     std::vector<double> dev2(nsys);
     DBuf<double> blk_dev2;
     int it = 0;
     while (it < o.max_iter) {
         dbcsr_mult_stats ms{};
-        multiply(1.0, X.get(), X.get(), 0.0, X2.get(), o.eps_filter, tier, &ms, false, sym_mode(tier, it + 1));
-        flops += ms.flops;
-        nprod += ms.n_products;
-        ms_mult += ms.ms_numeric;
+        multiply(1.0, X.get(), X.get(), 0.0, X2.get(), o.eps_filter, tier, &ms, false, sym);
+        account(ms, tier);
         ++it;
         // per-system ||X2_s - 1||_F^2 over the kept blocks of the system's rows
         blk_dev2.alloc(std::max<int64_t>(X2->nnzb, 1), st);
@@ -297,17 +304,15 @@ dbcsr_status sign_iterate_batched(int32_t nsys, dbcsr_matrix_* const* H, const d
         }
         if (o.verbose)
             std::fprintf(stderr, "[batch] it %3d %s systems done %d/%d formed %lld %.1f GF %.2f ms\n", it,
-                         tier == DBCSR_BF16 ? "bf16" : "fp64", (int)std::count_if(done.begin(), done.end(), [](int d) { return d != 0; }),
+                         tier == DBCSR_FP64 ? "fp64" : tier == DBCSR_BF16 ? "bf16" : "bf16x3", (int)std::count_if(done.begin(), done.end(), [](int d) { return d != 0; }),
                          nsys, (long long)ms.n_formed, ms.flops * 1e-9, ms.ms_numeric);
         if (all_done) break;
-        if (tier == DBCSR_BF16 && any_below_switch) {
+        if (tier != DBCSR_FP64 && any_below_switch) {
             tier = DBCSR_FP64;
             first_fp64 = it + 1;
         }
-        multiply(-0.5, X.get(), X2.get(), 1.5, X.get(), o.eps_filter, tier, &ms, false, sym_mode(tier, it));
-        flops += ms.flops;
-        nprod += ms.n_products;
-        ms_mult += ms.ms_numeric;
+        multiply(-0.5, X.get(), X2.get(), 1.5, X.get(), o.eps_filter, tier, &ms, false, sym);
+        account(ms, tier);
     }
     for (int32_t s = 0; s < nsys; ++s)
         if (!done[s]) done[s] = 3;
@@ -366,6 +371,12 @@ dbcsr_status sign_iterate_batched(int32_t nsys, dbcsr_matrix_* const* H, const d
         rep[s].n_products = nprod;
         rep[s].ms_total = ms_total;
         rep[s].ms_multiply = ms_mult;
+        rep[s].ms_symbolic = ms_sym;
+        rep[s].ms_filter = ms_filt;
+        rep[s].ms_low = ms_low;
+        rep[s].flops_low = flops_low;
+        rep[s].bytes_min_fp64 = bytes_min;
+        rep[s].launches_fp64 = launches_fp64;
         all_conv = all_conv && rep[s].converged;
         if (reps) reps[s] = rep[s];
     }

@@ -236,8 +236,8 @@ void mlp_features(int prec, int m, int n, int k, const TuneCfg& c, float* f) {
     f[1] = n / 32.f;
     f[2] = k / 32.f;
     f[3] = (float)(std::log2((double)mn * k) / 15.0);
-    f[4] = (float)(prec == DBCSR_BF16 ? mn / tiles : mn / lanes);          // useful fraction of the lanes / tiles
-    f[5] = (prec != DBCSR_BF16 && mn > 32 && (mn & 31) == 1) ? 1.f : 0.f;  // K-split remainder kernel
+    f[4] = (float)(is_bf16(prec) ? mn / tiles : mn / lanes);          // useful fraction of the lanes / tiles
+    f[5] = (!is_bf16(prec) && mn > 32 && (mn & 31) == 1) ? 1.f : 0.f;  // K-split remainder kernel
     f[6] = c.tpb / 256.f;
     f[7] = (float)(std::log2((double)c.ctas_per_sm) / 6.0);
     f[8] = (float)c.colmajor;

@@ -699,9 +699,13 @@ struct SmmBf16Args {
     int64_t a_stride;
     const __nv_bfloat16* b16;   // B-role packed (transposed) blocks, block b at b16 + b * b_stride
     int64_t b_stride;
+    const __nv_bfloat16* a16_lo;   // SPLIT: packed residuals, same layout
+    const __nv_bfloat16* b16_lo;
 };
 
-template <int MT, int NT>
+// SPLIT (DBCSR_BF16X3): operands x = hi + lo, both BF16; per fragment set three MMAs
+// accumulate hi*hi + hi*lo + lo*hi in FP32 (the lo*lo term, ~2^-16 relative, is left out).
+template <int MT, int NT, bool SPLIT>
 __global__ void __launch_bounds__(256) k_smm_bf16(int64_t nlist, const int64_t* __restrict__ list, SmmBf16Args G) {
     const SmmArgs& S = G.base;
     const int lane = threadIdx.x & 31, gid = lane >> 2, tig = lane & 3;
@@ -735,14 +739,20 @@ __global__ void __launch_bounds__(256) k_smm_bf16(int64_t nlist, const int64_t* 
                 const int KT = (kk + 15) >> 4, ld = 16 * KT;     // padded inner size = row length of both tiles
                 const uint32_t* __restrict__ Ap = reinterpret_cast<const uint32_t*>(G.a16 + aoq);
                 const uint32_t* __restrict__ Bp = reinterpret_cast<const uint32_t*>(G.b16 + boq);
+                const uint32_t* __restrict__ Apl = SPLIT ? reinterpret_cast<const uint32_t*>(G.a16_lo + aoq) : nullptr;
+                const uint32_t* __restrict__ Bpl = SPLIT ? reinterpret_cast<const uint32_t*>(G.b16_lo + boq) : nullptr;
                 for (int kt = 0; kt < KT; ++kt) {
                     const int c0 = (kt * 16 + tig * 2) >> 1;      // 32-bit word of columns (c, c+1)
-                    uint32_t bf[NT][2];
+                    uint32_t bf[NT][2], bl[NT][2];
 #pragma unroll
                     for (int nt = 0; nt < NT; ++nt) {
                         const int row = (nt * 8 + gid) * (ld >> 1);
                         bf[nt][0] = __ldg(Bp + row + c0);
                         bf[nt][1] = __ldg(Bp + row + c0 + 4);
+                        if (SPLIT) {
+                            bl[nt][0] = __ldg(Bpl + row + c0);
+                            bl[nt][1] = __ldg(Bpl + row + c0 + 4);
+                        }
                     }
 #pragma unroll
                     for (int mt = 0; mt < MT; ++mt) {
@@ -751,6 +761,15 @@ __global__ void __launch_bounds__(256) k_smm_bf16(int64_t nlist, const int64_t* 
                         const uint32_t a2 = __ldg(Ap + r0 + c0 + 4), a3 = __ldg(Ap + r1 + c0 + 4);
 #pragma unroll
                         for (int nt = 0; nt < NT; ++nt) mma_bf16(acc[mt][nt], a0, a1, a2, a3, bf[nt][0], bf[nt][1]);
+                        if (SPLIT) {
+                            const uint32_t l0 = __ldg(Apl + r0 + c0), l1 = __ldg(Apl + r1 + c0);
+                            const uint32_t l2 = __ldg(Apl + r0 + c0 + 4), l3 = __ldg(Apl + r1 + c0 + 4);
+#pragma unroll
+                            for (int nt = 0; nt < NT; ++nt) {
+                                mma_bf16(acc[mt][nt], a0, a1, a2, a3, bl[nt][0], bl[nt][1]);
+                                mma_bf16(acc[mt][nt], l0, l1, l2, l3, bf[nt][0], bf[nt][1]);
+                            }
+                        }
                     }
                 }
             }
@@ -791,19 +810,21 @@ __global__ void __launch_bounds__(256) k_smm_bf16(int64_t nlist, const int64_t* 
 using SmmBf16Kernel = void (*)(int64_t, const int64_t*, SmmBf16Args);
 
 // Kernel of a BF16 class (MT, NT) = ((cls - 1) / 4 + 1, (cls - 1) % 4 + 1).
-SmmBf16Kernel bf16_kernel(int cls) {
+template <bool SPLIT>
+SmmBf16Kernel bf16_kernel_t(int cls) {
     switch (cls) {
-        case 1: return &k_smm_bf16<1, 1>;
-        case 2: return &k_smm_bf16<1, 2>;
-        case 3: return &k_smm_bf16<1, 3>;
-        case 4: return &k_smm_bf16<1, 4>;
-        case 5: return &k_smm_bf16<2, 1>;
-        case 6: return &k_smm_bf16<2, 2>;
-        case 7: return &k_smm_bf16<2, 3>;
-        case 8: return &k_smm_bf16<2, 4>;
+        case 1: return &k_smm_bf16<1, 1, SPLIT>;
+        case 2: return &k_smm_bf16<1, 2, SPLIT>;
+        case 3: return &k_smm_bf16<1, 3, SPLIT>;
+        case 4: return &k_smm_bf16<1, 4, SPLIT>;
+        case 5: return &k_smm_bf16<2, 1, SPLIT>;
+        case 6: return &k_smm_bf16<2, 2, SPLIT>;
+        case 7: return &k_smm_bf16<2, 3, SPLIT>;
+        case 8: return &k_smm_bf16<2, 4, SPLIT>;
         default: return nullptr;
     }
 }
+SmmBf16Kernel bf16_kernel(int cls, bool split) { return split ? bf16_kernel_t<true>(cls) : bf16_kernel_t<false>(cls); }
 
 // FP64 -> BF16, one rounding to nearest (ties to even) of the 52-bit significand to
 // 7 stored bits, from the IEEE-754 encodings.  Values below the binary32 normal
@@ -838,7 +859,8 @@ __device__ __forceinline__ __nv_bfloat16 f64_to_bf16_rne(double x) {
 // (16 ceil(k/16)) tile.  Padding is zero.
 __global__ void k_pack_bf16(int64_t nb, int role, const int32_t* __restrict__ row, const int32_t* __restrict__ col,
                             const int32_t* __restrict__ bs, const int64_t* __restrict__ off,
-                            const double* __restrict__ data, int64_t stride, __nv_bfloat16* __restrict__ out) {
+                            const double* __restrict__ data, int64_t stride, __nv_bfloat16* __restrict__ out,
+                            __nv_bfloat16* __restrict__ out_lo) {
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t b = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); b < nb; b += warps) {
@@ -849,13 +871,19 @@ __global__ void k_pack_bf16(int64_t nb, int role, const int32_t* __restrict__ ro
             const int R = 16 * ((r_sz + 15) / 16), L = 16 * ((c_sz + 15) / 16);
             for (int e = lane; e < R * L; e += 32) {
                 const int i = e / L, t = e - i * L;
-                o[e] = f64_to_bf16_rne((i < r_sz && t < c_sz) ? x[i * c_sz + t] : 0.0);
+                const double v = (i < r_sz && t < c_sz) ? x[i * c_sz + t] : 0.0;
+                const __nv_bfloat16 hi = f64_to_bf16_rne(v);
+                o[e] = hi;
+                if (out_lo) out_lo[b * stride + e] = f64_to_bf16_rne(v - (double)__bfloat162float(hi));
             }
         } else {                                                 // B: k = r_sz rows, n = c_sz columns, stored n x k
             const int R = 8 * ((c_sz + 7) / 8), L = 16 * ((r_sz + 15) / 16);
             for (int e = lane; e < R * L; e += 32) {
                 const int j = e / L, t = e - j * L;
-                o[e] = f64_to_bf16_rne((j < c_sz && t < r_sz) ? x[t * c_sz + j] : 0.0);
+                const double v = (j < c_sz && t < r_sz) ? x[t * c_sz + j] : 0.0;
+                const __nv_bfloat16 hi = f64_to_bf16_rne(v);
+                o[e] = hi;
+                if (out_lo) out_lo[b * stride + e] = f64_to_bf16_rne(v - (double)__bfloat162float(hi));
             }
         }
     }
@@ -918,10 +946,12 @@ void launch_smm_shape(int prec, int m, int n, int64_t cnt, const int64_t* list, 
         fail(DBCSR_EINVAL, "launch configuration out of range");
     const int wpc = cfg.tpb / 32;
     const int64_t grid = std::min<int64_t>(ceil_div(cnt, wpc), (int64_t)152 * cfg.ctas_per_sm);
-    if (prec == DBCSR_BF16) {
-        SmmBf16Kernel kern = bf16_kernel(((m + 15) / 16 - 1) * 4 + (n + 7) / 8);
+    if (is_bf16(prec)) {
+        const bool split = prec == DBCSR_BF16X3;
+        if (split && (!pk.a16_lo || !pk.b16_lo)) fail(DBCSR_EINVAL, "multiply: split BF16 needs the residual packs");
+        SmmBf16Kernel kern = bf16_kernel(((m + 15) / 16 - 1) * 4 + (n + 7) / 8, split);
         if (!kern) fail(DBCSR_ECAPACITY, "multiply: block shape beyond the BF16 kernel table");
-        SmmBf16Args ga{sa, pk.a16, pk.a_stride, pk.b16, pk.b_stride};
+        SmmBf16Args ga{sa, pk.a16, pk.a_stride, pk.b16, pk.b_stride, pk.a16_lo, pk.b16_lo};
         kern<<<(unsigned)grid, cfg.tpb, 0, s>>>(cnt, list, ga);
     } else {
         const int mn = m * n;
@@ -964,10 +994,16 @@ void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbc
     check_finalized(B);
     if (!C) fail(DBCSR_EINVAL, "multiply: null C");
     if (A->h_bs != B->h_bs || A->h_bs != C->h_bs) fail(DBCSR_EINVAL, "multiply: block sizes of A, B and C differ");
-    if (prec != DBCSR_FP64 && prec != DBCSR_BF16) fail(DBCSR_EINVAL, "multiply: prec must be DBCSR_FP64 or DBCSR_BF16");
+    if (prec != DBCSR_FP64 && !is_bf16(prec))
+        fail(DBCSR_EINVAL, "multiply: prec must be DBCSR_FP64, DBCSR_BF16 or DBCSR_BF16X3");
     if (!(eps >= 0.0)) fail(DBCSR_EINVAL, "multiply: eps_filter must be >= 0");
     const bool use_c = (beta != 0.0);
     if (use_c) check_finalized(C);
+    // compulsory operand traffic of the block-product launches: A and B read once, the computed
+    // C blocks written once, a C input that is neither A nor B read once
+    double bytes_min = 8.0 * ((double)A->nel + (B != A ? (double)B->nel : 0.0) +
+                              (use_c && C != A && C != B ? (double)C->nel : 0.0));
+    int32_t n_smm_launches = 0;
     const int32_t nblk = A->nblk;
     if (nblk > kMaxBlockRows) fail(DBCSR_ECAPACITY, "multiply: more than 262144 block rows");
     cudaStream_t s = C->stream;
@@ -1115,7 +1151,7 @@ void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbc
                    B->off.p, B->data.p, use_c ? C->off.p : nullptr, use_c ? C->data.p : nullptr, A->bs.p,
                    alpha, beta, c_data.p, c_norm.p, c_dev2.p};
         // one launch per (m, n) block shape over that shape's blocks (kept in CSR order)
-        const bool bf16 = (prec == DBCSR_BF16);
+        const bool bf16 = is_bf16(prec);
         DBuf<int32_t> flag;
         DBuf<int64_t> pos, list;
         flag.alloc(nform, s);
@@ -1135,29 +1171,38 @@ void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbc
                 k_class_scatter<<<grid_for(nform, 256), 256, 0, s>>>(nform, flag.p, pos.p, list.p + at);
                 DBG_LAUNCH_CK();
                 launches.push_back({m, n, cnt});
+                bytes_min += 8.0 * (double)cnt * m * n;
                 at += cnt;
             }
-        DBuf<__nv_bfloat16> a16, b16;
+        DBuf<__nv_bfloat16> a16, b16, a16_lo, b16_lo;
         Bf16Packs pk{};
         if (bf16) {
             // operands rounded to BF16 (nearest even) once per product, into fragment-ready copies
+            // (and, for split products, the rounded residuals x - hi)
+            const bool split = prec == DBCSR_BF16X3;
             const int maxbs = *std::max_element(A->h_bs.begin(), A->h_bs.end());
             pk.a_stride = pack_stride(0, maxbs);
             pk.b_stride = pack_stride(1, maxbs);
             a16.alloc(std::max<int64_t>(A->nnzb, 1) * pk.a_stride, s);
             b16.alloc(std::max<int64_t>(B->nnzb, 1) * pk.b_stride, s);
+            if (split) {
+                a16_lo.alloc(std::max<int64_t>(A->nnzb, 1) * pk.a_stride, s);
+                b16_lo.alloc(std::max<int64_t>(B->nnzb, 1) * pk.b_stride, s);
+            }
             if (A->nnzb) {
                 k_pack_bf16<<<grid_for(A->nnzb, 8), 256, 0, s>>>(A->nnzb, 0, A->row.p, A->col.p, A->bs.p, A->off.p,
-                                                                 A->data.p, pk.a_stride, a16.p);
+                                                                 A->data.p, pk.a_stride, a16.p, a16_lo.p);
                 DBG_LAUNCH_CK();
             }
             if (B->nnzb) {
                 k_pack_bf16<<<grid_for(B->nnzb, 8), 256, 0, s>>>(B->nnzb, 1, B->row.p, B->col.p, B->bs.p, B->off.p,
-                                                                 B->data.p, pk.b_stride, b16.p);
+                                                                 B->data.p, pk.b_stride, b16.p, b16_lo.p);
                 DBG_LAUNCH_CK();
             }
             pk.a16 = a16.p;
             pk.b16 = b16.p;
+            pk.a16_lo = a16_lo.p;
+            pk.b16_lo = b16_lo.p;
         }
         // the inner size the tuned configurations are looked up with: the largest block edge
         const int kmax = *std::max_element(A->h_bs.begin(), A->h_bs.end());
@@ -1167,6 +1212,7 @@ void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbc
             launch_smm_shape(prec, L.m, L.n, L.cnt, list.p + at, sa, pk, tune_lookup(prec, L.m, L.n, kmax), s);
             at += L.cnt;
         }
+        n_smm_launches = (int32_t)launches.size();
         if (sym_result) {
             DBG_CK(cudaEventRecord(ev.e[2], s));     // the copy / averaging is timed with the filter
             k_mirror_copy<<<grid_for(nform, 8), 256, 0, s>>>(nform, sym_result, mirror.p, f_row.p, f_col.p, f_off.p,
@@ -1220,6 +1266,8 @@ void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbc
         stats->ms_symbolic = ev.ms(0, 1);
         stats->ms_numeric = ev.ms(1, 2);
         stats->ms_filter = ev.ms(2, 3);
+        stats->bytes_min = n_smm_launches ? bytes_min : 0.0;
+        stats->n_launches = n_smm_launches;
     }
 }
 

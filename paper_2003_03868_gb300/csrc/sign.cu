@@ -47,15 +47,14 @@ dbcsr_status sign_iterate(dbcsr_matrix_* H, double mu, const dbcsr_sign_opts* op
     if (!(o.eps_filter >= 0) || !(o.tol > 0)) fail(DBCSR_EINVAL, "sign_iterate: need eps_filter >= 0 and tol > 0");
     if (o.prec != DBCSR_FP64 && o.prec != DBCSR_MIXED) fail(DBCSR_EINVAL, "sign_iterate: prec must be FP64 or MIXED");
     if (o.prec == DBCSR_MIXED && !(o.switch_tol > 0)) o.switch_tol = 1e-4;
-    // symmetric products (upper blocks computed, lower mirrored) in the FP64 tier; in the
-    // BF16 tier only on request (X2 there commutes with X only to BF16 accuracy)
-    // Every product of the iteration is symmetric in exact arithmetic.  FP64 products
-    // compute the blocks I <= J and mirror the rest.  BF16 products keep both
-    // triangles as computed (a BF16 X2 commutes with X only to BF16 accuracy, so X
-    // leaves the BF16 tier slightly asymmetric); the two products of the first FP64
-    // step keep the symmetric mean of both triangles, which makes X exactly
-    // symmetric again before the mirrored products take over.
+    // Every product of the iteration is symmetric in exact arithmetic.  FP64 and split-BF16
+    // products compute the blocks I <= J and mirror the rest.  Plain BF16 products keep both
+    // triangles as computed: a BF16 X2 commutes with X only to about 1e-3, so mirrored BF16
+    // products would steer X towards a different matrix; a mixed run with a plain BF16 tier
+    // therefore forms full products throughout and takes X's symmetric part at the end.
     const bool full = (o.flags & DBCSR_SIGN_FULL_PRODUCTS) != 0;
+    const int low = (o.flags & DBCSR_SIGN_PLAIN_BF16) ? DBCSR_BF16 : DBCSR_BF16X3;
+    const bool full_mixed = o.prec == DBCSR_MIXED && low == DBCSR_BF16;
 
     const auto t0 = std::chrono::steady_clock::now();
     cudaStream_t s = H->stream;
@@ -74,33 +73,41 @@ dbcsr_status sign_iterate(dbcsr_matrix_* H, double mu, const dbcsr_sign_opts* op
     bool converged = false, stalled = false;
     double res = 0.0;
     // precision ladder: BF16 operands / FP32 accumulation while r >= switch_tol, then FP64
-    int tier = (o.prec == DBCSR_MIXED) ? DBCSR_BF16 : DBCSR_FP64;
+    int tier = (o.prec == DBCSR_MIXED) ? low : DBCSR_FP64;
     int first_fp64 = (tier == DBCSR_FP64) ? 1 : 0;
-    auto sym_mode = [&](int tier_now, int step) {
-        (void)tier_now;
-        (void)step;
-        return (full || o.prec == DBCSR_MIXED) ? kSymNone : kSymMirror;
-    };
-    while (it < o.max_iter) {
-        dbcsr_mult_stats st{};
-        multiply(1.0, X.get(), X.get(), 0.0, X2.get(), o.eps_filter, tier, &st, true, sym_mode(tier, it + 1));
-        res = std::sqrt(st.dev2_filtered) / N;
+    const int sym = (full || full_mixed) ? kSymNone : kSymMirror;
+    auto account = [&](const dbcsr_mult_stats& st, int tier_of_product) {
         r.flops += st.flops;
         r.n_products += st.n_products;
         r.ms_multiply += st.ms_numeric;
+        r.ms_symbolic += st.ms_symbolic;
+        r.ms_filter += st.ms_filter;
+        if (tier_of_product != DBCSR_FP64) {
+            r.ms_low += st.ms_numeric;
+            r.flops_low += st.flops;
+        } else {
+            r.bytes_min_fp64 += st.bytes_min;
+            r.launches_fp64 += st.n_launches;
+        }
+    };
+    while (it < o.max_iter) {
+        dbcsr_mult_stats st{};
+        multiply(1.0, X.get(), X.get(), 0.0, X2.get(), o.eps_filter, tier, &st, true, sym);
+        res = std::sqrt(st.dev2_filtered) / N;
+        account(st, tier);
         if (it < DBCSR_MAX_HISTORY) r.residual_history[it] = res;
         ++it;
         if (!std::isfinite(res)) fail(DBCSR_ENAN, "sign_iterate: residual is not finite");
         if (o.verbose)
             std::fprintf(stderr, "[sign] it %3d %s r %.3e nnzb(X) %lld cand %lld formed %lld kept %lld %.1f GF %.2f ms\n",
-                         it, tier == DBCSR_BF16 ? "bf16" : "fp64", res, (long long)X->nnzb,
+                         it, tier == DBCSR_FP64 ? "fp64" : tier == DBCSR_BF16 ? "bf16" : "bf16x3", res, (long long)X->nnzb,
                          (long long)st.n_candidates, (long long)st.n_formed, (long long)st.n_kept, st.flops * 1e-9,
                          st.ms_numeric);
         // without filtering r_k / r_{k-1} only falls: a fast step followed by a slow one is a stall
         const bool slow = it >= 3 && it - 1 < DBCSR_MAX_HISTORY &&
                           r.residual_history[it - 2] < o.stall_ratio * r.residual_history[it - 3] &&
                           res > o.stall_ratio * r.residual_history[it - 2];
-        if (tier == DBCSR_BF16) {
+        if (tier != DBCSR_FP64) {
             // the low-precision tier ends at the switch residual (or when it stops making progress);
             // convergence is only ever declared on an FP64 product
             if (res < o.switch_tol || res < o.tol || slow) {
@@ -119,14 +126,13 @@ dbcsr_status sign_iterate(dbcsr_matrix_* H, double mu, const dbcsr_sign_opts* op
                 break;
             }
         }
-        multiply(-0.5, X.get(), X2.get(), 1.5, X.get(), o.eps_filter, tier, &st, false, sym_mode(tier, it));
-        r.flops += st.flops;
-        r.n_products += st.n_products;
-        r.ms_multiply += st.ms_numeric;
+        multiply(-0.5, X.get(), X2.get(), 1.5, X.get(), o.eps_filter, tier, &st, false, sym);
+        account(st, tier);
         if (it - 1 < DBCSR_MAX_HISTORY) r.nnzb_history[it - 1] = X->nnzb;
     }
-    // a mixed run forms both triangles of every product; its X is symmetric only to
-    // BF16 accuracy, so it is replaced by its symmetric part before P is formed
+    // X of a mixed run is symmetric only to the low tier's accuracy (both triangles formed with
+    // plain BF16; diagonal blocks summed in FP32 with split BF16), so it is replaced by its
+    // symmetric part before P is formed
     if (o.prec == DBCSR_MIXED && !full) symmetrize(X.get());
     copy_matrix(P, X.get());
     scale_shift(P, -0.5, 0.5);

@@ -52,7 +52,10 @@ struct Bf16Packs {
     int64_t a_stride = 0;
     const __nv_bfloat16* b16 = nullptr;
     int64_t b_stride = 0;
+    const __nv_bfloat16* a16_lo = nullptr;   // DBCSR_BF16X3: the residuals lo = bf16(x - hi)
+    const __nv_bfloat16* b16_lo = nullptr;
 };
+inline bool is_bf16(int prec) { return prec == DBCSR_BF16 || prec == DBCSR_BF16X3; }
 int64_t pack_stride(int role, int maxbs);
 
 // Launches the kernel of shape (m, n) over the cnt blocks listed in list.

@@ -138,6 +138,8 @@ struct SynthStack {
             DBG_LAUNCH_CK();
             pk.a16 = a16.p;
             pk.b16 = b16.p;
+            pk.a16_lo = a16.p;      // timing only: the residual packs may alias the leading ones
+            pk.b16_lo = b16.p;
         }
         args = SmmArgs{f_row.p, f_col.p, f_off.p, f_pbeg.p, f_cin.p, prod_a.p, prod_b.p, a_col.p, a_off.p, a.p,
                        b_off.p, b.p, nullptr, nullptr, bs.p, 1.0, 0.0, c.p, norm.p, dev2.p, 0, 0};
@@ -167,7 +169,7 @@ struct SynthStack {
 };
 
 void check_triple(int prec, int m, int n, int k) {
-    if (prec != DBCSR_FP64 && prec != DBCSR_BF16) fail(DBCSR_EINVAL, "tune: prec must be DBCSR_FP64 or DBCSR_BF16");
+    if (prec != DBCSR_FP64 && !is_bf16(prec)) fail(DBCSR_EINVAL, "tune: prec must be DBCSR_FP64, DBCSR_BF16 or DBCSR_BF16X3");
     if (m < 1 || n < 1 || k < 1 || m > kMaxBlock || n > kMaxBlock || k > kMaxBlock)
         fail(DBCSR_EINVAL, "tune: m, n, k must lie in [1, 32]");
 }
@@ -176,7 +178,7 @@ void check_triple(int prec, int m, int n, int k) {
 
 std::vector<TuneCfg> tune_space(int prec) {
     std::vector<TuneCfg> v;
-    if (prec == DBCSR_BF16) {
+    if (is_bf16(prec)) {
         for (int tpb : {64, 128, 256})
             for (int c : {4, 8, 16, 32, 64}) {
                 TuneCfg t;
@@ -240,7 +242,7 @@ extern "C" {
 
 dbcsr_status dbcsr_tune_space(int32_t prec, dbcsr_kernel_cfg* out, int32_t cap, int32_t* n) {
     return guard([&] {
-        if (prec != DBCSR_FP64 && prec != DBCSR_BF16) dbg::fail(DBCSR_EINVAL, "tune_space: prec must be FP64 or BF16");
+        if (prec != DBCSR_FP64 && !dbg::is_bf16(prec)) dbg::fail(DBCSR_EINVAL, "tune_space: prec must be FP64, BF16 or BF16X3");
         auto v = dbg::tune_space(prec);
         if (n) *n = (int32_t)v.size();
         if (out)
@@ -254,7 +256,7 @@ dbcsr_status dbcsr_time_config(int32_t prec, int32_t m, int32_t n, int32_t k, in
         dbg::check_triple(prec, m, n, k);
         if (stack_len < 1 || reps < 1 || ncfg < 1 || !cfgs || !ms_out) dbg::fail(DBCSR_EINVAL, "time_config: bad argument");
         cudaStream_t s = nullptr;
-        dbg::SynthStack st(m, n, k, stack_len, prec == DBCSR_BF16, s);
+        dbg::SynthStack st(m, n, k, stack_len, dbg::is_bf16(prec), s);
         for (int32_t i = 0; i < ncfg; ++i) ms_out[i] = st.time(prec, from_c(cfgs[i]), reps, s);
     });
 }
@@ -269,7 +271,7 @@ dbcsr_status dbcsr_autotune(const int32_t* mnk, int32_t ntriples, int32_t prec, 
         for (int32_t t = 0; t < ntriples; ++t) {
             const int m = mnk[3 * t], n = mnk[3 * t + 1], k = mnk[3 * t + 2];
             dbg::check_triple(prec, m, n, k);
-            dbg::SynthStack st(m, n, k, stack_len, prec == DBCSR_BF16, s);
+            dbg::SynthStack st(m, n, k, stack_len, dbg::is_bf16(prec), s);
             double best = 1e300;
             dbg::TuneCfg best_cfg = dbg::default_cfg(prec);
             for (const auto& c : space) {

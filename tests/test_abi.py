@@ -45,7 +45,44 @@ def test_version_and_error_string_without_gpu(libpath):
 
 def test_struct_layouts_match_header():
     from paper_2003_03868_gb300 import _ffi
-    assert ctypes.sizeof(_ffi.MultStats) == 9 * 8
+    assert ctypes.sizeof(_ffi.MultStats) == 11 * 8
     assert ctypes.sizeof(_ffi.SignOpts) == 8 + 8 + 4 + 4 + 8 + 8 + 4 + 4
     # 4 int32, 5 double, int64, 2 double, int64, then the histories
     assert _ffi.SignReport.residual_history.offset == 16 + 40 + 8 + 16 + 8
+    assert _ffi.SignReport.ms_symbolic.offset == _ffi.SignReport.nnzb_history.offset + 8 * _ffi.MAX_HISTORY
+
+
+def test_struct_layouts_match_the_c_compiler(tmp_path):
+    """sizeof / offsetof of every ABI struct, from gcc reading the header, equal the ctypes mirrors."""
+    import shutil
+    import subprocess
+    from paper_2003_03868_gb300 import _ffi
+    if not shutil.which("gcc"):
+        pytest.skip("no gcc")
+    probes = {
+        "dbcsr_mult_stats": (_ffi.MultStats, ["flops", "dev2_filtered", "ms_filter", "bytes_min", "n_launches"]),
+        "dbcsr_sign_opts": (_ffi.SignOpts, ["switch_tol", "verbose", "flags"]),
+        "dbcsr_sign_report": (_ffi.SignReport, ["alpha", "n_products", "residual_history", "nnzb_history",
+                                               "ms_symbolic", "ms_low", "flops_low", "bytes_min_fp64",
+                                               "launches_fp64"]),
+        "dbcsr_kernel_cfg": (_ffi.KernelCfg, ["prefetch2"]),
+        "dbcsr_tune_record": (_ffi.TuneRecord, ["cfg", "ms", "gflops"]),
+        "dbcsr_mlp_opts": (_ffi.MlpOpts, ["lr", "eps"]),
+        "dbcsr_mlp_report": (_ffi.MlpReport, [f[0] for f in _ffi.MlpReport._fields_]),
+    }
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "dbcsr_gb.h"', "int main(void) {"]
+    for t, (_, fields) in probes.items():
+        lines.append(f'  printf("{t} %zu\\n", sizeof({t}));')
+        for f in fields:
+            lines.append(f'  printf("{t}.{f} %zu\\n", offsetof({t}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.run(["gcc", "-std=c11", "-I", inc, str(src), "-o", str(exe)], check=True)
+    got = dict(l.split() for l in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines())
+    for t, (cls, fields) in probes.items():
+        assert int(got[t]) == ctypes.sizeof(cls), t
+        for f in fields:
+            assert int(got[f"{t}.{f}"]) == getattr(cls, f).offset, f"{t}.{f}"

@@ -3,6 +3,8 @@
 BF16 product: the oracle multiplies the operands rounded to bfloat16 (nearest,
 ties to even) in FP64; the GPU accumulates the same exact bf16 x bf16 products
 in FP32, so the difference is bounded by FP32 summation: |d_ij| <= K_ij u32 (|A||B|)_ij.
+Split BF16 product (BF16X3): the oracle forms Ah Bh + Ah Bl + Al Bh in FP64 from
+hi = bf16(x), lo = bf16(x - hi); the GPU accumulates the same exact products in FP32.
 Mixed sign iteration: the converged P must give the FP64 oracle's band energy
 within 1e-6 Ha/atom."""
 import json
@@ -13,7 +15,7 @@ import pytest
 
 import synth
 from oracle import bsr, sign
-from oracle.lowprec import round_bf16
+from oracle.lowprec import round_bf16, split_bf16
 
 pytestmark = pytest.mark.gpu
 
@@ -68,6 +70,61 @@ def test_bf16_product_matches_rounded_oracle(gb, si, density):
     assert st.flops == bsr.multiply(1.0, Ao, Bo, info=True)[1].flops
 
 
+def _split_reference(Ao, Bo):
+    parts = []
+    for M in (Ao, Bo):
+        h, l = M.copy(), M.copy()
+        h.data, l.data = split_bf16(M.data)
+        parts.append((h, l))
+    (Ah, Al), (Bh, Bl) = parts
+    ref = bsr.multiply(1.0, Ah, Bh)
+    for X, Y in ((Ah, Bl), (Al, Bh)):
+        t = bsr.multiply(1.0, X, Y)
+        assert np.array_equal(t.col, ref.col)
+        ref.data = ref.data + t.data
+    Aa, Ba = Ao.copy(), Bo.copy()
+    Aa.data = np.abs(Aa.data)
+    Ba.data = np.abs(Ba.data)
+    return ref, bsr.multiply(1.0, Aa, Ba)
+
+
+@pytest.mark.parametrize("si", range(len(SIZES)))
+@pytest.mark.parametrize("density", [0.1, 0.6])
+def test_bf16x3_product_matches_split_oracle(gb, si, density):
+    bs = SIZES[si]
+    a = synth.random_block_matrix(bs, density, 700 + si)
+    b = synth.random_block_matrix(bs, density, 800 + si)
+    A, B = gb.Matrix.of(a), gb.Matrix.of(b)
+    Ao, Bo = bsr.Mat.of(a), bsr.Mat.of(b)
+    C = gb.Matrix(A.blk_size, A.stream)
+    st = gb.multiply(1.0, A, B, 0.0, C, 0.0, prec=gb.DBCSR_BF16X3)
+    ref, mag = _split_reference(Ao, Bo)
+    rp, col, data = C.export()
+    assert np.array_equal(rp, ref.rp) and np.array_equal(col, ref.col)
+    # three FP32 sums of exact products, each term at most (1 + 2^-8)^2 |a||b|
+    kmax = int(np.max(bs)) * len(bs)
+    assert np.all(np.abs(data - ref.data) <= 2 * kmax * U32 * 1.1 * mag.data + 1e-300)
+    # about 16 significant bits: far closer to the FP64 product than plain BF16
+    exact = bsr.multiply(1.0, Ao, Bo)
+    assert np.all(np.abs(data - exact.data) <= (3 * 2.0 ** -16 + 2 * kmax * U32) * mag.data + 1e-300)
+    assert st.flops == bsr.multiply(1.0, Ao, Bo, info=True)[1].flops
+
+
+def test_bf16x3_filtered_product_keeps_the_split_oracle_pattern(gb):
+    # norms far from eps: the filtered patterns agree
+    bs = SIZES[1]
+    a = synth.random_block_matrix(bs, 0.5, 901, symmetric=True)
+    A, Ao = gb.Matrix.of(a), bsr.Mat.of(a)
+    C = gb.Matrix(A.blk_size, A.stream)
+    gb.multiply(1.0, A, A, 0.0, C, 1e-3, prec=gb.DBCSR_BF16X3)
+    ref, _ = _split_reference(Ao, Ao)
+    keep = bsr.keep_mask(ref, bsr.block_norms(ref)[0], 1e-3)
+    rp, col, data = C.export()
+    sel = bsr.select_blocks(ref, keep)
+    assert np.array_equal(col, sel.col)
+    assert np.allclose(data, sel.data, rtol=0, atol=1e-5 * np.abs(sel.data).max())
+
+
 def test_bf16_alpha_beta_and_aliasing(gb):
     bs = SIZES[0]
     x = synth.random_block_matrix(bs, 0.4, 501, symmetric=True)
@@ -94,16 +151,18 @@ def test_bf16_long_products_span_several_panels(gb):
     assert np.all(np.abs(data - ref.data) <= 2 * 920 * U32 * mag.data + 1e-300)
 
 
+@pytest.mark.parametrize("low", ["bf16x3", "bf16"])
 @pytest.mark.parametrize("n_mol,basis,eps", [(24, (13, 5), 1e-7), (16, (23, 7), 1e-6)])
-def test_mixed_sign_matches_fp64_oracle(gb, n_mol, basis, eps):
+def test_mixed_sign_matches_fp64_oracle(gb, n_mol, basis, eps, low):
     h = synth.build_hamiltonian(synth.small(n_mol, basis=basis, seed=990 + n_mol))
-    H = gb.Matrix.of(h.H)
-    g = gb.sign_iterate(H, 0.0, eps, 1e-8, prec=gb.DBCSR_MIXED, switch_tol=1e-4)
+    lo = gb.DBCSR_BF16X3 if low == "bf16x3" else gb.DBCSR_BF16
+    g = gb.sign_iterate(gb.Matrix.of(h.H), 0.0, eps, 1e-8, prec=gb.DBCSR_MIXED, switch_tol=1e-4, low=lo)
     o = sign.sign_iterate(bsr.Mat.of(h.H), 0.0, eps, 1e-8)
-    assert g.report.fp64_from > 1                     # some steps ran in BF16
+    assert g.report.fp64_from > 1                     # some steps ran in the low tier
     assert g.converged or g.report.stalled
     assert abs(g.report.e_band - o.e_band) / h.n_atoms < DE_ATOM
     assert g.report.trace_p == pytest.approx(h.n_occ, abs=1e-4)
+    assert g.report.ms_low > 0 and g.report.ms_low < g.report.ms_multiply
 
 
 @pytest.mark.slow
@@ -117,15 +176,32 @@ def test_mixed_sign_1024_waters(gb):
     assert g.report.trace_p == pytest.approx(4096, abs=1e-4)
 
 
-def test_mixed_density_matrix_is_symmetric(gb):
+@pytest.mark.parametrize("low", ["bf16x3", "bf16"])
+def test_mixed_density_matrix_is_symmetric(gb, low):
     h = synth.build_hamiltonian(synth.small(24, seed=990 + 24))
-    g = gb.sign_iterate(gb.Matrix.of(h.H), 0.0, 1e-7, 1e-8, prec=gb.DBCSR_MIXED)
+    lo = gb.DBCSR_BF16X3 if low == "bf16x3" else gb.DBCSR_BF16
+    g = gb.sign_iterate(gb.Matrix.of(h.H), 0.0, 1e-7, 1e-8, prec=gb.DBCSR_MIXED, low=lo)
     rp, col, data = g.P.export()
     D = bsr.to_dense(bsr.Mat(h.H.blk_size, rp, col, data))
-    assert np.linalg.norm(D - D.T) <= 1e-14 * np.linalg.norm(D)
-    # the default FP64 iteration mirrors its off-diagonal blocks; its diagonal blocks
-    # are computed, so they are symmetric to rounding
-    f = gb.sign_iterate(gb.Matrix.of(h.H), 0.0, 1e-7, 1e-8)
+    assert np.array_equal(D, D.T)                     # the final X is replaced by its symmetric part
+
+
+def test_fp64_density_matrix_is_symmetric_to_the_filter(gb):
+    # the default FP64 iteration mirrors its off-diagonal blocks; its diagonal blocks are
+    # computed, and those of X X2 are symmetric only as far as X and the filtered X2 commute
+    # (X2 = X^2 minus blocks of norm < eps), so the asymmetry stays below eps_filter
+    eps = 1e-7
+    h = synth.build_hamiltonian(synth.small(24, seed=990 + 24))
+    f = gb.sign_iterate(gb.Matrix.of(h.H), 0.0, eps, 1e-8)
     rp, col, data = f.P.export()
-    D = bsr.to_dense(bsr.Mat(h.H.blk_size, rp, col, data))
-    assert np.linalg.norm(D - D.T) <= 1e-14 * np.linalg.norm(D)
+    M = bsr.Mat(h.H.blk_size, rp, col, data)
+    D = bsr.to_dense(M)
+    assert np.linalg.norm(D - D.T) < eps
+    # off-diagonal blocks are exact mirrors
+    assert (M.rows != M.col).any()
+    bo = np.concatenate([[0], np.cumsum(h.H.blk_size)])
+    blockdiag = np.zeros(D.shape, dtype=bool)
+    for I in range(len(h.H.blk_size)):
+        blockdiag[bo[I]:bo[I + 1], bo[I]:bo[I + 1]] = True
+    Doff = np.where(blockdiag, 0.0, D)
+    assert np.array_equal(Doff, Doff.T)

@@ -1,7 +1,7 @@
 """Pin of the oracle's bfloat16 rounding (no GPU)."""
 import numpy as np
 
-from oracle.lowprec import round_bf16
+from oracle.lowprec import round_bf16, split_bf16
 
 
 def test_exact_values_unchanged():
@@ -30,3 +30,24 @@ def test_relative_error_bound_and_idempotent():
 
 def test_tiny_values_flush():
     assert round_bf16(np.array([2.0 ** -127]))[0] == 0.0
+
+
+def test_split_parts_and_error():
+    rng = np.random.default_rng(2)
+    x = rng.standard_normal(10000) * 10.0 ** rng.integers(-20, 20, 10000)
+    hi, lo = split_bf16(x)
+    # both parts are bfloat16 numbers, hi is the rounding of x, lo the rounding of the rest
+    assert np.array_equal(round_bf16(hi), hi) and np.array_equal(round_bf16(lo), lo)
+    assert np.array_equal(hi, round_bf16(x))
+    assert np.all(np.abs(lo) <= 2.0 ** -8 * np.abs(x))
+    # hi + lo has about 16 significant bits: |x - hi - lo| <= 2^-8 |x - hi| <= 2^-16 |x|
+    assert np.all(np.abs(x - hi - lo) <= 2.0 ** -8 * np.abs(x - hi))
+    assert np.all(np.abs(x - hi - lo) <= 2.0 ** -16 * np.abs(x))
+
+
+def test_split_of_short_values_is_exact():
+    # a value with at most 16 significant bits whose tail needs no rounding splits exactly
+    v = np.array([1.0, 1 + 2 ** -7 + 2 ** -9, -(3 + 2 ** -12), 0.0, 2 ** -50 * (1 + 2 ** -15)])
+    hi, lo = split_bf16(v)
+    assert np.array_equal(hi + lo, v)
+    assert split_bf16(np.array([1 + 2 ** -7]))[1][0] == 0.0
