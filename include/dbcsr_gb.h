@@ -142,6 +142,16 @@ const char* dbcsr_last_error(void);
 const char* dbcsr_version(void);
 
 /*
+ * Device memory.  Every buffer of the library (matrices, product stacks, scratch)
+ * comes from one stream-ordered memory pool per device, owned by the library, that
+ * keeps freed memory cached for reuse (the per-product stacks are allocated and freed
+ * every product).  dbcsr_pool_trim waits for the current device, then returns the
+ * cached memory above keep_bytes to the driver; memory held by live matrices stays.
+ * Not from the paper (an allocator detail of this library).
+ */
+dbcsr_status dbcsr_pool_trim(uint64_t keep_bytes);
+
+/*
  * Creates an empty matrix with nblk block rows/columns of edges blk_size[0..nblk-1]
  * (host array, each in [1, 32]).  stream: a cudaStream_t (NULL = the legacy
  * default stream); all work on the matrix is queued there.  The matrix starts

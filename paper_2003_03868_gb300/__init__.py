@@ -206,6 +206,11 @@ def _sign_flags(full_products: bool, low: int) -> int:
             | (_ffi.DBCSR_SIGN_PLAIN_BF16 if low == DBCSR_BF16 else 0))
 
 
+def pool_trim(keep_bytes: int = 0) -> None:
+    """Return the library's cached device memory above keep_bytes to the driver."""
+    _check(lib().dbcsr_pool_trim(int(keep_bytes)), "pool_trim")
+
+
 def sign_iterate(H: Matrix, mu: float, eps_filter: float, tol: float, max_iter: int = 100,
                  prec: int = DBCSR_FP64, switch_tol: float = 1e-4, stall_ratio: float = 0.5,
                  P: Matrix | None = None, verbose: bool = False, raise_on_notconv: bool = False,

@@ -66,6 +66,7 @@ P = C.c_void_p
 SIGNATURES = [
     ("dbcsr_last_error", C.c_char_p, []),
     ("dbcsr_version", C.c_char_p, []),
+    ("dbcsr_pool_trim", C.c_int, [C.c_uint64]),
     ("dbcsr_create", C.c_int, [C.POINTER(P), C.c_int32, P, P]),
     ("dbcsr_destroy", C.c_int, [P]),
     ("dbcsr_put_block", C.c_int, [P, C.c_int32, C.c_int32, P, C.c_int]),

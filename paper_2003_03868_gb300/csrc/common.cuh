@@ -48,7 +48,14 @@ extern std::atomic<int64_t> g_launches;
         DBG_CK(cudaGetLastError());                        \
     } while (0)
 
-// Device array allocated and freed in stream order (cudaMallocAsync pool).
+// The library's stream-ordered memory pool on the current device.  It keeps freed
+// memory cached (release threshold = max) so that the per-product stacks and
+// matrices are not unmapped at every host synchronisation and mapped again.
+cudaMemPool_t library_pool();
+// Waits for the device, then returns cached pool memory above keep_bytes to the driver.
+void trim_pool(uint64_t keep_bytes);
+
+// Device array allocated and freed in stream order from library_pool().
 template <class T>
 struct DBuf {
     T* p = nullptr;
@@ -73,7 +80,7 @@ struct DBuf {
         release();
         s = stream;
         n = count;
-        if (count > 0) DBG_CK(cudaMallocAsync((void**)&p, sizeof(T) * (size_t)count, stream));
+        if (count > 0) DBG_CK(cudaMallocFromPoolAsync((void**)&p, sizeof(T) * (size_t)count, library_pool(), stream));
     }
     void zero() {
         if (n > 0) DBG_CK(cudaMemsetAsync(p, 0, sizeof(T) * (size_t)n, s));

@@ -6,11 +6,51 @@
 // row of each block row[nnzb], element offsets off[nnzb+1], and the blocks
 // themselves row-major and packed in CSR order in data[nel] (FP64).
 #include <algorithm>
+#include <mutex>
 #include <numeric>
 
 #include "common.cuh"
 
 namespace dbg {
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_pool_mu;
+cudaMemPool_t g_pools[kMaxDevices] = {};
+}  // namespace
+
+cudaMemPool_t library_pool() {
+    int dev = 0;
+    DBG_CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) fail(DBCSR_ECAPACITY, "library_pool: device ordinal out of range");
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (!g_pools[dev]) {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        DBG_CK(cudaMemPoolCreate(&pool, &props));
+        uint64_t keep = ~0ull;
+        DBG_CK(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep));
+        g_pools[dev] = pool;
+    }
+    return g_pools[dev];
+}
+
+void trim_pool(uint64_t keep_bytes) {
+    int dev = 0;
+    DBG_CK(cudaGetDevice(&dev));
+    cudaMemPool_t pool = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_pool_mu);
+        if (dev >= 0 && dev < kMaxDevices) pool = g_pools[dev];
+    }
+    if (!pool) return;
+    DBG_CK(cudaDeviceSynchronize());
+    DBG_CK(cudaMemPoolTrimTo(pool, (size_t)keep_bytes));
+}
 
 HostScalars::HostScalars() {
     DBG_CK(cudaMallocHost((void**)&i, kCap * sizeof(int64_t)));
@@ -337,6 +377,10 @@ extern "C" {
 const char* dbcsr_last_error(void) { return g_last_error.c_str(); }
 
 const char* dbcsr_version(void) { return "dbcsr_gb 0.1 (sm_103a)"; }
+
+dbcsr_status dbcsr_pool_trim(uint64_t keep_bytes) {
+    return guarded([&] { dbg::trim_pool(keep_bytes); });
+}
 
 dbcsr_status dbcsr_create(dbcsr_matrix* out, int32_t nblk, const int32_t* blk_size, void* stream) {
     return guarded([&] {

@@ -703,10 +703,77 @@ struct SmmBf16Args {
     const __nv_bfloat16* b16_lo;
 };
 
+// Register fragments of one 16-wide k-slice of one block product: MT 16-row tiles of A,
+// NT 8-column tiles of B (and their residuals for SPLIT), loaded straight from the
+// fragment-ready packed copies.
+template <int MT, int NT, bool SPLIT>
+struct BfFrag {
+    uint32_t a[MT][4], b[NT][2];
+    uint32_t al[SPLIT ? MT : 1][4], bl[SPLIT ? NT : 1][2];
+
+    __device__ __forceinline__ void load(const SmmBf16Args& G, int64_t aoq, int64_t boq, int KT, int kt, int gid,
+                                         int tig) {
+        const int h = 8 * KT;                                 // 32-bit words per packed row (16 KT bf16)
+        const int c0 = kt * 8 + tig;                          // word of columns (16 kt + 2 tig, +1)
+        const uint32_t* __restrict__ Ap = reinterpret_cast<const uint32_t*>(G.a16 + aoq);
+        const uint32_t* __restrict__ Bp = reinterpret_cast<const uint32_t*>(G.b16 + boq);
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt) {
+            const int row = (nt * 8 + gid) * h;
+            b[nt][0] = __ldg(Bp + row + c0);
+            b[nt][1] = __ldg(Bp + row + c0 + 4);
+        }
+#pragma unroll
+        for (int mt = 0; mt < MT; ++mt) {
+            const int r0 = (mt * 16 + gid) * h, r1 = r0 + 8 * h;
+            a[mt][0] = __ldg(Ap + r0 + c0);
+            a[mt][1] = __ldg(Ap + r1 + c0);
+            a[mt][2] = __ldg(Ap + r0 + c0 + 4);
+            a[mt][3] = __ldg(Ap + r1 + c0 + 4);
+        }
+        if (SPLIT) {
+            const uint32_t* __restrict__ Apl = reinterpret_cast<const uint32_t*>(G.a16_lo + aoq);
+            const uint32_t* __restrict__ Bpl = reinterpret_cast<const uint32_t*>(G.b16_lo + boq);
+#pragma unroll
+            for (int nt = 0; nt < NT; ++nt) {
+                const int row = (nt * 8 + gid) * h;
+                bl[SPLIT ? nt : 0][0] = __ldg(Bpl + row + c0);
+                bl[SPLIT ? nt : 0][1] = __ldg(Bpl + row + c0 + 4);
+            }
+#pragma unroll
+            for (int mt = 0; mt < MT; ++mt) {
+                const int r0 = (mt * 16 + gid) * h, r1 = r0 + 8 * h;
+                al[SPLIT ? mt : 0][0] = __ldg(Apl + r0 + c0);
+                al[SPLIT ? mt : 0][1] = __ldg(Apl + r1 + c0);
+                al[SPLIT ? mt : 0][2] = __ldg(Apl + r0 + c0 + 4);
+                al[SPLIT ? mt : 0][3] = __ldg(Apl + r1 + c0 + 4);
+            }
+        }
+    }
+
+    __device__ __forceinline__ void mma(float (&acc)[MT][NT][4]) const {
+#pragma unroll
+        for (int mt = 0; mt < MT; ++mt) {
+#pragma unroll
+            for (int nt = 0; nt < NT; ++nt) mma_bf16(acc[mt][nt], a[mt][0], a[mt][1], a[mt][2], a[mt][3], b[nt][0], b[nt][1]);
+            if (SPLIT) {
+#pragma unroll
+                for (int nt = 0; nt < NT; ++nt) {
+                    mma_bf16(acc[mt][nt], a[mt][0], a[mt][1], a[mt][2], a[mt][3], bl[SPLIT ? nt : 0][0],
+                             bl[SPLIT ? nt : 0][1]);
+                    mma_bf16(acc[mt][nt], al[SPLIT ? mt : 0][0], al[SPLIT ? mt : 0][1], al[SPLIT ? mt : 0][2],
+                             al[SPLIT ? mt : 0][3], b[nt][0], b[nt][1]);
+                }
+            }
+        }
+    }
+};
+
 // SPLIT (DBCSR_BF16X3): operands x = hi + lo, both BF16; per fragment set three MMAs
 // accumulate hi*hi + hi*lo + lo*hi in FP32 (the lo*lo term, ~2^-16 relative, is left out).
 template <int MT, int NT, bool SPLIT>
-__global__ void __launch_bounds__(256) k_smm_bf16(int64_t nlist, const int64_t* __restrict__ list, SmmBf16Args G) {
+__global__ void __launch_bounds__(256, (MT * NT <= 2 || MT * NT >= 6) ? 2 : 3) k_smm_bf16(int64_t nlist, const int64_t* __restrict__ list, SmmBf16Args G) {
+    constexpr bool PIPE = MT * NT <= 2;
     const SmmArgs& S = G.base;
     const int lane = threadIdx.x & 31, gid = lane >> 2, tig = lane & 3;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -732,44 +799,48 @@ __global__ void __launch_bounds__(256) k_smm_bf16(int64_t nlist, const int64_t* 
                 bo = (int64_t)bi * G.b_stride;
                 kq = S.bs[S.a_col[ai]];
             }
-            for (int q = 0; q < cnt; ++q) {
-                const int64_t aoq = __shfl_sync(0xffffffffu, ao, q);
-                const int64_t boq = __shfl_sync(0xffffffffu, bo, q);
-                const int kk = __shfl_sync(0xffffffffu, kq, q);
-                const int KT = (kk + 15) >> 4, ld = 16 * KT;     // padded inner size = row length of both tiles
-                const uint32_t* __restrict__ Ap = reinterpret_cast<const uint32_t*>(G.a16 + aoq);
-                const uint32_t* __restrict__ Bp = reinterpret_cast<const uint32_t*>(G.b16 + boq);
-                const uint32_t* __restrict__ Apl = SPLIT ? reinterpret_cast<const uint32_t*>(G.a16_lo + aoq) : nullptr;
-                const uint32_t* __restrict__ Bpl = SPLIT ? reinterpret_cast<const uint32_t*>(G.b16_lo + boq) : nullptr;
-                for (int kt = 0; kt < KT; ++kt) {
-                    const int c0 = (kt * 16 + tig * 2) >> 1;      // 32-bit word of columns (c, c+1)
-                    uint32_t bf[NT][2], bl[NT][2];
-#pragma unroll
-                    for (int nt = 0; nt < NT; ++nt) {
-                        const int row = (nt * 8 + gid) * (ld >> 1);
-                        bf[nt][0] = __ldg(Bp + row + c0);
-                        bf[nt][1] = __ldg(Bp + row + c0 + 4);
-                        if (SPLIT) {
-                            bl[nt][0] = __ldg(Bpl + row + c0);
-                            bl[nt][1] = __ldg(Bpl + row + c0 + 4);
+            if (PIPE) {
+                // Software pipeline over the batch's units (product q, 16-wide k-slice kt): the
+                // fragments of the next unit are loaded before the MMAs of the current one.
+                // Every accumulator still sees its MMAs in the order (q, kt, hi*hi, hi*lo, lo*hi).
+                BfFrag<MT, NT, SPLIT> cur, nxt;
+                int q = 0, kt = 0;
+                int64_t aoq = __shfl_sync(0xffffffffu, ao, 0), boq = __shfl_sync(0xffffffffu, bo, 0);
+                int KT = (__shfl_sync(0xffffffffu, kq, 0) + 15) >> 4;
+                cur.load(G, aoq, boq, KT, kt, gid, tig);
+                while (true) {
+                    int nq = q, nkt = kt + 1, nKT = KT;
+                    int64_t naoq = aoq, nboq = boq;
+                    if (nkt == KT) {
+                        nq = q + 1;
+                        nkt = 0;
+                        if (nq < cnt) {                                 // warp-uniform
+                            naoq = __shfl_sync(0xffffffffu, ao, nq);
+                            nboq = __shfl_sync(0xffffffffu, bo, nq);
+                            nKT = (__shfl_sync(0xffffffffu, kq, nq) + 15) >> 4;
                         }
                     }
-#pragma unroll
-                    for (int mt = 0; mt < MT; ++mt) {
-                        const int r0 = (mt * 16 + gid) * (ld >> 1), r1 = r0 + 8 * (ld >> 1);
-                        const uint32_t a0 = __ldg(Ap + r0 + c0), a1 = __ldg(Ap + r1 + c0);
-                        const uint32_t a2 = __ldg(Ap + r0 + c0 + 4), a3 = __ldg(Ap + r1 + c0 + 4);
-#pragma unroll
-                        for (int nt = 0; nt < NT; ++nt) mma_bf16(acc[mt][nt], a0, a1, a2, a3, bf[nt][0], bf[nt][1]);
-                        if (SPLIT) {
-                            const uint32_t l0 = __ldg(Apl + r0 + c0), l1 = __ldg(Apl + r1 + c0);
-                            const uint32_t l2 = __ldg(Apl + r0 + c0 + 4), l3 = __ldg(Apl + r1 + c0 + 4);
-#pragma unroll
-                            for (int nt = 0; nt < NT; ++nt) {
-                                mma_bf16(acc[mt][nt], a0, a1, a2, a3, bl[nt][0], bl[nt][1]);
-                                mma_bf16(acc[mt][nt], l0, l1, l2, l3, bf[nt][0], bf[nt][1]);
-                            }
-                        }
+                    const bool more = nq < cnt;
+                    if (more) nxt.load(G, naoq, nboq, nKT, nkt, gid, tig);
+                    cur.mma(acc);
+                    if (!more) break;
+                    cur = nxt;
+                    q = nq;
+                    kt = nkt;
+                    KT = nKT;
+                    aoq = naoq;
+                    boq = nboq;
+                }
+            } else {
+                // larger fragment sets: one unit in flight per warp, more warps per SM
+                for (int q = 0; q < cnt; ++q) {
+                    const int64_t aoq = __shfl_sync(0xffffffffu, ao, q);
+                    const int64_t boq = __shfl_sync(0xffffffffu, bo, q);
+                    const int KT = (__shfl_sync(0xffffffffu, kq, q) + 15) >> 4;
+                    for (int kt = 0; kt < KT; ++kt) {
+                        BfFrag<MT, NT, SPLIT> f;
+                        f.load(G, aoq, boq, KT, kt, gid, tig);
+                        f.mma(acc);
                     }
                 }
             }
