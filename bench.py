@@ -153,40 +153,56 @@ def run_reference(args):
 
 def run_batch(args, gb, synth, torch, barrier):
     """64 uneven water systems (n_mol log-uniform in [100, 2000], O/H blocks per system):
-    one batched sign iteration vs the same systems solved one after the other."""
+    one batched sign iteration vs the same systems solved one after the other, in FP64
+    and with the mixed-precision ladder."""
     ws = synth.batch_systems()
     hs = [synth.build_hamiltonian(w) for w in ws]
     stream = torch.cuda.current_stream()
     Hs = [gb.Matrix.of(h.H, stream=stream.cuda_stream) for h in hs]
     eps, tol = ws[0].eps_filter, ws[0].tol
-    prec = gb.DBCSR_MIXED if args.batch_mixed else gb.DBCSR_FP64
-    for _ in range(args.warmup):
-        gb.sign_iterate_batched(Hs, [0.0] * len(Hs), eps, tol, prec=prec)
-    barrier()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        Ps, reps, st = gb.sign_iterate_batched(Hs, [0.0] * len(Hs), eps, tol, prec=prec)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms_b = e0.elapsed_time(e1) / args.steps
-    # the same systems one by one
-    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    s0.record(stream)
-    seq = [gb.sign_iterate(H, 0.0, eps, tol, prec=prec) for H in Hs]
-    s1.record(stream)
-    torch.cuda.synchronize()
-    ms_s = s0.elapsed_time(s1)
-    de = max(abs(r.e_band - g.report.e_band) / h.n_atoms for r, g, h in zip(reps, seq, hs))
-    out = {"metric": "block-GEMM TFLOP/s (batched sign iteration)", "value": reps[0].flops / (ms_b * 1e-3) / 1e12,
-           "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_b,
-           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-           "dtype": "f64" if prec == gb.DBCSR_FP64 else "bf16/f32 then f64", "data": "synthetic",
+
+    def leg(prec):
+        for _ in range(args.warmup):
+            gb.sign_iterate_batched(Hs, [0.0] * len(Hs), eps, tol, prec=prec)
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            Ps, reps, st = gb.sign_iterate_batched(Hs, [0.0] * len(Hs), eps, tol, prec=prec)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_b = e0.elapsed_time(e1) / args.steps
+        # the same systems one by one
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        seq = [gb.sign_iterate(H, 0.0, eps, tol, prec=prec) for H in Hs]
+        s1.record(stream)
+        torch.cuda.synchronize()
+        ms_s = s0.elapsed_time(s1)
+        de = max(abs(r.e_band - g.report.e_band) / h.n_atoms for r, g, h in zip(reps, seq, hs))
+        its = [r.iterations for r in reps]
+        return {"ms_per_step": ms_b, "value": reps[0].flops / (ms_b * 1e-3) / 1e12, "unit": "TFLOP/s",
+                "sequential_ms": ms_s, "speedup_vs_sequential": ms_s / ms_b,
+                "systems_converged": sum(int(r.converged) for r in reps),
+                "systems_stalled": sum(int(r.stalled) for r in reps),
+                "max_de_band_per_atom_vs_sequential": de, "iterations_min": min(its), "iterations_max": max(its),
+                "ms_multiply": reps[0].ms_multiply, "ms_low": reps[0].ms_low}, reps
+
+    f64, reps64 = leg(gb.DBCSR_FP64)
+    mixed = None
+    if not args.no_mixed:
+        mixed, repsm = leg(gb.DBCSR_MIXED)
+        mixed["speedup_vs_fp64_batched"] = f64["ms_per_step"] / mixed["ms_per_step"]
+        mixed["max_de_band_per_atom_vs_fp64"] = max(abs(a.e_band - b.e_band) / h.n_atoms
+                                                    for a, b, h in zip(repsm, reps64, hs))
+        mixed["dtype"] = "bf16x3 (split bf16 hi+lo operands, fp32 accumulate), then f64"
+    out = {"metric": "block-GEMM TFLOP/s (batched sign iteration)", "value": f64["value"],
+           "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": f64["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64", "data": "synthetic",
            "config": {"workload": "batch-64", "systems": len(ws), "molecules": sum(w.n_mol for w in ws),
                       "atoms": sum(w.n_atoms for w in ws), "eps_filter": eps, "tol": tol},
-           "sequential_ms": ms_s, "speedup_vs_sequential": ms_s / ms_b,
-           "systems_converged": sum(int(r.converged) for r in reps), "systems_stalled": sum(int(r.stalled) for r in reps),
-           "max_de_band_per_atom_vs_sequential": de, "iterations_max": max(r.iterations for r in reps)}
+           **{k: v for k, v in f64.items() if k not in ("value", "ms_per_step", "unit")}, "mixed": mixed}
     print(json.dumps(out))
     return 0
 
@@ -203,11 +219,11 @@ def main():
     ap.add_argument("--ref-steps", type=int, default=1, help="Newton-Schulz steps per oracle sample (reference arm)")
     ap.add_argument("--cpu-steps", type=int, default=2, help="Newton-Schulz steps in the oracle CPU baseline")
     ap.add_argument("--workload", default="sign-1024h2o",
-                    choices=["sign-1024h2o", "sign-512h2o", "sign-4096h2o", "batch-64"],
-                    help="sign-512h2o: a smaller case for profiler captures; sign-4096h2o: 4,096 waters with "
-                         "O/H blocks 23/7 (FP64 and mixed); batch-64: 64 uneven systems batched vs one by one")
+                    choices=["sign-1024h2o", "sign-512h2o", "sign-512h2o-23-7", "sign-4096h2o", "batch-64"],
+                    help="sign-512h2o, sign-512h2o-23-7: smaller cases for profiler captures; sign-4096h2o: "
+                         "4,096 waters with O/H blocks 23/7 (FP64 and mixed); batch-64: 64 uneven systems "
+                         "batched vs one by one")
     ap.add_argument("--verbose", action="store_true")
-    ap.add_argument("--batch-mixed", action="store_true", help="batch-64 with the mixed-precision ladder")
     args = ap.parse_args()
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
@@ -242,8 +258,10 @@ def main():
 
     if args.workload == "batch-64":
         return run_batch(args, gb, synth, torch, barrier)
-    w = {"sign-1024h2o": synth.SIGN_1024, "sign-4096h2o": synth.SIGN_4096}.get(args.workload) or synth.Workload(
-        "sign-512h2o-dzvp-fp64", 512, (13, 5), synth.configs.BASE_SEED + 12, 1e-7, 1e-9)
+    w = {"sign-1024h2o": synth.SIGN_1024, "sign-4096h2o": synth.SIGN_4096,
+         "sign-512h2o": synth.Workload("sign-512h2o-dzvp-fp64", 512, (13, 5), synth.configs.BASE_SEED + 12, 1e-7, 1e-9),
+         "sign-512h2o-23-7": synth.Workload("sign-512h2o-23-7", 512, (23, 7), synth.configs.BASE_SEED + 13, 1e-6, 1e-8,
+                                            1e-4)}[args.workload]
     h = synth.build_hamiltonian(w)
     stream = torch.cuda.current_stream()
     H = gb.Matrix.of(h.H, stream=stream.cuda_stream)

@@ -11,10 +11,10 @@
 // Per system: its own Gershgorin scale alpha_s, X_0 = (H_s - mu_s 1) / alpha_s,
 // residual r_s = ||X2_s - 1||_F / N_s from the blocks of its rows, and its own
 // convergence / stall record (same tests as the single-system iteration).  A
-// system that has converged keeps iterating at its fixed point until every system
-// is done (its X changes only within the filter's noise).  With DBCSR_MIXED the
-// whole batch leaves the BF16 tier once any system's residual drops below the
-// switch.
+// system that is done leaves the batch at once: its P is written out and the batch
+// matrices are compacted to the systems still running, so later products spend
+// nothing on it.  With DBCSR_MIXED the whole batch leaves the low-precision tier
+// once any system's residual drops below the switch.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -30,6 +30,12 @@ namespace {
 __global__ void k_shift_i32(int64_t n, const int32_t* __restrict__ in, int32_t add, int32_t* __restrict__ out) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         out[i] = in[i] + add;
+}
+
+__global__ void k_gather_i64(int64_t n, const int64_t* __restrict__ idx, const int64_t* __restrict__ src,
+                             int64_t* __restrict__ out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = src[idx[i]];
 }
 
 __global__ void k_shift_i64(int64_t n, const int64_t* __restrict__ in, int64_t add, int64_t* __restrict__ out) {
@@ -264,10 +270,138 @@ dbcsr_status sign_iterate_batched(int32_t nsys, dbcsr_matrix_* const* H, const d
             launches_fp64 += ms.n_launches;
         }
     };
+    // Active systems, in batch order, with their block-row ranges in the current X.  A system
+    // that is done leaves the batch at once: its P is written and X (and X2, which the next
+    // update reads) are compacted to the systems still running, so no product is spent on
+    // a finished system.
+    std::vector<int32_t> act(nsys), act_beg(row_beg);
+    for (int32_t s = 0; s < nsys; ++s) act[s] = s;
+    std::vector<int32_t> cur_bs = bs;
+    DBuf<int64_t> d_idx, d_vals;
+    // block and element offsets of the active systems' ranges in m: b[a], e[a] for a = 0..nact
+    auto range_offsets = [&](const dbcsr_matrix_* m, std::vector<int64_t>& b, std::vector<int64_t>& e) {
+        const size_t na = act.size();
+        std::vector<int64_t> hrp(m->nblk + 1);
+        DBG_CK(cudaMemcpyAsync(hrp.data(), m->rp.p, sizeof(int64_t) * (m->nblk + 1), cudaMemcpyDeviceToHost, st));
+        DBG_CK(cudaStreamSynchronize(st));
+        b.resize(na + 1);
+        for (size_t a = 0; a <= na; ++a) b[a] = hrp[act_beg[a]];
+        d_idx.alloc((int64_t)na + 1, st);
+        d_vals.alloc((int64_t)na + 1, st);
+        DBG_CK(cudaMemcpyAsync(d_idx.p, b.data(), sizeof(int64_t) * (na + 1), cudaMemcpyHostToDevice, st));
+        k_gather_i64<<<grid_for((int64_t)na + 1, 256), 256, 0, st>>>((int64_t)na + 1, d_idx.p, m->off.p, d_vals.p);
+        DBG_LAUNCH_CK();
+        e.resize(na + 1);
+        DBG_CK(cudaMemcpyAsync(e.data(), d_vals.p, sizeof(int64_t) * (na + 1), cudaMemcpyDeviceToHost, st));
+        DBG_CK(cudaStreamSynchronize(st));
+    };
+    // copies rows [r0, r1) of the block-diagonal m (blocks [b0, b1), elements [e0, e1)) into
+    // dst at block row dr0, block db0, element de0
+    auto copy_rows = [&](const dbcsr_matrix_* m, int32_t r0, int32_t r1, int64_t b0, int64_t b1, int64_t e0, int64_t e1,
+                         dbcsr_matrix_* dst, int32_t dr0, int64_t db0, int64_t de0, cudaStream_t ds) {
+        k_shift_i64<<<grid_for(r1 - r0 + 1, 256), 256, 0, ds>>>(r1 - r0 + 1, m->rp.p + r0, db0 - b0, dst->rp.p + dr0);
+        DBG_LAUNCH_CK();
+        if (b1 > b0) {
+            k_shift_i32<<<grid_for(b1 - b0, 256), 256, 0, ds>>>(b1 - b0, m->col.p + b0, dr0 - r0, dst->col.p + db0);
+            DBG_LAUNCH_CK();
+            k_shift_i32<<<grid_for(b1 - b0, 256), 256, 0, ds>>>(b1 - b0, m->row.p + b0, dr0 - r0, dst->row.p + db0);
+            DBG_LAUNCH_CK();
+        }
+        k_shift_i64<<<grid_for(b1 - b0 + 1, 256), 256, 0, ds>>>(b1 - b0 + 1, m->off.p + b0, de0 - e0, dst->off.p + db0);
+        DBG_LAUNCH_CK();
+        if (e1 > e0)
+            DBG_CK(cudaMemcpyAsync(dst->data.p + de0, m->data.p + e0, sizeof(double) * (e1 - e0), cudaMemcpyDeviceToDevice, ds));
+    };
+    // the active systems flagged in `leave` leave the batch: P_s = (1 - X_s) / 2, then X and
+    // (when given) X2 keep only the others
+    auto retire = [&](const std::vector<char>& leave, dbcsr_matrix_* x2) {
+        std::vector<int64_t> xb, xe, yb, ye;
+        range_offsets(X.get(), xb, xe);
+        if (x2) range_offsets(x2, yb, ye);
+        const size_t na = act.size();
+        for (size_t a = 0; a < na; ++a) {
+            if (!leave[a]) continue;
+            const int32_t sid = act[a];
+            dbcsr_matrix_* pm = P[sid];
+            cudaStream_t ps = pm->stream;
+            if (ps != st) DBG_CK(cudaStreamSynchronize(st));
+            const int32_t nb_s = act_beg[a + 1] - act_beg[a];
+            const int64_t nbk = xb[a + 1] - xb[a], nel_s = xe[a + 1] - xe[a];
+            pm->rp.alloc(nb_s + 1, ps);
+            pm->col.alloc(std::max<int64_t>(nbk, 1), ps);
+            pm->row.alloc(std::max<int64_t>(nbk, 1), ps);
+            pm->off.alloc(nbk + 1, ps);
+            pm->data.alloc(std::max<int64_t>(nel_s, 1), ps);
+            copy_rows(X.get(), act_beg[a], act_beg[a + 1], xb[a], xb[a + 1], xe[a], xe[a + 1], pm, 0, 0, 0, ps);
+            pm->nnzb = nbk;
+            pm->nel = nel_s;
+            pm->norms_valid = false;
+            pm->finalized = true;
+            // X of a mixed run is symmetric only to the low tier's accuracy: keep its symmetric part
+            if (o.prec == DBCSR_MIXED && !full) symmetrize(pm);
+            scale_shift(pm, -0.5, 0.5);
+            dbcsr_sign_report& R = rep[sid];
+            R.trace_p = trace(pm);
+            R.e_band = trace_product(pm, H[sid]);
+            R.converged = done[sid] == 1;
+            R.stalled = done[sid] == 2;
+            R.fp64_from = first_fp64;
+            R.nnzb_x = pm->nnzb;
+        }
+        // (trace_product synchronised each P's stream, so nothing still reads the old X)
+        // the systems that stay, renumbered from block row 0
+        std::vector<int32_t> nact, nbeg{0}, nbs;
+        for (size_t a = 0; a < na; ++a) {
+            if (leave[a]) continue;
+            nact.push_back(act[a]);
+            nbs.insert(nbs.end(), cur_bs.begin() + act_beg[a], cur_bs.begin() + act_beg[a + 1]);
+            nbeg.push_back((int32_t)nbs.size());
+        }
+        auto rebuild = [&](const dbcsr_matrix_* m, const std::vector<int64_t>& b, const std::vector<int64_t>& e) {
+            int64_t nnzb_new = 0, nel_new = 0;
+            for (size_t a = 0; a < na; ++a)
+                if (!leave[a]) {
+                    nnzb_new += b[a + 1] - b[a];
+                    nel_new += e[a + 1] - e[a];
+                }
+            auto y = make_matrix(nbs, st);
+            y->rp.alloc(y->nblk + 1, st);
+            y->col.alloc(std::max<int64_t>(nnzb_new, 1), st);
+            y->row.alloc(std::max<int64_t>(nnzb_new, 1), st);
+            y->off.alloc(nnzb_new + 1, st);
+            y->data.alloc(std::max<int64_t>(nel_new, 1), st);
+            int64_t db = 0, de = 0;
+            size_t k = 0;
+            for (size_t a = 0; a < na; ++a) {
+                if (leave[a]) continue;
+                copy_rows(m, act_beg[a], act_beg[a + 1], b[a], b[a + 1], e[a], e[a + 1], y.get(), nbeg[k], db, de, st);
+                db += b[a + 1] - b[a];
+                de += e[a + 1] - e[a];
+                ++k;
+            }
+            y->nnzb = nnzb_new;
+            y->nel = nel_new;
+            y->norms_valid = false;
+            y->finalized = true;
+            return y;
+        };
+        if (!nact.empty()) {
+            // each old matrix is freed (stream-ordered, after its copies) before the next is rebuilt
+            X = rebuild(X.get(), xb, xe);
+            if (x2) X2 = rebuild(x2, yb, ye);
+        }
+        act = std::move(nact);
+        act_beg = std::move(nbeg);
+        cur_bs = std::move(nbs);
+        if (!act.empty())
+            DBG_CK(cudaMemcpyAsync(d_row_beg.p, act_beg.data(), sizeof(int32_t) * act_beg.size(), cudaMemcpyHostToDevice, st));
+    };
+
     std::vector<double> dev2(nsys);
     DBuf<double> blk_dev2;
     int it = 0;
-    while (it < o.max_iter) {
+    while (it < o.max_iter && !act.empty()) {
+        const int32_t nact = (int32_t)act.size();
         dbcsr_mult_stats ms{};
         multiply(1.0, X.get(), X.get(), 0.0, X2.get(), o.eps_filter, tier, &ms, false, sym);
         account(ms, tier);
@@ -275,38 +409,42 @@ dbcsr_status sign_iterate_batched(int32_t nsys, dbcsr_matrix_* const* H, const d
         // per-system ||X2_s - 1||_F^2 over the kept blocks of the system's rows
         blk_dev2.alloc(std::max<int64_t>(X2->nnzb, 1), st);
         compute_block_norms(X2.get(), nullptr, blk_dev2.p);
-        k_bbeg_from_rows<<<1, 128, 0, st>>>(nsys, X2->rp.p, d_row_beg.p, d_bbeg.p);
+        k_bbeg_from_rows<<<1, 128, 0, st>>>(nact, X2->rp.p, d_row_beg.p, d_bbeg.p);
         DBG_LAUNCH_CK();
-        k_segment_sum<<<std::min<int32_t>(nsys, 1024), 256, 0, st>>>(nsys, d_bbeg.p, blk_dev2.p, d_dev2.p);
+        k_segment_sum<<<std::min<int32_t>(nact, 1024), 256, 0, st>>>(nact, d_bbeg.p, blk_dev2.p, d_dev2.p);
         DBG_LAUNCH_CK();
-        DBG_CK(cudaMemcpyAsync(dev2.data(), d_dev2.p, sizeof(double) * nsys, cudaMemcpyDeviceToHost, st));
+        DBG_CK(cudaMemcpyAsync(dev2.data(), d_dev2.p, sizeof(double) * nact, cudaMemcpyDeviceToHost, st));
         DBG_CK(cudaStreamSynchronize(st));
-        bool all_done = true, any_below_switch = false;
-        for (int32_t s = 0; s < nsys; ++s) {
-            const double r = std::sqrt(dev2[s]) / nsys_dim[s];
-            dbcsr_sign_report& R = rep[s];
-            if (!std::isfinite(r)) fail(DBCSR_ENAN, "sign_iterate_batched: residual of system " + std::to_string(s) + " is not finite");
-            if (!done[s]) {
-                if (it - 1 < DBCSR_MAX_HISTORY) R.residual_history[it - 1] = r;
-                R.iterations = it;
-                R.residual = r;
-                const bool slow = it >= 3 && it - 1 < DBCSR_MAX_HISTORY &&
-                                  R.residual_history[it - 2] < o.stall_ratio * R.residual_history[it - 3] &&
-                                  r > o.stall_ratio * R.residual_history[it - 2];
-                if (tier == DBCSR_FP64) {
-                    if (r < o.tol) done[s] = 1;
-                    else if (slow && it >= first_fp64 + 2) done[s] = 2;
-                } else if (r < o.switch_tol || r < o.tol || slow) {
-                    any_below_switch = true;
-                }
+        bool any_below_switch = false, any_done = false;
+        std::vector<char> leave(nact, 0);
+        for (int32_t a = 0; a < nact; ++a) {
+            const int32_t sid = act[a];
+            const double r = std::sqrt(dev2[a]) / nsys_dim[sid];
+            dbcsr_sign_report& R = rep[sid];
+            if (!std::isfinite(r)) fail(DBCSR_ENAN, "sign_iterate_batched: residual of system " + std::to_string(sid) + " is not finite");
+            if (it - 1 < DBCSR_MAX_HISTORY) R.residual_history[it - 1] = r;
+            R.iterations = it;
+            R.residual = r;
+            const bool slow = it >= 3 && it - 1 < DBCSR_MAX_HISTORY &&
+                              R.residual_history[it - 2] < o.stall_ratio * R.residual_history[it - 3] &&
+                              r > o.stall_ratio * R.residual_history[it - 2];
+            if (tier == DBCSR_FP64) {
+                if (r < o.tol) done[sid] = 1;
+                else if (slow && it >= first_fp64 + 2) done[sid] = 2;
+            } else if (r < o.switch_tol || r < o.tol || slow) {
+                any_below_switch = true;
             }
-            all_done = all_done && done[s];
+            if (done[sid]) {
+                leave[a] = 1;
+                any_done = true;
+            }
         }
         if (o.verbose)
-            std::fprintf(stderr, "[batch] it %3d %s systems done %d/%d formed %lld %.1f GF %.2f ms\n", it,
-                         tier == DBCSR_FP64 ? "fp64" : tier == DBCSR_BF16 ? "bf16" : "bf16x3", (int)std::count_if(done.begin(), done.end(), [](int d) { return d != 0; }),
-                         nsys, (long long)ms.n_formed, ms.flops * 1e-9, ms.ms_numeric);
-        if (all_done) break;
+            std::fprintf(stderr, "[batch] it %3d %s systems running %d/%d formed %lld %.1f GF %.2f ms\n", it,
+                         tier == DBCSR_FP64 ? "fp64" : tier == DBCSR_BF16 ? "bf16" : "bf16x3", nact, nsys,
+                         (long long)ms.n_formed, ms.flops * 1e-9, ms.ms_numeric);
+        if (any_done) retire(leave, X2.get());
+        if (act.empty()) break;
         if (tier != DBCSR_FP64 && any_below_switch) {
             tier = DBCSR_FP64;
             first_fp64 = it + 1;
@@ -314,54 +452,9 @@ dbcsr_status sign_iterate_batched(int32_t nsys, dbcsr_matrix_* const* H, const d
         multiply(-0.5, X.get(), X2.get(), 1.5, X.get(), o.eps_filter, tier, &ms, false, sym);
         account(ms, tier);
     }
-    for (int32_t s = 0; s < nsys; ++s)
-        if (!done[s]) done[s] = 3;
-
-    // a mixed batch forms both triangles of every product: keep X's symmetric part
-    if (o.prec == DBCSR_MIXED && !full) symmetrize(X.get());
-
-    // ---- split X back into the systems: P_s = (1 - X_s) / 2
-    std::vector<int64_t> hrp(nblk + 1);
-    DBG_CK(cudaMemcpyAsync(hrp.data(), X->rp.p, sizeof(int64_t) * (nblk + 1), cudaMemcpyDeviceToHost, st));
-    std::vector<int64_t> hoff(X->nnzb + 1);
-    DBG_CK(cudaMemcpyAsync(hoff.data(), X->off.p, sizeof(int64_t) * (X->nnzb + 1), cudaMemcpyDeviceToHost, st));
-    DBG_CK(cudaStreamSynchronize(st));
-    for (int32_t s = 0; s < nsys; ++s) {
-        dbcsr_matrix_* p = P[s];
-        cudaStream_t ps = p->stream;
-        if (ps != st) DBG_CK(cudaStreamSynchronize(st));
-        const int32_t r0 = row_beg[s], r1 = row_beg[s + 1], nb_s = r1 - r0;
-        const int64_t b0 = hrp[r0], b1 = hrp[r1], e0 = hoff[b0], e1 = hoff[b1];
-        p->rp.alloc(nb_s + 1, ps);
-        p->col.alloc(std::max<int64_t>(b1 - b0, 1), ps);
-        p->row.alloc(std::max<int64_t>(b1 - b0, 1), ps);
-        p->off.alloc(b1 - b0 + 1, ps);
-        p->data.alloc(std::max<int64_t>(e1 - e0, 1), ps);
-        k_shift_i64<<<grid_for(nb_s + 1, 256), 256, 0, ps>>>(nb_s + 1, X->rp.p + r0, -b0, p->rp.p);
-        DBG_LAUNCH_CK();
-        if (b1 > b0) {
-            k_shift_i32<<<grid_for(b1 - b0, 256), 256, 0, ps>>>(b1 - b0, X->col.p + b0, -r0, p->col.p);
-            DBG_LAUNCH_CK();
-            k_shift_i32<<<grid_for(b1 - b0, 256), 256, 0, ps>>>(b1 - b0, X->row.p + b0, -r0, p->row.p);
-            DBG_LAUNCH_CK();
-        }
-        k_shift_i64<<<grid_for(b1 - b0 + 1, 256), 256, 0, ps>>>(b1 - b0 + 1, X->off.p + b0, -e0, p->off.p);
-        DBG_LAUNCH_CK();
-        if (e1 > e0)
-            DBG_CK(cudaMemcpyAsync(p->data.p, X->data.p + e0, sizeof(double) * (e1 - e0), cudaMemcpyDeviceToDevice, ps));
-        p->nnzb = b1 - b0;
-        p->nel = e1 - e0;
-        p->norms_valid = false;
-        p->finalized = true;
-        scale_shift(p, -0.5, 0.5);
-        dbcsr_sign_report& R = rep[s];
-        R.trace_p = trace(p);
-        R.e_band = trace_product(p, H[s]);
-        R.converged = done[s] == 1;
-        R.stalled = done[s] == 2;
-        R.fp64_from = first_fp64;
-        R.nnzb_x = p->nnzb;
-    }
+    // systems still running at max_iter
+    for (int32_t sid : act) done[sid] = 3;
+    if (!act.empty()) retire(std::vector<char>(act.size(), 1), nullptr);
     DBG_CK(cudaStreamSynchronize(st));
     const double ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     bool all_conv = true;

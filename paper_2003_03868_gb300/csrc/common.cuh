@@ -54,6 +54,10 @@ extern std::atomic<int64_t> g_launches;
 cudaMemPool_t library_pool();
 // Waits for the device, then returns cached pool memory above keep_bytes to the driver.
 void trim_pool(uint64_t keep_bytes);
+// Stream-ordered allocation from library_pool().  When the device is out of memory the
+// cached free memory is returned to the driver (after the device is idle) and the
+// allocation is tried once more; a second failure throws DBCSR_ENOMEM.
+void pool_alloc(void** p, size_t bytes, cudaStream_t s);
 
 // Device array allocated and freed in stream order from library_pool().
 template <class T>
@@ -80,7 +84,7 @@ struct DBuf {
         release();
         s = stream;
         n = count;
-        if (count > 0) DBG_CK(cudaMallocFromPoolAsync((void**)&p, sizeof(T) * (size_t)count, library_pool(), stream));
+        if (count > 0) pool_alloc((void**)&p, sizeof(T) * (size_t)count, stream);
     }
     void zero() {
         if (n > 0) DBG_CK(cudaMemsetAsync(p, 0, sizeof(T) * (size_t)n, s));

@@ -52,6 +52,22 @@ void trim_pool(uint64_t keep_bytes) {
     DBG_CK(cudaMemPoolTrimTo(pool, (size_t)keep_bytes));
 }
 
+void pool_alloc(void** p, size_t bytes, cudaStream_t s) {
+    cudaMemPool_t pool = library_pool();
+    cudaError_t e = cudaMallocFromPoolAsync(p, bytes, pool, s);
+    if (e == cudaErrorMemoryAllocation) {
+        (void)cudaGetLastError();
+        DBG_CK(cudaDeviceSynchronize());
+        DBG_CK(cudaMemPoolTrimTo(pool, 0));
+        e = cudaMallocFromPoolAsync(p, bytes, pool, s);
+    }
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        fail(e == cudaErrorMemoryAllocation ? DBCSR_ENOMEM : DBCSR_ECUDA,
+             std::string("device allocation of ") + std::to_string(bytes) + " bytes: " + cudaGetErrorString(e));
+    }
+}
+
 HostScalars::HostScalars() {
     DBG_CK(cudaMallocHost((void**)&i, kCap * sizeof(int64_t)));
     DBG_CK(cudaMallocHost((void**)&d, 64 * sizeof(double)));

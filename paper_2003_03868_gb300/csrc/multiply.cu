@@ -466,20 +466,28 @@ __device__ __forceinline__ ProdMeta fetch_meta(const SmmArgs& S, int64_t base, i
 // lanes first fetch the metadata of 32 products at once (one product each:
 // block offsets and inner size) and broadcast it with shuffles, so the
 // dependent index loads are not paid product by product.
-template <int E>
+template <int E, bool PAIR>
 __global__ void __launch_bounds__(256) k_smm_f64(int64_t nlist, const int64_t* __restrict__ list, SmmArgs S) {
-    const int lane = threadIdx.x & 31;
-    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < nlist; w += warps) {
+    // PAIR: two warps (neighbours in the CTA) share one C block, each owning half of its
+    // element slots, so a large block needs half the registers per thread; the halves'
+    // norm sums meet in shared memory behind a 64-thread named barrier of the pair.
+    constexpr int EL = PAIR ? (E + 1) / 2 : E;
+    __shared__ double sh_part[PAIR ? 4 : 1][2][2];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int part = PAIR ? (warp & 1) : 0, pair = PAIR ? (warp >> 1) : warp;
+    const int per_cta = PAIR ? (blockDim.x >> 6) : (blockDim.x >> 5);
+    const int64_t stride = (int64_t)gridDim.x * per_cta;
+    int parity = 0;
+    for (int64_t w = (int64_t)blockIdx.x * per_cta + pair; w < nlist; w += stride, parity ^= 1) {
         const int64_t k = list[w];
         const int I = S.f_row[k], J = S.f_col[k];
         const int m = S.bs[I], n = S.bs[J];
         const int mn = m * n;
-        int ii[E], jj[E];
-        double acc[E];
+        int ii[EL], jj[EL];
+        double acc[EL];
 #pragma unroll
-        for (int e = 0; e < E; ++e) {
-            const int idx = lane + 32 * e;
+        for (int e = 0; e < EL; ++e) {
+            const int idx = lane + 32 * (part * EL + e);
             int i = 0, j = 0;
             if (idx < mn) elem_of(idx, m, n, S.colmajor, i, j);
             ii[e] = i;
@@ -500,7 +508,7 @@ __global__ void __launch_bounds__(256) k_smm_f64(int64_t nlist, const int64_t* _
                 const double* __restrict__ B = S.b_data + boq;
                 for (int t = 0; t < kk; ++t) {
 #pragma unroll
-                    for (int e = 0; e < E; ++e)
+                    for (int e = 0; e < EL; ++e)
                         acc[e] = fma(__ldg(A + ii[e] * kk + t), __ldg(B + t * n + jj[e]), acc[e]);
                 }
             }
@@ -511,8 +519,8 @@ __global__ void __launch_bounds__(256) k_smm_f64(int64_t nlist, const int64_t* _
         double* out = S.c_data + S.f_off[k];
         double sq = 0.0, d = 0.0;
 #pragma unroll
-        for (int e = 0; e < E; ++e) {
-            const int idx = lane + 32 * e;
+        for (int e = 0; e < EL; ++e) {
+            const int idx = lane + 32 * (part * EL + e);
             if (idx < mn) {
                 const int pos = ii[e] * n + jj[e];
                 double v = S.alpha * acc[e];
@@ -528,7 +536,21 @@ __global__ void __launch_bounds__(256) k_smm_f64(int64_t nlist, const int64_t* _
             sq += __shfl_xor_sync(0xffffffffu, sq, o);
             d += __shfl_xor_sync(0xffffffffu, d, o);
         }
-        if (lane == 0) {
+        if (PAIR) {
+            // slot parity alternates, so one barrier per block suffices: the second half
+            // can rewrite this slot only after passing the next block's barrier, which the
+            // first half reaches after reading it
+            if (part == 1 && lane == 0) {
+                sh_part[pair][parity][0] = sq;
+                sh_part[pair][parity][1] = d;
+            }
+            asm volatile("bar.sync %0, 64;" ::"r"(1 + pair) : "memory");
+            if (part == 0 && lane == 0) {
+                sq += sh_part[pair][parity][0];
+                d += sh_part[pair][parity][1];
+            }
+        }
+        if (part == 0 && lane == 0) {
             S.c_norm[k] = sqrt(sq);
             S.c_dev2[k] = d;
         }
@@ -648,11 +670,17 @@ __global__ void k_class_scatter(int64_t nform, const int32_t* __restrict__ flag,
 
 using SmmKernel = void (*)(int64_t, const int64_t*, SmmArgs);
 
+// Classes with at least kPairMinE element slots per lane run as warp pairs (PAIR) when
+// the CTA holds whole pairs: 23x23 blocks (E = 17) need 164 registers per thread on one
+// warp and left 5.5 warps per SM with the FP64 pipe 62% busy.
+constexpr int kPairMinE = 6;
 template <int... Es>
 struct SmmTable {
-    static SmmKernel get(int e) {
-        SmmKernel t[] = {nullptr, &k_smm_f64<Es>...};
-        return (e >= 1 && e <= (int)sizeof...(Es)) ? t[e] : nullptr;
+    static SmmKernel get(int e, bool pair) {
+        SmmKernel t[] = {nullptr, &k_smm_f64<Es, false>...};
+        SmmKernel tp[] = {nullptr, &k_smm_f64<Es, (Es >= kPairMinE)>...};
+        if (e < 1 || e > (int)sizeof...(Es)) return nullptr;
+        return pair ? tp[e] : t[e];
     }
 };
 using SmmF64 = SmmTable<1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18, 19, 20, 21, 22, 23, 24, 25,
@@ -668,10 +696,12 @@ struct SmmKsTable {
 using SmmF64Ks1 = SmmKsTable<1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18, 19, 20, 21, 22, 23, 24, 25,
                              26, 27, 28, 29, 30, 31>;
 
-SmmKernel f64_kernel(int cls) {
+// pair: the launch's CTAs hold whole warp pairs (threads per CTA a multiple of 64)
+SmmKernel f64_kernel(int cls, bool pair) {
     if (cls > kF64ClassKs1 && cls < kF64Classes) return SmmF64Ks1::get(cls - kF64ClassKs1);
-    return SmmF64::get(cls);
+    return SmmF64::get(cls, pair);
 }
+bool f64_class_pairs(int cls) { return cls >= kPairMinE && cls <= 32; }
 
 
 // ------------------------------------------------------------ BF16 tensor-core SMM
@@ -695,10 +725,10 @@ __device__ __forceinline__ void mma_bf16(float* c, uint32_t a0, uint32_t a1, uin
 
 struct SmmBf16Args {
     SmmArgs base;
-    const __nv_bfloat16* a16;   // A-role packed blocks, block b at a16 + b * a_stride
-    int64_t a_stride;
-    const __nv_bfloat16* b16;   // B-role packed (transposed) blocks, block b at b16 + b * b_stride
-    int64_t b_stride;
+    const __nv_bfloat16* a16;   // A-role packed blocks, block b at a16 + a_po[b]
+    const int64_t* a_po;
+    const __nv_bfloat16* b16;   // B-role packed (transposed) blocks, block b at b16 + b_po[b]
+    const int64_t* b_po;
     const __nv_bfloat16* a16_lo;   // SPLIT: packed residuals, same layout
     const __nv_bfloat16* b16_lo;
 };
@@ -795,8 +825,8 @@ __global__ void __launch_bounds__(256, (MT * NT <= 2 || MT * NT >= 6) ? 2 : 3) k
             int kq = 0;
             if (lane < cnt) {
                 const int32_t ai = S.prod_a[base + lane], bi = S.prod_b[base + lane];
-                ao = (int64_t)ai * G.a_stride;
-                bo = (int64_t)bi * G.b_stride;
+                ao = G.a_po[ai];
+                bo = G.b_po[bi];
                 kq = S.bs[S.a_col[ai]];
             }
             if (PIPE) {
@@ -928,16 +958,23 @@ __device__ __forceinline__ __nv_bfloat16 f64_to_bf16_rne(double x) {
 // fixed stride: role 0 (A): block (I, K) as a (16 ceil(m/16)) x (16 ceil(k/16))
 // row-major tile; role 1 (B): block (K, J) transposed, as an (8 ceil(n/8)) x
 // (16 ceil(k/16)) tile.  Padding is zero.
+__global__ void k_pack_sizes(int64_t nb, int role, const int32_t* __restrict__ row, const int32_t* __restrict__ col,
+                             const int32_t* __restrict__ bs, int64_t* __restrict__ sz) {
+    for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nb; b += (int64_t)gridDim.x * blockDim.x)
+        sz[b] = pack_size(role, bs[row[b]], bs[col[b]]);
+}
+
 __global__ void k_pack_bf16(int64_t nb, int role, const int32_t* __restrict__ row, const int32_t* __restrict__ col,
                             const int32_t* __restrict__ bs, const int64_t* __restrict__ off,
-                            const double* __restrict__ data, int64_t stride, __nv_bfloat16* __restrict__ out,
-                            __nv_bfloat16* __restrict__ out_lo) {
+                            const double* __restrict__ data, const int64_t* __restrict__ po,
+                            __nv_bfloat16* __restrict__ out, __nv_bfloat16* __restrict__ out_lo) {
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t b = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); b < nb; b += warps) {
         const int r_sz = bs[row[b]], c_sz = bs[col[b]];         // the block is r_sz x c_sz, row-major
         const double* x = data + off[b];
-        __nv_bfloat16* o = out + b * stride;
+        __nv_bfloat16* o = out + po[b];
+        __nv_bfloat16* ol = out_lo ? out_lo + po[b] : nullptr;
         if (role == 0) {                                         // A: m = r_sz rows, k = c_sz columns
             const int R = 16 * ((r_sz + 15) / 16), L = 16 * ((c_sz + 15) / 16);
             for (int e = lane; e < R * L; e += 32) {
@@ -945,7 +982,7 @@ __global__ void k_pack_bf16(int64_t nb, int role, const int32_t* __restrict__ ro
                 const double v = (i < r_sz && t < c_sz) ? x[i * c_sz + t] : 0.0;
                 const __nv_bfloat16 hi = f64_to_bf16_rne(v);
                 o[e] = hi;
-                if (out_lo) out_lo[b * stride + e] = f64_to_bf16_rne(v - (double)__bfloat162float(hi));
+                if (ol) ol[e] = f64_to_bf16_rne(v - (double)__bfloat162float(hi));
             }
         } else {                                                 // B: k = r_sz rows, n = c_sz columns, stored n x k
             const int R = 8 * ((c_sz + 7) / 8), L = 16 * ((r_sz + 15) / 16);
@@ -954,7 +991,7 @@ __global__ void k_pack_bf16(int64_t nb, int role, const int32_t* __restrict__ ro
                 const double v = (j < c_sz && t < r_sz) ? x[t * c_sz + j] : 0.0;
                 const __nv_bfloat16 hi = f64_to_bf16_rne(v);
                 o[e] = hi;
-                if (out_lo) out_lo[b * stride + e] = f64_to_bf16_rne(v - (double)__bfloat162float(hi));
+                if (ol) ol[e] = f64_to_bf16_rne(v - (double)__bfloat162float(hi));
             }
         }
     }
@@ -995,12 +1032,6 @@ __global__ void k_keep_twinned(int64_t nb, const int64_t* __restrict__ mirror, i
 
 }  // namespace
 
-// Largest packed tile of a role for blocks of edge <= maxbs.
-int64_t pack_stride(int role, int maxbs) {
-    const int64_t L = 16 * ((maxbs + 15) / 16);
-    return role == 0 ? 16 * ((maxbs + 15) / 16) * L : 8 * ((maxbs + 7) / 8) * L;
-}
-
 TuneCfg default_cfg(int prec) {
     TuneCfg c;
     if (prec == DBCSR_BF16) {
@@ -1022,17 +1053,19 @@ void launch_smm_shape(int prec, int m, int n, int64_t cnt, const int64_t* list, 
         if (split && (!pk.a16_lo || !pk.b16_lo)) fail(DBCSR_EINVAL, "multiply: split BF16 needs the residual packs");
         SmmBf16Kernel kern = bf16_kernel(((m + 15) / 16 - 1) * 4 + (n + 7) / 8, split);
         if (!kern) fail(DBCSR_ECAPACITY, "multiply: block shape beyond the BF16 kernel table");
-        SmmBf16Args ga{sa, pk.a16, pk.a_stride, pk.b16, pk.b_stride, pk.a16_lo, pk.b16_lo};
+        SmmBf16Args ga{sa, pk.a16, pk.a_po, pk.b16, pk.b_po, pk.a16_lo, pk.b16_lo};
         kern<<<(unsigned)grid, cfg.tpb, 0, s>>>(cnt, list, ga);
     } else {
         const int mn = m * n;
         const int cls = (mn > 32 && (mn & 31) == 1) ? kF64ClassKs1 + (mn >> 5) : (mn + 31) >> 5;
-        SmmKernel kern = f64_kernel(cls);
+        const bool pair = f64_class_pairs(cls) && cfg.tpb % 64 == 0;
+        SmmKernel kern = f64_kernel(cls, pair);
         if (!kern) fail(DBCSR_ECAPACITY, "multiply: block shape beyond the kernel table");
         SmmArgs a = sa;
         a.colmajor = cfg.colmajor;
         a.prefetch2 = cfg.prefetch2;
-        kern<<<(unsigned)grid, cfg.tpb, 0, s>>>(cnt, list, a);
+        const int64_t g = pair ? std::min<int64_t>(ceil_div(cnt, wpc / 2), (int64_t)152 * cfg.ctas_per_sm) : grid;
+        kern<<<(unsigned)g, cfg.tpb, 0, s>>>(cnt, list, a);
     }
     DBG_LAUNCH_CK();
 }
@@ -1246,32 +1279,52 @@ void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbc
                 at += cnt;
             }
         DBuf<__nv_bfloat16> a16, b16, a16_lo, b16_lo;
+        DBuf<int64_t> a_psz, a_po, b_psz, b_po;
         Bf16Packs pk{};
         if (bf16) {
             // operands rounded to BF16 (nearest even) once per product, into fragment-ready copies
-            // (and, for split products, the rounded residuals x - hi)
+            // (and, for split products, the rounded residuals x - hi); every block takes its own
+            // padded tile, placed by a prefix sum of the tile sizes
             const bool split = prec == DBCSR_BF16X3;
-            const int maxbs = *std::max_element(A->h_bs.begin(), A->h_bs.end());
-            pk.a_stride = pack_stride(0, maxbs);
-            pk.b_stride = pack_stride(1, maxbs);
-            a16.alloc(std::max<int64_t>(A->nnzb, 1) * pk.a_stride, s);
-            b16.alloc(std::max<int64_t>(B->nnzb, 1) * pk.b_stride, s);
+            a_psz.alloc(std::max<int64_t>(A->nnzb, 1), s);
+            a_po.alloc(A->nnzb + 1, s);
+            b_psz.alloc(std::max<int64_t>(B->nnzb, 1), s);
+            b_po.alloc(B->nnzb + 1, s);
+            if (A->nnzb) {
+                k_pack_sizes<<<grid_for(A->nnzb, 256), 256, 0, s>>>(A->nnzb, 0, A->row.p, A->col.p, A->bs.p, a_psz.p);
+                DBG_LAUNCH_CK();
+            }
+            if (B->nnzb) {
+                k_pack_sizes<<<grid_for(B->nnzb, 256), 256, 0, s>>>(B->nnzb, 1, B->row.p, B->col.p, B->bs.p, b_psz.p);
+                DBG_LAUNCH_CK();
+            }
+            scan_exclusive(a_psz.p, a_po.p, A->nnzb, s);
+            scan_exclusive(b_psz.p, b_po.p, B->nnzb, s);
+            int64_t tot[2];
+            {
+                const int64_t* src[2] = {a_po.p + A->nnzb, b_po.p + B->nnzb};
+                read_i64s(src, 2, tot, s);
+            }
+            a16.alloc(std::max<int64_t>(tot[0], 1), s);
+            b16.alloc(std::max<int64_t>(tot[1], 1), s);
             if (split) {
-                a16_lo.alloc(std::max<int64_t>(A->nnzb, 1) * pk.a_stride, s);
-                b16_lo.alloc(std::max<int64_t>(B->nnzb, 1) * pk.b_stride, s);
+                a16_lo.alloc(std::max<int64_t>(tot[0], 1), s);
+                b16_lo.alloc(std::max<int64_t>(tot[1], 1), s);
             }
             if (A->nnzb) {
                 k_pack_bf16<<<grid_for(A->nnzb, 8), 256, 0, s>>>(A->nnzb, 0, A->row.p, A->col.p, A->bs.p, A->off.p,
-                                                                 A->data.p, pk.a_stride, a16.p, a16_lo.p);
+                                                                 A->data.p, a_po.p, a16.p, a16_lo.p);
                 DBG_LAUNCH_CK();
             }
             if (B->nnzb) {
                 k_pack_bf16<<<grid_for(B->nnzb, 8), 256, 0, s>>>(B->nnzb, 1, B->row.p, B->col.p, B->bs.p, B->off.p,
-                                                                 B->data.p, pk.b_stride, b16.p, b16_lo.p);
+                                                                 B->data.p, b_po.p, b16.p, b16_lo.p);
                 DBG_LAUNCH_CK();
             }
             pk.a16 = a16.p;
+            pk.a_po = a_po.p;
             pk.b16 = b16.p;
+            pk.b_po = b_po.p;
             pk.a16_lo = a16_lo.p;
             pk.b16_lo = b16_lo.p;
         }

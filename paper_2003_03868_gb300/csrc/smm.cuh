@@ -45,18 +45,23 @@ std::vector<TuneCfg> tune_space(int prec);
 void mlp_features(int prec, int m, int n, int k, const TuneCfg& c, float* f);
 
 // Fragment-ready BF16 copies of the operands (BF16 products only): block b of A
-// at a16 + b * a_stride (m x k padded to 16-multiples), block b of B transposed at
-// b16 + b * b_stride (n x k padded to 8 x 16-multiples).
+// at a16 + a_po[b] (m x k padded to 16-multiples), block b of B transposed at
+// b16 + b_po[b] (n x k padded to 8 x 16-multiples).  Each block takes its own
+// padded size, so mixed block sizes waste no slots.
 struct Bf16Packs {
     const __nv_bfloat16* a16 = nullptr;
-    int64_t a_stride = 0;
+    const int64_t* a_po = nullptr;
     const __nv_bfloat16* b16 = nullptr;
-    int64_t b_stride = 0;
-    const __nv_bfloat16* a16_lo = nullptr;   // DBCSR_BF16X3: the residuals lo = bf16(x - hi)
+    const int64_t* b_po = nullptr;
+    const __nv_bfloat16* a16_lo = nullptr;   // DBCSR_BF16X3: the residuals lo = bf16(x - hi), same offsets
     const __nv_bfloat16* b16_lo = nullptr;
 };
 inline bool is_bf16(int prec) { return prec == DBCSR_BF16 || prec == DBCSR_BF16X3; }
-int64_t pack_stride(int role, int maxbs);
+// Packed tile size (elements) of an r x c block in a role (0: A, m x k; 1: B, k x n stored n x k).
+__host__ __device__ inline int64_t pack_size(int role, int r, int c) {
+    return role == 0 ? (int64_t)(16 * ((r + 15) / 16)) * (16 * ((c + 15) / 16))
+                     : (int64_t)(8 * ((c + 7) / 8)) * (16 * ((r + 15) / 16));
+}
 
 // Launches the kernel of shape (m, n) over the cnt blocks listed in list.
 void launch_smm_shape(int prec, int m, int n, int64_t cnt, const int64_t* list, const SmmArgs& sa,

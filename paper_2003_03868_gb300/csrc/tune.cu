@@ -85,6 +85,11 @@ __global__ void k_pack_synth(int64_t nblk, int role, int r_sz, int c_sz, const d
     }
 }
 
+__global__ void k_stride_offsets(int64_t n, int64_t stride, int64_t* __restrict__ out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = i * stride;
+}
+
 // A synthetic (m, n, k) stack resident on the device.
 struct SynthStack {
     int m, n, k;
@@ -92,7 +97,7 @@ struct SynthStack {
     DBuf<double> a, b, c, norm, dev2;
     DBuf<__nv_bfloat16> a16, b16;
     DBuf<int32_t> prod_a, prod_b, a_col, f_row, f_col, bs;
-    DBuf<int64_t> a_off, b_off, f_off, f_pbeg, f_cin, list;
+    DBuf<int64_t> a_off, b_off, f_off, f_pbeg, f_cin, list, a_po, b_po;
     SmmArgs args{};
     Bf16Packs pk{};
 
@@ -127,17 +132,24 @@ struct SynthStack {
             a_col.p, f_row.p, f_col.p, f_off.p, f_pbeg.p, f_cin.p, list.p);
         DBG_LAUNCH_CK();
         if (bf16) {
-            const int maxbs = std::max(m, std::max(n, k));
-            pk.a_stride = pack_stride(0, maxbs);
-            pk.b_stride = pack_stride(1, maxbs);
-            a16.alloc((int64_t)kPool * pk.a_stride, s);
-            b16.alloc((int64_t)kPool * pk.b_stride, s);
-            k_pack_synth<<<grid_for(a16.n, 256, 152 * 64), 256, 0, s>>>(kPool, 0, m, k, a.p, pk.a_stride, a16.p);
+            // every pool block has the same shape: tiles at a fixed stride
+            const int64_t sa = pack_size(0, m, k), sb = pack_size(1, k, n);
+            a16.alloc((int64_t)kPool * sa, s);
+            b16.alloc((int64_t)kPool * sb, s);
+            a_po.alloc(kPool + 1, s);
+            b_po.alloc(kPool + 1, s);
+            k_stride_offsets<<<grid_for(kPool + 1, 256), 256, 0, s>>>(kPool + 1, sa, a_po.p);
             DBG_LAUNCH_CK();
-            k_pack_synth<<<grid_for(b16.n, 256, 152 * 64), 256, 0, s>>>(kPool, 1, k, n, b.p, pk.b_stride, b16.p);
+            k_stride_offsets<<<grid_for(kPool + 1, 256), 256, 0, s>>>(kPool + 1, sb, b_po.p);
+            DBG_LAUNCH_CK();
+            k_pack_synth<<<grid_for(a16.n, 256, 152 * 64), 256, 0, s>>>(kPool, 0, m, k, a.p, sa, a16.p);
+            DBG_LAUNCH_CK();
+            k_pack_synth<<<grid_for(b16.n, 256, 152 * 64), 256, 0, s>>>(kPool, 1, k, n, b.p, sb, b16.p);
             DBG_LAUNCH_CK();
             pk.a16 = a16.p;
+            pk.a_po = a_po.p;
             pk.b16 = b16.p;
+            pk.b_po = b_po.p;
             pk.a16_lo = a16.p;      // timing only: the residual packs may alias the leading ones
             pk.b16_lo = b16.p;
         }

@@ -53,13 +53,35 @@ def test_batch_matches_oracle_per_system(gb, prec):
 
 
 def test_batch_equals_single_system_runs(gb):
+    # the systems finish at different steps and leave the batch one after another; every
+    # block product of a system is the same sum in the same order as in its own run, so
+    # the FP64 density matrices agree bit for bit
     hs = _systems(5, 23)
     Hs = [gb.Matrix.of(h.H) for h in hs]
-    Ps, reps, st = gb.sign_iterate_batched(Hs, [0.0] * len(hs), 1e-7, 1e-9)
-    for h, H, r in zip(hs, Hs, reps):
-        g = gb.sign_iterate(H, 0.0, 1e-7, 1e-9)
+    # mu near a band edge (the gap is [-0.25, 0.25]) slows a system down
+    mus = [0.0, 0.2, 0.0, -0.22, 0.1]
+    Ps, reps, st = gb.sign_iterate_batched(Hs, mus, 1e-7, 1e-9)
+    its = set()
+    for h, H, P, r, mu in zip(hs, Hs, Ps, reps, mus):
+        g = gb.sign_iterate(H, mu, 1e-7, 1e-9)
         assert abs(r.e_band - g.report.e_band) / h.n_atoms < 1e-9
         assert r.iterations == g.report.iterations
+        its.add(r.iterations)
+        for a, b in zip(P.export(), g.P.export()):
+            assert np.array_equal(a, b)
+    assert len(its) > 1
+
+
+def test_batch_stopped_by_max_iter(gb):
+    hs = _systems(3, 31)
+    Hs = [gb.Matrix.of(h.H) for h in hs]
+    Ps, reps, st = gb.sign_iterate_batched(Hs, [0.0] * len(hs), 1e-7, 1e-12, max_iter=3)
+    assert st == gb._ffi.DBCSR_ENOTCONV
+    for h, H, P, r in zip(hs, Hs, Ps, reps):
+        assert r.iterations == 3 and not r.converged and not r.stalled
+        g = gb.sign_iterate(H, 0.0, 1e-7, 1e-12, max_iter=3)
+        for a, b in zip(P.export(), g.P.export()):
+            assert np.array_equal(a, b)
 
 
 def test_batch_of_one_and_different_mu(gb):
