@@ -35,7 +35,7 @@ FALLBACK_BF16_BURST, FALLBACK_BF16_SUSTAINED = 1900.0, 1700.0
 # averaged over the 84 k_smm_f64 launches of one sign-1024h2o step, from one ncu capture of
 # the current kernels (profiles/k_smm_f64_traffic_sign1024h2o.md).  Set to None when the
 # kernels change.
-SMM_F64_TRAFFIC = {"sign-1024h2o-dzvp-fp64": 2.8191e9}
+SMM_F64_TRAFFIC = {}
 
 
 def bf16_peak():
@@ -207,6 +207,118 @@ def run_batch(args, gb, synth, torch, barrier):
     return 0
 
 
+def run_predictor(args, gb, synth, torch, barrier):
+    """Learned launch configurations on the 20,736-water mixed sign iteration (O/H = 23/7,
+    N = 767,232): the MLP is trained on autotuner timings of triples drawn from {4..32}^3
+    (the workload's own triples held out), predicts configurations for the workload's
+    block shapes, and the mixed iteration runs with the default, the predicted and the
+    exhaustively tuned configurations."""
+    import numpy as np
+    w = synth.SIGN_20736 if args.predictor_waters == synth.SIGN_20736.n_mol else synth.Workload(
+        f"sign-{args.predictor_waters}h2o-23-7-mixed", args.predictor_waters, (23, 7), synth.configs.BASE_SEED + 14,
+        1e-6, 1e-8, 1e-4)
+    bo, bh = w.basis
+    target = [(m, n, max(w.basis)) for m in (bo, bh) for n in (bo, bh)]
+    rng = np.random.default_rng(20736)
+    train = []
+    while len(train) < args.train_triples:
+        t = tuple(int(v) for v in rng.integers(4, 33, 3))
+        if t not in target and t not in train:
+            train.append(t)
+    precs = {"fp64": gb.DBCSR_FP64, "bf16x3": gb.DBCSR_BF16X3}
+    gb.tune_clear()
+    t0 = time.time()
+    recs_train = {k: gb.autotune(train, p, stack_len=args.tune_stack, reps=3) for k, p in precs.items()}
+    tune_train_s = time.time() - t0
+    models, mlp_rep = {}, {}
+    for k, p in precs.items():
+        models[k], rep = gb.train_predictor(recs_train[k], p)
+        mlp_rep[k] = {"loss_first": rep.loss_first, "loss_last": rep.loss_last, "ms": rep.ms,
+                      "samples": len(recs_train[k])}
+    pred = {k: gb.mlp_predict_best(models[k], target, p) for k, p in precs.items()}
+    gb.tune_clear()
+    t0 = time.time()
+    recs_target = {k: gb.autotune(target, p, stack_len=args.tune_stack, reps=3) for k, p in precs.items()}
+    tune_target_s = time.time() - t0
+    best = {k: {t: gb.tune_get(p, *t)[0] for t in target} for k, p in precs.items()}
+    gb.tune_clear()
+    default = {k: gb.tune_get(p, 1, 1, 1)[0] for k, p in precs.items()}
+
+    def key(c):
+        return (c.tpb, c.ctas_per_sm, c.colmajor, c.prefetch2)
+
+    # synthetic-stack time of the predicted and default configurations relative to the best
+    ratios = {}
+    for k in precs:
+        rs = []
+        for t, c in zip(target, pred[k]):
+            tm = {key(r.cfg): r.ms for r in recs_target[k] if (r.m, r.n, r.k) == t}
+            bt = min(tm.values())
+            rs.append({"mnk": list(t), "predicted_over_best": tm[key(c)] / bt,
+                       "default_over_best": tm[key(default[k])] / bt})
+        ratios[k] = rs
+
+    h = synth.build_hamiltonian(w)
+    stream = torch.cuda.current_stream()
+    H = gb.Matrix.of(h.H, stream=stream.cuda_stream)
+
+    def install(which):
+        gb.tune_clear()
+        if which == "default":
+            return
+        for k, p in precs.items():
+            for t, c in zip(target, pred[k]) if which == "mlp" else best[k].items():
+                gb.tune_set(p, *t, c)
+
+    def timed(prec):
+        for _ in range(args.warmup):
+            gb.sign_iterate(H, h.mu, w.eps_filter, w.tol, prec=prec, switch_tol=w.switch)
+        barrier()
+        l0 = gb.lib().dbcsr_launch_count()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fl = 0.0
+        for _ in range(args.steps):
+            r = gb.sign_iterate(H, h.mu, w.eps_filter, w.tol, prec=prec, switch_tol=w.switch)
+            fl += r.report.flops
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        return {"time_to_p_ms": ms, "gpu_launches": gb.lib().dbcsr_launch_count() - l0, "tflops": fl / args.steps / (ms * 1e-3) / 1e12, "iterations": r.report.iterations,
+                "fp64_from_step": r.report.fp64_from, "converged": bool(r.report.converged),
+                "stalled": bool(r.report.stalled), "e_band": r.report.e_band, "trace_p": r.report.trace_p,
+                "ms_low": r.report.ms_low, "ms_multiply": r.report.ms_multiply}
+
+    clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
+    runs = {}
+    for which in ("default", "mlp", "exhaustive"):
+        install(which)
+        runs[which] = timed(gb.DBCSR_MIXED)
+    install("exhaustive")
+    fp64 = timed(gb.DBCSR_FP64)
+    clk = clocks.stop()
+    for v in runs.values():
+        v["de_band_per_atom_vs_fp64"] = abs(v["e_band"] - fp64["e_band"]) / h.n_atoms
+    out = {"metric": "block-GEMM TFLOP/s (mixed sign iteration, MLP-predicted launch configurations)",
+           "value": runs["mlp"]["tflops"], "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": runs["mlp"]["time_to_p_ms"], "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3 then f64", "data": "synthetic",
+           "config": {"workload": w.name, "n_mol": w.n_mol, "N": w.n, "blocks": {"O": bo, "H": bh},
+                      "eps_filter": w.eps_filter, "tol": w.tol, "switch": w.switch,
+                      "l2": "inputs larger than L2 (H alone is %.0f MB)" % (h.H.data.nbytes / 1e6)},
+           "runs": runs, "fp64_exhaustive": fp64,
+           "mlp_over_exhaustive_time": runs["mlp"]["time_to_p_ms"] / runs["exhaustive"]["time_to_p_ms"],
+           "default_over_exhaustive_time": runs["default"]["time_to_p_ms"] / runs["exhaustive"]["time_to_p_ms"],
+           "mixed_speedup_vs_fp64": fp64["time_to_p_ms"] / runs["mlp"]["time_to_p_ms"],
+           "synthetic_ratios": ratios, "mlp": mlp_rep,
+           "tuning": {"train_triples": len(train), "stack_len": args.tune_stack, "train_s": tune_train_s,
+                      "target_s": tune_target_s},
+           "clocks": clk, "gpu_launches": runs["mlp"]["gpu_launches"]}
+    print(json.dumps(out))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -219,10 +331,15 @@ def main():
     ap.add_argument("--ref-steps", type=int, default=1, help="Newton-Schulz steps per oracle sample (reference arm)")
     ap.add_argument("--cpu-steps", type=int, default=2, help="Newton-Schulz steps in the oracle CPU baseline")
     ap.add_argument("--workload", default="sign-1024h2o",
-                    choices=["sign-1024h2o", "sign-512h2o", "sign-512h2o-23-7", "sign-4096h2o", "batch-64"],
+                    choices=["sign-1024h2o", "sign-512h2o", "sign-512h2o-23-7", "sign-4096h2o", "batch-64",
+                             "sign-20736h2o-mlp"],
                     help="sign-512h2o, sign-512h2o-23-7: smaller cases for profiler captures; sign-4096h2o: "
                          "4,096 waters with O/H blocks 23/7 (FP64 and mixed); batch-64: 64 uneven systems "
-                         "batched vs one by one")
+                         "batched vs one by one; sign-20736h2o-mlp: the mixed iteration on 20,736 waters with "
+                         "default, MLP-predicted and exhaustively tuned launch configurations")
+    ap.add_argument("--train-triples", type=int, default=48, help="sign-20736h2o-mlp: autotuned training triples")
+    ap.add_argument("--tune-stack", type=int, default=500000, help="products of the autotuner's synthetic stacks")
+    ap.add_argument("--predictor-waters", type=int, default=20736, help="sign-20736h2o-mlp: waters of the system")
     ap.add_argument("--verbose", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -258,6 +375,8 @@ def main():
 
     if args.workload == "batch-64":
         return run_batch(args, gb, synth, torch, barrier)
+    if args.workload == "sign-20736h2o-mlp":
+        return run_predictor(args, gb, synth, torch, barrier)
     w = {"sign-1024h2o": synth.SIGN_1024, "sign-4096h2o": synth.SIGN_4096,
          "sign-512h2o": synth.Workload("sign-512h2o-dzvp-fp64", 512, (13, 5), synth.configs.BASE_SEED + 12, 1e-7, 1e-9),
          "sign-512h2o-23-7": synth.Workload("sign-512h2o-23-7", 512, (23, 7), synth.configs.BASE_SEED + 13, 1e-6, 1e-8,

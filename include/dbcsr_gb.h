@@ -284,8 +284,11 @@ dbcsr_status dbcsr_tune_space(int32_t prec, dbcsr_kernel_cfg* out, int32_t cap, 
  * Autotuner (section "Batched execution": kernels are tuned per (m, n, k) over
  * their parameters and the best parameter set kept).  For each triple
  * mnk[3t..3t+2] (each in [1, 32]) a synthetic stack of stack_len products is
- * built on the device (C blocks of ~27 products, A/B blocks drawn from pools of
- * 20,000), every configuration of dbcsr_tune_space is launched reps times
+ * built on the device, imitating one shape launch of a real product: C blocks of
+ * 32 products, A/B blocks drawn at random from pools of about 512 MB together
+ * (several times the L2).  Real launches hold 1e4 to 1e6 C blocks, so stack_len
+ * of 5e5 or more gives timings that carry over.  Every configuration of
+ * dbcsr_tune_space is launched reps times
  * (median taken) and the fastest becomes the tuned entry (prec, m, n, k) that
  * dbcsr_multiply uses for its m x n blocks when the largest block edge of the
  * matrix is k.  Up to cap timings go to recs (may be NULL); *nrec = their total.

@@ -259,7 +259,7 @@ def tune_space(prec: int = DBCSR_FP64):
     return list(arr)
 
 
-def autotune(triples, prec: int = DBCSR_FP64, stack_len: int = 100000, reps: int = 5):
+def autotune(triples, prec: int = DBCSR_FP64, stack_len: int = 500000, reps: int = 5):
     """Times every configuration on a synthetic stack per (m, n, k); the fastest
     enters the tune table.  Returns the list of TuneRecord timings."""
     t = np.ascontiguousarray(np.asarray(triples, dtype=np.int32).reshape(-1, 3))
@@ -271,7 +271,7 @@ def autotune(triples, prec: int = DBCSR_FP64, stack_len: int = 100000, reps: int
     return list(recs)[:n.value]
 
 
-def time_configs(m: int, n: int, k: int, cfgs, prec: int = DBCSR_FP64, stack_len: int = 100000, reps: int = 5):
+def time_configs(m: int, n: int, k: int, cfgs, prec: int = DBCSR_FP64, stack_len: int = 500000, reps: int = 5):
     """Median launch time (ms) of each configuration on the synthetic (m, n, k) stack."""
     arr = (KernelCfg * len(cfgs))(*cfgs)
     out = np.zeros(len(cfgs))
@@ -350,6 +350,23 @@ def mlp_train(params, X, T, epochs: int = 2000, lr: float = 1e-3, beta1: float =
     _check(lib().dbcsr_mlp_train(int(X.shape[1]), _ptr(p), _ptr(X), _ptr(T), int(X.shape[0]), C.byref(o),
                                  C.byref(r)), "mlp_train")
     return p, r
+
+
+def train_predictor(recs, prec: int = DBCSR_FP64, epochs: int = 3000, lr: float = 2e-3, seed: int = 3):
+    """Trains the prediction MLP on autotuner records (TuneRecord list) of one precision.
+
+    Target: the log launch time, centred per (m, n, k) triple and scaled to unit variance,
+    so the model learns how the configuration changes the time of a triple.  Returns
+    (params, MlpReport)."""
+    tri = [(r.m, r.n, r.k) for r in recs]
+    X = mlp_features(tri, [r.cfg for r in recs], prec)
+    y = np.log(np.array([r.ms for r in recs]))
+    mean = {}
+    for t in set(tri):
+        mean[t] = float(np.mean([yy for tt, yy in zip(tri, y) if tt == t]))
+    T = np.array([yy - mean[t] for t, yy in zip(tri, y)])
+    T = (T / max(T.std(), 1e-12)).astype(np.float32)
+    return mlp_train(mlp_init(MLP_FEATURES, seed=seed), X, T, epochs=epochs, lr=lr)
 
 
 def mlp_predict_best(params, triples, prec: int = DBCSR_FP64):

@@ -24,8 +24,17 @@ namespace {
 std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int, int>, TuneCfg> g_tune;
 
-constexpr int kPool = 20000;
-constexpr int kProductsPerC = 27;
+// The synthetic stack imitates one shape launch of a sign-iteration product: operand
+// pools several times larger than L2 (kPoolBytes for A and B together, so products
+// miss in L2 as real ones do), C blocks of kProductsPerC products each (one metadata
+// batch), and products that draw their A and B blocks at random from the pools.
+constexpr int64_t kPoolMin = 20000;
+constexpr int64_t kPoolBytes = 512ll << 20;
+constexpr int kProductsPerC = 32;
+
+int64_t pool_blocks(int m, int n, int k) {
+    return std::max<int64_t>(kPoolMin, kPoolBytes / (8 * ((int64_t)m * k + (int64_t)k * n)));
+}
 
 __device__ __forceinline__ uint64_t mix(uint64_t z) {
     z += 0x9E3779B97F4A7C15ull;
@@ -39,17 +48,17 @@ __global__ void k_fill_uniform(int64_t n, uint64_t seed, double* __restrict__ x)
         x[i] = (double)(mix(seed ^ (uint64_t)i) >> 11) * (2.0 / 9007199254740992.0) - 1.0;
 }
 
-__global__ void k_fill_stack_synth(int64_t nprod, int64_t nc, uint64_t seed, int m, int n, int k,
+__global__ void k_fill_stack_synth(int64_t nprod, int64_t nc, int64_t npool, uint64_t seed, int m, int n, int k,
                                    int32_t* __restrict__ prod_a, int32_t* __restrict__ prod_b,
                                    int64_t* __restrict__ a_off, int64_t* __restrict__ b_off, int32_t* __restrict__ a_col,
                                    int32_t* __restrict__ f_row, int32_t* __restrict__ f_col, int64_t* __restrict__ f_off,
                                    int64_t* __restrict__ f_pbeg, int64_t* __restrict__ f_cin, int64_t* __restrict__ list) {
     const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t p = tid; p < nprod; p += stride) {
-        prod_a[p] = (int32_t)(mix(seed + 2 * (uint64_t)p) % kPool);
-        prod_b[p] = (int32_t)(mix(seed + 2 * (uint64_t)p + 1) % kPool);
+        prod_a[p] = (int32_t)(mix(seed + 2 * (uint64_t)p) % (uint64_t)npool);
+        prod_b[p] = (int32_t)(mix(seed + 2 * (uint64_t)p + 1) % (uint64_t)npool);
     }
-    for (int64_t i = tid; i < kPool; i += stride) {
+    for (int64_t i = tid; i < npool; i += stride) {
         a_off[i] = i * (int64_t)m * k;
         b_off[i] = i * (int64_t)k * n;
         a_col[i] = 2;                     // block size table {m, n, k}: K blocks have edge k
@@ -93,7 +102,7 @@ __global__ void k_stride_offsets(int64_t n, int64_t stride, int64_t* __restrict_
 // A synthetic (m, n, k) stack resident on the device.
 struct SynthStack {
     int m, n, k;
-    int64_t nprod, nc;
+    int64_t nprod, nc, npool;
     DBuf<double> a, b, c, norm, dev2;
     DBuf<__nv_bfloat16> a16, b16;
     DBuf<int32_t> prod_a, prod_b, a_col, f_row, f_col, bs;
@@ -103,20 +112,21 @@ struct SynthStack {
 
     SynthStack(int m_, int n_, int k_, int64_t stack_len, bool bf16, cudaStream_t s) : m(m_), n(n_), k(k_) {
         nprod = stack_len;
+        npool = pool_blocks(m, n, k);
         nc = ceil_div(stack_len, kProductsPerC);
-        a.alloc((int64_t)kPool * m * k, s);
-        b.alloc((int64_t)kPool * k * n, s);
+        a.alloc(npool * m * k, s);
+        b.alloc(npool * k * n, s);
         c.alloc(nc * m * n, s);
         norm.alloc(nc, s);
         dev2.alloc(nc, s);
         prod_a.alloc(nprod, s);
         prod_b.alloc(nprod, s);
-        a_col.alloc(kPool, s);
+        a_col.alloc(npool, s);
         f_row.alloc(nc, s);
         f_col.alloc(nc, s);
         bs.alloc(3, s);
-        a_off.alloc(kPool, s);
-        b_off.alloc(kPool, s);
+        a_off.alloc(npool, s);
+        b_off.alloc(npool, s);
         f_off.alloc(nc, s);
         f_pbeg.alloc(nc + 1, s);
         f_cin.alloc(nc, s);
@@ -127,24 +137,24 @@ struct SynthStack {
         DBG_LAUNCH_CK();
         k_fill_uniform<<<grid_for(b.n, 256), 256, 0, s>>>(b.n, 0x5A5Aull + (uint64_t)n * 977 + k, b.p);
         DBG_LAUNCH_CK();
-        k_fill_stack_synth<<<grid_for(std::max<int64_t>(nprod, kPool), 256), 256, 0, s>>>(
-            nprod, nc, 0x1234ull + (uint64_t)(m * 10000 + n * 100 + k), m, n, k, prod_a.p, prod_b.p, a_off.p, b_off.p,
+        k_fill_stack_synth<<<grid_for(std::max<int64_t>(nprod, npool), 256), 256, 0, s>>>(
+            nprod, nc, npool, 0x1234ull + (uint64_t)(m * 10000 + n * 100 + k), m, n, k, prod_a.p, prod_b.p, a_off.p, b_off.p,
             a_col.p, f_row.p, f_col.p, f_off.p, f_pbeg.p, f_cin.p, list.p);
         DBG_LAUNCH_CK();
         if (bf16) {
             // every pool block has the same shape: tiles at a fixed stride
             const int64_t sa = pack_size(0, m, k), sb = pack_size(1, k, n);
-            a16.alloc((int64_t)kPool * sa, s);
-            b16.alloc((int64_t)kPool * sb, s);
-            a_po.alloc(kPool + 1, s);
-            b_po.alloc(kPool + 1, s);
-            k_stride_offsets<<<grid_for(kPool + 1, 256), 256, 0, s>>>(kPool + 1, sa, a_po.p);
+            a16.alloc(npool * sa, s);
+            b16.alloc(npool * sb, s);
+            a_po.alloc(npool + 1, s);
+            b_po.alloc(npool + 1, s);
+            k_stride_offsets<<<grid_for(npool + 1, 256), 256, 0, s>>>(npool + 1, sa, a_po.p);
             DBG_LAUNCH_CK();
-            k_stride_offsets<<<grid_for(kPool + 1, 256), 256, 0, s>>>(kPool + 1, sb, b_po.p);
+            k_stride_offsets<<<grid_for(npool + 1, 256), 256, 0, s>>>(npool + 1, sb, b_po.p);
             DBG_LAUNCH_CK();
-            k_pack_synth<<<grid_for(a16.n, 256, 152 * 64), 256, 0, s>>>(kPool, 0, m, k, a.p, sa, a16.p);
+            k_pack_synth<<<grid_for(a16.n, 256, 152 * 64), 256, 0, s>>>(npool, 0, m, k, a.p, sa, a16.p);
             DBG_LAUNCH_CK();
-            k_pack_synth<<<grid_for(b16.n, 256, 152 * 64), 256, 0, s>>>(kPool, 1, k, n, b.p, sb, b16.p);
+            k_pack_synth<<<grid_for(b16.n, 256, 152 * 64), 256, 0, s>>>(npool, 1, k, n, b.p, sb, b16.p);
             DBG_LAUNCH_CK();
             pk.a16 = a16.p;
             pk.a_po = a_po.p;
