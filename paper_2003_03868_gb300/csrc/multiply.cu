@@ -407,28 +407,52 @@ __global__ void k_fill_stack(int32_t nblk, RowPattern P, int nwords, FillArgs F)
     __shared__ int sh_scan[32];
     uint32_t* bm = smem;
     int* wpre = (int*)(smem + nwords);
-    int32_t* sh_cur = (int32_t*)(smem + 2 * nwords);
+    // use_smem: per candidate of the row, its stack base (-1 if not formed) and cursor
+    int64_t* sh_base = (int64_t*)(smem + 2 * ((nwords + 1) & ~1));
     for (int32_t I = blockIdx.x; I < nblk; I += gridDim.x) {
         const int nc = build_row(P, I, bm, wpre, nwords, sh_scan);
         const int64_t cb = F.coff[I];
-        const int64_t kb = F.kidx[cb];
-        const int nk = (int)(F.kidx[cb + nc] - kb);
-        int32_t* cur = F.use_smem ? sh_cur : F.cursor + kb;
-        for (int r = threadIdx.x; r < nk; r += blockDim.x) cur[r] = 0;
-        __syncthreads();
-        for (int64_t p = P.a_rp[I]; p < P.a_rp[I + 1]; ++p) {
-            const int32_t K = P.a_col[p];
-            for (int64_t q = P.b_rp[K] + threadIdx.x; q < P.b_rp[K + 1]; q += blockDim.x) {
-                const int64_t c = cb + rank_of(bm, wpre, P.b_col[q]);
-                if (!F.keep[c]) continue;
-                const int64_t k = F.kidx[c];
-                const int32_t at = cur[k - kb];
-                cur[k - kb] = at + 1;
-                const int64_t pos = F.pbeg[k] + at;
-                F.prod_a[pos] = (int32_t)p;
-                F.prod_b[pos] = (int32_t)q;
+        if (F.use_smem) {
+            int32_t* cur = (int32_t*)(sh_base + nc);
+            for (int r = threadIdx.x; r < nc; r += blockDim.x) {
+                const int64_t c = cb + r;
+                sh_base[r] = F.keep[c] ? F.pbeg[F.kidx[c]] : -1;
+                cur[r] = 0;
             }
             __syncthreads();
+            for (int64_t p = P.a_rp[I]; p < P.a_rp[I + 1]; ++p) {
+                const int32_t K = P.a_col[p];
+                for (int64_t q = P.b_rp[K] + threadIdx.x; q < P.b_rp[K + 1]; q += blockDim.x) {
+                    const int r = rank_of(bm, wpre, P.b_col[q]);
+                    const int64_t b0 = sh_base[r];
+                    if (b0 < 0) continue;
+                    const int32_t at = cur[r];
+                    cur[r] = at + 1;
+                    F.prod_a[b0 + at] = (int32_t)p;
+                    F.prod_b[b0 + at] = (int32_t)q;
+                }
+                __syncthreads();
+            }
+        } else {
+            const int64_t kb = F.kidx[cb];
+            const int nk = (int)(F.kidx[cb + nc] - kb);
+            int32_t* cur = F.cursor + kb;
+            for (int r = threadIdx.x; r < nk; r += blockDim.x) cur[r] = 0;
+            __syncthreads();
+            for (int64_t p = P.a_rp[I]; p < P.a_rp[I + 1]; ++p) {
+                const int32_t K = P.a_col[p];
+                for (int64_t q = P.b_rp[K] + threadIdx.x; q < P.b_rp[K + 1]; q += blockDim.x) {
+                    const int64_t c = cb + rank_of(bm, wpre, P.b_col[q]);
+                    if (!F.keep[c]) continue;
+                    const int64_t k = F.kidx[c];
+                    const int32_t at = cur[k - kb];
+                    cur[k - kb] = at + 1;
+                    const int64_t pos = F.pbeg[k] + at;
+                    F.prod_a[pos] = (int32_t)p;
+                    F.prod_b[pos] = (int32_t)q;
+                }
+                __syncthreads();
+            }
         }
     }
 }
@@ -1231,7 +1255,7 @@ void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbc
     DBuf<int32_t> prod_a, prod_b, cursor;
     prod_a.alloc(std::max<int64_t>(nprod, 1), s);
     prod_b.alloc(std::max<int64_t>(nprod, 1), s);
-    const size_t sm_fill = sm_rank + (size_t)max_row * sizeof(int32_t);
+    const size_t sm_fill = sm_rank + (size_t)max_row * (sizeof(int64_t) + sizeof(int32_t));
     const bool fill_smem = sm_fill <= (size_t)kSymSmemBudget;
     if (!fill_smem) cursor.alloc(nf1, s);
     if (nprod) {
