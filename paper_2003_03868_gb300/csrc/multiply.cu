@@ -731,14 +731,35 @@ bool f64_class_pairs(int cls) { return cls >= kPairMinE && cls <= 32; }
 // ------------------------------------------------------------ BF16 tensor-core SMM
 // BF16 operands (rounded to nearest even from FP64), FP32 accumulation on the
 // tensor cores (mma.sync m16n8k16), FP64 epilogue.  Before the products, every
-// block is packed once into a fragment-ready copy: an A-role copy of block
-// (I, K) holds its m x k values in a zero-padded (16 MT) x (16 KT) row-major tile
-// and a B-role copy of block (K, J) holds its transpose, n x k, in a zero-padded
-// (8 NT) x (16 KT) tile.  Each block sits at a fixed stride, so a product's
+// block is packed once into fragment order: an A-role copy of block (I, K) holds its
+// m x k values as MT x KT zero-padded 16 x 16 sub-tiles, each stored as the four
+// 32-bit A registers of lane 0, then of lane 1, ... (512 B); a B-role copy of block
+// (K, J) holds NT x KT zero-padded 16 (k) x 8 (n) sub-tiles as the two B registers of
+// each lane (256 B).  A lane thus fetches its A fragment with one 128-bit load and
+// its B fragment with one 64-bit load, and a warp's load is one contiguous, aligned
+// run of 512 or 256 bytes.  Blocks sit at prefix-summed offsets, so a product's
 // operands are found from its block index alone.  One warp owns one C block
-// (m <= 16 MT, n <= 8 NT) and, per product, loads its A and B fragments with
-// aligned 32-bit loads straight from the packed copies and issues KT x MT x NT
-// MMAs -- no shared-memory staging.  Zero padding adds nothing to the sums.
+// (m <= 16 MT, n <= 8 NT) and issues KT x MT x NT MMAs per product -- no
+// shared-memory staging.  Zero padding adds nothing to the sums.
+//
+// Register layout of m16n8k16 (gid = lane / 4, tig = lane % 4): A register j holds
+// A[gid + 8 (j & 1)][2 tig + 8 (j >> 1) + {0, 1}]; B register j holds
+// B[2 tig + 8 j + {0, 1}][gid].
+__host__ __device__ __forceinline__ int64_t frag_index_a(int KT, int i, int t) {
+    // element (i, t) of an A-role block (row i < 16 MT, column t < 16 KT)
+    const int mt = i >> 4, kt = t >> 4, ii = i & 15, tt = t & 15;
+    const int lane = (ii & 7) * 4 + ((tt & 7) >> 1);
+    const int j = (ii >> 3) | ((tt >> 3) << 1);
+    return ((int64_t)(mt * KT + kt) * 32 + lane) * 8 + j * 2 + (tt & 1);
+}
+__host__ __device__ __forceinline__ int64_t frag_index_b(int KT, int t, int c) {
+    // element (t, c) of a B-role block (row t < 16 KT along k, column c < 8 NT along n)
+    const int nt = c >> 3, kt = t >> 4, cc = c & 7, tt = t & 15;
+    const int lane = cc * 4 + ((tt & 7) >> 1);
+    const int j = tt >> 3;
+    return ((int64_t)(nt * KT + kt) * 32 + lane) * 4 + j * 2 + (tt & 1);
+}
+
 __device__ __forceinline__ void mma_bf16(float* c, uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t b0,
                                          uint32_t b1) {
     asm volatile(
@@ -757,81 +778,65 @@ struct SmmBf16Args {
     const __nv_bfloat16* b16_lo;
 };
 
-// Register fragments of one 16-wide k-slice of one block product: MT 16-row tiles of A,
-// NT 8-column tiles of B (and their residuals for SPLIT), loaded straight from the
-// fragment-ready packed copies.
-template <int MT, int NT, bool SPLIT>
-struct BfFrag {
-    uint32_t a[MT][4], b[NT][2];
-    uint32_t al[SPLIT ? MT : 1][4], bl[SPLIT ? NT : 1][2];
+// One pipeline stage of a warp: the fragments of one unit (a product's 16-wide k-slice)
+// as each lane's own bytes -- MT A sub-tiles (16 B per lane each), NT B sub-tiles (8 B per
+// lane each), then the same for the residuals when SPLIT.
+__host__ __device__ constexpr int bf16_stage_bytes(int MT, int NT, bool split) {
+    return (MT * 512 + NT * 256) * (split ? 2 : 1);
+}
+// Units in flight per warp: as many stages as fit in 12 KB, between 2 and 8.
+__host__ __device__ constexpr int bf16_stages(int MT, int NT, bool split) {
+    return 12288 / bf16_stage_bytes(MT, NT, split) < 2 ? 2
+           : (12288 / bf16_stage_bytes(MT, NT, split) > 8 ? 8 : 12288 / bf16_stage_bytes(MT, NT, split));
+}
 
-    __device__ __forceinline__ void load(const SmmBf16Args& G, int64_t aoq, int64_t boq, int KT, int kt, int gid,
-                                         int tig) {
-        const int h = 8 * KT;                                 // 32-bit words per packed row (16 KT bf16)
-        const int c0 = kt * 8 + tig;                          // word of columns (16 kt + 2 tig, +1)
-        const uint32_t* __restrict__ Ap = reinterpret_cast<const uint32_t*>(G.a16 + aoq);
-        const uint32_t* __restrict__ Bp = reinterpret_cast<const uint32_t*>(G.b16 + boq);
-#pragma unroll
-        for (int nt = 0; nt < NT; ++nt) {
-            const int row = (nt * 8 + gid) * h;
-            b[nt][0] = __ldg(Bp + row + c0);
-            b[nt][1] = __ldg(Bp + row + c0 + 4);
-        }
-#pragma unroll
-        for (int mt = 0; mt < MT; ++mt) {
-            const int r0 = (mt * 16 + gid) * h, r1 = r0 + 8 * h;
-            a[mt][0] = __ldg(Ap + r0 + c0);
-            a[mt][1] = __ldg(Ap + r1 + c0);
-            a[mt][2] = __ldg(Ap + r0 + c0 + 4);
-            a[mt][3] = __ldg(Ap + r1 + c0 + 4);
-        }
-        if (SPLIT) {
-            const uint32_t* __restrict__ Apl = reinterpret_cast<const uint32_t*>(G.a16_lo + aoq);
-            const uint32_t* __restrict__ Bpl = reinterpret_cast<const uint32_t*>(G.b16_lo + boq);
-#pragma unroll
-            for (int nt = 0; nt < NT; ++nt) {
-                const int row = (nt * 8 + gid) * h;
-                bl[SPLIT ? nt : 0][0] = __ldg(Bpl + row + c0);
-                bl[SPLIT ? nt : 0][1] = __ldg(Bpl + row + c0 + 4);
-            }
-#pragma unroll
-            for (int mt = 0; mt < MT; ++mt) {
-                const int r0 = (mt * 16 + gid) * h, r1 = r0 + 8 * h;
-                al[SPLIT ? mt : 0][0] = __ldg(Apl + r0 + c0);
-                al[SPLIT ? mt : 0][1] = __ldg(Apl + r1 + c0);
-                al[SPLIT ? mt : 0][2] = __ldg(Apl + r0 + c0 + 4);
-                al[SPLIT ? mt : 0][3] = __ldg(Apl + r1 + c0 + 4);
-            }
-        }
-    }
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async8(uint32_t dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
-    __device__ __forceinline__ void mma(float (&acc)[MT][NT][4]) const {
-#pragma unroll
-        for (int mt = 0; mt < MT; ++mt) {
-#pragma unroll
-            for (int nt = 0; nt < NT; ++nt) mma_bf16(acc[mt][nt], a[mt][0], a[mt][1], a[mt][2], a[mt][3], b[nt][0], b[nt][1]);
-            if (SPLIT) {
-#pragma unroll
-                for (int nt = 0; nt < NT; ++nt) {
-                    mma_bf16(acc[mt][nt], a[mt][0], a[mt][1], a[mt][2], a[mt][3], bl[SPLIT ? nt : 0][0],
-                             bl[SPLIT ? nt : 0][1]);
-                    mma_bf16(acc[mt][nt], al[SPLIT ? mt : 0][0], al[SPLIT ? mt : 0][1], al[SPLIT ? mt : 0][2],
-                             al[SPLIT ? mt : 0][3], b[nt][0], b[nt][1]);
-                }
-            }
-        }
-    }
+// Product metadata of 32 consecutive stack entries, one per lane: packed-tile offsets of
+// its A and B blocks and its inner size k.
+struct BfMeta {
+    int64_t ao, bo;
+    int kq;
 };
+__device__ __forceinline__ BfMeta bf_meta(const SmmBf16Args& G, int64_t base, int64_t pe, int lane) {
+    BfMeta m{0, 0, 0};
+    if (base + lane < pe) {
+        const int32_t ai = G.base.prod_a[base + lane], bi = G.base.prod_b[base + lane];
+        m.ao = G.a_po[ai];
+        m.bo = G.b_po[bi];
+        m.kq = G.base.bs[G.base.a_col[ai]];
+    }
+    return m;
+}
 
 // SPLIT (DBCSR_BF16X3): operands x = hi + lo, both BF16; per fragment set three MMAs
 // accumulate hi*hi + hi*lo + lo*hi in FP32 (the lo*lo term, ~2^-16 relative, is left out).
+//
+// Each warp streams its C block's units (product q, k-slice kt) through a ring of S
+// shared-memory stages: the fragments of unit u + S - 1 are copied with cp.async while
+// unit u is multiplied, so up to S - 1 units' loads are in flight per warp.  A lane copies
+// only the bytes of its own fragments and reads only those back, so the per-thread
+// cp.async group waits are the only synchronisation.  Every accumulator sees its MMAs in
+// the order (q, kt, hi*hi, hi*lo, lo*hi).
 template <int MT, int NT, bool SPLIT>
-__global__ void __launch_bounds__(256, (MT * NT <= 2 || MT * NT >= 6) ? 2 : 3) k_smm_bf16(int64_t nlist, const int64_t* __restrict__ list, SmmBf16Args G) {
-    constexpr bool PIPE = MT * NT <= 2;
+__global__ void __launch_bounds__(256, 2) k_smm_bf16(int64_t nlist, const int64_t* __restrict__ list, SmmBf16Args G) {
+    constexpr int SB = bf16_stage_bytes(MT, NT, SPLIT), NS = bf16_stages(MT, NT, SPLIT);
+    constexpr int A_OFF_LO = MT * 512 + NT * 256, B_OFF = MT * 512;
+    extern __shared__ __align__(16) unsigned char bf_smem[];
     const SmmArgs& S = G.base;
-    const int lane = threadIdx.x & 31, gid = lane >> 2, tig = lane & 3;
+    const int lane = threadIdx.x & 31, gid = lane >> 2, tig = lane & 3, warp = threadIdx.x >> 5;
+    const uint32_t ring = (uint32_t)__cvta_generic_to_shared(bf_smem) + (uint32_t)(warp * NS * SB);
+    const unsigned char* ring_ptr = bf_smem + warp * NS * SB;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < nlist; w += warps) {
+    for (int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; w < nlist; w += warps) {
         const int64_t k = list[w];
         const int I = S.f_row[k], J = S.f_col[k];
         const int m = S.bs[I], n = S.bs[J];
@@ -843,62 +848,106 @@ __global__ void __launch_bounds__(256, (MT * NT <= 2 || MT * NT >= 6) ? 2 : 3) k
 #pragma unroll
                 for (int i = 0; i < 4; ++i) acc[mt][nt][i] = 0.f;
         const int64_t pb = S.f_pbeg[k], pe = S.f_pbeg[k + 1];
-        for (int64_t base = pb; base < pe; base += 32) {
-            const int cnt = (int)min((int64_t)32, pe - base);
-            int64_t ao = 0, bo = 0;
-            int kq = 0;
-            if (lane < cnt) {
-                const int32_t ai = S.prod_a[base + lane], bi = S.prod_b[base + lane];
-                ao = G.a_po[ai];
-                bo = G.b_po[bi];
-                kq = S.bs[S.a_col[ai]];
-            }
-            if (PIPE) {
-                // Software pipeline over the batch's units (product q, 16-wide k-slice kt): the
-                // fragments of the next unit are loaded before the MMAs of the current one.
-                // Every accumulator still sees its MMAs in the order (q, kt, hi*hi, hi*lo, lo*hi).
-                BfFrag<MT, NT, SPLIT> cur, nxt;
-                int q = 0, kt = 0;
-                int64_t aoq = __shfl_sync(0xffffffffu, ao, 0), boq = __shfl_sync(0xffffffffu, bo, 0);
-                int KT = (__shfl_sync(0xffffffffu, kq, 0) + 15) >> 4;
-                cur.load(G, aoq, boq, KT, kt, gid, tig);
-                while (true) {
-                    int nq = q, nkt = kt + 1, nKT = KT;
-                    int64_t naoq = aoq, nboq = boq;
-                    if (nkt == KT) {
-                        nq = q + 1;
-                        nkt = 0;
-                        if (nq < cnt) {                                 // warp-uniform
-                            naoq = __shfl_sync(0xffffffffu, ao, nq);
-                            nboq = __shfl_sync(0xffffffffu, bo, nq);
-                            nKT = (__shfl_sync(0xffffffffu, kq, nq) + 15) >> 4;
-                        }
-                    }
-                    const bool more = nq < cnt;
-                    if (more) nxt.load(G, naoq, nboq, nKT, nkt, gid, tig);
-                    cur.mma(acc);
-                    if (!more) break;
-                    cur = nxt;
-                    q = nq;
-                    kt = nkt;
-                    KT = nKT;
-                    aoq = naoq;
-                    boq = nboq;
+        const int64_t np = pe - pb;
+        // metadata of the consumer's batch (cur) and the next one (nxt); the producer runs at
+        // most NS - 1 < 32 units ahead, so it never needs a later batch
+        BfMeta cur = bf_meta(G, pb, pe, lane), nxt = bf_meta(G, pb + 32, pe, lane);
+        int64_t cbat = 0;                       // consumer's batch index
+        int64_t pp = 0;                         // producer: product index (from pb) and k-slice
+        int ktp = 0, slot_p = 0;
+        auto produce = [&]() {
+            if (pp < np) {
+                const bool in_cur = (pp >> 5) == cbat;
+                const int src = (int)(pp & 31);
+                const int64_t ao = __shfl_sync(0xffffffffu, in_cur ? cur.ao : nxt.ao, src);
+                const int64_t bo = __shfl_sync(0xffffffffu, in_cur ? cur.bo : nxt.bo, src);
+                const int KT = (__shfl_sync(0xffffffffu, in_cur ? cur.kq : nxt.kq, src) + 15) >> 4;
+                const uint32_t st = ring + (uint32_t)(slot_p * SB);
+                const unsigned char* ag = reinterpret_cast<const unsigned char*>(G.a16 + ao);
+                const unsigned char* bg = reinterpret_cast<const unsigned char*>(G.b16 + bo);
+#pragma unroll
+                for (int mt = 0; mt < MT; ++mt) cp_async16(st + mt * 512 + lane * 16, ag + ((mt * KT + ktp) * 32 + lane) * 16);
+#pragma unroll
+                for (int nt = 0; nt < NT; ++nt)
+                    cp_async8(st + B_OFF + nt * 256 + lane * 8, bg + ((nt * KT + ktp) * 32 + lane) * 8);
+                if (SPLIT) {
+                    const unsigned char* agl = reinterpret_cast<const unsigned char*>(G.a16_lo + ao);
+                    const unsigned char* bgl = reinterpret_cast<const unsigned char*>(G.b16_lo + bo);
+#pragma unroll
+                    for (int mt = 0; mt < MT; ++mt)
+                        cp_async16(st + A_OFF_LO + mt * 512 + lane * 16, agl + ((mt * KT + ktp) * 32 + lane) * 16);
+#pragma unroll
+                    for (int nt = 0; nt < NT; ++nt)
+                        cp_async8(st + A_OFF_LO + B_OFF + nt * 256 + lane * 8,
+                                  bgl + ((nt * KT + ktp) * 32 + lane) * 8);
                 }
-            } else {
-                // larger fragment sets: one unit in flight per warp, more warps per SM
-                for (int q = 0; q < cnt; ++q) {
-                    const int64_t aoq = __shfl_sync(0xffffffffu, ao, q);
-                    const int64_t boq = __shfl_sync(0xffffffffu, bo, q);
-                    const int KT = (__shfl_sync(0xffffffffu, kq, q) + 15) >> 4;
-                    for (int kt = 0; kt < KT; ++kt) {
-                        BfFrag<MT, NT, SPLIT> f;
-                        f.load(G, aoq, boq, KT, kt, gid, tig);
-                        f.mma(acc);
+                if (++ktp == KT) {
+                    ktp = 0;
+                    ++pp;
+                }
+            }
+            cp_async_commit();                  // one group per call, empty past the end
+            slot_p = (slot_p + 1 == NS) ? 0 : slot_p + 1;
+        };
+#pragma unroll
+        for (int i = 0; i < NS - 1; ++i) produce();
+        int64_t pc = 0;                         // consumer: product index and k-slice
+        int ktc = 0, slot_c = 0;
+        while (pc < np) {
+            produce();
+            cp_async_wait<NS - 1>();            // this lane's copies of the consumer's unit have landed
+            const unsigned char* sp = ring_ptr + slot_c * SB;
+            uint32_t a[MT][4], b[NT][2], al[SPLIT ? MT : 1][4], bl[SPLIT ? NT : 1][2];
+#pragma unroll
+            for (int mt = 0; mt < MT; ++mt) {
+                const uint4 v = *reinterpret_cast<const uint4*>(sp + mt * 512 + lane * 16);
+                a[mt][0] = v.x; a[mt][1] = v.y; a[mt][2] = v.z; a[mt][3] = v.w;
+            }
+#pragma unroll
+            for (int nt = 0; nt < NT; ++nt) {
+                const uint2 v = *reinterpret_cast<const uint2*>(sp + B_OFF + nt * 256 + lane * 8);
+                b[nt][0] = v.x; b[nt][1] = v.y;
+            }
+            if (SPLIT) {
+#pragma unroll
+                for (int mt = 0; mt < MT; ++mt) {
+                    const uint4 v = *reinterpret_cast<const uint4*>(sp + A_OFF_LO + mt * 512 + lane * 16);
+                    al[SPLIT ? mt : 0][0] = v.x; al[SPLIT ? mt : 0][1] = v.y;
+                    al[SPLIT ? mt : 0][2] = v.z; al[SPLIT ? mt : 0][3] = v.w;
+                }
+#pragma unroll
+                for (int nt = 0; nt < NT; ++nt) {
+                    const uint2 v = *reinterpret_cast<const uint2*>(sp + A_OFF_LO + B_OFF + nt * 256 + lane * 8);
+                    bl[SPLIT ? nt : 0][0] = v.x; bl[SPLIT ? nt : 0][1] = v.y;
+                }
+            }
+#pragma unroll
+            for (int mt = 0; mt < MT; ++mt) {
+#pragma unroll
+                for (int nt = 0; nt < NT; ++nt) mma_bf16(acc[mt][nt], a[mt][0], a[mt][1], a[mt][2], a[mt][3], b[nt][0], b[nt][1]);
+                if (SPLIT) {
+#pragma unroll
+                    for (int nt = 0; nt < NT; ++nt) {
+                        mma_bf16(acc[mt][nt], a[mt][0], a[mt][1], a[mt][2], a[mt][3], bl[SPLIT ? nt : 0][0],
+                                 bl[SPLIT ? nt : 0][1]);
+                        mma_bf16(acc[mt][nt], al[SPLIT ? mt : 0][0], al[SPLIT ? mt : 0][1], al[SPLIT ? mt : 0][2],
+                                 al[SPLIT ? mt : 0][3], b[nt][0], b[nt][1]);
                     }
+                }
+            }
+            slot_c = (slot_c + 1 == NS) ? 0 : slot_c + 1;
+            const int KTc = (__shfl_sync(0xffffffffu, cur.kq, (int)(pc & 31)) + 15) >> 4;
+            if (++ktc == KTc) {
+                ktc = 0;
+                ++pc;
+                if ((pc & 31) == 0 && pc < np) {  // the consumer enters the next batch
+                    ++cbat;
+                    cur = nxt;
+                    nxt = bf_meta(G, pb + (cbat + 1) * 32, pe, lane);
                 }
             }
         }
+        cp_async_wait<0>();                     // the empty trailing groups
         // epilogue in FP64
         const int64_t ci = S.f_cin[k];
         const double* cin = ci >= 0 ? S.ci_data + S.ci_off[ci] : nullptr;
@@ -1000,22 +1049,24 @@ __global__ void k_pack_bf16(int64_t nb, int role, const int32_t* __restrict__ ro
         __nv_bfloat16* o = out + po[b];
         __nv_bfloat16* ol = out_lo ? out_lo + po[b] : nullptr;
         if (role == 0) {                                         // A: m = r_sz rows, k = c_sz columns
-            const int R = 16 * ((r_sz + 15) / 16), L = 16 * ((c_sz + 15) / 16);
+            const int R = 16 * ((r_sz + 15) / 16), L = 16 * ((c_sz + 15) / 16), KT = L / 16;
             for (int e = lane; e < R * L; e += 32) {
                 const int i = e / L, t = e - i * L;
                 const double v = (i < r_sz && t < c_sz) ? x[i * c_sz + t] : 0.0;
                 const __nv_bfloat16 hi = f64_to_bf16_rne(v);
-                o[e] = hi;
-                if (ol) ol[e] = f64_to_bf16_rne(v - (double)__bfloat162float(hi));
+                const int64_t d = frag_index_a(KT, i, t);
+                o[d] = hi;
+                if (ol) ol[d] = f64_to_bf16_rne(v - (double)__bfloat162float(hi));
             }
-        } else {                                                 // B: k = r_sz rows, n = c_sz columns, stored n x k
-            const int R = 8 * ((c_sz + 7) / 8), L = 16 * ((r_sz + 15) / 16);
+        } else {                                                 // B: k = r_sz rows, n = c_sz columns
+            const int R = 16 * ((r_sz + 15) / 16), L = 8 * ((c_sz + 7) / 8), KT = R / 16;
             for (int e = lane; e < R * L; e += 32) {
-                const int j = e / L, t = e - j * L;
-                const double v = (j < c_sz && t < r_sz) ? x[t * c_sz + j] : 0.0;
+                const int t = e / L, c = e - t * L;
+                const double v = (t < r_sz && c < c_sz) ? x[t * c_sz + c] : 0.0;
                 const __nv_bfloat16 hi = f64_to_bf16_rne(v);
-                o[e] = hi;
-                if (ol) ol[e] = f64_to_bf16_rne(v - (double)__bfloat162float(hi));
+                const int64_t d = frag_index_b(KT, t, c);
+                o[d] = hi;
+                if (ol) ol[d] = f64_to_bf16_rne(v - (double)__bfloat162float(hi));
             }
         }
     }
@@ -1075,10 +1126,15 @@ void launch_smm_shape(int prec, int m, int n, int64_t cnt, const int64_t* list, 
     if (is_bf16(prec)) {
         const bool split = prec == DBCSR_BF16X3;
         if (split && (!pk.a16_lo || !pk.b16_lo)) fail(DBCSR_EINVAL, "multiply: split BF16 needs the residual packs");
-        SmmBf16Kernel kern = bf16_kernel(((m + 15) / 16 - 1) * 4 + (n + 7) / 8, split);
+        const int mt = (m + 15) / 16, nt = (n + 7) / 8;
+        SmmBf16Kernel kern = bf16_kernel((mt - 1) * 4 + nt, split);
         if (!kern) fail(DBCSR_ECAPACITY, "multiply: block shape beyond the BF16 kernel table");
         SmmBf16Args ga{sa, pk.a16, pk.a_po, pk.b16, pk.b_po, pk.a16_lo, pk.b16_lo};
-        kern<<<(unsigned)grid, cfg.tpb, 0, s>>>(cnt, list, ga);
+        // the warps' stage rings
+        const size_t smem = (size_t)(cfg.tpb / 32) * bf16_stages(mt, nt, split) * bf16_stage_bytes(mt, nt, split);
+        if (smem > 48 * 1024)
+            DBG_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        kern<<<(unsigned)grid, cfg.tpb, smem, s>>>(cnt, list, ga);
     } else {
         const int mn = m * n;
         const int cls = (mn > 32 && (mn & 31) == 1) ? kF64ClassKs1 + (mn >> 5) : (mn + 31) >> 5;

@@ -75,9 +75,10 @@ __global__ void k_fill_stack_synth(int64_t nprod, int64_t nc, int64_t npool, uin
     }
 }
 
-// Packed BF16 pools for timing (rounding mode is irrelevant here): A blocks m x k as
-// (16 ceil(m/16)) x (16 ceil(k/16)) tiles, B blocks k x n transposed as
-// (8 ceil(n/8)) x (16 ceil(k/16)) tiles, zero padded, at the given strides.
+// Packed BF16 pools for timing: A blocks m x k in (16 ceil(m/16)) x (16 ceil(k/16)) tiles,
+// B blocks k x n in (16 ceil(k/16)) x (8 ceil(n/8)) tiles, zero padded, at the given
+// strides.  The element order inside a tile does not matter for timing (the products
+// load whole tiles either way); only the tile sizes and places do.
 __global__ void k_pack_synth(int64_t nblk, int role, int r_sz, int c_sz, const double* __restrict__ in,
                              int64_t stride, __nv_bfloat16* __restrict__ out) {
     const int R = role == 0 ? 16 * ((r_sz + 15) / 16) : 8 * ((c_sz + 7) / 8);
