@@ -205,8 +205,17 @@ dbcsr_status dbcsr_scale_shift(dbcsr_matrix m, double scale, double shift);
  * The sum over K of each C_IJ is taken in ascending K.  C may be the same
  * handle as A and/or B.  The result is formed on the pattern of A*B (union C's
  * pattern when beta != 0) less the candidates that the exact norm-bound
- * prescreen proves would be filtered.  prec: DBCSR_FP64, DBCSR_BF16 or DBCSR_BF16X3.
+ * prescreen proves would be filtered.  prec: DBCSR_FP64, DBCSR_BF16 or DBCSR_BF16X3
+ * (BF16 kinds: the operands are rounded to BF16 once per call; the sums run in FP32 on
+ * the tensor cores; alpha, beta, C_in and the result stay FP64).  The stack of block
+ * products is built on the device (section "Local multiplication": traversal and
+ * generation) and each block shape runs as one batched launch (section "Batched
+ * execution"), with the tuned launch configuration when the tune table has one.
  * stats may be NULL; when given, the call synchronises and fills it.
+ * Errors: EINVAL (null handle, A, B, C with different block sizes, unknown prec,
+ * eps_filter < 0 or NaN), ESTATE (A, B, or C when beta != 0, not finalized), ECAPACITY
+ * (more than 262,144 block rows), ENOMEM (device memory), ECUDA.  On error C is
+ * unchanged unless the failure happened after the new blocks were installed (ECUDA).
  */
 dbcsr_status dbcsr_multiply(double alpha, dbcsr_matrix A, dbcsr_matrix B, double beta, dbcsr_matrix C,
                             double eps_filter, int32_t prec, dbcsr_mult_stats* stats);

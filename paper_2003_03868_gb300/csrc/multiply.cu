@@ -16,9 +16,13 @@
 //                    offsets (prefix sums) and data offsets.
 //  4. k_fill_stack   per row: the product stack (a_blk, b_blk), grouped by C
 //                    block and in ascending K inside each group.
-//  5. k_smm_f64      output-stationary batched small GEMM: one warp owns one C
-//                    block and sums its products in stack order (no atomics);
-//                    the epilogue applies alpha/beta and writes the block norm.
+//  5. k_smm_f64      output-stationary batched small GEMM: one warp (or a pair of
+//                    warps for large blocks) owns one C block and sums its
+//                    products in stack order (no atomics); the epilogue applies
+//                    alpha/beta and writes the block norm.  k_smm_bf16 is the
+//                    tensor-core counterpart (plain or split BF16 operands).
+//     With a symmetric result only the blocks I <= J are computed; k_mirror_copy
+//     copies the others as transposes.
 //  6. filter         blocks with norm < eps dropped (diagonal kept), compaction.
 #include <cuda_bf16.h>
 
@@ -1027,16 +1031,17 @@ __device__ __forceinline__ __nv_bfloat16 f64_to_bf16_rne(double x) {
     return __ushort_as_bfloat16(out);
 }
 
-// Fragment-ready BF16 copies of every block of a matrix (one warp per block), at a
-// fixed stride: role 0 (A): block (I, K) as a (16 ceil(m/16)) x (16 ceil(k/16))
-// row-major tile; role 1 (B): block (K, J) transposed, as an (8 ceil(n/8)) x
-// (16 ceil(k/16)) tile.  Padding is zero.
+// Packed tile size of every block in a role (the offsets are their prefix sum).
 __global__ void k_pack_sizes(int64_t nb, int role, const int32_t* __restrict__ row, const int32_t* __restrict__ col,
                              const int32_t* __restrict__ bs, int64_t* __restrict__ sz) {
     for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nb; b += (int64_t)gridDim.x * blockDim.x)
         sz[b] = pack_size(role, bs[row[b]], bs[col[b]]);
 }
 
+// BF16 copies of every block of a matrix (one warp per block), in mma.sync register order
+// (frag_index_a / frag_index_b), at the prefix-summed offsets po: role 0 (A): block (I, K)
+// as MT x KT sub-tiles of 16 x 16; role 1 (B): block (K, J) as NT x KT sub-tiles of 16 (k) x
+// 8 (n).  Padding is zero.  out_lo (split products): the rounded residuals x - hi.
 __global__ void k_pack_bf16(int64_t nb, int role, const int32_t* __restrict__ row, const int32_t* __restrict__ col,
                             const int32_t* __restrict__ bs, const int64_t* __restrict__ off,
                             const double* __restrict__ data, const int64_t* __restrict__ po,

@@ -5,8 +5,9 @@
 // Here the parameters are launch-time choices that leave the arithmetic
 // unchanged: threads per CTA, CTAs per SM of the grid, the lane-to-element order
 // and double-buffered product metadata (FP64); threads per CTA and CTAs per SM
-// (BF16).  A synthetic stack for (m, n, k) has stack_len products spread over
-// C blocks of ~27 products each, with A and B blocks drawn from pools of 20,000.
+// (BF16).  A synthetic stack for (m, n, k) imitates one shape launch of a real
+// product: stack_len products over C blocks of 32 products each, with A and B blocks
+// drawn at random from pools of about 512 MB together (several times the L2).
 #include <algorithm>
 #include <cstdio>
 #include <fstream>
