@@ -327,15 +327,21 @@ __global__ void k_sym_average(int64_t nform, const int64_t* __restrict__ mirror,
 }
 
 // Work of the blocks that are computed (not mirrored): flops, products, and a
-// histogram by block shape (m, n).
+// histogram by block shape (m, n).  Blocks that are copied or dropped get no product
+// stack (f_np = 0, comp = 0).
 __global__ void k_form_stats(int64_t nform, const int32_t* __restrict__ f_row, const int32_t* __restrict__ f_col,
-                             const int64_t* __restrict__ f_np, const int32_t* __restrict__ f_ksum,
+                             int64_t* __restrict__ f_np, const int32_t* __restrict__ f_ksum,
                              const int64_t* __restrict__ mirror, int sym, const int32_t* __restrict__ bs,
                              unsigned long long* __restrict__ flops, unsigned long long* __restrict__ nprod,
-                             unsigned long long* __restrict__ shape_cnt) {
+                             unsigned long long* __restrict__ shape_cnt, uint8_t* __restrict__ comp) {
     unsigned long long lf = 0, lp = 0;
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nform; k += (int64_t)gridDim.x * blockDim.x) {
-        if (block_role(sym, f_row[k], f_col[k], mirror[k]) != 0) continue;
+        const bool computed = block_role(sym, f_row[k], f_col[k], mirror[k]) == 0;
+        comp[k] = computed ? 1 : 0;
+        if (!computed) {
+            f_np[k] = 0;
+            continue;
+        }
         const int m = bs[f_row[k]], n = bs[f_col[k]];
         lf += 2ull * (unsigned long long)m * (unsigned long long)n * (unsigned long long)f_ksum[k];
         lp += (unsigned long long)f_np[k];
@@ -399,6 +405,7 @@ __global__ void k_form_rp(int32_t nblk, const int64_t* __restrict__ coff, const 
 struct FillArgs {
     const int64_t* coff;
     const int32_t* keep;
+    const uint8_t* comp;     // per formed block: 1 if computed (only those get stack entries)
     const int64_t* kidx;
     const int64_t* pbeg;
     int32_t* cursor;
@@ -420,7 +427,7 @@ __global__ void k_fill_stack(int32_t nblk, RowPattern P, int nwords, FillArgs F)
             int32_t* cur = (int32_t*)(sh_base + nc);
             for (int r = threadIdx.x; r < nc; r += blockDim.x) {
                 const int64_t c = cb + r;
-                sh_base[r] = F.keep[c] ? F.pbeg[F.kidx[c]] : -1;
+                sh_base[r] = (F.keep[c] && F.comp[F.kidx[c]]) ? F.pbeg[F.kidx[c]] : -1;
                 cur[r] = 0;
             }
             __syncthreads();
@@ -449,6 +456,7 @@ __global__ void k_fill_stack(int32_t nblk, RowPattern P, int nwords, FillArgs F)
                     const int64_t c = cb + rank_of(bm, wpre, P.b_col[q]);
                     if (!F.keep[c]) continue;
                     const int64_t k = F.kidx[c];
+                    if (!F.comp[k]) continue;
                     const int32_t at = cur[k - kb];
                     cur[k - kb] = at + 1;
                     const int64_t pos = F.pbeg[k] + at;
@@ -1259,8 +1267,10 @@ void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbc
     // 3. formed-block metadata
     const int64_t nf1 = std::max<int64_t>(nform, 1);
     DBuf<int32_t> f_row, f_col, f_ksum;
+    DBuf<uint8_t> f_comp;                 // 1: the block is computed (0: copied from its twin or dropped)
     DBuf<int64_t> f_area, f_np, f_cin, f_off, f_pbeg, f_rp, flops, nprod_exec, shape_cnt, mirror;
     f_ksum.alloc(nf1, s);
+    f_comp.alloc(nf1, s);
     mirror.alloc(nf1, s);
     nprod_exec.alloc(1, s);
     nprod_exec.zero();
@@ -1296,7 +1306,7 @@ void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbc
                                                           sym_result, A->bs.p,
                                                           (unsigned long long*)flops.p,
                                                           (unsigned long long*)nprod_exec.p,
-                                                          (unsigned long long*)shape_cnt.p);
+                                                          (unsigned long long*)shape_cnt.p, f_comp.p);
         DBG_LAUNCH_CK();
     }
     scan_exclusive(f_area.p, f_off.p, nform, s);
@@ -1320,7 +1330,7 @@ void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbc
     const bool fill_smem = sm_fill <= (size_t)kSymSmemBudget;
     if (!fill_smem) cursor.alloc(nf1, s);
     if (nprod) {
-        FillArgs fa{coff.p, keep.p, kidx.p, f_pbeg.p, cursor.p, prod_a.p, prod_b.p, fill_smem ? 1 : 0};
+        FillArgs fa{coff.p, keep.p, f_comp.p, kidx.p, f_pbeg.p, cursor.p, prod_a.p, prod_b.p, fill_smem ? 1 : 0};
         const size_t sm = fill_smem ? sm_fill : sm_rank;
         if (sm > 48 * 1024) DBG_CK(cudaFuncSetAttribute(k_fill_stack, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         k_fill_stack<<<sym_grid(nblk), kSymThreads, sm, s>>>(nblk, P, nwords, fa);
