@@ -206,6 +206,50 @@ def run_batch(args, gb, synth, torch, barrier):
     return 0
 
 
+def run_mult32(args, gb, synth, torch, barrier):
+    """The single product C = A A of the 32-water decay matrix (N = 736, eps 1e-6): one-off
+    products (stack builder, block products, filter, with their host round trips) against
+    replays of a planned product (one CUDA graph of the numeric phase on fixed patterns)."""
+    w = synth.DECAY_32
+    a = synth.build_decay(w)
+    stream = torch.cuda.current_stream()
+    A = gb.Matrix.of(a, stream=stream.cuda_stream)
+    C1 = gb.Matrix(A.blk_size, stream.cuda_stream)
+    reps = max(20, 50 * args.steps)
+
+    def timed(fn, n):
+        for _ in range(args.warmup):
+            fn()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(n):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / n
+
+    st = gb.multiply(1.0, A, A, 0.0, C1, w.eps_filter)
+    ms_once = timed(lambda: gb.multiply(1.0, A, A, 0.0, C1, w.eps_filter, stats=False), reps)
+    C2 = gb.Matrix(A.blk_size, stream.cuda_stream)
+    plan = gb.Plan(1.0, A, A, C2, w.eps_filter)
+    l0 = gb.lib().dbcsr_launch_count()
+    ms_plan = timed(plan.execute, reps * 10)
+    launches = (gb.lib().dbcsr_launch_count() - l0) // (args.warmup + reps * 10)
+    out = {"metric": "block-GEMM GFLOP/s (single product C = A A, planned and replayed as a CUDA graph)",
+           "value": st.flops / (ms_plan * 1e-3) / 1e9, "unit": "GFLOP/s", "n_gpus": 1, "steps": reps * 10,
+           "warmup": args.warmup, "ms_per_step": ms_plan, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": w.name, "n_mol": w.n_mol, "N": w.n, "blocks": {"O": 13, "H": 5},
+                      "eps_filter": w.eps_filter, "l2": "inputs smaller than L2 (4.3 MB): a launch-bound case"},
+           "flops_per_product": st.flops, "products": st.n_products, "blocks_formed": st.n_formed,
+           "blocks_kept": st.n_kept, "one_off_ms": ms_once, "one_off_gflops": st.flops / (ms_once * 1e-3) / 1e9,
+           "planned_speedup": ms_once / ms_plan, "gpu_launches": launches}
+    plan.close()
+    print(json.dumps(out))
+    return 0
+
+
 def run_predictor(args, gb, synth, torch, barrier):
     """Learned launch configurations on the 20,736-water mixed sign iteration (O/H = 23/7,
     N = 767,232): the MLP is trained on autotuner timings of triples drawn from {4..32}^3
@@ -331,11 +375,12 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=2, help="Newton-Schulz steps in the oracle CPU baseline")
     ap.add_argument("--workload", default="sign-1024h2o",
                     choices=["sign-1024h2o", "sign-512h2o", "sign-512h2o-23-7", "sign-4096h2o", "batch-64",
-                             "sign-20736h2o-mlp"],
+                             "sign-20736h2o-mlp", "mult-32h2o"],
                     help="sign-512h2o, sign-512h2o-23-7: smaller cases for profiler captures; sign-4096h2o: "
                          "4,096 waters with O/H blocks 23/7 (FP64 and mixed); batch-64: 64 uneven systems "
                          "batched vs one by one; sign-20736h2o-mlp: the mixed iteration on 20,736 waters with "
-                         "default, MLP-predicted and exhaustively tuned launch configurations")
+                         "default, MLP-predicted and exhaustively tuned launch configurations; mult-32h2o: the "
+                         "32-water product, one-off vs planned (CUDA graph)")
     ap.add_argument("--train-triples", type=int, default=48, help="sign-20736h2o-mlp: autotuned training triples")
     ap.add_argument("--tune-stack", type=int, default=500000, help="products of the autotuner's synthetic stacks")
     ap.add_argument("--predictor-waters", type=int, default=20736, help="sign-20736h2o-mlp: waters of the system")
@@ -376,6 +421,8 @@ def main():
         return run_batch(args, gb, synth, torch, barrier)
     if args.workload == "sign-20736h2o-mlp":
         return run_predictor(args, gb, synth, torch, barrier)
+    if args.workload == "mult-32h2o":
+        return run_mult32(args, gb, synth, torch, barrier)
     w = {"sign-1024h2o": synth.SIGN_1024, "sign-4096h2o": synth.SIGN_4096,
          "sign-512h2o": synth.Workload("sign-512h2o-dzvp-fp64", 512, (13, 5), synth.configs.BASE_SEED + 12, 1e-7, 1e-9),
          "sign-512h2o-23-7": synth.Workload("sign-512h2o-23-7", 512, (23, 7), synth.configs.BASE_SEED + 13, 1e-6, 1e-8,

@@ -220,6 +220,44 @@ dbcsr_status dbcsr_scale_shift(dbcsr_matrix m, double scale, double shift);
 dbcsr_status dbcsr_multiply(double alpha, dbcsr_matrix A, dbcsr_matrix B, double beta, dbcsr_matrix C,
                             double eps_filter, int32_t prec, dbcsr_mult_stats* stats);
 
+/*
+ * Planned products on fixed patterns (DBCSR's multiply with a retained sparsity, for
+ * repeated products whose patterns do not change, as in an SCF loop).
+ *
+ * dbcsr_multiply_plan computes C = alpha * A * B once, like dbcsr_multiply with beta = 0,
+ * and keeps what its numeric phase needs: the product stacks (built with the norm-bound
+ * prescreen on the current values), the per-shape block lists and, for BF16 kinds, the
+ * packed operands.  C receives the formed pattern; blocks whose norm is below eps_filter
+ * are set to zero instead of removed, so the pattern stays fixed.  The numeric phase
+ * (packing, block products, zeroing) is captured as one CUDA graph.
+ * dbcsr_multiply_execute replays it on C's stream: C = alpha * A * B on C's planned
+ * pattern, with the current values of A and B (change them with dbcsr_put_values), and
+ * no host synchronisation.  A block product whose prescreen bound was below eps at plan
+ * time stays excluded.
+ *   - A, B, C: finalized (C may be empty), C distinct from A and B, equal block sizes.
+ *     While the plan lives, their arrays are pinned: put_block, finalize, filter, copy into
+ *     them, multiply into C and destroy fail with DBCSR_ESTATE.  Values may change.
+ *   - prec: DBCSR_FP64, DBCSR_BF16 or DBCSR_BF16X3.  stats (may be NULL): of the plan's
+ *     first product.
+ *   - *out: the plan, owned by the caller; dbcsr_plan_destroy waits for its executions
+ *     and frees it (NULL accepted).
+ * Errors: as dbcsr_multiply, and EINVAL for C aliasing A or B; ECUDA if the graph cannot
+ * be captured.  Not from the paper's text beyond DBCSR's operations.
+ */
+typedef struct dbcsr_plan_* dbcsr_plan;
+dbcsr_status dbcsr_multiply_plan(double alpha, dbcsr_matrix A, dbcsr_matrix B, dbcsr_matrix C, double eps_filter,
+                                 int32_t prec, dbcsr_plan* out, dbcsr_mult_stats* stats);
+dbcsr_status dbcsr_multiply_execute(dbcsr_plan plan);
+dbcsr_status dbcsr_plan_destroy(dbcsr_plan plan);
+
+/*
+ * Replaces every value of the finalized matrix m, keeping its pattern: data holds nelem
+ * doubles, the blocks row-major in block-CSR order (the layout of dbcsr_export);
+ * on_device as for dbcsr_put_blocks.  Allowed while a plan uses m.  Host sources are
+ * copied before the call returns.
+ */
+dbcsr_status dbcsr_put_values(dbcsr_matrix m, const double* data, int on_device);
+
 /* Removes the blocks of m with Frobenius norm strictly below eps (diagonal blocks kept). */
 dbcsr_status dbcsr_filter(dbcsr_matrix m, double eps);
 

@@ -133,9 +133,19 @@ class Matrix:
     def trace(self) -> float:
         return trace(self)
 
+    def put_values(self, data):
+        """Replaces every value, keeping the pattern (data in block-CSR order, as export()).
+
+        ``data`` is a numpy float64 array (host) or an int device pointer."""
+        if isinstance(data, int):
+            _check(lib().dbcsr_put_values(self.handle, C.c_void_p(data), 1), "put_values")
+        else:
+            d = np.ascontiguousarray(data, dtype=np.float64)
+            _check(lib().dbcsr_put_values(self.handle, _ptr(d), 0), "put_values")
+
     def close(self):
         if getattr(self, "handle", None) is not None and self.handle.value:
-            lib().dbcsr_destroy(self.handle)
+            _check(lib().dbcsr_destroy(self.handle), "destroy")
             self.handle = C.c_void_p()
 
     def __del__(self):
@@ -152,6 +162,33 @@ def multiply(alpha: float, A: Matrix, B: Matrix, beta: float, C_: Matrix, eps_fi
     _check(lib().dbcsr_multiply(float(alpha), A.handle, B.handle, float(beta), C_.handle, float(eps_filter),
                                 int(prec), C.byref(st) if stats else None), "multiply")
     return st
+
+
+class Plan:
+    """A planned product C = alpha A B on fixed patterns, replayed as one CUDA graph
+    (dbcsr_multiply_plan / dbcsr_multiply_execute).  Holds its matrices alive."""
+
+    def __init__(self, alpha: float, A: Matrix, B: Matrix, C_: Matrix, eps_filter: float = 0.0,
+                 prec: int = DBCSR_FP64):
+        self.A, self.B, self.C = A, B, C_
+        self.handle = C.c_void_p()
+        self.stats = MultStats()
+        _check(lib().dbcsr_multiply_plan(float(alpha), A.handle, B.handle, C_.handle, float(eps_filter), int(prec),
+                                         C.byref(self.handle), C.byref(self.stats)), "multiply_plan")
+
+    def execute(self):
+        _check(lib().dbcsr_multiply_execute(self.handle), "multiply_execute")
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            lib().dbcsr_plan_destroy(self.handle)
+            self.handle = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def filter(M: Matrix, eps: float):  # noqa: A001 - the C ABI's name

@@ -67,6 +67,11 @@ SIGNATURES = [
     ("dbcsr_last_error", C.c_char_p, []),
     ("dbcsr_version", C.c_char_p, []),
     ("dbcsr_pool_trim", C.c_int, [C.c_uint64]),
+    ("dbcsr_multiply_plan", C.c_int, [C.c_double, P, P, P, C.c_double, C.c_int32, C.POINTER(P),
+                                      C.POINTER(MultStats)]),
+    ("dbcsr_multiply_execute", C.c_int, [P]),
+    ("dbcsr_plan_destroy", C.c_int, [P]),
+    ("dbcsr_put_values", C.c_int, [P, P, C.c_int]),
     ("dbcsr_create", C.c_int, [C.POINTER(P), C.c_int32, P, P]),
     ("dbcsr_destroy", C.c_int, [P]),
     ("dbcsr_put_block", C.c_int, [P, C.c_int32, C.c_int32, P, C.c_int]),

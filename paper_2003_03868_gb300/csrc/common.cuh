@@ -2,6 +2,7 @@
 // stream-ordered device buffers, the matrix object and internal entry points.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <atomic>
@@ -127,6 +128,8 @@ struct dbcsr_matrix_ {
     dbg::DBuf<double> norms;             // [nnzb] Frobenius norms (valid iff norms_valid)
     bool norms_valid = false;
 
+    int plans = 0;                       // live multiply plans that use this matrix's arrays
+
     // staging area of put_block(s) before finalize
     std::vector<int32_t> st_row, st_col;
     std::vector<int64_t> st_src;         // element offset of each staged block in st_dev
@@ -178,8 +181,28 @@ void trace_product_parts_into(dbcsr_matrix_* a, dbcsr_matrix_* b, double* part, 
 constexpr int kSymNone = 0, kSymMirror = 1, kSymAverage = 2;
 // m <- (m + m^T) / 2 on the blocks that have a twin; blocks without one are dropped.
 void symmetrize(dbcsr_matrix_* m);
+// A planned product C = alpha A B on fixed patterns: the buffers its numeric phase needs
+// and that phase captured as one CUDA graph (dbcsr_multiply_plan).
+struct MultPlan {
+    cudaGraphExec_t exec = nullptr;
+    int64_t kernels = 0;                 // kernel launches per execution
+    cudaStream_t stream = nullptr;
+    dbcsr_matrix_* A = nullptr;
+    dbcsr_matrix_* B = nullptr;
+    dbcsr_matrix_* C = nullptr;
+    std::vector<DBuf<int32_t>> bufs_i32;
+    std::vector<DBuf<int64_t>> bufs_i64;
+    std::vector<DBuf<double>> bufs_f64;
+    std::vector<DBuf<__nv_bfloat16>> bufs_bf16;
+    ~MultPlan();
+};
+// plan: build a plan instead of a one-off product (beta = 0, C distinct from A and B, no
+// symmetric result); C then holds the formed pattern with blocks under eps zeroed.
 void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbcsr_matrix_* C, double eps,
-              int prec, dbcsr_mult_stats* stats, bool want_dev2, int sym_result = kSymNone);
+              int prec, dbcsr_mult_stats* stats, bool want_dev2, int sym_result = kSymNone, MultPlan* plan = nullptr);
+void execute_plan(MultPlan* plan);
+// Fails with DBCSR_ESTATE when a live plan uses m's arrays (they must not be replaced).
+void check_unplanned(const dbcsr_matrix_* m, const char* where);
 
 // ---- sign.cu
 dbcsr_status sign_iterate(dbcsr_matrix_* H, double mu, const dbcsr_sign_opts* opts, dbcsr_matrix_* P,

@@ -106,6 +106,11 @@ double read_f64(const double* dev, cudaStream_t s) {
     return hs.d[0];
 }
 
+void check_unplanned(const dbcsr_matrix_* m, const char* where) {
+    if (m && m->plans > 0)
+        fail(DBCSR_ESTATE, std::string(where) + ": a multiply plan uses this matrix (destroy the plan first)");
+}
+
 void check_finalized(const dbcsr_matrix_* m) {
     if (!m) fail(DBCSR_EINVAL, "null matrix handle");
     if (!m->finalized) fail(DBCSR_ESTATE, "matrix is not finalized");
@@ -248,6 +253,7 @@ void ensure_norms(dbcsr_matrix_* m) {
 }
 
 void copy_matrix(dbcsr_matrix_* dst, const dbcsr_matrix_* src) {
+    check_unplanned(dst, "copy");
     check_finalized(src);
     if (dst == src) return;
     if (dst->h_bs != src->h_bs) fail(DBCSR_EINVAL, "copy: block sizes differ");
@@ -295,6 +301,7 @@ void scale_shift(dbcsr_matrix_* m, double scale, double shift) {
 }
 
 void compact(dbcsr_matrix_* m, const int32_t* keep, const double* norms_in) {
+    check_unplanned(m, "filter");
     cudaStream_t s = m->stream;
     const int64_t nb = m->nnzb;
     DBuf<int64_t> newidx;
@@ -424,7 +431,20 @@ dbcsr_status dbcsr_create(dbcsr_matrix* out, int32_t nblk, const int32_t* blk_si
 dbcsr_status dbcsr_destroy(dbcsr_matrix m) {
     return guarded([&] {
         if (!m) return;
+        dbg::check_unplanned(m, "destroy");
         delete m;
+    });
+}
+
+dbcsr_status dbcsr_put_values(dbcsr_matrix m, const double* data, int on_device) {
+    return guarded([&] {
+        dbg::check_finalized(m);
+        if (!data && m->nel) dbg::fail(DBCSR_EINVAL, "put_values: null data");
+        if (m->nel)
+            DBG_CK(cudaMemcpyAsync(m->data.p, data, sizeof(double) * m->nel,
+                                   on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, m->stream));
+        if (!on_device) DBG_CK(cudaStreamSynchronize(m->stream));
+        m->norms_valid = false;
     });
 }
 
@@ -433,6 +453,7 @@ dbcsr_status dbcsr_destroy(dbcsr_matrix m) {
 static void stage(dbcsr_matrix m, int64_t n, const int32_t* rows, const int32_t* cols, const double* packed,
                   int on_device) {
     if (!m) fail(DBCSR_EINVAL, "null matrix handle");
+    dbg::check_unplanned(m, "put_block");
     if (m->finalized) fail(DBCSR_ESTATE, "put_block: matrix already finalized");
     if (n < 0 || (n > 0 && (!rows || !cols || !packed))) fail(DBCSR_EINVAL, "put_blocks: null argument");
     int64_t total = 0;

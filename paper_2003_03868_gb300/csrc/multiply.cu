@@ -1086,6 +1086,22 @@ __global__ void k_pack_bf16(int64_t nb, int role, const int32_t* __restrict__ ro
 }
 
 
+// Planned products keep their pattern: a block (not diagonal) whose norm is below eps
+// is set to zero instead of being removed.
+__global__ void k_zero_small(int64_t nb, const int32_t* __restrict__ row, const int32_t* __restrict__ col,
+                             const int32_t* __restrict__ bs, const int64_t* __restrict__ off,
+                             double* __restrict__ data, double* __restrict__ norms, double eps) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t b = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); b < nb; b += warps) {
+        if (row[b] == col[b] || !(norms[b] < eps)) continue;
+        const int area = bs[row[b]] * bs[col[b]];
+        double* x = data + off[b];
+        for (int e = lane; e < area; e += 32) x[e] = 0.0;
+        if (lane == 0) norms[b] = 0.0;
+    }
+}
+
 __global__ void k_keep_filter(int64_t nb, const int32_t* __restrict__ row, const int32_t* __restrict__ col,
                               const double* __restrict__ norms, const double* __restrict__ dev2, double eps,
                               int32_t* __restrict__ keep, double* __restrict__ dev2_kept) {
@@ -1165,6 +1181,7 @@ void launch_smm_shape(int prec, int m, int n, int64_t cnt, const int64_t* list, 
 
 void symmetrize(dbcsr_matrix_* m) {
     check_finalized(m);
+    check_unplanned(m, "symmetrize");
     cudaStream_t s = m->stream;
     const int64_t nb = m->nnzb;
     if (nb == 0) return;
@@ -1186,10 +1203,15 @@ void symmetrize(dbcsr_matrix_* m) {
 }
 
 void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbcsr_matrix_* C, double eps, int prec,
-              dbcsr_mult_stats* stats, bool want_dev2, int sym_result) {
+              dbcsr_mult_stats* stats, bool want_dev2, int sym_result, MultPlan* plan) {
     check_finalized(A);
     check_finalized(B);
     if (!C) fail(DBCSR_EINVAL, "multiply: null C");
+    check_unplanned(C, "multiply");
+    if (plan) {
+        if (beta != 0.0 || sym_result) fail(DBCSR_EINVAL, "multiply_plan: only C = alpha A B (beta = 0)");
+        if (C == A || C == B) fail(DBCSR_EINVAL, "multiply_plan: C must differ from A and B");
+    }
     if (A->h_bs != B->h_bs || A->h_bs != C->h_bs) fail(DBCSR_EINVAL, "multiply: block sizes of A, B and C differ");
     if (prec != DBCSR_FP64 && !is_bf16(prec))
         fail(DBCSR_EINVAL, "multiply: prec must be DBCSR_FP64, DBCSR_BF16 or DBCSR_BF16X3");
@@ -1345,20 +1367,27 @@ void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbc
     c_data.alloc(std::max<int64_t>(nel, 1), s);
     c_norm.alloc(nf1, s);
     c_dev2.alloc(nf1, s);
+    // kept by a plan: the shape lists, the BF16 packs and the launch sequence
+    DBuf<int64_t> list;
+    DBuf<__nv_bfloat16> a16, b16, a16_lo, b16_lo;
+    DBuf<int64_t> a_psz, a_po, b_psz, b_po;
+    Bf16Packs pk{};
+    SmmArgs sa{};
+    struct ShapeLaunch { int m, n; int64_t cnt; };
+    std::vector<ShapeLaunch> launches;
+    const int kmax = *std::max_element(A->h_bs.begin(), A->h_bs.end());
     if (nform) {
-        SmmArgs sa{f_row.p, f_col.p, f_off.p, f_pbeg.p, f_cin.p, prod_a.p, prod_b.p, A->col.p, A->off.p, A->data.p,
-                   B->off.p, B->data.p, use_c ? C->off.p : nullptr, use_c ? C->data.p : nullptr, A->bs.p,
-                   alpha, beta, c_data.p, c_norm.p, c_dev2.p};
+        sa = SmmArgs{f_row.p, f_col.p, f_off.p, f_pbeg.p, f_cin.p, prod_a.p, prod_b.p, A->col.p, A->off.p, A->data.p,
+                     B->off.p, B->data.p, use_c ? C->off.p : nullptr, use_c ? C->data.p : nullptr, A->bs.p,
+                     alpha, beta, c_data.p, c_norm.p, c_dev2.p};
         // one launch per (m, n) block shape over that shape's blocks (kept in CSR order)
         const bool bf16 = is_bf16(prec);
         DBuf<int32_t> flag;
-        DBuf<int64_t> pos, list;
+        DBuf<int64_t> pos;
         flag.alloc(nform, s);
         pos.alloc(nform + 1, s);
         list.alloc(nform, s);
         int64_t at = 0;
-        struct ShapeLaunch { int m, n; int64_t cnt; };
-        std::vector<ShapeLaunch> launches;
         for (int m = 1; m <= kMaxBlock; ++m)
             for (int n = 1; n <= kMaxBlock; ++n) {
                 const int64_t cnt = shapes[m * (kMaxBlock + 1) + n];
@@ -1373,9 +1402,6 @@ void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbc
                 bytes_min += 8.0 * (double)cnt * m * n;
                 at += cnt;
             }
-        DBuf<__nv_bfloat16> a16, b16, a16_lo, b16_lo;
-        DBuf<int64_t> a_psz, a_po, b_psz, b_po;
-        Bf16Packs pk{};
         if (bf16) {
             // operands rounded to BF16 (nearest even) once per product, into fragment-ready copies
             // (and, for split products, the rounded residuals x - hi); every block takes its own
@@ -1423,8 +1449,7 @@ void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbc
             pk.a16_lo = a16_lo.p;
             pk.b16_lo = b16_lo.p;
         }
-        // the inner size the tuned configurations are looked up with: the largest block edge
-        const int kmax = *std::max_element(A->h_bs.begin(), A->h_bs.end());
+        // the tuned configurations are looked up with the largest block edge as the inner size
         DBG_CK(cudaEventRecord(ev.e[1], s));
         at = 0;
         for (const ShapeLaunch& L : launches) {
@@ -1445,7 +1470,10 @@ void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbc
         }
     }
     if (!sym_result || !nform) DBG_CK(cudaEventRecord(ev.e[2], s));
-    prod_a.release(); prod_b.release();
+    if (!plan) {
+        prod_a.release();
+        prod_b.release();
+    }
 
     // install the formed blocks as C (A or B may alias C: every read above is queued before)
     C->rp = std::move(f_rp);
@@ -1458,6 +1486,98 @@ void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbc
     C->norms = std::move(c_norm);
     C->norms_valid = true;
     C->finalized = true;
+
+    if (plan) {
+        // 6'. a plan keeps the formed pattern: blocks under eps are zeroed, not removed, so
+        // that every execution writes the same arrays; then the whole numeric phase
+        // (packing, block products, zeroing) is captured into one graph
+        auto zero_small = [&](cudaStream_t zs) {
+            if (!nform) return;
+            k_zero_small<<<grid_for(nform, 8), 256, 0, zs>>>(nform, C->row.p, C->col.p, C->bs.p, C->off.p, C->data.p,
+                                                            C->norms.p, eps);
+            DBG_LAUNCH_CK();
+        };
+        zero_small(s);
+        // captured on a private stream (the legacy default stream cannot be captured); the
+        // graph is launched on C's stream
+        cudaStream_t cs = nullptr;
+        DBG_CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        cudaGraph_t graph = nullptr;
+        const int64_t l0 = g_launches.load();
+        try {
+            DBG_CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+            if (nform && is_bf16(prec)) {
+                if (A->nnzb) {
+                    k_pack_bf16<<<grid_for(A->nnzb, 8), 256, 0, cs>>>(A->nnzb, 0, A->row.p, A->col.p, A->bs.p,
+                                                                      A->off.p, A->data.p, a_po.p, a16.p, a16_lo.p);
+                    DBG_LAUNCH_CK();
+                }
+                if (B->nnzb) {
+                    k_pack_bf16<<<grid_for(B->nnzb, 8), 256, 0, cs>>>(B->nnzb, 1, B->row.p, B->col.p, B->bs.p,
+                                                                      B->off.p, B->data.p, b_po.p, b16.p, b16_lo.p);
+                    DBG_LAUNCH_CK();
+                }
+            }
+            int64_t at = 0;
+            for (const ShapeLaunch& L : launches) {
+                launch_smm_shape(prec, L.m, L.n, L.cnt, list.p + at, sa, pk, tune_lookup(prec, L.m, L.n, kmax), cs);
+                at += L.cnt;
+            }
+            zero_small(cs);
+            DBG_CK(cudaStreamEndCapture(cs, &graph));
+        } catch (...) {
+            cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+            if (cudaStreamIsCapturing(cs, &cst) == cudaSuccess && cst != cudaStreamCaptureStatusNone) {
+                cudaGraph_t g = nullptr;
+                (void)cudaStreamEndCapture(cs, &g);
+                if (g) cudaGraphDestroy(g);
+            }
+            cudaStreamDestroy(cs);
+            (void)cudaGetLastError();
+            throw;
+        }
+        cudaStreamDestroy(cs);
+        cudaGraphExec_t exec = nullptr;
+        const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        DBG_CK(ie);
+        plan->exec = exec;
+        plan->kernels = g_launches.load() - l0;
+        plan->stream = s;
+        plan->A = A;
+        plan->B = B;
+        plan->C = C;
+        plan->bufs_i32.push_back(std::move(prod_a));
+        plan->bufs_i32.push_back(std::move(prod_b));
+        plan->bufs_i64.push_back(std::move(list));
+        plan->bufs_i64.push_back(std::move(f_pbeg));
+        plan->bufs_i64.push_back(std::move(f_cin));
+        plan->bufs_i64.push_back(std::move(a_po));
+        plan->bufs_i64.push_back(std::move(b_po));
+        plan->bufs_f64.push_back(std::move(c_dev2));
+        plan->bufs_bf16.push_back(std::move(a16));
+        plan->bufs_bf16.push_back(std::move(b16));
+        plan->bufs_bf16.push_back(std::move(a16_lo));
+        plan->bufs_bf16.push_back(std::move(b16_lo));
+        A->plans++;
+        B->plans++;
+        C->plans++;
+        DBG_CK(cudaEventRecord(ev.e[3], s));
+        if (stats) {
+            DBG_CK(cudaStreamSynchronize(s));
+            stats->n_candidates = ncand;
+            stats->n_formed = nform;
+            stats->n_kept = C->nnzb;
+            stats->n_products = nprod_done;
+            stats->flops = nflop;
+            stats->ms_symbolic = ev.ms(0, 1);
+            stats->ms_numeric = ev.ms(1, 2);
+            stats->ms_filter = ev.ms(2, 3);
+            stats->bytes_min = bytes_min;
+            stats->n_launches = n_smm_launches;
+        }
+        return;
+    }
 
     // 6. filter
     DBuf<int32_t> keep2;
@@ -1490,4 +1610,78 @@ void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbc
     }
 }
 
+void execute_plan(MultPlan* plan) {
+    if (!plan || !plan->exec) fail(DBCSR_EINVAL, "multiply_execute: null plan");
+    dbcsr_matrix_* A = plan->A;
+    dbcsr_matrix_* B = plan->B;
+    if (A->stream != plan->stream) DBG_CK(cudaStreamSynchronize(A->stream));
+    if (B->stream != plan->stream) DBG_CK(cudaStreamSynchronize(B->stream));
+    DBG_CK(cudaGraphLaunch(plan->exec, plan->stream));
+    g_launches.fetch_add(plan->kernels, std::memory_order_relaxed);
+    plan->C->norms_valid = true;
+}
+
+MultPlan::~MultPlan() {
+    if (exec) {
+        cudaStreamSynchronize(stream);      // no execution may still use the buffers
+        cudaGraphExecDestroy(exec);
+    }
+    if (A) A->plans--;
+    if (B) B->plans--;
+    if (C) C->plans--;
+}
+
 }  // namespace dbg
+
+extern "C" {
+
+struct dbcsr_plan_ {
+    dbg::MultPlan plan;
+};
+
+dbcsr_status dbcsr_multiply_plan(double alpha, dbcsr_matrix A, dbcsr_matrix B, dbcsr_matrix C, double eps_filter,
+                                 int32_t prec, dbcsr_plan* out, dbcsr_mult_stats* stats) {
+    if (!out) {
+        dbg::set_last_error("multiply_plan: null output handle");
+        return DBCSR_EINVAL;
+    }
+    *out = nullptr;
+    auto* p = new dbcsr_plan_();
+    try {
+        if (!A || !B) dbg::fail(DBCSR_EINVAL, "multiply_plan: null handle");
+        dbg::multiply(alpha, A, B, 0.0, C, eps_filter, prec, stats, false, dbg::kSymNone, &p->plan);
+        *out = p;
+        dbg::set_last_error("");
+        return DBCSR_OK;
+    } catch (const dbg::Error& e) {
+        delete p;
+        dbg::set_last_error(e.what());
+        return e.code;
+    } catch (const std::exception& e) {
+        delete p;
+        dbg::set_last_error(e.what());
+        return DBCSR_ECUDA;
+    }
+}
+
+dbcsr_status dbcsr_multiply_execute(dbcsr_plan plan) {
+    try {
+        if (!plan) dbg::fail(DBCSR_EINVAL, "multiply_execute: null plan");
+        dbg::execute_plan(&plan->plan);
+        dbg::set_last_error("");
+        return DBCSR_OK;
+    } catch (const dbg::Error& e) {
+        dbg::set_last_error(e.what());
+        return e.code;
+    } catch (const std::exception& e) {
+        dbg::set_last_error(e.what());
+        return DBCSR_ECUDA;
+    }
+}
+
+dbcsr_status dbcsr_plan_destroy(dbcsr_plan plan) {
+    delete plan;
+    return DBCSR_OK;
+}
+
+}  // extern "C"
