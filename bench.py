@@ -154,7 +154,14 @@ def run_batch(args, gb, synth, torch, barrier):
     """64 uneven water systems (n_mol log-uniform in [100, 2000], O/H blocks per system):
     one batched sign iteration vs the same systems solved one after the other, in FP64
     and with the mixed-precision ladder."""
-    ws = synth.batch_systems()
+    from paper_2003_03868_gb300 import ranks
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+    # every rank solves its own 64 systems (independent problems: weak scaling, no data exchange)
+    ws = synth.batch_systems(seed=synth.batch_seed(rank))
     hs = [synth.build_hamiltonian(w) for w in ws]
     stream = torch.cuda.current_stream()
     Hs = [gb.Matrix.of(h.H, stream=stream.cuda_stream) for h in hs]
@@ -170,7 +177,8 @@ def run_batch(args, gb, synth, torch, barrier):
             Ps, reps, st = gb.sign_iterate_batched(Hs, [0.0] * len(Hs), eps, tol, prec=prec)
         e1.record(stream)
         torch.cuda.synchronize()
-        ms_b = e0.elapsed_time(e1) / args.steps
+        barrier()
+        ms_b, flops_all = ranks.job_timing(e0.elapsed_time(e1) / args.steps, reps[0].flops, dist, "cuda")
         # the same systems one by one
         s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         s0.record(stream)
@@ -180,7 +188,7 @@ def run_batch(args, gb, synth, torch, barrier):
         ms_s = s0.elapsed_time(s1)
         de = max(abs(r.e_band - g.report.e_band) / h.n_atoms for r, g, h in zip(reps, seq, hs))
         its = [r.iterations for r in reps]
-        return {"ms_per_step": ms_b, "value": reps[0].flops / (ms_b * 1e-3) / 1e12, "unit": "TFLOP/s",
+        return {"ms_per_step": ms_b, "value": flops_all / (ms_b * 1e-3) / 1e12, "unit": "TFLOP/s",
                 "sequential_ms": ms_s, "speedup_vs_sequential": ms_s / ms_b,
                 "systems_converged": sum(int(r.converged) for r in reps),
                 "systems_stalled": sum(int(r.stalled) for r in reps),
@@ -196,13 +204,17 @@ def run_batch(args, gb, synth, torch, barrier):
                                                     for a, b, h in zip(repsm, reps64, hs))
         mixed["dtype"] = "bf16x3 (split bf16 hi+lo operands, fp32 accumulate), then f64"
     out = {"metric": "block-GEMM TFLOP/s (batched sign iteration)", "value": f64["value"],
-           "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": f64["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f64", "data": "synthetic",
-           "config": {"workload": "batch-64", "systems": len(ws), "molecules": sum(w.n_mol for w in ws),
-                      "atoms": sum(w.n_atoms for w in ws), "eps_filter": eps, "tol": tol},
+           "config": {"workload": "batch-64", "systems_per_rank": len(ws), "molecules_rank0": sum(w.n_mol for w in ws),
+                      "atoms_rank0": sum(w.n_atoms for w in ws), "eps_filter": eps, "tol": tol,
+                      "parallelism": f"independent systems, 64 per rank x{world}"},
            **{k: v for k, v in f64.items() if k not in ("value", "ms_per_step", "unit")}, "mixed": mixed}
-    print(json.dumps(out))
+    if rank == 0:
+        print(json.dumps(out))
+    if dist:
+        dist.destroy_process_group()
     return 0
 
 
@@ -419,10 +431,14 @@ def main():
 
     if args.workload == "batch-64":
         return run_batch(args, gb, synth, torch, barrier)
-    if args.workload == "sign-20736h2o-mlp":
-        return run_predictor(args, gb, synth, torch, barrier)
-    if args.workload == "mult-32h2o":
-        return run_mult32(args, gb, synth, torch, barrier)
+    if args.workload in ("sign-20736h2o-mlp", "mult-32h2o"):
+        # one-GPU studies: under torchrun rank 0 alone runs them
+        if rank != 0:
+            if dist:
+                dist.destroy_process_group()
+            return 0
+        return (run_predictor if args.workload == "sign-20736h2o-mlp" else run_mult32)(args, gb, synth, torch,
+                                                                                         lambda: torch.cuda.synchronize())
     w = {"sign-1024h2o": synth.SIGN_1024, "sign-4096h2o": synth.SIGN_4096,
          "sign-512h2o": synth.Workload("sign-512h2o-dzvp-fp64", 512, (13, 5), synth.configs.BASE_SEED + 12, 1e-7, 1e-9),
          "sign-512h2o-23-7": synth.Workload("sign-512h2o-23-7", 512, (23, 7), synth.configs.BASE_SEED + 13, 1e-6, 1e-8,
@@ -460,13 +476,8 @@ def main():
     launches = gb.lib().dbcsr_launch_count() - l0
     clk = clocks.stop()
     ms = e0.elapsed_time(e1)
-    t = torch.tensor([ms, flops], dtype=torch.float64, device="cuda")
-    if dist:
-        mx = t.clone()
-        dist.all_reduce(mx[0:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(mx[1:2], op=dist.ReduceOp.SUM)
-        t = mx
-    ms_all, flops_all = float(t[0]), float(t[1])
+    from paper_2003_03868_gb300 import ranks
+    ms_all, flops_all = ranks.job_timing(ms, flops, dist, "cuda")
     value = flops_all / (ms_all * 1e-3) / 1e12
 
     # the same workload with the precision ladder: split-BF16 tensor-core products while r >= 1e-4,

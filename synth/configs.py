@@ -45,6 +45,11 @@ SIGN_4096 = Workload("sign-4096h2o-23-7-mixed", 4096, (23, 7), BASE_SEED + 3, 1e
 SIGN_20736 = Workload("sign-20736h2o-23-7-mixed", 20736, (23, 7), BASE_SEED + 5, 1e-6, 1e-8, 1e-4)
 
 
+def batch_seed(rank: int = 0) -> int:
+    """Seed of the uneven-system batch solved by one rank (each rank its own systems)."""
+    return BASE_SEED * 100 + 100000 * rank
+
+
 def batch_systems(n_sys: int = 64, seed: int = BASE_SEED * 100, lo: int = 100, hi: int = 2000):
     """64 uneven systems: n_mol log-uniform in [lo, hi], O in {13, 23}, H in {5, 7}."""
     out = []
