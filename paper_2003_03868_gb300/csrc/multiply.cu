@@ -126,6 +126,7 @@ __global__ void k_cand_count(int32_t nblk, RowPattern P, int nwords, int64_t* __
         if (threadIdx.x == 0) {
             ccnt[I] = n;
             atomicMax(max_row, (unsigned long long)n);
+            atomicMax(max_row + 1, (unsigned long long)(P.a_rp[I + 1] - P.a_rp[I]));
         }
         __syncthreads();
     }
@@ -140,20 +141,30 @@ struct BoundArgs {
     double* bound; int32_t* pcnt; int32_t* ksum; int64_t* cin;
     int32_t* keep;
     int use_smem;
+    int use_fast;            // FP32 upper bound with atomics (needs use_smem and < 4096 terms per candidate)
 };
 
+// The norm bound is accumulated in FP32 with shared-memory atomics, in any order, so the
+// K loop needs no barrier.  Each term is scaled up by (1 + 2^-10) before it is added; with
+// fewer than 2^12 terms per candidate (checked by the caller, or the exact FP64 path runs)
+// the FP32 rounding of the sum stays below that margin, so the result is an upper bound of
+// the exact bound and a candidate is skipped only when its exact bound is below eps_lo.
+// Which near-threshold blocks are formed may then vary from run to run; the filtered
+// result cannot (a block whose norm reaches eps always has its bound above eps_lo).
 __global__ void k_cand_bound(int32_t nblk, RowPattern P, int nwords, BoundArgs B) {
     extern __shared__ uint32_t smem[];
     __shared__ int sh_scan[32];
     uint32_t* bm = smem;
     int* wpre = (int*)(smem + nwords);
     double* sh_bound = (double*)(smem + 2 * ((nwords + 1) & ~1));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     for (int32_t I = blockIdx.x; I < nblk; I += gridDim.x) {
         const int nc = build_row(P, I, bm, wpre, nwords, sh_scan);
         const int64_t cb = B.coff[I];
         double* bnd = B.use_smem ? sh_bound : B.bound + cb;
         int32_t* pc = B.use_smem ? (int32_t*)(sh_bound + nc) : B.pcnt + cb;
         int32_t* ks = B.use_smem ? pc + nc : B.ksum + cb;
+        float* fb = (float*)(pc + 2 * nc);      // use_fast: FP32 bounds after the counters
         // candidates in ascending J
         for (int w = threadIdx.x; w < nwords; w += blockDim.x) {
             uint32_t bits = bm[w];
@@ -166,6 +177,7 @@ __global__ void k_cand_bound(int32_t nblk, RowPattern P, int nwords, BoundArgs B
                 bnd[r] = 0.0;
                 pc[r] = 0;
                 ks[r] = 0;
+                if (B.use_fast) fb[r] = 0.f;
                 if (B.cin) B.cin[cb + r] = -1;
                 ++r;
             }
@@ -174,20 +186,38 @@ __global__ void k_cand_bound(int32_t nblk, RowPattern P, int nwords, BoundArgs B
         if (P.c_col)
             for (int64_t q = P.c_rp[I] + threadIdx.x; q < P.c_rp[I + 1]; q += blockDim.x)
                 B.cin[cb + rank_of(bm, wpre, P.c_col[q])] = q;
-        __syncthreads();
-        // ascending K, one K at a time: every accumulator is updated in a fixed order
-        for (int64_t p = P.a_rp[I]; p < P.a_rp[I + 1]; ++p) {
-            const int32_t K = P.a_col[p];
-            const double na = B.abs_alpha * B.a_norm[p];
-            const int kk = B.bs[K];
-            for (int64_t q = P.b_rp[K] + threadIdx.x; q < P.b_rp[K + 1]; q += blockDim.x) {
-                const int r = rank_of(bm, wpre, P.b_col[q]);
-                bnd[r] = bnd[r] + na * B.b_norm[q];
-                pc[r] += 1;
-                ks[r] += kk;
+        if (B.use_fast) {
+            // warps over K, lanes over the blocks of B's row K, no barrier
+            for (int64_t p = P.a_rp[I] + warp; p < P.a_rp[I + 1]; p += nw) {
+                const int32_t K = P.a_col[p];
+                const float na = (float)(B.abs_alpha * B.a_norm[p]) * 1.0009765625f;
+                const int kk = B.bs[K];
+                for (int64_t q = P.b_rp[K] + lane; q < P.b_rp[K + 1]; q += 32) {
+                    const int r = rank_of(bm, wpre, P.b_col[q]);
+                    atomicAdd(&fb[r], __fmul_ru(na, __double2float_ru(B.b_norm[q])));
+                    atomicAdd(&pc[r], 1);
+                    atomicAdd(&ks[r], kk);
+                }
             }
             __syncthreads();
+            for (int r = threadIdx.x; r < nc; r += blockDim.x) bnd[r] = (double)fb[r] * 1.0009765625;
+        } else {
+            __syncthreads();
+            // ascending K, one K at a time: every accumulator is updated in a fixed order
+            for (int64_t p = P.a_rp[I]; p < P.a_rp[I + 1]; ++p) {
+                const int32_t K = P.a_col[p];
+                const double na = B.abs_alpha * B.a_norm[p];
+                const int kk = B.bs[K];
+                for (int64_t q = P.b_rp[K] + threadIdx.x; q < P.b_rp[K + 1]; q += blockDim.x) {
+                    const int r = rank_of(bm, wpre, P.b_col[q]);
+                    bnd[r] = bnd[r] + na * B.b_norm[q];
+                    pc[r] += 1;
+                    ks[r] += kk;
+                }
+                __syncthreads();
+            }
         }
+        __syncthreads();
         for (int r = threadIdx.x; r < nc; r += blockDim.x) {
             double b = bnd[r];
             const int64_t ci = B.cin ? B.cin[cb + r] : -1;
@@ -1243,7 +1273,7 @@ void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbc
     DBuf<int64_t> ccnt, coff, maxrow;
     ccnt.alloc(nblk, s);
     coff.alloc(nblk + 1, s);
-    maxrow.alloc(1, s);
+    maxrow.alloc(2, s);                   // largest candidate count and largest A row of a block row
     maxrow.zero();
     {
         const size_t sm = sm_rank;
@@ -1252,12 +1282,12 @@ void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbc
         DBG_LAUNCH_CK();
     }
     scan_exclusive(ccnt.p, coff.p, nblk, s);
-    int64_t h2[2];
+    int64_t h2[3];
     {
-        const int64_t* src[2] = {coff.p + nblk, maxrow.p};
-        read_i64s(src, 2, h2, s);
+        const int64_t* src[3] = {coff.p + nblk, maxrow.p, maxrow.p + 1};
+        read_i64s(src, 3, h2, s);
     }
-    const int64_t ncand = h2[0], max_row = h2[1];
+    const int64_t ncand = h2[0], max_row = h2[1], max_arow = h2[2];
 
     // 2. candidates, bounds and the prescreen decision
     DBuf<int32_t> cand_row, cand_col, pcnt, ksum, keep;
@@ -1271,13 +1301,16 @@ void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbc
     keep.alloc(nc1, s);
     kidx.alloc(ncand + 1, s);
     if (use_c) cin.alloc(nc1, s);
-    const size_t sm_acc = sm_rank + (size_t)max_row * (sizeof(double) + 2 * sizeof(int32_t));
+    const size_t sm_acc = sm_rank + (size_t)max_row * (sizeof(double) + 2 * sizeof(int32_t) + sizeof(float));
     const bool acc_smem = sm_acc <= (size_t)kSymSmemBudget;
+    // a candidate's bound has at most (largest A row) terms: the FP32 margin covers 4095
+    const bool fast_bound = acc_smem && max_arow < 4096;
     if (!acc_smem) bound.alloc(nc1, s);
     if (ncand) {
         BoundArgs ba{std::fabs(alpha), std::fabs(beta), eps * (1.0 - 1e-12), A->norms.p, B->norms.p,
                      use_c ? C->norms.p : nullptr, A->bs.p, coff.p, cand_row.p, cand_col.p,
-                     bound.p, pcnt.p, ksum.p, use_c ? cin.p : nullptr, keep.p, acc_smem ? 1 : 0};
+                     bound.p, pcnt.p, ksum.p, use_c ? cin.p : nullptr, keep.p, acc_smem ? 1 : 0,
+                     fast_bound ? 1 : 0};
         const size_t sm = acc_smem ? sm_acc : sm_rank;
         if (sm > 48 * 1024) DBG_CK(cudaFuncSetAttribute(k_cand_bound, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         k_cand_bound<<<sym_grid(nblk), kSymThreads, sm, s>>>(nblk, P, nwords, ba);
