@@ -183,3 +183,22 @@ def test_bitwise_reproducible(gb):
         gb.multiply(1.0, A, A, 0.0, C, 1e-6)
         outs.append(C.export()[2].tobytes())
     assert outs[0] == outs[1]
+
+
+def test_pool_trim_keeps_live_matrices(gb):
+    # the library's caching pool hands its free memory back; live matrices are untouched
+    import torch
+    a = synth.random_block_matrix(SIZES[0], 0.5, 77)
+    A, Ao = gb.Matrix.of(a), bsr.Mat.of(a)
+    C_ = gb.Matrix(A.blk_size, A.stream)
+    gb.multiply(1.0, A, A, 0.0, C_, 0.0)
+    before = C_.export()
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    gb.pool_trim(0)
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 >= free0
+    for x, y in zip(before, C_.export()):
+        assert np.array_equal(x, y)
+    gb.multiply(1.0, A, A, 0.0, C_, 0.0)         # the pool grows again on demand
+    _assert_same(C_, bsr.multiply(1.0, Ao, Ao))
