@@ -407,6 +407,22 @@ dbcsr_status dbcsr_mlp_predict_best(int32_t prec, const float* params, const int
                                     dbcsr_kernel_cfg* best, float* best_pred);
 
 /*
+ * The prediction with the exhaustive autotune as its fallback and measured time as the
+ * judge (section "Batched execution": the model fills in the untuned kernels; the tuner
+ * stays the reference).  For each triple mnk[3t..3t+2]:
+ *   - the MLP (params, as for dbcsr_mlp_predict_best) picks a configuration;
+ *   - the prediction and the default configuration are timed on the synthetic stack
+ *     (stack_len products, median of reps launches);
+ *   - if the prediction's time is at most (1 + tolerance) times the default's, it enters
+ *     the tune table; otherwise every configuration of dbcsr_tune_space is timed on that
+ *     stack and the fastest enters the table.
+ * fell_back[t] (may be NULL) receives 1 where the exhaustive search ran.
+ * Errors: EINVAL (bad argument or triple), and those of dbcsr_mlp_predict_best.
+ */
+dbcsr_status dbcsr_tune_predicted(int32_t prec, const float* params, const int32_t* mnk, int32_t ntriples,
+                                  int64_t stack_len, int32_t reps, double tolerance, int32_t* fell_back);
+
+/*
  * Solves nsys independent systems H[s] (each symmetric, all diagonal blocks
  * present, any block sizes) as one batch: the matrices are stacked into one
  * block-diagonal matrix, so every product forms all systems' blocks in the same

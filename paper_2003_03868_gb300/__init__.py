@@ -406,6 +406,19 @@ def train_predictor(recs, prec: int = DBCSR_FP64, epochs: int = 3000, lr: float 
     return mlp_train(mlp_init(MLP_FEATURES, seed=seed), X, T, epochs=epochs, lr=lr)
 
 
+def tune_predicted(params, triples, prec: int = DBCSR_FP64, stack_len: int = 500000, reps: int = 3,
+                   tolerance: float = 0.02):
+    """Installs the MLP's configuration for each triple when its measured time is within
+    tolerance of the default's, else the exhaustive best (dbcsr_tune_predicted).  Returns
+    the per-triple fallback flags."""
+    t = np.ascontiguousarray(np.asarray(triples, dtype=np.int32).reshape(-1, 3))
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    fb = np.zeros(t.shape[0], dtype=np.int32)
+    _check(lib().dbcsr_tune_predicted(int(prec), _ptr(p), _ptr(t), int(t.shape[0]), int(stack_len), int(reps),
+                                      float(tolerance), _ptr(fb)), "tune_predicted")
+    return [bool(x) for x in fb]
+
+
 def mlp_predict_best(params, triples, prec: int = DBCSR_FP64):
     """Predicted-fastest configuration of every triple (list of KernelCfg)."""
     t = np.ascontiguousarray(np.asarray(triples, dtype=np.int32).reshape(-1, 3))

@@ -72,6 +72,7 @@ SIGNATURES = [
     ("dbcsr_multiply_execute", C.c_int, [P]),
     ("dbcsr_plan_destroy", C.c_int, [P]),
     ("dbcsr_put_values", C.c_int, [P, P, C.c_int]),
+    ("dbcsr_tune_predicted", C.c_int, [C.c_int32, P, P, C.c_int32, C.c_int64, C.c_int32, C.c_double, P]),
     ("dbcsr_create", C.c_int, [C.POINTER(P), C.c_int32, P, P]),
     ("dbcsr_destroy", C.c_int, [P]),
     ("dbcsr_put_block", C.c_int, [P, C.c_int32, C.c_int32, P, C.c_int]),

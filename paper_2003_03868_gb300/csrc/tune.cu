@@ -317,6 +317,44 @@ dbcsr_status dbcsr_autotune(const int32_t* mnk, int32_t ntriples, int32_t prec, 
     });
 }
 
+dbcsr_status dbcsr_tune_predicted(int32_t prec, const float* params, const int32_t* mnk, int32_t ntriples,
+                                  int64_t stack_len, int32_t reps, double tolerance, int32_t* fell_back) {
+    return guard([&] {
+        if (!params || !mnk || ntriples < 1 || stack_len < 1 || reps < 1 || !(tolerance == tolerance))
+            dbg::fail(DBCSR_EINVAL, "tune_predicted: bad argument");
+        for (int32_t t = 0; t < ntriples; ++t) dbg::check_triple(prec, mnk[3 * t], mnk[3 * t + 1], mnk[3 * t + 2]);
+        std::vector<dbcsr_kernel_cfg> pred(ntriples);
+        const dbcsr_status ps = dbcsr_mlp_predict_best(prec, params, mnk, ntriples, pred.data(), nullptr);
+        if (ps != DBCSR_OK) dbg::fail(ps, "tune_predicted: prediction failed");
+        const auto space = dbg::tune_space(prec);
+        const dbg::TuneCfg dflt = dbg::default_cfg(prec);
+        cudaStream_t s = nullptr;
+        for (int32_t t = 0; t < ntriples; ++t) {
+            const int m = mnk[3 * t], n = mnk[3 * t + 1], k = mnk[3 * t + 2];
+            dbg::SynthStack st(m, n, k, stack_len, dbg::is_bf16(prec), s);
+            // measured time judges the prediction: kept if within tolerance of the default,
+            // otherwise the exhaustive search over the space decides
+            dbg::TuneCfg chosen = from_c(pred[t]);
+            const double tp = st.time(prec, chosen, reps, s);
+            const double td = st.time(prec, dflt, reps, s);
+            const bool fb = !(tp <= td * (1.0 + tolerance));
+            if (fb) {
+                double best = 1e300;
+                for (const auto& c : space) {
+                    const double ms = st.time(prec, c, reps, s);
+                    if (ms < best) {
+                        best = ms;
+                        chosen = c;
+                    }
+                }
+            }
+            if (fell_back) fell_back[t] = fb ? 1 : 0;
+            std::lock_guard<std::mutex> lock(dbg::g_tune_mu);
+            dbg::g_tune[{prec, m, n, k}] = chosen;
+        }
+    });
+}
+
 dbcsr_status dbcsr_tune_set(int32_t prec, int32_t m, int32_t n, int32_t k, const dbcsr_kernel_cfg* cfg) {
     return guard([&] {
         dbg::check_triple(prec, m, n, k);

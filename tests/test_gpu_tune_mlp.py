@@ -137,3 +137,29 @@ def test_mlp_predicted_configs_gain_over_default(gb):
     print(f"held-out: predicted/best {gm_pred:.3f} (median {np.median(r_pred):.3f}), default/best {gm_def:.3f}")
     assert gm_pred <= gm_def * 1.02
     gb.tune_clear()
+
+
+def test_predictor_with_exhaustive_fallback(gb):
+    triples = [(13, 13, 13), (5, 13, 13)]
+    params = gb.mlp_init(10, seed=5)
+    pred = gb.mlp_predict_best(params, triples)
+    space = gb.tune_space(gb.DBCSR_FP64)
+
+    def key(c):
+        return (c.tpb, c.ctas_per_sm, c.colmajor, c.prefetch2)
+
+    # an infinite tolerance always keeps the prediction
+    gb.tune_clear()
+    fb = gb.tune_predicted(params, triples, stack_len=20000, reps=2, tolerance=float("inf"))
+    assert fb == [False, False]
+    for t, c in zip(triples, pred):
+        got, found = gb.tune_get(gb.DBCSR_FP64, *t)
+        assert found and key(got) == key(c)
+    # a tolerance of -1 never does: the exhaustive search decides, among the space
+    gb.tune_clear()
+    fb = gb.tune_predicted(params, triples, stack_len=20000, reps=2, tolerance=-1.0)
+    assert fb == [True, True]
+    for t in triples:
+        got, found = gb.tune_get(gb.DBCSR_FP64, *t)
+        assert found and key(got) in {key(c) for c in space}
+    gb.tune_clear()
