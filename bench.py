@@ -495,10 +495,10 @@ def main():
     # then FP64 (and, for comparison, the ladder with plain BF16 products)
     mixed = None
     if not args.no_mixed:
-        def time_mixed(low):
+        def time_mixed(low, correction=False):
             def one():
                 return gb.sign_iterate(H, h.mu, w.eps_filter, w.tol, prec=gb.DBCSR_MIXED, switch_tol=1e-4,
-                                       low=low, verbose=args.verbose)
+                                       low=low, low_correction=correction, verbose=args.verbose)
             for _ in range(args.warmup):
                 one()
             barrier()
@@ -537,6 +537,15 @@ def main():
         mixed["plain_bf16"] = {"time_to_p_ms": mps / args.steps, "iterations": rp_.report.iterations,
                                "fp64_from_step": rp_.report.fp64_from,
                                "de_band_per_atom_vs_fp64": abs(rp_.report.e_band - ebands[-1]) / h.n_atoms}
+        # option beyond the FP64 tail: its update correction X (X^2 - 1) in split BF16
+        rc_, mcs, _ = time_mixed(gb.DBCSR_BF16X3, correction=True)
+        mixed["low_correction"] = {"time_to_p_ms": mcs / args.steps,
+                                   "speedup_vs_fp64": (ms_all / args.steps) / (mcs / args.steps),
+                                   "iterations": rc_.report.iterations, "converged": bool(rc_.report.converged),
+                                   "stalled": bool(rc_.report.stalled), "residual": rc_.report.residual,
+                                   "de_band_per_atom_vs_fp64": abs(rc_.report.e_band - ebands[-1]) / h.n_atoms,
+                                   "note": "DBCSR_SIGN_LOW_CORRECTION: X*X, residual, test, filter and traces "
+                                           "in FP64; the update's correction product in split BF16"}
 
     # end to end through the public API: inputs from pinned host memory, report read back
     e2e = None

@@ -107,6 +107,13 @@ typedef struct {
  * every product and symmetrises the final X. */
 #define DBCSR_SIGN_FULL_PRODUCTS 1
 #define DBCSR_SIGN_PLAIN_BF16 2
+/* DBCSR_MIXED, after the switch: the update X <- 1.5 X - 0.5 X X2 is taken as
+ * X - 0.5 X (X2 - 1), with the product X (X2 - 1) in split BF16.  Near convergence
+ * X2 - 1 is small, so the error of that product (about 2^-16 of |X| |X2 - 1|) stays far
+ * below the eps_filter truncation; X*X, the residual, the convergence test, the filter
+ * and the traces stay FP64.  Off by default: the default FP64 tier computes both
+ * products in FP64. */
+#define DBCSR_SIGN_LOW_CORRECTION 4
 
 #define DBCSR_MAX_HISTORY 128
 

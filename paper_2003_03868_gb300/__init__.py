@@ -236,11 +236,12 @@ class SignResult:
         return [self.report.residual_history[i] for i in range(n)]
 
 
-def _sign_flags(full_products: bool, low: int) -> int:
+def _sign_flags(full_products: bool, low: int, low_correction: bool = False) -> int:
     if low not in (DBCSR_BF16, DBCSR_BF16X3):
         raise ValueError("low must be DBCSR_BF16 or DBCSR_BF16X3")
     return ((_ffi.DBCSR_SIGN_FULL_PRODUCTS if full_products else 0)
-            | (_ffi.DBCSR_SIGN_PLAIN_BF16 if low == DBCSR_BF16 else 0))
+            | (_ffi.DBCSR_SIGN_PLAIN_BF16 if low == DBCSR_BF16 else 0)
+            | (_ffi.DBCSR_SIGN_LOW_CORRECTION if low_correction else 0))
 
 
 def pool_trim(keep_bytes: int = 0) -> None:
@@ -251,14 +252,15 @@ def pool_trim(keep_bytes: int = 0) -> None:
 def sign_iterate(H: Matrix, mu: float, eps_filter: float, tol: float, max_iter: int = 100,
                  prec: int = DBCSR_FP64, switch_tol: float = 1e-4, stall_ratio: float = 0.5,
                  P: Matrix | None = None, verbose: bool = False, raise_on_notconv: bool = False,
-                 full_products: bool = False, low: int = DBCSR_BF16X3) -> SignResult:
+                 full_products: bool = False, low: int = DBCSR_BF16X3, low_correction: bool = False) -> SignResult:
     """Density matrix P = (1 - sign(H - mu 1)) / 2 by the Newton-Schulz iteration.
 
     With prec=DBCSR_MIXED, `low` picks the product of the low-precision tier:
-    the split DBCSR_BF16X3 (default) or plain DBCSR_BF16."""
+    the split DBCSR_BF16X3 (default) or plain DBCSR_BF16; low_correction takes the
+    FP64 tier's update correction X (X^2 - 1) in split BF16 (DBCSR_SIGN_LOW_CORRECTION)."""
     P = Matrix(H.blk_size, H.stream) if P is None else P
     o = SignOpts(float(eps_filter), float(tol), int(max_iter), int(prec), float(switch_tol), float(stall_ratio),
-                 1 if verbose else 0, _sign_flags(full_products, low))
+                 1 if verbose else 0, _sign_flags(full_products, low, low_correction))
     rep = SignReport()
     st = lib().dbcsr_sign_iterate(H.handle, float(mu), C.byref(o), P.handle, C.byref(rep))
     if st != _ffi.DBCSR_OK and (st != _ffi.DBCSR_ENOTCONV or raise_on_notconv):
@@ -268,7 +270,7 @@ def sign_iterate(H: Matrix, mu: float, eps_filter: float, tol: float, max_iter: 
 
 def sign_iterate_batched(Hs, mus, eps_filter: float, tol: float, max_iter: int = 100, prec: int = DBCSR_FP64,
                          switch_tol: float = 1e-4, stall_ratio: float = 0.5, verbose: bool = False,
-                         low: int = DBCSR_BF16X3):
+                         low: int = DBCSR_BF16X3, low_correction: bool = False):
     """Density matrices of many independent systems in one batch (dbcsr_sign_iterate_batched).
 
     Returns (list of P matrices, list of SignReport, status)."""
@@ -278,7 +280,7 @@ def sign_iterate_batched(Hs, mus, eps_filter: float, tol: float, max_iter: int =
     parr = (C.c_void_p * n)(*[p.handle.value for p in Ps])
     mu = np.ascontiguousarray(mus, dtype=np.float64)
     o = SignOpts(float(eps_filter), float(tol), int(max_iter), int(prec), float(switch_tol), float(stall_ratio),
-                 1 if verbose else 0, _sign_flags(False, low))
+                 1 if verbose else 0, _sign_flags(False, low, low_correction))
     reps = (SignReport * n)()
     st = lib().dbcsr_sign_iterate_batched(n, harr, _ptr(mu), C.byref(o), parr, reps)
     if st not in (_ffi.DBCSR_OK, _ffi.DBCSR_ENOTCONV):

@@ -10,7 +10,7 @@ LIB_PATH = os.path.join(HERE, "libdbcsr_gb.so")
 DBCSR_OK, DBCSR_EINVAL, DBCSR_ENOMEM, DBCSR_ECAPACITY, DBCSR_ECUDA = 0, 1, 2, 3, 4
 DBCSR_ENAN, DBCSR_ENOTCONV, DBCSR_ETIMEOUT, DBCSR_ESTATE = 5, 6, 7, 8
 DBCSR_FP64, DBCSR_BF16, DBCSR_MIXED, DBCSR_BF16X3 = 0, 2, 3, 4
-DBCSR_SIGN_FULL_PRODUCTS, DBCSR_SIGN_PLAIN_BF16 = 1, 2
+DBCSR_SIGN_FULL_PRODUCTS, DBCSR_SIGN_PLAIN_BF16, DBCSR_SIGN_LOW_CORRECTION = 1, 2, 4
 MAX_HISTORY = 128
 
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECAPACITY", 4: "ECUDA", 5: "ENAN", 6: "ENOTCONV",

@@ -155,6 +155,7 @@ dbcsr_status sign_iterate_batched(int32_t nsys, dbcsr_matrix_* const* H, const d
     const bool full = (o.flags & DBCSR_SIGN_FULL_PRODUCTS) != 0;
     const int low = (o.flags & DBCSR_SIGN_PLAIN_BF16) ? DBCSR_BF16 : DBCSR_BF16X3;
     const bool full_mixed = o.prec == DBCSR_MIXED && low == DBCSR_BF16;
+    const bool correction = o.prec == DBCSR_MIXED && (o.flags & DBCSR_SIGN_LOW_CORRECTION) != 0;
 
     const auto t0 = std::chrono::steady_clock::now();
     cudaStream_t st = H[0]->stream;
@@ -449,8 +450,15 @@ dbcsr_status sign_iterate_batched(int32_t nsys, dbcsr_matrix_* const* H, const d
             tier = DBCSR_FP64;
             first_fp64 = it + 1;
         }
-        multiply(-0.5, X.get(), X2.get(), 1.5, X.get(), o.eps_filter, tier, &ms, false, sym);
-        account(ms, tier);
+        if (correction && tier == DBCSR_FP64) {
+            // X <- X - 0.5 X (X2 - 1): the small correction in split BF16, X itself in FP64
+            scale_shift(X2.get(), 1.0, -1.0);
+            multiply(-0.5, X.get(), X2.get(), 1.0, X.get(), o.eps_filter, DBCSR_BF16X3, &ms, false, sym);
+            account(ms, DBCSR_BF16X3);
+        } else {
+            multiply(-0.5, X.get(), X2.get(), 1.5, X.get(), o.eps_filter, tier, &ms, false, sym);
+            account(ms, tier);
+        }
     }
     // systems still running at max_iter
     for (int32_t sid : act) done[sid] = 3;

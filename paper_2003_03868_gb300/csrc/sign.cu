@@ -55,6 +55,7 @@ dbcsr_status sign_iterate(dbcsr_matrix_* H, double mu, const dbcsr_sign_opts* op
     const bool full = (o.flags & DBCSR_SIGN_FULL_PRODUCTS) != 0;
     const int low = (o.flags & DBCSR_SIGN_PLAIN_BF16) ? DBCSR_BF16 : DBCSR_BF16X3;
     const bool full_mixed = o.prec == DBCSR_MIXED && low == DBCSR_BF16;
+    const bool correction = o.prec == DBCSR_MIXED && (o.flags & DBCSR_SIGN_LOW_CORRECTION) != 0;
 
     const auto t0 = std::chrono::steady_clock::now();
     cudaStream_t s = H->stream;
@@ -126,8 +127,15 @@ dbcsr_status sign_iterate(dbcsr_matrix_* H, double mu, const dbcsr_sign_opts* op
                 break;
             }
         }
-        multiply(-0.5, X.get(), X2.get(), 1.5, X.get(), o.eps_filter, tier, &st, false, sym);
-        account(st, tier);
+        if (correction && tier == DBCSR_FP64) {
+            // X <- X - 0.5 X (X2 - 1): the small correction in split BF16, X itself in FP64
+            scale_shift(X2.get(), 1.0, -1.0);
+            multiply(-0.5, X.get(), X2.get(), 1.0, X.get(), o.eps_filter, DBCSR_BF16X3, &st, false, sym);
+            account(st, DBCSR_BF16X3);
+        } else {
+            multiply(-0.5, X.get(), X2.get(), 1.5, X.get(), o.eps_filter, tier, &st, false, sym);
+            account(st, tier);
+        }
         if (it - 1 < DBCSR_MAX_HISTORY) r.nnzb_history[it - 1] = X->nnzb;
     }
     // X of a mixed run is symmetric only to the low tier's accuracy (both triangles formed with

@@ -151,12 +151,13 @@ def test_bf16_long_products_span_several_panels(gb):
     assert np.all(np.abs(data - ref.data) <= 2 * 920 * U32 * mag.data + 1e-300)
 
 
-@pytest.mark.parametrize("low", ["bf16x3", "bf16"])
+@pytest.mark.parametrize("low", ["bf16x3", "bf16", "bf16x3+correction"])
 @pytest.mark.parametrize("n_mol,basis,eps", [(24, (13, 5), 1e-7), (16, (23, 7), 1e-6)])
 def test_mixed_sign_matches_fp64_oracle(gb, n_mol, basis, eps, low):
     h = synth.build_hamiltonian(synth.small(n_mol, basis=basis, seed=990 + n_mol))
-    lo = gb.DBCSR_BF16X3 if low == "bf16x3" else gb.DBCSR_BF16
-    g = gb.sign_iterate(gb.Matrix.of(h.H), 0.0, eps, 1e-8, prec=gb.DBCSR_MIXED, switch_tol=1e-4, low=lo)
+    lo = gb.DBCSR_BF16 if low == "bf16" else gb.DBCSR_BF16X3
+    g = gb.sign_iterate(gb.Matrix.of(h.H), 0.0, eps, 1e-8, prec=gb.DBCSR_MIXED, switch_tol=1e-4, low=lo,
+                        low_correction=low.endswith("correction"))
     o = sign.sign_iterate(bsr.Mat.of(h.H), 0.0, eps, 1e-8)
     assert g.report.fp64_from > 1                     # some steps ran in the low tier
     assert g.converged or g.report.stalled
