@@ -86,23 +86,31 @@ class Clocks:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        rows = []
-        for line in open(self.path):
-            f = [x.strip() for x in line.split(",")]
-            if len(f) < 9:
-                continue
-            try:
-                rows.append((float(f[1]), float(f[2]), f[5:9]))
-            except ValueError:
-                continue
+        with open(self.path) as f:
+            out = parse_clock_samples(f)
         os.unlink(self.path)
-        if not rows:
-            return None
-        sm = sorted(r[0] for r in rows)
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[2]) if v.lower() == "active"})
-        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
-                "samples": len(rows)}
+        return out
+
+
+def parse_clock_samples(lines):
+    """Median SM clock, the largest max clock and the throttle reasons seen, from
+    nvidia-smi lines of Clocks.Q (csv, noheader, nounits); None without samples."""
+    rows = []
+    for line in lines:
+        f = [x.strip() for x in line.split(",")]
+        if len(f) < 9:
+            continue
+        try:
+            rows.append((float(f[1]), float(f[2]), f[5:9]))
+        except ValueError:
+            continue
+    if not rows:
+        return None
+    sm = sorted(r[0] for r in rows)
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    reasons = sorted({names[i] for r in rows for i, v in enumerate(r[2]) if v.lower() == "active"})
+    return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
+            "samples": len(rows)}
 
 
 def oracle_sample(h, w, steps: int):
