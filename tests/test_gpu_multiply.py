@@ -202,3 +202,36 @@ def test_pool_trim_keeps_live_matrices(gb):
         assert np.array_equal(x, y)
     gb.multiply(1.0, A, A, 0.0, C_, 0.0)         # the pool grows again on demand
     _assert_same(C_, bsr.multiply(1.0, Ao, Ao))
+
+
+def _one_dense_row(nb, seed):
+    """Blocks of edge 1-3; row 0 holds every block, the other rows their diagonal and
+    three random blocks, so row 0 of A*A has ~nb candidates and nb products per block."""
+    from synth.waterbox import BlockMatrix
+    rng = np.random.default_rng(seed)
+    bs = rng.integers(1, 4, nb).astype(np.int32)
+    rows = [np.arange(nb)]
+    for i in range(1, nb):
+        rows.append(np.unique(np.concatenate([[i], rng.choice(nb, 3, replace=False)])))
+    rp = np.zeros(nb + 1, dtype=np.int64)
+    np.cumsum([len(r) for r in rows], out=rp[1:])
+    col = np.concatenate(rows).astype(np.int32)
+    rr = np.repeat(np.arange(nb), np.diff(rp))
+    vals = rng.uniform(-1, 1, int((bs[rr].astype(np.int64) * bs[col]).sum()))
+    return BlockMatrix(bs, rp, col, vals)
+
+
+@pytest.mark.parametrize("eps", [0.0, 0.5])
+def test_wide_rows_take_the_global_and_ordered_paths(gb, eps):
+    # row 0 has 9,000 A blocks (at least 4,096 selects the ordered FP64 bound) and about
+    # 9,000 candidates (too many for the shared-memory accumulators and stack cursors, which
+    # fit about 6,000 and 8,000)
+    a = _one_dense_row(9000, 8)
+    (A, Ao) = _pair(gb, a)
+    C = gb.Matrix(A.blk_size, A.stream)
+    st = gb.multiply(1.0, A, A, 0.0, C, eps)
+    Co, info = bsr.multiply(1.0, Ao, Ao, 0.0, None, eps, info=True)
+    _assert_same(C, Co)
+    assert st.n_candidates == info.unfiltered.nnzb
+    if eps == 0.0:
+        assert st.flops == info.flops
