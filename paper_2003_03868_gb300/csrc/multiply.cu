@@ -844,16 +844,18 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 
 // Product metadata of 32 consecutive stack entries, one per lane: packed-tile offsets of
 // its A and B blocks and its inner size k.
+// Offsets in tile units (A tiles are multiples of 256 elements, B tiles of 128), so that
+// they fit 32 bits and a metadata shuffle is one instruction.
 struct BfMeta {
-    int64_t ao, bo;
+    uint32_t ao, bo;
     int kq;
 };
 __device__ __forceinline__ BfMeta bf_meta(const SmmBf16Args& G, int64_t base, int64_t pe, int lane) {
     BfMeta m{0, 0, 0};
     if (base + lane < pe) {
         const int32_t ai = G.base.prod_a[base + lane], bi = G.base.prod_b[base + lane];
-        m.ao = G.a_po[ai];
-        m.bo = G.b_po[bi];
+        m.ao = (uint32_t)(G.a_po[ai] >> 8);
+        m.bo = (uint32_t)(G.b_po[bi] >> 7);
         m.kq = G.base.bs[G.base.a_col[ai]];
     }
     return m;
@@ -901,8 +903,8 @@ __global__ void __launch_bounds__(256, 2) k_smm_bf16(int64_t nlist, const int64_
             if (pp < np) {
                 const bool in_cur = (pp >> 5) == cbat;
                 const int src = (int)(pp & 31);
-                const int64_t ao = __shfl_sync(0xffffffffu, in_cur ? cur.ao : nxt.ao, src);
-                const int64_t bo = __shfl_sync(0xffffffffu, in_cur ? cur.bo : nxt.bo, src);
+                const int64_t ao = (int64_t)__shfl_sync(0xffffffffu, in_cur ? cur.ao : nxt.ao, src) << 8;
+                const int64_t bo = (int64_t)__shfl_sync(0xffffffffu, in_cur ? cur.bo : nxt.bo, src) << 7;
                 const int KT = (__shfl_sync(0xffffffffu, in_cur ? cur.kq : nxt.kq, src) + 15) >> 4;
                 const uint32_t st = ring + (uint32_t)(slot_p * SB);
                 const unsigned char* ag = reinterpret_cast<const unsigned char*>(G.a16 + ao);
@@ -1459,6 +1461,9 @@ void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbc
                 const int64_t* src[2] = {a_po.p + A->nnzb, b_po.p + B->nnzb};
                 read_i64s(src, 2, tot, s);
             }
+            // the kernel addresses tiles by 32-bit tile-unit offsets
+            if ((tot[0] >> 8) > 0xffffffffll || (tot[1] >> 7) > 0xffffffffll)
+                fail(DBCSR_ECAPACITY, "multiply: BF16 packs beyond 2^32 tiles");
             a16.alloc(std::max<int64_t>(tot[0], 1), s);
             b16.alloc(std::max<int64_t>(tot[1], 1), s);
             if (split) {
