@@ -266,6 +266,41 @@ def add_identity(M: Mat, scale: float, shift: float) -> Mat:
     return out
 
 
+def add(alpha: float, A: Mat, beta: float, B: Mat) -> Mat:
+    """alpha*A + beta*B on the union of the two patterns, unfiltered (DBCSR's add).
+
+    A block present in one operand only is that operand's term alone; in a block of
+    both, every element is alpha*a + beta*b (two rounded products, then their sum)."""
+    if not np.array_equal(A.bs, B.bs):
+        raise ValueError("block sizes differ")
+    nblk = A.nblk
+    ka = A.rows.astype(np.int64) * nblk + A.col
+    kb = B.rows.astype(np.int64) * nblk + B.col
+    keys = np.union1d(ka, kb)
+    rows = (keys // nblk).astype(np.int32)
+    rp = np.zeros(nblk + 1, dtype=np.int64)
+    np.cumsum(np.bincount(rows, minlength=nblk), out=rp[1:])
+    area = A.bs[rows].astype(np.int64) * A.bs[(keys % nblk)].astype(np.int64)
+    out = Mat(A.bs, rp, (keys % nblk).astype(np.int32), np.zeros(int(area.sum())))
+
+    def scatter(M: Mat, k: np.ndarray, scale: float):
+        """M's elements times scale at their places in out, and where they land."""
+        dst_blk = np.searchsorted(keys, k)
+        areas = np.diff(M.boff)
+        blk = np.repeat(np.arange(M.nnzb), areas)
+        dst = out.boff[dst_blk[blk]] + (np.arange(M.data.shape[0]) - M.boff[blk])
+        term = np.zeros(out.data.shape[0])
+        term[dst] = scale * M.data
+        has = np.zeros(out.data.shape[0], dtype=bool)
+        has[dst] = True
+        return term, has
+
+    ta, ha = scatter(A, ka, alpha)
+    tb, hb = scatter(B, kb, beta)
+    out.data[:] = np.where(ha & hb, ta + tb, np.where(ha, ta, tb))
+    return out
+
+
 def num_threads() -> int:
     return int(lib().oracle_num_threads())
 

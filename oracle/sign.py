@@ -25,11 +25,41 @@ Readings taken where the paper is silent:
   that does not (r_k > r_{k-1} / 2 after r_{k-1} < r_{k-2} / 2) means filtering
   has stalled the iteration (reported, not raised);
 * Tr(P) = (N - Tr X) / 2 and the band energy is E = Tr(P H), with no spin factor.
+
+Higher orders (section "Sign-Method": third- and fifth-order steps from Pade
+approximants, up to seventh order; the fifth-order step is printed as
+X_{k+1} = X_k (35 X^8 - 180 X^6 + 378 X^4 - 420 X^2 + 315) / 128 and taken with four
+products per iteration):
+
+* the step of order n + 1 is X <- X p_n(X^2) with p_n(y) = sum_{j<=n} c_j (1 - y)^j and
+  c_j = binom(2j, j) / 4^j, the series of (1 - z)^(-1/2) cut after j = n (sign(x) =
+  x (x^2)^(-1/2) = x (1 - (1 - x^2))^(-1/2)).  n = 1, 2, 3 give the refinement functions
+  f_1, f_2, f_3 printed in section "OT/IR", n = 4 the printed fifth-order step;
+* the paper names neither the four products nor where the filter sits between them.
+  The reading taken, with Y = filter(X X) (the residual test as above), Z = 1 - Y
+  (no product), Z2 = filter(Z Z) and the pairs q_i = c_2i + c_2i+1 Z:
+  p_n = q_0 + Z2 R with R = sum_{i>=1} Z2^(i-1) q_i (plus c_n Z2^(n/2 - 1) when n is even),
+  R summed innermost first, R <- filter(Z2 R + q_i); then V = filter(Z2 R),
+  U = q_0 + V (an unfiltered sum) and X <- filter(X U).  For n = 2, R = c_2 and
+  U = q_0 + c_2 Z2 directly.  For n = 4 that is exactly four products: X X, Z Z, Z2 R,
+  X U.  Orders 3, 4, 6, 7 take 3, 4, 5, 5.  Two choices here decide how far the
+  filtered iteration gets:
+  - powers of Z rather than of Y (the printed form): the c_j are positive and at most
+    1, so no intermediate is a cancelling sum of large terms;
+  - near convergence U - 1 is c_1 Z, a matrix of residual-sized blocks.  Filtering it
+    on its own (as the output of a product such as Z2 R + q_0) drops the corrections of
+    blocks just above eps, which then are never made: at eps 1e-7 the seventh order
+    stalled near r = 1e-8 that way, where Newton-Schulz reaches 4e-12.  Every filtered
+    product here holds either a Z2 factor or X, as Newton-Schulz's X (3 - Y) / 2 does;
+* the stall test above is kept for every order: per eigenvalue the step maps
+  e = 1 - x^2 to e' with e'/e increasing in e, the premise of that test.
 """
 from __future__ import annotations
 
 import dataclasses
+import math
 import time
+from fractions import Fraction
 
 import numpy as np
 
@@ -51,6 +81,8 @@ class SignResult:
     n_products: int
     seconds: float
     nnzb_history: list         # blocks of X after each step
+    multiplies: int = 0        # matrix products formed
+    order: int = 2
 
 
 def gershgorin(H: bsr.Mat, mu: float) -> float:
@@ -58,17 +90,74 @@ def gershgorin(H: bsr.Mat, mu: float) -> float:
     return float(bsr.abs_row_sums(H, mu).max())
 
 
+def series_coefficients(order: int) -> list:
+    """Exact c_0..c_n (n = order - 1), c_j = binom(2j, j) / 4^j: p_n(y) = sum_j c_j (1 - y)^j."""
+    return [Fraction(math.comb(2 * j, j), 4 ** j) for j in range(order)]
+
+
+def pade_coefficients(order: int) -> list:
+    """Exact coefficients a_0..a_n of the same p_n in powers of y, p_n(y) = sum_i a_i y^i
+    (the form the paper prints)."""
+    c = series_coefficients(order)
+    a = [Fraction(0)] * len(c)
+    for j, cj in enumerate(c):
+        for i in range(j + 1):                                   # (1 - y)^j, binomially
+            a[i] += cj * math.comb(j, i) * (-1) ** i
+    return a
+
+
+def _higher_order_update(X: bsr.Mat, Y: bsr.Mat, order: int, eps: float):
+    """X p_n(Y) for Y = filter(X X), by the four-product scheme of the module header.
+    Returns the new X and the (flops, block products, matrix products) it took."""
+    n = order - 1
+    c = [float(v) for v in series_coefficients(order)]
+    work = [0, 0, 0]
+
+    def mult(alpha, A, B, beta=0.0, Cin=None):
+        C, info = bsr.multiply(alpha, A, B, beta, Cin, eps=eps, info=True)
+        work[0] += info.flops
+        work[1] += info.n_products
+        work[2] += 1
+        return C
+
+    Z = bsr.add_identity(Y, -1.0, 1.0)                           # 1 - X^2
+
+    def pair(i):                                                 # c_2i+1 Z + c_2i 1
+        return bsr.add_identity(Z, c[2 * i + 1], c[2 * i])
+
+    Z2 = mult(1.0, Z, Z)
+    m = n // 2
+    if n % 2 == 0:
+        R = bsr.add(1.0, pair(m - 1), c[n], Z2)
+        i = m - 2
+    else:
+        R = pair(m)
+        i = m - 1
+    if n == 2:
+        U = R                                                    # q_0 + c_2 Z2
+    else:
+        while i >= 1:
+            R = mult(1.0, Z2, R, 1.0, pair(i))
+            i -= 1
+        U = bsr.add(1.0, pair(0), 1.0, mult(1.0, Z2, R))
+    return mult(1.0, X, U), work
+
+
 def sign_iterate(H: bsr.Mat, mu: float, eps: float, tol: float, max_iter: int = 100,
-                 stall_ratio: float = 0.5) -> SignResult:
+                 stall_ratio: float = 0.5, order: int = 2) -> SignResult:
     t0 = time.perf_counter()
     n = H.n
     alpha = gershgorin(H, mu)
     X = bsr.add_identity(H, 1.0 / alpha, -mu / alpha)          # (H - mu 1) / alpha
+    if not 2 <= order <= 7:
+        raise ValueError("order must be 2 to 7")
     res, flops, nprod, hist = [], 0, 0, []
+    mults = 0
     converged = stalled = False
     it = 0
     while it < max_iter:
         X2, info = bsr.multiply(1.0, X, X, eps=eps, info=True)
+        mults += 1
         it += 1
         flops += info.flops
         nprod += info.n_products
@@ -80,17 +169,24 @@ def sign_iterate(H: bsr.Mat, mu: float, eps: float, tol: float, max_iter: int = 
         if len(res) >= 3 and res[-2] < stall_ratio * res[-3] and r > stall_ratio * res[-2]:
             stalled = True
             break
-        T = bsr.add_identity(X2, -1.0, 3.0)                        # 3 1 - X^2
-        X, info = bsr.multiply(0.5, X, T, eps=eps, info=True)      # X (3 1 - X^2) / 2
-        flops += info.flops
-        nprod += info.n_products
+        if order == 2:
+            T = bsr.add_identity(X2, -1.0, 3.0)                    # 3 1 - X^2
+            X, info = bsr.multiply(0.5, X, T, eps=eps, info=True)  # X (3 1 - X^2) / 2
+            flops += info.flops
+            nprod += info.n_products
+            mults += 1
+        else:
+            X, (f, npr, nm) = _higher_order_update(X, X2, order, eps)
+            flops += f
+            nprod += npr
+            mults += nm
         hist.append(X.nnzb)
     P = bsr.add_identity(X, -0.5, 0.5)                             # (1 - X) / 2
     trace_p = bsr.trace(P)
     e_band = bsr.trace_product(P, H)
     return SignResult(X=X, P=P, iterations=it, residuals=res, converged=converged, stalled=stalled,
                       alpha=alpha, trace_p=trace_p, e_band=e_band, flops=flops, n_products=nprod,
-                      seconds=time.perf_counter() - t0, nnzb_history=hist)
+                      seconds=time.perf_counter() - t0, nnzb_history=hist, multiplies=mults, order=order)
 
 
 def band_energy(P: bsr.Mat, H: bsr.Mat) -> float:
