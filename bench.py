@@ -226,6 +226,86 @@ def run_batch(args, gb, synth, torch, barrier):
     return 0
 
 
+# matrix products per iteration of the sign iteration of each order (the last iteration of a
+# converged run forms only X X)
+PRODUCTS_PER_ITERATION = {2: 2, 3: 3, 4: 4, 5: 4, 6: 5, 7: 5}
+
+
+def run_orders(args, gb, synth, torch, barrier, w, h):
+    """The sign iteration of every order from 2 (Newton-Schulz) to 7 on one system:
+    time-to-P, iterations, products and flops in FP64, and with the mixed-precision ladder."""
+    from paper_2003_03868_gb300 import ranks
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+    stream = torch.cuda.current_stream()
+    H = gb.Matrix.of(h.H, stream=stream.cuda_stream)
+    orders = [int(o) for o in args.orders.split(",")]
+    clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
+    l0 = gb.lib().dbcsr_launch_count()
+
+    def leg(order, prec):
+        def one():
+            return gb.sign_iterate(H, h.mu, w.eps_filter, w.tol, prec=prec, switch_tol=w.switch or 1e-4,
+                                   order=order, verbose=args.verbose)
+        for _ in range(args.warmup):
+            one()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        flops = ms_mult = ms_sym = ms_low = 0.0
+        for _ in range(args.steps):
+            r = one()
+            flops += r.report.flops
+            ms_mult += r.report.ms_multiply
+            ms_sym += r.report.ms_symbolic
+            ms_low += r.report.ms_low
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ms, flops_all = ranks.job_timing(e0.elapsed_time(e1) / args.steps, flops / args.steps, dist, "cuda")
+        it = r.report.iterations
+        return {"order": order, "time_to_p_ms": ms, "iterations": it,
+                # a run that converged or stalled ended on the X X of its last iteration
+                "products": (PRODUCTS_PER_ITERATION[order] * (it - 1) + 1
+                             if (r.report.converged or r.report.stalled) else None),
+                "converged": bool(r.report.converged), "stalled": bool(r.report.stalled),
+                "residual": r.report.residual, "flops_per_step": flops / args.steps,
+                "value": flops_all / (ms * 1e-3) / 1e12,
+                "kernel_tflops": flops / (ms_mult * 1e-3) / 1e12 if ms_mult > 0 else None,
+                "ms_multiply": ms_mult / args.steps, "ms_symbolic": ms_sym / args.steps,
+                "ms_low": ms_low / args.steps, "fp64_from_step": r.report.fp64_from,
+                "trace_p": r.report.trace_p, "e_band": r.report.e_band}
+
+    f64 = [leg(o, gb.DBCSR_FP64) for o in orders]
+    mixed = [] if args.no_mixed else [leg(o, gb.DBCSR_MIXED) for o in orders]
+    launches = gb.lib().dbcsr_launch_count() - l0
+    clk = clocks.stop()
+    ref = next((x for x in f64 if x["order"] == 2), f64[0])
+    for x in f64 + mixed:
+        x["de_band_per_atom_vs_fp64_order2"] = abs(x["e_band"] - ref["e_band"]) / h.n_atoms
+        x["speedup_vs_fp64_order2"] = ref["time_to_p_ms"] / x["time_to_p_ms"]
+    best = min(f64, key=lambda x: x["time_to_p_ms"])
+    out = {"metric": "time-to-P by sign-iteration order (FP64; best order)", "value": best["time_to_p_ms"],
+           "unit": "ms", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": best["time_to_p_ms"], "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64", "data": "synthetic",
+           "config": {"workload": w.name + "-orders", "n_mol": w.n_mol, "N": w.n,
+                      "blocks": {"O": w.basis[0], "H": w.basis[1]}, "eps_filter": w.eps_filter, "tol": w.tol,
+                      "orders": orders, "mixed_switch": w.switch or 1e-4,
+                      "l2": "inputs larger than L2 (H alone is %.0f MB; 129 MB L2)" % (h.H.data.nbytes / 1e6),
+                      "parallelism": f"replicas x{world}"},
+           "best_order": best["order"], "fp64": f64, "mixed": mixed, "gpu_launches": launches, "clocks": clk}
+    if rank == 0:
+        print(json.dumps(out))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
 def run_mult32(args, gb, synth, torch, barrier):
     """The single product C = A A of the 32-water decay matrix (N = 736, eps 1e-6): one-off
     products (stack builder, block products, filter, with their host round trips) against
@@ -406,12 +486,14 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=2, help="Newton-Schulz steps in the oracle CPU baseline")
     ap.add_argument("--workload", default="sign-1024h2o",
                     choices=["sign-1024h2o", "sign-512h2o", "sign-512h2o-23-7", "sign-4096h2o", "batch-64",
-                             "sign-20736h2o-mlp", "mult-32h2o"],
+                             "sign-20736h2o-mlp", "mult-32h2o", "sign-1024h2o-orders", "sign-4096h2o-orders"],
                     help="sign-512h2o, sign-512h2o-23-7: smaller cases for profiler captures; sign-4096h2o: "
                          "4,096 waters with O/H blocks 23/7 (FP64 and mixed); batch-64: 64 uneven systems "
                          "batched vs one by one; sign-20736h2o-mlp: the mixed iteration on 20,736 waters with "
                          "default, MLP-predicted and exhaustively tuned launch configurations; mult-32h2o: the "
-                         "32-water product, one-off vs planned (CUDA graph)")
+                         "32-water product, one-off vs planned (CUDA graph); sign-1024h2o-orders, "
+                         "sign-4096h2o-orders: the sign iteration of orders 2 to 7 (--orders), FP64 and mixed")
+    ap.add_argument("--orders", default="2,3,4,5,6,7", help="sign-*-orders: the orders to time")
     ap.add_argument("--train-triples", type=int, default=48, help="sign-20736h2o-mlp: autotuned training triples")
     ap.add_argument("--tune-stack", type=int, default=500000, help="products of the autotuner's synthetic stacks")
     ap.add_argument("--predictor-waters", type=int, default=20736, help="sign-20736h2o-mlp: waters of the system")
@@ -459,10 +541,13 @@ def main():
         return (run_predictor if args.workload == "sign-20736h2o-mlp" else run_mult32)(args, gb, synth, torch,
                                                                                          lambda: torch.cuda.synchronize())
     w = {"sign-1024h2o": synth.SIGN_1024, "sign-4096h2o": synth.SIGN_4096,
+         "sign-1024h2o-orders": synth.SIGN_1024, "sign-4096h2o-orders": synth.SIGN_4096,
          "sign-512h2o": synth.Workload("sign-512h2o-dzvp-fp64", 512, (13, 5), synth.configs.BASE_SEED + 12, 1e-7, 1e-9),
          "sign-512h2o-23-7": synth.Workload("sign-512h2o-23-7", 512, (23, 7), synth.configs.BASE_SEED + 13, 1e-6, 1e-8,
                                             1e-4)}[args.workload]
     h = synth.build_hamiltonian(w)
+    if args.workload.endswith("-orders"):
+        return run_orders(args, gb, synth, torch, barrier, w, h)
     stream = torch.cuda.current_stream()
     H = gb.Matrix.of(h.H, stream=stream.cuda_stream)
 

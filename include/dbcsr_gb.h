@@ -91,15 +91,18 @@ typedef struct {
     double stall_ratio;        /* stall test: r_k > ratio*r_{k-1} after r_{k-1} < ratio*r_{k-2} (default 0.5 when <= 0) */
     int32_t verbose;           /* 1: print one line per step to stderr */
     int32_t flags;             /* DBCSR_SIGN_* bits, 0 = defaults */
+    int32_t order;             /* order of the iteration, 2 to 7 (0 = 2, Newton-Schulz); see dbcsr_sign_iterate */
+    int32_t reserved;          /* 0 */
 } dbcsr_sign_opts;
 
 /* dbcsr_sign_opts.flags.  Every product of the iteration has a symmetric exact
- * result.  By default every product forms only the blocks I <= J and copies the
- * blocks I > J as transposes (blocks without a formed twin are dropped), so X stays
- * symmetric and the products cost half.  The low tier of a DBCSR_MIXED iteration
- * uses split-BF16 products (DBCSR_BF16X3), which commute with X to about 1e-5;
- * the final X of a mixed run is replaced by its symmetric part (its diagonal
- * blocks are summed in FP32).
+ * result.  By default every product forms only the blocks I <= J, copies the
+ * blocks I > J as transposes (blocks without a formed twin are dropped) and
+ * replaces each diagonal block by its symmetric part, so X stays exactly symmetric
+ * and the products cost half.  (Left as computed, the antisymmetric part of the
+ * diagonal blocks grows from product to product under mirroring.)  The low tier of
+ * a DBCSR_MIXED iteration uses split-BF16 products (DBCSR_BF16X3), which commute
+ * with X to about 1e-5.
  * DBCSR_SIGN_FULL_PRODUCTS: form both triangles of every product and keep them as
  * computed (no final symmetrisation).
  * DBCSR_SIGN_PLAIN_BF16: DBCSR_MIXED's low tier uses plain BF16 products.  A BF16
@@ -112,7 +115,7 @@ typedef struct {
  * X2 - 1 is small, so the error of that product (about 2^-16 of |X| |X2 - 1|) stays far
  * below the eps_filter truncation; X*X, the residual, the convergence test, the filter
  * and the traces stay FP64.  Off by default: the default FP64 tier computes both
- * products in FP64. */
+ * products in FP64.  Order 2 only (EINVAL with a higher order). */
 #define DBCSR_SIGN_LOW_CORRECTION 4
 
 #define DBCSR_MAX_HISTORY 128
@@ -207,6 +210,18 @@ dbcsr_status dbcsr_copy(dbcsr_matrix dst, dbcsr_matrix src);
 dbcsr_status dbcsr_scale_shift(dbcsr_matrix m, double scale, double shift);
 
 /*
+ * A = alpha * A + beta * B on the union of the two patterns (DBCSR's add; the
+ * higher-order sign iterations of section "Sign-Method" sum polynomial terms with
+ * it).  A block present in one operand only is that operand's term alone.  Each
+ * element is alpha*a + beta*b with both products rounded before the sum (no fused
+ * multiply-add), so results do not depend on the launch.  No filtering.  B may be
+ * the same handle as A.  A's arrays are replaced; B is unchanged.
+ * Errors: EINVAL (null handle, different block sizes), ESTATE (A or B not
+ * finalized, A used by a multiply plan), ENOMEM, ECUDA.
+ */
+dbcsr_status dbcsr_add(double alpha, dbcsr_matrix A, double beta, dbcsr_matrix B);
+
+/*
  * C = beta * C + alpha * A * B, then every block of C with Frobenius norm
  * strictly below eps_filter is removed (diagonal blocks are always kept).
  * The sum over K of each C_IJ is taken in ascending K.  C may be the same
@@ -299,12 +314,17 @@ dbcsr_status dbcsr_trace_product_noalloc(dbcsr_matrix A, dbcsr_matrix B, double*
 dbcsr_status dbcsr_gershgorin(dbcsr_matrix A, double mu, double* out);
 
 /*
- * Density matrix by the second-order Newton-Schulz sign iteration
- * (section "Sign-Method"; S = 1):
+ * Density matrix by the sign iteration (section "Sign-Method"; S = 1):
  *   X_0 = (H - mu 1) / alpha, alpha = dbcsr_gershgorin(H, mu);
  *   repeat: X2 = filter(X X); r = ||X2 - 1||_F / N; stop if r < tol;
- *           X <- filter(1.5 X - 0.5 X X2)          (= X (3 - X^2) / 2);
+ *           X <- filter(X p(X2));
  *   P_out = (1 - X) / 2.
+ * opts->order picks p.  Order 2 (default) is the Newton-Schulz step, taken as
+ * X <- filter(1.5 X - 0.5 X X2) (= X (3 - X^2) / 2).  Orders 3 to 7 are the polynomial
+ * Pade steps p(y) = sum_{j <= order-1} binom(2j, j) / 4^j (1 - y)^j; order 5 is the
+ * printed X (35 X^8 - 180 X^6 + 378 X^4 - 420 X^2 + 315) / 128.  They evaluate p in
+ * powers of Y2 = filter(X2 X2) with a filter after every product: 3, 4, 4, 5 and 5
+ * products per iteration for orders 3, 4, 5, 6 and 7 (order 5: X2, Y2, Y2 U, X U).
  * H must be symmetric with every diagonal block present.  P_out receives the
  * result (its previous content is replaced).  rep may be NULL.  Returns
  * DBCSR_ENOTCONV (P_out and rep still filled) when max_iter or the stall test

@@ -130,6 +130,10 @@ class Matrix:
     def filter(self, eps: float):
         _check(lib().dbcsr_filter(self.handle, float(eps)), "filter")
 
+    def add(self, other: "Matrix", alpha: float = 1.0, beta: float = 1.0):
+        """self <- alpha * self + beta * other on the union of the patterns (dbcsr_add)."""
+        add(alpha, self, beta, other)
+
     def trace(self) -> float:
         return trace(self)
 
@@ -195,6 +199,11 @@ def filter(M: Matrix, eps: float):  # noqa: A001 - the C ABI's name
     M.filter(eps)
 
 
+def add(alpha: float, A: Matrix, beta: float, B: Matrix):
+    """A <- alpha * A + beta * B on the union of the patterns, no filtering (dbcsr_add)."""
+    _check(lib().dbcsr_add(float(alpha), A.handle, float(beta), B.handle), "add")
+
+
 def trace(M: Matrix) -> float:
     out = C.c_double()
     _check(lib().dbcsr_trace(M.handle, C.byref(out)), "trace")
@@ -252,15 +261,17 @@ def pool_trim(keep_bytes: int = 0) -> None:
 def sign_iterate(H: Matrix, mu: float, eps_filter: float, tol: float, max_iter: int = 100,
                  prec: int = DBCSR_FP64, switch_tol: float = 1e-4, stall_ratio: float = 0.5,
                  P: Matrix | None = None, verbose: bool = False, raise_on_notconv: bool = False,
-                 full_products: bool = False, low: int = DBCSR_BF16X3, low_correction: bool = False) -> SignResult:
-    """Density matrix P = (1 - sign(H - mu 1)) / 2 by the Newton-Schulz iteration.
+                 full_products: bool = False, low: int = DBCSR_BF16X3, low_correction: bool = False,
+                 order: int = 2) -> SignResult:
+    """Density matrix P = (1 - sign(H - mu 1)) / 2 by the sign iteration of the given order
+    (2: Newton-Schulz; 3 to 7: the polynomial Pade steps, see dbcsr_sign_iterate).
 
     With prec=DBCSR_MIXED, `low` picks the product of the low-precision tier:
     the split DBCSR_BF16X3 (default) or plain DBCSR_BF16; low_correction takes the
     FP64 tier's update correction X (X^2 - 1) in split BF16 (DBCSR_SIGN_LOW_CORRECTION)."""
     P = Matrix(H.blk_size, H.stream) if P is None else P
     o = SignOpts(float(eps_filter), float(tol), int(max_iter), int(prec), float(switch_tol), float(stall_ratio),
-                 1 if verbose else 0, _sign_flags(full_products, low, low_correction))
+                 1 if verbose else 0, _sign_flags(full_products, low, low_correction), int(order), 0)
     rep = SignReport()
     st = lib().dbcsr_sign_iterate(H.handle, float(mu), C.byref(o), P.handle, C.byref(rep))
     if st != _ffi.DBCSR_OK and (st != _ffi.DBCSR_ENOTCONV or raise_on_notconv):
@@ -270,8 +281,9 @@ def sign_iterate(H: Matrix, mu: float, eps_filter: float, tol: float, max_iter: 
 
 def sign_iterate_batched(Hs, mus, eps_filter: float, tol: float, max_iter: int = 100, prec: int = DBCSR_FP64,
                          switch_tol: float = 1e-4, stall_ratio: float = 0.5, verbose: bool = False,
-                         low: int = DBCSR_BF16X3, low_correction: bool = False):
-    """Density matrices of many independent systems in one batch (dbcsr_sign_iterate_batched).
+                         low: int = DBCSR_BF16X3, low_correction: bool = False, order: int = 2):
+    """Density matrices of many independent systems in one batch (dbcsr_sign_iterate_batched),
+    by the sign iteration of the given order.
 
     Returns (list of P matrices, list of SignReport, status)."""
     n = len(Hs)
@@ -280,7 +292,7 @@ def sign_iterate_batched(Hs, mus, eps_filter: float, tol: float, max_iter: int =
     parr = (C.c_void_p * n)(*[p.handle.value for p in Ps])
     mu = np.ascontiguousarray(mus, dtype=np.float64)
     o = SignOpts(float(eps_filter), float(tol), int(max_iter), int(prec), float(switch_tol), float(stall_ratio),
-                 1 if verbose else 0, _sign_flags(False, low, low_correction))
+                 1 if verbose else 0, _sign_flags(False, low, low_correction), int(order), 0)
     reps = (SignReport * n)()
     st = lib().dbcsr_sign_iterate_batched(n, harr, _ptr(mu), C.byref(o), parr, reps)
     if st not in (_ffi.DBCSR_OK, _ffi.DBCSR_ENOTCONV):

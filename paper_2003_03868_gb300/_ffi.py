@@ -27,7 +27,7 @@ class MultStats(C.Structure):
 class SignOpts(C.Structure):
     _fields_ = [("eps_filter", C.c_double), ("tol", C.c_double), ("max_iter", C.c_int32), ("prec", C.c_int32),
                 ("switch_tol", C.c_double), ("stall_ratio", C.c_double), ("verbose", C.c_int32),
-                ("flags", C.c_int32)]
+                ("flags", C.c_int32), ("order", C.c_int32), ("reserved", C.c_int32)]
 
 
 class SignReport(C.Structure):
@@ -84,6 +84,7 @@ SIGNATURES = [
     ("dbcsr_copy", C.c_int, [P, P]),
     ("dbcsr_scale_shift", C.c_int, [P, C.c_double, C.c_double]),
     ("dbcsr_multiply", C.c_int, [C.c_double, P, P, C.c_double, P, C.c_double, C.c_int32, C.POINTER(MultStats)]),
+    ("dbcsr_add", C.c_int, [C.c_double, P, C.c_double, P]),
     ("dbcsr_filter", C.c_int, [P, C.c_double]),
     ("dbcsr_trace", C.c_int, [P, C.POINTER(C.c_double)]),
     ("dbcsr_trace_product", C.c_int, [P, P, C.POINTER(C.c_double)]),

@@ -149,6 +149,10 @@ dbcsr_status sign_iterate_batched(int32_t nsys, dbcsr_matrix_* const* H, const d
     if (!(o.eps_filter >= 0) || !(o.tol > 0)) fail(DBCSR_EINVAL, "sign_iterate_batched: need eps_filter >= 0 and tol > 0");
     if (o.prec != DBCSR_FP64 && o.prec != DBCSR_MIXED) fail(DBCSR_EINVAL, "sign_iterate_batched: prec must be FP64 or MIXED");
     if (o.prec == DBCSR_MIXED && !(o.switch_tol > 0)) o.switch_tol = 1e-4;
+    if (o.order == 0) o.order = 2;
+    if (o.order < 2 || o.order > 7) fail(DBCSR_EINVAL, "sign_iterate_batched: order must be 2 to 7");
+    if (o.order != 2 && (o.flags & DBCSR_SIGN_LOW_CORRECTION))
+        fail(DBCSR_EINVAL, "sign_iterate_batched: the low-precision correction applies to order 2 only");
     // Every product of the iteration is symmetric in exact arithmetic.  FP64 and split-BF16
     // products compute the blocks I <= J and mirror the rest; a plain BF16 tier forms full
     // products throughout and X's symmetric part is taken at the end.
@@ -338,8 +342,9 @@ dbcsr_status sign_iterate_batched(int32_t nsys, dbcsr_matrix_* const* H, const d
             pm->nel = nel_s;
             pm->norms_valid = false;
             pm->finalized = true;
-            // X of a mixed run is symmetric only to the low tier's accuracy: keep its symmetric part
-            if (o.prec == DBCSR_MIXED && !full) symmetrize(pm);
+            // X of a mixed run with a plain BF16 tier is symmetric only to that tier's accuracy: keep
+            // its symmetric part (mirrored products keep X exactly symmetric)
+            if (full_mixed && !full) symmetrize(pm);
             scale_shift(pm, -0.5, 0.5);
             dbcsr_sign_report& R = rep[sid];
             R.trace_p = trace(pm);
@@ -450,15 +455,7 @@ dbcsr_status sign_iterate_batched(int32_t nsys, dbcsr_matrix_* const* H, const d
             tier = DBCSR_FP64;
             first_fp64 = it + 1;
         }
-        if (correction && tier == DBCSR_FP64) {
-            // X <- X - 0.5 X (X2 - 1): the small correction in split BF16, X itself in FP64
-            scale_shift(X2.get(), 1.0, -1.0);
-            multiply(-0.5, X.get(), X2.get(), 1.0, X.get(), o.eps_filter, DBCSR_BF16X3, &ms, false, sym);
-            account(ms, DBCSR_BF16X3);
-        } else {
-            multiply(-0.5, X.get(), X2.get(), 1.5, X.get(), o.eps_filter, tier, &ms, false, sym);
-            account(ms, tier);
-        }
+        sign_update(X.get(), X2.get(), o.order, correction, o.eps_filter, tier, sym, account);
     }
     // systems still running at max_iter
     for (int32_t sid : act) done[sid] = 3;

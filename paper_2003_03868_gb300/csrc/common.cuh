@@ -8,6 +8,8 @@
 #include <atomic>
 #include <cstdint>
 #include <cstring>
+#include <functional>
+#include <memory>
 #include <stdexcept>
 #include <string>
 #include <utility>
@@ -164,6 +166,10 @@ void read_i64s(const int64_t* const* dev, int k, int64_t* out, cudaStream_t s, c
                int na = 0, int64_t* arr_out = nullptr);
 double read_f64(const double* dev, cudaStream_t s);
 
+// ---- add.cu
+// A <- alpha A + beta B on the union of the patterns (B may be A).
+void add(dbcsr_matrix_* A, double alpha, const dbcsr_matrix_* B, double beta);
+
 // ---- reduce.cu
 double trace(dbcsr_matrix_* m);
 double trace_product(dbcsr_matrix_* a, dbcsr_matrix_* b);
@@ -175,7 +181,8 @@ void trace_product_parts_into(dbcsr_matrix_* a, dbcsr_matrix_* b, double* part, 
 // sym_result: the caller knows alpha*A*B + beta*C is symmetric in exact arithmetic
 // (as every product of the sign iteration is), and the result is made exactly
 // symmetric; blocks without a formed twin (J, I) are dropped.
-//   kSymMirror:  only blocks I <= J are computed, their twins copied as transposes;
+//   kSymMirror:  only blocks I <= J are computed, their twins copied as transposes, and
+//                the diagonal blocks replaced by their symmetric parts;
 //   kSymAverage: both twins are computed and replaced by their symmetric mean
 //                (for operands that commute only approximately, e.g. BF16 products).
 constexpr int kSymNone = 0, kSymMirror = 1, kSymAverage = 2;
@@ -205,6 +212,15 @@ void execute_plan(MultPlan* plan);
 void check_unplanned(const dbcsr_matrix_* m, const char* where);
 
 // ---- sign.cu
+// A matrix with m's block sizes and stream, no pattern yet.
+std::unique_ptr<dbcsr_matrix_> make_like(const dbcsr_matrix_* m, cudaStream_t s);
+// c_0..c_n, c_j = binom(2j, j) / 4^j: the step polynomial p_n(y) = sum_j c_j (1 - y)^j.
+std::vector<double> sign_series_coeffs(int n);
+// One update X <- filter(X p_n(Y)) of the sign iteration of order n + 1, given
+// Y = filter(X X); products in precision tier with symmetry mode sym, each passed to account.
+// Y is overwritten (with 1 - Y for orders above 2, with Y - 1 in order 2's correction form).
+void sign_update(dbcsr_matrix_* X, dbcsr_matrix_* Y, int order, bool correction, double eps, int tier, int sym,
+                 const std::function<void(const dbcsr_mult_stats&, int)>& account);
 dbcsr_status sign_iterate(dbcsr_matrix_* H, double mu, const dbcsr_sign_opts* opts, dbcsr_matrix_* P,
                           dbcsr_sign_report* rep);
 

@@ -627,6 +627,10 @@ dbcsr_status dbcsr_scale_shift(dbcsr_matrix m, double scale, double shift) {
     return guarded([&] { dbg::scale_shift(m, scale, shift); });
 }
 
+dbcsr_status dbcsr_add(double alpha, dbcsr_matrix A, double beta, dbcsr_matrix B) {
+    return guarded([&] { dbg::add(A, alpha, B, beta); });
+}
+
 dbcsr_status dbcsr_filter(dbcsr_matrix m, double eps) {
     return guarded([&] { dbg::filter_matrix(m, eps, nullptr); });
 }

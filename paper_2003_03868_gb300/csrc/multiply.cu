@@ -22,7 +22,8 @@
 //                    alpha/beta and writes the block norm.  k_smm_bf16 is the
 //                    tensor-core counterpart (plain or split BF16 operands).
 //     With a symmetric result only the blocks I <= J are computed; k_mirror_copy
-//     copies the others as transposes.
+//     copies the others as transposes and k_sym_diag takes the symmetric part of
+//     the diagonal blocks.
 //  6. filter         blocks with norm < eps dropped (diagonal kept), compaction.
 #include <cuda_bf16.h>
 
@@ -295,6 +296,61 @@ __device__ __forceinline__ int block_role(int sym, int32_t I, int32_t J, int64_t
     return (I < J || sym == 2) ? 0 : 1;
 }
 
+// One warp: the m x m block P becomes (P + P^T) / 2 in place; *sq and *d receive the
+// lane's share of its squared norm and squared distance to 1.
+__device__ __forceinline__ void sym_diag_block(double* P, int m, int lane, double* sq, double* d) {
+    for (int e = lane; e < m * m; e += 32) {
+        const int i = e / m, j = e - i * m;
+        if (i < j) {
+            const double v = 0.5 * (P[i * m + j] + P[j * m + i]);
+            P[i * m + j] = v;
+            P[j * m + i] = v;
+        }
+    }
+    __syncwarp();
+    double s = 0.0, t = 0.0;
+    for (int e = lane; e < m * m; e += 32) {
+        const int i = e / m, j = e - i * m;
+        const double v = P[e];
+        s = fma(v, v, s);
+        const double w = (i == j) ? v - 1.0 : v;
+        t = fma(w, w, t);
+    }
+    *sq = s;
+    *d = t;
+}
+
+// sym = 1 (mirror): the diagonal blocks, computed in full, become their symmetric parts, so
+// that the result is exactly symmetric.  A diagonal block of A B is symmetric only as far
+// as A and B commute (and, in split BF16, only to the order of its FP32 sums); with
+// mirrored off-diagonal blocks an antisymmetric part left there grows from product to
+// product instead of dying out.  One warp per block row.
+__global__ void k_sym_diag(int32_t nblk, const int64_t* __restrict__ f_rp, const int32_t* __restrict__ f_col,
+                           const int64_t* __restrict__ f_off, const int32_t* __restrict__ bs,
+                           double* __restrict__ c_data, double* __restrict__ c_norm, double* __restrict__ c_dev2) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t I = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); I < nblk; I += warps) {
+        int64_t lo = f_rp[I], hi = f_rp[I + 1];
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (f_col[mid] < I) lo = mid + 1; else hi = mid;
+        }
+        if (!(lo < f_rp[I + 1] && f_col[lo] == I)) continue;
+        double sq, d;
+        sym_diag_block(c_data + f_off[lo], bs[I], lane, &sq, &d);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            sq += __shfl_xor_sync(0xffffffffu, sq, o);
+            d += __shfl_xor_sync(0xffffffffu, d, o);
+        }
+        if (lane == 0) {
+            c_norm[lo] = sqrt(sq);
+            c_dev2[lo] = d;
+        }
+    }
+}
+
 // sym = 2: C_IJ and C_JI become (C_IJ + C_JI^T) / 2 and its transpose, with their
 // norms and distances to 1 (the pair is handled by the warp of its I < J block;
 // diagonal blocks by their own warp).
@@ -313,23 +369,7 @@ __global__ void k_sym_average(int64_t nform, const int64_t* __restrict__ mirror,
         double* Q = c_data + f_off[t];
         double sq = 0.0, d = 0.0;
         if (I == J) {
-            // symmetrise the diagonal block in place: pairs (i, j) and (j, i), i < j
-            for (int e = lane; e < m * m; e += 32) {
-                const int i = e / m, j = e - i * m;
-                if (i < j) {
-                    const double v = 0.5 * (P[i * m + j] + P[j * m + i]);
-                    P[i * m + j] = v;
-                    P[j * m + i] = v;
-                }
-            }
-            __syncwarp();
-            for (int e = lane; e < m * m; e += 32) {
-                const int i = e / m, j = e - i * m;
-                const double v = P[e];
-                sq = fma(v, v, sq);
-                const double w = (i == j) ? v - 1.0 : v;
-                d = fma(w, w, d);
-            }
+            sym_diag_block(P, m, lane, &sq, &d);
         } else {
             for (int e = lane; e < m * n; e += 32) {
                 const int i = e / n, j = e - i * n;
@@ -1503,6 +1543,10 @@ void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbc
             if (sym_result == 2) {
                 k_sym_average<<<grid_for(nform, 8), 256, 0, s>>>(nform, mirror.p, f_row.p, f_col.p, f_off.p, A->bs.p,
                                                                 c_data.p, c_norm.p, c_dev2.p);
+                DBG_LAUNCH_CK();
+            } else {
+                k_sym_diag<<<grid_for(nblk, 8), 256, 0, s>>>(nblk, f_rp.p, f_col.p, f_off.p, A->bs.p, c_data.p,
+                                                            c_norm.p, c_dev2.p);
                 DBG_LAUNCH_CK();
             }
         }

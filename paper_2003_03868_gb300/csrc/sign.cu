@@ -1,21 +1,38 @@
-// Density matrix by the second-order Newton-Schulz sign iteration
-// (section "Sign-Method": sign(A) = A (A^2)^(-1/2), P = (1 - sign(H - mu 1)) / 2
-// with S = 1, eps_filter truncation after every product).
+// Density matrix by the sign iteration (section "Sign-Method": sign(A) = A (A^2)^(-1/2),
+// P = (1 - sign(H - mu 1)) / 2 with S = 1, eps_filter truncation after every product).
 //
 //   X_0 = (H - mu 1) / alpha,  alpha = Gershgorin bound of H - mu 1
-//   repeat:  X2 = filter(X X);  r = ||X2 - 1||_F / N;  stop when r < tol
-//            X  = filter(1.5 X - 0.5 X X2)       ( = X (3 - X^2) / 2 )
+//   repeat:  Y = filter(X X);  r = ||Y - 1||_F / N;  stop when r < tol
+//            X = filter(X p_n(Y))
 //   P = (1 - X) / 2,  Tr(P),  E_band = Tr(P H)
+//
+// p_n(y) = sum_{j<=n} c_j (1 - y)^j, c_j = binom(2j, j) / 4^j, is the series of
+// (1 - z)^(-1/2) at z = 1 - y cut after j = n, so X p_n(X^2) -> X (X^2)^(-1/2) with
+// order n + 1 (the polynomial Pade iterations).  n = 1 is the second-order
+// Newton-Schulz step X (3 - X^2) / 2 (the refinement function f_1 of section "OT/IR"),
+// n = 2, 3 the functions f_2, f_3, and n = 4 the printed fifth-order step
+// X (35 X^8 - 180 X^6 + 378 X^4 - 420 X^2 + 315) / 128, which the paper evaluates with
+// four products per iteration.  Here every order n >= 2 sums p_n in powers of
+// Z = 1 - Y, over the pairs q_i = c_2i + c_2i+1 Z, with Z2 = Z^2 and a filter after
+// every product:
+//   Z = 1 - Y;  Z2 = filter(Z Z);
+//   R = top pair (plus c_n Z2 when n is even);  R <- filter(Z2 R + q_i) down to i = 1;
+//   U = q_0 + filter(Z2 R)  (for n = 2: U = q_0 + c_2 Z2);  X <- filter(X U),
+// that is 3, 4, 4, 5, 5 products per iteration for orders 3 to 7.  The c_j are positive
+// and at most 1 (no cancelling sums of large terms, as in powers of Y), and every
+// filtered product holds a Z2 factor or X: near convergence U - 1 ~ c_1 Z is a matrix of
+// residual-sized blocks, and filtering it on its own would drop corrections just above
+// eps for good (the iteration then stalls well above the Newton-Schulz floor).
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <functional>
 #include <memory>
+#include <vector>
 
 #include "common.cuh"
 
 namespace dbg {
-
-namespace {
 
 std::unique_ptr<dbcsr_matrix_> make_like(const dbcsr_matrix_* m, cudaStream_t s) {
     auto x = std::make_unique<dbcsr_matrix_>();
@@ -28,7 +45,76 @@ std::unique_ptr<dbcsr_matrix_> make_like(const dbcsr_matrix_* m, cudaStream_t s)
     return x;
 }
 
-}  // namespace
+std::vector<double> sign_series_coeffs(int n) {
+    std::vector<double> c(n + 1);
+    c[0] = 1.0;
+    // binom(2j, j) / 4^j = c_j-1 (2j - 1) / (2j); every c_j is a short dyadic fraction, exact
+    for (int j = 1; j <= n; ++j) c[j] = c[j - 1] * (2 * j - 1) / (2 * j);
+    return c;
+}
+
+void sign_update(dbcsr_matrix_* X, dbcsr_matrix_* Y, int order, bool correction, double eps, int tier, int sym,
+                 const std::function<void(const dbcsr_mult_stats&, int)>& account) {
+    dbcsr_mult_stats st{};
+    if (order == 2) {
+        if (correction && tier == DBCSR_FP64) {
+            // X <- X - 0.5 X (Y - 1): the small correction in split BF16, X itself in FP64
+            scale_shift(Y, 1.0, -1.0);
+            multiply(-0.5, X, Y, 1.0, X, eps, DBCSR_BF16X3, &st, false, sym);
+            account(st, DBCSR_BF16X3);
+        } else {
+            multiply(-0.5, X, Y, 1.5, X, eps, tier, &st, false, sym);    // X (3 - Y) / 2
+            account(st, tier);
+        }
+        return;
+    }
+    const int n = order - 1;
+    const std::vector<double> c = sign_series_coeffs(n);
+    cudaStream_t s = X->stream;
+    scale_shift(Y, -1.0, 1.0);                            // Z = 1 - X^2, in place
+    dbcsr_matrix_* Z = Y;
+    auto Z2 = make_like(X, s);
+    multiply(1.0, Z, Z, 0.0, Z2.get(), eps, tier, &st, false, sym);
+    account(st, tier);
+    // pair i of p_n: c_2i+1 Z + c_2i 1
+    auto pair = [&](dbcsr_matrix_* dst, int i) {
+        copy_matrix(dst, Z);
+        scale_shift(dst, c[2 * i + 1], c[2 * i]);
+    };
+    const int m = n / 2;
+    auto R = make_like(X, s);
+    int i;
+    if (n % 2 == 0) {
+        pair(R.get(), m - 1);
+        add(R.get(), 1.0, Z2.get(), c[n]);               // c_n Z2 + c_n-1 Z + c_n-2
+        i = m - 2;
+    } else {
+        pair(R.get(), m);                                // c_n Z + c_n-1
+        i = m - 1;
+    }
+    std::unique_ptr<dbcsr_matrix_> U;
+    if (n == 2) {
+        U = std::move(R);                                // q_0 + c_2 Z2
+    } else {
+        for (; i >= 1; --i) {
+            auto V = make_like(X, s);
+            pair(V.get(), i);
+            multiply(1.0, Z2.get(), R.get(), 1.0, V.get(), eps, tier, &st, false, sym);
+            account(st, tier);
+            R = std::move(V);
+        }
+        auto V = make_like(X, s);
+        multiply(1.0, Z2.get(), R.get(), 0.0, V.get(), eps, tier, &st, false, sym);
+        account(st, tier);
+        R.reset();
+        U = make_like(X, s);
+        pair(U.get(), 0);
+        add(U.get(), 1.0, V.get(), 1.0);                 // q_0 + filter(Z2 R)
+    }
+    Z2.reset();
+    multiply(1.0, X, U.get(), 0.0, X, eps, tier, &st, false, sym);
+    account(st, tier);
+}
 
 dbcsr_status sign_iterate(dbcsr_matrix_* H, double mu, const dbcsr_sign_opts* opts, dbcsr_matrix_* P,
                           dbcsr_sign_report* rep) {
@@ -47,6 +133,10 @@ dbcsr_status sign_iterate(dbcsr_matrix_* H, double mu, const dbcsr_sign_opts* op
     if (!(o.eps_filter >= 0) || !(o.tol > 0)) fail(DBCSR_EINVAL, "sign_iterate: need eps_filter >= 0 and tol > 0");
     if (o.prec != DBCSR_FP64 && o.prec != DBCSR_MIXED) fail(DBCSR_EINVAL, "sign_iterate: prec must be FP64 or MIXED");
     if (o.prec == DBCSR_MIXED && !(o.switch_tol > 0)) o.switch_tol = 1e-4;
+    if (o.order == 0) o.order = 2;
+    if (o.order < 2 || o.order > 7) fail(DBCSR_EINVAL, "sign_iterate: order must be 2 to 7");
+    if (o.order != 2 && (o.flags & DBCSR_SIGN_LOW_CORRECTION))
+        fail(DBCSR_EINVAL, "sign_iterate: the low-precision correction applies to order 2 only");
     // Every product of the iteration is symmetric in exact arithmetic.  FP64 and split-BF16
     // products compute the blocks I <= J and mirror the rest.  Plain BF16 products keep both
     // triangles as computed: a BF16 X2 commutes with X only to about 1e-3, so mirrored BF16
@@ -127,21 +217,13 @@ dbcsr_status sign_iterate(dbcsr_matrix_* H, double mu, const dbcsr_sign_opts* op
                 break;
             }
         }
-        if (correction && tier == DBCSR_FP64) {
-            // X <- X - 0.5 X (X2 - 1): the small correction in split BF16, X itself in FP64
-            scale_shift(X2.get(), 1.0, -1.0);
-            multiply(-0.5, X.get(), X2.get(), 1.0, X.get(), o.eps_filter, DBCSR_BF16X3, &st, false, sym);
-            account(st, DBCSR_BF16X3);
-        } else {
-            multiply(-0.5, X.get(), X2.get(), 1.5, X.get(), o.eps_filter, tier, &st, false, sym);
-            account(st, tier);
-        }
+        sign_update(X.get(), X2.get(), o.order, correction, o.eps_filter, tier, sym, account);
         if (it - 1 < DBCSR_MAX_HISTORY) r.nnzb_history[it - 1] = X->nnzb;
     }
-    // X of a mixed run is symmetric only to the low tier's accuracy (both triangles formed with
-    // plain BF16; diagonal blocks summed in FP32 with split BF16), so it is replaced by its
-    // symmetric part before P is formed
-    if (o.prec == DBCSR_MIXED && !full) symmetrize(X.get());
+    // X of a mixed run with a plain BF16 tier (both triangles formed) is symmetric only to that
+    // tier's accuracy, so it is replaced by its symmetric part before P is formed; mirrored
+    // products keep X exactly symmetric
+    if (full_mixed && !full) symmetrize(X.get());
     copy_matrix(P, X.get());
     scale_shift(P, -0.5, 0.5);
     r.trace_p = trace(P);
