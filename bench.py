@@ -46,6 +46,14 @@ def bf16_peak():
         return FALLBACK_BF16_SUSTAINED, "fallback bf16 sustained"
 
 
+def hbm_peak():
+    """Measured HBM copy bandwidth (GB/s)."""
+    try:
+        return float(json.load(open(PEAKS_FILE))["hbm_gbs"]), "measured copy"
+    except Exception:
+        return 6800.0, "fallback copy"
+
+
 def fp64_peak():
     """FP64 roofline peak: the measured bf16 peak times the nominal FP64/bf16 ratio."""
     try:
@@ -283,6 +291,37 @@ def run_orders(args, gb, synth, torch, barrier, w, h):
     f64 = [leg(o, gb.DBCSR_FP64) for o in orders]
     mixed = [] if args.no_mixed else [leg(o, gb.DBCSR_MIXED) for o in orders]
     launches = gb.lib().dbcsr_launch_count() - l0
+
+    # the block-sparse add of the even orders, A <- A + c B, on matrices of the iteration's size:
+    # A = H (the pattern of X_0) and B = filter(H H) (the pattern of X^2), so that the union
+    # is B's pattern grown by H's.  Bound by HBM: A and B read once, the sum written once.
+    B = gb.Matrix(H.blk_size, stream.cuda_stream)
+    gb.multiply(1.0, H, H, 0.0, B, w.eps_filter)
+    def nel(M):
+        return int(M.info()[2])
+    ms_add, bytes_add = 0.0, 0.0
+    for k in range(args.warmup + args.steps):
+        A = H.copy()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        a0.record(stream)
+        gb.add(1.0, A, 0.375, B)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        if k >= args.warmup:
+            ms_add += a0.elapsed_time(a1)
+            bytes_add += 8.0 * (nel(H) + nel(B) + nel(A))
+        A.close()
+    hp, hp_src = hbm_peak()
+    gbs = bytes_add / (ms_add * 1e-3) / 1e9
+    add = {"kernel": "dbcsr_add (k_union_rows x2, k_add_values)", "ms_per_call": ms_add / args.steps,
+           "blocks": {"A": H.nnzb, "B": B.nnzb},
+           "algorithmic_bytes_per_call": bytes_add / args.steps,
+           "roofline": {"bound": "hbm", "achieved": gbs, "peak": hp, "unit": "GB/s", "frac": gbs / hp,
+                        "peak_source": hp_src,
+                        "note": "8 bytes per element of A, B and the sum; call time including its two "
+                                "host readbacks of the union size"}}
+    B.close()
     clk = clocks.stop()
     ref = next((x for x in f64 if x["order"] == 2), f64[0])
     for x in f64 + mixed:
@@ -298,7 +337,8 @@ def run_orders(args, gb, synth, torch, barrier, w, h):
                       "orders": orders, "mixed_switch": w.switch or 1e-4,
                       "l2": "inputs larger than L2 (H alone is %.0f MB; 129 MB L2)" % (h.H.data.nbytes / 1e6),
                       "parallelism": f"replicas x{world}"},
-           "best_order": best["order"], "fp64": f64, "mixed": mixed, "gpu_launches": launches, "clocks": clk}
+           "best_order": best["order"], "fp64": f64, "mixed": mixed, "add": add, "gpu_launches": launches,
+           "clocks": clk}
     if rank == 0:
         print(json.dumps(out))
     if dist:
