@@ -53,6 +53,17 @@ products per iteration):
     product here holds either a Z2 factor or X, as Newton-Schulz's X (3 - Y) / 2 does;
 * the stall test above is kept for every order: per eigenvalue the step maps
   e = 1 - x^2 to e' with e'/e increasing in e, the premise of that test.
+
+Non-orthogonal basis (section "Sign-Method": P = (1 - sign(S^-1 K - mu 1)) S^-1 / 2,
+with inverse square roots from the sign of the block matrix [[0, A], [1, 0]], which is
+[[0, A^(1/2)], [A^(-1/2), 0]]):
+
+* inverse_sqrt runs the sign iteration of the chosen order on that block matrix, in the
+  coupled form its block structure gives (Y, Z below), on A = S / g with g the largest
+  absolute row sum of S, from Y_0 = A, Z_0 = 1, testing ||Z Y - 1||_F / N;
+* density_matrix_nonorth takes the reading P = S^(-1/2) P' S^(-1/2), where P' is the
+  density matrix of K' = S^(-1/2) K S^(-1/2) (the sign of S^-1 K - mu 1 is the sign of
+  K' - mu 1 under the similarity by S^(1/2)); every product is filtered.
 """
 from __future__ import annotations
 
@@ -106,21 +117,16 @@ def pade_coefficients(order: int) -> list:
     return a
 
 
-def _higher_order_update(X: bsr.Mat, Y: bsr.Mat, order: int, eps: float):
-    """X p_n(Y) for Y = filter(X X), by the four-product scheme of the module header.
-    Returns the new X and the (flops, block products, matrix products) it took."""
+def _step_polynomial(Y: bsr.Mat, order: int, eps: float, mult) -> bsr.Mat:
+    """U = p_n(Y) for the step of the given order, by the scheme of the module header
+    (Y = filter(X X), or Z Y in the square-root iteration); mult(alpha, A, B, beta, Cin)
+    forms one filtered product.  Order 2: U = (3 - Y) / 2, no product."""
     n = order - 1
     c = [float(v) for v in series_coefficients(order)]
-    work = [0, 0, 0]
+    if n == 1:
+        return bsr.add_identity(Y, -c[1], c[0] + c[1])             # 1 + (1 - Y)/2
 
-    def mult(alpha, A, B, beta=0.0, Cin=None):
-        C, info = bsr.multiply(alpha, A, B, beta, Cin, eps=eps, info=True)
-        work[0] += info.flops
-        work[1] += info.n_products
-        work[2] += 1
-        return C
-
-    Z = bsr.add_identity(Y, -1.0, 1.0)                           # 1 - X^2
+    Z = bsr.add_identity(Y, -1.0, 1.0)                           # 1 - Y
 
     def pair(i):                                                 # c_2i+1 Z + c_2i 1
         return bsr.add_identity(Z, c[2 * i + 1], c[2 * i])
@@ -134,13 +140,34 @@ def _higher_order_update(X: bsr.Mat, Y: bsr.Mat, order: int, eps: float):
         R = pair(m)
         i = m - 1
     if n == 2:
-        U = R                                                    # q_0 + c_2 Z2
-    else:
-        while i >= 1:
-            R = mult(1.0, Z2, R, 1.0, pair(i))
-            i -= 1
-        U = bsr.add(1.0, pair(0), 1.0, mult(1.0, Z2, R))
-    return mult(1.0, X, U), work
+        return R                                                 # q_0 + c_2 Z2
+    while i >= 1:
+        R = mult(1.0, Z2, R, 1.0, pair(i))
+        i -= 1
+    return bsr.add(1.0, pair(0), 1.0, mult(1.0, Z2, R))
+
+
+class _Work:
+    """Counts the filtered products of an iteration."""
+
+    def __init__(self, eps: float):
+        self.eps, self.flops, self.n_products, self.multiplies = eps, 0, 0, 0
+
+    def __call__(self, alpha, A, B, beta=0.0, Cin=None, info=False):
+        C, inf = bsr.multiply(alpha, A, B, beta, Cin, eps=self.eps, info=True)
+        self.flops += inf.flops
+        self.n_products += inf.n_products
+        self.multiplies += 1
+        return (C, inf) if info else C
+
+
+def _higher_order_update(X: bsr.Mat, Y: bsr.Mat, order: int, eps: float):
+    """X p_n(Y) for Y = filter(X X), by the four-product scheme of the module header.
+    Returns the new X and the (flops, block products, matrix products) it took."""
+    w = _Work(eps)
+    U = _step_polynomial(Y, order, eps, w)
+    Xn = w(1.0, X, U)
+    return Xn, (w.flops, w.n_products, w.multiplies)
 
 
 def sign_iterate(H: bsr.Mat, mu: float, eps: float, tol: float, max_iter: int = 100,
@@ -192,3 +219,94 @@ def sign_iterate(H: bsr.Mat, mu: float, eps: float, tol: float, max_iter: int = 
 def band_energy(P: bsr.Mat, H: bsr.Mat) -> float:
     """E_band = Tr(P H)."""
     return bsr.trace_product(P, H)
+
+
+# ------------------------------------------------------------------ non-orthogonal basis
+@dataclasses.dataclass
+class SqrtResult:
+    Sinvsqrt: bsr.Mat          # S^(-1/2)
+    Ssqrt: bsr.Mat             # S^(1/2)
+    iterations: int
+    residuals: list            # ||Z Y - 1||_F / N per step
+    converged: bool
+    stalled: bool
+    scale: float               # g: the iteration runs on S / g
+    flops: int
+    n_products: int
+    multiplies: int
+
+
+def identity_like(M: bsr.Mat) -> bsr.Mat:
+    """The identity with M's block sizes (diagonal blocks only)."""
+    nb = M.nblk
+    data = np.concatenate([np.eye(int(b)).ravel() for b in M.bs]) if nb else np.zeros(0)
+    return bsr.Mat(M.bs, np.arange(nb + 1, dtype=np.int64), np.arange(nb, dtype=np.int32), data)
+
+
+def inverse_sqrt(S: bsr.Mat, eps: float, tol: float, max_iter: int = 100, stall_ratio: float = 0.5,
+                 order: int = 2) -> SqrtResult:
+    """S^(-1/2) and S^(1/2) of a symmetric positive definite S by the sign iteration on the
+    block matrix [[0, A], [1, 0]] (section "Sign-Method": its sign is [[0, A^(1/2)],
+    [A^(-1/2), 0]]), A = S / g with g = max_i sum_j |S_ij| so that the spectrum of A lies in
+    (0, 1].  The iterate keeps the form [[0, Y], [Z, 0]]; its square is diag(Y Z, Z Y), and
+    with Y, Z functions of A (so Y Z = Z Y) the step X <- X p(X^2) reads
+        W = filter(Z Y);  r = ||W - 1||_F / N;  stop when r < tol;
+        U = p(W);  Y <- filter(Y U);  Z <- filter(U Z)
+    from Y_0 = A, Z_0 = 1 (U as in the sign iteration of the same order).  Then
+    S^(1/2) = sqrt(g) Y and S^(-1/2) = Z / sqrt(g).  The stall test is the sign iteration's."""
+    if not 2 <= order <= 7:
+        raise ValueError("order must be 2 to 7")
+    n = S.n
+    g = gershgorin(S, 0.0)
+    Y = bsr.add_identity(S, 1.0 / g, 0.0)
+    Zm = identity_like(S)
+    w = _Work(eps)
+    res = []
+    converged = stalled = False
+    it = 0
+    while it < max_iter:
+        W, inf = w(1.0, Zm, Y, info=True)
+        it += 1
+        r = float(np.sqrt(inf.dev2)) / n
+        res.append(r)
+        if r < tol:
+            converged = True
+            break
+        if len(res) >= 3 and res[-2] < stall_ratio * res[-3] and r > stall_ratio * res[-2]:
+            stalled = True
+            break
+        U = _step_polynomial(W, order, eps, w)
+        Y = w(1.0, Y, U)
+        Zm = w(1.0, U, Zm)
+    rg = float(np.sqrt(g))
+    return SqrtResult(Sinvsqrt=bsr.add_identity(Zm, 1.0 / rg, 0.0), Ssqrt=bsr.add_identity(Y, rg, 0.0),
+                      iterations=it, residuals=res, converged=converged, stalled=stalled, scale=g,
+                      flops=w.flops, n_products=w.n_products, multiplies=w.multiplies)
+
+
+@dataclasses.dataclass
+class NonorthResult:
+    P: bsr.Mat                 # density matrix in the non-orthogonal basis
+    sign: SignResult           # the sign iteration on S^(-1/2) K S^(-1/2)
+    sqrt: SqrtResult
+    trace_ps: float            # Tr(P S), the electron count (states)
+    e_band: float              # Tr(P K)
+    flops: int                 # every block product: square root, transforms, sign
+
+
+def density_matrix_nonorth(K: bsr.Mat, S: bsr.Mat, mu: float, eps: float, tol: float, max_iter: int = 100,
+                           order: int = 2, sqrt_tol: float | None = None) -> NonorthResult:
+    """P = (1 - sign(S^-1 K - mu 1)) S^-1 / 2 (section "Sign-Method").
+
+    Reading: sign(S^-1 K - mu 1) = S^(-1/2) sign(S^(-1/2) K S^(-1/2) - mu 1) S^(1/2) (a
+    similarity), so P = S^(-1/2) P' S^(-1/2) with P' the orthogonal-basis density matrix of
+    K' = S^(-1/2) K S^(-1/2); S^(-1/2) comes from inverse_sqrt.  Every product is filtered.
+    Tr(P S) = Tr(P') and Tr(P K) = Tr(P' K')."""
+    sq = inverse_sqrt(S, eps, sqrt_tol if sqrt_tol is not None else tol, max_iter, order=order)
+    w = _Work(eps)
+    Zs = sq.Sinvsqrt
+    Kp = w(1.0, w(1.0, Zs, K), Zs)
+    r = sign_iterate(Kp, mu, eps, tol, max_iter, order=order)
+    P = w(1.0, w(1.0, Zs, r.P), Zs)
+    return NonorthResult(P=P, sign=r, sqrt=sq, trace_ps=bsr.trace_product(P, S), e_band=bsr.trace_product(P, K),
+                         flops=sq.flops + w.flops + r.flops)

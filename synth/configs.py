@@ -11,7 +11,7 @@ import math
 import numpy as np
 
 from . import splitmix
-from .waterbox import Hamiltonian, gapped_hamiltonian, decay_matrix, place_waters, BlockMatrix
+from .waterbox import Hamiltonian, gapped_hamiltonian, decay_matrix, overlap_matrix, place_waters, BlockMatrix
 
 BASE_SEED = 200303868
 
@@ -71,6 +71,12 @@ def small(n_mol: int, basis=(13, 5), seed: int = BASE_SEED + 11, box: float | No
 def build_hamiltonian(w: Workload, box: float | None = None) -> Hamiltonian:
     wb = place_waters(w.n_mol, w.seed, box=box)
     return gapped_hamiltonian(wb, w.basis, w.seed)
+
+
+def build_overlap(w: Workload, box: float | None = None) -> BlockMatrix:
+    """The overlap matrix S of the workload's water box (same pattern as its Hamiltonian)."""
+    wb = place_waters(w.n_mol, w.seed, box=box)
+    return overlap_matrix(wb, w.basis, w.seed)
 
 
 def build_decay(w: Workload, box: float | None = None) -> BlockMatrix:

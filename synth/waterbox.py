@@ -16,6 +16,15 @@ sizes and sparsity structure:
   r_IJ < 8 A; its entries are u * exp(-0.3 r_IJ^2) with u uniform in [-1, 1);
   block (J, I) is the transpose of block (I, J); a diagonal block is
   (U + U^T)/2 + 2 I;
+* an *overlap matrix* S for a non-orthogonal basis: 1 + sigma * |D|, where D is a
+  decay matrix on the same pattern drawn from an independent stream, without the
+  diagonal shift (entries taken in absolute value, as overlaps of nearby s-like
+  functions are positive), and sigma = 0.9 / (largest row sum of |D|).  By the
+  Gershgorin bound the eigenvalues of S lie in [0.1, 1.9], so S is symmetric positive
+  definite (on water boxes they fall in about [0.9, 1.6]).  By Sylvester's law of
+  inertia and Ostrowski's theorem the generalized problem H c = S c e keeps the gapped
+  Hamiltonian's occupied count at mu = 0, with eigenvalues in [-17.5, -0.13] or
+  [0.13, 17.5];
 * a *gapped Hamiltonian*: for every molecule the intra-molecular d x d part of
   the decay matrix is diagonalised and its eigenvalues replaced by
   -1 + 0.25 t (the 4 lowest) and +1 + 0.25 t (the other d - 4), t evenly
@@ -50,6 +59,7 @@ N_OCC_PER_MOL = 4        # occupied states per water (8 valence electrons / 2)
 
 # sub-stream tags
 _TAG_POS, _TAG_ORI, _TAG_VAL = 1, 2, 3
+_TAG_OVERLAP = 4
 
 
 @dataclasses.dataclass
@@ -328,6 +338,41 @@ def decay_matrix(wb: WaterBox, basis: tuple[int, int], seed: int,
         d = 0.5 * (u + np.transpose(u, (0, 2, 1))) + shift * np.eye(bm_)[None, :, :]
         data[idx] = d.reshape(-1, area)
     return m, (ui, uj, r, pos_up, pos_lo)
+
+
+def _abs_row_sums(A: BlockMatrix, select: np.ndarray) -> np.ndarray:
+    """Sum over the selected blocks of |entries| along every matrix row."""
+    bs = A.blk_size
+    rows = A.rows()
+    boff = A.blk_off()
+    roff = np.zeros(bs.shape[0] + 1, dtype=np.int64)
+    np.cumsum(bs, out=roff[1:])
+    rowsum = np.zeros(A.n)
+    for bm in np.unique(bs):
+        for bn in np.unique(bs):
+            sel = np.nonzero(select & (bs[rows] == bm) & (bs[A.col] == bn))[0]
+            area = int(bm) * int(bn)
+            ar = np.arange(area, dtype=np.int64)
+            for ch in _chunks(sel, area):
+                v = np.abs(A.data[boff[ch][:, None] + ar[None, :]]).reshape(-1, bm, bn).sum(axis=2)
+                tgt = roff[rows[ch]][:, None] + np.arange(bm)[None, :]
+                np.add.at(rowsum, tgt.ravel(), v.ravel())
+    return rowsum
+
+
+def overlap_matrix(wb: WaterBox, basis: tuple[int, int], seed: int, spread: float = 0.9) -> BlockMatrix:
+    """Synthetic overlap S = 1 + sigma |D| on the decay pattern (see module docstring):
+    eigenvalues in [1 - spread, 1 + spread]."""
+    D, _ = decay_matrix(wb, basis, splitmix.substream(seed, _TAG_OVERLAP), shift=0.0)
+    rowsum = _abs_row_sums(D, np.ones(D.col.shape[0], dtype=bool))
+    sigma = spread / float(rowsum.max())
+    data = np.abs(D.data) * sigma
+    rows = D.rows()
+    boff = D.blk_off()
+    for b in np.nonzero(rows == D.col)[0]:
+        m = int(D.blk_size[rows[b]])
+        data[boff[b]:boff[b] + m * m:m + 1] += 1.0
+    return BlockMatrix(D.blk_size, D.row_ptr, D.col, data)
 
 
 @dataclasses.dataclass

@@ -80,3 +80,13 @@ def test_workload_sizes():
     assert len(sys_) == 64
     assert all(100 <= s.n_mol <= 2000 for s in sys_)
     assert {s.basis[0] for s in sys_} == {13, 23} and {s.basis[1] for s in sys_} == {5, 7}
+
+
+def test_overlap_is_deterministic_and_on_the_hamiltonian_pattern():
+    w = synth.small(12, seed=31337)
+    a, b = synth.build_overlap(w), synth.build_overlap(w)
+    h = synth.build_hamiltonian(w)
+    assert np.array_equal(a.data, b.data)
+    assert np.array_equal(a.row_ptr, h.H.row_ptr) and np.array_equal(a.col, h.H.col)
+    assert np.all(a.data >= 0)                             # 1 + sigma |D|
+    assert not np.array_equal(synth.build_overlap(synth.small(12, seed=31338)).data[:50], a.data[:50])
