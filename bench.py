@@ -346,6 +346,81 @@ def run_orders(args, gb, synth, torch, barrier, w, h):
     return 0
 
 
+def run_nonorth(args, gb, synth, torch, barrier, w, h):
+    """The density matrix in a non-orthogonal basis, P = (1 - sign(S^-1 K - mu 1)) S^-1 / 2,
+    on the workload's water box with its synthetic overlap S: the square root S^-1/2, the
+    congruences and the sign iteration, FP64 and mixed, for each order of --orders."""
+    from paper_2003_03868_gb300 import ranks
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+    s_bm = synth.build_overlap(w)
+    stream = torch.cuda.current_stream()
+    K = gb.Matrix.of(h.H, stream=stream.cuda_stream)
+    S = gb.Matrix.of(s_bm, stream=stream.cuda_stream)
+    orders = [int(o) for o in args.orders.split(",")]
+    clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
+    l0 = gb.lib().dbcsr_launch_count()
+
+    def leg(order, prec):
+        def one():
+            return gb.sign_iterate_nonorth(K, S, h.mu, w.eps_filter, w.tol, prec=prec,
+                                           switch_tol=w.switch or 1e-4, order=order, verbose=args.verbose)
+        for _ in range(args.warmup):
+            one()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        flops = ms_mult = ms_sqrt = 0.0
+        for _ in range(args.steps):
+            r = one()
+            flops += r.report.flops + r.report_sqrt.flops
+            ms_mult += r.report.ms_multiply + r.report_sqrt.ms_multiply
+            ms_sqrt += r.report_sqrt.ms_total
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ms, flops_all = ranks.job_timing(e0.elapsed_time(e1) / args.steps, flops / args.steps, dist, "cuda")
+        rr, rs = r.report, r.report_sqrt
+        return {"order": order, "time_to_p_ms": ms, "sqrt_ms": ms_sqrt / args.steps,
+                "value": flops_all / (ms * 1e-3) / 1e12,
+                "kernel_tflops": flops / (ms_mult * 1e-3) / 1e12 if ms_mult > 0 else None,
+                "flops_per_step": flops / args.steps,
+                "sqrt": {"iterations": rs.iterations, "converged": bool(rs.converged), "stalled": bool(rs.stalled),
+                         "residual": rs.residual, "scale": rs.alpha, "fp64_from_step": rs.fp64_from},
+                "sign": {"iterations": rr.iterations, "converged": bool(rr.converged), "stalled": bool(rr.stalled),
+                         "residual": rr.residual, "fp64_from_step": rr.fp64_from},
+                "trace_ps": rr.trace_p, "trace_ps_error": rr.trace_p - h.n_occ, "e_band": rr.e_band}
+
+    f64 = [leg(o, gb.DBCSR_FP64) for o in orders]
+    mixed = [] if args.no_mixed else [leg(o, gb.DBCSR_MIXED) for o in orders]
+    launches = gb.lib().dbcsr_launch_count() - l0
+    clk = clocks.stop()
+    ref = f64[0]
+    for x in f64 + mixed:
+        x["de_band_per_atom_vs_fp64_first"] = abs(x["e_band"] - ref["e_band"]) / h.n_atoms
+    best = min(f64 + mixed, key=lambda x: x["time_to_p_ms"])
+    out = {"metric": "time-to-P, non-orthogonal basis (S^-1/2, congruences, sign iteration)",
+           "value": f64[0]["time_to_p_ms"], "unit": "ms", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": f64[0]["time_to_p_ms"], "higher_is_better": False,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": w.name + "-nonorth", "n_mol": w.n_mol, "N": w.n,
+                      "blocks": {"O": w.basis[0], "H": w.basis[1]}, "eps_filter": w.eps_filter, "tol": w.tol,
+                      "orders": orders, "overlap": "1 + 0.9 |D| / max row sum (synthetic; eigenvalues in [0.1, 1.9])",
+                      "l2": "inputs larger than L2 (K alone is %.0f MB; 129 MB L2)" % (h.H.data.nbytes / 1e6),
+                      "parallelism": f"replicas x{world}"},
+           "fp64": f64, "mixed": mixed, "fastest": {"order": best["order"], "time_to_p_ms": best["time_to_p_ms"]},
+           "gpu_launches": launches, "clocks": clk}
+    if rank == 0:
+        print(json.dumps(out))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
 def run_mult32(args, gb, synth, torch, barrier):
     """The single product C = A A of the 32-water decay matrix (N = 736, eps 1e-6): one-off
     products (stack builder, block products, filter, with their host round trips) against
@@ -526,13 +601,15 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=2, help="Newton-Schulz steps in the oracle CPU baseline")
     ap.add_argument("--workload", default="sign-1024h2o",
                     choices=["sign-1024h2o", "sign-512h2o", "sign-512h2o-23-7", "sign-4096h2o", "batch-64",
-                             "sign-20736h2o-mlp", "mult-32h2o", "sign-1024h2o-orders", "sign-4096h2o-orders"],
+                             "sign-20736h2o-mlp", "mult-32h2o", "sign-1024h2o-orders", "sign-4096h2o-orders",
+                             "sign-1024h2o-nonorth", "sign-4096h2o-nonorth"],
                     help="sign-512h2o, sign-512h2o-23-7: smaller cases for profiler captures; sign-4096h2o: "
                          "4,096 waters with O/H blocks 23/7 (FP64 and mixed); batch-64: 64 uneven systems "
                          "batched vs one by one; sign-20736h2o-mlp: the mixed iteration on 20,736 waters with "
                          "default, MLP-predicted and exhaustively tuned launch configurations; mult-32h2o: the "
                          "32-water product, one-off vs planned (CUDA graph); sign-1024h2o-orders, "
-                         "sign-4096h2o-orders: the sign iteration of orders 2 to 7 (--orders), FP64 and mixed")
+                         "sign-4096h2o-orders: the sign iteration of orders 2 to 7 (--orders), FP64 and mixed; "
+                         "sign-1024h2o-nonorth, sign-4096h2o-nonorth: the density matrix with an overlap matrix S")
     ap.add_argument("--orders", default="2,3,4,5,6,7", help="sign-*-orders: the orders to time")
     ap.add_argument("--train-triples", type=int, default=48, help="sign-20736h2o-mlp: autotuned training triples")
     ap.add_argument("--tune-stack", type=int, default=500000, help="products of the autotuner's synthetic stacks")
@@ -582,12 +659,15 @@ def main():
                                                                                          lambda: torch.cuda.synchronize())
     w = {"sign-1024h2o": synth.SIGN_1024, "sign-4096h2o": synth.SIGN_4096,
          "sign-1024h2o-orders": synth.SIGN_1024, "sign-4096h2o-orders": synth.SIGN_4096,
+         "sign-1024h2o-nonorth": synth.SIGN_1024, "sign-4096h2o-nonorth": synth.SIGN_4096,
          "sign-512h2o": synth.Workload("sign-512h2o-dzvp-fp64", 512, (13, 5), synth.configs.BASE_SEED + 12, 1e-7, 1e-9),
          "sign-512h2o-23-7": synth.Workload("sign-512h2o-23-7", 512, (23, 7), synth.configs.BASE_SEED + 13, 1e-6, 1e-8,
                                             1e-4)}[args.workload]
     h = synth.build_hamiltonian(w)
     if args.workload.endswith("-orders"):
         return run_orders(args, gb, synth, torch, barrier, w, h)
+    if args.workload.endswith("-nonorth"):
+        return run_nonorth(args, gb, synth, torch, barrier, w, h)
     stream = torch.cuda.current_stream()
     H = gb.Matrix.of(h.H, stream=stream.cuda_stream)
 

@@ -333,6 +333,46 @@ dbcsr_status dbcsr_gershgorin(dbcsr_matrix A, double mu, double* out);
 dbcsr_status dbcsr_sign_iterate(dbcsr_matrix H, double mu, const dbcsr_sign_opts* opts, dbcsr_matrix P_out,
                                 dbcsr_sign_report* rep);
 
+/*
+ * S^(-1/2) and S^(1/2) of a symmetric positive definite S (section "Sign-Method": the
+ * sign of the block matrix [[0, A], [1, 0]] is [[0, A^(1/2)], [A^(-1/2), 0]]).  The sign
+ * iteration of order opts->order runs on that block matrix in its coupled form, on
+ * A = S / g with g = dbcsr_gershgorin(S, 0):
+ *   Y_0 = A, Z_0 = 1;  repeat: W = filter(Z Y); r = ||W - 1||_F / N; stop if r < tol;
+ *                               U = p(W); Y <- filter(Y U); Z <- filter(U Z);
+ *   S_invsqrt = Z / sqrt(g), S_sqrt = sqrt(g) Y.
+ * With the precision ladder (prec DBCSR_MIXED), Y = A Z is restored in FP64 at the
+ * switch (the iteration does not undo the low tier's perturbations of A by itself).
+ * p is the step polynomial of dbcsr_sign_iterate (order 2: U = (3 - W) / 2).  opts as
+ * for dbcsr_sign_iterate (eps_filter, tol, max_iter, prec FP64 or MIXED with switch_tol,
+ * stall_ratio, order, DBCSR_SIGN_FULL_PRODUCTS / DBCSR_SIGN_PLAIN_BF16); the
+ * low-precision correction is refused.  S_sqrt may be NULL.  The outputs are replaced
+ * and must differ from S and from each other.  rep (may be NULL): iterations,
+ * residuals, alpha = g, nnzb_x = blocks of Z, work and times; trace_p and e_band are 0.
+ * Returns DBCSR_ENOTCONV (outputs and rep still filled) when max_iter or the stall test
+ * ended the iteration.  Errors: EINVAL, ESTATE, ENOMEM, ENAN, ECUDA.
+ */
+dbcsr_status dbcsr_inverse_sqrt(dbcsr_matrix S, const dbcsr_sign_opts* opts, dbcsr_matrix S_invsqrt,
+                                dbcsr_matrix S_sqrt, dbcsr_sign_report* rep);
+
+/*
+ * Density matrix in a non-orthogonal basis (section "Sign-Method"):
+ *   P = (1 - sign(S^-1 K - mu 1)) S^-1 / 2,
+ * evaluated through the similarity sign(S^-1 K - mu 1) = S^(-1/2) sign(K' - mu 1) S^(1/2)
+ * with K' = S^(-1/2) K S^(-1/2):
+ *   S^(-1/2) by dbcsr_inverse_sqrt (same opts), K' = filter(filter(S^(-1/2) K) S^(-1/2)),
+ *   P' = dbcsr_sign_iterate(K', mu, opts), P = filter(filter(S^(-1/2) P') S^(-1/2)).
+ * The four congruence products run in FP64.  K and S symmetric with the same block sizes,
+ * every diagonal block present; P_out is replaced and must differ from K and S.
+ * rep (may be NULL): the sign iteration's report, with trace_p = Tr(P S) (the occupied
+ * count), e_band = Tr(P K), and the congruences' work and the square root's time included
+ * in flops / ms_multiply / ms_total.  rep_sqrt (may be NULL): the square root's report.
+ * Returns DBCSR_ENOTCONV (P_out and the reports still filled) when either iteration
+ * ended before its tolerance.  Errors: as dbcsr_sign_iterate.
+ */
+dbcsr_status dbcsr_sign_iterate_nonorth(dbcsr_matrix K, dbcsr_matrix S, double mu, const dbcsr_sign_opts* opts,
+                                        dbcsr_matrix P_out, dbcsr_sign_report* rep, dbcsr_sign_report* rep_sqrt);
+
 /* Launch configuration of the block-product kernel of one (m, n, k) stack.  No
  * field changes the arithmetic: every C element is summed in the same order. */
 typedef struct {

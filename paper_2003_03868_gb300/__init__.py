@@ -279,6 +279,67 @@ def sign_iterate(H: Matrix, mu: float, eps_filter: float, tol: float, max_iter: 
     return SignResult(P=P, report=rep, status=st)
 
 
+@dataclasses.dataclass
+class SqrtResult:
+    Sinvsqrt: Matrix
+    Ssqrt: Matrix | None
+    report: SignReport
+    status: int
+
+    @property
+    def converged(self) -> bool:
+        return bool(self.report.converged)
+
+    @property
+    def residuals(self):
+        return [self.report.residual_history[i] for i in range(min(self.report.iterations, _ffi.MAX_HISTORY))]
+
+
+def inverse_sqrt(S: Matrix, eps_filter: float, tol: float, max_iter: int = 100, prec: int = DBCSR_FP64,
+                 switch_tol: float = 1e-4, stall_ratio: float = 0.5, order: int = 2, full_products: bool = False,
+                 low: int = DBCSR_BF16X3, want_sqrt: bool = True, verbose: bool = False,
+                 raise_on_notconv: bool = False) -> SqrtResult:
+    """S^(-1/2) (and S^(1/2)) by the sign iteration on [[0, S], [1, 0]] (dbcsr_inverse_sqrt)."""
+    Zi = Matrix(S.blk_size, S.stream)
+    Ys = Matrix(S.blk_size, S.stream) if want_sqrt else None
+    o = SignOpts(float(eps_filter), float(tol), int(max_iter), int(prec), float(switch_tol), float(stall_ratio),
+                 1 if verbose else 0, _sign_flags(full_products, low, False), int(order), 0)
+    rep = SignReport()
+    st = lib().dbcsr_inverse_sqrt(S.handle, C.byref(o), Zi.handle, Ys.handle if Ys else None, C.byref(rep))
+    if st != _ffi.DBCSR_OK and (st != _ffi.DBCSR_ENOTCONV or raise_on_notconv):
+        _check(st, "inverse_sqrt")
+    return SqrtResult(Sinvsqrt=Zi, Ssqrt=Ys, report=rep, status=st)
+
+
+@dataclasses.dataclass
+class NonorthResult:
+    P: Matrix
+    report: SignReport          # the sign iteration on S^-1/2 K S^-1/2; trace_p = Tr(P S), e_band = Tr(P K)
+    report_sqrt: SignReport     # the square root of S
+    status: int
+
+    @property
+    def converged(self) -> bool:
+        return bool(self.report.converged) and bool(self.report_sqrt.converged)
+
+
+def sign_iterate_nonorth(K: Matrix, S: Matrix, mu: float, eps_filter: float, tol: float, max_iter: int = 100,
+                         prec: int = DBCSR_FP64, switch_tol: float = 1e-4, stall_ratio: float = 0.5, order: int = 2,
+                         full_products: bool = False, low: int = DBCSR_BF16X3, low_correction: bool = False,
+                         P: Matrix | None = None, verbose: bool = False,
+                         raise_on_notconv: bool = False) -> NonorthResult:
+    """P = (1 - sign(S^-1 K - mu 1)) S^-1 / 2 (dbcsr_sign_iterate_nonorth)."""
+    P = Matrix(K.blk_size, K.stream) if P is None else P
+    o = SignOpts(float(eps_filter), float(tol), int(max_iter), int(prec), float(switch_tol), float(stall_ratio),
+                 1 if verbose else 0, _sign_flags(full_products, low, low_correction), int(order), 0)
+    rep, reps = SignReport(), SignReport()
+    st = lib().dbcsr_sign_iterate_nonorth(K.handle, S.handle, float(mu), C.byref(o), P.handle, C.byref(rep),
+                                          C.byref(reps))
+    if st != _ffi.DBCSR_OK and (st != _ffi.DBCSR_ENOTCONV or raise_on_notconv):
+        _check(st, "sign_iterate_nonorth")
+    return NonorthResult(P=P, report=rep, report_sqrt=reps, status=st)
+
+
 def sign_iterate_batched(Hs, mus, eps_filter: float, tol: float, max_iter: int = 100, prec: int = DBCSR_FP64,
                          switch_tol: float = 1e-4, stall_ratio: float = 0.5, verbose: bool = False,
                          low: int = DBCSR_BF16X3, low_correction: bool = False, order: int = 2):

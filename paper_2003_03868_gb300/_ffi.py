@@ -91,6 +91,9 @@ SIGNATURES = [
     ("dbcsr_trace_product_noalloc", C.c_int, [P, P, P]),
     ("dbcsr_gershgorin", C.c_int, [P, C.c_double, C.POINTER(C.c_double)]),
     ("dbcsr_sign_iterate", C.c_int, [P, C.c_double, C.POINTER(SignOpts), P, C.POINTER(SignReport)]),
+    ("dbcsr_inverse_sqrt", C.c_int, [P, C.POINTER(SignOpts), P, P, C.POINTER(SignReport)]),
+    ("dbcsr_sign_iterate_nonorth", C.c_int, [P, P, C.c_double, C.POINTER(SignOpts), P, C.POINTER(SignReport),
+                                             C.POINTER(SignReport)]),
     ("dbcsr_sign_iterate_batched", C.c_int, [C.c_int32, P, P, C.POINTER(SignOpts), P, P]),
     ("dbcsr_tune_space", C.c_int, [C.c_int32, P, C.c_int32, C.POINTER(C.c_int32)]),
     ("dbcsr_autotune", C.c_int, [P, C.c_int32, C.c_int32, C.c_int64, C.c_int32, P, C.c_int64, C.POINTER(C.c_int64)]),

@@ -211,11 +211,23 @@ void execute_plan(MultPlan* plan);
 // Fails with DBCSR_ESTATE when a live plan uses m's arrays (they must not be replaced).
 void check_unplanned(const dbcsr_matrix_* m, const char* where);
 
+// ---- sqrt.cu
+// S^(-1/2) (into Sinv) and, when Ssqrt is given, S^(1/2) by the sign iteration on [[0, S], [1, 0]].
+dbcsr_status inverse_sqrt(dbcsr_matrix_* S, const dbcsr_sign_opts* opts, dbcsr_matrix_* Sinv, dbcsr_matrix_* Ssqrt,
+                          dbcsr_sign_report* rep);
+dbcsr_status sign_iterate_nonorth(dbcsr_matrix_* K, dbcsr_matrix_* S, double mu, const dbcsr_sign_opts* opts,
+                                  dbcsr_matrix_* P, dbcsr_sign_report* rep, dbcsr_sign_report* rep_sqrt);
+
 // ---- sign.cu
 // A matrix with m's block sizes and stream, no pattern yet.
 std::unique_ptr<dbcsr_matrix_> make_like(const dbcsr_matrix_* m, cudaStream_t s);
 // c_0..c_n, c_j = binom(2j, j) / 4^j: the step polynomial p_n(y) = sum_j c_j (1 - y)^j.
 std::vector<double> sign_series_coeffs(int n);
+// U = p_n(Y) for the step of order n + 1 (Y = filter(X X), or Z Y in the square-root
+// iteration): order 2 gives (3 - Y) / 2 with no product; higher orders sum p_n in powers of
+// 1 - Y with filtered products (Y is then overwritten with 1 - Y).
+std::unique_ptr<dbcsr_matrix_> step_polynomial(dbcsr_matrix_* Y, int order, double eps, int tier, int sym,
+                                               const std::function<void(const dbcsr_mult_stats&, int)>& account);
 // One update X <- filter(X p_n(Y)) of the sign iteration of order n + 1, given
 // Y = filter(X X); products in precision tier with symmetry mode sym, each passed to account.
 // Y is overwritten (with 1 - Y for orders above 2, with Y - 1 in order 2's correction form).

@@ -670,4 +670,22 @@ dbcsr_status dbcsr_sign_iterate(dbcsr_matrix H, double mu, const dbcsr_sign_opts
     return st;
 }
 
+dbcsr_status dbcsr_inverse_sqrt(dbcsr_matrix S, const dbcsr_sign_opts* opts, dbcsr_matrix S_invsqrt,
+                                dbcsr_matrix S_sqrt, dbcsr_sign_report* rep) {
+    dbcsr_status st = DBCSR_OK;
+    dbcsr_status g = guarded([&] { st = dbg::inverse_sqrt(S, opts, S_invsqrt, S_sqrt, rep); });
+    if (g != DBCSR_OK) return g;
+    if (st != DBCSR_OK) g_last_error = "square-root iteration did not reach the tolerance";
+    return st;
+}
+
+dbcsr_status dbcsr_sign_iterate_nonorth(dbcsr_matrix K, dbcsr_matrix S, double mu, const dbcsr_sign_opts* opts,
+                                        dbcsr_matrix P_out, dbcsr_sign_report* rep, dbcsr_sign_report* rep_sqrt) {
+    dbcsr_status st = DBCSR_OK;
+    dbcsr_status g = guarded([&] { st = dbg::sign_iterate_nonorth(K, S, mu, opts, P_out, rep, rep_sqrt); });
+    if (g != DBCSR_OK) return g;
+    if (st != DBCSR_OK) g_last_error = "an iteration did not reach the tolerance";
+    return st;
+}
+
 }  // extern "C"

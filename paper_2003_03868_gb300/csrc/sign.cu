@@ -53,6 +53,58 @@ std::vector<double> sign_series_coeffs(int n) {
     return c;
 }
 
+std::unique_ptr<dbcsr_matrix_> step_polynomial(dbcsr_matrix_* Y, int order, double eps, int tier, int sym,
+                                               const std::function<void(const dbcsr_mult_stats&, int)>& account) {
+    const int n = order - 1;
+    const std::vector<double> c = sign_series_coeffs(n);
+    cudaStream_t s = Y->stream;
+    dbcsr_mult_stats st{};
+    if (n == 1) {
+        auto U = make_like(Y, s);
+        copy_matrix(U.get(), Y);
+        scale_shift(U.get(), -c[1], c[0] + c[1]);         // 1 + (1 - Y) / 2
+        return U;
+    }
+    scale_shift(Y, -1.0, 1.0);                            // Z = 1 - Y, in place
+    dbcsr_matrix_* Z = Y;
+    auto Z2 = make_like(Y, s);
+    multiply(1.0, Z, Z, 0.0, Z2.get(), eps, tier, &st, false, sym);
+    account(st, tier);
+    // pair i of p_n: c_2i+1 Z + c_2i 1
+    auto pair = [&](dbcsr_matrix_* dst, int i) {
+        copy_matrix(dst, Z);
+        scale_shift(dst, c[2 * i + 1], c[2 * i]);
+    };
+    const int m = n / 2;
+    auto R = make_like(Y, s);
+    int i;
+    if (n % 2 == 0) {
+        pair(R.get(), m - 1);
+        add(R.get(), 1.0, Z2.get(), c[n]);               // c_n Z2 + c_n-1 Z + c_n-2
+        i = m - 2;
+    } else {
+        pair(R.get(), m);                                // c_n Z + c_n-1
+        i = m - 1;
+    }
+    if (n == 2) return R;                                // q_0 + c_2 Z2
+    for (; i >= 1; --i) {
+        auto V = make_like(Y, s);
+        pair(V.get(), i);
+        multiply(1.0, Z2.get(), R.get(), 1.0, V.get(), eps, tier, &st, false, sym);
+        account(st, tier);
+        R = std::move(V);
+    }
+    auto V = make_like(Y, s);
+    multiply(1.0, Z2.get(), R.get(), 0.0, V.get(), eps, tier, &st, false, sym);
+    account(st, tier);
+    R.reset();
+    Z2.reset();
+    auto U = make_like(Y, s);
+    pair(U.get(), 0);
+    add(U.get(), 1.0, V.get(), 1.0);                     // q_0 + filter(Z2 R)
+    return U;
+}
+
 void sign_update(dbcsr_matrix_* X, dbcsr_matrix_* Y, int order, bool correction, double eps, int tier, int sym,
                  const std::function<void(const dbcsr_mult_stats&, int)>& account) {
     dbcsr_mult_stats st{};
@@ -68,50 +120,7 @@ void sign_update(dbcsr_matrix_* X, dbcsr_matrix_* Y, int order, bool correction,
         }
         return;
     }
-    const int n = order - 1;
-    const std::vector<double> c = sign_series_coeffs(n);
-    cudaStream_t s = X->stream;
-    scale_shift(Y, -1.0, 1.0);                            // Z = 1 - X^2, in place
-    dbcsr_matrix_* Z = Y;
-    auto Z2 = make_like(X, s);
-    multiply(1.0, Z, Z, 0.0, Z2.get(), eps, tier, &st, false, sym);
-    account(st, tier);
-    // pair i of p_n: c_2i+1 Z + c_2i 1
-    auto pair = [&](dbcsr_matrix_* dst, int i) {
-        copy_matrix(dst, Z);
-        scale_shift(dst, c[2 * i + 1], c[2 * i]);
-    };
-    const int m = n / 2;
-    auto R = make_like(X, s);
-    int i;
-    if (n % 2 == 0) {
-        pair(R.get(), m - 1);
-        add(R.get(), 1.0, Z2.get(), c[n]);               // c_n Z2 + c_n-1 Z + c_n-2
-        i = m - 2;
-    } else {
-        pair(R.get(), m);                                // c_n Z + c_n-1
-        i = m - 1;
-    }
-    std::unique_ptr<dbcsr_matrix_> U;
-    if (n == 2) {
-        U = std::move(R);                                // q_0 + c_2 Z2
-    } else {
-        for (; i >= 1; --i) {
-            auto V = make_like(X, s);
-            pair(V.get(), i);
-            multiply(1.0, Z2.get(), R.get(), 1.0, V.get(), eps, tier, &st, false, sym);
-            account(st, tier);
-            R = std::move(V);
-        }
-        auto V = make_like(X, s);
-        multiply(1.0, Z2.get(), R.get(), 0.0, V.get(), eps, tier, &st, false, sym);
-        account(st, tier);
-        R.reset();
-        U = make_like(X, s);
-        pair(U.get(), 0);
-        add(U.get(), 1.0, V.get(), 1.0);                 // q_0 + filter(Z2 R)
-    }
-    Z2.reset();
+    auto U = step_polynomial(Y, order, eps, tier, sym, account);
     multiply(1.0, X, U.get(), 0.0, X, eps, tier, &st, false, sym);
     account(st, tier);
 }
