@@ -421,6 +421,84 @@ def run_nonorth(args, gb, synth, torch, barrier, w, h):
     return 0
 
 
+def run_purify(args, gb, synth, torch, barrier, w, h):
+    """Canonical density matrices without a known mu: TC2 and TRS4 purification, and the sign
+    method with mu bisected on H + 1.0 (the shift moves the gap off mu = 0) in the bracket
+    [0.3, 5.0], next to the sign method at the known mid-gap mu.  The bracket's lower end
+    lies just above the occupied band, as an estimate from an earlier step would: a trial
+    mu inside a band makes sign(H - mu) non-local, and the filtered X then fills in toward
+    a dense matrix (on 1,024 waters it passed a million blocks within ten steps)."""
+    from paper_2003_03868_gb300 import ranks
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+    stream = torch.cuda.current_stream()
+    H = gb.Matrix.of(h.H, stream=stream.cuda_stream)
+    shift = 1.0
+    Hs = H.copy()
+    Hs.scale_shift(1.0, shift)
+    clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
+    l0 = gb.lib().dbcsr_launch_count()
+
+    def leg(run):
+        for _ in range(args.warmup):
+            run()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        flops = ms_mult = 0.0
+        for _ in range(args.steps):
+            r = run()
+            flops += r.report.flops
+            ms_mult += r.report.ms_multiply
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ms, flops_all = ranks.job_timing(e0.elapsed_time(e1) / args.steps, flops / args.steps, dist, "cuda")
+        return r, {"time_to_p_ms": ms, "value": flops_all / (ms * 1e-3) / 1e12, "flops_per_step": flops / args.steps,
+                   "kernel_tflops": flops / (ms_mult * 1e-3) / 1e12 if ms_mult > 0 else None,
+                   "iterations": r.report.iterations, "converged": bool(r.report.converged),
+                   "trace_p": r.report.trace_p, "trace_p_error": r.report.trace_p - h.n_occ,
+                   "e_band": r.report.e_band}
+
+    rs, ref = leg(lambda: gb.sign_iterate(H, h.mu, w.eps_filter, w.tol))
+    ref["residual"] = rs.report.residual
+    legs = {"sign_known_mu": ref}
+    for m in ("tc2", "trs4"):
+        r, x = leg(lambda: gb.purify(H, h.n_occ, w.eps_filter, w.tol, method=m))
+        x["idempotency"] = r.report.residual
+        legs[m] = x
+    bracket = (shift - 0.7, shift + 4.0)
+    rm, x = leg(lambda: gb.sign_mu_search(Hs, h.n_occ, w.eps_filter, w.tol, mu_lo=bracket[0], mu_hi=bracket[1]))
+    x.update({"mu": rm.mu, "evaluations": rm.evaluations, "shift": shift, "bracket": bracket,
+              "e_band": rm.report.e_band - shift * h.n_occ})      # back to H's energy
+    legs["sign_mu_search"] = x
+    for k, x in legs.items():
+        x["de_band_per_atom_vs_sign"] = abs(x["e_band"] - ref["e_band"]) / h.n_atoms
+        x["speedup_vs_sign_known_mu"] = ref["time_to_p_ms"] / x["time_to_p_ms"]
+    launches = gb.lib().dbcsr_launch_count() - l0
+    clk = clocks.stop()
+    best = min(("tc2", "trs4", "sign_mu_search"), key=lambda k: legs[k]["time_to_p_ms"])
+    out = {"metric": "time-to-P without a known chemical potential (FP64; fastest canonical method)",
+           "value": legs[best]["time_to_p_ms"], "unit": "ms", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": legs[best]["time_to_p_ms"], "higher_is_better": False,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": w.name + "-purify", "n_mol": w.n_mol, "N": w.n, "n_occ": h.n_occ,
+                      "blocks": {"O": w.basis[0], "H": w.basis[1]}, "eps_filter": w.eps_filter, "tol": w.tol,
+                      "mu_search_on": f"H + {shift} 1",
+                      "l2": "inputs larger than L2 (H alone is %.0f MB; 129 MB L2)" % (h.H.data.nbytes / 1e6),
+                      "parallelism": f"replicas x{world}"},
+           "fastest": best, "legs": legs, "gpu_launches": launches, "clocks": clk}
+    if rank == 0:
+        print(json.dumps(out))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
 def run_mult32(args, gb, synth, torch, barrier):
     """The single product C = A A of the 32-water decay matrix (N = 736, eps 1e-6): one-off
     products (stack builder, block products, filter, with their host round trips) against
@@ -602,14 +680,16 @@ def main():
     ap.add_argument("--workload", default="sign-1024h2o",
                     choices=["sign-1024h2o", "sign-512h2o", "sign-512h2o-23-7", "sign-4096h2o", "batch-64",
                              "sign-20736h2o-mlp", "mult-32h2o", "sign-1024h2o-orders", "sign-4096h2o-orders",
-                             "sign-1024h2o-nonorth", "sign-4096h2o-nonorth"],
+                             "sign-1024h2o-nonorth", "sign-4096h2o-nonorth", "sign-1024h2o-purify",
+                             "sign-4096h2o-purify"],
                     help="sign-512h2o, sign-512h2o-23-7: smaller cases for profiler captures; sign-4096h2o: "
                          "4,096 waters with O/H blocks 23/7 (FP64 and mixed); batch-64: 64 uneven systems "
                          "batched vs one by one; sign-20736h2o-mlp: the mixed iteration on 20,736 waters with "
                          "default, MLP-predicted and exhaustively tuned launch configurations; mult-32h2o: the "
                          "32-water product, one-off vs planned (CUDA graph); sign-1024h2o-orders, "
                          "sign-4096h2o-orders: the sign iteration of orders 2 to 7 (--orders), FP64 and mixed; "
-                         "sign-1024h2o-nonorth, sign-4096h2o-nonorth: the density matrix with an overlap matrix S")
+                         "sign-1024h2o-nonorth, sign-4096h2o-nonorth: the density matrix with an overlap matrix S; "
+                         "sign-1024h2o-purify, sign-4096h2o-purify: TC2, TRS4 and the mu search")
     ap.add_argument("--orders", default="2,3,4,5,6,7", help="sign-*-orders: the orders to time")
     ap.add_argument("--train-triples", type=int, default=48, help="sign-20736h2o-mlp: autotuned training triples")
     ap.add_argument("--tune-stack", type=int, default=500000, help="products of the autotuner's synthetic stacks")
@@ -660,6 +740,7 @@ def main():
     w = {"sign-1024h2o": synth.SIGN_1024, "sign-4096h2o": synth.SIGN_4096,
          "sign-1024h2o-orders": synth.SIGN_1024, "sign-4096h2o-orders": synth.SIGN_4096,
          "sign-1024h2o-nonorth": synth.SIGN_1024, "sign-4096h2o-nonorth": synth.SIGN_4096,
+         "sign-1024h2o-purify": synth.SIGN_1024, "sign-4096h2o-purify": synth.SIGN_4096,
          "sign-512h2o": synth.Workload("sign-512h2o-dzvp-fp64", 512, (13, 5), synth.configs.BASE_SEED + 12, 1e-7, 1e-9),
          "sign-512h2o-23-7": synth.Workload("sign-512h2o-23-7", 512, (23, 7), synth.configs.BASE_SEED + 13, 1e-6, 1e-8,
                                             1e-4)}[args.workload]
@@ -668,6 +749,8 @@ def main():
         return run_orders(args, gb, synth, torch, barrier, w, h)
     if args.workload.endswith("-nonorth"):
         return run_nonorth(args, gb, synth, torch, barrier, w, h)
+    if args.workload.endswith("-purify"):
+        return run_purify(args, gb, synth, torch, barrier, w, h)
     stream = torch.cuda.current_stream()
     H = gb.Matrix.of(h.H, stream=stream.cuda_stream)
 

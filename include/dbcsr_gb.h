@@ -373,6 +373,42 @@ dbcsr_status dbcsr_inverse_sqrt(dbcsr_matrix S, const dbcsr_sign_opts* opts, dbc
 dbcsr_status dbcsr_sign_iterate_nonorth(dbcsr_matrix K, dbcsr_matrix S, double mu, const dbcsr_sign_opts* opts,
                                         dbcsr_matrix P_out, dbcsr_sign_report* rep, dbcsr_sign_report* rep_sqrt);
 
+/*
+ * Canonical density matrix without a chemical potential (section "Purification
+ * methods": CP2K's trace-conserving TC2 and trace-resetting TRS4; the steps follow the
+ * published algorithms of Niklasson (2002) and Niklasson, Tymczak and Challacombe (2003)):
+ *   X_0 = (g 1 - H) / (2 g), g = dbcsr_gershgorin(H, 0);
+ *   repeat: e = (Tr X - Tr X^2) / N; stop when |e| < tol;
+ *     DBCSR_PURIFY_TC2:  X <- X^2 if Tr X > n_occ, else 2 X - X^2;
+ *     DBCSR_PURIFY_TRS4: X2 = X^2, gamma = (n_occ - Tr F) / Tr G with F = X2 (4 X - 3 X2),
+ *       G = X2 (1 - X)^2; gamma in [0, 6]: X <- F + gamma G; gamma > 6: 2 X - X2;
+ *       gamma < 0: X2.
+ *   P_out = X, the projector on the n_occ lowest states of H (H symmetric, a gap after
+ *   state n_occ, every diagonal block present).
+ * Every product is filtered with eps_filter (and mirrored unless DBCSR_SIGN_FULL_PRODUCTS).
+ * opts: eps_filter, tol, max_iter (default 100), verbose, flags; prec must be DBCSR_FP64.
+ * rep (may be NULL): iterations = steps, residual_history = e before each step, alpha = g,
+ * trace_p = Tr P, e_band = Tr(P H), work and times.  Returns DBCSR_ENOTCONV (P_out and
+ * rep still filled) after max_iter steps.  Errors: EINVAL (unknown method, n_occ outside
+ * [0, N], ...), ESTATE, ENOMEM, ENAN, ECUDA.
+ */
+#define DBCSR_PURIFY_TC2 1
+#define DBCSR_PURIFY_TRS4 2
+dbcsr_status dbcsr_purify(dbcsr_matrix H, double n_occ, int32_t method, const dbcsr_sign_opts* opts,
+                          dbcsr_matrix P_out, dbcsr_sign_report* rep);
+
+/*
+ * The sign method with its chemical potential placed for a canonical occupation
+ * (section "Purification methods": extra iterations that find mu): mu bisects
+ * [mu_lo, mu_hi] (NaN: the Gershgorin interval [-g, g] of H), one dbcsr_sign_iterate per
+ * trial, until |Tr P(mu) - n_occ| < 1/2.  *mu_out and *evaluations (may be NULL) receive
+ * the final mu and the number of trials (at most 60); rep (may be NULL) the last trial's
+ * report with the work and time of all trials.  Returns DBCSR_ENOTCONV when no trial
+ * reached the occupation, or the last sign iteration did not converge.
+ */
+dbcsr_status dbcsr_sign_mu_search(dbcsr_matrix H, double n_occ, double mu_lo, double mu_hi, const dbcsr_sign_opts* opts,
+                                  dbcsr_matrix P_out, double* mu_out, int32_t* evaluations, dbcsr_sign_report* rep);
+
 /* Launch configuration of the block-product kernel of one (m, n, k) stack.  No
  * field changes the arithmetic: every C element is summed in the same order. */
 typedef struct {

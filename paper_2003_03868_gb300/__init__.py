@@ -340,6 +340,51 @@ def sign_iterate_nonorth(K: Matrix, S: Matrix, mu: float, eps_filter: float, tol
     return NonorthResult(P=P, report=rep, report_sqrt=reps, status=st)
 
 
+def purify(H: Matrix, n_occ: float, eps_filter: float, tol: float, method: str = "tc2", max_iter: int = 100,
+           full_products: bool = False, P: Matrix | None = None, verbose: bool = False,
+           raise_on_notconv: bool = False) -> SignResult:
+    """Canonical projector on the n_occ lowest states of H by TC2 or TRS4 purification
+    (dbcsr_purify).  report.residual_history holds (Tr X - Tr X^2) / N per step."""
+    m = {"tc2": _ffi.DBCSR_PURIFY_TC2, "trs4": _ffi.DBCSR_PURIFY_TRS4}[method]
+    P = Matrix(H.blk_size, H.stream) if P is None else P
+    o = SignOpts(float(eps_filter), float(tol), int(max_iter), DBCSR_FP64, 0.0, 0.0, 1 if verbose else 0,
+                 _sign_flags(full_products, DBCSR_BF16X3, False), 0, 0)
+    rep = SignReport()
+    st = lib().dbcsr_purify(H.handle, float(n_occ), m, C.byref(o), P.handle, C.byref(rep))
+    if st != _ffi.DBCSR_OK and (st != _ffi.DBCSR_ENOTCONV or raise_on_notconv):
+        _check(st, "purify")
+    return SignResult(P=P, report=rep, status=st)
+
+
+@dataclasses.dataclass
+class MuSearchResult:
+    P: Matrix
+    mu: float
+    evaluations: int
+    report: SignReport
+    status: int
+
+
+def sign_mu_search(H: Matrix, n_occ: float, eps_filter: float, tol: float, mu_lo: float | None = None,
+                   mu_hi: float | None = None, max_iter: int = 100, prec: int = DBCSR_FP64, switch_tol: float = 1e-4,
+                   order: int = 2, P: Matrix | None = None, verbose: bool = False,
+                   raise_on_notconv: bool = False) -> MuSearchResult:
+    """The sign method with mu bisected until Tr P = n_occ within 1/2 (dbcsr_sign_mu_search)."""
+    P = Matrix(H.blk_size, H.stream) if P is None else P
+    o = SignOpts(float(eps_filter), float(tol), int(max_iter), int(prec), float(switch_tol), 0.5, 1 if verbose else 0,
+                 0, int(order), 0)
+    rep = SignReport()
+    mu = C.c_double()
+    ev = C.c_int32()
+    lo = float("nan") if mu_lo is None else float(mu_lo)
+    hi = float("nan") if mu_hi is None else float(mu_hi)
+    st = lib().dbcsr_sign_mu_search(H.handle, float(n_occ), lo, hi, C.byref(o), P.handle, C.byref(mu), C.byref(ev),
+                                    C.byref(rep))
+    if st != _ffi.DBCSR_OK and (st != _ffi.DBCSR_ENOTCONV or raise_on_notconv):
+        _check(st, "sign_mu_search")
+    return MuSearchResult(P=P, mu=mu.value, evaluations=ev.value, report=rep, status=st)
+
+
 def sign_iterate_batched(Hs, mus, eps_filter: float, tol: float, max_iter: int = 100, prec: int = DBCSR_FP64,
                          switch_tol: float = 1e-4, stall_ratio: float = 0.5, verbose: bool = False,
                          low: int = DBCSR_BF16X3, low_correction: bool = False, order: int = 2):

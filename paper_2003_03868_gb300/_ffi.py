@@ -10,6 +10,7 @@ LIB_PATH = os.path.join(HERE, "libdbcsr_gb.so")
 DBCSR_OK, DBCSR_EINVAL, DBCSR_ENOMEM, DBCSR_ECAPACITY, DBCSR_ECUDA = 0, 1, 2, 3, 4
 DBCSR_ENAN, DBCSR_ENOTCONV, DBCSR_ETIMEOUT, DBCSR_ESTATE = 5, 6, 7, 8
 DBCSR_FP64, DBCSR_BF16, DBCSR_MIXED, DBCSR_BF16X3 = 0, 2, 3, 4
+DBCSR_PURIFY_TC2, DBCSR_PURIFY_TRS4 = 1, 2
 DBCSR_SIGN_FULL_PRODUCTS, DBCSR_SIGN_PLAIN_BF16, DBCSR_SIGN_LOW_CORRECTION = 1, 2, 4
 MAX_HISTORY = 128
 
@@ -92,6 +93,9 @@ SIGNATURES = [
     ("dbcsr_gershgorin", C.c_int, [P, C.c_double, C.POINTER(C.c_double)]),
     ("dbcsr_sign_iterate", C.c_int, [P, C.c_double, C.POINTER(SignOpts), P, C.POINTER(SignReport)]),
     ("dbcsr_inverse_sqrt", C.c_int, [P, C.POINTER(SignOpts), P, P, C.POINTER(SignReport)]),
+    ("dbcsr_purify", C.c_int, [P, C.c_double, C.c_int32, C.POINTER(SignOpts), P, C.POINTER(SignReport)]),
+    ("dbcsr_sign_mu_search", C.c_int, [P, C.c_double, C.c_double, C.c_double, C.POINTER(SignOpts), P,
+                                       C.POINTER(C.c_double), C.POINTER(C.c_int32), C.POINTER(SignReport)]),
     ("dbcsr_sign_iterate_nonorth", C.c_int, [P, P, C.c_double, C.POINTER(SignOpts), P, C.POINTER(SignReport),
                                              C.POINTER(SignReport)]),
     ("dbcsr_sign_iterate_batched", C.c_int, [C.c_int32, P, P, C.POINTER(SignOpts), P, P]),

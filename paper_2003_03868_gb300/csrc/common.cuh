@@ -45,11 +45,24 @@ extern std::atomic<int64_t> g_launches;
 
 // Every kernel launch site is followed by DBG_LAUNCH_CK(): it checks the launch
 // and counts it (dbcsr_launch_count).
-#define DBG_LAUNCH_CK()                                    \
-    do {                                                   \
-        ::dbg::g_launches.fetch_add(1, std::memory_order_relaxed); \
-        DBG_CK(cudaGetLastError());                        \
+#define DBG_LAUNCH_CK()                                                                          \
+    do {                                                                                         \
+        ::dbg::g_launches.fetch_add(1, std::memory_order_relaxed);                               \
+        cudaError_t e_ = cudaGetLastError();                                                     \
+        if (e_ != cudaSuccess)                                                                   \
+            ::dbg::fail(e_ == cudaErrorMemoryAllocation ? DBCSR_ENOMEM : DBCSR_ECUDA,            \
+                        std::string("kernel launch at ") + __FILE__ + ":" + std::to_string(__LINE__) + \
+                            ": " + cudaGetErrorString(e_));                                      \
     } while (0)
+
+// Sets kernel's dynamic shared-memory limit to dyn bytes before a launch that asks for them.
+// The default limit (48 KB) covers static and dynamic shared memory together, so a launch
+// just under 48 KB of dynamic memory fails too when the kernel has static arrays; the
+// attribute is therefore set for every nonzero request.
+template <class K>
+inline void allow_dyn_smem(K kernel, size_t dyn) {
+    if (dyn > 0) DBG_CK(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+}
 
 // The library's stream-ordered memory pool on the current device.  It keeps freed
 // memory cached (release threshold = max) so that the per-product stacks and
@@ -210,6 +223,12 @@ void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbc
 void execute_plan(MultPlan* plan);
 // Fails with DBCSR_ESTATE when a live plan uses m's arrays (they must not be replaced).
 void check_unplanned(const dbcsr_matrix_* m, const char* where);
+
+// ---- purify.cu
+dbcsr_status purify(dbcsr_matrix_* H, double n_occ, int32_t method, const dbcsr_sign_opts* opts, dbcsr_matrix_* P,
+                    dbcsr_sign_report* rep);
+dbcsr_status sign_mu_search(dbcsr_matrix_* H, double n_occ, double mu_lo, double mu_hi, const dbcsr_sign_opts* opts,
+                            dbcsr_matrix_* P, double* mu_out, int32_t* evaluations, dbcsr_sign_report* rep);
 
 // ---- sqrt.cu
 // S^(-1/2) (into Sinv) and, when Ssqrt is given, S^(1/2) by the sign iteration on [[0, S], [1, 0]].

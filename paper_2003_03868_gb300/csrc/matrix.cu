@@ -688,4 +688,22 @@ dbcsr_status dbcsr_sign_iterate_nonorth(dbcsr_matrix K, dbcsr_matrix S, double m
     return st;
 }
 
+dbcsr_status dbcsr_purify(dbcsr_matrix H, double n_occ, int32_t method, const dbcsr_sign_opts* opts,
+                          dbcsr_matrix P_out, dbcsr_sign_report* rep) {
+    dbcsr_status st = DBCSR_OK;
+    dbcsr_status g = guarded([&] { st = dbg::purify(H, n_occ, method, opts, P_out, rep); });
+    if (g != DBCSR_OK) return g;
+    if (st != DBCSR_OK) g_last_error = "purification did not reach the tolerance";
+    return st;
+}
+
+dbcsr_status dbcsr_sign_mu_search(dbcsr_matrix H, double n_occ, double mu_lo, double mu_hi, const dbcsr_sign_opts* opts,
+                                  dbcsr_matrix P_out, double* mu_out, int32_t* evaluations, dbcsr_sign_report* rep) {
+    dbcsr_status st = DBCSR_OK;
+    dbcsr_status g = guarded([&] { st = dbg::sign_mu_search(H, n_occ, mu_lo, mu_hi, opts, P_out, mu_out, evaluations, rep); });
+    if (g != DBCSR_OK) return g;
+    if (st != DBCSR_OK) g_last_error = "no chemical potential with the requested occupation was reached";
+    return st;
+}
+
 }  // extern "C"

@@ -1233,8 +1233,7 @@ void launch_smm_shape(int prec, int m, int n, int64_t cnt, const int64_t* list, 
         SmmBf16Args ga{sa, pk.a16, pk.a_po, pk.b16, pk.b_po, pk.a16_lo, pk.b16_lo};
         // the warps' stage rings
         const size_t smem = (size_t)(cfg.tpb / 32) * bf16_stages(mt, nt, split) * bf16_stage_bytes(mt, nt, split);
-        if (smem > 48 * 1024)
-            DBG_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        allow_dyn_smem(kern, smem);
         kern<<<(unsigned)grid, cfg.tpb, smem, s>>>(cnt, list, ga);
     } else {
         const int mn = m * n;
@@ -1319,7 +1318,7 @@ void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbc
     maxrow.zero();
     {
         const size_t sm = sm_rank;
-        if (sm > 48 * 1024) DBG_CK(cudaFuncSetAttribute(k_cand_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        allow_dyn_smem(k_cand_count, sm);
         k_cand_count<<<sym_grid(nblk), kSymThreads, sm, s>>>(nblk, P, nwords, ccnt.p, (unsigned long long*)maxrow.p);
         DBG_LAUNCH_CK();
     }
@@ -1354,7 +1353,7 @@ void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbc
                      bound.p, pcnt.p, ksum.p, use_c ? cin.p : nullptr, keep.p, acc_smem ? 1 : 0,
                      fast_bound ? 1 : 0};
         const size_t sm = acc_smem ? sm_acc : sm_rank;
-        if (sm > 48 * 1024) DBG_CK(cudaFuncSetAttribute(k_cand_bound, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        allow_dyn_smem(k_cand_bound, sm);
         k_cand_bound<<<sym_grid(nblk), kSymThreads, sm, s>>>(nblk, P, nwords, ba);
         DBG_LAUNCH_CK();
     }
@@ -1429,7 +1428,7 @@ void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbc
     if (nprod) {
         FillArgs fa{coff.p, keep.p, f_comp.p, kidx.p, f_pbeg.p, cursor.p, prod_a.p, prod_b.p, fill_smem ? 1 : 0};
         const size_t sm = fill_smem ? sm_fill : sm_rank;
-        if (sm > 48 * 1024) DBG_CK(cudaFuncSetAttribute(k_fill_stack, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        allow_dyn_smem(k_fill_stack, sm);
         k_fill_stack<<<sym_grid(nblk), kSymThreads, sm, s>>>(nblk, P, nwords, fa);
         DBG_LAUNCH_CK();
     }

@@ -235,3 +235,39 @@ def test_wide_rows_take_the_global_and_ordered_paths(gb, eps):
     assert st.n_candidates == info.unfiltered.nnzb
     if eps == 0.0:
         assert st.flops == info.flops
+
+
+def _one_row_of(c, nb):
+    """1x1 blocks; row 0 holds blocks 0..c-1, every other row its diagonal: row 0 of A*A has
+    exactly c candidates."""
+    from synth.waterbox import BlockMatrix
+    rng = np.random.default_rng(c)
+    rows = [np.arange(c)] + [np.array([i]) for i in range(1, nb)]
+    rp = np.zeros(nb + 1, dtype=np.int64)
+    np.cumsum([len(r) for r in rows], out=rp[1:])
+    col = np.concatenate(rows).astype(np.int32)
+    return BlockMatrix(np.ones(nb, dtype=np.int32), rp, col, rng.uniform(-1, 1, col.shape[0]))
+
+
+def test_row_lengths_at_the_default_shared_memory_limit(gb):
+    # The stack builder keeps a row's candidates in dynamic shared memory (20 bytes each in
+    # the bound pass, 12 in the fill pass, after a bitmap).  Rows whose dynamic size falls
+    # just under 48 KB need the opt-in too, as the kernels' static arrays count against the
+    # same limit; sweep every row length whose dynamic size lies in the top 1 KB below it.
+    def sm_rank(nb):
+        nwords = (nb + 31) // 32
+        return 2 * ((nwords + 1) & ~1) * 4
+
+    cases = set()
+    for per in (20, 12):
+        for c in range(2000, 4200):
+            dyn = sm_rank(c + 64) + per * c
+            if 48 * 1024 - 1024 < dyn <= 48 * 1024:
+                cases.add(c)
+    assert len(cases) > 100
+    for c in sorted(cases):
+        a = _one_row_of(c, c + 64)
+        (A, Ao) = _pair(gb, a)
+        C = gb.Matrix(A.blk_size, A.stream)
+        gb.multiply(1.0, A, A, 0.0, C, 0.0)
+        _assert_same(C, bsr.multiply(1.0, Ao, Ao))
