@@ -499,6 +499,70 @@ def run_purify(args, gb, synth, torch, barrier, w, h):
     return 0
 
 
+def run_submatrix(args, gb, synth, torch, barrier):
+    """The submatrix method against the sparse Newton-Schulz iteration on 6,192 waters with
+    a minimal basis (SZV, N = 37,152): time-to-P and band-energy error per atom against a
+    tight reference (Newton-Schulz at eps_filter 1e-9), as the paper compares them."""
+    from paper_2003_03868_gb300 import ranks
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+    w = synth.SUBMATRIX_6192
+    h = synth.build_hamiltonian(w)
+    stream = torch.cuda.current_stream()
+    H = gb.Matrix.of(h.H, stream=stream.cuda_stream)
+    clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
+    l0 = gb.lib().dbcsr_launch_count()
+    ref = gb.sign_iterate(H, h.mu, 1e-9, 1e-10)
+    e_ref = ref.report.e_band
+
+    def leg(run):
+        for _ in range(args.warmup):
+            run()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            r = run()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ms, flops_all = ranks.job_timing(e0.elapsed_time(e1) / args.steps, r.report.flops, dist, "cuda")
+        return {"time_to_p_ms": ms, "iterations": r.report.iterations, "converged": bool(r.report.converged),
+                "stalled": bool(r.report.stalled), "residual": r.report.residual, "gflop": r.report.flops * 1e-9,
+                "trace_p_error": r.report.trace_p - h.n_occ,
+                "de_band_per_atom": abs(r.report.e_band - e_ref) / h.n_atoms,
+                "rel_energy_error": abs(r.report.e_band - e_ref) / abs(e_ref)}
+
+    legs = {}
+    for eps in (1e-5, 1e-6, 1e-7):
+        legs[f"newton_schulz_eps{eps:g}"] = leg(lambda: gb.sign_iterate(H, h.mu, eps, 1e-9))
+    x = leg(lambda: gb.submatrix_sign(H, h.mu, 1e-5, prec=gb.DBCSR_MIXED))
+    x["dtype"] = "f32 (tf32 tensor-core GEMMs while r >= 1e-3, then fp32 GEMMs)"
+    legs["submatrix_tf32_fp32"] = x
+    launches = gb.lib().dbcsr_launch_count() - l0
+    clk = clocks.stop()
+    out = {"metric": "time-to-P and band-energy error, submatrix method vs Newton-Schulz (6,192 H2O, SZV)",
+           "value": legs["submatrix_tf32_fp32"]["time_to_p_ms"], "unit": "ms", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": legs["submatrix_tf32_fp32"]["time_to_p_ms"],
+           "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64",
+           "data": "synthetic",
+           "config": {"workload": w.name, "n_mol": w.n_mol, "N": w.n, "blocks": {"O": w.basis[0], "H": w.basis[1]},
+                      "reference": "Newton-Schulz FP64, eps_filter 1e-9, tol 1e-10",
+                      "e_band_reference": e_ref, "reference_iterations": ref.report.iterations,
+                      "l2": "inputs larger than L2 (H alone is %.0f MB; 129 MB L2)" % (h.H.data.nbytes / 1e6),
+                      "parallelism": f"replicas x{world}"},
+           "legs": legs, "gpu_launches": launches, "clocks": clk}
+    if rank == 0:
+        print(json.dumps(out))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
 def run_mult32(args, gb, synth, torch, barrier):
     """The single product C = A A of the 32-water decay matrix (N = 736, eps 1e-6): one-off
     products (stack builder, block products, filter, with their host round trips) against
@@ -681,7 +745,7 @@ def main():
                     choices=["sign-1024h2o", "sign-512h2o", "sign-512h2o-23-7", "sign-4096h2o", "batch-64",
                              "sign-20736h2o-mlp", "mult-32h2o", "sign-1024h2o-orders", "sign-4096h2o-orders",
                              "sign-1024h2o-nonorth", "sign-4096h2o-nonorth", "sign-1024h2o-purify",
-                             "sign-4096h2o-purify"],
+                             "sign-4096h2o-purify", "submatrix-6192h2o-szv"],
                     help="sign-512h2o, sign-512h2o-23-7: smaller cases for profiler captures; sign-4096h2o: "
                          "4,096 waters with O/H blocks 23/7 (FP64 and mixed); batch-64: 64 uneven systems "
                          "batched vs one by one; sign-20736h2o-mlp: the mixed iteration on 20,736 waters with "
@@ -689,7 +753,8 @@ def main():
                          "32-water product, one-off vs planned (CUDA graph); sign-1024h2o-orders, "
                          "sign-4096h2o-orders: the sign iteration of orders 2 to 7 (--orders), FP64 and mixed; "
                          "sign-1024h2o-nonorth, sign-4096h2o-nonorth: the density matrix with an overlap matrix S; "
-                         "sign-1024h2o-purify, sign-4096h2o-purify: TC2, TRS4 and the mu search")
+                         "sign-1024h2o-purify, sign-4096h2o-purify: TC2, TRS4 and the mu search; "
+                         "submatrix-6192h2o-szv: the submatrix method against Newton-Schulz")
     ap.add_argument("--orders", default="2,3,4,5,6,7", help="sign-*-orders: the orders to time")
     ap.add_argument("--train-triples", type=int, default=48, help="sign-20736h2o-mlp: autotuned training triples")
     ap.add_argument("--tune-stack", type=int, default=500000, help="products of the autotuner's synthetic stacks")
@@ -729,6 +794,8 @@ def main():
 
     if args.workload == "batch-64":
         return run_batch(args, gb, synth, torch, barrier)
+    if args.workload == "submatrix-6192h2o-szv":
+        return run_submatrix(args, gb, synth, torch, barrier)
     if args.workload in ("sign-20736h2o-mlp", "mult-32h2o"):
         # one-GPU studies: under torchrun rank 0 alone runs them
         if rank != 0:

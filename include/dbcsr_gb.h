@@ -392,6 +392,27 @@ dbcsr_status dbcsr_sign_iterate_nonorth(dbcsr_matrix K, dbcsr_matrix S, double m
  * rep still filled) after max_iter steps.  Errors: EINVAL (unknown method, n_occ outside
  * [0, N], ...), ESTATE, ENOMEM, ENAN, ECUDA.
  */
+/*
+ * Density matrix by the submatrix method (section "Submatrix Method"): one dense
+ * principal submatrix per block column j, over I_j = the pattern of column j of H (the
+ * atom and the atoms overlapping it), purified densely; block (i, j) of P_out, i in I_j,
+ * is taken from submatrix j.  P_out receives H's pattern (H symmetric in pattern).
+ *   X_0 = (H[I_j, I_j] - mu 1) / alpha, alpha = dbcsr_gershgorin(H, mu), padded to a
+ *   multiple of 16 with an identity block; all submatrices of one padded size run as one
+ *   batch of dense Newton-Schulz steps X <- 1.5 X - 0.5 X X^2 until every
+ *   ||X^2 - 1||_F / n_pad < tol; P = (1 - X) / 2 on the taken blocks.
+ * The dense products are strided-batched cuBLAS GEMMs.  opts: tol, max_iter, verbose;
+ * prec DBCSR_FP64 (DGEMM) or DBCSR_MIXED (FP32: TF32 tensor-core GEMMs while the largest
+ * residual is >= switch_tol, default 1e-3, then plain FP32 GEMMs; tol must then stay
+ * above the FP32 rounding floor, about 1e-6).  eps_filter is not used.  rep: iterations
+ * (the most of any batch), residual (the largest), fp64_from = the first step after the
+ * TF32 phase, n_products = submatrices, flops = dense GEMM flops, trace_p, e_band.
+ * Returns DBCSR_ENOTCONV when a batch ended at max_iter.  Errors: EINVAL (a missing
+ * diagonal block, ...), ESTATE, ENOMEM, ENAN, ECUDA.
+ */
+dbcsr_status dbcsr_submatrix_sign(dbcsr_matrix H, double mu, const dbcsr_sign_opts* opts, dbcsr_matrix P_out,
+                                  dbcsr_sign_report* rep);
+
 #define DBCSR_PURIFY_TC2 1
 #define DBCSR_PURIFY_TRS4 2
 dbcsr_status dbcsr_purify(dbcsr_matrix H, double n_occ, int32_t method, const dbcsr_sign_opts* opts,

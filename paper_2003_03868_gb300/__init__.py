@@ -340,6 +340,21 @@ def sign_iterate_nonorth(K: Matrix, S: Matrix, mu: float, eps_filter: float, tol
     return NonorthResult(P=P, report=rep, report_sqrt=reps, status=st)
 
 
+def submatrix_sign(H: Matrix, mu: float, tol: float, max_iter: int = 100, prec: int = DBCSR_FP64,
+                   switch_tol: float = 1e-3, P: Matrix | None = None, verbose: bool = False,
+                   raise_on_notconv: bool = False) -> SignResult:
+    """P by the submatrix method: dense sign of every block column's neighbourhood
+    (dbcsr_submatrix_sign).  prec=DBCSR_MIXED runs the dense products in FP32 (TF32 tensor
+    cores until the residual drops below switch_tol)."""
+    P = Matrix(H.blk_size, H.stream) if P is None else P
+    o = SignOpts(0.0, float(tol), int(max_iter), int(prec), float(switch_tol), 0.5, 1 if verbose else 0, 0, 0, 0)
+    rep = SignReport()
+    st = lib().dbcsr_submatrix_sign(H.handle, float(mu), C.byref(o), P.handle, C.byref(rep))
+    if st != _ffi.DBCSR_OK and (st != _ffi.DBCSR_ENOTCONV or raise_on_notconv):
+        _check(st, "submatrix_sign")
+    return SignResult(P=P, report=rep, status=st)
+
+
 def purify(H: Matrix, n_occ: float, eps_filter: float, tol: float, method: str = "tc2", max_iter: int = 100,
            full_products: bool = False, P: Matrix | None = None, verbose: bool = False,
            raise_on_notconv: bool = False) -> SignResult:

@@ -224,6 +224,10 @@ void execute_plan(MultPlan* plan);
 // Fails with DBCSR_ESTATE when a live plan uses m's arrays (they must not be replaced).
 void check_unplanned(const dbcsr_matrix_* m, const char* where);
 
+// ---- submatrix.cu
+dbcsr_status submatrix_sign(dbcsr_matrix_* H, double mu, const dbcsr_sign_opts* opts, dbcsr_matrix_* P,
+                            dbcsr_sign_report* rep);
+
 // ---- purify.cu
 dbcsr_status purify(dbcsr_matrix_* H, double n_occ, int32_t method, const dbcsr_sign_opts* opts, dbcsr_matrix_* P,
                     dbcsr_sign_report* rep);

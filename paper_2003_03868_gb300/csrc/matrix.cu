@@ -706,4 +706,13 @@ dbcsr_status dbcsr_sign_mu_search(dbcsr_matrix H, double n_occ, double mu_lo, do
     return st;
 }
 
+dbcsr_status dbcsr_submatrix_sign(dbcsr_matrix H, double mu, const dbcsr_sign_opts* opts, dbcsr_matrix P_out,
+                                  dbcsr_sign_report* rep) {
+    dbcsr_status st = DBCSR_OK;
+    dbcsr_status g = guarded([&] { st = dbg::submatrix_sign(H, mu, opts, P_out, rep); });
+    if (g != DBCSR_OK) return g;
+    if (st != DBCSR_OK) g_last_error = "a submatrix did not reach the tolerance";
+    return st;
+}
+
 }  // extern "C"

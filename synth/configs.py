@@ -45,6 +45,11 @@ SIGN_4096 = Workload("sign-4096h2o-23-7-mixed", 4096, (23, 7), BASE_SEED + 3, 1e
 SIGN_20736 = Workload("sign-20736h2o-23-7-mixed", 20736, (23, 7), BASE_SEED + 5, 1e-6, 1e-8, 1e-4)
 
 
+# The submatrix method's comparison system: 6,192 waters with a minimal basis (SZV: 4
+# functions on O, 1 on H), N = 37,152.
+SUBMATRIX_6192 = Workload("submatrix-6192h2o-szv", 6192, (4, 1), BASE_SEED + 6, 1e-6, 1e-9)
+
+
 def batch_seed(rank: int = 0) -> int:
     """Seed of the uneven-system batch solved by one rank (each rank its own systems)."""
     return BASE_SEED * 100 + 100000 * rank

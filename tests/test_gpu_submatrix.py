@@ -1,0 +1,68 @@
+"""GPU parity of the submatrix method (dbcsr_submatrix_sign: batched dense sign of every
+block column's neighbourhood) against the oracle's per-submatrix eigendecomposition."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import bsr, submatrix
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gb():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2003_03868_gb300 as m
+    m.lib()
+    return m
+
+
+def _mat(M):
+    rp, col, data = M.export()
+    return bsr.Mat(M.blk_size, rp, col, data)
+
+
+@pytest.mark.parametrize("n_mol,basis", [(4, (13, 5)), (48, (4, 1)), (40, (13, 5)), (24, (23, 7))])
+def test_submatrix_matches_oracle(gb, n_mol, basis):
+    h = synth.build_hamiltonian(synth.small(n_mol, basis=basis, seed=6000 + n_mol))
+    Ho = bsr.Mat.of(h.H)
+    o = submatrix.submatrix_density(Ho, 0.0)
+    g = gb.submatrix_sign(gb.Matrix.of(h.H), 0.0, 1e-12)
+    assert g.converged
+    P = _mat(g.P)
+    assert np.array_equal(P.rp, o.rp) and np.array_equal(P.col, o.col)
+    assert np.linalg.norm(P.data - o.data) / np.linalg.norm(o.data) < 1e-10
+    assert g.report.n_products == Ho.nblk                      # one submatrix per block column
+    assert g.report.e_band == pytest.approx(bsr.trace_product(o, Ho), abs=1e-9 * h.n_atoms)
+
+
+def test_complete_neighbourhoods_give_the_exact_projector(gb):
+    h = synth.build_hamiltonian(synth.small(4, seed=77))
+    Hd = bsr.to_dense(bsr.Mat.of(h.H))
+    w, Q = np.linalg.eigh(Hd)
+    g = gb.submatrix_sign(gb.Matrix.of(h.H), 0.0, 1e-13)
+    assert np.linalg.norm(bsr.to_dense(_mat(g.P)) - Q[:, w < 0] @ Q[:, w < 0].T) < 1e-11
+
+
+def test_submatrix_fp32_tf32(gb):
+    h = synth.build_hamiltonian(synth.small(48, basis=(4, 1), seed=6100))
+    H = gb.Matrix.of(h.H)
+    f = gb.submatrix_sign(H, 0.0, 1e-12)
+    m = gb.submatrix_sign(H, 0.0, 1e-5, prec=gb.DBCSR_MIXED)
+    assert m.converged and m.report.fp64_from > 1             # some steps on the TF32 tensor cores
+    # FP32 floor: elements of X to about 1e-5 on these ~300-dimensional submatrices
+    assert abs(m.report.e_band - f.report.e_band) / h.n_atoms < 1e-5
+    assert m.report.trace_p == pytest.approx(h.n_occ, abs=1e-3)
+
+
+def test_submatrix_arguments_are_checked(gb):
+    h = synth.build_hamiltonian(synth.small(4, seed=1))
+    H = gb.Matrix.of(h.H)
+    with pytest.raises(gb.DbcsrError) as e:
+        gb.submatrix_sign(H, 0.0, 1e-9, P=H)
+    assert e.value.status == gb._ffi.DBCSR_EINVAL
+    with pytest.raises(gb.DbcsrError) as e:
+        gb.submatrix_sign(H, 0.0, 0.0)
+    assert e.value.status == gb._ffi.DBCSR_EINVAL
