@@ -554,9 +554,10 @@ dbcsr_status dbcsr_tune_predicted(int32_t prec, const float* params, const int32
  * products into stacks (section "Local multiplication") applied across systems.
  * Per system: X_0 = (H[s] - mu[s] 1) / alpha_s with its own Gershgorin bound,
  * its own residual ||X2_s - 1||_F / N_s, convergence and stall tests as in
- * dbcsr_sign_iterate.  Systems that converge early keep iterating at their fixed
- * point until all are done.  With DBCSR_MIXED the batch leaves the BF16 tier
- * once any system's residual is below switch_tol.
+ * dbcsr_sign_iterate, and the step of opts->order (2 to 7).  A system that
+ * converges or stalls writes its P_out and leaves the batch (the matrices are
+ * compacted to the running systems).  With DBCSR_MIXED the batch leaves the BF16
+ * tier once any system's residual is below switch_tol.
  *   H[nsys], mu[nsys] (host arrays); P_out[nsys]: created by the caller with the
  *   block sizes of H[s], receive (1 - X_s) / 2; reps[nsys] (may be NULL):
  *   per-system iterations, residuals, alpha, Tr(P), E_band; flops, products and
