@@ -34,3 +34,15 @@ def test_clock_samples():
     got = bench.parse_clock_samples(lines)
     assert got == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
     assert bench.parse_clock_samples([]) is None
+
+
+def test_products_per_iteration_match_the_oracle():
+    # the orders workload reports k (it - 1) + 1 products for a run that ended on X X
+    import bench
+    import synth
+    from oracle import bsr, sign
+    H = bsr.Mat.of(synth.build_hamiltonian(synth.small(6, seed=12)).H)
+    for order, k in bench.PRODUCTS_PER_ITERATION.items():
+        r = sign.sign_iterate(H, 0.0, 1e-7, 1e-9, order=order)
+        assert r.converged or r.stalled
+        assert r.multiplies == k * (r.iterations - 1) + 1, order
