@@ -310,3 +310,49 @@ def density_matrix_nonorth(K: bsr.Mat, S: bsr.Mat, mu: float, eps: float, tol: f
     P = w(1.0, w(1.0, Zs, r.P), Zs)
     return NonorthResult(P=P, sign=r, sqrt=sq, trace_ps=bsr.trace_product(P, S), e_band=bsr.trace_product(P, K),
                          flops=sq.flops + w.flops + r.flops)
+
+
+# ------------------------------------------------------------------ Hotelling inverse
+@dataclasses.dataclass
+class InverseResult:
+    Ainv: bsr.Mat
+    iterations: int
+    residuals: list            # ||A X - 1||_F / N per step
+    converged: bool
+    stalled: bool
+    scale: float               # X_0 = 1 / g
+    flops: int
+    multiplies: int
+
+
+def hotelling_inverse(A: bsr.Mat, eps: float, tol: float, max_iter: int = 100,
+                      stall_ratio: float = 0.5) -> InverseResult:
+    """A^-1 of a symmetric positive definite A by Hotelling's iteration (section
+    "Preconditioners": X <- X (2 1 - A X), with aggressive filtering of the iterates).
+
+    Readings: X_0 = 1 / g with g = max_i sum_j |A_ij| (so the spectrum of A X_0 lies in
+    (0, 1] and the residual 1 - A X contracts); each step forms T = filter(A X), tests
+    r = ||T - 1||_F / N, stops when r < tol, and otherwise sets X <- filter(2 X - X T).
+    Since 1 - A X (2 - A X) = (1 - A X)^2, the residual squares at every unfiltered step.
+    The stall test is the sign iteration's."""
+    n = A.n
+    g = gershgorin(A, 0.0)
+    X = bsr.add_identity(identity_like(A), 1.0 / g, 0.0)
+    w = _Work(eps)
+    res = []
+    converged = stalled = False
+    it = 0
+    while it < max_iter:
+        T, inf = w(1.0, A, X, info=True)
+        it += 1
+        r = float(np.sqrt(inf.dev2)) / n
+        res.append(r)
+        if r < tol:
+            converged = True
+            break
+        if len(res) >= 3 and res[-2] < stall_ratio * res[-3] and r > stall_ratio * res[-2]:
+            stalled = True
+            break
+        X = w(-1.0, X, T, 2.0, X)                                # 2 X - X T
+    return InverseResult(Ainv=X, iterations=it, residuals=res, converged=converged, stalled=stalled, scale=g,
+                         flops=w.flops, multiplies=w.multiplies)

@@ -125,3 +125,23 @@ def test_filtered_density_matrix_energy(system, order):
     assert r.sign.converged or r.sign.stalled
     assert abs(r.e_band - e[e < 0].sum()) / h.n_atoms < 1e-6
     assert r.trace_ps == pytest.approx(h.n_occ, abs=1e-5)
+
+
+def test_hotelling_inverse(system):
+    _, _, S = system
+    Sd = bsr.to_dense(S)
+    n = Sd.shape[0]
+    r = sign.hotelling_inverse(S, eps=0.0, tol=1e-13)
+    assert r.converged
+    assert np.linalg.norm(bsr.to_dense(r.Ainv) - np.linalg.inv(Sd)) / np.linalg.norm(np.linalg.inv(Sd)) < 1e-12
+    # the residual squares exactly: 1 - S X_1 = (1 - S X_0)^2 with X_0 = 1 / g
+    one = sign.hotelling_inverse(S, eps=0.0, tol=1e-300, max_iter=2)
+    R0 = np.eye(n) - Sd / one.scale
+    assert one.residuals[0] == pytest.approx(np.linalg.norm(R0) / n, rel=1e-12)
+    assert one.residuals[1] == pytest.approx(np.linalg.norm(R0 @ R0) / n, rel=1e-10)
+    # two products per step, the last step forms S X only
+    assert r.multiplies == 2 * r.iterations - 1
+    # and S^-1 = (S^-1/2)^2
+    q = sign.inverse_sqrt(S, eps=0.0, tol=1e-13)
+    Z = bsr.to_dense(q.Sinvsqrt)
+    assert np.linalg.norm(Z @ Z - bsr.to_dense(r.Ainv)) / np.linalg.norm(Z @ Z) < 1e-11
