@@ -356,6 +356,20 @@ dbcsr_status dbcsr_inverse_sqrt(dbcsr_matrix S, const dbcsr_sign_opts* opts, dbc
                                 dbcsr_matrix S_sqrt, dbcsr_sign_report* rep);
 
 /*
+ * A^-1 of a symmetric positive definite A by Hotelling's iteration (section
+ * "Preconditioners": X <- X (2 1 - A X), the iterates filtered):
+ *   X_0 = 1 / g, g = dbcsr_gershgorin(A, 0);
+ *   repeat: T = filter(A X); r = ||T - 1||_F / N; stop if r < tol; X <- filter(2 X - X T).
+ * The unfiltered residual squares at every step, (1 - A X') = (1 - A X)^2.  Products are
+ * mirrored (X is a polynomial in A) unless DBCSR_SIGN_FULL_PRODUCTS.  opts: eps_filter,
+ * tol, max_iter, stall_ratio, verbose, flags; prec must be DBCSR_FP64.  A_inv is replaced
+ * and must differ from A.  rep (may be NULL): iterations, residuals, alpha = g, work.
+ * Returns DBCSR_ENOTCONV when max_iter or the stall test ended the iteration.
+ */
+dbcsr_status dbcsr_inverse_hotelling(dbcsr_matrix A, const dbcsr_sign_opts* opts, dbcsr_matrix A_inv,
+                                     dbcsr_sign_report* rep);
+
+/*
  * Density matrix in a non-orthogonal basis (section "Sign-Method"):
  *   P = (1 - sign(S^-1 K - mu 1)) S^-1 / 2,
  * evaluated through the similarity sign(S^-1 K - mu 1) = S^(-1/2) sign(K' - mu 1) S^(1/2)

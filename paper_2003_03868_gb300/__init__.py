@@ -311,6 +311,20 @@ def inverse_sqrt(S: Matrix, eps_filter: float, tol: float, max_iter: int = 100, 
     return SqrtResult(Sinvsqrt=Zi, Ssqrt=Ys, report=rep, status=st)
 
 
+def inverse_hotelling(A: Matrix, eps_filter: float, tol: float, max_iter: int = 100, full_products: bool = False,
+                      verbose: bool = False, raise_on_notconv: bool = False) -> SignResult:
+    """A^-1 by Hotelling's iteration X <- X (2 - A X) (dbcsr_inverse_hotelling); the result is
+    in .P."""
+    Ai = Matrix(A.blk_size, A.stream)
+    o = SignOpts(float(eps_filter), float(tol), int(max_iter), DBCSR_FP64, 0.0, 0.5, 1 if verbose else 0,
+                 _sign_flags(full_products, DBCSR_BF16X3, False), 0, 0)
+    rep = SignReport()
+    st = lib().dbcsr_inverse_hotelling(A.handle, C.byref(o), Ai.handle, C.byref(rep))
+    if st != _ffi.DBCSR_OK and (st != _ffi.DBCSR_ENOTCONV or raise_on_notconv):
+        _check(st, "inverse_hotelling")
+    return SignResult(P=Ai, report=rep, status=st)
+
+
 @dataclasses.dataclass
 class NonorthResult:
     P: Matrix

@@ -92,6 +92,7 @@ SIGNATURES = [
     ("dbcsr_trace_product_noalloc", C.c_int, [P, P, P]),
     ("dbcsr_gershgorin", C.c_int, [P, C.c_double, C.POINTER(C.c_double)]),
     ("dbcsr_sign_iterate", C.c_int, [P, C.c_double, C.POINTER(SignOpts), P, C.POINTER(SignReport)]),
+    ("dbcsr_inverse_hotelling", C.c_int, [P, C.POINTER(SignOpts), P, C.POINTER(SignReport)]),
     ("dbcsr_inverse_sqrt", C.c_int, [P, C.POINTER(SignOpts), P, P, C.POINTER(SignReport)]),
     ("dbcsr_submatrix_sign", C.c_int, [P, C.c_double, C.POINTER(SignOpts), P, C.POINTER(SignReport)]),
     ("dbcsr_purify", C.c_int, [P, C.c_double, C.c_int32, C.POINTER(SignOpts), P, C.POINTER(SignReport)]),

@@ -238,6 +238,8 @@ dbcsr_status sign_mu_search(dbcsr_matrix_* H, double n_occ, double mu_lo, double
 // S^(-1/2) (into Sinv) and, when Ssqrt is given, S^(1/2) by the sign iteration on [[0, S], [1, 0]].
 dbcsr_status inverse_sqrt(dbcsr_matrix_* S, const dbcsr_sign_opts* opts, dbcsr_matrix_* Sinv, dbcsr_matrix_* Ssqrt,
                           dbcsr_sign_report* rep);
+dbcsr_status inverse_hotelling(dbcsr_matrix_* A, const dbcsr_sign_opts* opts, dbcsr_matrix_* Ainv,
+                               dbcsr_sign_report* rep);
 dbcsr_status sign_iterate_nonorth(dbcsr_matrix_* K, dbcsr_matrix_* S, double mu, const dbcsr_sign_opts* opts,
                                   dbcsr_matrix_* P, dbcsr_sign_report* rep, dbcsr_sign_report* rep_sqrt);
 

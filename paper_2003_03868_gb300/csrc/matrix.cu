@@ -679,6 +679,15 @@ dbcsr_status dbcsr_inverse_sqrt(dbcsr_matrix S, const dbcsr_sign_opts* opts, dbc
     return st;
 }
 
+dbcsr_status dbcsr_inverse_hotelling(dbcsr_matrix A, const dbcsr_sign_opts* opts, dbcsr_matrix A_inv,
+                                     dbcsr_sign_report* rep) {
+    dbcsr_status st = DBCSR_OK;
+    dbcsr_status g = guarded([&] { st = dbg::inverse_hotelling(A, opts, A_inv, rep); });
+    if (g != DBCSR_OK) return g;
+    if (st != DBCSR_OK) g_last_error = "Hotelling iteration did not reach the tolerance";
+    return st;
+}
+
 dbcsr_status dbcsr_sign_iterate_nonorth(dbcsr_matrix K, dbcsr_matrix S, double mu, const dbcsr_sign_opts* opts,
                                         dbcsr_matrix P_out, dbcsr_sign_report* rep, dbcsr_sign_report* rep_sqrt) {
     dbcsr_status st = DBCSR_OK;

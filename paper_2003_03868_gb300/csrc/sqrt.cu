@@ -14,6 +14,9 @@
 //     ladder the low tier's errors would stay in the result (Tr(P S) off by about 1e-3 on
 //     1,024 waters); at the switch to FP64, Y <- filter(A Z) restores the relation and the
 //     FP64 steps converge to the root of the true A.
+//   * A^-1 of a positive definite A by Hotelling's iteration (section "Preconditioners"):
+//     X_0 = 1 / g, repeat T = filter(A X), stop when ||T - 1||_F / N < tol,
+//     X <- filter(2 X - X T); the residual 1 - A X squares at every step.
 //   * P = (1 - sign(S^-1 K - mu 1)) S^-1 / 2, evaluated through the similarity
 //     sign(S^-1 K - mu 1) = S^(-1/2) sign(K' - mu 1) S^(1/2), K' = S^(-1/2) K S^(-1/2):
 //     P = S^(-1/2) P' S^(-1/2) with P' the density matrix of K'.  Every product is filtered.
@@ -218,6 +221,74 @@ dbcsr_status inverse_sqrt(dbcsr_matrix_* S, const dbcsr_sign_opts* opts, dbcsr_m
     r.stalled = stalled ? 1 : 0;
     r.residual = res;
     r.nnzb_x = Z->nnzb;
+    r.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (rep) *rep = r;
+    return converged ? DBCSR_OK : DBCSR_ENOTCONV;
+}
+
+dbcsr_status inverse_hotelling(dbcsr_matrix_* A, const dbcsr_sign_opts* opts, dbcsr_matrix_* Ainv,
+                               dbcsr_sign_report* rep) {
+    check_finalized(A);
+    if (!Ainv) fail(DBCSR_EINVAL, "inverse_hotelling: null A_inv");
+    if (Ainv->h_bs != A->h_bs) fail(DBCSR_EINVAL, "inverse_hotelling: A_inv block sizes differ from A");
+    if (Ainv == A) fail(DBCSR_EINVAL, "inverse_hotelling: A_inv must differ from A");
+    check_unplanned(Ainv, "inverse_hotelling");
+    dbcsr_sign_opts o = checked_opts(opts, "inverse_hotelling");
+    if (o.prec != DBCSR_FP64) fail(DBCSR_EINVAL, "inverse_hotelling: prec must be FP64");
+    const int sym = (o.flags & DBCSR_SIGN_FULL_PRODUCTS) ? kSymNone : kSymMirror;   // X is a polynomial in A
+    const auto t0 = std::chrono::steady_clock::now();
+    cudaStream_t s = A->stream;
+    const double N = (double)A->n;
+    const double g = gershgorin(A, 0.0);
+    if (!(g > 0) || !std::isfinite(g)) fail(DBCSR_EINVAL, "inverse_hotelling: Gershgorin bound is zero or not finite");
+    auto X = make_identity(A);
+    scale_shift(X.get(), 1.0 / g, 0.0);                       // X_0 = 1 / g
+    auto T = make_like(A, s);
+    dbcsr_sign_report r{};
+    r.alpha = g;
+    int it = 0;
+    bool converged = false, stalled = false;
+    double res = 0.0;
+    while (it < o.max_iter) {
+        dbcsr_mult_stats st{};
+        multiply(1.0, A, X.get(), 0.0, T.get(), o.eps_filter, DBCSR_FP64, &st, true, sym);
+        res = std::sqrt(st.dev2_filtered) / N;
+        r.flops += st.flops;
+        r.n_products += st.n_products;
+        r.ms_multiply += st.ms_numeric;
+        r.ms_symbolic += st.ms_symbolic;
+        r.ms_filter += st.ms_filter;
+        if (it < DBCSR_MAX_HISTORY) r.residual_history[it] = res;
+        ++it;
+        if (!std::isfinite(res)) fail(DBCSR_ENAN, "inverse_hotelling: residual is not finite");
+        if (o.verbose)
+            std::fprintf(stderr, "[inverse] it %3d r %.3e nnzb(X) %lld\n", it, res, (long long)X->nnzb);
+        if (res < o.tol) {
+            converged = true;
+            break;
+        }
+        if (it >= 3 && it - 1 < DBCSR_MAX_HISTORY && r.residual_history[it - 2] < o.stall_ratio * r.residual_history[it - 3] &&
+            res > o.stall_ratio * r.residual_history[it - 2]) {
+            stalled = true;
+            break;
+        }
+        multiply(-1.0, X.get(), T.get(), 2.0, X.get(), o.eps_filter, DBCSR_FP64, &st, false, sym);   // 2 X - X A X
+        r.flops += st.flops;
+        r.n_products += st.n_products;
+        r.ms_multiply += st.ms_numeric;
+        r.ms_symbolic += st.ms_symbolic;
+        r.ms_filter += st.ms_filter;
+        if (it - 1 < DBCSR_MAX_HISTORY) r.nnzb_history[it - 1] = X->nnzb;
+    }
+    copy_matrix(Ainv, X.get());
+    DBG_CK(cudaStreamSynchronize(s));
+    DBG_CK(cudaStreamSynchronize(Ainv->stream));
+    r.iterations = it;
+    r.fp64_from = 1;
+    r.converged = converged ? 1 : 0;
+    r.stalled = stalled ? 1 : 0;
+    r.residual = res;
+    r.nnzb_x = X->nnzb;
     r.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     if (rep) *rep = r;
     return converged ? DBCSR_OK : DBCSR_ENOTCONV;

@@ -144,3 +144,20 @@ def test_nonorth_arguments_are_checked(gb):
     with pytest.raises(gb.DbcsrError) as e:
         gb.inverse_sqrt(S, 0.0, 1e-9, order=9)
     assert e.value.status == gb._ffi.DBCSR_EINVAL
+
+
+@pytest.mark.parametrize("n_mol,basis,eps,tol", CASES)
+def test_hotelling_inverse_matches_oracle(gb, n_mol, basis, eps, tol):
+    h, s = _system(n_mol, basis, 7070 + n_mol)
+    So = bsr.Mat.of(s)
+    o = sign.hotelling_inverse(So, eps, tol)
+    S = gb.Matrix.of(s)
+    f = gb.inverse_hotelling(S, eps, tol, full_products=True)
+    assert bool(f.report.converged) == o.converged and f.report.iterations == o.iterations
+    np.testing.assert_allclose(f.residuals, o.residuals, rtol=1e-6, atol=1e-12)
+    got = _mat(f.P)
+    assert np.linalg.norm(bsr.to_dense(got) - bsr.to_dense(o.Ainv)) / np.linalg.norm(o.Ainv.data) < 1e-9
+    g = gb.inverse_hotelling(S, eps, tol)                      # mirrored products
+    X, Sd = bsr.to_dense(_mat(g.P)), bsr.to_dense(So)
+    assert np.array_equal(X, X.T)
+    assert np.linalg.norm(Sd @ X - np.eye(Sd.shape[0])) / np.sqrt(Sd.shape[0]) < max(1e-11, 10 * eps)
