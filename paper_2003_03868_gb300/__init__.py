@@ -12,6 +12,7 @@ from __future__ import annotations
 
 import ctypes as C
 import dataclasses
+import os
 
 import numpy as np
 
@@ -86,6 +87,22 @@ class Matrix:
     def of(cls, bm, stream: int | None = None) -> "Matrix":
         """From any object with blk_size/row_ptr/col/data (the input generator's format)."""
         return cls.from_blocks(bm.blk_size, bm.row_ptr, bm.col, bm.data, stream)
+
+    @classmethod
+    def load(cls, path: str, stream: int | None = None) -> "Matrix":
+        """A finalized matrix read from a file written by save (dbcsr_load)."""
+        nblk, _, _ = file_info(path)
+        m = cls.__new__(cls)
+        m.blk_size = np.fromfile(path, dtype=np.int32, count=nblk, offset=32)
+        m.stream = current_stream() if stream is None else int(stream)
+        h = C.c_void_p()
+        _check(lib().dbcsr_load(C.byref(h), os.fsencode(path), C.c_void_p(m.stream)), "load")
+        m.handle = h
+        return m
+
+    def save(self, path: str):
+        """Writes the matrix to a file (dbcsr_save; layout in dbcsr_gb.h)."""
+        _check(lib().dbcsr_save(self.handle, os.fsencode(path)), "save")
 
     def put_block(self, row: int, col: int, block):
         b = np.ascontiguousarray(block, dtype=np.float64)
@@ -193,6 +210,13 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def file_info(path: str):
+    """(nblk, nnzb, nel) of a matrix file, read and checked on the host (dbcsr_file_info)."""
+    nb, nz, ne = C.c_int32(), C.c_int64(), C.c_int64()
+    _check(lib().dbcsr_file_info(os.fsencode(path), C.byref(nb), C.byref(nz), C.byref(ne)), "file_info")
+    return nb.value, nz.value, ne.value
 
 
 def filter(M: Matrix, eps: float):  # noqa: A001 - the C ABI's name

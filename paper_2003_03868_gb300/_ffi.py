@@ -86,6 +86,9 @@ SIGNATURES = [
     ("dbcsr_scale_shift", C.c_int, [P, C.c_double, C.c_double]),
     ("dbcsr_multiply", C.c_int, [C.c_double, P, P, C.c_double, P, C.c_double, C.c_int32, C.POINTER(MultStats)]),
     ("dbcsr_add", C.c_int, [C.c_double, P, C.c_double, P]),
+    ("dbcsr_save", C.c_int, [P, C.c_char_p]),
+    ("dbcsr_load", C.c_int, [C.POINTER(P), C.c_char_p, P]),
+    ("dbcsr_file_info", C.c_int, [C.c_char_p, C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     ("dbcsr_filter", C.c_int, [P, C.c_double]),
     ("dbcsr_trace", C.c_int, [P, C.POINTER(C.c_double)]),
     ("dbcsr_trace_product", C.c_int, [P, P, C.POINTER(C.c_double)]),

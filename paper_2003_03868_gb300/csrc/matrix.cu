@@ -9,6 +9,9 @@
 #include <mutex>
 #include <numeric>
 
+#include <cstdio>
+#include <cstring>
+
 #include "common.cuh"
 
 namespace dbg {
@@ -390,6 +393,80 @@ dbcsr_status guarded(F&& f) {
 }
 }  // namespace
 
+namespace {
+// The matrix file: 8-byte magic "DBCSRGB1", int32 nblk, int32 0, int64 nnzb, int64 nel,
+// then int32 blk_size[nblk], int64 row_ptr[nblk + 1], int32 col[nnzb], double data[nel],
+// each in the host's byte order (little-endian on the supported hosts).
+constexpr char kFileMagic[8] = {'D', 'B', 'C', 'S', 'R', 'G', 'B', '1'};
+
+struct MatrixFile {
+    int32_t nblk = 0;
+    int64_t nnzb = 0, nel = 0;
+    std::vector<int32_t> bs, col;
+    std::vector<int64_t> rp;
+    std::vector<double> data;
+};
+
+// Reads and checks a whole matrix file on the host (no device work).
+MatrixFile read_matrix_file(const char* path) {
+    using dbg::fail;
+    if (!path) fail(DBCSR_EINVAL, "load: null path");
+    std::FILE* f = std::fopen(path, "rb");
+    if (!f) fail(DBCSR_EINVAL, std::string("load: cannot open ") + path);
+    struct Closer {
+        std::FILE* f;
+        ~Closer() { std::fclose(f); }
+    } closer{f};
+    auto read = [&](void* dst, size_t size, size_t count) {
+        if (count && std::fread(dst, size, count, f) != count) fail(DBCSR_EINVAL, "load: file too short");
+    };
+    if (std::fseek(f, 0, SEEK_END) != 0) fail(DBCSR_EINVAL, "load: cannot size the file");
+    const int64_t fsize = (int64_t)std::ftell(f);
+    if (fsize < 0 || std::fseek(f, 0, SEEK_SET) != 0) fail(DBCSR_EINVAL, "load: cannot size the file");
+    char magic[8];
+    int32_t nblk = 0, zero = 0;
+    int64_t nnzb = 0, nel = 0;
+    read(magic, 1, 8);
+    if (std::memcmp(magic, kFileMagic, 8) != 0) fail(DBCSR_EINVAL, "load: not a matrix file");
+    read(&nblk, sizeof nblk, 1);
+    read(&zero, sizeof zero, 1);
+    read(&nnzb, sizeof nnzb, 1);
+    read(&nel, sizeof nel, 1);
+    // sizes bounded by the file before any product is formed, then the exact length
+    if (nblk < 1 || zero != 0 || nnzb < 0 || nel < 0 || nblk > fsize / 12 || nnzb > fsize / 4 || nel > fsize / 8)
+        fail(DBCSR_EINVAL, "load: bad header");
+    const int64_t expect = 32 + 4 * (int64_t)nblk + 8 * ((int64_t)nblk + 1) + 4 * nnzb + 8 * nel;
+    if (expect != fsize) fail(DBCSR_EINVAL, "load: file length does not match the header");
+    MatrixFile m;
+    m.nblk = nblk;
+    m.nnzb = nnzb;
+    m.nel = nel;
+    m.bs.resize(nblk);
+    m.rp.resize(nblk + 1);
+    m.col.resize(nnzb);
+    m.data.resize(nel);
+    read(m.bs.data(), sizeof(int32_t), nblk);
+    read(m.rp.data(), sizeof(int64_t), nblk + 1);
+    read(m.col.data(), sizeof(int32_t), nnzb);
+    read(m.data.data(), sizeof(double), nel);
+    for (int32_t b : m.bs)
+        if (b < 1 || b > dbg::kMaxBlock) fail(DBCSR_EINVAL, "load: block edge outside [1, 32]");
+    if (m.rp[0] != 0 || m.rp[nblk] != nnzb) fail(DBCSR_EINVAL, "load: bad row pointers");
+    int64_t area = 0;
+    for (int32_t i = 0; i < nblk; ++i) {
+        if (m.rp[i + 1] < m.rp[i]) fail(DBCSR_EINVAL, "load: bad row pointers");
+        for (int64_t q = m.rp[i]; q < m.rp[i + 1]; ++q) {
+            const int32_t c = m.col[q];
+            if (c < 0 || c >= nblk || (q > m.rp[i] && c <= m.col[q - 1]))
+                fail(DBCSR_EINVAL, "load: columns out of range or not ascending");
+            area += (int64_t)m.bs[i] * m.bs[c];
+        }
+    }
+    if (area != nel) fail(DBCSR_EINVAL, "load: data size does not match the blocks");
+    return m;
+}
+}  // namespace
+
 namespace dbg {
 [[noreturn]] void fail(dbcsr_status code, const std::string& msg) { throw Error(code, msg); }
 void set_last_error(const std::string& msg) { g_last_error = msg; }
@@ -722,6 +799,64 @@ dbcsr_status dbcsr_submatrix_sign(dbcsr_matrix H, double mu, const dbcsr_sign_op
     if (g != DBCSR_OK) return g;
     if (st != DBCSR_OK) g_last_error = "a submatrix did not reach the tolerance";
     return st;
+}
+
+dbcsr_status dbcsr_save(dbcsr_matrix m, const char* path) {
+    return guarded([&] {
+        dbg::check_finalized(m);
+        if (!path) fail(DBCSR_EINVAL, "save: null path");
+        std::vector<int64_t> rp(m->nblk + 1);
+        std::vector<int32_t> col(std::max<int64_t>(m->nnzb, 1));
+        std::vector<double> data(std::max<int64_t>(m->nel, 1));
+        cudaStream_t s = m->stream;
+        DBG_CK(cudaMemcpyAsync(rp.data(), m->rp.p, sizeof(int64_t) * (m->nblk + 1), cudaMemcpyDeviceToHost, s));
+        if (m->nnzb) DBG_CK(cudaMemcpyAsync(col.data(), m->col.p, sizeof(int32_t) * m->nnzb, cudaMemcpyDeviceToHost, s));
+        if (m->nel) DBG_CK(cudaMemcpyAsync(data.data(), m->data.p, sizeof(double) * m->nel, cudaMemcpyDeviceToHost, s));
+        DBG_CK(cudaStreamSynchronize(s));
+        std::FILE* f = std::fopen(path, "wb");
+        if (!f) fail(DBCSR_EINVAL, std::string("save: cannot open ") + path);
+        const int32_t zero = 0;
+        bool ok = std::fwrite(kFileMagic, 1, 8, f) == 8 && std::fwrite(&m->nblk, sizeof(int32_t), 1, f) == 1 &&
+                  std::fwrite(&zero, sizeof(int32_t), 1, f) == 1 && std::fwrite(&m->nnzb, sizeof(int64_t), 1, f) == 1 &&
+                  std::fwrite(&m->nel, sizeof(int64_t), 1, f) == 1 &&
+                  std::fwrite(m->h_bs.data(), sizeof(int32_t), m->nblk, f) == (size_t)m->nblk &&
+                  std::fwrite(rp.data(), sizeof(int64_t), m->nblk + 1, f) == (size_t)(m->nblk + 1) &&
+                  (m->nnzb == 0 || std::fwrite(col.data(), sizeof(int32_t), m->nnzb, f) == (size_t)m->nnzb) &&
+                  (m->nel == 0 || std::fwrite(data.data(), sizeof(double), m->nel, f) == (size_t)m->nel);
+        ok = (std::fclose(f) == 0) && ok;
+        if (!ok) fail(DBCSR_EINVAL, std::string("save: write failed on ") + path);
+    });
+}
+
+dbcsr_status dbcsr_file_info(const char* path, int32_t* nblk, int64_t* nnzb, int64_t* nel) {
+    return guarded([&] {
+        const MatrixFile mf = read_matrix_file(path);
+        if (nblk) *nblk = mf.nblk;
+        if (nnzb) *nnzb = mf.nnzb;
+        if (nel) *nel = mf.nel;
+    });
+}
+
+dbcsr_status dbcsr_load(dbcsr_matrix* out, const char* path, void* stream) {
+    return guarded([&] {
+        if (!out) fail(DBCSR_EINVAL, "load: null output handle");
+        const MatrixFile mf = read_matrix_file(path);
+        dbcsr_matrix m = nullptr;
+        dbcsr_status st = dbcsr_create(&m, mf.nblk, mf.bs.data(), stream);
+        if (st != DBCSR_OK) fail(st, g_last_error);
+        try {
+            std::vector<int32_t> rows(std::max<int64_t>(mf.nnzb, 1));
+            for (int32_t i = 0; i < mf.nblk; ++i)
+                for (int64_t q = mf.rp[i]; q < mf.rp[i + 1]; ++q) rows[q] = i;
+            stage(m, mf.nnzb, rows.data(), mf.col.data(), mf.data.data(), 0);
+            st = dbcsr_finalize(m);
+            if (st != DBCSR_OK) fail(st, g_last_error);
+        } catch (...) {
+            dbcsr_destroy(m);
+            throw;
+        }
+        *out = m;
+    });
 }
 
 }  // extern "C"

@@ -1,0 +1,95 @@
+"""The matrix file format, checked on the host without a GPU (dbcsr_file_info), and the
+save / load round trip on the GPU."""
+import numpy as np
+import pytest
+
+import synth
+
+
+def _write(path, bs, rp, col, data, magic=b"DBCSRGB1", zero=0, extra=b""):
+    with open(path, "wb") as f:
+        f.write(magic)
+        f.write(np.int32(len(bs)).tobytes())
+        f.write(np.int32(zero).tobytes())
+        f.write(np.int64(len(col)).tobytes())
+        f.write(np.int64(len(data)).tobytes())
+        f.write(np.asarray(bs, np.int32).tobytes())
+        f.write(np.asarray(rp, np.int64).tobytes())
+        f.write(np.asarray(col, np.int32).tobytes())
+        f.write(np.asarray(data, np.float64).tobytes())
+        f.write(extra)
+
+
+@pytest.fixture(scope="module")
+def gb():
+    import paper_2003_03868_gb300 as m
+    m.lib()
+    return m
+
+
+@pytest.fixture
+def good(tmp_path):
+    a = synth.random_block_matrix([13, 5, 5, 23, 7, 1] * 3, 0.4, 5, empty_rows=(4,))
+    p = tmp_path / "m.bin"
+    _write(p, a.blk_size, a.row_ptr, a.col, a.data)
+    return a, p
+
+
+def test_file_info_reads_a_valid_file(gb, good):
+    a, p = good
+    assert gb.file_info(str(p)) == (18, a.col.shape[0], a.data.shape[0])
+
+
+@pytest.mark.parametrize("breakage", ["magic", "short", "trailing", "reserved", "col_order", "col_range",
+                                      "row_ptr", "data_size", "block_edge"])
+def test_file_info_rejects_broken_files(gb, good, tmp_path, breakage):
+    a, _ = good
+    bs, rp, col, data = a.blk_size.copy(), a.row_ptr.copy(), a.col.copy(), a.data.copy()
+    kw = {}
+    if breakage == "magic":
+        kw["magic"] = b"DBCSRGB2"
+    elif breakage == "trailing":
+        kw["extra"] = b"\0"
+    elif breakage == "reserved":
+        kw["zero"] = 1
+    elif breakage == "col_order":
+        i = int(np.argmax(np.diff(rp) >= 2))
+        col[rp[i]], col[rp[i] + 1] = col[rp[i] + 1], col[rp[i]]
+    elif breakage == "col_range":
+        col[0] = len(bs)
+    elif breakage == "row_ptr":
+        rp[-1] -= 1
+    elif breakage == "data_size":
+        data = data[:-1]
+    elif breakage == "block_edge":
+        bs[0] = 33
+    p = tmp_path / "bad.bin"
+    _write(p, bs, rp, col, data, **kw)
+    if breakage == "short":
+        raw = open(p, "rb").read()
+        open(p, "wb").write(raw[:-5])
+    with pytest.raises(gb.DbcsrError) as e:
+        gb.file_info(str(p))
+    assert e.value.status == gb._ffi.DBCSR_EINVAL
+    with pytest.raises(gb.DbcsrError):
+        gb.file_info(str(tmp_path / "missing.bin"))
+
+
+@pytest.mark.gpu
+def test_save_load_round_trip(gb, good, tmp_path):
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    a, p = good
+    M = gb.Matrix.of(a)
+    out = tmp_path / "saved.bin"
+    M.save(str(out))
+    assert open(out, "rb").read() == open(p, "rb").read()     # the same bytes as the layout above
+    L = gb.Matrix.load(str(out))
+    assert np.array_equal(L.blk_size, a.blk_size)
+    for x, y in zip(L.export(), (a.row_ptr, a.col, a.data)):
+        assert np.array_equal(x, y)
+    E = gb.Matrix.of(synth.random_block_matrix([5] * 4, 0.0, 1, diag=False))   # no blocks
+    E.save(str(tmp_path / "empty.bin"))
+    assert gb.file_info(str(tmp_path / "empty.bin")) == (4, 0, 0)
+    assert gb.Matrix.load(str(tmp_path / "empty.bin")).nnzb == 0
