@@ -99,3 +99,51 @@ def test_swapped_square_roots_fail_the_generalized_eigenproblem_pin(system, monk
 
     monkeypatch.setattr(sign, "inverse_sqrt", swapped)
     assert _nonorth_error(h, K, S) > 1e-2
+
+
+class _FlippedTrace:
+    """bsr with Tr(X) reflected about n_occ, so that every trace comparison turns around."""
+
+    def __init__(self, n_occ):
+        from oracle import bsr as real
+        self._real, self._n = real, n_occ
+
+    def __getattr__(self, name):
+        return getattr(self._real, name)
+
+    def trace(self, M):
+        return 2 * self._n - self._real.trace(M)
+
+
+def _projector_error(h, H, method):
+    from oracle import purify
+    w, Q = np.linalg.eigh(bsr.to_dense(H))
+    Pe = Q[:, :h.n_occ] @ Q[:, :h.n_occ].T
+    r = purify.purify(H, h.n_occ, eps=0.0, tol=1e-13, method=method, max_iter=60)
+    return np.linalg.norm(bsr.to_dense(r.P) - Pe) / np.linalg.norm(Pe)
+
+
+def test_an_inverted_tc2_branch_fails_the_projector_pin(system, monkeypatch):
+    from oracle import purify
+    h, H, _ = system
+    assert _projector_error(h, H, "tc2") < 1e-10
+    monkeypatch.setattr(purify, "bsr", _FlippedTrace(h.n_occ))
+    assert _projector_error(h, H, "tc2") > 1e-2
+
+
+def test_a_reversed_bisection_fails_the_gap_pin(system, monkeypatch):
+    from oracle import purify
+    h, H, _ = system
+    Hs = bsr.add_identity(H, 1.0, 1.0)                      # the gap away from the interval's middle
+    w = np.linalg.eigvalsh(bsr.to_dense(Hs))
+    in_gap = lambda mu: w[h.n_occ - 1] < mu < w[h.n_occ]   # noqa: E731
+    assert in_gap(purify.mu_search(Hs, h.n_occ, 0.0, 1e-12).mu)
+    real = sign.sign_iterate
+
+    def reflected(*a, **k):
+        r = real(*a, **k)
+        r.trace_p = 2 * h.n_occ - r.trace_p
+        return r
+
+    monkeypatch.setattr(purify.sign, "sign_iterate", reflected)
+    assert not in_gap(purify.mu_search(Hs, h.n_occ, 0.0, 1e-12, max_eval=12).mu)
