@@ -168,7 +168,6 @@ struct Gemm<float> {
 
 struct ChunkResult {
     int iterations = 0, tf32_iterations = 0;
-    bool stalled = false;
     double r_max = 0.0, flops = 0.0;
 };
 
@@ -299,7 +298,6 @@ dbcsr_status submatrix_sign(dbcsr_matrix_* H, double mu, const dbcsr_sign_opts* 
     } guard{hb};
     DBG_CUBLAS(cublasSetStream(hb, s));
     int max_it = 0, max_tf32 = 0;
-    bool stalled = false;
     double r_max = 0.0, flops = 0.0;
     int64_t nsub = 0;
     for (auto& kv : by_size) {
@@ -326,7 +324,6 @@ dbcsr_status submatrix_sign(dbcsr_matrix_* H, double mu, const dbcsr_sign_opts* 
             max_it = std::max(max_it, cr.iterations);
             max_tf32 = std::max(max_tf32, cr.tf32_iterations);
             r_max = std::max(r_max, cr.r_max);
-            stalled = stalled || cr.stalled;
             flops += cr.flops;
             nsub += (int64_t)ck.sub_j.size();
         }
@@ -338,7 +335,7 @@ dbcsr_status submatrix_sign(dbcsr_matrix_* H, double mu, const dbcsr_sign_opts* 
     r.iterations = max_it;
     r.fp64_from = mixed ? max_tf32 + 1 : 1;
     r.converged = r_max < o.tol ? 1 : 0;
-    r.stalled = stalled ? 1 : 0;
+    r.stalled = 0;
     r.residual = r_max;
     r.flops = flops;
     r.n_products = nsub;
