@@ -208,10 +208,11 @@ dbcsr_status dbcsr_export(dbcsr_matrix m, int64_t* row_ptr, int32_t* col, double
  * the given CUDA stream, NULL = default) from such a file and finalizes it.  The file:
  * 8 bytes "DBCSRGB1", int32 nblk, int32 0, int64 nnzb, int64 nel, int32 blk_size[nblk],
  * int64 row_ptr[nblk + 1], int32 col[nnzb] (ascending per row), double data[nel] (blocks
- * row-major in CSR order), in the host's byte order.  dbcsr_file_info reads and checks a
+ * row-major in CSR order), in the host's byte order, then the uint32 CRC-32 (IEEE 802.3 /
+ * zlib) of all the bytes before it.  dbcsr_file_info reads and checks a
  * whole file on the host, without device work, and returns its sizes (each pointer may be
  * NULL).  Errors: EINVAL (null argument, unreadable or unwritable path, a file that is
- * not a valid matrix file: wrong magic, length, row pointers, columns or sizes),
+ * not a valid matrix file: wrong magic, length, checksum, row pointers, columns or sizes),
  * ESTATE (save of an unfinalized matrix), ENOMEM, ECUDA.
  */
 dbcsr_status dbcsr_save(dbcsr_matrix m, const char* path);

@@ -6,6 +6,7 @@
 // row of each block row[nnzb], element offsets off[nnzb+1], and the blocks
 // themselves row-major and packed in CSR order in data[nel] (FP64).
 #include <algorithm>
+#include <array>
 #include <mutex>
 #include <numeric>
 
@@ -396,8 +397,27 @@ dbcsr_status guarded(F&& f) {
 namespace {
 // The matrix file: 8-byte magic "DBCSRGB1", int32 nblk, int32 0, int64 nnzb, int64 nel,
 // then int32 blk_size[nblk], int64 row_ptr[nblk + 1], int32 col[nnzb], double data[nel],
-// each in the host's byte order (little-endian on the supported hosts).
+// each in the host's byte order (little-endian on the supported hosts), and last the
+// uint32 CRC-32 of all the bytes before it.
 constexpr char kFileMagic[8] = {'D', 'B', 'C', 'S', 'R', 'G', 'B', '1'};
+
+// CRC-32 as in IEEE 802.3 / zlib: reflected polynomial 0xEDB88320, register preset to all
+// ones and inverted at the end; crc = crc32_update(crc, bytes) continues a running value.
+uint32_t crc32_update(uint32_t crc, const void* buf, size_t len) {
+    static const auto table = [] {
+        std::array<uint32_t, 256> t{};
+        for (uint32_t i = 0; i < 256; ++i) {
+            uint32_t c = i;
+            for (int k = 0; k < 8; ++k) c = (c & 1u) ? 0xEDB88320u ^ (c >> 1) : c >> 1;
+            t[i] = c;
+        }
+        return t;
+    }();
+    const auto* p = static_cast<const unsigned char*>(buf);
+    crc = ~crc;
+    for (size_t i = 0; i < len; ++i) crc = table[(crc ^ p[i]) & 0xFFu] ^ (crc >> 8);
+    return ~crc;
+}
 
 struct MatrixFile {
     int32_t nblk = 0;
@@ -417,8 +437,10 @@ MatrixFile read_matrix_file(const char* path) {
         std::FILE* f;
         ~Closer() { std::fclose(f); }
     } closer{f};
+    uint32_t crc = 0;
     auto read = [&](void* dst, size_t size, size_t count) {
         if (count && std::fread(dst, size, count, f) != count) fail(DBCSR_EINVAL, "load: file too short");
+        crc = crc32_update(crc, dst, size * count);
     };
     if (std::fseek(f, 0, SEEK_END) != 0) fail(DBCSR_EINVAL, "load: cannot size the file");
     const int64_t fsize = (int64_t)std::ftell(f);
@@ -435,7 +457,7 @@ MatrixFile read_matrix_file(const char* path) {
     // sizes bounded by the file before any product is formed, then the exact length
     if (nblk < 1 || zero != 0 || nnzb < 0 || nel < 0 || nblk > fsize / 12 || nnzb > fsize / 4 || nel > fsize / 8)
         fail(DBCSR_EINVAL, "load: bad header");
-    const int64_t expect = 32 + 4 * (int64_t)nblk + 8 * ((int64_t)nblk + 1) + 4 * nnzb + 8 * nel;
+    const int64_t expect = 32 + 4 * (int64_t)nblk + 8 * ((int64_t)nblk + 1) + 4 * nnzb + 8 * nel + 4;
     if (expect != fsize) fail(DBCSR_EINVAL, "load: file length does not match the header");
     MatrixFile m;
     m.nblk = nblk;
@@ -449,6 +471,10 @@ MatrixFile read_matrix_file(const char* path) {
     read(m.rp.data(), sizeof(int64_t), nblk + 1);
     read(m.col.data(), sizeof(int32_t), nnzb);
     read(m.data.data(), sizeof(double), nel);
+    const uint32_t computed = crc;
+    uint32_t stored = 0;
+    read(&stored, sizeof stored, 1);
+    if (stored != computed) fail(DBCSR_EINVAL, "load: checksum mismatch");
     for (int32_t b : m.bs)
         if (b < 1 || b > dbg::kMaxBlock) fail(DBCSR_EINVAL, "load: block edge outside [1, 32]");
     if (m.rp[0] != 0 || m.rp[nblk] != nnzb) fail(DBCSR_EINVAL, "load: bad row pointers");
@@ -816,13 +842,17 @@ dbcsr_status dbcsr_save(dbcsr_matrix m, const char* path) {
         std::FILE* f = std::fopen(path, "wb");
         if (!f) fail(DBCSR_EINVAL, std::string("save: cannot open ") + path);
         const int32_t zero = 0;
-        bool ok = std::fwrite(kFileMagic, 1, 8, f) == 8 && std::fwrite(&m->nblk, sizeof(int32_t), 1, f) == 1 &&
-                  std::fwrite(&zero, sizeof(int32_t), 1, f) == 1 && std::fwrite(&m->nnzb, sizeof(int64_t), 1, f) == 1 &&
-                  std::fwrite(&m->nel, sizeof(int64_t), 1, f) == 1 &&
-                  std::fwrite(m->h_bs.data(), sizeof(int32_t), m->nblk, f) == (size_t)m->nblk &&
-                  std::fwrite(rp.data(), sizeof(int64_t), m->nblk + 1, f) == (size_t)(m->nblk + 1) &&
-                  (m->nnzb == 0 || std::fwrite(col.data(), sizeof(int32_t), m->nnzb, f) == (size_t)m->nnzb) &&
-                  (m->nel == 0 || std::fwrite(data.data(), sizeof(double), m->nel, f) == (size_t)m->nel);
+        uint32_t crc = 0;
+        auto put = [&](const void* src, size_t size, size_t count) {
+            crc = crc32_update(crc, src, size * count);
+            return count == 0 || std::fwrite(src, size, count, f) == count;
+        };
+        bool ok = put(kFileMagic, 1, 8) && put(&m->nblk, sizeof(int32_t), 1) && put(&zero, sizeof(int32_t), 1) &&
+                  put(&m->nnzb, sizeof(int64_t), 1) && put(&m->nel, sizeof(int64_t), 1) &&
+                  put(m->h_bs.data(), sizeof(int32_t), m->nblk) && put(rp.data(), sizeof(int64_t), m->nblk + 1) &&
+                  put(col.data(), sizeof(int32_t), m->nnzb) && put(data.data(), sizeof(double), m->nel);
+        const uint32_t final_crc = crc;
+        ok = ok && std::fwrite(&final_crc, sizeof final_crc, 1, f) == 1;
         ok = (std::fclose(f) == 0) && ok;
         if (!ok) fail(DBCSR_EINVAL, std::string("save: write failed on ") + path);
     });

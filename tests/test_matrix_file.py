@@ -1,23 +1,21 @@
 """The matrix file format, checked on the host without a GPU (dbcsr_file_info), and the
 save / load round trip on the GPU."""
+import zlib
+
 import numpy as np
 import pytest
 
 import synth
 
 
-def _write(path, bs, rp, col, data, magic=b"DBCSRGB1", zero=0, extra=b""):
+def _write(path, bs, rp, col, data, magic=b"DBCSRGB1", zero=0, extra=b"", crc_delta=0):
+    body = b"".join([magic, np.int32(len(bs)).tobytes(), np.int32(zero).tobytes(), np.int64(len(col)).tobytes(),
+                     np.int64(len(data)).tobytes(), np.asarray(bs, np.int32).tobytes(),
+                     np.asarray(rp, np.int64).tobytes(), np.asarray(col, np.int32).tobytes(),
+                     np.asarray(data, np.float64).tobytes()])
+    crc = (zlib.crc32(body) + crc_delta) & 0xFFFFFFFF
     with open(path, "wb") as f:
-        f.write(magic)
-        f.write(np.int32(len(bs)).tobytes())
-        f.write(np.int32(zero).tobytes())
-        f.write(np.int64(len(col)).tobytes())
-        f.write(np.int64(len(data)).tobytes())
-        f.write(np.asarray(bs, np.int32).tobytes())
-        f.write(np.asarray(rp, np.int64).tobytes())
-        f.write(np.asarray(col, np.int32).tobytes())
-        f.write(np.asarray(data, np.float64).tobytes())
-        f.write(extra)
+        f.write(body + np.uint32(crc).tobytes() + extra)
 
 
 @pytest.fixture(scope="module")
@@ -41,7 +39,7 @@ def test_file_info_reads_a_valid_file(gb, good):
 
 
 @pytest.mark.parametrize("breakage", ["magic", "short", "trailing", "reserved", "col_order", "col_range",
-                                      "row_ptr", "data_size", "block_edge"])
+                                      "row_ptr", "data_size", "block_edge", "checksum", "flipped_bit"])
 def test_file_info_rejects_broken_files(gb, good, tmp_path, breakage):
     a, _ = good
     bs, rp, col, data = a.blk_size.copy(), a.row_ptr.copy(), a.col.copy(), a.data.copy()
@@ -63,11 +61,17 @@ def test_file_info_rejects_broken_files(gb, good, tmp_path, breakage):
         data = data[:-1]
     elif breakage == "block_edge":
         bs[0] = 33
+    elif breakage == "checksum":
+        kw["crc_delta"] = 1
     p = tmp_path / "bad.bin"
     _write(p, bs, rp, col, data, **kw)
     if breakage == "short":
         raw = open(p, "rb").read()
         open(p, "wb").write(raw[:-5])
+    elif breakage == "flipped_bit":                         # one bit of the data, CRC unchanged
+        raw = bytearray(open(p, "rb").read())
+        raw[-20] ^= 0x04
+        open(p, "wb").write(bytes(raw))
     with pytest.raises(gb.DbcsrError) as e:
         gb.file_info(str(p))
     assert e.value.status == gb._ffi.DBCSR_EINVAL
