@@ -957,7 +957,8 @@ def main():
                       "parallelism": f"replicas x{world}"},
            "time_to_p_ms": ms_all / args.steps,
            "iterations": iters[-1], "converged": all(conv), "trace_p": trp[-1], "n_occ": h.n_occ,
-           "e_band": ebands[-1], "residual": r.report.residual, "stalled": bool(r.report.stalled),
+           "e_band": ebands[-1], "e_band_both_spins": 2.0 * ebands[-1],
+           "residual": r.report.residual, "stalled": bool(r.report.stalled),
            "gpu_launches": launches, "clocks": clk, "roofline": roofline, "e2e": e2e, "mixed": mixed}
 
     if rank == 0 and world == 1 and not args.no_cpu:
