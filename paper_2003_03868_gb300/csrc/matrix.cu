@@ -477,10 +477,13 @@ MatrixFile read_matrix_file(const char* path) {
     if (stored != computed) fail(DBCSR_EINVAL, "load: checksum mismatch");
     for (int32_t b : m.bs)
         if (b < 1 || b > dbg::kMaxBlock) fail(DBCSR_EINVAL, "load: block edge outside [1, 32]");
+    // the whole row-pointer array is checked before any column is read: a pointer past
+    // nnzb in the middle of the array would otherwise index beyond the column vector
     if (m.rp[0] != 0 || m.rp[nblk] != nnzb) fail(DBCSR_EINVAL, "load: bad row pointers");
+    for (int32_t i = 0; i < nblk; ++i)
+        if (m.rp[i + 1] < m.rp[i] || m.rp[i + 1] > nnzb) fail(DBCSR_EINVAL, "load: bad row pointers");
     int64_t area = 0;
     for (int32_t i = 0; i < nblk; ++i) {
-        if (m.rp[i + 1] < m.rp[i]) fail(DBCSR_EINVAL, "load: bad row pointers");
         for (int64_t q = m.rp[i]; q < m.rp[i + 1]; ++q) {
             const int32_t c = m.col[q];
             if (c < 0 || c >= nblk || (q > m.rp[i] && c <= m.col[q - 1]))

@@ -39,7 +39,7 @@ def test_file_info_reads_a_valid_file(gb, good):
 
 
 @pytest.mark.parametrize("breakage", ["magic", "short", "trailing", "reserved", "col_order", "col_range",
-                                      "row_ptr", "data_size", "block_edge", "checksum", "flipped_bit"])
+                                      "row_ptr", "row_ptr_past_end", "data_size", "block_edge", "checksum", "flipped_bit"])
 def test_file_info_rejects_broken_files(gb, good, tmp_path, breakage):
     a, _ = good
     bs, rp, col, data = a.blk_size.copy(), a.row_ptr.copy(), a.col.copy(), a.data.copy()
@@ -57,6 +57,10 @@ def test_file_info_rejects_broken_files(gb, good, tmp_path, breakage):
         col[0] = len(bs)
     elif breakage == "row_ptr":
         rp[-1] -= 1
+    elif breakage == "row_ptr_past_end":
+        # an inner pointer beyond the column count, the last one still right (the file's
+        # CRC is recomputed, so only the layout check can catch it)
+        rp[1] = len(col) + 50
     elif breakage == "data_size":
         data = data[:-1]
     elif breakage == "block_edge":

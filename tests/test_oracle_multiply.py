@@ -178,3 +178,55 @@ def test_thread_count_does_not_change_results(monkeypatch):
         outs.append(subprocess.run([sys.executable, "-c", code], cwd=root, env=env, capture_output=True,
                                    text=True, check=True).stdout.strip())
     assert outs[0] == outs[1]
+
+
+def _dense_block(D, roff, I, J):
+    return D[roff[I]:roff[I + 1], roff[J]:roff[J + 1]]
+
+
+@pytest.mark.parametrize("bs", [SIZES[0], SIZES[1], SIZES[2], [32, 1, 17, 32, 2]])
+@pytest.mark.parametrize("alpha,beta", [(1.0, 0.0), (-0.5, 1.5), (2.0, -1.0)])
+def test_product_block_matches_dense_and_full_product(bs, alpha, beta):
+    # product_block checks sampled outputs of products too large for the oracle's full
+    # multiply; every block of small ragged products (including blocks outside the
+    # product's pattern, empty rows and a C input) must equal the dense definition
+    # alpha*A*B + beta*C_in and the same block of the full oracle product
+    A = _mat(bs, 0.45, 21, empty_rows=(1,))
+    B = _mat(bs, 0.45, 22, empty_rows=(len(bs) - 1,))
+    Cin = _mat(bs, 0.3, 23)
+    Ad, Bd, Cd = bsr.to_dense(A), bsr.to_dense(B), bsr.to_dense(Cin)
+    ref = alpha * (Ad @ Bd) + beta * Cd
+    full = bsr.to_dense(bsr.multiply(alpha, A, B, beta, Cin if beta != 0.0 else None))
+    roff = np.concatenate([[0], np.cumsum(bs)])
+    scale = max(1.0, np.abs(ref).max())
+    n_absent = 0
+    for I, J in itertools.product(range(len(bs)), repeat=2):
+        got = bsr.product_block(I, J, alpha, A, B, beta, Cin)
+        assert got.shape == (bs[I], bs[J])
+        want = _dense_block(ref, roff, I, J)
+        np.testing.assert_allclose(got, want, rtol=0, atol=1e-15 * scale * 8)
+        # same loop order as the full product: equal to rounding of the last bit
+        np.testing.assert_allclose(got, _dense_block(full, roff, I, J), rtol=0, atol=1e-15 * scale)
+        if np.all(want == 0.0):
+            n_absent += 1
+            assert np.all(got == 0.0)
+    # the empty row of A gives whole zero block rows (beta C_in aside)
+    assert n_absent >= 1 or beta != 0.0
+
+
+def test_product_block_wrong_b_block_fails_the_pin():
+    # planted mistake: the block of B found for (K, J) is its neighbour in storage (an
+    # off-by-one of the search), emulated by shifting B's block offsets by one block
+    bs = SIZES[0]
+    A, B = _mat(bs, 0.5, 24), _mat(bs, 0.5, 25)
+    ref = bsr.to_dense(A) @ bsr.to_dense(B)
+    roff = np.concatenate([[0], np.cumsum(bs)])
+    good_err = max(np.abs(bsr.product_block(I, J, 1.0, A, B) - _dense_block(ref, roff, I, J)).max()
+                   for I, J in itertools.product(range(len(bs)), repeat=2))
+    assert good_err < 1e-13
+    Bbad = B.copy()
+    Bbad.boff = np.concatenate([B.boff[1:], [B.boff[-1]]]).astype(np.int64)
+    Bbad.data = np.concatenate([B.data, np.zeros(32 * 32)])    # reads stay inside the buffer
+    bad_err = max(np.abs(bsr.product_block(I, J, 1.0, A, Bbad) - _dense_block(ref, roff, I, J)).max()
+                  for I, J in itertools.product(range(len(bs)), repeat=2))
+    assert bad_err > 1e-2
