@@ -1,16 +1,21 @@
 #!/usr/bin/env python3
-"""Benchmark: time-to-P and block-GEMM throughput of the FP64 Newton-Schulz sign
-iteration on the 1,024-water synthetic Hamiltonian (N = 23,552, eps 1e-7, tol 1e-9).
+"""Benchmark: time-to-P and block-GEMM throughput of the mixed-precision sign
+iteration against the plain FP64 one, on the 4,096-water synthetic Hamiltonian
+with 23/7 atom blocks (N = 151,552, eps 1e-6, tol 1e-8; split-BF16 tensor-core
+products until ||X^2 - 1||_F / N < 1e-4, FP64 after).
 
 One step = one complete sign iteration from the resident H to the density matrix
-P (every product, filter, trace of the path).  value = algorithmic FP64 flops of
-all block products executed in the timed steps / device time (TFLOP/s);
-ms_per_step = time-to-P.  With --gpus N > 1 (torchrun) every rank solves its own
-replica (the path is not sharded across GPUs here: replicas only, weak scaling).
+P (every product, filter, trace of the path).  value = executed block-product
+flops (2 m n k per product, unpadded) of the mixed iteration / device time
+(TFLOP/s); ms_per_step = its time-to-P.  The FP64 iteration of the same H, the
+1,024-water FP64 configuration (13/5 blocks, eps 1e-7, tol 1e-9) and its mixed
+ladder are timed beside it.  With --gpus N > 1 (torchrun) every rank solves its
+own replica (the path is not sharded across GPUs here: replicas only, weak
+scaling).
 
 --impl reference times the FP64 CPU oracle (plain C) on the host cores, each step
-a bounded sample of the same workload (the first product X0.X0 restricted to a
-fixed set of block rows).
+a bounded sample of the same workload: the oracle's first product X0.X0 of the
+4,096-water iteration restricted to a fixed set of block rows of its left factor.
 """
 from __future__ import annotations
 
@@ -31,10 +36,11 @@ NOMINAL_BF16 = 2250.0
 NOMINAL_FP64 = 1.25
 FALLBACK_BF16_BURST, FALLBACK_BF16_SUSTAINED = 1900.0, 1700.0
 
-# DRAM traffic of the FP64 block-product kernels (dram__bytes_read.sum + dram__bytes_write.sum),
-# averaged over the 84 k_smm_f64 launches of one sign-1024h2o step, from one single-pass ncu
-# capture of the current kernels.  Cleared whenever the kernels change.
-SMM_F64_TRAFFIC = {"sign-1024h2o-dzvp-fp64": 2.856e9}
+# DRAM bytes per executed flop of the FP64 block-product kernels (dram__bytes_read.sum +
+# dram__bytes_write.sum over the captured launches / their flops), from a capture of a few
+# launches of the small 512-water 23/7 case; a full launch's traffic is this ratio times its
+# flops.  None until captured for the current kernel (cleared whenever the kernel changes).
+SMM_F64_BYTES_PER_FLOP = None
 
 
 def bf16_peak():
@@ -54,14 +60,25 @@ def hbm_peak():
         return 6800.0, "fallback copy"
 
 
-def fp64_peak():
-    """FP64 roofline peak: the measured bf16 peak times the nominal FP64/bf16 ratio."""
+def fp64_derived_peak():
+    """The measured bf16 peak times the nominal FP64/bf16 ratio (context only)."""
     try:
-        pk = json.load(open(PEAKS_FILE))
-        bf16, src = float(pk["bf16_tflops_sustained"]), "measured bf16 sustained x nominal fp64/bf16"
+        bf16 = float(json.load(open(PEAKS_FILE))["bf16_tflops_sustained"])
     except Exception:
-        bf16, src = FALLBACK_BF16_SUSTAINED, "fallback bf16 sustained x nominal fp64/bf16"
-    return bf16 * NOMINAL_FP64 / NOMINAL_BF16, src
+        bf16 = FALLBACK_BF16_SUSTAINED
+    return bf16 * NOMINAL_FP64 / NOMINAL_BF16
+
+
+def fp64_peak(gb, torch):
+    """FP64 roofline peak: the higher of the library's DFMA and DMMA (m8n8k4) loops, measured
+    on this GPU with every SM busy (MEASURED_PEAKS.json holds no FP64 figure)."""
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    dfma = gb.lib().dbcsr_bench_peak(0, 4096, sms * 8, 256) / 1e3
+    dmma = gb.lib().dbcsr_bench_peak(1, 4096, sms * 8, 256) / 1e3
+    peak = max(dfma, dmma)
+    return peak, {"peak_source": "measured FP64 (max of the DFMA and DMMA loops, dbcsr_bench_peak)",
+                  "fp64_dfma_measured_tflops": dfma, "fp64_dmma_measured_tflops": dmma,
+                  "fp64_derived_tflops": fp64_derived_peak(), "sms": sms}
 
 
 class Clocks:
@@ -138,27 +155,65 @@ def sample_text(steps, flops, dt):
             f"block, no prescreen)")
 
 
+class RowsSample:
+    """A bounded sample of the sign iteration's first product for the oracle: X0 = (H - mu)/alpha
+    (alpha the Gershgorin bound), and the product of its first ``rows`` block rows with the whole
+    X0, filtered at eps, as the oracle computes it (every candidate block formed)."""
+
+    def __init__(self, h, w, frac: float):
+        from oracle import bsr, sign
+        self.bsr = bsr
+        Ho = bsr.Mat.of(h.H)
+        alpha = sign.gershgorin(Ho, h.mu)
+        self.X0 = bsr.add_identity(Ho, 1.0 / alpha, -h.mu / alpha)
+        X = self.X0
+        self.rows = max(1, int(round(frac * X.nblk)))
+        nz = int(X.rp[self.rows])
+        rp = X.rp.copy()
+        rp[self.rows + 1:] = nz
+        self.A = bsr.Mat(X.bs, rp, X.col[:nz].copy(), X.data[:int(X.boff[nz])].copy())
+        self.eps = w.eps_filter
+
+    def run(self):
+        t0 = time.perf_counter()
+        _, info = self.bsr.multiply(1.0, self.A, self.X0, eps=self.eps, info=True)
+        return float(info.flops), time.perf_counter() - t0, self.bsr.num_threads()
+
+    def text(self, flops, dt):
+        return (f"the oracle's first product X0.X0 of the iteration restricted to block rows 0..{self.rows - 1} "
+                f"of {self.X0.nblk} ({flops / 1e9:.0f} GFLOP executed in {dt:.1f} s; the oracle forms every "
+                f"candidate block, no prescreen)")
+
+
+# block rows of the 4,096-water X0 in one oracle sample: a reference-arm step (about 5 s on 16
+# host cores) and the CPU baseline of the main line (about 10 s)
+REF_ROWS_FRAC, CPU_ROWS_FRAC = 1.0 / 8, 1.0 / 4
+HEADLINE_METRIC = "block-GEMM TFLOP/s & time-to-P at 1e-6 Ha/atom, mixed vs FP64 on GB300"
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     import synth
-    w = synth.SIGN_1024
+    w = synth.SIGN_4096
     h = synth.build_hamiltonian(w)
+    smp = RowsSample(h, w, REF_ROWS_FRAC)
     for _ in range(args.warmup):
-        oracle_sample(h, w, args.ref_steps)
-    tot_f, tot_t = 0, 0.0
+        smp.run()
+    tot_f, tot_t = 0.0, 0.0
     for _ in range(args.steps):
-        f, dt, cores = oracle_sample(h, w, args.ref_steps)
+        f, dt, cores = smp.run()
         tot_f += f
         tot_t += dt
     value = tot_f / tot_t / 1e12
-    sample = sample_text(args.ref_steps, f, dt) + ", one per step"
-    out = {"metric": "block-GEMM TFLOP/s (FP64 sign iteration, time-to-P)", "value": value, "unit": "TFLOP/s",
+    sample = smp.text(f, dt) + ", one per step"
+    out = {"metric": HEADLINE_METRIC, "value": value, "unit": "TFLOP/s",
            "impl": "reference", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": tot_t / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": w.name, "n_mol": w.n_mol, "N": w.n, "eps_filter": w.eps_filter, "tol": w.tol,
+           "config": {"workload": "sign-4096h2o-23-7-mixed-vs-fp64", "n_mol": w.n_mol, "N": w.n,
+                      "blocks": {"O": w.basis[0], "H": w.basis[1]}, "eps_filter": w.eps_filter, "tol": w.tol,
                       "sample": sample},
            "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cores, "kind": "oracle", "sample": sample},
            "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -730,6 +785,202 @@ def run_predictor(args, gb, synth, torch, barrier):
     return 0
 
 
+def sign_leg(gb, torch, barrier, H, h, w, steps, warmup, prec, **kw):
+    """``steps`` timed sign iterations of H (after ``warmup`` untimed ones) on the current stream:
+    device time-to-P from CUDA events around the timed calls, and the reports' work counters."""
+    stream = torch.cuda.current_stream()
+
+    def one():
+        return gb.sign_iterate(H, h.mu, w.eps_filter, w.tol, prec=prec, switch_tol=w.switch or 1e-4, **kw)
+
+    for _ in range(warmup):
+        one()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    acc = {k: 0.0 for k in ("flops", "flops_low", "ms_low", "ms_multiply", "ms_symbolic", "ms_filter",
+                            "bytes_min_fp64", "launches_fp64")}
+    for _ in range(steps):
+        r = one()
+        for k in acc:
+            acc[k] += float(getattr(r.report, k))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    return r, ms, acc
+
+
+def fp64_roofline(acc, ms, steps, peak, peak_info):
+    """k_smm_f64 in a step: executed FP64 flops over the FP64 block-product kernels' own time
+    (CUDA events the library records around them on the launching stream)."""
+    f = acc["flops"] - acc["flops_low"]
+    t = acc["ms_multiply"] - acc["ms_low"]
+    nl = acc["launches_fp64"]
+    achieved = f / (t * 1e-3) / 1e12 if t > 0 else 0.0
+    return {"bound": "fp64", "kernel": "k_smm_f64", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak,
+            "traffic": SMM_F64_BYTES_PER_FLOP * f / nl if SMM_F64_BYTES_PER_FLOP and nl else None,
+            "traffic_note": "DRAM bytes per launch: bytes per flop of a small-case capture x flops per launch",
+            "kernel_share_of_step": t / ms if ms > 0 else None, "launches_per_step": nl / steps,
+            "compulsory_bytes_per_launch": acc["bytes_min_fp64"] / nl if nl else None,
+            "ms_per_step": t / steps, **peak_info}
+
+
+def low_roofline(acc, ms, steps):
+    """The low tier's split-BF16 block-product kernel against the measured sustained bf16 peak."""
+    bpk, bpk_src = bf16_peak()
+    low_alg = acc["flops_low"] / (acc["ms_low"] * 1e-3) / 1e12 if acc["ms_low"] > 0 else 0.0
+    return {"bound": "tensor", "kernel": LOW_TIER_KERNEL, "achieved": 3 * low_alg, "unit": "TFLOP/s",
+            "peak": bpk, "frac": 3 * low_alg / bpk, "peak_source": bpk_src, "algorithmic_tflops": low_alg,
+            "kernel_share_of_step": acc["ms_low"] / ms if ms > 0 else None, "ms_per_step": acc["ms_low"] / steps,
+            "note": "achieved counts the three bf16 products (hi*hi, hi*lo, lo*hi) of every unpadded "
+                    "2mnk block product"}
+
+
+LOW_TIER_KERNEL = "k_smm_bf16<MT,NT,split>"
+
+
+def run_headline(args, gb, synth, torch, barrier, dist, rank, world, local):
+    """The metric's own configuration: mixed vs FP64 sign iteration on 4,096 waters (23/7 blocks),
+    with the 1,024-water FP64 configuration (13/5) and its mixed ladder beside it."""
+    import numpy as np
+    from paper_2003_03868_gb300 import ranks
+    w = synth.SIGN_4096
+    h = synth.build_hamiltonian(w)
+    stream = torch.cuda.current_stream()
+    H = gb.Matrix.of(h.H, stream=stream.cuda_stream)
+    side_steps = max(1, min(args.steps, args.side_steps))
+    peak, peak_info = fp64_peak(gb, torch)
+
+    # main leg: the mixed ladder (split BF16 while r >= 1e-4, then FP64), args.steps timed steps
+    clocks = Clocks(local)
+    l0 = gb.lib().dbcsr_launch_count()
+    for _ in range(args.warmup):
+        gb.sign_iterate(H, h.mu, w.eps_filter, w.tol, prec=gb.DBCSR_MIXED, switch_tol=w.switch)
+    barrier()
+    clocks.start()
+    l1 = gb.lib().dbcsr_launch_count()
+    rm, ms_m, acc_m = sign_leg(gb, torch, barrier, H, h, w, args.steps, 0, gb.DBCSR_MIXED)
+    launches = gb.lib().dbcsr_launch_count() - l1
+    clk = clocks.stop()
+    ms_all, flops_all = ranks.job_timing(ms_m, acc_m["flops"], dist, "cuda")
+    value = flops_all / (ms_all * 1e-3) / 1e12
+
+    # the plain FP64 iteration of the same H
+    rf, ms_f, acc_f = sign_leg(gb, torch, barrier, H, h, w, side_steps, 1, gb.DBCSR_FP64)
+    ms_f_all, flops_f_all = ranks.job_timing(ms_f, acc_f["flops"], dist, "cuda")
+    fp64 = {"time_to_p_ms": ms_f_all / side_steps, "value": flops_f_all / (ms_f_all * 1e-3) / 1e12,
+            "unit": "TFLOP/s", "steps": side_steps, "iterations": rf.report.iterations,
+            "converged": bool(rf.report.converged), "stalled": bool(rf.report.stalled),
+            "residual": rf.report.residual, "trace_p": rf.report.trace_p, "e_band": rf.report.e_band,
+            "roofline": fp64_roofline(acc_f, ms_f, side_steps, peak, peak_info),
+            "ms_per_step": {k: acc_f[k] / side_steps for k in ("ms_multiply", "ms_symbolic", "ms_filter")}}
+
+    # option: the FP64 tail's update correction in split BF16
+    rc, ms_c, _ = sign_leg(gb, torch, barrier, H, h, w, side_steps, 1, gb.DBCSR_MIXED, low_correction=True)
+    low_correction = {"time_to_p_ms": ms_c / side_steps, "speedup_vs_fp64": ms_f / ms_c * 1.0,
+                      "steps": side_steps, "iterations": rc.report.iterations, "converged": bool(rc.report.converged),
+                      "de_band_per_atom_vs_fp64": abs(rc.report.e_band - rf.report.e_band) / h.n_atoms,
+                      "note": "DBCSR_SIGN_LOW_CORRECTION: X*X, residual, test, filter and traces in FP64; "
+                              "the update's correction product in split BF16"}
+
+    # end to end through the public API: H from pinned host memory each step, P exported to pinned
+    # host memory each step (row pointers, block columns, values), the report read back
+    e2e = None
+    if not args.no_e2e:
+        e2e_steps = max(1, min(args.steps, args.e2e_steps))
+        data_pin = torch.from_numpy(np.ascontiguousarray(h.H.data)).pin_memory()
+        rows_pin = torch.from_numpy(np.ascontiguousarray(
+            np.repeat(np.arange(h.H.blk_size.shape[0], dtype=np.int32), np.diff(h.H.row_ptr)))).pin_memory()
+        cols_pin = torch.from_numpy(np.ascontiguousarray(h.H.col, dtype=np.int32)).pin_memory()
+        nb, nzp, nep = rm.P.info()
+        cap_z, cap_e = int(nzp * 1.25) + 1024, int(nep * 1.25) + 65536
+        p_rp = torch.empty(nb + 1, dtype=torch.int64).pin_memory()
+        p_col = torch.empty(cap_z, dtype=torch.int32).pin_memory()
+        p_dat = torch.empty(cap_e, dtype=torch.float64).pin_memory()
+        h2d = int(data_pin.numel() * 8 + rows_pin.numel() * 4 + cols_pin.numel() * 4)
+        barrier()
+        f0 = time.perf_counter()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record(stream)
+        fl, d2h = 0.0, 0
+        for _ in range(e2e_steps):
+            Hs = gb.Matrix.from_pinned(h.H.blk_size, rows_pin.data_ptr(), cols_pin.data_ptr(), cols_pin.numel(),
+                                       data_pin.data_ptr(), stream=stream.cuda_stream)
+            rr = gb.sign_iterate(Hs, h.mu, w.eps_filter, w.tol, prec=gb.DBCSR_MIXED, switch_tol=w.switch)
+            d2h += rr.P.export_to(p_rp.data_ptr(), p_col.data_ptr(), cap_z, p_dat.data_ptr(), cap_e)
+            fl += rr.report.flops
+            d2h += 3 * 8                                                # trace, band energy, residual
+            _ = (float(rr.report.e_band), float(rr.report.trace_p), float(rr.report.residual))
+            rr.P.close()
+            Hs.close()
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        ms2 = ev[0].elapsed_time(ev[1])
+        e2e = {"value": fl / (ms2 * 1e-3) / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h // e2e_steps, "ms_per_step": ms2 / e2e_steps, "steps": e2e_steps,
+               "wall_s": time.perf_counter() - f0,
+               "note": "dbcsr_put_blocks + dbcsr_finalize from pinned host buffers, the mixed sign iteration, "
+                       "dbcsr_export of P into pinned host buffers"}
+
+    # the 1,024-water configuration beside it: FP64 (eps 1e-7, tol 1e-9) and the mixed ladder
+    w2 = synth.SIGN_1024
+    h2 = synth.build_hamiltonian(w2)
+    H2 = gb.Matrix.of(h2.H, stream=stream.cuda_stream)
+    r2f, ms2f, acc2f = sign_leg(gb, torch, barrier, H2, h2, w2, side_steps, 1, gb.DBCSR_FP64)
+    r2m, ms2m, acc2m = sign_leg(gb, torch, barrier, H2, h2, w2, side_steps, 1, gb.DBCSR_MIXED)
+    c2 = {"workload": w2.name, "n_mol": w2.n_mol, "N": w2.n, "blocks": {"O": w2.basis[0], "H": w2.basis[1]},
+          "eps_filter": w2.eps_filter, "tol": w2.tol, "steps": side_steps,
+          "fp64": {"time_to_p_ms": ms2f / side_steps, "value": acc2f["flops"] / (ms2f * 1e-3) / 1e12,
+                   "iterations": r2f.report.iterations, "converged": bool(r2f.report.converged),
+                   "stalled": bool(r2f.report.stalled), "residual": r2f.report.residual,
+                   "trace_p": r2f.report.trace_p, "e_band": r2f.report.e_band,
+                   "roofline": fp64_roofline(acc2f, ms2f, side_steps, peak, peak_info)},
+          "mixed": {"time_to_p_ms": ms2m / side_steps, "value": acc2m["flops"] / (ms2m * 1e-3) / 1e12,
+                    "speedup_vs_fp64": ms2f / ms2m, "iterations": r2m.report.iterations,
+                    "fp64_from_step": r2m.report.fp64_from, "converged": bool(r2m.report.converged),
+                    "stalled": bool(r2m.report.stalled),
+                    "de_band_per_atom_vs_fp64": abs(r2m.report.e_band - r2f.report.e_band) / h2.n_atoms,
+                    "low_tier_roofline": low_roofline(acc2m, ms2m, side_steps)},
+          "unit": "TFLOP/s", "unit_time": "ms"}
+    H2.close()
+
+    f_roof = fp64_roofline(acc_m, ms_m, args.steps, peak, peak_info)
+    l_roof = low_roofline(acc_m, ms_m, args.steps)
+    dominant = f_roof if f_roof["kernel_share_of_step"] >= (l_roof["kernel_share_of_step"] or 0.0) else l_roof
+    out = {"metric": HEADLINE_METRIC, "value": value, "unit": "TFLOP/s",
+           "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_all / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3+f64",
+           "data": "synthetic",
+           "config": {"workload": "sign-4096h2o-23-7-mixed-vs-fp64", "n_mol": w.n_mol, "N": w.n,
+                      "blocks": {"O": w.basis[0], "H": w.basis[1]}, "eps_filter": w.eps_filter, "tol": w.tol,
+                      "switch": w.switch, "mu": h.mu,
+                      "l2": "inputs larger than L2 (H alone is %.0f MB; 129 MB L2)" % (h.H.data.nbytes / 1e6),
+                      "parallelism": f"replicas x{world}"},
+           "time_to_p_ms": ms_all / args.steps, "iterations": rm.report.iterations,
+           "fp64_from_step": rm.report.fp64_from, "converged": bool(rm.report.converged),
+           "stalled": bool(rm.report.stalled), "residual": rm.report.residual, "trace_p": rm.report.trace_p,
+           "n_occ": h.n_occ, "e_band": rm.report.e_band, "e_band_both_spins": 2.0 * rm.report.e_band,
+           "de_band_per_atom_vs_fp64": abs(rm.report.e_band - rf.report.e_band) / h.n_atoms,
+           "speedup_vs_fp64": fp64["time_to_p_ms"] / (ms_all / args.steps),
+           "ms_per_step_phases": {k: acc_m[k] / args.steps for k in ("ms_low", "ms_multiply", "ms_symbolic",
+                                                                      "ms_filter")},
+           "gpu_launches": launches, "clocks": clk, "roofline": dominant,
+           "fp64_tail_roofline": f_roof, "low_tier_roofline": l_roof,
+           "fp64": fp64, "low_correction": low_correction, "e2e": e2e, "sign_1024h2o": c2}
+    if rank == 0 and world == 1 and not args.no_cpu:
+        smp = RowsSample(h, w, CPU_ROWS_FRAC)
+        f, dt, cores = smp.run()
+        out["cpu_baseline"] = {"value": f / dt / 1e12, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+                               "sample": smp.text(f, dt)}
+    if rank == 0:
+        print(json.dumps(out))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -741,12 +992,16 @@ def main():
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision leg")
     ap.add_argument("--ref-steps", type=int, default=1, help="Newton-Schulz steps per oracle sample (reference arm)")
     ap.add_argument("--cpu-steps", type=int, default=2, help="Newton-Schulz steps in the oracle CPU baseline")
-    ap.add_argument("--workload", default="sign-1024h2o",
-                    choices=["sign-1024h2o", "sign-512h2o", "sign-512h2o-23-7", "sign-4096h2o", "batch-64",
+    ap.add_argument("--side-steps", type=int, default=3, help="timed steps of the side legs of the default run")
+    ap.add_argument("--e2e-steps", type=int, default=5, help="timed steps of the end-to-end leg")
+    ap.add_argument("--workload", default="sign-4096h2o-mixed",
+                    choices=["sign-4096h2o-mixed", "sign-1024h2o", "sign-512h2o", "sign-512h2o-23-7", "sign-4096h2o", "batch-64",
                              "sign-20736h2o-mlp", "mult-32h2o", "sign-1024h2o-orders", "sign-4096h2o-orders",
                              "sign-1024h2o-nonorth", "sign-4096h2o-nonorth", "sign-1024h2o-purify",
                              "sign-4096h2o-purify", "submatrix-6192h2o-szv"],
-                    help="sign-512h2o, sign-512h2o-23-7: smaller cases for profiler captures; sign-4096h2o: "
+                    help="sign-4096h2o-mixed (default): the mixed vs FP64 sign iteration on 4,096 waters (23/7) "
+                         "with the 1,024-water configuration beside it; sign-1024h2o: the FP64 iteration on "
+                         "1,024 waters (13/5) with its ladders; sign-512h2o, sign-512h2o-23-7: smaller cases for profiler captures; sign-4096h2o: "
                          "4,096 waters with O/H blocks 23/7 (FP64 and mixed); batch-64: 64 uneven systems "
                          "batched vs one by one; sign-20736h2o-mlp: the mixed iteration on 20,736 waters with "
                          "default, MLP-predicted and exhaustively tuned launch configurations; mult-32h2o: the "
@@ -792,6 +1047,8 @@ def main():
         gb.lib()
     import synth
 
+    if args.workload == "sign-4096h2o-mixed":
+        return run_headline(args, gb, synth, torch, barrier, dist, rank, world, local)
     if args.workload == "batch-64":
         return run_batch(args, gb, synth, torch, barrier)
     if args.workload == "submatrix-6192h2o-szv":
@@ -934,18 +1191,15 @@ def main():
                "d2h_bytes_per_step": 8 * 3, "ms_per_step": ms2 / args.steps,
                "wall_s": time.perf_counter() - f0}
 
-    peak, peak_src = fp64_peak()
+    peak, peak_info = fp64_peak(gb, torch)
     achieved = flops / (ms_mult * 1e-3) / 1e12 if ms_mult > 0 else 0.0
     roofline = {"bound": "fp64", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": SMM_F64_TRAFFIC.get(w.name), "kernel": "k_smm_f64",
-                "peak_source": peak_src, "kernel_share_of_step": ms_mult / ms if ms > 0 else None,
+                "frac": achieved / peak, "kernel": "k_smm_f64",
+                "traffic": (SMM_F64_BYTES_PER_FLOP * flops / smm_launches
+                            if SMM_F64_BYTES_PER_FLOP and smm_launches else None),
+                "kernel_share_of_step": ms_mult / ms if ms > 0 else None,
                 "launches_per_step": smm_launches / args.steps,
-                "compulsory_bytes_per_launch": bytes_min / smm_launches if smm_launches else None}
-    try:
-        roofline["fp64_dfma_measured_tflops"] = gb.lib().dbcsr_bench_peak(0, 4096, 152 * 8, 256) / 1e3
-        roofline["fp64_dmma_measured_tflops"] = gb.lib().dbcsr_bench_peak(1, 4096, 152 * 8, 256) / 1e3
-    except Exception:
-        pass
+                "compulsory_bytes_per_launch": bytes_min / smm_launches if smm_launches else None, **peak_info}
 
     out = {"metric": "block-GEMM TFLOP/s (FP64 sign iteration, time-to-P)", "value": value, "unit": "TFLOP/s",
            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_all / args.steps,

@@ -556,9 +556,48 @@ dbcsr_status dbcsr_mlp_train(int32_t nfeat, float* params, const float* X, const
                              const dbcsr_mlp_opts* opts, dbcsr_mlp_report* rep);
 
 /* For each triple, the configuration of dbcsr_tune_space(prec) with the lowest
- * predicted value (and that value in best_pred, may be NULL). */
+ * predicted value (and that value in best_pred, may be NULL).  params == NULL takes the
+ * model dbcsr_predictor_train keeps for prec (ESTATE if there is none). */
 dbcsr_status dbcsr_mlp_predict_best(int32_t prec, const float* params, const int32_t* mnk, int32_t ntriples,
                                     dbcsr_kernel_cfg* best, float* best_pred);
+
+/*
+ * The autotuner's timings as a records file (text, one record per line:
+ * "prec m n k tpb ctas_per_sm colmajor prefetch2 ms", a '#' line first), the input of
+ * dbcsr_predictor_train.  append = 0 truncates the file and writes the header line;
+ * append = 1 adds the records after those already there.  Errors: EINVAL (bad argument,
+ * file not writable).  Not from the paper (a file format of this library).
+ */
+dbcsr_status dbcsr_tune_records_save(const char* path, const dbcsr_tune_record* recs, int64_t n, int32_t append);
+
+/*
+ * Trains the performance-prediction model on the autotuner's timings (section "Batched
+ * execution": the tuning data train a model that predicts parameters for the kernels
+ * nobody tuned).  From the records of precision prec in the records file tune_records:
+ *   - features of each (m, n, k, configuration) as dbcsr_mlp_features;
+ *   - target = log(ms) minus the mean log(ms) of the record's (m, n, k) triple, divided
+ *     by the standard deviation of these centred values over all the records (population
+ *     form, at least 1e-12): the model learns how the configuration changes a triple's time;
+ *   - Glorot-uniform initial weights from seed (dbcsr_mlp_init), then opts->epochs
+ *     full-batch Adam steps on the GPU (dbcsr_mlp_train; rep receives its losses and time).
+ * The trained parameters are kept by the library, one model per precision (a later call
+ * replaces it): dbcsr_mlp_predict_best and dbcsr_tune_predicted use it when given
+ * params == NULL, and dbcsr_predictor_params copies it out.
+ * Errors: EINVAL (null opts, unreadable or malformed file, no record of prec, a record out
+ * of range), those of dbcsr_mlp_train.
+ */
+dbcsr_status dbcsr_predictor_train(const char* tune_records, int32_t prec, uint64_t seed, const dbcsr_mlp_opts* opts,
+                                   dbcsr_mlp_report* rep);
+
+/* The features (X[n * DBCSR_MLP_FEATURES]) and targets (T[n]) dbcsr_predictor_train builds
+ * from a records file, on the host: *n receives the number of records of prec; up to cap of
+ * them are written (X and T may be NULL).  Errors as dbcsr_predictor_train's file checks. */
+dbcsr_status dbcsr_predictor_data(const char* tune_records, int32_t prec, float* X, float* T, int64_t cap,
+                                  int64_t* n);
+
+/* Copies the model kept for prec (dbcsr_mlp_param_count(DBCSR_MLP_FEATURES) floats) into
+ * params.  Errors: EINVAL (null params), ESTATE (no model trained for prec). */
+dbcsr_status dbcsr_predictor_params(int32_t prec, float* params);
 
 /*
  * The prediction with the exhaustive autotune as its fallback and measured time as the
@@ -570,7 +609,8 @@ dbcsr_status dbcsr_mlp_predict_best(int32_t prec, const float* params, const int
  *   - if the prediction's time is at most (1 + tolerance) times the default's, it enters
  *     the tune table; otherwise every configuration of dbcsr_tune_space is timed on that
  *     stack and the fastest enters the table.
- * fell_back[t] (may be NULL) receives 1 where the exhaustive search ran.
+ * fell_back[t] (may be NULL) receives 1 where the exhaustive search ran.  params == NULL
+ * takes the model dbcsr_predictor_train keeps for prec.
  * Errors: EINVAL (bad argument or triple), and those of dbcsr_mlp_predict_best.
  */
 dbcsr_status dbcsr_tune_predicted(int32_t prec, const float* params, const int32_t* mnk, int32_t ntriples,

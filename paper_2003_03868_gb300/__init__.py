@@ -84,6 +84,18 @@ class Matrix:
         return m
 
     @classmethod
+    def from_pinned(cls, blk_size, rows_ptr: int, cols_ptr: int, nblocks: int, data_ptr: int,
+                    stream: int | None = None) -> "Matrix":
+        """Matrix from host buffers given by address (block rows and columns as int32, values
+        packed block after block, row-major): one dbcsr_put_blocks and dbcsr_finalize, with no
+        copy through numpy.  Pinned host buffers let the upload run at the link's speed."""
+        m = cls(blk_size, stream)
+        _check(lib().dbcsr_put_blocks(m.handle, int(nblocks), C.c_void_p(int(rows_ptr)), C.c_void_p(int(cols_ptr)),
+                                      C.c_void_p(int(data_ptr)), 0), "put_blocks")
+        m.finalize()
+        return m
+
+    @classmethod
     def of(cls, bm, stream: int | None = None) -> "Matrix":
         """From any object with blk_size/row_ptr/col/data (the input generator's format)."""
         return cls.from_blocks(bm.blk_size, bm.row_ptr, bm.col, bm.data, stream)
@@ -135,6 +147,17 @@ class Matrix:
         data = np.empty(ne, dtype=np.float64)
         _check(lib().dbcsr_export(self.handle, _ptr(rp), _ptr(col), _ptr(data)), "export")
         return rp, col, data
+
+    def export_to(self, rp_ptr: int, col_ptr: int, col_cap: int, data_ptr: int, data_cap: int) -> int:
+        """dbcsr_export into host buffers given by address (row pointers: nblk + 1 int64; block
+        columns: int32, room for col_cap; values: float64, room for data_cap).  Returns the bytes
+        copied; raises ValueError when the matrix does not fit."""
+        nb, nz, ne = self.info()
+        if nz > col_cap or ne > data_cap:
+            raise ValueError(f"export_to: {nz} blocks / {ne} values exceed the buffers ({col_cap} / {data_cap})")
+        _check(lib().dbcsr_export(self.handle, C.c_void_p(int(rp_ptr)), C.c_void_p(int(col_ptr)),
+                                  C.c_void_p(int(data_ptr))), "export")
+        return 8 * (nb + 1) + 4 * nz + 8 * ne
 
     def copy(self) -> "Matrix":
         out = Matrix(self.blk_size, self.stream)
@@ -562,30 +585,58 @@ def mlp_train(params, X, T, epochs: int = 2000, lr: float = 1e-3, beta1: float =
     return p, r
 
 
-def train_predictor(recs, prec: int = DBCSR_FP64, epochs: int = 3000, lr: float = 2e-3, seed: int = 3):
-    """Trains the prediction MLP on autotuner records (TuneRecord list) of one precision.
+def tune_records_save(path: str, recs, append: bool = False):
+    """Writes autotuner records (TuneRecord list) to a records file (dbcsr_tune_records_save)."""
+    arr = (TuneRecord * len(recs))(*recs)
+    _check(lib().dbcsr_tune_records_save(os.fsencode(path), arr, len(recs), 1 if append else 0), "tune_records_save")
 
-    Target: the log launch time, centred per (m, n, k) triple and scaled to unit variance,
-    so the model learns how the configuration changes the time of a triple.  Returns
-    (params, MlpReport)."""
-    tri = [(r.m, r.n, r.k) for r in recs]
-    X = mlp_features(tri, [r.cfg for r in recs], prec)
-    y = np.log(np.array([r.ms for r in recs]))
-    mean = {}
-    for t in set(tri):
-        mean[t] = float(np.mean([yy for tt, yy in zip(tri, y) if tt == t]))
-    T = np.array([yy - mean[t] for t, yy in zip(tri, y)])
-    T = (T / max(T.std(), 1e-12)).astype(np.float32)
-    return mlp_train(mlp_init(MLP_FEATURES, seed=seed), X, T, epochs=epochs, lr=lr)
+
+def predictor_data(path: str, prec: int = DBCSR_FP64):
+    """(X, T): the features and targets dbcsr_predictor_train builds from a records file."""
+    n = C.c_int64()
+    _check(lib().dbcsr_predictor_data(os.fsencode(path), int(prec), None, None, 0, C.byref(n)), "predictor_data")
+    X = np.zeros((n.value, MLP_FEATURES), dtype=np.float32)
+    T = np.zeros(n.value, dtype=np.float32)
+    _check(lib().dbcsr_predictor_data(os.fsencode(path), int(prec), _ptr(X), _ptr(T), n.value, C.byref(n)),
+           "predictor_data")
+    return X, T
+
+
+def predictor_train(path: str, prec: int = DBCSR_FP64, epochs: int = 3000, lr: float = 2e-3, seed: int = 3,
+                    beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8):
+    """Trains the library's prediction model on a records file (dbcsr_predictor_train); the
+    library keeps the model for prec.  Returns (params, MlpReport)."""
+    o = MlpOpts(int(epochs), 0, float(lr), float(beta1), float(beta2), float(eps))
+    r = MlpReport()
+    _check(lib().dbcsr_predictor_train(os.fsencode(path), int(prec), int(seed), C.byref(o), C.byref(r)),
+           "predictor_train")
+    p = np.zeros(lib().dbcsr_mlp_param_count(MLP_FEATURES), dtype=np.float32)
+    _check(lib().dbcsr_predictor_params(int(prec), _ptr(p)), "predictor_params")
+    return p, r
+
+
+def train_predictor(recs, prec: int = DBCSR_FP64, epochs: int = 3000, lr: float = 2e-3, seed: int = 3):
+    """Trains the prediction model on autotuner records (TuneRecord list) of one precision:
+    the records go to a temporary records file and dbcsr_predictor_train builds the targets
+    and trains there.  Returns (params, MlpReport)."""
+    import tempfile
+    fd, path = tempfile.mkstemp(suffix=".tune")
+    os.close(fd)
+    try:
+        tune_records_save(path, recs)
+        return predictor_train(path, prec, epochs=epochs, lr=lr, seed=seed)
+    finally:
+        os.unlink(path)
 
 
 def tune_predicted(params, triples, prec: int = DBCSR_FP64, stack_len: int = 500000, reps: int = 3,
                    tolerance: float = 0.02):
     """Installs the MLP's configuration for each triple when its measured time is within
     tolerance of the default's, else the exhaustive best (dbcsr_tune_predicted).  Returns
-    the per-triple fallback flags."""
+    the per-triple fallback flags.  params=None takes the model the library keeps for prec
+    (predictor_train)."""
     t = np.ascontiguousarray(np.asarray(triples, dtype=np.int32).reshape(-1, 3))
-    p = np.ascontiguousarray(params, dtype=np.float32)
+    p = None if params is None else np.ascontiguousarray(params, dtype=np.float32)
     fb = np.zeros(t.shape[0], dtype=np.int32)
     _check(lib().dbcsr_tune_predicted(int(prec), _ptr(p), _ptr(t), int(t.shape[0]), int(stack_len), int(reps),
                                       float(tolerance), _ptr(fb)), "tune_predicted")
@@ -593,9 +644,10 @@ def tune_predicted(params, triples, prec: int = DBCSR_FP64, stack_len: int = 500
 
 
 def mlp_predict_best(params, triples, prec: int = DBCSR_FP64):
-    """Predicted-fastest configuration of every triple (list of KernelCfg)."""
+    """Predicted-fastest configuration of every triple (list of KernelCfg); params=None takes
+    the model the library keeps for prec (predictor_train)."""
     t = np.ascontiguousarray(np.asarray(triples, dtype=np.int32).reshape(-1, 3))
-    p = np.ascontiguousarray(params, dtype=np.float32)
+    p = None if params is None else np.ascontiguousarray(params, dtype=np.float32)
     best = (KernelCfg * t.shape[0])()
     _check(lib().dbcsr_mlp_predict_best(int(prec), _ptr(p), _ptr(t), int(t.shape[0]), best, None),
            "mlp_predict_best")

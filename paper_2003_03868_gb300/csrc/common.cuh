@@ -261,8 +261,14 @@ void sign_update(dbcsr_matrix_* X, dbcsr_matrix_* Y, int order, bool correction,
 dbcsr_status sign_iterate(dbcsr_matrix_* H, double mu, const dbcsr_sign_opts* opts, dbcsr_matrix_* P,
                           dbcsr_sign_report* rep);
 
+// Streaming multiprocessors of the current device (cudaDevAttrMultiProcessorCount, queried
+// once per device and cached; 152 on a GB300).
+int num_sms();
+
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
-inline unsigned grid_for(int64_t work, int per, int64_t cap = 152 * 64) {
+// Grid of ceil(work / per) CTAs, at least 1, at most cap (default: 64 CTAs per SM).
+inline unsigned grid_for(int64_t work, int per, int64_t cap = -1) {
+    if (cap < 0) cap = (int64_t)num_sms() * 64;
     int64_t g = ceil_div(work, per);
     if (g < 1) g = 1;
     if (g > cap) g = cap;

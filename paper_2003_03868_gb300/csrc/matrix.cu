@@ -43,6 +43,20 @@ cudaMemPool_t library_pool() {
     return g_pools[dev];
 }
 
+int num_sms() {
+    static std::atomic<int> cache[kMaxDevices] = {};
+    int dev = 0;
+    DBG_CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) fail(DBCSR_ECAPACITY, "num_sms: device ordinal out of range");
+    int n = cache[dev].load(std::memory_order_relaxed);
+    if (n <= 0) {
+        DBG_CK(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev));
+        if (n <= 0) fail(DBCSR_ECUDA, "num_sms: no multiprocessors reported");
+        cache[dev].store(n, std::memory_order_relaxed);
+    }
+    return n;
+}
+
 void trim_pool(uint64_t keep_bytes) {
     int dev = 0;
     DBG_CK(cudaGetDevice(&dev));

@@ -8,8 +8,14 @@
 // Training: full-batch mean squared error, Adam.  Every kernel is deterministic:
 // gradients of a weight are summed by one thread over the samples in order, and
 // the loss by a fixed tree.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <fstream>
+#include <map>
+#include <mutex>
+#include <sstream>
+#include <tuple>
 #include <vector>
 
 #include "common.cuh"
@@ -197,12 +203,12 @@ struct MlpWork {
         }
     }
     void forward(cudaStream_t s) {
-        k_mlp_forward<<<grid_for(B, 8, 152 * 16), 256, 0, s>>>(B, nf, P.p, X.p, H1.p, H2.p, Y.p);
+        k_mlp_forward<<<grid_for(B, 8, num_sms() * 16), 256, 0, s>>>(B, nf, P.p, X.p, H1.p, H2.p, Y.p);
         DBG_LAUNCH_CK();
     }
     void gradient(cudaStream_t s) {
         forward(s);
-        k_mlp_backprop<<<grid_for(B, 8, 152 * 16), 256, 0, s>>>(B, nf, P.p, T.p, H1.p, H2.p, Y.p, DY.p, D2.p, D1.p,
+        k_mlp_backprop<<<grid_for(B, 8, num_sms() * 16), 256, 0, s>>>(B, nf, P.p, T.p, H1.p, H2.p, Y.p, DY.p, D2.p, D1.p,
                                                                 ERR.p);
         DBG_LAUNCH_CK();
         const int64_t np = n_params(nf);
@@ -244,9 +250,155 @@ void mlp_features(int prec, int m, int n, int k, const TuneCfg& c, float* f) {
     f[9] = (float)c.prefetch2;
 }
 
+// The model trained by dbcsr_predictor_train, one per precision, for the calls that take
+// params == NULL.
+std::mutex g_pred_mu;
+std::map<int, std::vector<float>> g_predictor;
+
+// One timing record of the autotuner as it is read back from a records file.
+struct Rec {
+    int prec, m, n, k;
+    TuneCfg c;
+    double ms;
+};
+
+std::vector<Rec> read_records(const char* path, int prec) {
+    if (!path) fail(DBCSR_EINVAL, "predictor: null path");
+    std::ifstream f(path);
+    if (!f) fail(DBCSR_EINVAL, std::string("predictor: cannot open ") + path);
+    std::vector<Rec> out;
+    std::string line;
+    while (std::getline(f, line)) {
+        if (line.empty() || line[0] == '#') continue;
+        std::istringstream is(line);
+        Rec r;
+        if (!(is >> r.prec >> r.m >> r.n >> r.k >> r.c.tpb >> r.c.ctas_per_sm >> r.c.colmajor >> r.c.prefetch2 >> r.ms))
+            fail(DBCSR_EINVAL, "predictor: malformed line: " + line);
+        if (r.m < 1 || r.m > kMaxBlock || r.n < 1 || r.n > kMaxBlock || r.k < 1 || r.k > kMaxBlock ||
+            r.c.tpb < 32 || r.c.tpb > 256 || r.c.tpb % 32 || r.c.ctas_per_sm < 1 || !(r.ms > 0.0) ||
+            !std::isfinite(r.ms))
+            fail(DBCSR_EINVAL, "predictor: record out of range: " + line);
+        if (r.prec == prec) out.push_back(r);
+    }
+    if (out.empty()) fail(DBCSR_EINVAL, std::string("predictor: no records of this precision in ") + path);
+    return out;
+}
+
+// The training set of the prediction model from the autotuner's timings of one precision:
+// the features of every (m, n, k, configuration) and, as the target, the log of its time
+// minus the mean log time of its (m, n, k) triple, divided by the standard deviation of
+// those centred values over all records (population form, floored at 1e-12).  The model
+// thus learns how a configuration changes the time of a triple, not the triple's size.
+void predictor_data(const std::vector<Rec>& recs, std::vector<float>& X, std::vector<float>& T) {
+    const int nf = DBCSR_MLP_FEATURES;
+    const size_t n = recs.size();
+    X.assign(n * nf, 0.f);
+    T.assign(n, 0.f);
+    std::map<std::tuple<int, int, int>, std::pair<double, int64_t>> tri;
+    std::vector<double> y(n);
+    for (size_t i = 0; i < n; ++i) {
+        const Rec& r = recs[i];
+        mlp_features(r.prec, r.m, r.n, r.k, r.c, X.data() + i * nf);
+        y[i] = std::log(r.ms);
+        auto& acc = tri[{r.m, r.n, r.k}];
+        acc.first += y[i];
+        acc.second += 1;
+    }
+    std::vector<double> t(n);
+    double mean = 0.0;
+    for (size_t i = 0; i < n; ++i) {
+        const auto& acc = tri[{recs[i].m, recs[i].n, recs[i].k}];
+        t[i] = y[i] - acc.first / (double)acc.second;
+        mean += t[i];
+    }
+    mean /= (double)n;
+    double var = 0.0;
+    for (size_t i = 0; i < n; ++i) var += (t[i] - mean) * (t[i] - mean);
+    const double sd = std::max(std::sqrt(var / (double)n), 1e-12);
+    for (size_t i = 0; i < n; ++i) T[i] = (float)(t[i] / sd);
+}
+
 }  // namespace dbg
 
 extern "C" {
+
+dbcsr_status dbcsr_tune_records_save(const char* path, const dbcsr_tune_record* recs, int64_t n, int32_t append) {
+    try {
+        if (!path || n < 0 || (n > 0 && !recs)) dbg::fail(DBCSR_EINVAL, "tune_records_save: bad argument");
+        std::ofstream f(path, append ? std::ios::app : std::ios::trunc);
+        if (!f) dbg::fail(DBCSR_EINVAL, std::string("tune_records_save: cannot open ") + path);
+        if (!append) f << "# prec m n k tpb ctas_per_sm colmajor prefetch2 ms\n";
+        f.precision(17);
+        for (int64_t i = 0; i < n; ++i) {
+            const dbcsr_tune_record& r = recs[i];
+            f << r.prec << ' ' << r.m << ' ' << r.n << ' ' << r.k << ' ' << r.cfg.tpb << ' ' << r.cfg.ctas_per_sm << ' '
+              << r.cfg.colmajor << ' ' << r.cfg.prefetch2 << ' ' << r.ms << '\n';
+        }
+        if (!f) dbg::fail(DBCSR_EINVAL, std::string("tune_records_save: write failed on ") + path);
+        dbg::set_last_error("");
+        return DBCSR_OK;
+    } catch (const dbg::Error& e) {
+        dbg::set_last_error(e.what());
+        return e.code;
+    }
+}
+
+dbcsr_status dbcsr_predictor_data(const char* tune_records, int32_t prec, float* X, float* T, int64_t cap,
+                                  int64_t* n) {
+    try {
+        if (!n || cap < 0) dbg::fail(DBCSR_EINVAL, "predictor_data: bad argument");
+        const auto recs = dbg::read_records(tune_records, prec);
+        std::vector<float> x, t;
+        dbg::predictor_data(recs, x, t);
+        *n = (int64_t)recs.size();
+        const int64_t w = std::min<int64_t>(cap, *n);
+        if (w > 0 && X) std::memcpy(X, x.data(), sizeof(float) * w * DBCSR_MLP_FEATURES);
+        if (w > 0 && T) std::memcpy(T, t.data(), sizeof(float) * w);
+        dbg::set_last_error("");
+        return DBCSR_OK;
+    } catch (const dbg::Error& e) {
+        dbg::set_last_error(e.what());
+        return e.code;
+    }
+}
+
+dbcsr_status dbcsr_predictor_train(const char* tune_records, int32_t prec, uint64_t seed, const dbcsr_mlp_opts* opts,
+                                   dbcsr_mlp_report* rep) {
+    try {
+        if (!opts) dbg::fail(DBCSR_EINVAL, "predictor_train: null opts");
+        const auto recs = dbg::read_records(tune_records, prec);
+        std::vector<float> X, T;
+        dbg::predictor_data(recs, X, T);
+        const int nf = DBCSR_MLP_FEATURES;
+        std::vector<float> params(dbg::n_params(nf));
+        dbcsr_status st = dbcsr_mlp_init(nf, seed, params.data());
+        if (st != DBCSR_OK) return st;
+        st = dbcsr_mlp_train(nf, params.data(), X.data(), T.data(), (int64_t)recs.size(), opts, rep);
+        if (st != DBCSR_OK) return st;
+        std::lock_guard<std::mutex> lk(dbg::g_pred_mu);
+        dbg::g_predictor[prec] = std::move(params);
+        dbg::set_last_error("");
+        return DBCSR_OK;
+    } catch (const dbg::Error& e) {
+        dbg::set_last_error(e.what());
+        return e.code;
+    }
+}
+
+dbcsr_status dbcsr_predictor_params(int32_t prec, float* params) {
+    try {
+        if (!params) dbg::fail(DBCSR_EINVAL, "predictor_params: null params");
+        std::lock_guard<std::mutex> lk(dbg::g_pred_mu);
+        auto it = dbg::g_predictor.find(prec);
+        if (it == dbg::g_predictor.end()) dbg::fail(DBCSR_ESTATE, "predictor_params: no model trained for this precision");
+        std::memcpy(params, it->second.data(), sizeof(float) * it->second.size());
+        dbg::set_last_error("");
+        return DBCSR_OK;
+    } catch (const dbg::Error& e) {
+        dbg::set_last_error(e.what());
+        return e.code;
+    }
+}
 
 dbcsr_status dbcsr_mlp_features(int32_t prec, const int32_t* mnk, const dbcsr_kernel_cfg* cfgs, int64_t n,
                                 float* out) {
@@ -272,7 +424,17 @@ dbcsr_status dbcsr_mlp_features(int32_t prec, const int32_t* mnk, const dbcsr_ke
 dbcsr_status dbcsr_mlp_predict_best(int32_t prec, const float* params, const int32_t* mnk, int32_t ntriples,
                                     dbcsr_kernel_cfg* best, float* best_pred) {
     try {
-        if (!params || !mnk || !best || ntriples < 1) dbg::fail(DBCSR_EINVAL, "mlp_predict_best: bad argument");
+        if (!mnk || !best || ntriples < 1) dbg::fail(DBCSR_EINVAL, "mlp_predict_best: bad argument");
+        std::vector<float> kept;
+        if (!params) {
+            // the model that dbcsr_predictor_train keeps for this precision
+            std::lock_guard<std::mutex> lk(dbg::g_pred_mu);
+            auto it = dbg::g_predictor.find(prec);
+            if (it == dbg::g_predictor.end())
+                dbg::fail(DBCSR_ESTATE, "mlp_predict_best: params NULL and no model trained for this precision");
+            kept = it->second;
+            params = kept.data();
+        }
         const auto space = dbg::tune_space(prec);
         const int nf = DBCSR_MLP_FEATURES;
         const int64_t B = (int64_t)ntriples * (int64_t)space.size();
@@ -389,7 +551,7 @@ dbcsr_status dbcsr_mlp_train(int32_t nfeat, float* params, const float* X, const
             DBG_LAUNCH_CK();
         }
         w.forward(s);
-        dbg::k_mlp_backprop<<<dbg::grid_for(B, 8, 152 * 16), 256, 0, s>>>(B, nfeat, w.P.p, w.T.p, w.H1.p, w.H2.p,
+        dbg::k_mlp_backprop<<<dbg::grid_for(B, 8, dbg::num_sms() * 16), 256, 0, s>>>(B, nfeat, w.P.p, w.T.p, w.H1.p, w.H2.p,
                                                                           w.Y.p, w.DY.p, w.D2.p, w.D1.p, w.ERR.p);
         DBG_LAUNCH_CK();
         dbg::k_sum_f32<<<1, 256, 0, s>>>(B, w.ERR.p, w.loss.p);

@@ -1199,7 +1199,7 @@ struct EventSet {
     }
 };
 
-int sym_grid(int32_t nblk) { return std::min<int32_t>(nblk, 152 * 8); }
+int sym_grid(int32_t nblk) { return std::min<int32_t>(nblk, num_sms() * 8); }
 
 __global__ void k_keep_twinned(int64_t nb, const int64_t* __restrict__ mirror, int32_t* __restrict__ keep) {
     for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nb; b += (int64_t)gridDim.x * blockDim.x)
@@ -1223,7 +1223,7 @@ void launch_smm_shape(int prec, int m, int n, int64_t cnt, const int64_t* list, 
     if (cfg.tpb < 32 || cfg.tpb > 256 || cfg.tpb % 32 || cfg.ctas_per_sm < 1)
         fail(DBCSR_EINVAL, "launch configuration out of range");
     const int wpc = cfg.tpb / 32;
-    const int64_t grid = std::min<int64_t>(ceil_div(cnt, wpc), (int64_t)152 * cfg.ctas_per_sm);
+    const int64_t grid = std::min<int64_t>(ceil_div(cnt, wpc), (int64_t)num_sms() * cfg.ctas_per_sm);
     if (is_bf16(prec)) {
         const bool split = prec == DBCSR_BF16X3;
         if (split && (!pk.a16_lo || !pk.b16_lo)) fail(DBCSR_EINVAL, "multiply: split BF16 needs the residual packs");
@@ -1244,7 +1244,7 @@ void launch_smm_shape(int prec, int m, int n, int64_t cnt, const int64_t* list, 
         SmmArgs a = sa;
         a.colmajor = cfg.colmajor;
         a.prefetch2 = cfg.prefetch2;
-        const int64_t g = pair ? std::min<int64_t>(ceil_div(cnt, wpc / 2), (int64_t)152 * cfg.ctas_per_sm) : grid;
+        const int64_t g = pair ? std::min<int64_t>(ceil_div(cnt, wpc / 2), (int64_t)num_sms() * cfg.ctas_per_sm) : grid;
         kern<<<(unsigned)g, cfg.tpb, 0, s>>>(cnt, list, a);
     }
     DBG_LAUNCH_CK();

@@ -30,7 +30,7 @@ struct SmmArgs {
 // (every C element is summed in the same order whatever the configuration).
 struct TuneCfg {
     int tpb = 256;           // threads per CTA (multiple of 32, <= 256)
-    int ctas_per_sm = 32;    // grid = min(warps needed / warps per CTA, 152 * ctas_per_sm)
+    int ctas_per_sm = 32;    // grid = min(warps needed / warps per CTA, (SM count) * ctas_per_sm)
     int colmajor = 0;        // FP64 only
     int prefetch2 = 0;       // FP64 only
 };

@@ -193,7 +193,7 @@ ChunkResult run_chunk(const Chunk& ck, dbcsr_matrix_* H, dbcsr_matrix_* P, doubl
     U.alloc(elems, s);
     DBuf<double> r2;
     r2.alloc(b, s);
-    const unsigned grid = (unsigned)std::min<int64_t>(b, 152 * 8);
+    const unsigned grid = (unsigned)std::min<int64_t>(b, (int64_t)num_sms() * 8);
     k_sub_gather<T><<<grid, 256, 0, s>>>(b, d_j.p, d_start.p, d_doff.p, d_n.p, n, H->rp.p, H->col.p, H->off.p,
                                          H->data.p, H->bs.p, mu, inv_alpha, X.p);
     DBG_LAUNCH_CK();

@@ -154,9 +154,9 @@ struct SynthStack {
             DBG_LAUNCH_CK();
             k_stride_offsets<<<grid_for(npool + 1, 256), 256, 0, s>>>(npool + 1, sb, b_po.p);
             DBG_LAUNCH_CK();
-            k_pack_synth<<<grid_for(a16.n, 256, 152 * 64), 256, 0, s>>>(npool, 0, m, k, a.p, sa, a16.p);
+            k_pack_synth<<<grid_for(a16.n, 256, num_sms() * 64), 256, 0, s>>>(npool, 0, m, k, a.p, sa, a16.p);
             DBG_LAUNCH_CK();
-            k_pack_synth<<<grid_for(b16.n, 256, 152 * 64), 256, 0, s>>>(npool, 1, k, n, b.p, sb, b16.p);
+            k_pack_synth<<<grid_for(b16.n, 256, num_sms() * 64), 256, 0, s>>>(npool, 1, k, n, b.p, sb, b16.p);
             DBG_LAUNCH_CK();
             pk.a16 = a16.p;
             pk.a_po = a_po.p;
@@ -320,7 +320,7 @@ dbcsr_status dbcsr_autotune(const int32_t* mnk, int32_t ntriples, int32_t prec, 
 dbcsr_status dbcsr_tune_predicted(int32_t prec, const float* params, const int32_t* mnk, int32_t ntriples,
                                   int64_t stack_len, int32_t reps, double tolerance, int32_t* fell_back) {
     return guard([&] {
-        if (!params || !mnk || ntriples < 1 || stack_len < 1 || reps < 1 || !(tolerance == tolerance))
+        if (!mnk || ntriples < 1 || stack_len < 1 || reps < 1 || !(tolerance == tolerance))
             dbg::fail(DBCSR_EINVAL, "tune_predicted: bad argument");
         for (int32_t t = 0; t < ntriples; ++t) dbg::check_triple(prec, mnk[3 * t], mnk[3 * t + 1], mnk[3 * t + 2]);
         std::vector<dbcsr_kernel_cfg> pred(ntriples);

@@ -6,21 +6,51 @@ import pytest
 import bench
 
 
-def test_fp64_peak_from_measured_bf16(tmp_path, monkeypatch):
+def test_derived_fp64_peak_from_measured_bf16(tmp_path, monkeypatch):
     f = tmp_path / "peaks.json"
     f.write_text(json.dumps({"bf16_tflops_sustained": 1753.8, "bf16_tflops": 1931.0, "hbm_gbs": 6782.0}))
     monkeypatch.setattr(bench, "PEAKS_FILE", str(f))
-    peak, src = bench.fp64_peak()
-    assert peak == pytest.approx(1753.8 * 1.25 / 2250.0)
-    assert src.startswith("measured")
+    assert bench.fp64_derived_peak() == pytest.approx(1753.8 * 1.25 / 2250.0)
     assert bench.bf16_peak() == (1753.8, "measured bf16 sustained")
 
 
 def test_peaks_fall_back_when_absent(tmp_path, monkeypatch):
     monkeypatch.setattr(bench, "PEAKS_FILE", str(tmp_path / "missing.json"))
-    peak, src = bench.fp64_peak()
-    assert peak == pytest.approx(1700.0 * 1.25 / 2250.0) and src.startswith("fallback")
+    assert bench.fp64_derived_peak() == pytest.approx(1700.0 * 1.25 / 2250.0)
     assert bench.bf16_peak()[1].startswith("fallback")
+
+
+def test_fp64_roofline_uses_the_measured_rate():
+    # the FP64 denominator is the higher of the two measured FP64 loops, not the derived one
+    class Lib:
+        def dbcsr_bench_peak(self, kind, iters, blocks, threads):
+            return 1055.0 if kind == 0 else 1099.0
+
+    class GB:
+        def lib(self):
+            return Lib()
+
+    class Props:
+        multi_processor_count = 152
+
+    class Cuda:
+        def current_device(self):
+            return 0
+
+        def get_device_properties(self, d):
+            return Props()
+
+    class Torch:
+        cuda = Cuda()
+
+    peak, info = bench.fp64_peak(GB(), Torch())
+    assert peak == pytest.approx(1.099) and info["fp64_dfma_measured_tflops"] == pytest.approx(1.055)
+    acc = {"flops": 10e12, "flops_low": 2e12, "ms_multiply": 9000.0, "ms_low": 1000.0, "bytes_min_fp64": 8e9,
+           "launches_fp64": 80.0}
+    roof = bench.fp64_roofline(acc, 10000.0, 2, peak, info)
+    assert roof["achieved"] == pytest.approx(8e12 / 8.0 / 1e12)
+    assert roof["frac"] == pytest.approx(1.0 / 1.099)
+    assert roof["kernel_share_of_step"] == pytest.approx(0.8)
 
 
 def test_clock_samples():

@@ -139,6 +139,36 @@ def test_mlp_predicted_configs_gain_over_default(gb):
     gb.tune_clear()
 
 
+def test_predictor_trained_in_the_library(gb, tmp_path):
+    """dbcsr_predictor_train builds the targets from the tuner's records file and trains on
+    the GPU: the same parameters as training on targets prepared in numpy from the same
+    records, and the kept model answers predictions with params=None."""
+    gb.tune_clear()
+    triples = [(13, 13, 13), (13, 5, 13), (5, 5, 5), (23, 7, 23)]
+    recs = gb.autotune(triples, gb.DBCSR_FP64, stack_len=20000, reps=2)
+    path = str(tmp_path / "recs.tune")
+    gb.tune_records_save(path, recs)
+    tri = [(r.m, r.n, r.k) for r in recs]
+    X = gb.mlp_features(tri, [r.cfg for r in recs])
+    y = np.log(np.array([r.ms for r in recs]))
+    mean = {t: np.mean([yy for tt, yy in zip(tri, y) if tt == t]) for t in set(tri)}
+    T = np.array([yy - mean[t] for t, yy in zip(tri, y)])
+    T = (T / T.std()).astype(np.float32)
+    Xl, Tl = gb.predictor_data(path)
+    np.testing.assert_array_equal(Xl, X)
+    np.testing.assert_allclose(Tl, T, rtol=1e-5, atol=1e-5)
+    p_lib, rep = gb.predictor_train(path, epochs=400, lr=2e-3, seed=3)
+    p_ref, rep_ref = gb.mlp_train(gb.mlp_init(10, seed=3), Xl, Tl, epochs=400, lr=2e-3)
+    np.testing.assert_array_equal(p_lib, p_ref)                 # deterministic training, same data
+    assert rep.loss_last < rep.loss_first
+    p_np, _ = gb.mlp_train(gb.mlp_init(10, seed=3), X, T, epochs=400, lr=2e-3)
+    np.testing.assert_allclose(p_lib, p_np, rtol=0, atol=1e-3)   # numpy-prepared targets
+    key = lambda c: (c.tpb, c.ctas_per_sm, c.colmajor, c.prefetch2)
+    held = [(7, 7, 7), (23, 23, 7)]
+    assert [key(c) for c in gb.mlp_predict_best(None, held)] == [key(c) for c in gb.mlp_predict_best(p_lib, held)]
+    gb.tune_clear()
+
+
 def test_predictor_with_exhaustive_fallback(gb):
     triples = [(13, 13, 13), (5, 13, 13)]
     params = gb.mlp_init(10, seed=5)

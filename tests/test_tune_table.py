@@ -1,6 +1,8 @@
 """The tune table's host-side logic (set, get, save, load, validation) without a GPU."""
 import os
 
+import numpy as np
+
 import pytest
 
 
@@ -55,3 +57,58 @@ def test_mlp_host_side_init_and_features(gb):
     f = gb.mlp_features([(13, 5, 13)], [gb.KernelCfg(128, 8, 1, 0)])[0]
     expect = [13 / 32, 5 / 32, 13 / 32, np.log2(845) / 15, 65 / 96, 1.0, 0.5, 0.5, 1.0, 0.0]
     np.testing.assert_allclose(f, expect, rtol=1e-6)
+
+
+def _records(gb, rng, prec, triples):
+    recs = []
+    for (m, n, k) in triples:
+        for c in gb.tune_space(prec)[::7]:
+            r = gb.TuneRecord()
+            r.m, r.n, r.k, r.prec = m, n, k, prec
+            r.cfg = c
+            r.ms = float(np.exp(rng.normal(0.0, 0.5)) * m * n * k / 1e3)
+            r.gflops = 1.0
+            recs.append(r)
+    return recs
+
+
+def test_predictor_training_data_from_records_file(gb, tmp_path):
+    # the targets dbcsr_predictor_train regresses: log time, centred per (m, n, k) triple,
+    # divided by the population standard deviation of the centred values
+    rng = np.random.default_rng(21)
+    rf = _records(gb, rng, gb.DBCSR_FP64, [(13, 5, 13), (23, 7, 23), (4, 4, 4)])
+    rb = _records(gb, rng, gb.DBCSR_BF16, [(13, 13, 13)])
+    path = str(tmp_path / "recs.tune")
+    gb.tune_records_save(path, rf[:5])
+    gb.tune_records_save(path, rf[5:] + rb, append=True)
+    X, T = gb.predictor_data(path, gb.DBCSR_FP64)
+    assert X.shape == (len(rf), gb.MLP_FEATURES) and T.shape == (len(rf),)
+    tri = [(r.m, r.n, r.k) for r in rf]
+    np.testing.assert_array_equal(X, gb.mlp_features(tri, [r.cfg for r in rf]))
+    y = np.log(np.array([r.ms for r in rf]))
+    mean = {t: np.mean([yy for tt, yy in zip(tri, y) if tt == t]) for t in set(tri)}
+    t = np.array([yy - mean[tt] for tt, yy in zip(tri, y)])
+    np.testing.assert_allclose(T, t / t.std(), rtol=1e-6, atol=1e-6)
+    for tt in set(tri):                           # centred per triple
+        assert abs(np.mean([v for v, u in zip(T, tri) if u == tt])) < 1e-5
+    assert abs(float(np.std(T.astype(np.float64))) - 1.0) < 1e-5
+    Xb, Tb = gb.predictor_data(path, gb.DBCSR_BF16)
+    assert Xb.shape[0] == len(rb)
+
+
+def test_predictor_records_are_checked(gb, tmp_path):
+    bad = tmp_path / "bad.tune"
+    bad.write_text("0 13 5 13 128 8 0 0 -1.0\n")       # a non-positive time
+    with pytest.raises(gb.DbcsrError):
+        gb.predictor_data(str(bad))
+    bad.write_text("0 13 5 13 128 8 0\n")               # a field missing
+    with pytest.raises(gb.DbcsrError):
+        gb.predictor_data(str(bad))
+    bad.write_text("# nothing\n")
+    with pytest.raises(gb.DbcsrError):
+        gb.predictor_data(str(bad))
+    with pytest.raises(gb.DbcsrError):
+        gb.predictor_data(str(tmp_path / "missing.tune"))
+    # no model trained yet for the plain BF16 precision (params == NULL is refused)
+    p = np.zeros(gb.lib().dbcsr_mlp_param_count(gb.MLP_FEATURES), dtype=np.float32)
+    assert gb.lib().dbcsr_predictor_params(99, gb._ptr(p)) == gb._ffi.DBCSR_ESTATE
