@@ -122,6 +122,21 @@ struct HostScalars {
 };
 HostScalars& host_scalars();
 
+// Groups of block rows (= block columns) read as one dense tile by the tensor-core tier
+// (lowtier.cu): at most kGroupWidth rows and kGroupMembers blocks per group.
+constexpr int kGroupWidth = 112;
+constexpr int kGroupMembers = 16;
+constexpr int32_t kMaxBlockRowsLt = 262144;
+struct Groups {
+    int32_t ngrp = 0, nblk = 0, max_members = 0;
+    std::vector<int32_t> h_w;            // host copy of the widths
+    DBuf<int32_t> g_of;                  // [nblk] group of every block
+    DBuf<int32_t> g_pos;                 // [nblk] first row of the block inside its group
+    DBuf<int32_t> g_ptr;                 // [ngrp + 1] members of group k: g_mem[g_ptr[k] .. g_ptr[k+1])
+    DBuf<int32_t> g_mem;                 // [nblk] blocks in ascending order per group
+    DBuf<int32_t> g_w;                   // [ngrp] rows of every group
+};
+
 }  // namespace dbg
 
 // The matrix object behind the opaque C handle.
@@ -144,6 +159,11 @@ struct dbcsr_matrix_ {
     bool norms_valid = false;
 
     int plans = 0;                       // live multiply plans that use this matrix's arrays
+
+    // groups of blocks for the tensor-core tier: computed from this matrix (or inherited from
+    // the operand of the product that formed it) at its first BF16 product; any partition
+    // gives the same products, the groups only decide how dense the tiles are
+    std::shared_ptr<dbg::Groups> groups;
 
     // staging area of put_block(s) before finalize
     std::vector<int32_t> st_row, st_col;
@@ -199,6 +219,7 @@ void trace_product_parts_into(dbcsr_matrix_* a, dbcsr_matrix_* b, double* part, 
 //   kSymAverage: both twins are computed and replaced by their symmetric mean
 //                (for operands that commute only approximately, e.g. BF16 products).
 constexpr int kSymNone = 0, kSymMirror = 1, kSymAverage = 2;
+struct LowTierPlan;
 // m <- (m + m^T) / 2 on the blocks that have a twin; blocks without one are dropped.
 void symmetrize(dbcsr_matrix_* m);
 // A planned product C = alpha A B on fixed patterns: the buffers its numeric phase needs
@@ -214,6 +235,8 @@ struct MultPlan {
     std::vector<DBuf<int64_t>> bufs_i64;
     std::vector<DBuf<double>> bufs_f64;
     std::vector<DBuf<__nv_bfloat16>> bufs_bf16;
+    std::vector<DBuf<uint8_t>> bufs_u8;
+    LowTierPlan* lt = nullptr;           // BF16 products: the tensor-core tier's symbolic results
     ~MultPlan();
 };
 // plan: build a plan instead of a one-off product (beta = 0, C distinct from A and B, no
@@ -223,6 +246,34 @@ void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbc
 void execute_plan(MultPlan* plan);
 // Fails with DBCSR_ESTATE when a live plan uses m's arrays (they must not be replaced).
 void check_unplanned(const dbcsr_matrix_* m, const char* where);
+
+// ---- lowtier.cu
+// Groups of neighbouring blocks from the strongest couplings (block norms) of m.
+std::shared_ptr<Groups> build_groups(dbcsr_matrix_* m);
+// Where the tensor-core tier writes: the formed blocks of the product (CSR over block rows,
+// computed flags, element offsets, C input) and the result arrays.
+struct LowTierOut {
+    const int64_t* f_rp; const int32_t* f_col; const uint8_t* f_comp; const int64_t* f_off; const int64_t* f_cin;
+    const int64_t* ci_off; const double* ci_data;
+    double alpha, beta;
+    double* c_data; double* c_norm; double* c_dev2;
+};
+struct LowTierPlan;
+void lowtier_plan_delete(LowTierPlan* p);
+// Symbolic phase of a tensor-core product: group tile patterns of A, B and C and the per-C-tile
+// stacks.  sym_operands: A and B are exactly symmetric (B's tiles are then read transposed from
+// its row-major packing, and from A's packing when B is A).
+std::unique_ptr<LowTierPlan, void (*)(LowTierPlan*)> lowtier_prepare(int prec, dbcsr_matrix_* A, dbcsr_matrix_* B,
+                                                                     std::shared_ptr<Groups> groups, bool sym_operands,
+                                                                     const int64_t* f_rp, const int32_t* f_col,
+                                                                     const uint8_t* f_comp, cudaStream_t s);
+// Numeric phase: packs A and B (their current values), then runs the tensor-core kernel.
+void lowtier_pack(LowTierPlan& L, dbcsr_matrix_* A, dbcsr_matrix_* B, cudaStream_t s);
+void lowtier_run(LowTierPlan& L, dbcsr_matrix_* A, const LowTierOut& o, cudaStream_t s);
+// Fails with DBCSR_ETIMEOUT when a bounded wait of the kernel ran out (synchronises s).
+void lowtier_check(LowTierPlan& L, cudaStream_t s);
+int64_t lowtier_entries(const LowTierPlan& L);
+int64_t lowtier_tiles(const LowTierPlan& L);
 
 // ---- submatrix.cu
 dbcsr_status submatrix_sign(dbcsr_matrix_* H, double mu, const dbcsr_sign_opts* opts, dbcsr_matrix_* P,

@@ -290,10 +290,14 @@ __global__ void k_find_mirror(int64_t nform, const int32_t* __restrict__ f_row, 
 // sym = 1 (mirror): I < J computed, I > J copied; sym = 2 (average): both twins
 // computed and then replaced by their symmetric mean; blocks without a formed twin
 // are dropped in both modes.
-__device__ __forceinline__ int block_role(int sym, int32_t I, int32_t J, int64_t mirror) {
+// grp (BF16 products, nullable): blocks are ordered by their group first, so that all the
+// computed blocks between two groups lie in one group tile of the tensor-core tier.
+__device__ __forceinline__ int block_role(int sym, int32_t I, int32_t J, int64_t mirror, const int32_t* grp) {
     if (!sym || I == J) return 0;
     if (mirror < 0) return 2;
-    return (I < J || sym == 2) ? 0 : 1;
+    if (sym == 2) return 0;
+    const bool first = grp ? (grp[I] < grp[J] || (grp[I] == grp[J] && I < J)) : I < J;
+    return first ? 0 : 1;
 }
 
 // One warp: the m x m block P becomes (P + P^T) / 2 in place; *sq and *d receive the
@@ -403,10 +407,11 @@ __global__ void k_form_stats(int64_t nform, const int32_t* __restrict__ f_row, c
                              int64_t* __restrict__ f_np, const int32_t* __restrict__ f_ksum,
                              const int64_t* __restrict__ mirror, int sym, const int32_t* __restrict__ bs,
                              unsigned long long* __restrict__ flops, unsigned long long* __restrict__ nprod,
-                             unsigned long long* __restrict__ shape_cnt, uint8_t* __restrict__ comp) {
+                             unsigned long long* __restrict__ shape_cnt, uint8_t* __restrict__ comp,
+                             const int32_t* __restrict__ grp) {
     unsigned long long lf = 0, lp = 0;
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nform; k += (int64_t)gridDim.x * blockDim.x) {
-        const bool computed = block_role(sym, f_row[k], f_col[k], mirror[k]) == 0;
+        const bool computed = block_role(sym, f_row[k], f_col[k], mirror[k], grp) == 0;
         comp[k] = computed ? 1 : 0;
         if (!computed) {
             f_np[k] = 0;
@@ -433,11 +438,12 @@ __global__ void k_form_stats(int64_t nform, const int32_t* __restrict__ f_row, c
 __global__ void k_mirror_copy(int64_t nform, int sym, const int64_t* __restrict__ mirror,
                               const int32_t* __restrict__ f_row, const int32_t* __restrict__ f_col,
                               const int64_t* __restrict__ f_off, const int32_t* __restrict__ bs,
-                              double* __restrict__ c_data, double* __restrict__ c_norm, double* __restrict__ c_dev2) {
+                              double* __restrict__ c_data, double* __restrict__ c_norm, double* __restrict__ c_dev2,
+                              const int32_t* __restrict__ grp) {
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t k = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); k < nform; k += warps) {
-        const int role = block_role(sym, f_row[k], f_col[k], mirror[k]);
+        const int role = block_role(sym, f_row[k], f_col[k], mirror[k], grp);
         if (role == 0) continue;
         if (role == 2) {
             if (lane == 0) {
@@ -764,7 +770,7 @@ __global__ void k_shape_flags(int64_t nform, const int32_t* __restrict__ f_row, 
                               int32_t* __restrict__ flag) {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nform; k += (int64_t)gridDim.x * blockDim.x) {
         const int32_t I = f_row[k], J = f_col[k];
-        flag[k] = (bs[I] == m && bs[J] == n && block_role(sym, I, J, mirror[k]) == 0) ? 1 : 0;
+        flag[k] = (bs[I] == m && bs[J] == n && block_role(sym, I, J, mirror[k], nullptr) == 0) ? 1 : 0;
     }
 }
 
@@ -1084,80 +1090,6 @@ SmmBf16Kernel bf16_kernel_t(int cls) {
 }
 SmmBf16Kernel bf16_kernel(int cls, bool split) { return split ? bf16_kernel_t<true>(cls) : bf16_kernel_t<false>(cls); }
 
-// FP64 -> BF16, one rounding to nearest (ties to even) of the 52-bit significand to
-// 7 stored bits, from the IEEE-754 encodings.  Values below the binary32 normal
-// range become signed zero, values above it infinity.
-__device__ __forceinline__ __nv_bfloat16 f64_to_bf16_rne(double x) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    const unsigned short sign = (unsigned short)((b >> 48) & 0x8000u);
-    const int e = (int)((b >> 52) & 0x7ff);
-    const unsigned long long mant = b & 0xFFFFFFFFFFFFFull;
-    unsigned short out;
-    if (e == 0x7ff) {
-        out = sign | 0x7f80u | (mant ? 0x40u : 0u);
-    } else {
-        const int eb = e - 1023 + 127;
-        if (eb >= 0xff) {
-            out = sign | 0x7f80u;
-        } else if (eb <= 0) {
-            out = sign;
-        } else {
-            unsigned long long top = ((unsigned long long)eb << 7) | (mant >> 45);
-            const unsigned long long rem = mant & ((1ull << 45) - 1), half = 1ull << 44;
-            if (rem > half || (rem == half && (top & 1ull))) top += 1;   // a carry moves into the exponent
-            out = (top >= (0xffull << 7)) ? (unsigned short)(sign | 0x7f80u) : (unsigned short)(sign | top);
-        }
-    }
-    return __ushort_as_bfloat16(out);
-}
-
-// Packed tile size of every block in a role (the offsets are their prefix sum).
-__global__ void k_pack_sizes(int64_t nb, int role, const int32_t* __restrict__ row, const int32_t* __restrict__ col,
-                             const int32_t* __restrict__ bs, int64_t* __restrict__ sz) {
-    for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nb; b += (int64_t)gridDim.x * blockDim.x)
-        sz[b] = pack_size(role, bs[row[b]], bs[col[b]]);
-}
-
-// BF16 copies of every block of a matrix (one warp per block), in mma.sync register order
-// (frag_index_a / frag_index_b), at the prefix-summed offsets po: role 0 (A): block (I, K)
-// as MT x KT sub-tiles of 16 x 16; role 1 (B): block (K, J) as NT x KT sub-tiles of 16 (k) x
-// 8 (n).  Padding is zero.  out_lo (split products): the rounded residuals x - hi.
-__global__ void k_pack_bf16(int64_t nb, int role, const int32_t* __restrict__ row, const int32_t* __restrict__ col,
-                            const int32_t* __restrict__ bs, const int64_t* __restrict__ off,
-                            const double* __restrict__ data, const int64_t* __restrict__ po,
-                            __nv_bfloat16* __restrict__ out, __nv_bfloat16* __restrict__ out_lo) {
-    const int lane = threadIdx.x & 31;
-    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t b = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); b < nb; b += warps) {
-        const int r_sz = bs[row[b]], c_sz = bs[col[b]];         // the block is r_sz x c_sz, row-major
-        const double* x = data + off[b];
-        __nv_bfloat16* o = out + po[b];
-        __nv_bfloat16* ol = out_lo ? out_lo + po[b] : nullptr;
-        if (role == 0) {                                         // A: m = r_sz rows, k = c_sz columns
-            const int R = 16 * ((r_sz + 15) / 16), L = 16 * ((c_sz + 15) / 16), KT = L / 16;
-            for (int e = lane; e < R * L; e += 32) {
-                const int i = e / L, t = e - i * L;
-                const double v = (i < r_sz && t < c_sz) ? x[i * c_sz + t] : 0.0;
-                const __nv_bfloat16 hi = f64_to_bf16_rne(v);
-                const int64_t d = frag_index_a(KT, i, t);
-                o[d] = hi;
-                if (ol) ol[d] = f64_to_bf16_rne(v - (double)__bfloat162float(hi));
-            }
-        } else {                                                 // B: k = r_sz rows, n = c_sz columns
-            const int R = 16 * ((r_sz + 15) / 16), L = 8 * ((c_sz + 7) / 8), KT = R / 16;
-            for (int e = lane; e < R * L; e += 32) {
-                const int t = e / L, c = e - t * L;
-                const double v = (t < r_sz && c < c_sz) ? x[t * c_sz + c] : 0.0;
-                const __nv_bfloat16 hi = f64_to_bf16_rne(v);
-                const int64_t d = frag_index_b(KT, t, c);
-                o[d] = hi;
-                if (ol) ol[d] = f64_to_bf16_rne(v - (double)__bfloat162float(hi));
-            }
-        }
-    }
-}
-
-
 // Planned products keep their pattern: a block (not diagonal) whose norm is below eps
 // is set to zero instead of being removed.
 __global__ void k_zero_small(int64_t nb, const int32_t* __restrict__ row, const int32_t* __restrict__ col,
@@ -1300,6 +1232,16 @@ void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbc
     if (A->stream != s) DBG_CK(cudaStreamSynchronize(A->stream));
     if (B->stream != s) DBG_CK(cudaStreamSynchronize(B->stream));
 
+    // BF16 products run on the tensor-core tier, on groups of blocks (kept with the matrices)
+    const bool bf16 = is_bf16(prec);
+    std::shared_ptr<Groups> groups = A->groups ? A->groups : B->groups;
+    if (bf16 && (!groups || groups->nblk != nblk)) {
+        groups = build_groups(A);
+        A->groups = groups;
+    }
+    if (groups && groups->nblk != nblk) groups.reset();
+    const int32_t* grp = bf16 ? groups->g_of.p : nullptr;
+
     EventSet ev;
     DBG_CK(cudaEventRecord(ev.e[0], s));
     ensure_norms(A);
@@ -1402,7 +1344,7 @@ void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbc
                                                           sym_result, A->bs.p,
                                                           (unsigned long long*)flops.p,
                                                           (unsigned long long*)nprod_exec.p,
-                                                          (unsigned long long*)shape_cnt.p, f_comp.p);
+                                                          (unsigned long long*)shape_cnt.p, f_comp.p, grp);
         DBG_LAUNCH_CK();
     }
     scan_exclusive(f_area.p, f_off.p, nform, s);
@@ -1420,12 +1362,12 @@ void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbc
 
     // 4. product stacks
     DBuf<int32_t> prod_a, prod_b, cursor;
-    prod_a.alloc(std::max<int64_t>(nprod, 1), s);
-    prod_b.alloc(std::max<int64_t>(nprod, 1), s);
+    prod_a.alloc(std::max<int64_t>(bf16 ? 1 : nprod, 1), s);
+    prod_b.alloc(std::max<int64_t>(bf16 ? 1 : nprod, 1), s);
     const size_t sm_fill = sm_rank + (size_t)max_row * (sizeof(int64_t) + sizeof(int32_t));
     const bool fill_smem = sm_fill <= (size_t)kSymSmemBudget;
-    if (!fill_smem) cursor.alloc(nf1, s);
-    if (nprod) {
+    if (!fill_smem && !bf16) cursor.alloc(nf1, s);
+    if (nprod && !bf16) {
         FillArgs fa{coff.p, keep.p, f_comp.p, kidx.p, f_pbeg.p, cursor.p, prod_a.p, prod_b.p, fill_smem ? 1 : 0};
         const size_t sm = fill_smem ? sm_fill : sm_rank;
         allow_dyn_smem(k_fill_stack, sm);
@@ -1441,31 +1383,33 @@ void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbc
     c_data.alloc(std::max<int64_t>(nel, 1), s);
     c_norm.alloc(nf1, s);
     c_dev2.alloc(nf1, s);
-    // kept by a plan: the shape lists, the BF16 packs and the launch sequence
+    // kept by a plan: the shape lists, the tensor-core tier's patterns and the launch sequence
     DBuf<int64_t> list;
-    DBuf<__nv_bfloat16> a16, b16, a16_lo, b16_lo;
-    DBuf<int64_t> a_psz, a_po, b_psz, b_po;
-    Bf16Packs pk{};
     SmmArgs sa{};
     struct ShapeLaunch { int m, n; int64_t cnt; };
     std::vector<ShapeLaunch> launches;
+    std::unique_ptr<LowTierPlan, void (*)(LowTierPlan*)> lt(nullptr, lowtier_plan_delete);
+    LowTierOut lto{};
     const int kmax = *std::max_element(A->h_bs.begin(), A->h_bs.end());
     if (nform) {
         sa = SmmArgs{f_row.p, f_col.p, f_off.p, f_pbeg.p, f_cin.p, prod_a.p, prod_b.p, A->col.p, A->off.p, A->data.p,
                      B->off.p, B->data.p, use_c ? C->off.p : nullptr, use_c ? C->data.p : nullptr, A->bs.p,
                      alpha, beta, c_data.p, c_norm.p, c_dev2.p};
-        // one launch per (m, n) block shape over that shape's blocks (kept in CSR order)
-        const bool bf16 = is_bf16(prec);
+        // FP64: one launch per (m, n) block shape over that shape's blocks (kept in CSR order)
         DBuf<int32_t> flag;
         DBuf<int64_t> pos;
-        flag.alloc(nform, s);
-        pos.alloc(nform + 1, s);
-        list.alloc(nform, s);
+        if (!bf16) {
+            flag.alloc(nform, s);
+            pos.alloc(nform + 1, s);
+            list.alloc(nform, s);
+        }
         int64_t at = 0;
         for (int m = 1; m <= kMaxBlock; ++m)
             for (int n = 1; n <= kMaxBlock; ++n) {
                 const int64_t cnt = shapes[m * (kMaxBlock + 1) + n];
                 if (!cnt) continue;
+                bytes_min += 8.0 * (double)cnt * m * n;
+                if (bf16) continue;
                 k_shape_flags<<<grid_for(nform, 256), 256, 0, s>>>(nform, f_row.p, f_col.p, A->bs.p, mirror.p,
                                                                    sym_result, m, n, flag.p);
                 DBG_LAUNCH_CK();
@@ -1473,71 +1417,33 @@ void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbc
                 k_class_scatter<<<grid_for(nform, 256), 256, 0, s>>>(nform, flag.p, pos.p, list.p + at);
                 DBG_LAUNCH_CK();
                 launches.push_back({m, n, cnt});
-                bytes_min += 8.0 * (double)cnt * m * n;
                 at += cnt;
             }
         if (bf16) {
-            // operands rounded to BF16 (nearest even) once per product, into fragment-ready copies
-            // (and, for split products, the rounded residuals x - hi); every block takes its own
-            // padded tile, placed by a prefix sum of the tile sizes
-            const bool split = prec == DBCSR_BF16X3;
-            a_psz.alloc(std::max<int64_t>(A->nnzb, 1), s);
-            a_po.alloc(A->nnzb + 1, s);
-            b_psz.alloc(std::max<int64_t>(B->nnzb, 1), s);
-            b_po.alloc(B->nnzb + 1, s);
-            if (A->nnzb) {
-                k_pack_sizes<<<grid_for(A->nnzb, 256), 256, 0, s>>>(A->nnzb, 0, A->row.p, A->col.p, A->bs.p, a_psz.p);
-                DBG_LAUNCH_CK();
-            }
-            if (B->nnzb) {
-                k_pack_sizes<<<grid_for(B->nnzb, 256), 256, 0, s>>>(B->nnzb, 1, B->row.p, B->col.p, B->bs.p, b_psz.p);
-                DBG_LAUNCH_CK();
-            }
-            scan_exclusive(a_psz.p, a_po.p, A->nnzb, s);
-            scan_exclusive(b_psz.p, b_po.p, B->nnzb, s);
-            int64_t tot[2];
-            {
-                const int64_t* src[2] = {a_po.p + A->nnzb, b_po.p + B->nnzb};
-                read_i64s(src, 2, tot, s);
-            }
-            // the kernel addresses tiles by 32-bit tile-unit offsets
-            if ((tot[0] >> 8) > 0xffffffffll || (tot[1] >> 7) > 0xffffffffll)
-                fail(DBCSR_ECAPACITY, "multiply: BF16 packs beyond 2^32 tiles");
-            a16.alloc(std::max<int64_t>(tot[0], 1), s);
-            b16.alloc(std::max<int64_t>(tot[1], 1), s);
-            if (split) {
-                a16_lo.alloc(std::max<int64_t>(tot[0], 1), s);
-                b16_lo.alloc(std::max<int64_t>(tot[1], 1), s);
-            }
-            if (A->nnzb) {
-                k_pack_bf16<<<grid_for(A->nnzb, 8), 256, 0, s>>>(A->nnzb, 0, A->row.p, A->col.p, A->bs.p, A->off.p,
-                                                                 A->data.p, a_po.p, a16.p, a16_lo.p);
-                DBG_LAUNCH_CK();
-            }
-            if (B->nnzb) {
-                k_pack_bf16<<<grid_for(B->nnzb, 8), 256, 0, s>>>(B->nnzb, 1, B->row.p, B->col.p, B->bs.p, B->off.p,
-                                                                 B->data.p, b_po.p, b16.p, b16_lo.p);
-                DBG_LAUNCH_CK();
-            }
-            pk.a16 = a16.p;
-            pk.a_po = a_po.p;
-            pk.b16 = b16.p;
-            pk.b_po = b_po.p;
-            pk.a16_lo = a16_lo.p;
-            pk.b16_lo = b16_lo.p;
+            // the tensor-core tier on groups of blocks: group tile patterns and stacks, then the
+            // operands packed (split) into tiles -- all counted with the symbolic phase
+            lt = lowtier_prepare(prec, A, B, groups, sym_result == kSymMirror, f_rp.p, f_col.p, f_comp.p, s);
+            lowtier_pack(*lt, A, B, s);
+            lto = LowTierOut{f_rp.p, f_col.p, f_comp.p, f_off.p, use_c ? f_cin.p : nullptr,
+                             use_c ? C->off.p : nullptr, use_c ? C->data.p : nullptr, alpha, beta,
+                             c_data.p, c_norm.p, c_dev2.p};
         }
         // the tuned configurations are looked up with the largest block edge as the inner size
         DBG_CK(cudaEventRecord(ev.e[1], s));
+        if (bf16) {
+            lowtier_run(*lt, A, lto, s);
+            n_smm_launches = 1;
+        }
         at = 0;
         for (const ShapeLaunch& L : launches) {
-            launch_smm_shape(prec, L.m, L.n, L.cnt, list.p + at, sa, pk, tune_lookup(prec, L.m, L.n, kmax), s);
+            launch_smm_shape(prec, L.m, L.n, L.cnt, list.p + at, sa, Bf16Packs{}, tune_lookup(prec, L.m, L.n, kmax), s);
             at += L.cnt;
         }
-        n_smm_launches = (int32_t)launches.size();
+        if (!bf16)         n_smm_launches = (int32_t)launches.size();
         if (sym_result) {
             DBG_CK(cudaEventRecord(ev.e[2], s));     // the copy / averaging is timed with the filter
             k_mirror_copy<<<grid_for(nform, 8), 256, 0, s>>>(nform, sym_result, mirror.p, f_row.p, f_col.p, f_off.p,
-                                                            A->bs.p, c_data.p, c_norm.p, c_dev2.p);
+                                                            A->bs.p, c_data.p, c_norm.p, c_dev2.p, grp);
             DBG_LAUNCH_CK();
             if (sym_result == 2) {
                 k_sym_average<<<grid_for(nform, 8), 256, 0, s>>>(nform, mirror.p, f_row.p, f_col.p, f_off.p, A->bs.p,
@@ -1567,6 +1473,7 @@ void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbc
     C->norms = std::move(c_norm);
     C->norms_valid = true;
     C->finalized = true;
+    if (groups) C->groups = groups;
 
     if (plan) {
         // 6'. a plan keeps the formed pattern: blocks under eps are zeroed, not removed, so
@@ -1587,21 +1494,14 @@ void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbc
         const int64_t l0 = g_launches.load();
         try {
             DBG_CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-            if (nform && is_bf16(prec)) {
-                if (A->nnzb) {
-                    k_pack_bf16<<<grid_for(A->nnzb, 8), 256, 0, cs>>>(A->nnzb, 0, A->row.p, A->col.p, A->bs.p,
-                                                                      A->off.p, A->data.p, a_po.p, a16.p, a16_lo.p);
-                    DBG_LAUNCH_CK();
-                }
-                if (B->nnzb) {
-                    k_pack_bf16<<<grid_for(B->nnzb, 8), 256, 0, cs>>>(B->nnzb, 1, B->row.p, B->col.p, B->bs.p,
-                                                                      B->off.p, B->data.p, b_po.p, b16.p, b16_lo.p);
-                    DBG_LAUNCH_CK();
-                }
+            if (lt) {
+                lowtier_pack(*lt, A, B, cs);
+                lowtier_run(*lt, A, lto, cs);
             }
             int64_t at = 0;
             for (const ShapeLaunch& L : launches) {
-                launch_smm_shape(prec, L.m, L.n, L.cnt, list.p + at, sa, pk, tune_lookup(prec, L.m, L.n, kmax), cs);
+                launch_smm_shape(prec, L.m, L.n, L.cnt, list.p + at, sa, Bf16Packs{}, tune_lookup(prec, L.m, L.n, kmax),
+                                 cs);
                 at += L.cnt;
             }
             zero_small(cs);
@@ -1633,13 +1533,9 @@ void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbc
         plan->bufs_i64.push_back(std::move(list));
         plan->bufs_i64.push_back(std::move(f_pbeg));
         plan->bufs_i64.push_back(std::move(f_cin));
-        plan->bufs_i64.push_back(std::move(a_po));
-        plan->bufs_i64.push_back(std::move(b_po));
         plan->bufs_f64.push_back(std::move(c_dev2));
-        plan->bufs_bf16.push_back(std::move(a16));
-        plan->bufs_bf16.push_back(std::move(b16));
-        plan->bufs_bf16.push_back(std::move(a16_lo));
-        plan->bufs_bf16.push_back(std::move(b16_lo));
+        plan->bufs_u8.push_back(std::move(f_comp));
+        plan->lt = lt.release();
         A->plans++;
         B->plans++;
         C->plans++;
@@ -1674,6 +1570,7 @@ void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbc
     if (want_dev2) det_sum(dev2k.p, nform, dsum.p, s);
     compact(C, keep2.p, C->norms.p);
     DBG_CK(cudaEventRecord(ev.e[3], s));
+    if (lt) lowtier_check(*lt, s);
 
     if (stats) {
         DBG_CK(cudaStreamSynchronize(s));
@@ -1707,6 +1604,7 @@ MultPlan::~MultPlan() {
         cudaStreamSynchronize(stream);      // no execution may still use the buffers
         cudaGraphExecDestroy(exec);
     }
+    if (lt) lowtier_plan_delete(lt);
     if (A) A->plans--;
     if (B) B->plans--;
     if (C) C->plans--;
