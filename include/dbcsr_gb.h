@@ -79,6 +79,10 @@ typedef struct {
                                   computed C blocks written once (a C input other than A, B read once) */
     int32_t n_launches;        /* block-product kernel launches (one per block shape) */
     int32_t reserved;
+    /* BF16 products (the tensor-core tier on groups of atom blocks): */
+    double flops_tensor;       /* executed MMA flops, 2 M N K per MMA, padding and every split product counted */
+    double bytes_tensor;       /* bytes its bulk copies move from global into shared memory */
+    int64_t n_tiles;           /* group tiles of C formed */
 } dbcsr_mult_stats;
 
 /* Options of the sign iteration. */
@@ -143,6 +147,8 @@ typedef struct {
     double flops_low;          /* executed 2*m*k*n of the low tier's products */
     double bytes_min_fp64;     /* sum of dbcsr_mult_stats.bytes_min over the FP64 products */
     int64_t launches_fp64;     /* sum of dbcsr_mult_stats.n_launches over the FP64 products */
+    double flops_tensor;       /* sum of dbcsr_mult_stats.flops_tensor over the low tier's products */
+    double bytes_tensor;       /* sum of dbcsr_mult_stats.bytes_tensor over the low tier's products */
 } dbcsr_sign_report;
 
 /* Last error message of the calling host thread ("" if none). */

@@ -22,7 +22,8 @@ class MultStats(C.Structure):
     _fields_ = [("n_candidates", C.c_int64), ("n_formed", C.c_int64), ("n_kept", C.c_int64),
                 ("n_products", C.c_int64), ("flops", C.c_double), ("dev2_filtered", C.c_double),
                 ("ms_symbolic", C.c_double), ("ms_numeric", C.c_double), ("ms_filter", C.c_double),
-                ("bytes_min", C.c_double), ("n_launches", C.c_int32), ("reserved", C.c_int32)]
+                ("bytes_min", C.c_double), ("n_launches", C.c_int32), ("reserved", C.c_int32),
+                ("flops_tensor", C.c_double), ("bytes_tensor", C.c_double), ("n_tiles", C.c_int64)]
 
 
 class SignOpts(C.Structure):
@@ -38,7 +39,8 @@ class SignReport(C.Structure):
                 ("ms_multiply", C.c_double), ("nnzb_x", C.c_int64),
                 ("residual_history", C.c_double * MAX_HISTORY), ("nnzb_history", C.c_int64 * MAX_HISTORY),
                 ("ms_symbolic", C.c_double), ("ms_filter", C.c_double), ("ms_low", C.c_double),
-                ("flops_low", C.c_double), ("bytes_min_fp64", C.c_double), ("launches_fp64", C.c_int64)]
+                ("flops_low", C.c_double), ("bytes_min_fp64", C.c_double), ("launches_fp64", C.c_int64),
+                ("flops_tensor", C.c_double), ("bytes_tensor", C.c_double)]
 
 
 class KernelCfg(C.Structure):

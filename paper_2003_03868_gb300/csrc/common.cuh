@@ -135,6 +135,8 @@ struct Groups {
     DBuf<int32_t> g_ptr;                 // [ngrp + 1] members of group k: g_mem[g_ptr[k] .. g_ptr[k+1])
     DBuf<int32_t> g_mem;                 // [nblk] blocks in ascending order per group
     DBuf<int32_t> g_w;                   // [ngrp] rows of every group
+    DBuf<int32_t> g_mrec;                // [nblk] per member slot (g_mem order): first row | rows << 8
+    DBuf<int32_t> g_midx;                // [nblk] member index of every block inside its group
 };
 
 }  // namespace dbg
@@ -265,15 +267,19 @@ void lowtier_plan_delete(LowTierPlan* p);
 // its row-major packing, and from A's packing when B is A).
 std::unique_ptr<LowTierPlan, void (*)(LowTierPlan*)> lowtier_prepare(int prec, dbcsr_matrix_* A, dbcsr_matrix_* B,
                                                                      std::shared_ptr<Groups> groups, bool sym_operands,
-                                                                     const int64_t* f_rp, const int32_t* f_col,
+                                                                     int64_t nform, const int64_t* f_rp,
+                                                                     const int32_t* f_row, const int32_t* f_col,
                                                                      const uint8_t* f_comp, cudaStream_t s);
 // Numeric phase: packs A and B (their current values), then runs the tensor-core kernel.
 void lowtier_pack(LowTierPlan& L, dbcsr_matrix_* A, dbcsr_matrix_* B, cudaStream_t s);
 void lowtier_run(LowTierPlan& L, dbcsr_matrix_* A, const LowTierOut& o, cudaStream_t s);
 // Fails with DBCSR_ETIMEOUT when a bounded wait of the kernel ran out (synchronises s).
 void lowtier_check(LowTierPlan& L, cudaStream_t s);
-int64_t lowtier_entries(const LowTierPlan& L);
 int64_t lowtier_tiles(const LowTierPlan& L);
+// Executed MMA flops (2 M N K per MMA, every split product, padding included) and the bytes
+// its bulk copies move into shared memory.
+double lowtier_tensor_flops(const LowTierPlan& L);
+double lowtier_copy_bytes(const LowTierPlan& L);
 
 // ---- submatrix.cu
 dbcsr_status submatrix_sign(dbcsr_matrix_* H, double mu, const dbcsr_sign_opts* opts, dbcsr_matrix_* P,

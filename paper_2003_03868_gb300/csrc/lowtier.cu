@@ -38,8 +38,11 @@ namespace dbg {
 namespace {
 
 constexpr int kTileRows = 128;                 // M of the MMA; rows of every packed tile
-constexpr int kStageBytesMax = 2 * 2 * 2 * kTileRows * 16;   // A and B steps, hi and lo: 16 KB
-constexpr int kStages = 10;
+constexpr int kGroupRows = (kGroupWidth + 7) & ~7;          // packed rows of the widest group
+constexpr int kRunMax = 2;                     // K steps per stage (one bulk copy per operand)
+constexpr int kStageBytesMax = kRunMax * 2 * 2 * 2 * kGroupRows * 16;   // 28 KB
+constexpr int kStages = 5;
+constexpr int kOutStride = kTileRows - 15;     // 113 floats per staged output row (odd: no bank conflicts)
 constexpr int kLtThreads = 192;                // producer, MMA, 4 epilogue warps
 constexpr int kTmemCols = 256;                 // two accumulators of up to 128 columns
 constexpr long long kWaitLimit = 4000000000ll; // about 2 s at 2 GHz
@@ -124,10 +127,12 @@ std::shared_ptr<Groups> build_groups(dbcsr_matrix_* M) {
     g_w.assign(ng, 0);
     for (int32_t i = 0; i < nb; ++i) g_ptr[g_of[i] + 1]++;
     for (int32_t k = 0; k < ng; ++k) g_ptr[k + 1] += g_ptr[k];
-    std::vector<int32_t> fill(g_ptr.begin(), g_ptr.end() - 1);
+    std::vector<int32_t> fill(g_ptr.begin(), g_ptr.end() - 1), g_mrec(nb), g_midx(nb);
     int max_members = 0;
     for (int32_t i = 0; i < nb; ++i) {
         const int32_t k = g_of[i];
+        g_midx[i] = fill[k] - g_ptr[k];
+        g_mrec[fill[k]] = g_w[k] | (M->h_bs[i] << 8);
         g_mem[fill[k]++] = i;
         g_pos[i] = g_w[k];
         g_w[k] += M->h_bs[i];
@@ -142,6 +147,10 @@ std::shared_ptr<Groups> build_groups(dbcsr_matrix_* M) {
     g->g_ptr.alloc(ng + 1, s);
     g->g_mem.alloc(nb, s);
     g->g_w.alloc(ng, s);
+    g->g_mrec.alloc(nb, s);
+    g->g_midx.alloc(nb, s);
+    DBG_CK(cudaMemcpyAsync(g->g_mrec.p, g_mrec.data(), sizeof(int32_t) * nb, cudaMemcpyHostToDevice, s));
+    DBG_CK(cudaMemcpyAsync(g->g_midx.p, g_midx.data(), sizeof(int32_t) * nb, cudaMemcpyHostToDevice, s));
     DBG_CK(cudaMemcpyAsync(g->g_of.p, g_of.data(), sizeof(int32_t) * nb, cudaMemcpyHostToDevice, s));
     DBG_CK(cudaMemcpyAsync(g->g_pos.p, g_pos.data(), sizeof(int32_t) * nb, cudaMemcpyHostToDevice, s));
     DBG_CK(cudaMemcpyAsync(g->g_ptr.p, g_ptr.data(), sizeof(int32_t) * (ng + 1), cudaMemcpyHostToDevice, s));
@@ -257,11 +266,30 @@ __global__ void k_gt_pattern(int32_t ngrp, GView g, const int64_t* __restrict__ 
 
 __device__ __forceinline__ int lt_ksteps(int w) { return (w + 15) >> 4; }
 
-// Packed bytes of every tile: ceil(width of its K group / 16) steps of nparts * 4 KB.
-__global__ void k_gt_bytes(int64_t nt, const int32_t* __restrict__ t_kgrp, const int32_t* __restrict__ g_w,
-                           int nparts, int64_t* __restrict__ bytes) {
+__device__ __forceinline__ int lt_rows(int w) { return (w + 7) & ~7; }
+
+// Packed bytes of every tile: ceil(width of its K group / 16) steps, each nparts x 2 chunks of
+// (width of its row group, rounded up to 8) rows x 16 bytes.
+__global__ void k_gt_bytes(int64_t nt, const int32_t* __restrict__ t_kgrp, const int32_t* __restrict__ t_rgrp,
+                           const int32_t* __restrict__ g_w, int nparts, int64_t* __restrict__ bytes) {
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nt; t += (int64_t)gridDim.x * blockDim.x)
-        bytes[t] = (int64_t)lt_ksteps(g_w[t_kgrp[t]]) * nparts * 2 * kTileRows * 16;
+        bytes[t] = (int64_t)lt_ksteps(g_w[t_kgrp[t]]) * nparts * 2 * lt_rows(g_w[t_rgrp[t]]) * 16;
+}
+
+// K steps of every tile that hold a nonzero column (bit s: columns 16 s .. 16 s + 15 of the
+// tile's K group): a block (I, K) of an A-style tile covers K's columns; a transposed (B-role)
+// tile's block (K, J) covers K's.  Steps with no block are all zero and are skipped.
+__global__ void k_gt_kmask(int64_t nb, const int32_t* __restrict__ row, const int32_t* __restrict__ col,
+                           const int32_t* __restrict__ bs, const int32_t* __restrict__ g_pos,
+                           const int32_t* __restrict__ blk_tile, int transpose, unsigned* __restrict__ kmask) {
+    for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nb; b += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t t = blk_tile[b];
+        if (t < 0) continue;
+        const int32_t K = transpose ? row[b] : col[b];
+        const int p0 = g_pos[K], p1 = p0 + bs[K] - 1;
+        const unsigned bits = ((2u << (p1 >> 4)) - 1u) & ~((1u << (p0 >> 4)) - 1u);
+        atomicOr(kmask + t, bits);
+    }
 }
 
 // For a symmetric pattern: tT[t] = the tile (c, r) of tile t = (r, c).
@@ -312,14 +340,15 @@ struct PackArgs {
     int64_t nb;
     const int32_t* row; const int32_t* col; const int64_t* off; const double* data; const int32_t* bs;
     const int32_t* blk_tile; const int64_t* t_off;
-    const int32_t* g_pos;
+    const int32_t* g_pos; const int32_t* g_of; const int32_t* g_w;
     int transpose;       // 0: block (I, K) -> rows of I, K columns of K; 1: block (K, J) -> rows of J, K of K
     int nparts;          // 1: plain BF16; 2: hi and lo
     uint8_t* pack;
 };
 
-// One warp per block: its elements into the tile, at (row, kcol) -> step kcol / 16, chunk
-// (kcol / 8) % 2, row, element kcol % 8; the lo part one chunk pair after the hi part.
+// One warp per block: its elements into the tile, at (row, kcol) -> step kcol / 16, part (hi,
+// lo), chunk (kcol / 8) % 2, row, element kcol % 8, with R = the tile's rows rounded up to 8:
+// step s at s * nparts * 2 * R * 16 bytes, chunk at R * 16, row at 16.
 __global__ void k_gt_pack(PackArgs P) {
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -331,16 +360,17 @@ __global__ void k_gt_pack(PackArgs P) {
         const int pi = P.g_pos[I], pj = P.g_pos[J];
         const double* src = P.data + P.off[b];
         uint8_t* base = P.pack + P.t_off[t];
-        const int slab = P.nparts * 2 * kTileRows * 16;
+        const int R = lt_rows(P.g_w[P.g_of[P.transpose ? J : I]]);
+        const int slab = P.nparts * 2 * R * 16;
         for (int e = lane; e < m * n; e += 32) {
             const int i = e / n, j = e - i * n;
             const int r = P.transpose ? pj + j : pi + i;
             const int kc = P.transpose ? pi + i : pj + j;
             const double x = src[e];
             const uint16_t hi = lt_bf16_bits(x);
-            uint8_t* p = base + (int64_t)(kc >> 4) * slab + ((kc >> 3) & 1) * (kTileRows * 16) + r * 16 + (kc & 7) * 2;
+            uint8_t* p = base + (int64_t)(kc >> 4) * slab + ((kc >> 3) & 1) * (R * 16) + r * 16 + (kc & 7) * 2;
             *(uint16_t*)p = hi;
-            if (P.nparts == 2) *(uint16_t*)(p + 2 * kTileRows * 16) = lt_bf16_bits(x - lt_bf16_value(hi));
+            if (P.nparts == 2) *(uint16_t*)(p + 2 * R * 16) = lt_bf16_bits(x - lt_bf16_value(hi));
         }
     }
 }
@@ -419,17 +449,75 @@ __global__ void k_gt_stack(int32_t ngrp, StackArgs S, int nwords) {
     }
 }
 
+// Per stack entry, what the kernel's producer and MMA warps need without dependent loads:
+// ea = byte offset of the A tile | the K steps where both tiles hold a nonzero column (a bit
+// mask; offsets are multiples of 4 KB), eb = byte offset of the B tile.
+__global__ void k_lt_entry_meta(int64_t ne, const int32_t* __restrict__ st_a, const int32_t* __restrict__ st_b,
+                                const unsigned* __restrict__ a_kmask, const unsigned* __restrict__ b_kmask,
+                                const int64_t* __restrict__ a_off, const int64_t* __restrict__ b_off,
+                                int64_t* __restrict__ ea, int64_t* __restrict__ eb) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < ne; e += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t ta = st_a[e], tb = st_b[e];
+        ea[e] = a_off[ta] | (int64_t)(a_kmask[ta] & b_kmask[tb] & 255u);
+        eb[e] = b_off[tb];
+    }
+}
+
+// The C tiles' tables: tbl[tile][member of I][member of J] = formed block k, for every formed
+// block the product computes (the rest of the table holds -1).
+__global__ void k_lt_ctable(int64_t nform, const int32_t* __restrict__ blk_tile, const int32_t* __restrict__ f_row,
+                            const int32_t* __restrict__ f_col, const int32_t* __restrict__ g_midx,
+                            int32_t* __restrict__ tbl) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nform; k += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t t = blk_tile[k];
+        if (t < 0) continue;
+        tbl[(int64_t)t * (kGroupMembers * kGroupMembers) + g_midx[f_row[k]] * kGroupMembers + g_midx[f_col[k]]] =
+            (int32_t)k;
+    }
+}
+
+// Work of the tensor-core kernel per C tile: live[t] = 1 if any K step of its stack is
+// multiplied (a tile without one is written as zeros); and the sums over the executed K steps
+// of 1, of N and of the copied rows, from which the MMA flops and the copied bytes follow.
+__global__ void k_lt_work(int64_t ntiles, const int64_t* __restrict__ s_ptr, const int64_t* __restrict__ ea,
+                          const int32_t* __restrict__ c_trow, const int32_t* __restrict__ c_tcol,
+                          const int32_t* __restrict__ g_w, uint8_t* __restrict__ live,
+                          unsigned long long* __restrict__ out) {
+    unsigned long long ks = 0, ksn = 0, ksr = 0;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ntiles; t += (int64_t)gridDim.x * blockDim.x) {
+        const int wc = g_w[c_tcol[t]], wr = g_w[c_trow[t]];
+        const int N = ((wc + 15) >> 4) << 4;
+        const int rows = ((wr + 7) & ~7) + ((wc + 7) & ~7);
+        unsigned long long k = 0;
+        for (int64_t e = s_ptr[t]; e < s_ptr[t + 1]; ++e) k += (unsigned long long)__popcll(ea[e] & 255);
+        live[t] = k ? 1 : 0;
+        ks += k;
+        ksn += k * N;
+        ksr += k * rows;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        ks += __shfl_xor_sync(0xffffffffu, ks, o);
+        ksn += __shfl_xor_sync(0xffffffffu, ksn, o);
+        ksr += __shfl_xor_sync(0xffffffffu, ksr, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (ks) atomicAdd(out, ks);
+        if (ksn) atomicAdd(out + 1, ksn);
+        if (ksr) atomicAdd(out + 2, ksr);
+    }
+}
+
 // ------------------------------------------------------------------ the tensor-core kernel
 struct LtArgs {
     int64_t ntiles;
     const int32_t* c_trow; const int32_t* c_tcol; const int64_t* s_ptr;
-    const int32_t* st_a; const int32_t* st_b;
-    const int32_t* a_tkgrp;                  // K group of every A tile
-    const uint8_t* a_pack; const int64_t* a_off;
-    const uint8_t* b_pack; const int64_t* b_off;
+    const int64_t* ea; const int64_t* eb;    // per stack entry: A offset | K-step mask, B offset
+    const uint8_t* t_live;                   // per C tile: 1 if any K step is multiplied
+    const uint8_t* a_pack; const uint8_t* b_pack;
     GView g;
-    const int32_t* bs;
-    const int64_t* f_rp; const int32_t* f_col; const uint8_t* f_comp; const int64_t* f_off; const int64_t* f_cin;
+    const int32_t* g_mrec;                   // per member slot: first row | rows << 8
+    const int32_t* c_tbl;                    // per C tile, 16 x 16: formed block of (row member, column member) or -1
+    const int64_t* f_off; const int64_t* f_cin;
     const int64_t* ci_off; const double* ci_data;
     double alpha, beta;
     double* c_data; double* c_norm; double* c_dev2;
@@ -439,13 +527,12 @@ struct LtArgs {
 
 struct LtShared {
     alignas(1024) uint8_t stage[kStages][kStageBytesMax];
-    double psq[kGroupMembers][kTileRows];    // per (column member, row): sum of squares
-    double pd2[kTileRows];                   // per row: squared distance to 1 of the diagonal block
+    float out[kTileRows][kOutStride];        // the finished accumulator, staged for coalesced writes
     int32_t tbl[kGroupMembers][kGroupMembers];
-    int16_t rowm[kTileRows];                 // member | (row within member) << 5, -1 beyond the width
-    int16_t colm[kTileRows];
-    int32_t rowblk[kGroupMembers];
-    int32_t colblk[kGroupMembers];
+    int64_t koff[kGroupMembers][kGroupMembers];   // element offset of the formed block
+    int64_t kcin[kGroupMembers][kGroupMembers];   // element offset of its C input, -1 without
+    int32_t rowblk[kGroupMembers], colblk[kGroupMembers];
+    int32_t rowrec[kGroupMembers], colrec[kGroupMembers];   // first row | rows << 8
     uint64_t full[kStages], empty[kStages], acc_full[2], acc_empty[2], fin;
     uint32_t tmem_base;
     int abort;                               // set once by a role whose wait ran out
@@ -459,6 +546,15 @@ __device__ __forceinline__ int lt_aborted(const LtShared& S) { return *(volatile
 __device__ __forceinline__ void lt_fail(const LtArgs& A, LtShared& S) {
     *(volatile int*)&S.abort = 1;
     atomicExch(A.err, 1);
+}
+
+// The next run of consecutive set bits of mask (at most kRunMax long): first bit and length.
+__device__ __forceinline__ int lt_next_run(unsigned& mask, int& len) {
+    const int k = __ffs(mask) - 1;
+    len = 1;
+    while (len < kRunMax && (mask & (1u << (k + len)))) ++len;
+    mask &= ~(((1u << len) - 1u) << k);
+    return k;
 }
 
 __global__ void __launch_bounds__(kLtThreads, 1) k_lowtier(LtArgs A) {
@@ -487,38 +583,57 @@ __global__ void __launch_bounds__(kLtThreads, 1) k_lowtier(LtArgs A) {
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = S.tmem_base;
-    const int slab = A.nparts * 2 * kTileRows * 16;   // bytes of one K step of one operand
+    const int np = A.nparts;
 
     if (warp == 0) {
-        // ---------------- producer: the tile's stack, K step by K step, into the stage ring
-        if (lane == 0) {
-            int stage = 0;
-            uint32_t phase = 0;
-            int64_t armed = 0;
-            for (int64_t t = blockIdx.x; t < A.ntiles && !lt_aborted(S); t += gridDim.x) {
-                for (int64_t e = A.s_ptr[t]; e < A.s_ptr[t + 1] && !lt_aborted(S); ++e) {
-                    const int32_t ta = A.st_a[e], tb = A.st_b[e];
-                    const int ks = lt_ksteps(A.g.g_w[A.a_tkgrp[ta]]);
-                    const uint8_t* pa = A.a_pack + A.a_off[ta];
-                    const uint8_t* pb = A.b_pack + A.b_off[tb];
-                    for (int k = 0; k < ks; ++k) {
-                        if (!tc::mbar_wait(&S.empty[stage], phase ^ 1u, kWaitLimit)) {
-                            lt_fail(A, S);
-                            break;
-                        }
-                        tc::mbar_arrive_expect_tx(&S.full[stage], 2 * slab);
-                        tc::bulk_g2s(S.stage[stage], pa + (int64_t)k * slab, slab, &S.full[stage]);
-                        tc::bulk_g2s(S.stage[stage] + slab, pb + (int64_t)k * slab, slab, &S.full[stage]);
-                        ++armed;
-                        if (++stage == kStages) {
-                            stage = 0;
-                            phase ^= 1u;
+        // ---------------- producer: per stack entry, the K steps where both tiles are nonzero, in
+        // runs of up to kRunMax consecutive steps, one bulk copy per operand and run.  A K step of
+        // a tile with R rows (its group's width rounded up to 8) is np x 2 chunks of R x 16 bytes.
+        // The warp fetches the metadata of 32 entries at once (one per lane); lane 0 issues.
+        int stage = 0;
+        uint32_t phase = 0;
+        int64_t armed = 0;
+        bool stop = false;
+        for (int64_t t = blockIdx.x; t < A.ntiles && !stop; t += gridDim.x) {
+            const int64_t e0 = A.s_ptr[t], e1 = A.s_ptr[t + 1];
+            const int ra = lt_rows(A.g.g_w[A.c_trow[t]]), rb = lt_rows(A.g.g_w[A.c_tcol[t]]);
+            const int sa_bytes = np * 2 * ra * 16, sb_bytes = np * 2 * rb * 16;
+            for (int64_t eb0 = e0; eb0 < e1 && !stop; eb0 += 32) {
+                const int64_t my = eb0 + lane;
+                const int64_t mea = my < e1 ? A.ea[my] : 0, meb = my < e1 ? A.eb[my] : 0;
+                const int cnt = (int)min((int64_t)32, e1 - eb0);
+                for (int x = 0; x < cnt && !stop; ++x) {
+                    const int64_t va = __shfl_sync(0xffffffffu, mea, x), vb = __shfl_sync(0xffffffffu, meb, x);
+                    if (lane == 0) {
+                        unsigned mask = (unsigned)(va & 255);
+                        const uint8_t* pa = A.a_pack + (va & ~(int64_t)255);
+                        const uint8_t* pb = A.b_pack + vb;
+                        while (mask) {
+                            int len;
+                            const int k = lt_next_run(mask, len);
+                            if (!tc::mbar_wait(&S.empty[stage], phase ^ 1u, kWaitLimit)) {
+                                lt_fail(A, S);
+                                break;
+                            }
+                            tc::mbar_arrive_expect_tx(&S.full[stage], (uint32_t)(len * (sa_bytes + sb_bytes)));
+                            tc::bulk_g2s(S.stage[stage], pa + (int64_t)k * sa_bytes, (uint32_t)(len * sa_bytes),
+                                         &S.full[stage]);
+                            tc::bulk_g2s(S.stage[stage] + len * sa_bytes, pb + (int64_t)k * sb_bytes,
+                                         (uint32_t)(len * sb_bytes), &S.full[stage]);
+                            ++armed;
+                            if (++stage == kStages) {
+                                stage = 0;
+                                phase ^= 1u;
+                            }
                         }
                     }
+                    stop = __shfl_sync(0xffffffffu, lt_aborted(S), 0) != 0;
                 }
             }
-            // no copy may still be landing in shared memory when the CTA exits: wait (bounded)
-            // for the last armed stages (after a normal run the MMA warp consumed them all)
+        }
+        // no copy may still be landing in shared memory when the CTA exits: wait (bounded)
+        // for the last armed stages (after a normal run the MMA warp consumed them all)
+        if (lane == 0)
             for (int64_t x = 0; x < armed && x < kStages; ++x) {
                 if (--stage < 0) {
                     stage = kStages - 1;
@@ -526,63 +641,81 @@ __global__ void __launch_bounds__(kLtThreads, 1) k_lowtier(LtArgs A) {
                 }
                 if (!tc::mbar_wait(&S.full[stage], phase, kWaitLimit)) lt_fail(A, S);
             }
-        }
     } else if (warp == 1) {
-        // ---------------- MMA issuer
-        if (lane == 0) {
-            int stage = 0;
-            uint32_t phase = 0;
-            int it = 0;
-            for (int64_t t = blockIdx.x; t < A.ntiles && !lt_aborted(S); t += gridDim.x, ++it) {
-                const int acc = it & 1;
-                const uint32_t acc_phase = (uint32_t)(it >> 1) & 1u;
-                if (!tc::mbar_wait(&S.acc_empty[acc], acc_phase ^ 1u, kWaitLimit)) {
-                    lt_fail(A, S);
-                    break;
-                }
+        // ---------------- MMA issuer (lane 0): the same runs as the producer, np MMAs per K step
+        // (hi*hi, then hi*lo and lo*hi for split operands); the warp fetches 32 entries' masks at once
+        int stage = 0;
+        uint32_t phase = 0;
+        int it = 0;
+        bool stop = false;
+        for (int64_t t = blockIdx.x; t < A.ntiles && !stop; t += gridDim.x, ++it) {
+            const int acc = it & 1;
+            const uint32_t acc_phase = (uint32_t)(it >> 1) & 1u;
+            const int wc = A.g.g_w[A.c_tcol[t]];
+            const int ra = lt_rows(A.g.g_w[A.c_trow[t]]), rb = lt_rows(wc);
+            const int sa_bytes = np * 2 * ra * 16, sb_bytes = np * 2 * rb * 16;
+            const uint32_t idesc = tc::instr_desc(1, kTileRows, ((wc + 15) >> 4) << 4);
+            const uint32_t d_tmem = tmem + (uint32_t)(acc * 128);
+            if (lane == 0) {
+                if (!tc::mbar_wait(&S.acc_empty[acc], acc_phase ^ 1u, kWaitLimit)) lt_fail(A, S);
                 tc::fence_after_sync();
-                const int N = ((A.g.g_w[A.c_tcol[t]] + 15) >> 4) << 4;
-                const uint32_t idesc = tc::instr_desc(1, kTileRows, N);
-                const uint32_t d_tmem = tmem + (uint32_t)(acc * 128);
-                uint32_t accumulate = 0;
-                for (int64_t e = A.s_ptr[t]; e < A.s_ptr[t + 1] && !lt_aborted(S); ++e) {
-                    const int ks = lt_ksteps(A.g.g_w[A.a_tkgrp[A.st_a[e]]]);
-                    for (int k = 0; k < ks; ++k) {
-                        if (!tc::mbar_wait(&S.full[stage], phase, kWaitLimit)) {
-                            lt_fail(A, S);
-                            break;
-                        }
-                        tc::fence_after_sync();
-                        const uint32_t sa = tc::smem_u32(S.stage[stage]);
-                        const uint32_t sb = sa + (uint32_t)slab;
-                        const uint32_t part = 2 * kTileRows * 16;   // hi -> lo
-                        const uint64_t ah = tc::smem_desc(sa, kTileRows * 16, 128);
-                        const uint64_t bh = tc::smem_desc(sb, kTileRows * 16, 128);
-                        tc::mma_f16(d_tmem, ah, bh, idesc, accumulate);
-                        accumulate = 1;
-                        if (A.nparts == 2) {
-                            const uint64_t al = tc::smem_desc(sa + part, kTileRows * 16, 128);
-                            const uint64_t bl = tc::smem_desc(sb + part, kTileRows * 16, 128);
-                            tc::mma_f16(d_tmem, ah, bl, idesc, 1);
-                            tc::mma_f16(d_tmem, al, bh, idesc, 1);
-                        }
-                        tc::mma_commit(&S.empty[stage]);         // the stage is free once these MMAs ran
-                        if (++stage == kStages) {
-                            stage = 0;
-                            phase ^= 1u;
+            }
+            stop = __shfl_sync(0xffffffffu, lt_aborted(S), 0) != 0;
+            uint32_t accumulate = 0;
+            const int64_t e0 = A.s_ptr[t], e1 = A.s_ptr[t + 1];
+            for (int64_t eb0 = e0; eb0 < e1 && !stop; eb0 += 32) {
+                const int64_t my = eb0 + lane;
+                const unsigned mym = my < e1 ? (unsigned)(A.ea[my] & 255) : 0u;
+                const int cnt = (int)min((int64_t)32, e1 - eb0);
+                for (int x = 0; x < cnt && !stop; ++x) {
+                    unsigned mask = __shfl_sync(0xffffffffu, mym, x);
+                    if (lane == 0) {
+                        while (mask) {
+                            int len;
+                            lt_next_run(mask, len);
+                            if (!tc::mbar_wait(&S.full[stage], phase, kWaitLimit)) {
+                                lt_fail(A, S);
+                                break;
+                            }
+                            tc::fence_after_sync();
+                            const uint32_t s0 = tc::smem_u32(S.stage[stage]);
+                            for (int j = 0; j < len; ++j) {
+                                const uint32_t sa = s0 + (uint32_t)(j * sa_bytes);
+                                const uint32_t sb = s0 + (uint32_t)(len * sa_bytes + j * sb_bytes);
+                                const uint64_t ah = tc::smem_desc(sa, ra * 16, 128);
+                                const uint64_t bh = tc::smem_desc(sb, rb * 16, 128);
+                                tc::mma_f16(d_tmem, ah, bh, idesc, accumulate);
+                                accumulate = 1;
+                                if (np == 2) {
+                                    const uint64_t al = tc::smem_desc(sa + 2 * ra * 16, ra * 16, 128);
+                                    const uint64_t bl = tc::smem_desc(sb + 2 * rb * 16, rb * 16, 128);
+                                    tc::mma_f16(d_tmem, ah, bl, idesc, 1);
+                                    tc::mma_f16(d_tmem, al, bh, idesc, 1);
+                                }
+                            }
+                            tc::mma_commit(&S.empty[stage]);         // the stage is free once these MMAs ran
+                            if (++stage == kStages) {
+                                stage = 0;
+                                phase ^= 1u;
+                            }
                         }
                     }
+                    stop = __shfl_sync(0xffffffffu, lt_aborted(S), 0) != 0;
                 }
-                tc::mma_commit(&S.acc_full[acc]);                // the accumulator is complete
             }
-            // every MMA this thread issued has completed before the TMEM is released
+            if (lane == 0) tc::mma_commit(&S.acc_full[acc]);      // the accumulator is complete
+        }
+        // every MMA this thread issued has completed before the TMEM is released
+        if (lane == 0) {
             tc::mma_commit(&S.fin);
             if (!tc::mbar_wait(&S.fin, 0, kWaitLimit)) lt_fail(A, S);
         }
     } else {
-        // ---------------- epilogue: warps 2..5, TMEM lanes 32 * (warp % 4) ..
+        // ---------------- epilogue: warps 2..5.  The accumulator (TMEM lanes 32 * (warp % 4) ..)
+        // is staged in shared memory, the TMEM released, then each formed atom block is written
+        // by one warp, lanes over its contiguous elements, with its norm summed in a fixed order.
         const int et = threadIdx.x - 64;                          // 0..127
-        const int q = warp & 3;
+        const int q = warp & 3, ew = et >> 5;
         const int r = 32 * q + lane;                              // tile row of this thread
         int it = 0;
         for (int64_t t = blockIdx.x; t < A.ntiles; t += gridDim.x, ++it) {
@@ -594,50 +727,34 @@ __global__ void __launch_bounds__(kLtThreads, 1) k_lowtier(LtArgs A) {
             const int32_t G = A.c_trow[t], Gc = A.c_tcol[t];
             const int32_t m0 = A.g.g_ptr[G], nm = A.g.g_ptr[G + 1] - m0;
             const int32_t n0 = A.g.g_ptr[Gc], nn = A.g.g_ptr[Gc + 1] - n0;
-            const int wr = A.g.g_w[G], wc = A.g.g_w[Gc];
-            // the atom blocks of the tile this product writes: tbl[a][b] = formed block or -1
-            for (int p = et; p < nm * nn; p += 128) {
-                const int a = p / nn, b = p - a * nn;
-                const int32_t I = A.g.g_mem[m0 + a], J = A.g.g_mem[n0 + b];
-                int64_t lo = A.f_rp[I], hi = A.f_rp[I + 1];
-                while (lo < hi) {
-                    const int64_t mid = (lo + hi) >> 1;
-                    if (A.f_col[mid] < J) lo = mid + 1; else hi = mid;
+            const int wc = A.g.g_w[Gc];
+            // the atom blocks of the tile this product writes (tables of the symbolic phase)
+            for (int p = et; p < kGroupMembers * kGroupMembers; p += 128) {
+                const int a = p >> 4, b = p & 15;
+                const int32_t k = A.c_tbl[t * (kGroupMembers * kGroupMembers) + p];
+                S.tbl[a][b] = k;
+                if (k >= 0) {
+                    S.koff[a][b] = A.f_off[k];
+                    const int64_t ci = A.f_cin ? A.f_cin[k] : -1;
+                    S.kcin[a][b] = ci >= 0 ? A.ci_off[ci] : -1;
                 }
-                const bool found = lo < A.f_rp[I + 1] && A.f_col[lo] == J && A.f_comp[lo];
-                S.tbl[a][b] = found ? (int32_t)lo : -1;
             }
-            if (et < nm) S.rowblk[et] = A.g.g_mem[m0 + et];
-            if (et < nn) S.colblk[et] = A.g.g_mem[n0 + et];
-            for (int a = et; a < kTileRows; a += 128) S.rowm[a] = -1;
-            for (int a = et; a < kTileRows; a += 128) S.colm[a] = -1;
-            lt_epi_sync();
             if (et < nm) {
-                const int32_t I = S.rowblk[et];
-                const int p0 = A.g.g_pos[I];
-                for (int i = 0; i < A.bs[I]; ++i) S.rowm[p0 + i] = (int16_t)(et | (i << 5));
+                S.rowblk[et] = A.g.g_mem[m0 + et];
+                S.rowrec[et] = A.g_mrec[m0 + et];
             }
             if (et < nn) {
-                const int32_t J = S.colblk[et];
-                const int p0 = A.g.g_pos[J];
-                for (int j = 0; j < A.bs[J]; ++j) S.colm[p0 + j] = (int16_t)(et | (j << 5));
+                S.colblk[et] = A.g.g_mem[n0 + et];
+                S.colrec[et] = A.g_mrec[n0 + et];
             }
-            for (int b = 0; b < nn; ++b) S.psq[b][r] = 0.0;
-            S.pd2[r] = 0.0;
-            lt_epi_sync();
             // every tile's accumulator phase completes (a tile without products commits no MMA
-            // and is written as zeros, but its phase is still waited for)
-            const bool empty = A.s_ptr[t] == A.s_ptr[t + 1];
-            // the TMEM loads are warp-collective: a warp reads only if all its lanes saw the phase
+            // and is written as zeros, but its phase is still waited for); the TMEM loads are
+            // warp-collective: a warp reads only if all its lanes saw the phase
+            const bool empty = !A.t_live[t];
             const bool ok = __all_sync(0xffffffffu, tc::mbar_wait(&S.acc_full[acc], acc_phase, kWaitLimit));
             if (!ok) lt_fail(A, S);
             tc::fence_after_sync();
-            const int rv = (ok && r < wr) ? S.rowm[r] : -1;
-            const int a = rv >= 0 ? (rv & 31) : 0, i = rv >= 0 ? (rv >> 5) : 0;
-            const int32_t I = S.rowblk[a];
             const int ncol = ((wc + 15) >> 4) << 4;
-            double sq = 0.0, d2 = 0.0;
-            int cur_b = -1;
             for (int c0 = 0; c0 < ncol; c0 += 16) {
                 float v[16];
                 if (!empty && ok) {
@@ -646,53 +763,44 @@ __global__ void __launch_bounds__(kLtThreads, 1) k_lowtier(LtArgs A) {
 #pragma unroll
                     for (int x = 0; x < 16; ++x) v[x] = 0.f;
                 }
-                if (rv < 0) continue;
 #pragma unroll
-                for (int x = 0; x < 16; ++x) {
-                    const int c = c0 + x;
-                    const int cv = c < wc ? S.colm[c] : -1;
-                    if (cv < 0) continue;
-                    const int b = cv & 31, j = cv >> 5;
-                    if (b != cur_b) {
-                        if (cur_b >= 0) S.psq[cur_b][r] = sq;
-                        sq = 0.0;
-                        cur_b = b;
-                    }
-                    const int64_t k = S.tbl[a][b];
-                    if (k < 0) continue;
-                    const int32_t J = S.colblk[b];
-                    const int n = A.bs[J];
-                    double val = A.alpha * (double)v[x];
-                    const int64_t ci = A.f_cin ? A.f_cin[k] : -1;
-                    if (ci >= 0) val = val + A.beta * A.ci_data[A.ci_off[ci] + (int64_t)i * n + j];
-                    A.c_data[A.f_off[k] + (int64_t)i * n + j] = val;
-                    sq = fma(val, val, sq);
-                    if (I == J) {
-                        const double w = (i == j) ? val - 1.0 : val;
-                        d2 = fma(w, w, d2);
-                    }
-                }
+                for (int x = 0; x < 16; ++x)
+                    if (c0 + x < kOutStride) S.out[r][c0 + x] = v[x];
             }
-            if (cur_b >= 0) S.psq[cur_b][r] = sq;
-            S.pd2[r] = d2;
             // the accumulator may be reused once every lane has read it
             tc::fence_before_sync();
             lt_epi_sync();
             tc::mbar_arrive(&S.acc_empty[acc]);
-            // norms and distances to 1 of the written blocks, rows summed in order
-            for (int p = et; p < nm * nn && ok; p += 128) {
-                const int aa = p / nn, bb = p - aa * nn;
-                const int32_t k = S.tbl[aa][bb];
-                if (k < 0) continue;
-                const int32_t Ia = S.rowblk[aa], Jb = S.colblk[bb];
-                const int p0 = A.g.g_pos[Ia];
-                double s2 = 0.0, dd = 0.0;
-                for (int x = 0; x < A.bs[Ia]; ++x) {
-                    s2 += S.psq[bb][p0 + x];
-                    dd += S.pd2[p0 + x];
+            if (ok) {
+                for (int p = ew; p < nm * nn; p += 4) {
+                    const int a = p / nn, b = p - a * nn;
+                    if (S.tbl[a][b] < 0) continue;
+                    const int ra0 = S.rowrec[a] & 255, m = S.rowrec[a] >> 8;
+                    const int cb0 = S.colrec[b] & 255, n = S.colrec[b] >> 8;
+                    const bool diag = S.rowblk[a] == S.colblk[b];
+                    double* out = A.c_data + S.koff[a][b];
+                    const int64_t ci = S.kcin[a][b];
+                    double sq = 0.0, d2 = 0.0;
+                    for (int e = lane; e < m * n; e += 32) {
+                        const int i = e / n, j = e - i * n;
+                        double val = A.alpha * (double)S.out[ra0 + i][cb0 + j];
+                        if (ci >= 0) val = val + A.beta * A.ci_data[ci + e];
+                        out[e] = val;
+                        sq = fma(val, val, sq);
+                        const double w = (diag && i == j) ? val - 1.0 : val;
+                        d2 = fma(w, w, d2);
+                    }
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        sq += __shfl_xor_sync(0xffffffffu, sq, o);
+                        d2 += __shfl_xor_sync(0xffffffffu, d2, o);
+                    }
+                    if (lane == 0) {
+                        const int32_t k = S.tbl[a][b];
+                        A.c_norm[k] = sqrt(sq);
+                        A.c_dev2[k] = d2;
+                    }
                 }
-                A.c_norm[k] = sqrt(s2);
-                A.c_dev2[k] = (Ia == Jb) ? dd : s2;
             }
             lt_epi_sync();
         }
@@ -746,13 +854,13 @@ TilePattern tile_pattern(const Groups& g, const int64_t* rp, const int32_t* col,
 }
 
 // Offsets of the packed tiles (bytes) and the total.
-int64_t tile_offsets(const TilePattern& P, const int32_t* t_kgrp, const Groups& g, int nparts, DBuf<int64_t>& off,
-                     cudaStream_t s) {
+int64_t tile_offsets(const TilePattern& P, const int32_t* t_kgrp, const int32_t* t_rgrp, const Groups& g, int nparts,
+                     DBuf<int64_t>& off, cudaStream_t s) {
     DBuf<int64_t> bytes;
     bytes.alloc(std::max<int64_t>(P.nt, 1), s);
     off.alloc(P.nt + 1, s);
     if (P.nt) {
-        k_gt_bytes<<<grid_for(P.nt, 256), 256, 0, s>>>(P.nt, t_kgrp, g.g_w.p, nparts, bytes.p);
+        k_gt_bytes<<<grid_for(P.nt, 256), 256, 0, s>>>(P.nt, t_kgrp, t_rgrp, g.g_w.p, nparts, bytes.p);
         DBG_LAUNCH_CK();
     }
     scan_exclusive(bytes.p, off.p, P.nt, s);
@@ -773,6 +881,10 @@ struct LowTierPlan {
     bool b_from_a_style = false;  // B's operand tiles are read from B's own rows (symmetric B)
     DBuf<int> err;
     std::shared_ptr<Groups> groups;
+    int64_t ksteps = 0, ksteps_n = 0, ksteps_rows = 0;   // over the executed K steps: 1, N, copied rows
+    DBuf<uint8_t> t_live;               // per C tile: 1 if any K step is multiplied
+    DBuf<int64_t> ea, eb;               // per entry: A offset | K steps, B offset
+    DBuf<int32_t> c_tbl;                // per C tile: 16 x 16 formed blocks
 };
 
 void lowtier_plan_delete(LowTierPlan* p) { delete p; }
@@ -784,7 +896,7 @@ void pack_operand(const dbcsr_matrix_* M, const TilePattern& P, const DBuf<int64
     if (!bytes || !M->nnzb) return;
     DBG_CK(cudaMemsetAsync(pack.p, 0, (size_t)bytes, s));
     PackArgs pa{M->nnzb, M->row.p, M->col.p, M->off.p, M->data.p, M->bs.p, P.blk_tile.p, off.p, g.g_pos.p,
-                transpose, nparts, pack.p};
+                g.g_of.p, g.g_w.p, transpose, nparts, pack.p};
     k_gt_pack<<<grid_for(M->nnzb, 8), 256, 0, s>>>(pa);
     DBG_LAUNCH_CK();
 }
@@ -793,7 +905,8 @@ void pack_operand(const dbcsr_matrix_* M, const TilePattern& P, const DBuf<int64
 
 std::unique_ptr<LowTierPlan, void (*)(LowTierPlan*)> lowtier_prepare(int prec, dbcsr_matrix_* A, dbcsr_matrix_* B,
                                                                      std::shared_ptr<Groups> groups, bool sym_operands,
-                                                                     const int64_t* f_rp, const int32_t* f_col,
+                                                                     int64_t nform, const int64_t* f_rp,
+                                                                     const int32_t* f_row, const int32_t* f_col,
                                                                      const uint8_t* f_comp, cudaStream_t s) {
     std::unique_ptr<LowTierPlan, void (*)(LowTierPlan*)> L(new LowTierPlan(), lowtier_plan_delete);
     const Groups& g = *groups;
@@ -802,7 +915,7 @@ std::unique_ptr<LowTierPlan, void (*)(LowTierPlan*)> lowtier_prepare(int prec, d
     if (g.ngrp > kMaxBlockRowsLt) fail(DBCSR_ECAPACITY, "multiply: too many groups for the tensor-core tier");
     // A: rows = A's group rows, K = its column groups
     L->ap = tile_pattern(g, A->rp.p, A->col.p, nullptr, A->nnzb, true, s);
-    L->a_bytes = tile_offsets(L->ap, L->ap.t_col.p, g, L->nparts, L->a_off, s);
+    L->a_bytes = tile_offsets(L->ap, L->ap.t_col.p, L->ap.t_row.p, g, L->nparts, L->a_off, s);
     // B: symmetric operands read their K-major tiles from the A-style tiles of the transposed
     // position; otherwise B is packed transposed (rows = its column group, K = its row group)
     L->b_is_a = sym_operands && B == A;
@@ -811,7 +924,8 @@ std::unique_ptr<LowTierPlan, void (*)(LowTierPlan*)> lowtier_prepare(int prec, d
     L->err.zero();
     if (!L->b_is_a) {
         L->bp = tile_pattern(g, B->rp.p, B->col.p, nullptr, B->nnzb, true, s);
-        L->b_bytes = tile_offsets(L->bp, sym_operands ? L->bp.t_col.p : L->bp.t_row.p, g, L->nparts, L->b_off, s);
+        L->b_bytes = tile_offsets(L->bp, sym_operands ? L->bp.t_col.p : L->bp.t_row.p,
+                                  sym_operands ? L->bp.t_row.p : L->bp.t_col.p, g, L->nparts, L->b_off, s);
     }
     const TilePattern& bpat = L->b_is_a ? L->ap : L->bp;
     if (sym_operands && bpat.nt) {
@@ -820,11 +934,17 @@ std::unique_ptr<LowTierPlan, void (*)(LowTierPlan*)> lowtier_prepare(int prec, d
                                                                L->b_map.p, L->err.p);
         DBG_LAUNCH_CK();
     }
-    // C tiles: group pairs of the atom blocks the product computes
-    const int32_t nblk = A->nblk;
-    (void)nblk;
-    L->cp = tile_pattern(g, f_rp, f_col, f_comp, 0, false, s);
+    // C tiles: group pairs of the atom blocks the product computes, and each tile's table of them
+    L->cp = tile_pattern(g, f_rp, f_col, f_comp, nform, true, s);
     L->ntiles = L->cp.nt;
+    L->c_tbl.alloc(std::max<int64_t>(L->ntiles, 1) * kGroupMembers * kGroupMembers, s);
+    if (L->ntiles) {
+        DBG_CK(cudaMemsetAsync(L->c_tbl.p, 0xff, sizeof(int32_t) * L->ntiles * kGroupMembers * kGroupMembers, s));
+        k_lt_ctable<<<grid_for(nform, 256), 256, 0, s>>>(nform, L->cp.blk_tile.p, f_row, f_col, g.g_midx.p,
+                                                          L->c_tbl.p);
+        DBG_LAUNCH_CK();
+    }
+    L->cp.blk_tile.release();
     // stacks
     const int nwords = pattern_words(g.ngrp);
     int64_t max_row = 0;
@@ -864,6 +984,48 @@ std::unique_ptr<LowTierPlan, void (*)(LowTierPlan*)> lowtier_prepare(int prec, d
         k_gt_stack<<<grid, 256, sm, s>>>(g.ngrp, sa, nwords);
         DBG_LAUNCH_CK();
     }
+    // nonzero K steps of every operand tile, and per entry those of both its tiles
+    DBuf<unsigned> a_km, b_km;
+    a_km.alloc(std::max<int64_t>(L->ap.nt, 1), s);
+    a_km.zero();
+    if (A->nnzb) {
+        k_gt_kmask<<<grid_for(A->nnzb, 256), 256, 0, s>>>(A->nnzb, A->row.p, A->col.p, A->bs.p, g.g_pos.p,
+                                                           L->ap.blk_tile.p, 0, a_km.p);
+        DBG_LAUNCH_CK();
+    }
+    if (!L->b_is_a) {
+        b_km.alloc(std::max<int64_t>(L->bp.nt, 1), s);
+        b_km.zero();
+        if (B->nnzb) {
+            k_gt_kmask<<<grid_for(B->nnzb, 256), 256, 0, s>>>(B->nnzb, B->row.p, B->col.p, B->bs.p, g.g_pos.p,
+                                                               L->bp.blk_tile.p, L->b_from_a_style ? 0 : 1, b_km.p);
+            DBG_LAUNCH_CK();
+        }
+    }
+    L->ea.alloc(std::max<int64_t>(L->nentries, 1), s);
+    L->eb.alloc(std::max<int64_t>(L->nentries, 1), s);
+    if (L->nentries) {
+        k_lt_entry_meta<<<grid_for(L->nentries, 256), 256, 0, s>>>(
+            L->nentries, L->st_a.p, L->st_b.p, a_km.p, L->b_is_a ? a_km.p : b_km.p, L->a_off.p,
+            L->b_is_a ? L->a_off.p : L->b_off.p, L->ea.p, L->eb.p);
+        DBG_LAUNCH_CK();
+    }
+    L->t_live.alloc(std::max<int64_t>(L->ntiles, 1), s);
+    if (L->ntiles) {
+        DBuf<int64_t> w;
+        w.alloc(3, s);
+        w.zero();
+        k_lt_work<<<grid_for(L->ntiles, 256), 256, 0, s>>>(L->ntiles, L->s_ptr.p, L->ea.p, L->cp.t_row.p,
+                                                            L->cp.t_col.p, g.g_w.p, L->t_live.p,
+                                                            (unsigned long long*)w.p);
+        DBG_LAUNCH_CK();
+        int64_t h[3];
+        DBG_CK(cudaMemcpyAsync(h, w.p, sizeof h, cudaMemcpyDeviceToHost, s));
+        DBG_CK(cudaStreamSynchronize(s));
+        L->ksteps = h[0];
+        L->ksteps_n = h[1];
+        L->ksteps_rows = h[2];
+    }
     L->a_pack.alloc(std::max<int64_t>(L->a_bytes, 16), s);
     if (!L->b_is_a) L->b_pack.alloc(std::max<int64_t>(L->b_bytes, 16), s);
     return L;
@@ -883,18 +1045,14 @@ void lowtier_run(LowTierPlan& L, dbcsr_matrix_* A, const LowTierOut& o, cudaStre
     a.c_trow = L.cp.t_row.p;
     a.c_tcol = L.cp.t_col.p;
     a.s_ptr = L.s_ptr.p;
-    a.st_a = L.st_a.p;
-    a.st_b = L.st_b.p;
-    a.a_tkgrp = L.ap.t_col.p;
+    a.ea = L.ea.p;
+    a.eb = L.eb.p;
+    a.t_live = L.t_live.p;
     a.a_pack = L.a_pack.p;
-    a.a_off = L.a_off.p;
     a.b_pack = L.b_is_a ? L.a_pack.p : L.b_pack.p;
-    a.b_off = L.b_is_a ? L.a_off.p : L.b_off.p;
     a.g = GView{g.g_of.p, g.g_pos.p, g.g_ptr.p, g.g_mem.p, g.g_w.p};
-    a.bs = A->bs.p;
-    a.f_rp = o.f_rp;
-    a.f_col = o.f_col;
-    a.f_comp = o.f_comp;
+    a.g_mrec = g.g_mrec.p;
+    a.c_tbl = L.c_tbl.p;
     a.f_off = o.f_off;
     a.f_cin = o.f_cin;
     a.ci_off = o.ci_off;
@@ -921,7 +1079,8 @@ void lowtier_check(LowTierPlan& L, cudaStream_t s) {
     if (e == 2) fail(DBCSR_EINVAL, "multiply: an operand declared symmetric has an asymmetric pattern");
 }
 
-int64_t lowtier_entries(const LowTierPlan& L) { return L.nentries; }
 int64_t lowtier_tiles(const LowTierPlan& L) { return L.ntiles; }
+double lowtier_tensor_flops(const LowTierPlan& L) { return 2.0 * kTileRows * 16.0 * (double)L.ksteps_n * L.nparts; }
+double lowtier_copy_bytes(const LowTierPlan& L) { return (double)L.ksteps_rows * L.nparts * 2 * 16; }
 
 }  // namespace dbg

@@ -1422,7 +1422,8 @@ void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbc
         if (bf16) {
             // the tensor-core tier on groups of blocks: group tile patterns and stacks, then the
             // operands packed (split) into tiles -- all counted with the symbolic phase
-            lt = lowtier_prepare(prec, A, B, groups, sym_result == kSymMirror, f_rp.p, f_col.p, f_comp.p, s);
+            lt = lowtier_prepare(prec, A, B, groups, sym_result == kSymMirror, nform, f_rp.p, f_row.p, f_col.p,
+                                 f_comp.p, s);
             lowtier_pack(*lt, A, B, s);
             lto = LowTierOut{f_rp.p, f_col.p, f_comp.p, f_off.p, use_c ? f_cin.p : nullptr,
                              use_c ? C->off.p : nullptr, use_c ? C->data.p : nullptr, alpha, beta,
@@ -1552,6 +1553,9 @@ void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbc
             stats->ms_filter = ev.ms(2, 3);
             stats->bytes_min = bytes_min;
             stats->n_launches = n_smm_launches;
+            stats->flops_tensor = plan->lt ? lowtier_tensor_flops(*plan->lt) : 0.0;
+            stats->bytes_tensor = plan->lt ? lowtier_copy_bytes(*plan->lt) : 0.0;
+            stats->n_tiles = plan->lt ? lowtier_tiles(*plan->lt) : 0;
         }
         return;
     }
@@ -1585,6 +1589,9 @@ void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbc
         stats->ms_filter = ev.ms(2, 3);
         stats->bytes_min = n_smm_launches ? bytes_min : 0.0;
         stats->n_launches = n_smm_launches;
+        stats->flops_tensor = lt ? lowtier_tensor_flops(*lt) : 0.0;
+        stats->bytes_tensor = lt ? lowtier_copy_bytes(*lt) : 0.0;
+        stats->n_tiles = lt ? lowtier_tiles(*lt) : 0;
     }
 }
 

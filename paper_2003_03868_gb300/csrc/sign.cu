@@ -185,6 +185,8 @@ dbcsr_status sign_iterate(dbcsr_matrix_* H, double mu, const dbcsr_sign_opts* op
         if (tier_of_product != DBCSR_FP64) {
             r.ms_low += st.ms_numeric;
             r.flops_low += st.flops;
+            r.flops_tensor += st.flops_tensor;
+            r.bytes_tensor += st.bytes_tensor;
         } else {
             r.bytes_min_fp64 += st.bytes_min;
             r.launches_fp64 += st.n_launches;
