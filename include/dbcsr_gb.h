@@ -623,6 +623,32 @@ dbcsr_status dbcsr_tune_predicted(int32_t prec, const float* params, const int32
                                   int64_t stack_len, int32_t reps, double tolerance, int32_t* fell_back);
 
 /*
+ * Sharding over several GPUs (section "DBCSR library": block rows and columns distributed over
+ * the processes, products by Cannon's algorithm with asynchronous point-to-point messages).
+ * Here a matrix is split into domains of block rows, one per rank; C = A B then needs on each
+ * rank the rows of B indexed by the block columns of its rows of A -- its own rows and a halo
+ * of neighbouring rows -- so one exchange of halo rows per product suffices and scalars
+ * (residual, traces) take one sum over the ranks.  Both calls are host-only (no GPU, no
+ * matrix handle): they take a block pattern as host arrays (row_ptr[nblk + 1], col[nnzb],
+ * columns in [0, nblk)).
+ *
+ * dbcsr_partition_rows: owner[nblk] receives the rank (0 .. nparts-1) of every block row.
+ * The domains come from recursive bisection of the block graph (I ~ J when block (I, J) is
+ * present): each part is ordered by breadth-first distance from a far block and cut at the
+ * median of the row weights (blocks per row + 1), so domains are compact regions of the
+ * coupling graph, found without coordinates.  Deterministic.  A rank may receive no row when
+ * nparts is close to nblk.  Errors: EINVAL (bad pattern, nparts outside [1, nblk]).
+ *
+ * dbcsr_halo_rows: the block rows that rank's rows reference through their block columns but
+ * that other ranks own, ascending: *n receives their number, up to cap are written to halo.
+ * Errors: EINVAL.
+ */
+dbcsr_status dbcsr_partition_rows(int32_t nblk, const int64_t* row_ptr, const int32_t* col, int32_t nparts,
+                                  int32_t* owner);
+dbcsr_status dbcsr_halo_rows(int32_t nblk, const int64_t* row_ptr, const int32_t* col, const int32_t* owner,
+                             int32_t rank, int32_t* halo, int32_t cap, int32_t* n);
+
+/*
  * Solves nsys independent systems H[s] (each symmetric, all diagonal blocks
  * present, any block sizes) as one batch: the matrices are stacked into one
  * block-diagonal matrix, so every product forms all systems' blocks in the same

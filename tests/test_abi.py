@@ -45,7 +45,7 @@ def test_version_and_error_string_without_gpu(libpath):
 
 def test_struct_layouts_match_header():
     from paper_2003_03868_gb300 import _ffi
-    assert ctypes.sizeof(_ffi.MultStats) == 11 * 8
+    assert ctypes.sizeof(_ffi.MultStats) == 14 * 8
     assert ctypes.sizeof(_ffi.SignOpts) == 8 + 8 + 4 + 4 + 8 + 8 + 4 + 4 + 4 + 4
     # 4 int32, 5 double, int64, 2 double, int64, then the histories
     assert _ffi.SignReport.residual_history.offset == 16 + 40 + 8 + 16 + 8
@@ -60,11 +60,12 @@ def test_struct_layouts_match_the_c_compiler(tmp_path):
     if not shutil.which("gcc"):
         pytest.skip("no gcc")
     probes = {
-        "dbcsr_mult_stats": (_ffi.MultStats, ["flops", "dev2_filtered", "ms_filter", "bytes_min", "n_launches"]),
+        "dbcsr_mult_stats": (_ffi.MultStats, ["flops", "dev2_filtered", "ms_filter", "bytes_min", "n_launches",
+                                               "flops_tensor", "bytes_tensor", "n_tiles"]),
         "dbcsr_sign_opts": (_ffi.SignOpts, ["switch_tol", "verbose", "flags", "order", "reserved"]),
         "dbcsr_sign_report": (_ffi.SignReport, ["alpha", "n_products", "residual_history", "nnzb_history",
                                                "ms_symbolic", "ms_low", "flops_low", "bytes_min_fp64",
-                                               "launches_fp64"]),
+                                               "launches_fp64", "flops_tensor", "bytes_tensor"]),
         "dbcsr_kernel_cfg": (_ffi.KernelCfg, ["prefetch2"]),
         "dbcsr_tune_record": (_ffi.TuneRecord, ["cfg", "ms", "gflops"]),
         "dbcsr_mlp_opts": (_ffi.MlpOpts, ["lr", "eps"]),
