@@ -466,13 +466,21 @@ dbcsr_status dbcsr_purify(dbcsr_matrix H, double n_occ, int32_t method, const db
 dbcsr_status dbcsr_sign_mu_search(dbcsr_matrix H, double n_occ, double mu_lo, double mu_hi, const dbcsr_sign_opts* opts,
                                   dbcsr_matrix P_out, double* mu_out, int32_t* evaluations, dbcsr_sign_report* rep);
 
-/* Launch configuration of the block-product kernel of one (m, n, k) stack.  No
- * field changes the arithmetic: every C element is summed in the same order. */
+/* Configuration of the FP64 block-product kernel of one (m, n, k) stack: its work split
+ * and its launch.  The launch fields leave the arithmetic unchanged (every C element is
+ * summed in the same order); split changes the rounding order only (the block norm's for a
+ * warp pair, one remainder element's for the K-split). */
+#define DBCSR_SPLIT_DEFAULT (-1) /* K-split when m n = 32 EF + 1, else a warp pair from 6 slots per lane */
+#define DBCSR_SPLIT_WARP 0       /* one warp per C block, lane l owns elements l, l + 32, ... */
+#define DBCSR_SPLIT_PAIR 1       /* two warps per C block, half of the element slots each (m n > 32, tpb % 64 == 0) */
+#define DBCSR_SPLIT_K 2          /* 32 EF elements over the lanes, the last one summed along K by all lanes
+                                    (m n = 32 EF + 1 only) */
 typedef struct {
-    int32_t tpb;          /* threads per CTA: 64, 128 or 256 */
-    int32_t ctas_per_sm;  /* grid = min(C blocks / warps per CTA, 152 * ctas_per_sm) */
-    int32_t colmajor;     /* FP64: lane-to-element order, 0 row-major, 1 column-major */
-    int32_t prefetch2;    /* FP64: 1 = fetch the next 32 products' metadata ahead */
+    int32_t tpb;          /* threads per CTA: 32 to 256, a multiple of 32 */
+    int32_t ctas_per_sm;  /* grid = min(C blocks / warps per CTA, (SM count) * ctas_per_sm) */
+    int32_t colmajor;     /* lane-to-element order, 0 row-major, 1 column-major */
+    int32_t prefetch2;    /* 1 = fetch the next 32 products' metadata ahead */
+    int32_t split;        /* DBCSR_SPLIT_* */
 } dbcsr_kernel_cfg;
 
 /* One timing of the autotuner. */
@@ -483,7 +491,11 @@ typedef struct {
     double gflops;        /* 2 m n k * stack_len / time */
 } dbcsr_tune_record;
 
-/* The configurations the autotuner times for prec (DBCSR_FP64 or DBCSR_BF16):
+/* The configurations the autotuner times (prec DBCSR_FP64; the BF16 products run on the
+ * tensor-core tier, one tile shape for every block shape, with nothing to tune per (m, n, k):
+ * EINVAL): work splits x threads per CTA x CTAs per SM x lane order x metadata prefetch.
+ * Not every configuration applies to every shape (a warp pair needs m n > 32, the K-split
+ * m n = 32 EF + 1); the tuner, the model's choice and the table skip or reject those.
  * *n receives their number; up to cap of them are written to out (may be NULL). */
 dbcsr_status dbcsr_tune_space(int32_t prec, dbcsr_kernel_cfg* out, int32_t cap, int32_t* n);
 
@@ -503,12 +515,13 @@ dbcsr_status dbcsr_tune_space(int32_t prec, dbcsr_kernel_cfg* out, int32_t cap, 
 dbcsr_status dbcsr_autotune(const int32_t* mnk, int32_t ntriples, int32_t prec, int64_t stack_len, int32_t reps,
                             dbcsr_tune_record* recs, int64_t cap, int64_t* nrec);
 
-/* Times ncfg given configurations on the synthetic (m, n, k) stack: ms_out[i]. */
+/* Times ncfg given configurations on the synthetic (m, n, k) stack: ms_out[i] (EINVAL when one
+ * does not apply to the shape). */
 dbcsr_status dbcsr_time_config(int32_t prec, int32_t m, int32_t n, int32_t k, int64_t stack_len, int32_t reps,
                                const dbcsr_kernel_cfg* cfgs, int32_t ncfg, double* ms_out);
 
 /* Tune table: set (cfg NULL removes), get (*found = 0 and the default when absent),
- * clear, and save/load as text lines "prec m n k tpb ctas_per_sm colmajor prefetch2". */
+ * clear, and save/load as text lines "prec m n k tpb ctas_per_sm colmajor prefetch2 split". */
 dbcsr_status dbcsr_tune_set(int32_t prec, int32_t m, int32_t n, int32_t k, const dbcsr_kernel_cfg* cfg);
 dbcsr_status dbcsr_tune_get(int32_t prec, int32_t m, int32_t n, int32_t k, dbcsr_kernel_cfg* cfg, int* found);
 dbcsr_status dbcsr_tune_clear(void);
@@ -524,7 +537,7 @@ dbcsr_status dbcsr_tune_load(const char* path);
  *   W1[64][nfeat], b1[64], W2[64][64], b2[64], W3[64], b3.
  * Targets are whatever the caller regresses (the tests use standardised log times).
  */
-#define DBCSR_MLP_FEATURES 10
+#define DBCSR_MLP_FEATURES 12
 
 typedef struct {
     int32_t epochs;       /* full-batch Adam steps */
@@ -546,8 +559,9 @@ int64_t dbcsr_mlp_param_count(int32_t nfeat);
 dbcsr_status dbcsr_mlp_init(int32_t nfeat, uint64_t seed, float* params);
 
 /* Features of samples (m, n, k, cfg): mnk[3i..3i+2], cfgs[i] -> out[i * DBCSR_MLP_FEATURES ...]:
- * m/32, n/32, k/32, log2(m n k)/15, useful fraction of the lanes (FP64) or tensor tiles (BF16),
- * K-split flag, tpb/256, log2(ctas_per_sm)/6, colmajor, prefetch2. */
+ * m/32, n/32, k/32, log2(m n k)/15, useful fraction of the lane slots, K-split flag, tpb/256,
+ * log2(ctas_per_sm)/6, colmajor, prefetch2, warp-pair flag, element slots per lane / 32 (the
+ * work split resolved for the shape).  EINVAL when a configuration does not apply. */
 dbcsr_status dbcsr_mlp_features(int32_t prec, const int32_t* mnk, const dbcsr_kernel_cfg* cfgs, int64_t n, float* out);
 
 /* y_out[b] = model(X[b * nfeat ...]) for B samples (host arrays; runs on the GPU). */
@@ -569,7 +583,7 @@ dbcsr_status dbcsr_mlp_predict_best(int32_t prec, const float* params, const int
 
 /*
  * The autotuner's timings as a records file (text, one record per line:
- * "prec m n k tpb ctas_per_sm colmajor prefetch2 ms", a '#' line first), the input of
+ * "prec m n k tpb ctas_per_sm colmajor prefetch2 split ms", a '#' line first), the input of
  * dbcsr_predictor_train.  append = 0 truncates the file and writes the header line;
  * append = 1 adds the records after those already there.  Errors: EINVAL (bad argument,
  * file not writable).  Not from the paper (a file format of this library).

@@ -44,7 +44,8 @@ class SignReport(C.Structure):
 
 
 class KernelCfg(C.Structure):
-    _fields_ = [("tpb", C.c_int32), ("ctas_per_sm", C.c_int32), ("colmajor", C.c_int32), ("prefetch2", C.c_int32)]
+    _fields_ = [("tpb", C.c_int32), ("ctas_per_sm", C.c_int32), ("colmajor", C.c_int32), ("prefetch2", C.c_int32),
+                ("split", C.c_int32)]
 
 
 class TuneRecord(C.Structure):
@@ -62,7 +63,7 @@ class MlpReport(C.Structure):
                 ("reserved", C.c_int32)]
 
 
-MLP_FEATURES = 10
+MLP_FEATURES = 12
 
 # (name, restype, argtypes) of every exported entry point
 P = C.c_void_p

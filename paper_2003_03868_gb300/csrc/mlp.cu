@@ -235,19 +235,24 @@ uint64_t splitmix(uint64_t& s) {
 
 // Features of one (m, n, k, configuration) sample, kMlpFeatures of them.
 void mlp_features(int prec, int m, int n, int k, const TuneCfg& c, float* f) {
+    (void)prec;
     const int mn = m * n;
-    const double lanes = 32.0 * ((mn + 31) / 32);
-    const double tiles = 16.0 * ((m + 15) / 16) * 8.0 * ((n + 7) / 8);
+    const int split = resolve_split(m, n, c);
+    const int E = (mn + 31) / 32;                                     // element slots per lane, one warp
+    const double lanes = 32.0 * (split == kSplitK ? (mn >> 5) + 1 : E);
+    const int el = split == kSplitPair ? (E + 1) / 2 : (split == kSplitK ? (mn >> 5) : E);
     f[0] = m / 32.f;
     f[1] = n / 32.f;
     f[2] = k / 32.f;
     f[3] = (float)(std::log2((double)mn * k) / 15.0);
-    f[4] = (float)(is_bf16(prec) ? mn / tiles : mn / lanes);          // useful fraction of the lanes / tiles
-    f[5] = (!is_bf16(prec) && mn > 32 && (mn & 31) == 1) ? 1.f : 0.f;  // K-split remainder kernel
+    f[4] = (float)(mn / lanes);                                       // useful fraction of the lane slots
+    f[5] = split == kSplitK ? 1.f : 0.f;                              // K-split remainder kernel
     f[6] = c.tpb / 256.f;
     f[7] = (float)(std::log2((double)c.ctas_per_sm) / 6.0);
     f[8] = (float)c.colmajor;
     f[9] = (float)c.prefetch2;
+    f[10] = split == kSplitPair ? 1.f : 0.f;                          // warp pair
+    f[11] = el / 32.f;                                                // element slots (registers) per lane
 }
 
 // The model trained by dbcsr_predictor_train, one per precision, for the calls that take
@@ -272,11 +277,11 @@ std::vector<Rec> read_records(const char* path, int prec) {
         if (line.empty() || line[0] == '#') continue;
         std::istringstream is(line);
         Rec r;
-        if (!(is >> r.prec >> r.m >> r.n >> r.k >> r.c.tpb >> r.c.ctas_per_sm >> r.c.colmajor >> r.c.prefetch2 >> r.ms))
+        if (!(is >> r.prec >> r.m >> r.n >> r.k >> r.c.tpb >> r.c.ctas_per_sm >> r.c.colmajor >> r.c.prefetch2 >>
+              r.c.split >> r.ms))
             fail(DBCSR_EINVAL, "predictor: malformed line: " + line);
         if (r.m < 1 || r.m > kMaxBlock || r.n < 1 || r.n > kMaxBlock || r.k < 1 || r.k > kMaxBlock ||
-            r.c.tpb < 32 || r.c.tpb > 256 || r.c.tpb % 32 || r.c.ctas_per_sm < 1 || !(r.ms > 0.0) ||
-            !std::isfinite(r.ms))
+            !cfg_valid(r.m, r.n, r.c) || !(r.ms > 0.0) || !std::isfinite(r.ms))
             fail(DBCSR_EINVAL, "predictor: record out of range: " + line);
         if (r.prec == prec) out.push_back(r);
     }
@@ -327,12 +332,12 @@ dbcsr_status dbcsr_tune_records_save(const char* path, const dbcsr_tune_record* 
         if (!path || n < 0 || (n > 0 && !recs)) dbg::fail(DBCSR_EINVAL, "tune_records_save: bad argument");
         std::ofstream f(path, append ? std::ios::app : std::ios::trunc);
         if (!f) dbg::fail(DBCSR_EINVAL, std::string("tune_records_save: cannot open ") + path);
-        if (!append) f << "# prec m n k tpb ctas_per_sm colmajor prefetch2 ms\n";
+        if (!append) f << "# prec m n k tpb ctas_per_sm colmajor prefetch2 split ms\n";
         f.precision(17);
         for (int64_t i = 0; i < n; ++i) {
             const dbcsr_tune_record& r = recs[i];
             f << r.prec << ' ' << r.m << ' ' << r.n << ' ' << r.k << ' ' << r.cfg.tpb << ' ' << r.cfg.ctas_per_sm << ' '
-              << r.cfg.colmajor << ' ' << r.cfg.prefetch2 << ' ' << r.ms << '\n';
+              << r.cfg.colmajor << ' ' << r.cfg.prefetch2 << ' ' << r.cfg.split << ' ' << r.ms << '\n';
         }
         if (!f) dbg::fail(DBCSR_EINVAL, std::string("tune_records_save: write failed on ") + path);
         dbg::set_last_error("");
@@ -410,7 +415,9 @@ dbcsr_status dbcsr_mlp_features(int32_t prec, const int32_t* mnk, const dbcsr_ke
             c.ctas_per_sm = cfgs[i].ctas_per_sm;
             c.colmajor = cfgs[i].colmajor;
             c.prefetch2 = cfgs[i].prefetch2;
-            if (c.ctas_per_sm < 1) dbg::fail(DBCSR_EINVAL, "mlp_features: ctas_per_sm must be >= 1");
+            c.split = cfgs[i].split;
+            if (!dbg::cfg_valid(mnk[3 * i], mnk[3 * i + 1], c))
+                dbg::fail(DBCSR_EINVAL, "mlp_features: configuration out of range for the shape");
             dbg::mlp_features(prec, mnk[3 * i], mnk[3 * i + 1], mnk[3 * i + 2], c, out + i * DBCSR_MLP_FEATURES);
         }
         dbg::set_last_error("");
@@ -449,11 +456,14 @@ dbcsr_status dbcsr_mlp_predict_best(int32_t prec, const float* params, const int
         DBG_CK(cudaMemcpyAsync(Y.data(), w.Y.p, sizeof(float) * B, cudaMemcpyDeviceToHost, s));
         DBG_CK(cudaStreamSynchronize(s));
         for (int32_t t = 0; t < ntriples; ++t) {
-            size_t arg = 0;
-            for (size_t c = 1; c < space.size(); ++c)
-                if (Y[t * space.size() + c] < Y[t * space.size() + arg]) arg = c;
+            // the lowest prediction among the configurations that apply to the triple's shape
+            int64_t arg = -1;
+            for (size_t c = 0; c < space.size(); ++c) {
+                if (!dbg::cfg_valid(mnk[3 * t], mnk[3 * t + 1], space[c])) continue;
+                if (arg < 0 || Y[t * space.size() + c] < Y[t * space.size() + arg]) arg = (int64_t)c;
+            }
             const dbg::TuneCfg& b = space[arg];
-            best[t] = dbcsr_kernel_cfg{b.tpb, b.ctas_per_sm, b.colmajor, b.prefetch2};
+            best[t] = dbcsr_kernel_cfg{b.tpb, b.ctas_per_sm, b.colmajor, b.prefetch2, b.split};
             if (best_pred) best_pred[t] = Y[t * space.size() + arg];
         }
         dbg::set_last_error("");

@@ -19,8 +19,8 @@
 //  5. k_smm_f64      output-stationary batched small GEMM: one warp (or a pair of
 //                    warps for large blocks) owns one C block and sums its
 //                    products in stack order (no atomics); the epilogue applies
-//                    alpha/beta and writes the block norm.  k_smm_bf16 is the
-//                    tensor-core counterpart (plain or split BF16 operands).
+//                    alpha/beta and writes the block norm.  BF16 products run on
+//                    the tensor-core tier instead (lowtier.cu).
 //     With a symmetric result only the blocks I <= J are computed; k_mirror_copy
 //     copies the others as transposes and k_sym_diag takes the symmetric part of
 //     the diagonal blocks.
@@ -790,7 +790,7 @@ template <int... Es>
 struct SmmTable {
     static SmmKernel get(int e, bool pair) {
         SmmKernel t[] = {nullptr, &k_smm_f64<Es, false>...};
-        SmmKernel tp[] = {nullptr, &k_smm_f64<Es, (Es >= kPairMinE)>...};
+        SmmKernel tp[] = {nullptr, &k_smm_f64<Es, (Es >= 2)>...};
         if (e < 1 || e > (int)sizeof...(Es)) return nullptr;
         return pair ? tp[e] : t[e];
     }
@@ -813,282 +813,7 @@ SmmKernel f64_kernel(int cls, bool pair) {
     if (cls > kF64ClassKs1 && cls < kF64Classes) return SmmF64Ks1::get(cls - kF64ClassKs1);
     return SmmF64::get(cls, pair);
 }
-bool f64_class_pairs(int cls) { return cls >= kPairMinE && cls <= 32; }
 
-
-// ------------------------------------------------------------ BF16 tensor-core SMM
-// BF16 operands (rounded to nearest even from FP64), FP32 accumulation on the
-// tensor cores (mma.sync m16n8k16), FP64 epilogue.  Before the products, every
-// block is packed once into fragment order: an A-role copy of block (I, K) holds its
-// m x k values as MT x KT zero-padded 16 x 16 sub-tiles, each stored as the four
-// 32-bit A registers of lane 0, then of lane 1, ... (512 B); a B-role copy of block
-// (K, J) holds NT x KT zero-padded 16 (k) x 8 (n) sub-tiles as the two B registers of
-// each lane (256 B).  A lane thus fetches its A fragment with one 128-bit load and
-// its B fragment with one 64-bit load, and a warp's load is one contiguous, aligned
-// run of 512 or 256 bytes.  Blocks sit at prefix-summed offsets, so a product's
-// operands are found from its block index alone.  One warp owns one C block
-// (m <= 16 MT, n <= 8 NT) and issues KT x MT x NT MMAs per product -- no
-// shared-memory staging.  Zero padding adds nothing to the sums.
-//
-// Register layout of m16n8k16 (gid = lane / 4, tig = lane % 4): A register j holds
-// A[gid + 8 (j & 1)][2 tig + 8 (j >> 1) + {0, 1}]; B register j holds
-// B[2 tig + 8 j + {0, 1}][gid].
-__host__ __device__ __forceinline__ int64_t frag_index_a(int KT, int i, int t) {
-    // element (i, t) of an A-role block (row i < 16 MT, column t < 16 KT)
-    const int mt = i >> 4, kt = t >> 4, ii = i & 15, tt = t & 15;
-    const int lane = (ii & 7) * 4 + ((tt & 7) >> 1);
-    const int j = (ii >> 3) | ((tt >> 3) << 1);
-    return ((int64_t)(mt * KT + kt) * 32 + lane) * 8 + j * 2 + (tt & 1);
-}
-__host__ __device__ __forceinline__ int64_t frag_index_b(int KT, int t, int c) {
-    // element (t, c) of a B-role block (row t < 16 KT along k, column c < 8 NT along n)
-    const int nt = c >> 3, kt = t >> 4, cc = c & 7, tt = t & 15;
-    const int lane = cc * 4 + ((tt & 7) >> 1);
-    const int j = tt >> 3;
-    return ((int64_t)(nt * KT + kt) * 32 + lane) * 4 + j * 2 + (tt & 1);
-}
-
-__device__ __forceinline__ void mma_bf16(float* c, uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t b0,
-                                         uint32_t b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
-
-struct SmmBf16Args {
-    SmmArgs base;
-    const __nv_bfloat16* a16;   // A-role packed blocks, block b at a16 + a_po[b]
-    const int64_t* a_po;
-    const __nv_bfloat16* b16;   // B-role packed (transposed) blocks, block b at b16 + b_po[b]
-    const int64_t* b_po;
-    const __nv_bfloat16* a16_lo;   // SPLIT: packed residuals, same layout
-    const __nv_bfloat16* b16_lo;
-};
-
-// One pipeline stage of a warp: the fragments of one unit (a product's 16-wide k-slice)
-// as each lane's own bytes -- MT A sub-tiles (16 B per lane each), NT B sub-tiles (8 B per
-// lane each), then the same for the residuals when SPLIT.
-__host__ __device__ constexpr int bf16_stage_bytes(int MT, int NT, bool split) {
-    return (MT * 512 + NT * 256) * (split ? 2 : 1);
-}
-// Units in flight per warp: as many stages as fit in 12 KB, between 2 and 8.
-__host__ __device__ constexpr int bf16_stages(int MT, int NT, bool split) {
-    return 12288 / bf16_stage_bytes(MT, NT, split) < 2 ? 2
-           : (12288 / bf16_stage_bytes(MT, NT, split) > 8 ? 8 : 12288 / bf16_stage_bytes(MT, NT, split));
-}
-
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async8(uint32_t dst, const void* src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(dst), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
-
-// Product metadata of 32 consecutive stack entries, one per lane: packed-tile offsets of
-// its A and B blocks and its inner size k.
-// Offsets in tile units (A tiles are multiples of 256 elements, B tiles of 128), so that
-// they fit 32 bits and a metadata shuffle is one instruction.
-struct BfMeta {
-    uint32_t ao, bo;
-    int kq;
-};
-__device__ __forceinline__ BfMeta bf_meta(const SmmBf16Args& G, int64_t base, int64_t pe, int lane) {
-    BfMeta m{0, 0, 0};
-    if (base + lane < pe) {
-        const int32_t ai = G.base.prod_a[base + lane], bi = G.base.prod_b[base + lane];
-        m.ao = (uint32_t)(G.a_po[ai] >> 8);
-        m.bo = (uint32_t)(G.b_po[bi] >> 7);
-        m.kq = G.base.bs[G.base.a_col[ai]];
-    }
-    return m;
-}
-
-// SPLIT (DBCSR_BF16X3): operands x = hi + lo, both BF16; per fragment set three MMAs
-// accumulate hi*hi + hi*lo + lo*hi in FP32 (the lo*lo term, ~2^-16 relative, is left out).
-//
-// Each warp streams its C block's units (product q, k-slice kt) through a ring of S
-// shared-memory stages: the fragments of unit u + S - 1 are copied with cp.async while
-// unit u is multiplied, so up to S - 1 units' loads are in flight per warp.  A lane copies
-// only the bytes of its own fragments and reads only those back, so the per-thread
-// cp.async group waits are the only synchronisation.  Every accumulator sees its MMAs in
-// the order (q, kt, hi*hi, hi*lo, lo*hi).
-template <int MT, int NT, bool SPLIT>
-__global__ void __launch_bounds__(256, 2) k_smm_bf16(int64_t nlist, const int64_t* __restrict__ list, SmmBf16Args G) {
-    constexpr int SB = bf16_stage_bytes(MT, NT, SPLIT), NS = bf16_stages(MT, NT, SPLIT);
-    constexpr int A_OFF_LO = MT * 512 + NT * 256, B_OFF = MT * 512;
-    extern __shared__ __align__(16) unsigned char bf_smem[];
-    const SmmArgs& S = G.base;
-    const int lane = threadIdx.x & 31, gid = lane >> 2, tig = lane & 3, warp = threadIdx.x >> 5;
-    const uint32_t ring = (uint32_t)__cvta_generic_to_shared(bf_smem) + (uint32_t)(warp * NS * SB);
-    const unsigned char* ring_ptr = bf_smem + warp * NS * SB;
-    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; w < nlist; w += warps) {
-        const int64_t k = list[w];
-        const int I = S.f_row[k], J = S.f_col[k];
-        const int m = S.bs[I], n = S.bs[J];
-        float acc[MT][NT][4];
-#pragma unroll
-        for (int mt = 0; mt < MT; ++mt)
-#pragma unroll
-            for (int nt = 0; nt < NT; ++nt)
-#pragma unroll
-                for (int i = 0; i < 4; ++i) acc[mt][nt][i] = 0.f;
-        const int64_t pb = S.f_pbeg[k], pe = S.f_pbeg[k + 1];
-        const int64_t np = pe - pb;
-        // metadata of the consumer's batch (cur) and the next one (nxt); the producer runs at
-        // most NS - 1 < 32 units ahead, so it never needs a later batch
-        BfMeta cur = bf_meta(G, pb, pe, lane), nxt = bf_meta(G, pb + 32, pe, lane);
-        int64_t cbat = 0;                       // consumer's batch index
-        int64_t pp = 0;                         // producer: product index (from pb) and k-slice
-        int ktp = 0, slot_p = 0;
-        auto produce = [&]() {
-            if (pp < np) {
-                const bool in_cur = (pp >> 5) == cbat;
-                const int src = (int)(pp & 31);
-                const int64_t ao = (int64_t)__shfl_sync(0xffffffffu, in_cur ? cur.ao : nxt.ao, src) << 8;
-                const int64_t bo = (int64_t)__shfl_sync(0xffffffffu, in_cur ? cur.bo : nxt.bo, src) << 7;
-                const int KT = (__shfl_sync(0xffffffffu, in_cur ? cur.kq : nxt.kq, src) + 15) >> 4;
-                const uint32_t st = ring + (uint32_t)(slot_p * SB);
-                const unsigned char* ag = reinterpret_cast<const unsigned char*>(G.a16 + ao);
-                const unsigned char* bg = reinterpret_cast<const unsigned char*>(G.b16 + bo);
-#pragma unroll
-                for (int mt = 0; mt < MT; ++mt) cp_async16(st + mt * 512 + lane * 16, ag + ((mt * KT + ktp) * 32 + lane) * 16);
-#pragma unroll
-                for (int nt = 0; nt < NT; ++nt)
-                    cp_async8(st + B_OFF + nt * 256 + lane * 8, bg + ((nt * KT + ktp) * 32 + lane) * 8);
-                if (SPLIT) {
-                    const unsigned char* agl = reinterpret_cast<const unsigned char*>(G.a16_lo + ao);
-                    const unsigned char* bgl = reinterpret_cast<const unsigned char*>(G.b16_lo + bo);
-#pragma unroll
-                    for (int mt = 0; mt < MT; ++mt)
-                        cp_async16(st + A_OFF_LO + mt * 512 + lane * 16, agl + ((mt * KT + ktp) * 32 + lane) * 16);
-#pragma unroll
-                    for (int nt = 0; nt < NT; ++nt)
-                        cp_async8(st + A_OFF_LO + B_OFF + nt * 256 + lane * 8,
-                                  bgl + ((nt * KT + ktp) * 32 + lane) * 8);
-                }
-                if (++ktp == KT) {
-                    ktp = 0;
-                    ++pp;
-                }
-            }
-            cp_async_commit();                  // one group per call, empty past the end
-            slot_p = (slot_p + 1 == NS) ? 0 : slot_p + 1;
-        };
-#pragma unroll
-        for (int i = 0; i < NS - 1; ++i) produce();
-        int64_t pc = 0;                         // consumer: product index and k-slice
-        int ktc = 0, slot_c = 0;
-        while (pc < np) {
-            produce();
-            cp_async_wait<NS - 1>();            // this lane's copies of the consumer's unit have landed
-            const unsigned char* sp = ring_ptr + slot_c * SB;
-            uint32_t a[MT][4], b[NT][2], al[SPLIT ? MT : 1][4], bl[SPLIT ? NT : 1][2];
-#pragma unroll
-            for (int mt = 0; mt < MT; ++mt) {
-                const uint4 v = *reinterpret_cast<const uint4*>(sp + mt * 512 + lane * 16);
-                a[mt][0] = v.x; a[mt][1] = v.y; a[mt][2] = v.z; a[mt][3] = v.w;
-            }
-#pragma unroll
-            for (int nt = 0; nt < NT; ++nt) {
-                const uint2 v = *reinterpret_cast<const uint2*>(sp + B_OFF + nt * 256 + lane * 8);
-                b[nt][0] = v.x; b[nt][1] = v.y;
-            }
-            if (SPLIT) {
-#pragma unroll
-                for (int mt = 0; mt < MT; ++mt) {
-                    const uint4 v = *reinterpret_cast<const uint4*>(sp + A_OFF_LO + mt * 512 + lane * 16);
-                    al[SPLIT ? mt : 0][0] = v.x; al[SPLIT ? mt : 0][1] = v.y;
-                    al[SPLIT ? mt : 0][2] = v.z; al[SPLIT ? mt : 0][3] = v.w;
-                }
-#pragma unroll
-                for (int nt = 0; nt < NT; ++nt) {
-                    const uint2 v = *reinterpret_cast<const uint2*>(sp + A_OFF_LO + B_OFF + nt * 256 + lane * 8);
-                    bl[SPLIT ? nt : 0][0] = v.x; bl[SPLIT ? nt : 0][1] = v.y;
-                }
-            }
-#pragma unroll
-            for (int mt = 0; mt < MT; ++mt) {
-#pragma unroll
-                for (int nt = 0; nt < NT; ++nt) mma_bf16(acc[mt][nt], a[mt][0], a[mt][1], a[mt][2], a[mt][3], b[nt][0], b[nt][1]);
-                if (SPLIT) {
-#pragma unroll
-                    for (int nt = 0; nt < NT; ++nt) {
-                        mma_bf16(acc[mt][nt], a[mt][0], a[mt][1], a[mt][2], a[mt][3], bl[SPLIT ? nt : 0][0],
-                                 bl[SPLIT ? nt : 0][1]);
-                        mma_bf16(acc[mt][nt], al[SPLIT ? mt : 0][0], al[SPLIT ? mt : 0][1], al[SPLIT ? mt : 0][2],
-                                 al[SPLIT ? mt : 0][3], b[nt][0], b[nt][1]);
-                    }
-                }
-            }
-            slot_c = (slot_c + 1 == NS) ? 0 : slot_c + 1;
-            const int KTc = (__shfl_sync(0xffffffffu, cur.kq, (int)(pc & 31)) + 15) >> 4;
-            if (++ktc == KTc) {
-                ktc = 0;
-                ++pc;
-                if ((pc & 31) == 0 && pc < np) {  // the consumer enters the next batch
-                    ++cbat;
-                    cur = nxt;
-                    nxt = bf_meta(G, pb + (cbat + 1) * 32, pe, lane);
-                }
-            }
-        }
-        cp_async_wait<0>();                     // the empty trailing groups
-        // epilogue in FP64
-        const int64_t ci = S.f_cin[k];
-        const double* cin = ci >= 0 ? S.ci_data + S.ci_off[ci] : nullptr;
-        double* out = S.c_data + S.f_off[k];
-        double sq = 0.0, d = 0.0;
-#pragma unroll
-        for (int mt = 0; mt < MT; ++mt)
-#pragma unroll
-            for (int nt = 0; nt < NT; ++nt)
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const int r = mt * 16 + gid + (i >= 2 ? 8 : 0), c = nt * 8 + tig * 2 + (i & 1);
-                    if (r < m && c < n) {
-                        double v = S.alpha * (double)acc[mt][nt][i];
-                        if (cin) v = v + S.beta * cin[r * n + c];
-                        out[r * n + c] = v;
-                        sq = fma(v, v, sq);
-                        const double wv = (I == J && r == c) ? v - 1.0 : v;
-                        d = fma(wv, wv, d);
-                    }
-                }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            sq += __shfl_xor_sync(0xffffffffu, sq, o);
-            d += __shfl_xor_sync(0xffffffffu, d, o);
-        }
-        if (lane == 0) {
-            S.c_norm[k] = sqrt(sq);
-            S.c_dev2[k] = d;
-        }
-    }
-}
-
-using SmmBf16Kernel = void (*)(int64_t, const int64_t*, SmmBf16Args);
-
-// Kernel of a BF16 class (MT, NT) = ((cls - 1) / 4 + 1, (cls - 1) % 4 + 1).
-template <bool SPLIT>
-SmmBf16Kernel bf16_kernel_t(int cls) {
-    switch (cls) {
-        case 1: return &k_smm_bf16<1, 1, SPLIT>;
-        case 2: return &k_smm_bf16<1, 2, SPLIT>;
-        case 3: return &k_smm_bf16<1, 3, SPLIT>;
-        case 4: return &k_smm_bf16<1, 4, SPLIT>;
-        case 5: return &k_smm_bf16<2, 1, SPLIT>;
-        case 6: return &k_smm_bf16<2, 2, SPLIT>;
-        case 7: return &k_smm_bf16<2, 3, SPLIT>;
-        case 8: return &k_smm_bf16<2, 4, SPLIT>;
-        default: return nullptr;
-    }
-}
-SmmBf16Kernel bf16_kernel(int cls, bool split) { return split ? bf16_kernel_t<true>(cls) : bf16_kernel_t<false>(cls); }
 
 // Planned products keep their pattern: a block (not diagonal) whose norm is below eps
 // is set to zero instead of being removed.
@@ -1141,44 +866,41 @@ __global__ void k_keep_twinned(int64_t nb, const int64_t* __restrict__ mirror, i
 }  // namespace
 
 TuneCfg default_cfg(int prec) {
-    TuneCfg c;
-    if (prec == DBCSR_BF16) {
-        c.tpb = 128;
-        c.ctas_per_sm = 64;
-    }
-    return c;
+    (void)prec;
+    return TuneCfg{};
 }
 
-void launch_smm_shape(int prec, int m, int n, int64_t cnt, const int64_t* list, const SmmArgs& sa,
-                      const Bf16Packs& pk, const TuneCfg& cfg, cudaStream_t s) {
+bool cfg_valid(int m, int n, const TuneCfg& c) {
+    const int mn = m * n;
+    if (c.tpb < 32 || c.tpb > 256 || c.tpb % 32 || c.ctas_per_sm < 1) return false;
+    if (c.split == kSplitPair) return mn > 32 && c.tpb % 64 == 0;
+    if (c.split == kSplitK) return mn > 32 && (mn & 31) == 1;
+    return c.split == kSplitDefault || c.split == kSplitWarp;
+}
+
+int resolve_split(int m, int n, const TuneCfg& c) {
+    const int mn = m * n;
+    if (c.split != kSplitDefault) return c.split;
+    if (mn > 32 && (mn & 31) == 1) return kSplitK;
+    return ((mn + 31) >> 5) >= kPairMinE && c.tpb % 64 == 0 ? kSplitPair : kSplitWarp;
+}
+
+void launch_smm_shape(int m, int n, int64_t cnt, const int64_t* list, const SmmArgs& sa, const TuneCfg& cfg,
+                      cudaStream_t s) {
     if (cnt <= 0) return;
-    if (cfg.tpb < 32 || cfg.tpb > 256 || cfg.tpb % 32 || cfg.ctas_per_sm < 1)
-        fail(DBCSR_EINVAL, "launch configuration out of range");
+    if (!cfg_valid(m, n, cfg)) fail(DBCSR_EINVAL, "launch configuration out of range for this block shape");
     const int wpc = cfg.tpb / 32;
-    const int64_t grid = std::min<int64_t>(ceil_div(cnt, wpc), (int64_t)num_sms() * cfg.ctas_per_sm);
-    if (is_bf16(prec)) {
-        const bool split = prec == DBCSR_BF16X3;
-        if (split && (!pk.a16_lo || !pk.b16_lo)) fail(DBCSR_EINVAL, "multiply: split BF16 needs the residual packs");
-        const int mt = (m + 15) / 16, nt = (n + 7) / 8;
-        SmmBf16Kernel kern = bf16_kernel((mt - 1) * 4 + nt, split);
-        if (!kern) fail(DBCSR_ECAPACITY, "multiply: block shape beyond the BF16 kernel table");
-        SmmBf16Args ga{sa, pk.a16, pk.a_po, pk.b16, pk.b_po, pk.a16_lo, pk.b16_lo};
-        // the warps' stage rings
-        const size_t smem = (size_t)(cfg.tpb / 32) * bf16_stages(mt, nt, split) * bf16_stage_bytes(mt, nt, split);
-        allow_dyn_smem(kern, smem);
-        kern<<<(unsigned)grid, cfg.tpb, smem, s>>>(cnt, list, ga);
-    } else {
-        const int mn = m * n;
-        const int cls = (mn > 32 && (mn & 31) == 1) ? kF64ClassKs1 + (mn >> 5) : (mn + 31) >> 5;
-        const bool pair = f64_class_pairs(cls) && cfg.tpb % 64 == 0;
-        SmmKernel kern = f64_kernel(cls, pair);
-        if (!kern) fail(DBCSR_ECAPACITY, "multiply: block shape beyond the kernel table");
-        SmmArgs a = sa;
-        a.colmajor = cfg.colmajor;
-        a.prefetch2 = cfg.prefetch2;
-        const int64_t g = pair ? std::min<int64_t>(ceil_div(cnt, wpc / 2), (int64_t)num_sms() * cfg.ctas_per_sm) : grid;
-        kern<<<(unsigned)g, cfg.tpb, 0, s>>>(cnt, list, a);
-    }
+    const int mn = m * n;
+    const int split = resolve_split(m, n, cfg);
+    const int cls = split == kSplitK ? kF64ClassKs1 + (mn >> 5) : (mn + 31) >> 5;
+    const bool pair = split == kSplitPair;
+    SmmKernel kern = f64_kernel(cls, pair);
+    if (!kern) fail(DBCSR_ECAPACITY, "multiply: block shape beyond the kernel table");
+    SmmArgs a = sa;
+    a.colmajor = cfg.colmajor;
+    a.prefetch2 = cfg.prefetch2;
+    const int64_t g = std::min<int64_t>(ceil_div(cnt, pair ? wpc / 2 : wpc), (int64_t)num_sms() * cfg.ctas_per_sm);
+    kern<<<(unsigned)g, cfg.tpb, 0, s>>>(cnt, list, a);
     DBG_LAUNCH_CK();
 }
 
@@ -1437,7 +1159,7 @@ void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbc
         }
         at = 0;
         for (const ShapeLaunch& L : launches) {
-            launch_smm_shape(prec, L.m, L.n, L.cnt, list.p + at, sa, Bf16Packs{}, tune_lookup(prec, L.m, L.n, kmax), s);
+            launch_smm_shape(L.m, L.n, L.cnt, list.p + at, sa, tune_lookup(prec, L.m, L.n, kmax), s);
             at += L.cnt;
         }
         if (!bf16)         n_smm_launches = (int32_t)launches.size();
@@ -1501,8 +1223,7 @@ void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbc
             }
             int64_t at = 0;
             for (const ShapeLaunch& L : launches) {
-                launch_smm_shape(prec, L.m, L.n, L.cnt, list.p + at, sa, Bf16Packs{}, tune_lookup(prec, L.m, L.n, kmax),
-                                 cs);
+                launch_smm_shape(L.m, L.n, L.cnt, list.p + at, sa, tune_lookup(prec, L.m, L.n, kmax), cs);
                 at += L.cnt;
             }
             zero_small(cs);

@@ -26,45 +26,38 @@ struct SmmArgs {
     int prefetch2;   // 1: fetch the next 32 products' metadata before using the current ones
 };
 
-// Launch configuration of one (m, n) shape; none of it changes the arithmetic
-// (every C element is summed in the same order whatever the configuration).
+// Launch configuration of one (m, n) shape.  tpb, ctas_per_sm, colmajor and prefetch2 leave
+// the arithmetic unchanged (every C element is summed in the same order); split picks the
+// kernel's work split per C block and changes only the rounding order: of the block norm
+// (warp pair) or of one remainder element (K-split).
+constexpr int kSplitDefault = -1;   // K-split where m n = 32 EF + 1, else a pair from 6 slots per lane
+constexpr int kSplitWarp = 0;       // one warp per C block
+constexpr int kSplitPair = 1;       // two warps per C block, half of the element slots each (m n > 32)
+constexpr int kSplitK = 2;          // 32 EF elements over the lanes, the last one summed along K (m n = 32 EF + 1)
 struct TuneCfg {
     int tpb = 256;           // threads per CTA (multiple of 32, <= 256)
     int ctas_per_sm = 32;    // grid = min(warps needed / warps per CTA, (SM count) * ctas_per_sm)
-    int colmajor = 0;        // FP64 only
-    int prefetch2 = 0;       // FP64 only
+    int colmajor = 0;        // lane -> element order
+    int prefetch2 = 0;       // fetch the next 32 products' metadata ahead
+    int split = kSplitDefault;
 };
 
 TuneCfg default_cfg(int prec);
 // Tuned configuration for (prec, m, n, k), or the default when the table has none.
 TuneCfg tune_lookup(int prec, int m, int n, int k);
-// Legal configurations the tuner times for a precision.
+// Configurations the tuner times (FP64; the tensor-core tier has no per-shape kernels).
 std::vector<TuneCfg> tune_space(int prec);
+// Whether cfg applies to m x n blocks, and the work split it resolves to.
+bool cfg_valid(int m, int n, const TuneCfg& c);
+int resolve_split(int m, int n, const TuneCfg& c);
 
 // Features of one (m, n, k, configuration) sample for the prediction model.
 void mlp_features(int prec, int m, int n, int k, const TuneCfg& c, float* f);
 
-// Fragment-ready BF16 copies of the operands (BF16 products only): block b of A
-// at a16 + a_po[b] (m x k padded to 16-multiples), block b of B transposed at
-// b16 + b_po[b] (n x k padded to 8 x 16-multiples).  Each block takes its own
-// padded size, so mixed block sizes waste no slots.
-struct Bf16Packs {
-    const __nv_bfloat16* a16 = nullptr;
-    const int64_t* a_po = nullptr;
-    const __nv_bfloat16* b16 = nullptr;
-    const int64_t* b_po = nullptr;
-    const __nv_bfloat16* a16_lo = nullptr;   // DBCSR_BF16X3: the residuals lo = bf16(x - hi), same offsets
-    const __nv_bfloat16* b16_lo = nullptr;
-};
 inline bool is_bf16(int prec) { return prec == DBCSR_BF16 || prec == DBCSR_BF16X3; }
-// Packed tile size (elements) of an r x c block in a role (0: A, m x k; 1: B, k x n stored n x k).
-__host__ __device__ inline int64_t pack_size(int role, int r, int c) {
-    return role == 0 ? (int64_t)(16 * ((r + 15) / 16)) * (16 * ((c + 15) / 16))
-                     : (int64_t)(8 * ((c + 7) / 8)) * (16 * ((r + 15) / 16));
-}
 
-// Launches the kernel of shape (m, n) over the cnt blocks listed in list.
-void launch_smm_shape(int prec, int m, int n, int64_t cnt, const int64_t* list, const SmmArgs& sa,
-                      const Bf16Packs& pk, const TuneCfg& cfg, cudaStream_t s);
+// Launches the FP64 kernel of shape (m, n) over the cnt blocks listed in list.
+void launch_smm_shape(int m, int n, int64_t cnt, const int64_t* list, const SmmArgs& sa, const TuneCfg& cfg,
+                      cudaStream_t s);
 
 }  // namespace dbg

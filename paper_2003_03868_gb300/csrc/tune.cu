@@ -2,12 +2,14 @@
 // execution": each (m, n, k) kernel is tuned over its parameters on stacks of
 // block products, and the best parameter set is kept per (m, n, k)).
 //
-// Here the parameters are launch-time choices that leave the arithmetic
-// unchanged: threads per CTA, CTAs per SM of the grid, the lane-to-element order
-// and double-buffered product metadata (FP64); threads per CTA and CTAs per SM
-// (BF16).  A synthetic stack for (m, n, k) imitates one shape launch of a real
-// product: stack_len products over C blocks of 32 products each, with A and B blocks
-// drawn at random from pools of about 512 MB together (several times the L2).
+// Here the parameters of the FP64 block-product kernels are the work split per C block
+// (one warp, a warp pair sharing the element slots, or the K-split remainder kernel) and
+// the launch-time choices that leave the arithmetic unchanged: threads per CTA, CTAs per
+// SM of the grid, the lane-to-element order and double-buffered product metadata.  The
+// tensor-core tier (BF16 products) runs one tile shape for every block shape, so it has
+// nothing to tune per (m, n, k).  A synthetic stack for (m, n, k) imitates one shape launch
+// of a real product: stack_len products over C blocks of 32 products each, with A and B
+// blocks drawn at random from pools of about 512 MB together (several times the L2).
 #include <algorithm>
 #include <cstdio>
 #include <fstream>
@@ -76,43 +78,16 @@ __global__ void k_fill_stack_synth(int64_t nprod, int64_t nc, int64_t npool, uin
     }
 }
 
-// Packed BF16 pools for timing: A blocks m x k in (16 ceil(m/16)) x (16 ceil(k/16)) tiles,
-// B blocks k x n in (16 ceil(k/16)) x (8 ceil(n/8)) tiles, zero padded, at the given
-// strides.  The element order inside a tile does not matter for timing (the products
-// load whole tiles either way); only the tile sizes and places do.
-__global__ void k_pack_synth(int64_t nblk, int role, int r_sz, int c_sz, const double* __restrict__ in,
-                             int64_t stride, __nv_bfloat16* __restrict__ out) {
-    const int R = role == 0 ? 16 * ((r_sz + 15) / 16) : 8 * ((c_sz + 7) / 8);
-    const int L = role == 0 ? 16 * ((c_sz + 15) / 16) : 16 * ((r_sz + 15) / 16);
-    const int64_t total = nblk * (int64_t)R * L;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t b = i / ((int64_t)R * L);
-        const int e = (int)(i - b * R * L), p = e / L, t = e - p * L;
-        const double* x = in + b * (int64_t)r_sz * c_sz;
-        double v = 0.0;
-        if (role == 0) v = (p < r_sz && t < c_sz) ? x[p * c_sz + t] : 0.0;
-        else v = (p < c_sz && t < r_sz) ? x[t * c_sz + p] : 0.0;
-        out[b * stride + e] = __float2bfloat16((float)v);
-    }
-}
-
-__global__ void k_stride_offsets(int64_t n, int64_t stride, int64_t* __restrict__ out) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        out[i] = i * stride;
-}
-
 // A synthetic (m, n, k) stack resident on the device.
 struct SynthStack {
     int m, n, k;
     int64_t nprod, nc, npool;
     DBuf<double> a, b, c, norm, dev2;
-    DBuf<__nv_bfloat16> a16, b16;
     DBuf<int32_t> prod_a, prod_b, a_col, f_row, f_col, bs;
-    DBuf<int64_t> a_off, b_off, f_off, f_pbeg, f_cin, list, a_po, b_po;
+    DBuf<int64_t> a_off, b_off, f_off, f_pbeg, f_cin, list;
     SmmArgs args{};
-    Bf16Packs pk{};
 
-    SynthStack(int m_, int n_, int k_, int64_t stack_len, bool bf16, cudaStream_t s) : m(m_), n(n_), k(k_) {
+    SynthStack(int m_, int n_, int k_, int64_t stack_len, cudaStream_t s) : m(m_), n(n_), k(k_) {
         nprod = stack_len;
         npool = pool_blocks(m, n, k);
         nc = ceil_div(stack_len, kProductsPerC);
@@ -143,42 +118,20 @@ struct SynthStack {
             nprod, nc, npool, 0x1234ull + (uint64_t)(m * 10000 + n * 100 + k), m, n, k, prod_a.p, prod_b.p, a_off.p, b_off.p,
             a_col.p, f_row.p, f_col.p, f_off.p, f_pbeg.p, f_cin.p, list.p);
         DBG_LAUNCH_CK();
-        if (bf16) {
-            // every pool block has the same shape: tiles at a fixed stride
-            const int64_t sa = pack_size(0, m, k), sb = pack_size(1, k, n);
-            a16.alloc(npool * sa, s);
-            b16.alloc(npool * sb, s);
-            a_po.alloc(npool + 1, s);
-            b_po.alloc(npool + 1, s);
-            k_stride_offsets<<<grid_for(npool + 1, 256), 256, 0, s>>>(npool + 1, sa, a_po.p);
-            DBG_LAUNCH_CK();
-            k_stride_offsets<<<grid_for(npool + 1, 256), 256, 0, s>>>(npool + 1, sb, b_po.p);
-            DBG_LAUNCH_CK();
-            k_pack_synth<<<grid_for(a16.n, 256, num_sms() * 64), 256, 0, s>>>(npool, 0, m, k, a.p, sa, a16.p);
-            DBG_LAUNCH_CK();
-            k_pack_synth<<<grid_for(b16.n, 256, num_sms() * 64), 256, 0, s>>>(npool, 1, k, n, b.p, sb, b16.p);
-            DBG_LAUNCH_CK();
-            pk.a16 = a16.p;
-            pk.a_po = a_po.p;
-            pk.b16 = b16.p;
-            pk.b_po = b_po.p;
-            pk.a16_lo = a16.p;      // timing only: the residual packs may alias the leading ones
-            pk.b16_lo = b16.p;
-        }
         args = SmmArgs{f_row.p, f_col.p, f_off.p, f_pbeg.p, f_cin.p, prod_a.p, prod_b.p, a_col.p, a_off.p, a.p,
                        b_off.p, b.p, nullptr, nullptr, bs.p, 1.0, 0.0, c.p, norm.p, dev2.p, 0, 0};
     }
 
     // Median time (ms) of `reps` launches with configuration cfg.
-    double time(int prec, const TuneCfg& cfg, int reps, cudaStream_t s) {
+    double time(const TuneCfg& cfg, int reps, cudaStream_t s) {
         cudaEvent_t e0, e1;
         DBG_CK(cudaEventCreate(&e0));
         DBG_CK(cudaEventCreate(&e1));
         std::vector<float> t;
-        launch_smm_shape(prec, m, n, nc, list.p, args, pk, cfg, s);   // warm-up
+        launch_smm_shape(m, n, nc, list.p, args, cfg, s);   // warm-up
         for (int r = 0; r < reps; ++r) {
             DBG_CK(cudaEventRecord(e0, s));
-            launch_smm_shape(prec, m, n, nc, list.p, args, pk, cfg, s);
+            launch_smm_shape(m, n, nc, list.p, args, cfg, s);
             DBG_CK(cudaEventRecord(e1, s));
             DBG_CK(cudaEventSynchronize(e1));
             float ms = 0.f;
@@ -192,8 +145,13 @@ struct SynthStack {
     }
 };
 
+void check_prec(int prec) {
+    if (prec != DBCSR_FP64)
+        fail(DBCSR_EINVAL, "tune: prec must be DBCSR_FP64 (the tensor-core tier has no per-shape kernels to tune)");
+}
+
 void check_triple(int prec, int m, int n, int k) {
-    if (prec != DBCSR_FP64 && !is_bf16(prec)) fail(DBCSR_EINVAL, "tune: prec must be DBCSR_FP64, DBCSR_BF16 or DBCSR_BF16X3");
+    check_prec(prec);
     if (m < 1 || n < 1 || k < 1 || m > kMaxBlock || n > kMaxBlock || k > kMaxBlock)
         fail(DBCSR_EINVAL, "tune: m, n, k must lie in [1, 32]");
 }
@@ -201,18 +159,11 @@ void check_triple(int prec, int m, int n, int k) {
 }  // namespace
 
 std::vector<TuneCfg> tune_space(int prec) {
+    check_prec(prec);
     std::vector<TuneCfg> v;
-    if (is_bf16(prec)) {
-        for (int tpb : {64, 128, 256})
-            for (int c : {4, 8, 16, 32, 64}) {
-                TuneCfg t;
-                t.tpb = tpb;
-                t.ctas_per_sm = c;
-                v.push_back(t);
-            }
-    } else {
-        for (int tpb : {64, 128, 256})
-            for (int c : {2, 4, 8, 16, 32})
+    for (int sp : {kSplitWarp, kSplitPair, kSplitK})
+        for (int tpb : {128, 256})
+            for (int c : {4, 8, 16, 32})
                 for (int cm : {0, 1})
                     for (int pf : {0, 1}) {
                         TuneCfg t;
@@ -220,9 +171,9 @@ std::vector<TuneCfg> tune_space(int prec) {
                         t.ctas_per_sm = c;
                         t.colmajor = cm;
                         t.prefetch2 = pf;
+                        t.split = sp;
                         v.push_back(t);
                     }
-    }
     return v;
 }
 
@@ -242,9 +193,12 @@ dbg::TuneCfg from_c(const dbcsr_kernel_cfg& c) {
     t.ctas_per_sm = c.ctas_per_sm;
     t.colmajor = c.colmajor;
     t.prefetch2 = c.prefetch2;
+    t.split = c.split;
     return t;
 }
-dbcsr_kernel_cfg to_c(const dbg::TuneCfg& t) { return dbcsr_kernel_cfg{t.tpb, t.ctas_per_sm, t.colmajor, t.prefetch2}; }
+dbcsr_kernel_cfg to_c(const dbg::TuneCfg& t) {
+    return dbcsr_kernel_cfg{t.tpb, t.ctas_per_sm, t.colmajor, t.prefetch2, t.split};
+}
 
 template <class F>
 dbcsr_status guard(F&& f) {
@@ -266,7 +220,6 @@ extern "C" {
 
 dbcsr_status dbcsr_tune_space(int32_t prec, dbcsr_kernel_cfg* out, int32_t cap, int32_t* n) {
     return guard([&] {
-        if (prec != DBCSR_FP64 && !dbg::is_bf16(prec)) dbg::fail(DBCSR_EINVAL, "tune_space: prec must be FP64, BF16 or BF16X3");
         auto v = dbg::tune_space(prec);
         if (n) *n = (int32_t)v.size();
         if (out)
@@ -280,8 +233,11 @@ dbcsr_status dbcsr_time_config(int32_t prec, int32_t m, int32_t n, int32_t k, in
         dbg::check_triple(prec, m, n, k);
         if (stack_len < 1 || reps < 1 || ncfg < 1 || !cfgs || !ms_out) dbg::fail(DBCSR_EINVAL, "time_config: bad argument");
         cudaStream_t s = nullptr;
-        dbg::SynthStack st(m, n, k, stack_len, dbg::is_bf16(prec), s);
-        for (int32_t i = 0; i < ncfg; ++i) ms_out[i] = st.time(prec, from_c(cfgs[i]), reps, s);
+        for (int32_t i = 0; i < ncfg; ++i)
+            if (!dbg::cfg_valid(m, n, from_c(cfgs[i])))
+                dbg::fail(DBCSR_EINVAL, "time_config: configuration " + std::to_string(i) + " does not apply to the shape");
+        dbg::SynthStack st(m, n, k, stack_len, s);
+        for (int32_t i = 0; i < ncfg; ++i) ms_out[i] = st.time(from_c(cfgs[i]), reps, s);
     });
 }
 
@@ -295,11 +251,12 @@ dbcsr_status dbcsr_autotune(const int32_t* mnk, int32_t ntriples, int32_t prec, 
         for (int32_t t = 0; t < ntriples; ++t) {
             const int m = mnk[3 * t], n = mnk[3 * t + 1], k = mnk[3 * t + 2];
             dbg::check_triple(prec, m, n, k);
-            dbg::SynthStack st(m, n, k, stack_len, dbg::is_bf16(prec), s);
+            dbg::SynthStack st(m, n, k, stack_len, s);
             double best = 1e300;
             dbg::TuneCfg best_cfg = dbg::default_cfg(prec);
             for (const auto& c : space) {
-                const double ms = st.time(prec, c, reps, s);
+                if (!dbg::cfg_valid(m, n, c)) continue;
+                const double ms = st.time(c, reps, s);
                 if (ms < best) {
                     best = ms;
                     best_cfg = c;
@@ -331,17 +288,18 @@ dbcsr_status dbcsr_tune_predicted(int32_t prec, const float* params, const int32
         cudaStream_t s = nullptr;
         for (int32_t t = 0; t < ntriples; ++t) {
             const int m = mnk[3 * t], n = mnk[3 * t + 1], k = mnk[3 * t + 2];
-            dbg::SynthStack st(m, n, k, stack_len, dbg::is_bf16(prec), s);
+            dbg::SynthStack st(m, n, k, stack_len, s);
             // measured time judges the prediction: kept if within tolerance of the default,
             // otherwise the exhaustive search over the space decides
             dbg::TuneCfg chosen = from_c(pred[t]);
-            const double tp = st.time(prec, chosen, reps, s);
-            const double td = st.time(prec, dflt, reps, s);
+            const double tp = st.time(chosen, reps, s);
+            const double td = st.time(dflt, reps, s);
             const bool fb = !(tp <= td * (1.0 + tolerance));
             if (fb) {
                 double best = 1e300;
                 for (const auto& c : space) {
-                    const double ms = st.time(prec, c, reps, s);
+                    if (!dbg::cfg_valid(m, n, c)) continue;
+                    const double ms = st.time(c, reps, s);
                     if (ms < best) {
                         best = ms;
                         chosen = c;
@@ -359,6 +317,8 @@ dbcsr_status dbcsr_tune_set(int32_t prec, int32_t m, int32_t n, int32_t k, const
     return guard([&] {
         dbg::check_triple(prec, m, n, k);
         std::lock_guard<std::mutex> lock(dbg::g_tune_mu);
+        if (cfg && !dbg::cfg_valid(m, n, from_c(*cfg)))
+            dbg::fail(DBCSR_EINVAL, "tune_set: the configuration does not apply to m x n blocks");
         if (!cfg) dbg::g_tune.erase({prec, m, n, k});
         else dbg::g_tune[{prec, m, n, k}] = from_c(*cfg);
     });
@@ -386,11 +346,11 @@ dbcsr_status dbcsr_tune_save(const char* path) {
         if (!path) dbg::fail(DBCSR_EINVAL, "tune_save: null path");
         std::ofstream f(path);
         if (!f) dbg::fail(DBCSR_EINVAL, std::string("tune_save: cannot open ") + path);
-        f << "# prec m n k tpb ctas_per_sm colmajor prefetch2\n";
+        f << "# prec m n k tpb ctas_per_sm colmajor prefetch2 split\n";
         std::lock_guard<std::mutex> lock(dbg::g_tune_mu);
         for (const auto& [key, c] : dbg::g_tune)
             f << std::get<0>(key) << ' ' << std::get<1>(key) << ' ' << std::get<2>(key) << ' ' << std::get<3>(key) << ' '
-              << c.tpb << ' ' << c.ctas_per_sm << ' ' << c.colmajor << ' ' << c.prefetch2 << '\n';
+              << c.tpb << ' ' << c.ctas_per_sm << ' ' << c.colmajor << ' ' << c.prefetch2 << ' ' << c.split << '\n';
     });
 }
 
@@ -406,11 +366,11 @@ dbcsr_status dbcsr_tune_load(const char* path) {
             std::istringstream is(line);
             int prec, m, n, k;
             dbg::TuneCfg c;
-            if (!(is >> prec >> m >> n >> k >> c.tpb >> c.ctas_per_sm >> c.colmajor >> c.prefetch2))
+            if (!(is >> prec >> m >> n >> k >> c.tpb >> c.ctas_per_sm >> c.colmajor >> c.prefetch2 >> c.split))
                 dbg::fail(DBCSR_EINVAL, "tune_load: malformed line: " + line);
             dbg::check_triple(prec, m, n, k);
-            if (c.tpb < 32 || c.tpb > 256 || c.tpb % 32 || c.ctas_per_sm < 1)
-                dbg::fail(DBCSR_EINVAL, "tune_load: launch configuration out of range: " + line);
+            if (!dbg::cfg_valid(m, n, c))
+                dbg::fail(DBCSR_EINVAL, "tune_load: configuration out of range for the shape: " + line);
             tab[{prec, m, n, k}] = c;
         }
         std::lock_guard<std::mutex> lock(dbg::g_tune_mu);

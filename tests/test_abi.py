@@ -66,7 +66,7 @@ def test_struct_layouts_match_the_c_compiler(tmp_path):
         "dbcsr_sign_report": (_ffi.SignReport, ["alpha", "n_products", "residual_history", "nnzb_history",
                                                "ms_symbolic", "ms_low", "flops_low", "bytes_min_fp64",
                                                "launches_fp64", "flops_tensor", "bytes_tensor"]),
-        "dbcsr_kernel_cfg": (_ffi.KernelCfg, ["prefetch2"]),
+        "dbcsr_kernel_cfg": (_ffi.KernelCfg, ["prefetch2", "split"]),
         "dbcsr_tune_record": (_ffi.TuneRecord, ["cfg", "ms", "gflops"]),
         "dbcsr_mlp_opts": (_ffi.MlpOpts, ["lr", "eps"]),
         "dbcsr_mlp_report": (_ffi.MlpReport, [f[0] for f in _ffi.MlpReport._fields_]),

@@ -22,43 +22,65 @@ def gb():
     m.tune_clear()
 
 
+def _key(c):
+    return (c.tpb, c.ctas_per_sm, c.colmajor, c.prefetch2, c.split)
+
+
+def _valid(c, m, n):
+    mn = m * n
+    if c.split == 1:
+        return mn > 32 and c.tpb % 64 == 0
+    if c.split == 2:
+        return mn > 32 and mn % 32 == 1
+    return True
+
+
 def test_autotune_records_and_table(gb):
     gb.tune_clear()
     triples = [(13, 13, 13), (13, 5, 13)]
     recs = gb.autotune(triples, gb.DBCSR_FP64, stack_len=20000, reps=3)
-    nsp = len(gb.tune_space(gb.DBCSR_FP64))
-    assert len(recs) == len(triples) * nsp
+    space = gb.tune_space(gb.DBCSR_FP64)
+    # only the configurations that apply to a shape are timed: no K-split for 169 elements
+    assert len(recs) == sum(sum(_valid(c, m, n) for c in space) for (m, n, k) in triples)
     assert all(r.ms > 0 and r.gflops > 0 for r in recs)
+    assert not [r for r in recs if (r.m, r.n) == (13, 13) and r.cfg.split == 2]
     default = gb.tune_get(gb.DBCSR_FP64, 4, 4, 4)[0]
     for (m, n, k) in triples:
         cfg, found = gb.tune_get(gb.DBCSR_FP64, m, n, k)
         assert found
         rs = [r for r in recs if (r.m, r.n, r.k) == (m, n, k)]
         best = min(r.ms for r in rs)
-        dflt = [r.ms for r in rs if (r.cfg.tpb, r.cfg.ctas_per_sm, r.cfg.colmajor, r.cfg.prefetch2) ==
-                (default.tpb, default.ctas_per_sm, default.colmajor, default.prefetch2)][0]
-        assert best <= dflt
-    brec = gb.autotune([(13, 5, 13)], gb.DBCSR_BF16, stack_len=20000, reps=3)
-    assert len(brec) == len(gb.tune_space(gb.DBCSR_BF16))
+        assert _key(cfg) == _key(min(rs, key=lambda r: r.ms).cfg)
+        assert best <= gb.time_configs(m, n, k, [default], stack_len=20000, reps=3)[0] * 1.05
+    with pytest.raises(gb.DbcsrError):
+        gb.autotune([(13, 5, 13)], gb.DBCSR_BF16X3, stack_len=20000, reps=3)
     gb.tune_clear()
 
 
-@pytest.mark.parametrize("prec", ["fp64", "bf16"])
-def test_configurations_leave_results_bit_identical(gb, prec):
-    p = gb.DBCSR_FP64 if prec == "fp64" else gb.DBCSR_BF16
+def test_launch_parameters_leave_results_bit_identical_and_splits_round_alike(gb):
+    # threads, CTAs per SM, lane order and prefetch never change a result bit; the work split
+    # changes only rounding (the norm's summation order, or one element summed along K)
     a = synth.build_decay(synth.DECAY_32)
     gb.tune_clear()
     A = gb.Matrix.of(a)
-    C = gb.Matrix(A.blk_size, A.stream)
-    gb.multiply(1.0, A, A, 0.0, C, 1e-6, prec=p)
-    ref = C.export()[2].tobytes()
-    space = gb.tune_space(p)
-    for cfg in space[:: max(1, len(space) // 12)]:
-        for (m, n) in [(13, 13), (13, 5), (5, 13), (5, 5)]:
-            gb.tune_set(p, m, n, 13, cfg)
-        C2 = gb.Matrix(A.blk_size, A.stream)
-        gb.multiply(1.0, A, A, 0.0, C2, 1e-6, prec=p)
-        assert C2.export()[2].tobytes() == ref, (cfg.tpb, cfg.ctas_per_sm, cfg.colmajor, cfg.prefetch2)
+
+    def run():
+        C = gb.Matrix(A.blk_size, A.stream)
+        gb.multiply(1.0, A, A, 0.0, C, 1e-6)
+        return C.export()[2]
+
+    ref = run()
+    shapes = [(13, 13), (13, 5), (5, 13), (5, 5)]
+    space = gb.tune_space(gb.DBCSR_FP64)
+    for split in (0, 1, 2):
+        outs = []
+        for cfg in [c for c in space if c.split == split][::5]:
+            for (m, n) in shapes:
+                c = cfg if _valid(cfg, m, n) else gb.KernelCfg(cfg.tpb, cfg.ctas_per_sm, cfg.colmajor, cfg.prefetch2, 0)
+                gb.tune_set(gb.DBCSR_FP64, m, n, 13, c)
+            outs.append(run())
+        assert all(o.tobytes() == outs[0].tobytes() for o in outs), split
+        np.testing.assert_allclose(outs[0], ref, rtol=0, atol=1e-14 * np.abs(ref).max())
     gb.tune_clear()
 
 
@@ -105,37 +127,39 @@ def test_mlp_training_reduces_loss(gb):
 
 @pytest.mark.slow
 def test_mlp_predicted_configs_gain_over_default(gb):
-    """Tune a training set of (m, n, k) triples exhaustively, train the MLP on the
-    standardised log times, predict configurations for held-out triples, and time
-    them against the default configuration and the exhaustive best."""
+    """Tune training triples exhaustively, train the model in the library on those timings,
+    predict configurations for held-out triples, and time them against the default and the
+    exhaustive best.  On the held-out triples where the default is at least 5% slower than
+    the best, the prediction must recover at least half of that loss (geometric means)."""
     rng = np.random.default_rng(11)
-    allt = [(int(m), int(n), int(k)) for m, n, k in rng.integers(4, 33, (40, 3))]
-    train, held = allt[:30], allt[30:]
+    allt = []
+    while len(allt) < 44:
+        t = tuple(int(v) for v in rng.integers(4, 33, 3))
+        if t not in allt:
+            allt.append(t)
+    train, held = allt[:32], allt[32:]
     gb.tune_clear()
     recs = gb.autotune(train, gb.DBCSR_FP64, stack_len=30000, reps=3)
-    cfgs = [r.cfg for r in recs]
-    X = gb.mlp_features([(r.m, r.n, r.k) for r in recs], cfgs)
-    y = np.log(np.array([r.ms for r in recs]))
-    # per-triple centring: the model learns how the configuration changes the time
-    tri = [(r.m, r.n, r.k) for r in recs]
-    mean = {t: np.mean([yy for tt, yy in zip(tri, y) if tt == t]) for t in set(tri)}
-    T = np.array([yy - mean[t] for t, yy in zip(tri, y)])
-    T = (T / T.std()).astype(np.float32)
-    p, rep = gb.mlp_train(gb.mlp_init(10, seed=3), X, T, epochs=3000, lr=2e-3)
-    assert rep.loss_last < rep.loss_first
+    p, rep = gb.train_predictor(recs, gb.DBCSR_FP64, epochs=3000, lr=2e-3, seed=3)
+    assert rep.loss_last < 0.5 * rep.loss_first
     pred = gb.mlp_predict_best(p, held)
     space = gb.tune_space(gb.DBCSR_FP64)
     default = gb.tune_get(gb.DBCSR_FP64, 4, 4, 4)[0]
-    r_pred, r_def = [], []
+    rows = []
     for t, c in zip(held, pred):
-        ts = gb.time_configs(*t, space, stack_len=30000, reps=3)
-        tp = gb.time_configs(*t, [c, default], stack_len=30000, reps=3)
-        r_pred.append(tp[0] / ts.min())
-        r_def.append(tp[1] / ts.min())
-    gm_pred = float(np.exp(np.mean(np.log(r_pred))))
-    gm_def = float(np.exp(np.mean(np.log(r_def))))
-    print(f"held-out: predicted/best {gm_pred:.3f} (median {np.median(r_pred):.3f}), default/best {gm_def:.3f}")
-    assert gm_pred <= gm_def * 1.02
+        valid = [s for s in space if _valid(s, t[0], t[1])]
+        assert _valid(c, t[0], t[1])
+        best = gb.time_configs(*t, valid, stack_len=30000, reps=3).min()
+        tp, td = gb.time_configs(*t, [c, default], stack_len=30000, reps=3)
+        rows.append((t, tp / best, td / best))
+    for t, rp_, rd in rows:
+        print(f"{t}: predicted/best {rp_:.3f}  default/best {rd:.3f}")
+    lossy = [(rp_, rd) for _, rp_, rd in rows if rd > 1.05]
+    assert len(lossy) >= 2, "the default is within 5% of the best on nearly every held-out triple"
+    gm_pred = float(np.exp(np.mean(np.log([x[0] for x in lossy]))))
+    gm_def = float(np.exp(np.mean(np.log([x[1] for x in lossy]))))
+    print(f"held-out triples where the default loses > 5%: predicted/best {gm_pred:.3f}, default/best {gm_def:.3f}")
+    assert gm_pred - 1.0 <= 0.5 * (gm_def - 1.0)
     gb.tune_clear()
 
 
@@ -158,25 +182,22 @@ def test_predictor_trained_in_the_library(gb, tmp_path):
     np.testing.assert_array_equal(Xl, X)
     np.testing.assert_allclose(Tl, T, rtol=1e-5, atol=1e-5)
     p_lib, rep = gb.predictor_train(path, epochs=400, lr=2e-3, seed=3)
-    p_ref, rep_ref = gb.mlp_train(gb.mlp_init(10, seed=3), Xl, Tl, epochs=400, lr=2e-3)
+    p_ref, rep_ref = gb.mlp_train(gb.mlp_init(gb.MLP_FEATURES, seed=3), Xl, Tl, epochs=400, lr=2e-3)
     np.testing.assert_array_equal(p_lib, p_ref)                 # deterministic training, same data
     assert rep.loss_last < rep.loss_first
-    p_np, _ = gb.mlp_train(gb.mlp_init(10, seed=3), X, T, epochs=400, lr=2e-3)
+    p_np, _ = gb.mlp_train(gb.mlp_init(gb.MLP_FEATURES, seed=3), X, T, epochs=400, lr=2e-3)
     np.testing.assert_allclose(p_lib, p_np, rtol=0, atol=1e-3)   # numpy-prepared targets
-    key = lambda c: (c.tpb, c.ctas_per_sm, c.colmajor, c.prefetch2)
     held = [(7, 7, 7), (23, 23, 7)]
-    assert [key(c) for c in gb.mlp_predict_best(None, held)] == [key(c) for c in gb.mlp_predict_best(p_lib, held)]
+    assert [_key(c) for c in gb.mlp_predict_best(None, held)] == [_key(c) for c in gb.mlp_predict_best(p_lib, held)]
     gb.tune_clear()
 
 
 def test_predictor_with_exhaustive_fallback(gb):
     triples = [(13, 13, 13), (5, 13, 13)]
-    params = gb.mlp_init(10, seed=5)
+    params = gb.mlp_init(gb.MLP_FEATURES, seed=5)
     pred = gb.mlp_predict_best(params, triples)
     space = gb.tune_space(gb.DBCSR_FP64)
-
-    def key(c):
-        return (c.tpb, c.ctas_per_sm, c.colmajor, c.prefetch2)
+    key = _key
 
     # an infinite tolerance always keeps the prediction
     gb.tune_clear()

@@ -16,18 +16,18 @@ def gb():
 
 def test_table_round_trip(gb, tmp_path):
     gb.tune_clear()
-    c = gb.KernelCfg(128, 8, 1, 1)
+    c = gb.KernelCfg(128, 8, 1, 1, 1)
     gb.tune_set(gb.DBCSR_FP64, 13, 5, 13, c)
-    gb.tune_set(gb.DBCSR_BF16, 23, 7, 23, gb.KernelCfg(64, 16, 0, 0))
+    gb.tune_set(gb.DBCSR_FP64, 23, 7, 23, gb.KernelCfg(64, 16, 0, 0, 2))      # 161 = 5 * 32 + 1: K-split
     got, found = gb.tune_get(gb.DBCSR_FP64, 13, 5, 13)
-    assert found and (got.tpb, got.ctas_per_sm, got.colmajor, got.prefetch2) == (128, 8, 1, 1)
+    assert found and (got.tpb, got.ctas_per_sm, got.colmajor, got.prefetch2, got.split) == (128, 8, 1, 1, 1)
     path = str(tmp_path / "tune.txt")
     gb.tune_save(path)
     gb.tune_clear()
     assert not gb.tune_get(gb.DBCSR_FP64, 13, 5, 13)[1]
     gb.tune_load(path)
-    got, found = gb.tune_get(gb.DBCSR_BF16, 23, 7, 23)
-    assert found and (got.tpb, got.ctas_per_sm) == (64, 16)
+    got, found = gb.tune_get(gb.DBCSR_FP64, 23, 7, 23)
+    assert found and (got.tpb, got.ctas_per_sm, got.split) == (64, 16, 2)
     gb.tune_set(gb.DBCSR_FP64, 13, 5, 13, None)
     assert not gb.tune_get(gb.DBCSR_FP64, 13, 5, 13)[1]
     gb.tune_clear()
@@ -36,14 +36,25 @@ def test_table_round_trip(gb, tmp_path):
 def test_default_when_absent_and_validation(gb, tmp_path):
     gb.tune_clear()
     c, found = gb.tune_get(gb.DBCSR_FP64, 4, 4, 4)
-    assert not found and c.tpb == 256
+    assert not found and c.tpb == 256 and c.split == -1
     with pytest.raises(gb.DbcsrError):
-        gb.tune_set(gb.DBCSR_FP64, 0, 5, 5, gb.KernelCfg(128, 8, 0, 0))
+        gb.tune_set(gb.DBCSR_FP64, 0, 5, 5, gb.KernelCfg(128, 8, 0, 0, 0))
+    with pytest.raises(gb.DbcsrError):                           # a warp pair for 16 elements
+        gb.tune_set(gb.DBCSR_FP64, 4, 4, 4, gb.KernelCfg(128, 8, 0, 0, 1))
+    with pytest.raises(gb.DbcsrError):                           # K-split: 169 = 5 * 32 + 9 elements
+        gb.tune_set(gb.DBCSR_FP64, 13, 13, 13, gb.KernelCfg(128, 8, 0, 0, 2))
     bad = tmp_path / "bad.txt"
-    bad.write_text("0 13 5 13 100 8 0 0\n")       # 100 threads: not a multiple of 32
+    bad.write_text("0 13 5 13 100 8 0 0 0\n")     # 100 threads: not a multiple of 32
     with pytest.raises(gb.DbcsrError):
         gb.tune_load(str(bad))
-    assert len(gb.tune_space(gb.DBCSR_FP64)) == 60 and len(gb.tune_space(gb.DBCSR_BF16)) == 15
+    bad.write_text("0 13 5 13 128 8 0 0\n")       # the split field missing
+    with pytest.raises(gb.DbcsrError):
+        gb.tune_load(str(bad))
+    # work splits x threads x CTAs per SM x lane order x prefetch; no per-shape BF16 kernels
+    space = gb.tune_space(gb.DBCSR_FP64)
+    assert len(space) == 96 and {c.split for c in space} == {0, 1, 2}
+    with pytest.raises(gb.DbcsrError):
+        gb.tune_space(gb.DBCSR_BF16)
 
 
 def test_mlp_host_side_init_and_features(gb):
@@ -52,17 +63,25 @@ def test_mlp_host_side_init_and_features(gb):
     p = gb.mlp_init(10, seed=1)
     assert p.size == omlp.n_params(10)
     W1, b1, W2, b2, W3, b3 = omlp.unpack(p, 10)
+    assert gb.MLP_FEATURES == 12
     assert np.all(b1 == 0) and np.all(b2 == 0) and b3 == 0
     assert np.abs(W1).max() <= np.sqrt(6 / 74) and np.abs(W2).max() <= np.sqrt(6 / 128)
-    f = gb.mlp_features([(13, 5, 13)], [gb.KernelCfg(128, 8, 1, 0)])[0]
-    expect = [13 / 32, 5 / 32, 13 / 32, np.log2(845) / 15, 65 / 96, 1.0, 0.5, 0.5, 1.0, 0.0]
-    np.testing.assert_allclose(f, expect, rtol=1e-6)
+    # 13 x 5 = 65 elements: one warp uses 3 slots per lane (96 lane slots); a pair 2 per lane;
+    # the K-split 2 per lane plus the remainder element
+    f = gb.mlp_features([(13, 5, 13)] * 3, [gb.KernelCfg(128, 8, 1, 0, s) for s in (0, 1, 2)])
+    base = [13 / 32, 5 / 32, 13 / 32, np.log2(845) / 15]
+    np.testing.assert_allclose(f[0], base + [65 / 96, 0.0, 0.5, 0.5, 1.0, 0.0, 0.0, 3 / 32], rtol=1e-6)
+    np.testing.assert_allclose(f[1], base + [65 / 96, 0.0, 0.5, 0.5, 1.0, 0.0, 1.0, 2 / 32], rtol=1e-6)
+    np.testing.assert_allclose(f[2], base + [65 / 96, 1.0, 0.5, 0.5, 1.0, 0.0, 0.0, 2 / 32], rtol=1e-6)
 
 
 def _records(gb, rng, prec, triples):
     recs = []
     for (m, n, k) in triples:
-        for c in gb.tune_space(prec)[::7]:
+        for c in gb.tune_space(gb.DBCSR_FP64)[::7]:
+            mn = m * n
+            if (c.split == 1 and mn <= 32) or (c.split == 2 and not (mn > 32 and mn % 32 == 1)):
+                continue
             r = gb.TuneRecord()
             r.m, r.n, r.k, r.prec = m, n, k, prec
             r.cfg = c
@@ -77,7 +96,7 @@ def test_predictor_training_data_from_records_file(gb, tmp_path):
     # divided by the population standard deviation of the centred values
     rng = np.random.default_rng(21)
     rf = _records(gb, rng, gb.DBCSR_FP64, [(13, 5, 13), (23, 7, 23), (4, 4, 4)])
-    rb = _records(gb, rng, gb.DBCSR_BF16, [(13, 13, 13)])
+    rb = _records(gb, rng, 99, [(13, 13, 13)])       # records of another precision are skipped
     path = str(tmp_path / "recs.tune")
     gb.tune_records_save(path, rf[:5])
     gb.tune_records_save(path, rf[5:] + rb, append=True)
@@ -92,16 +111,16 @@ def test_predictor_training_data_from_records_file(gb, tmp_path):
     for tt in set(tri):                           # centred per triple
         assert abs(np.mean([v for v, u in zip(T, tri) if u == tt])) < 1e-5
     assert abs(float(np.std(T.astype(np.float64))) - 1.0) < 1e-5
-    Xb, Tb = gb.predictor_data(path, gb.DBCSR_BF16)
+    Xb, Tb = gb.predictor_data(path, 99)
     assert Xb.shape[0] == len(rb)
 
 
 def test_predictor_records_are_checked(gb, tmp_path):
     bad = tmp_path / "bad.tune"
-    bad.write_text("0 13 5 13 128 8 0 0 -1.0\n")       # a non-positive time
+    bad.write_text("0 13 5 13 128 8 0 0 0 -1.0\n")     # a non-positive time
     with pytest.raises(gb.DbcsrError):
         gb.predictor_data(str(bad))
-    bad.write_text("0 13 5 13 128 8 0\n")               # a field missing
+    bad.write_text("0 13 5 13 128 8 0 0 -1.0\n")       # a field missing
     with pytest.raises(gb.DbcsrError):
         gb.predictor_data(str(bad))
     bad.write_text("# nothing\n")
