@@ -221,10 +221,11 @@ def run_reference(args):
     return 0
 
 
-def run_batch(args, gb, synth, torch, barrier):
-    """64 uneven water systems (n_mol log-uniform in [100, 2000], O/H blocks per system):
-    one batched sign iteration vs the same systems solved one after the other, in FP64
-    and with the mixed-precision ladder."""
+def run_batch(args, gb, synth, torch, barrier, small=False):
+    """64 uneven water systems (n_mol log-uniform in [100, 2000], or in [20, 100] with small,
+    O/H blocks per system): one batched sign iteration vs the same systems solved one after
+    the other, in FP64 and with the mixed-precision ladder, with the FP64 block products
+    launched per shape and with one work-queue launch per product."""
     from paper_2003_03868_gb300 import ranks
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -232,7 +233,8 @@ def run_batch(args, gb, synth, torch, barrier):
     if world > 1:
         import torch.distributed as dist
     # every rank solves its own 64 systems (independent problems: weak scaling, no data exchange)
-    ws = synth.batch_systems(seed=synth.batch_seed(rank))
+    ws = (synth.batch_systems(seed=synth.batch_seed(rank), lo=20, hi=100) if small
+          else synth.batch_systems(seed=synth.batch_seed(rank)))
     hs = [synth.build_hamiltonian(w) for w in ws]
     stream = torch.cuda.current_stream()
     Hs = [gb.Matrix.of(h.H, stream=stream.cuda_stream) for h in hs]
@@ -266,6 +268,7 @@ def run_batch(args, gb, synth, torch, barrier):
                 "max_de_band_per_atom_vs_sequential": de, "iterations_min": min(its), "iterations_max": max(its),
                 "ms_multiply": reps[0].ms_multiply, "ms_low": reps[0].ms_low}, reps
 
+    gb.set_fp64_schedule(gb.DBCSR_SCHEDULE_PER_SHAPE)
     f64, reps64 = leg(gb.DBCSR_FP64)
     mixed = None
     if not args.no_mixed:
@@ -274,14 +277,25 @@ def run_batch(args, gb, synth, torch, barrier):
         mixed["max_de_band_per_atom_vs_fp64"] = max(abs(a.e_band - b.e_band) / h.n_atoms
                                                     for a, b, h in zip(repsm, reps64, hs))
         mixed["dtype"] = "bf16x3 (split bf16 hi+lo operands, fp32 accumulate), then f64"
+    # the same legs with one work-queue launch per FP64 product (every shape of up to 9 slots
+    # per lane in one launch)
+    gb.set_fp64_schedule(gb.DBCSR_SCHEDULE_QUEUE)
+    f64q, _ = leg(gb.DBCSR_FP64)
+    mixedq = None if args.no_mixed else leg(gb.DBCSR_MIXED)[0]
+    gb.set_fp64_schedule(gb.DBCSR_SCHEDULE_PER_SHAPE)
+    queue = {"fp64": f64q, "mixed": mixedq,
+             "fp64_queue_over_per_shape_time": f64q["ms_per_step"] / f64["ms_per_step"],
+             "note": "DBCSR_SCHEDULE_QUEUE: one work-queue launch per FP64 product for the small shapes"}
+    name = "batch-64-small" if small else "batch-64"
     out = {"metric": "block-GEMM TFLOP/s (batched sign iteration)", "value": f64["value"],
            "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": f64["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f64", "data": "synthetic",
-           "config": {"workload": "batch-64", "systems_per_rank": len(ws), "molecules_rank0": sum(w.n_mol for w in ws),
+           "config": {"workload": name, "systems_per_rank": len(ws), "molecules_rank0": sum(w.n_mol for w in ws),
                       "atoms_rank0": sum(w.n_atoms for w in ws), "eps_filter": eps, "tol": tol,
                       "parallelism": f"independent systems, 64 per rank x{world}"},
-           **{k: v for k, v in f64.items() if k not in ("value", "ms_per_step", "unit")}, "mixed": mixed}
+           **{k: v for k, v in f64.items() if k not in ("value", "ms_per_step", "unit")}, "mixed": mixed,
+           "queue_schedule": queue}
     if rank == 0:
         print(json.dumps(out))
     if dist:
@@ -997,7 +1011,7 @@ def main():
     ap.add_argument("--side-steps", type=int, default=3, help="timed steps of the side legs of the default run")
     ap.add_argument("--e2e-steps", type=int, default=5, help="timed steps of the end-to-end leg")
     ap.add_argument("--workload", default="sign-4096h2o-mixed",
-                    choices=["sign-4096h2o-mixed", "sign-1024h2o", "sign-512h2o", "sign-512h2o-23-7", "sign-4096h2o", "batch-64",
+                    choices=["sign-4096h2o-mixed", "sign-1024h2o", "sign-512h2o", "sign-512h2o-23-7", "sign-4096h2o", "batch-64", "batch-64-small",
                              "sign-20736h2o-mlp", "mult-32h2o", "sign-1024h2o-orders", "sign-4096h2o-orders",
                              "sign-1024h2o-nonorth", "sign-4096h2o-nonorth", "sign-1024h2o-purify",
                              "sign-4096h2o-purify", "submatrix-6192h2o-szv"],
@@ -1051,8 +1065,8 @@ def main():
 
     if args.workload == "sign-4096h2o-mixed":
         return run_headline(args, gb, synth, torch, barrier, dist, rank, world, local)
-    if args.workload == "batch-64":
-        return run_batch(args, gb, synth, torch, barrier)
+    if args.workload in ("batch-64", "batch-64-small"):
+        return run_batch(args, gb, synth, torch, barrier, small=args.workload == "batch-64-small")
     if args.workload == "submatrix-6192h2o-szv":
         return run_submatrix(args, gb, synth, torch, barrier)
     if args.workload in ("sign-20736h2o-mlp", "mult-32h2o"):

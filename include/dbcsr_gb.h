@@ -288,6 +288,24 @@ dbcsr_status dbcsr_multiply(double alpha, dbcsr_matrix A, dbcsr_matrix B, double
  * Errors: as dbcsr_multiply, and EINVAL for C aliasing A or B; ECUDA if the graph cannot
  * be captured.  Not from the paper's text beyond DBCSR's operations.
  */
+/*
+ * How the FP64 block products of a product are launched (section "Local multiplication":
+ * block products are batched into stacks and the stacks executed by the small-matrix kernels).
+ *   DBCSR_SCHEDULE_PER_SHAPE (default): one launch per (m, n) block shape, each with the
+ *     configuration of the tune table (dbcsr_autotune) or the default;
+ *   DBCSR_SCHEDULE_QUEUE: one launch for every shape: the warps take C blocks from one work
+ *     queue (an atomic counter over the shape lists) and run the single-warp kernel of each
+ *     block's shape (K-split where m n = 32 EF + 1).  Products with a shape of more than 17
+ *     element slots per lane (m n > 544) keep the per-shape launches.
+ * Every C element is summed in the same order either way; the block norms differ only in
+ * rounding where the per-shape schedule uses warp pairs.  Library-wide; not from the paper.
+ * Errors: EINVAL (unknown mode).
+ */
+#define DBCSR_SCHEDULE_PER_SHAPE 0
+#define DBCSR_SCHEDULE_QUEUE 1
+dbcsr_status dbcsr_set_fp64_schedule(int32_t mode);
+int32_t dbcsr_get_fp64_schedule(void);
+
 typedef struct dbcsr_plan_* dbcsr_plan;
 dbcsr_status dbcsr_multiply_plan(double alpha, dbcsr_matrix A, dbcsr_matrix B, dbcsr_matrix C, double eps_filter,
                                  int32_t prec, dbcsr_plan* out, dbcsr_mult_stats* stats);

@@ -300,6 +300,19 @@ def _sign_flags(full_products: bool, low: int, low_correction: bool = False) -> 
             | (_ffi.DBCSR_SIGN_LOW_CORRECTION if low_correction else 0))
 
 
+DBCSR_SCHEDULE_PER_SHAPE, DBCSR_SCHEDULE_QUEUE = 0, 1
+
+
+def set_fp64_schedule(mode: int) -> None:
+    """DBCSR_SCHEDULE_PER_SHAPE (one launch per block shape, tuned) or DBCSR_SCHEDULE_QUEUE (one
+    work-queue launch per product) for the FP64 block products (dbcsr_set_fp64_schedule)."""
+    _check(lib().dbcsr_set_fp64_schedule(int(mode)), "set_fp64_schedule")
+
+
+def fp64_schedule() -> int:
+    return int(lib().dbcsr_get_fp64_schedule())
+
+
 def pool_trim(keep_bytes: int = 0) -> None:
     """Return the library's cached device memory above keep_bytes to the driver."""
     _check(lib().dbcsr_pool_trim(int(keep_bytes)), "pool_trim")

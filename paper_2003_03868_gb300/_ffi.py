@@ -127,6 +127,8 @@ SIGNATURES = [
     ("dbcsr_predictor_data", C.c_int, [C.c_char_p, C.c_int32, P, P, C.c_int64, C.POINTER(C.c_int64)]),
     ("dbcsr_predictor_params", C.c_int, [C.c_int32, P]),
     ("dbcsr_partition_rows", C.c_int, [C.c_int32, P, P, C.c_int32, P]),
+    ("dbcsr_set_fp64_schedule", C.c_int, [C.c_int32]),
+    ("dbcsr_get_fp64_schedule", C.c_int32, []),
     ("dbcsr_halo_rows", C.c_int, [C.c_int32, P, P, P, C.c_int32, P, C.c_int32, C.POINTER(C.c_int32)]),
     ("dbcsr_bench_peak", C.c_double, [C.c_int32, C.c_int32, C.c_int32, C.c_int32]),
     ("dbcsr_launch_count", C.c_int64, []),

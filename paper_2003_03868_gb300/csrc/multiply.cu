@@ -578,20 +578,13 @@ __device__ __forceinline__ ProdMeta fetch_meta(const SmmArgs& S, int64_t base, i
 // lanes first fetch the metadata of 32 products at once (one product each:
 // block offsets and inner size) and broadcast it with shuffles, so the
 // dependent index loads are not paid product by product.
+// C block k by one warp (or, PAIR, by the warp pair `pair`, this warp owning half `part` of
+// the element slots; sh_part is the pairs' exchange area, parity its alternating slot).
 template <int E, bool PAIR>
-__global__ void __launch_bounds__(256) k_smm_f64(int64_t nlist, const int64_t* __restrict__ list, SmmArgs S) {
-    // PAIR: two warps (neighbours in the CTA) share one C block, each owning half of its
-    // element slots, so a large block needs half the registers per thread; the halves'
-    // norm sums meet in shared memory behind a 64-thread named barrier of the pair.
+__device__ __forceinline__ void smm_block(int64_t k, const SmmArgs& S, int lane, int part, int pair, int parity,
+                                          double (*sh_part)[2][2]) {
     constexpr int EL = PAIR ? (E + 1) / 2 : E;
-    __shared__ double sh_part[PAIR ? 4 : 1][2][2];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int part = PAIR ? (warp & 1) : 0, pair = PAIR ? (warp >> 1) : warp;
-    const int per_cta = PAIR ? (blockDim.x >> 6) : (blockDim.x >> 5);
-    const int64_t stride = (int64_t)gridDim.x * per_cta;
-    int parity = 0;
-    for (int64_t w = (int64_t)blockIdx.x * per_cta + pair; w < nlist; w += stride, parity ^= 1) {
-        const int64_t k = list[w];
+    {
         const int I = S.f_row[k], J = S.f_col[k];
         const int m = S.bs[I], n = S.bs[J];
         const int mn = m * n;
@@ -669,6 +662,22 @@ __global__ void __launch_bounds__(256) k_smm_f64(int64_t nlist, const int64_t* _
     }
 }
 
+template <int E, bool PAIR>
+__global__ void __launch_bounds__(256) k_smm_f64(int64_t nlist, const int64_t* __restrict__ list, SmmArgs S) {
+    // PAIR: two warps (neighbours in the CTA) share one C block, each owning half of its
+    // element slots, so a large block needs half the registers per thread; the halves'
+    // norm sums meet in shared memory behind a 64-thread named barrier of the pair.
+    __shared__ double sh_part[PAIR ? 4 : 1][2][2];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int part = PAIR ? (warp & 1) : 0, pair = PAIR ? (warp >> 1) : warp;
+    const int per_cta = PAIR ? (blockDim.x >> 6) : (blockDim.x >> 5);
+    const int64_t stride = (int64_t)gridDim.x * per_cta;
+    int parity = 0;
+    for (int64_t w = (int64_t)blockIdx.x * per_cta + pair; w < nlist; w += stride, parity ^= 1)
+        smm_block<E, PAIR>(list[w], S, lane, part, pair, parity, sh_part);
+}
+
+
 // FP64 class with a K-split remainder: the first 32*EF elements of the block are
 // spread over the lanes as in k_smm_f64, and the last R elements are summed along
 // K instead: lane l takes the products l, l+32, ... of the block (the product
@@ -676,11 +685,8 @@ __global__ void __launch_bounds__(256) k_smm_f64(int64_t nlist, const int64_t* _
 // the 32 partial sums.  For m*n = 32*EF + 1 (13x5, 5x13, 23x7, 7x23) this removes
 // a 32-lane pass that would carry one useful element.
 template <int EF, int R>
-__global__ void __launch_bounds__(256) k_smm_f64_ks(int64_t nlist, const int64_t* __restrict__ list, SmmArgs S) {
-    const int lane = threadIdx.x & 31;
-    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < nlist; w += warps) {
-        const int64_t k = list[w];
+__device__ __forceinline__ void smm_block_ks(int64_t k, const SmmArgs& S, int lane) {
+    {
         const int I = S.f_row[k], J = S.f_col[k];
         const int m = S.bs[I], n = S.bs[J];
         int ii[EF], jj[EF], ir[R], jr[R];
@@ -763,6 +769,58 @@ __global__ void __launch_bounds__(256) k_smm_f64_ks(int64_t nlist, const int64_t
         }
     }
 }
+
+template <int EF, int R>
+__global__ void __launch_bounds__(256) k_smm_f64_ks(int64_t nlist, const int64_t* __restrict__ list, SmmArgs S) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < nlist; w += warps)
+        smm_block_ks<EF, R>(list[w], S, lane);
+}
+
+// One launch for every block shape of a product: the warps take C blocks from one work queue
+// (the shape lists one after another) in chunks of kQueueChunk with an atomic counter, and
+// each runs the single-warp body of its block's class (the K-split one where m n = 32 EF + 1).
+// Blocks of up to kQueueMaxE element slots per lane (13 x 13, 23 x 7 and smaller: two CTAs of
+// 256 threads fit an SM without spills); larger shapes keep their own launches.  Every C
+// element and norm is summed as by the single-warp kernels.
+constexpr int kQueueChunk = 4;
+constexpr int kQueueMaxE = 9;
+
+template <int E>
+__device__ __forceinline__ void queue_dispatch(int e, int ks, int64_t k, const SmmArgs& S, int lane) {
+    if constexpr (E <= kQueueMaxE) {
+        if (e == E) {
+            if constexpr (E >= 2) {
+                if (ks) {
+                    smm_block_ks<E - 1, 1>(k, S, lane);
+                    return;
+                }
+            }
+            smm_block<E, false>(k, S, lane, 0, 0, 0, nullptr);
+            return;
+        }
+        queue_dispatch<E + 1>(e, ks, k, S, lane);
+    }
+}
+
+__global__ void __launch_bounds__(256, 2) k_smm_f64_queue(int64_t nlist, const int64_t* __restrict__ list, SmmArgs S,
+                                                      unsigned long long* __restrict__ counter) {
+    const int lane = threadIdx.x & 31;
+    while (true) {
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(counter, (unsigned long long)kQueueChunk);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base >= (unsigned long long)nlist) break;
+        for (int c = 0; c < kQueueChunk && base + c < (unsigned long long)nlist; ++c) {
+            const int64_t k = list[base + c];
+            const int mn = S.bs[S.f_row[k]] * S.bs[S.f_col[k]];
+            const int ks = (mn > 32 && (mn & 31) == 1) ? 1 : 0;
+            queue_dispatch<1>((mn + 31) >> 5, ks, k, S, lane);
+        }
+    }
+}
+
 
 // Stable partition of the formed blocks by shape: flag[k] = (block k is m x n).
 __global__ void k_shape_flags(int64_t nform, const int32_t* __restrict__ f_row, const int32_t* __restrict__ f_col,
@@ -868,6 +926,27 @@ __global__ void k_keep_twinned(int64_t nb, const int64_t* __restrict__ mirror, i
 TuneCfg default_cfg(int prec) {
     (void)prec;
     return TuneCfg{};
+}
+
+std::atomic<int> g_fp64_schedule{0};
+
+// The whole formed-block list of a product (every shape) in one work-queue launch.
+void launch_smm_queue(int64_t cnt, const int64_t* list, const SmmArgs& sa, unsigned long long* counter,
+                      cudaStream_t s) {
+    if (cnt <= 0) return;
+    static int per_sm[64] = {};
+    int dev = 0;
+    DBG_CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) fail(DBCSR_ECAPACITY, "multiply: device ordinal out of range");
+    if (!per_sm[dev]) {
+        int b = 0;
+        DBG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_smm_f64_queue, 256, 0));
+        per_sm[dev] = std::max(b, 1);
+    }
+    DBG_CK(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s));
+    const int64_t g = std::min<int64_t>(ceil_div(cnt, 8), (int64_t)num_sms() * per_sm[dev]);
+    k_smm_f64_queue<<<(unsigned)g, 256, 0, s>>>(cnt, list, sa, counter);
+    DBG_LAUNCH_CK();
 }
 
 bool cfg_valid(int m, int n, const TuneCfg& c) {
@@ -1112,6 +1191,7 @@ void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbc
     std::vector<ShapeLaunch> launches;
     std::unique_ptr<LowTierPlan, void (*)(LowTierPlan*)> lt(nullptr, lowtier_plan_delete);
     LowTierOut lto{};
+    DBuf<int64_t> qcounter;                 // the work queue's counter (one-launch schedule)
     const int kmax = *std::max_element(A->h_bs.begin(), A->h_bs.end());
     if (nform) {
         sa = SmmArgs{f_row.p, f_col.p, f_off.p, f_pbeg.p, f_cin.p, prod_a.p, prod_b.p, A->col.p, A->off.p, A->data.p,
@@ -1125,11 +1205,15 @@ void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbc
             pos.alloc(nform + 1, s);
             list.alloc(nform, s);
         }
-        int64_t at = 0;
+        // with the one-launch schedule, the shapes the work queue takes come first in the list
+        const bool queue = !bf16 && g_fp64_schedule.load() == 1;
+        int64_t at = 0, at_q = 0;
+        for (int pass = 0; pass < 2; ++pass)
         for (int m = 1; m <= kMaxBlock; ++m)
             for (int n = 1; n <= kMaxBlock; ++n) {
                 const int64_t cnt = shapes[m * (kMaxBlock + 1) + n];
                 if (!cnt) continue;
+                if ((queue && ((m * n + 31) >> 5) <= kQueueMaxE) != (pass == 0)) continue;
                 bytes_min += 8.0 * (double)cnt * m * n;
                 if (bf16) continue;
                 k_shape_flags<<<grid_for(nform, 256), 256, 0, s>>>(nform, f_row.p, f_col.p, A->bs.p, mirror.p,
@@ -1138,6 +1222,7 @@ void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbc
                 scan_exclusive(flag.p, pos.p, nform, s);
                 k_class_scatter<<<grid_for(nform, 256), 256, 0, s>>>(nform, flag.p, pos.p, list.p + at);
                 DBG_LAUNCH_CK();
+                if (pass == 0) at_q += cnt;
                 launches.push_back({m, n, cnt});
                 at += cnt;
             }
@@ -1157,9 +1242,21 @@ void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbc
             lowtier_run(*lt, A, lto, s);
             n_smm_launches = 1;
         }
+        if (at_q > 0) {
+            // the queue's shapes in one launch, replacing their per-shape entries
+            std::vector<ShapeLaunch> rest{{0, 0, at_q}};
+            int64_t q = 0;
+            for (const ShapeLaunch& L : launches) {
+                if (q < at_q) q += L.cnt;
+                else rest.push_back(L);
+            }
+            launches = std::move(rest);
+            qcounter.alloc(1, s);
+        }
         at = 0;
         for (const ShapeLaunch& L : launches) {
-            launch_smm_shape(L.m, L.n, L.cnt, list.p + at, sa, tune_lookup(prec, L.m, L.n, kmax), s);
+            if (L.m == 0) launch_smm_queue(L.cnt, list.p, sa, (unsigned long long*)qcounter.p, s);
+            else launch_smm_shape(L.m, L.n, L.cnt, list.p + at, sa, tune_lookup(prec, L.m, L.n, kmax), s);
             at += L.cnt;
         }
         if (!bf16)         n_smm_launches = (int32_t)launches.size();
@@ -1223,7 +1320,8 @@ void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbc
             }
             int64_t at = 0;
             for (const ShapeLaunch& L : launches) {
-                launch_smm_shape(L.m, L.n, L.cnt, list.p + at, sa, tune_lookup(prec, L.m, L.n, kmax), cs);
+                if (L.m == 0) launch_smm_queue(L.cnt, list.p, sa, (unsigned long long*)qcounter.p, cs);
+                else launch_smm_shape(L.m, L.n, L.cnt, list.p + at, sa, tune_lookup(prec, L.m, L.n, kmax), cs);
                 at += L.cnt;
             }
             zero_small(cs);
@@ -1256,6 +1354,7 @@ void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbc
         plan->bufs_i64.push_back(std::move(f_pbeg));
         plan->bufs_i64.push_back(std::move(f_cin));
         plan->bufs_f64.push_back(std::move(c_dev2));
+        plan->bufs_i64.push_back(std::move(qcounter));
         plan->bufs_u8.push_back(std::move(f_comp));
         plan->lt = lt.release();
         A->plans++;
@@ -1341,6 +1440,18 @@ MultPlan::~MultPlan() {
 }  // namespace dbg
 
 extern "C" {
+
+dbcsr_status dbcsr_set_fp64_schedule(int32_t mode) {
+    if (mode != DBCSR_SCHEDULE_PER_SHAPE && mode != DBCSR_SCHEDULE_QUEUE) {
+        dbg::set_last_error("set_fp64_schedule: mode must be DBCSR_SCHEDULE_PER_SHAPE or DBCSR_SCHEDULE_QUEUE");
+        return DBCSR_EINVAL;
+    }
+    dbg::g_fp64_schedule.store(mode);
+    dbg::set_last_error("");
+    return DBCSR_OK;
+}
+
+int32_t dbcsr_get_fp64_schedule(void) { return dbg::g_fp64_schedule.load(); }
 
 struct dbcsr_plan_ {
     dbg::MultPlan plan;

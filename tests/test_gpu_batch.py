@@ -91,3 +91,47 @@ def test_batch_of_one_and_different_mu(gb):
     # mu anywhere in the gap gives the same projector
     assert abs(reps[0].e_band - reps[1].e_band) < 1e-8
     assert reps[0].alpha != reps[1].alpha
+
+
+@pytest.fixture
+def queue_schedule(gb):
+    gb.set_fp64_schedule(gb.DBCSR_SCHEDULE_QUEUE)
+    yield
+    gb.set_fp64_schedule(gb.DBCSR_SCHEDULE_PER_SHAPE)
+
+
+def test_one_launch_schedule_sums_like_the_per_shape_launches(gb):
+    # every C element is the same sum in the same order: only the norms of warp-pair classes
+    # (per-shape schedule) may round differently
+    a = synth.random_block_matrix([13, 5, 5, 23, 7, 7, 1, 32] * 3, 0.6, 41)
+    b = synth.random_block_matrix([13, 5, 5, 23, 7, 7, 1, 32] * 3, 0.6, 42)
+    A, B = gb.Matrix.of(a), gb.Matrix.of(b)
+    out = {}
+    for mode in (gb.DBCSR_SCHEDULE_PER_SHAPE, gb.DBCSR_SCHEDULE_QUEUE):
+        gb.set_fp64_schedule(mode)
+        C = gb.Matrix(A.blk_size, A.stream)
+        st = gb.multiply(1.0, A, B, 0.0, C, 0.0)
+        out[mode] = (C.export(), st.n_launches)
+    gb.set_fp64_schedule(gb.DBCSR_SCHEDULE_PER_SHAPE)
+    (rp0, c0, d0), n0 = out[gb.DBCSR_SCHEDULE_PER_SHAPE]
+    (rp1, c1, d1), n1 = out[gb.DBCSR_SCHEDULE_QUEUE]
+    assert np.array_equal(rp0, rp1) and np.array_equal(c0, c1) and np.array_equal(d0, d1)
+    # the small shapes share one launch; the shapes with more than 9 slots per lane keep theirs
+    big = sum(1 for m in (13, 5, 23, 7, 1, 32) for n in (13, 5, 23, 7, 1, 32) if (m * n + 31) // 32 > 9)
+    assert n1 == 1 + big and n0 > n1
+    ref = bsr.multiply(1.0, bsr.Mat.of(a), bsr.Mat.of(b))
+    np.testing.assert_allclose(d1, ref.data, rtol=0, atol=1e-12 * np.abs(ref.data).max())
+
+
+def test_batch_equals_single_runs_with_the_one_launch_schedule(gb, queue_schedule):
+    hs = _systems(5, 23)
+    Hs = [gb.Matrix.of(h.H) for h in hs]
+    mus = [0.0, 0.2, 0.0, -0.22, 0.1]
+    Ps, reps, st = gb.sign_iterate_batched(Hs, mus, 1e-7, 1e-9)
+    for h, H, P, r, mu in zip(hs, Hs, Ps, reps, mus):
+        g = gb.sign_iterate(H, mu, 1e-7, 1e-9)
+        o = sign.sign_iterate(bsr.Mat.of(h.H), mu, 1e-7, 1e-9)
+        assert abs(r.e_band - o.e_band) / h.n_atoms < 1e-7
+        assert r.iterations == g.report.iterations
+        for a, b in zip(P.export(), g.P.export()):
+            assert np.array_equal(a, b)
