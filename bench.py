@@ -868,6 +868,19 @@ def run_headline(args, gb, synth, torch, barrier, dist, rank, world, local):
     H = gb.Matrix.of(h.H, stream=stream.cuda_stream)
     side_steps = max(1, min(args.steps, args.side_steps))
     peak, peak_info = fp64_peak(gb, torch)
+    # the FP64 kernels' configurations for the block shapes of both workloads, picked by the
+    # autotuner (untimed setup, like a tuned parameter table shipped with the library)
+    tuning = None
+    gb.tune_clear()
+    if not args.no_tune:
+        t0 = time.time()
+        triples = [(m, n, max(b)) for b in ((23, 7), (13, 5)) for m in b for n in b]
+        recs = gb.autotune(triples, gb.DBCSR_FP64, stack_len=args.tune_stack, reps=3)
+        d = gb.tune_get(gb.DBCSR_FP64, 1, 1, 1)[0]
+        tuning = {"seconds": time.time() - t0, "stack_len": args.tune_stack, "configs_timed": len(recs),
+                  "triples": [{"mnk": list(t), "best_ms": min(r.ms for r in recs if (r.m, r.n, r.k) == t),
+                               "default_ms": float(gb.time_configs(*t, [d], stack_len=args.tune_stack, reps=3)[0]),
+                               "split": gb.tune_get(gb.DBCSR_FP64, *t)[0].split} for t in triples]}
 
     # main leg: the mixed ladder (split BF16 while r >= 1e-4, then FP64), args.steps timed steps
     clocks = Clocks(local)
@@ -984,7 +997,7 @@ def run_headline(args, gb, synth, torch, barrier, dist, rank, world, local):
                                                                       "ms_filter")},
            "gpu_launches": launches, "clocks": clk, "roofline": dominant,
            "fp64_tail_roofline": f_roof, "low_tier_roofline": l_roof,
-           "fp64": fp64, "low_correction": low_correction, "e2e": e2e, "sign_1024h2o": c2}
+           "fp64": fp64, "low_correction": low_correction, "e2e": e2e, "sign_1024h2o": c2, "tuning": tuning}
     if rank == 0 and world == 1 and not args.no_cpu:
         smp = RowsSample(h, w, CPU_ROWS_FRAC)
         f, dt, cores = smp.run()
@@ -1010,6 +1023,7 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=2, help="Newton-Schulz steps in the oracle CPU baseline")
     ap.add_argument("--side-steps", type=int, default=3, help="timed steps of the side legs of the default run")
     ap.add_argument("--e2e-steps", type=int, default=5, help="timed steps of the end-to-end leg")
+    ap.add_argument("--no-tune", action="store_true", help="default run: skip the autotuning of the block shapes")
     ap.add_argument("--workload", default="sign-4096h2o-mixed",
                     choices=["sign-4096h2o-mixed", "sign-1024h2o", "sign-512h2o", "sign-512h2o-23-7", "sign-4096h2o", "batch-64", "batch-64-small",
                              "sign-20736h2o-mlp", "mult-32h2o", "sign-1024h2o-orders", "sign-4096h2o-orders",

@@ -57,8 +57,10 @@ typedef enum {
     DBCSR_FP64 = 0,       /* FP64 operands, FP64 accumulation */
     DBCSR_BF16 = 2,       /* BF16 operands (round to nearest even), FP32 accumulation, FP64 result */
     DBCSR_MIXED = 3,      /* sign iteration only: low-precision tier while the residual >= switch, then FP64 */
-    DBCSR_BF16X3 = 4      /* split BF16 operands a = hi + lo (both BF16), A B ~ Ah Bh + Ah Bl + Al Bh on the
+    DBCSR_BF16X3 = 4,     /* split BF16 operands a = hi + lo (both BF16), A B ~ Ah Bh + Ah Bl + Al Bh on the
                              BF16 tensor cores with FP32 accumulation (about 16 significant bits), FP64 result */
+    DBCSR_TF32 = 5,       /* dense products only: FP32 data, TF32 operands (10 stored bits), FP32 accumulation */
+    DBCSR_TF32X3 = 6      /* dense products only: FP32 data, split TF32 operands (three products, about 21 bits) */
 } dbcsr_prec;
 
 /* Work counters of one product.  Counts refer to the blocks the product
@@ -653,6 +655,21 @@ dbcsr_status dbcsr_predictor_params(int32_t prec, float* params);
  */
 dbcsr_status dbcsr_tune_predicted(int32_t prec, const float* params, const int32_t* mnk, int32_t ntriples,
                                   int64_t stack_len, int32_t reps, double tolerance, int32_t* fell_back);
+
+/*
+ * Batched dense product C[b] = alpha A[b] B[b] + beta C[b], b < nb, for row-major n x n
+ * matrices at A + b n^2, B + b n^2, C + b n^2 in device memory (the caller's; the library
+ * allocates only its packing scratch), on the stream given (cudaStream_t, may be NULL).
+ * The submatrix method's dense step (section "Submatrix Method") runs on it.
+ *   prec DBCSR_FP64: double data, FP64 pipe;
+ *   DBCSR_TF32 / DBCSR_TF32X3: float data on the TF32 tensor cores, plain or split (three
+ *   products of TF32 halves, close to FP32 arithmetic).
+ * C must not overlap A or B.  Returns after the product completes.  Errors: EINVAL (bad
+ * argument, other prec), ECAPACITY (nb > 65535), ENOMEM, ETIMEOUT (a bounded wait of the
+ * tensor-core kernel ran out), ECUDA.
+ */
+dbcsr_status dbcsr_dense_multiply(int32_t prec, int64_t nb, int32_t n, double alpha, const void* A, const void* B,
+                                  double beta, void* C, void* stream);
 
 /*
  * Sharding over several GPUs (section "DBCSR library": block rows and columns distributed over

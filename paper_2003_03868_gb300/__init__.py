@@ -18,6 +18,7 @@ import numpy as np
 
 from . import _ffi
 from ._ffi import DBCSR_FP64, DBCSR_BF16, DBCSR_MIXED, DBCSR_BF16X3, MultStats, SignOpts, SignReport  # noqa: F401
+from ._ffi import DBCSR_TF32, DBCSR_TF32X3  # noqa: F401
 from ._ffi import KernelCfg, TuneRecord, MlpOpts, MlpReport, MLP_FEATURES  # noqa: F401
 
 
@@ -311,6 +312,16 @@ def set_fp64_schedule(mode: int) -> None:
 
 def fp64_schedule() -> int:
     return int(lib().dbcsr_get_fp64_schedule())
+
+
+def dense_multiply(prec: int, nb: int, n: int, alpha: float, A_ptr: int, B_ptr: int, beta: float, C_ptr: int,
+                   stream: int | None = None) -> None:
+    """C[b] = alpha A[b] B[b] + beta C[b] for nb row-major n x n matrices in device memory, given
+    by address (dbcsr_dense_multiply; double data for DBCSR_FP64, float for DBCSR_TF32 / TF32X3)."""
+    s = current_stream() if stream is None else int(stream)
+    _check(lib().dbcsr_dense_multiply(int(prec), int(nb), int(n), float(alpha), C.c_void_p(int(A_ptr)),
+                                      C.c_void_p(int(B_ptr)), float(beta), C.c_void_p(int(C_ptr)), C.c_void_p(s)),
+           "dense_multiply")
 
 
 def pool_trim(keep_bytes: int = 0) -> None:

@@ -9,7 +9,7 @@ LIB_PATH = os.path.join(HERE, "libdbcsr_gb.so")
 
 DBCSR_OK, DBCSR_EINVAL, DBCSR_ENOMEM, DBCSR_ECAPACITY, DBCSR_ECUDA = 0, 1, 2, 3, 4
 DBCSR_ENAN, DBCSR_ENOTCONV, DBCSR_ETIMEOUT, DBCSR_ESTATE = 5, 6, 7, 8
-DBCSR_FP64, DBCSR_BF16, DBCSR_MIXED, DBCSR_BF16X3 = 0, 2, 3, 4
+DBCSR_FP64, DBCSR_BF16, DBCSR_MIXED, DBCSR_BF16X3, DBCSR_TF32, DBCSR_TF32X3 = 0, 2, 3, 4, 5, 6
 DBCSR_PURIFY_TC2, DBCSR_PURIFY_TRS4 = 1, 2
 DBCSR_SIGN_FULL_PRODUCTS, DBCSR_SIGN_PLAIN_BF16, DBCSR_SIGN_LOW_CORRECTION = 1, 2, 4
 MAX_HISTORY = 128
@@ -128,6 +128,7 @@ SIGNATURES = [
     ("dbcsr_predictor_params", C.c_int, [C.c_int32, P]),
     ("dbcsr_partition_rows", C.c_int, [C.c_int32, P, P, C.c_int32, P]),
     ("dbcsr_set_fp64_schedule", C.c_int, [C.c_int32]),
+    ("dbcsr_dense_multiply", C.c_int, [C.c_int32, C.c_int64, C.c_int32, C.c_double, P, P, C.c_double, P, P]),
     ("dbcsr_get_fp64_schedule", C.c_int32, []),
     ("dbcsr_halo_rows", C.c_int, [C.c_int32, P, P, P, C.c_int32, P, C.c_int32, C.POINTER(C.c_int32)]),
     ("dbcsr_bench_peak", C.c_double, [C.c_int32, C.c_int32, C.c_int32, C.c_int32]),

@@ -2,7 +2,7 @@
 
 Every translation unit under csrc/ is compiled in parallel (-gencode
 arch=compute_103a,code=sm_103a -O3 -lineinfo), then linked into one shared
-library with the CUDA runtime linked statically and cuBLAS dynamically.
+library with the CUDA runtime linked statically (no other library).
 """
 from __future__ import annotations
 
@@ -28,16 +28,6 @@ def nvcc() -> str:
         if c and os.path.exists(c):
             return c
     raise RuntimeError("nvcc not found")
-
-
-def cublas_link(cc: str) -> list[str]:
-    """cuBLAS (the submatrix method's dense batched GEMMs), with the toolkit's library
-    directory as the run path."""
-    root = os.path.dirname(os.path.dirname(os.path.realpath(cc)))
-    dirs = [d for d in (os.path.join(root, "lib64"), *glob.glob(os.path.join(root, "targets", "*", "lib")))
-            if os.path.exists(os.path.join(d, "libcublas.so"))]
-    rp = [a for d in dirs[:1] for a in ("-Xlinker", "-rpath", "-Xlinker", d)]
-    return ["-lcublas", *(["-L", dirs[0]] if dirs else []), *rp]
 
 
 def _stale(obj: str, src: str) -> bool:
@@ -69,7 +59,7 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
         list(ex.map(one, todo))
     if todo or force or not os.path.exists(LIB):
         tmp = LIB + f".tmp{os.getpid()}"
-        cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "static", *cublas_link(cc)]
+        cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "static"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stderr}")

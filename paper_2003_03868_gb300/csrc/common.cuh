@@ -281,6 +281,15 @@ int64_t lowtier_tiles(const LowTierPlan& L);
 double lowtier_tensor_flops(const LowTierPlan& L);
 double lowtier_copy_bytes(const LowTierPlan& L);
 
+// ---- dense.cu
+// C[b] = alpha A[b] B[b] + beta C[b] for nb row-major n x n matrices (b < 65536): FP64 on the
+// FP64 pipe; FP32 storage on the TF32 tensor cores (split: three products of TF32 halves,
+// close to FP32 arithmetic).  C must not alias A or B.
+void dense_gemm_f64(int64_t nb, int n, double alpha, const double* A, const double* B, double beta, double* C,
+                    cudaStream_t s);
+void dense_gemm_tf32(int64_t nb, int n, float alpha, const float* A, const float* B, float beta, float* C, bool split,
+                     cudaStream_t s);
+
 // ---- submatrix.cu
 dbcsr_status submatrix_sign(dbcsr_matrix_* H, double mu, const dbcsr_sign_opts* opts, dbcsr_matrix_* P,
                             dbcsr_sign_report* rep);

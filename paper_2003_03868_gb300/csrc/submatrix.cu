@@ -11,14 +11,12 @@
 //   * block (i, j) of P, i in I_j: the rows of i and columns of j of (1 - X) / 2.  P has the
 //     pattern of H.
 //
-// The gather, residual and scatter kernels are the library's; the dense products are
-// strided-batched GEMMs of cuBLAS (plain library GEMMs).  The submatrices are grouped by
-// padded size and run in chunks of at most kChunkBytes of device memory.  FP64 uses
-// DGEMM; the mixed mode runs FP32 GEMMs on the TF32 tensor cores while the largest
-// residual is at least switch_tol, then plain FP32 GEMMs (the iteration corrects the
-// earlier rounding as in the sparse ladder).
-#include <cublas_v2.h>
-
+// Every kernel is the library's: gather, residual, scatter, and the batched dense products
+// (dense.cu).  The submatrices are grouped by padded size and run in chunks of at most
+// kChunkBytes of device memory.  FP64 runs on the FP64 pipe; the mixed mode stores FP32 and
+// multiplies on the TF32 tensor cores while the largest residual is at least switch_tol,
+// then with split TF32 (three products of TF32 halves, close to FP32 arithmetic; the
+// iteration corrects the earlier rounding as in the sparse ladder).
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -34,14 +32,6 @@ namespace {
 
 constexpr int kPad = 16;                          // submatrix edges rounded up to 16
 constexpr size_t kChunkBytes = size_t(8) << 30;   // X, X2 and the update buffer of one chunk
-
-#define DBG_CUBLAS(call)                                                                   \
-    do {                                                                                   \
-        cublasStatus_t s_ = (call);                                                        \
-        if (s_ != CUBLAS_STATUS_SUCCESS)                                                   \
-            ::dbg::fail(s_ == CUBLAS_STATUS_ALLOC_FAILED ? DBCSR_ENOMEM : DBCSR_ECUDA,     \
-                        std::string(#call) + ": cuBLAS status " + std::to_string((int)s_)); \
-    } while (0)
 
 __device__ __forceinline__ int64_t find_col(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
                                             int64_t row, int32_t c) {
@@ -145,26 +135,16 @@ struct Chunk {
     std::vector<int64_t> dstart;
 };
 
-template <class T>
-struct Gemm;
-template <>
-struct Gemm<double> {
-    static cublasStatus_t run(cublasHandle_t h, int n, double alpha, const double* A, const double* B, double beta,
-                              double* C, int b) {
-        const long long st = (long long)n * n;
-        return cublasDgemmStridedBatched(h, CUBLAS_OP_N, CUBLAS_OP_N, n, n, n, &alpha, A, n, st, B, n, st, &beta, C, n,
-                                         st, b);
-    }
-};
-template <>
-struct Gemm<float> {
-    static cublasStatus_t run(cublasHandle_t h, int n, double alpha, const float* A, const float* B, double beta,
-                              float* C, int b) {
-        const long long st = (long long)n * n;
-        const float a = (float)alpha, c = (float)beta;
-        return cublasSgemmStridedBatched(h, CUBLAS_OP_N, CUBLAS_OP_N, n, n, n, &a, A, n, st, B, n, st, &c, C, n, st, b);
-    }
-};
+// C = alpha A B + beta C for every matrix of the chunk: FP64, or FP32 storage in TF32
+// (split: three products of TF32 halves).
+void batched_gemm(int32_t b, int n, double alpha, const double* A, const double* B, double beta, double* C, bool,
+                  cudaStream_t s) {
+    dense_gemm_f64(b, n, alpha, A, B, beta, C, s);
+}
+void batched_gemm(int32_t b, int n, double alpha, const float* A, const float* B, double beta, float* C, bool split,
+                  cudaStream_t s) {
+    dense_gemm_tf32(b, n, (float)alpha, A, B, (float)beta, C, split, s);
+}
 
 struct ChunkResult {
     int iterations = 0, tf32_iterations = 0;
@@ -173,7 +153,7 @@ struct ChunkResult {
 
 template <class T>
 ChunkResult run_chunk(const Chunk& ck, dbcsr_matrix_* H, dbcsr_matrix_* P, double mu, double inv_alpha,
-                      const dbcsr_sign_opts& o, bool mixed, cublasHandle_t hb, cudaStream_t s) {
+                      const dbcsr_sign_opts& o, bool mixed, cudaStream_t s) {
     const int32_t b = (int32_t)ck.sub_j.size();
     const int n = ck.n_pad;
     const int64_t elems = (int64_t)b * n * n;
@@ -200,10 +180,9 @@ ChunkResult run_chunk(const Chunk& ck, dbcsr_matrix_* H, dbcsr_matrix_* P, doubl
     std::vector<double> h_r2(b);
     ChunkResult cr;
     bool tf32 = mixed;
-    DBG_CUBLAS(cublasSetMathMode(hb, tf32 ? CUBLAS_TF32_TENSOR_OP_MATH : CUBLAS_DEFAULT_MATH));
     const double gemm_flops = 2.0 * (double)n * n * n * b;
     while (true) {
-        DBG_CUBLAS(Gemm<T>::run(hb, n, 1.0, X.p, X.p, 0.0, X2.p, b));          // X2 = X X
+        batched_gemm(b, n, 1.0, X.p, X.p, 0.0, X2.p, !tf32, s);                // X2 = X X
         cr.flops += gemm_flops;
         k_sub_residual<T><<<grid, 256, 0, s>>>(b, n, X2.p, r2.p);
         DBG_LAUNCH_CK();
@@ -224,13 +203,12 @@ ChunkResult run_chunk(const Chunk& ck, dbcsr_matrix_* H, dbcsr_matrix_* P, doubl
         // 1e-4 relative error per product over n ~ 400) lies below the switch.
         if (tf32 && rm < o.switch_tol) {
             tf32 = false;
-            DBG_CUBLAS(cublasSetMathMode(hb, CUBLAS_DEFAULT_MATH));
         }
         if (!tf32 && rm < o.tol) break;
         if (cr.iterations >= o.max_iter) break;
         // X <- 1.5 X - 0.5 X X2
         DBG_CK(cudaMemcpyAsync(U.p, X.p, sizeof(T) * elems, cudaMemcpyDeviceToDevice, s));
-        DBG_CUBLAS(Gemm<T>::run(hb, n, -0.5, X.p, X2.p, 1.5, U.p, b));
+        batched_gemm(b, n, -0.5, X.p, X2.p, 1.5, U.p, !tf32, s);
         cr.flops += gemm_flops;
         std::swap(X.p, U.p);
     }
@@ -290,13 +268,6 @@ dbcsr_status submatrix_sign(dbcsr_matrix_* H, double mu, const dbcsr_sign_opts* 
     }
     dbcsr_sign_report r{};
     r.alpha = alpha;
-    cublasHandle_t hb = nullptr;
-    DBG_CUBLAS(cublasCreate(&hb));
-    struct HandleGuard {
-        cublasHandle_t h;
-        ~HandleGuard() { if (h) cublasDestroy(h); }
-    } guard{hb};
-    DBG_CUBLAS(cublasSetStream(hb, s));
     int max_it = 0, max_tf32 = 0;
     double r_max = 0.0, flops = 0.0;
     int64_t nsub = 0;
@@ -319,8 +290,8 @@ dbcsr_status submatrix_sign(dbcsr_matrix_* H, double mu, const dbcsr_sign_opts* 
                 }
                 ck.sub_n.push_back(acc);
             }
-            const ChunkResult cr = mixed ? run_chunk<float>(ck, H, P, mu, 1.0 / alpha, o, true, hb, s)
-                                         : run_chunk<double>(ck, H, P, mu, 1.0 / alpha, o, false, hb, s);
+            const ChunkResult cr = mixed ? run_chunk<float>(ck, H, P, mu, 1.0 / alpha, o, true, s)
+                                         : run_chunk<double>(ck, H, P, mu, 1.0 / alpha, o, false, s);
             max_it = std::max(max_it, cr.iterations);
             max_tf32 = std::max(max_tf32, cr.tf32_iterations);
             r_max = std::max(r_max, cr.r_max);

@@ -66,3 +66,38 @@ def test_submatrix_arguments_are_checked(gb):
     with pytest.raises(gb.DbcsrError) as e:
         gb.submatrix_sign(H, 0.0, 0.0)
     assert e.value.status == gb._ffi.DBCSR_EINVAL
+
+
+@pytest.mark.parametrize("n,nb", [(16, 1), (100, 3), (130, 2), (257, 1), (400, 2)])
+def test_dense_products_match_fp64_reference(gb, n, nb):
+    # the submatrix method's dense kernels against FP64 products: FP64 to rounding; TF32 and
+    # split TF32 within the rounding of their operands (2^-11 and about 2^-21 relative) summed
+    # over n terms, in FP32 accumulation
+    import torch
+    rng = np.random.default_rng(n + nb)
+    A = rng.uniform(-1, 1, (nb, n, n))
+    B = rng.uniform(-1, 1, (nb, n, n))
+    C0 = rng.uniform(-1, 1, (nb, n, n))
+    ref = -0.5 * np.einsum("bij,bjk->bik", A, B) + 1.5 * C0
+    mag = 0.5 * np.einsum("bij,bjk->bik", np.abs(A), np.abs(B)) + 1.5 * np.abs(C0)
+    for prec, dt, tol in ((gb.DBCSR_FP64, torch.float64, 4 * n * 2.0 ** -53),
+                          (gb.DBCSR_TF32, torch.float32, 2.0 ** -10 + n * 2.0 ** -24),
+                          (gb.DBCSR_TF32X3, torch.float32, 2.0 ** -19 + n * 2.0 ** -24)):
+        a = torch.tensor(A, dtype=dt, device="cuda")
+        b = torch.tensor(B, dtype=dt, device="cuda")
+        c = torch.tensor(C0, dtype=dt, device="cuda")
+        gb.dense_multiply(prec, nb, n, -0.5, a.data_ptr(), b.data_ptr(), 1.5, c.data_ptr())
+        torch.cuda.synchronize()
+        got = c.double().cpu().numpy()
+        # the inputs as the kernel saw them (FP32 data carries its own rounding)
+        inp_err = 0 if dt == torch.float64 else 2.0 ** -23 * 3
+        assert np.all(np.abs(got - ref) <= (tol + inp_err) * mag + 1e-300), prec
+    if n >= 100:     # plain TF32 really rounds: its error is far above split TF32's
+        a = torch.tensor(A, dtype=torch.float32, device="cuda")
+        b = torch.tensor(B, dtype=torch.float32, device="cuda")
+        errs = []
+        for prec in (gb.DBCSR_TF32, gb.DBCSR_TF32X3):
+            c = torch.zeros((nb, n, n), dtype=torch.float32, device="cuda")
+            gb.dense_multiply(prec, nb, n, 1.0, a.data_ptr(), b.data_ptr(), 0.0, c.data_ptr())
+            errs.append(np.abs(c.double().cpu().numpy() - np.einsum("bij,bjk->bik", A, B)).max())
+        assert errs[0] > 30 * errs[1]
