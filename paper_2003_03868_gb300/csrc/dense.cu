@@ -26,7 +26,7 @@ constexpr int kDM = 128;                 // M of the MMA and rows of an A tile
 constexpr int kDNMax = 256;              // rows of the widest B tile (N of the MMA)
 constexpr int kDStepK = 8;               // TF32 elements per MMA K step (32 bytes)
 constexpr int kDRun = 2;                 // K steps per stage
-constexpr int kDStages = 3;
+constexpr int kDStages = 4;
 constexpr int kDThreads = 128;
 constexpr long long kDWaitLimit = 4000000000ll;
 
@@ -39,27 +39,37 @@ __device__ __forceinline__ float to_tf32(float x) {
 // Packs a batch of n x n row-major matrices into tiles: tile (b, t) holds rows
 // [t R, t R + R) of M[b] (transpose = 0) or of M[b]^T (transpose = 1), all K = kpad columns,
 // as K steps of 8: per step np parts (hi, lo) x 2 chunks x R rows x 16 bytes.  Zero outside n.
+// A thread writes one 16-byte chunk row (4 consecutive K elements of one row), threads in the
+// order of the packed layout, so the writes are contiguous.
 __global__ void k_dense_pack(int64_t total, int n, int kpad, int R, int ntiles, int np, int transpose,
                              const float* __restrict__ M, float* __restrict__ out) {
+    const int nsteps = kpad / kDStepK;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        // e enumerates (b, t, row r, column c) with c fastest
-        const int c = (int)(e % kpad);
-        int64_t rest = e / kpad;
-        const int r = (int)(rest % R);
-        rest /= R;
+        // e enumerates (b, t, step, chunk, row r) with r fastest
+        const int r = (int)(e % R);
+        int64_t rest = e / R;
+        const int ch = (int)(rest % 2);
+        rest /= 2;
+        const int st = (int)(rest % nsteps);
+        rest /= nsteps;
         const int t = (int)(rest % ntiles);
         const int64_t b = rest / ntiles;
-        const int row = t * R + r;
-        float x = 0.f;
-        if (row < n && c < n) x = transpose ? M[b * n * n + (int64_t)c * n + row] : M[b * n * n + (int64_t)row * n + c];
-        const float hi = to_tf32(x);
+        const int row = t * R + r, c0 = st * kDStepK + ch * 4;
+        float x[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int c = c0 + q;
+            x[q] = (row < n && c < n) ? (transpose ? M[b * n * n + (int64_t)c * n + row] : M[b * n * n + (int64_t)row * n + c])
+                                      : 0.f;
+        }
         const int64_t step_bytes = (int64_t)np * 2 * R * 16;
-        const int64_t tile_bytes = (int64_t)(kpad / kDStepK) * step_bytes;
-        uint8_t* base = reinterpret_cast<uint8_t*>(out) + (b * ntiles + t) * tile_bytes + (c / kDStepK) * step_bytes;
-        const int within = c % kDStepK;
-        float* p = reinterpret_cast<float*>(base + (within / 4) * (R * 16) + r * 16) + (within & 3);
-        *p = hi;
-        if (np == 2) *reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(p) + 2 * R * 16) = to_tf32(x - hi);
+        uint8_t* base = reinterpret_cast<uint8_t*>(out) + ((b * ntiles + t) * nsteps + st) * step_bytes + ch * (R * 16) +
+                        r * 16;
+        float4 hi = make_float4(to_tf32(x[0]), to_tf32(x[1]), to_tf32(x[2]), to_tf32(x[3]));
+        *reinterpret_cast<float4*>(base) = hi;
+        if (np == 2)
+            *reinterpret_cast<float4*>(base + 2 * R * 16) =
+                make_float4(to_tf32(x[0] - hi.x), to_tf32(x[1] - hi.y), to_tf32(x[2] - hi.z), to_tf32(x[3] - hi.w));
     }
 }
 
@@ -144,12 +154,16 @@ __global__ void __launch_bounds__(kDThreads, 1) k_dense_tf32(DenseArgs D) {
                 }
             }
             tc::mma_commit(&S.empty[slot]);
-            if (s + kDStages < nstage) {
-                if (!tc::mbar_wait(&S.empty[slot], phase, kDWaitLimit)) {
+            // refill the previous stage's slot: its MMAs ran before these, which keep the tensor
+            // cores busy while this thread waits
+            const int pr = s - 1;
+            if (pr >= 0 && pr + kDStages < nstage) {
+                const int pslot = pr % kDStages;
+                if (!tc::mbar_wait(&S.empty[pslot], (uint32_t)(pr / kDStages) & 1u, kDWaitLimit)) {
                     ok = false;
                     break;
                 }
-                issue(s + kDStages);
+                issue(pr + kDStages);
             }
         }
         tc::mma_commit(&S.done);
@@ -266,7 +280,7 @@ void dense_gemm_tf32(int64_t nb, int n, float alpha, const float* A, const float
     pb.alloc(b_bytes / 4, s);
     err.alloc(1, s);
     err.zero();
-    const int64_t ta = nb * ntm * (int64_t)kDM * kpad, tb = nb * ntn * (int64_t)NT * kpad;
+    const int64_t ta = nb * ntm * (int64_t)kDM * (kpad / 4), tb = nb * ntn * (int64_t)NT * (kpad / 4);
     k_dense_pack<<<grid_for(ta, 256), 256, 0, s>>>(ta, n, kpad, kDM, ntm, np, 0, A, pa.p);
     DBG_LAUNCH_CK();
     k_dense_pack<<<grid_for(tb, 256), 256, 0, s>>>(tb, n, kpad, NT, ntn, np, 1, B, pb.p);
