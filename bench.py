@@ -36,11 +36,13 @@ NOMINAL_BF16 = 2250.0
 NOMINAL_FP64 = 1.25
 FALLBACK_BF16_BURST, FALLBACK_BF16_SUSTAINED = 1900.0, 1700.0
 
-# DRAM bytes per executed flop of the FP64 block-product kernels (dram__bytes_read.sum +
-# dram__bytes_write.sum over the captured launches / their flops), from a capture of a few
-# launches of the small 512-water 23/7 case; a full launch's traffic is this ratio times its
-# flops.  None until captured for the current kernel (cleared whenever the kernel changes).
-SMM_F64_BYTES_PER_FLOP = None
+# DRAM bytes per flop of the FP64 block-product kernels: dram__bytes_read.sum +
+# dram__bytes_write.sum over three captured launches (7x7, 23x7 and 7x23 classes of one product
+# of the 512-water 23/7 case) divided by their executed DFMA flops (2 x
+# sm__sass_thread_inst_executed_op_dfma_pred_on.sum): 2.494 GB / 21.63 GFLOP.  A full launch's
+# traffic is this ratio times its flops (the larger systems are assumed to re-read operands at the
+# same rate per flop).  Reset to None whenever the kernel changes.
+SMM_F64_BYTES_PER_FLOP = 0.1153
 
 
 def bf16_peak():
@@ -815,7 +817,7 @@ def sign_leg(gb, torch, barrier, H, h, w, steps, warmup, prec, **kw):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     acc = {k: 0.0 for k in ("flops", "flops_low", "ms_low", "ms_multiply", "ms_symbolic", "ms_filter",
-                            "bytes_min_fp64", "launches_fp64")}
+                            "bytes_min_fp64", "launches_fp64", "flops_tensor", "bytes_tensor")}
     for _ in range(steps):
         r = one()
         for k in acc:
@@ -847,14 +849,20 @@ def low_roofline(acc, ms, steps):
     """The low tier's split-BF16 block-product kernel against the measured sustained bf16 peak."""
     bpk, bpk_src = bf16_peak()
     low_alg = acc["flops_low"] / (acc["ms_low"] * 1e-3) / 1e12 if acc["ms_low"] > 0 else 0.0
+    t = acc["ms_low"] * 1e-3
     return {"bound": "tensor", "kernel": LOW_TIER_KERNEL, "achieved": 3 * low_alg, "unit": "TFLOP/s",
             "peak": bpk, "frac": 3 * low_alg / bpk, "peak_source": bpk_src, "algorithmic_tflops": low_alg,
+            "executed_tflops": acc["flops_tensor"] / t / 1e12 if t > 0 else None,
+            "padding_factor": acc["flops_tensor"] / (3 * acc["flops_low"]) if acc["flops_low"] > 0 else None,
+            "copy_gbs": acc["bytes_tensor"] / t / 1e9 if t > 0 else None,
             "kernel_share_of_step": acc["ms_low"] / ms if ms > 0 else None, "ms_per_step": acc["ms_low"] / steps,
-            "note": "achieved counts the three bf16 products (hi*hi, hi*lo, lo*hi) of every unpadded "
-                    "2mnk block product"}
+            "note": "achieved counts the three bf16 products (hi*hi, hi*lo, lo*hi) of every unpadded 2mnk "
+                    "block product; executed_tflops counts every issued MMA (group-tile padding included); "
+                    "the time is k_lowtier's own (CUDA events around its launch); the operand packing is "
+                    "timed with the symbolic phase"}
 
 
-LOW_TIER_KERNEL = "k_smm_bf16<MT,NT,split>"
+LOW_TIER_KERNEL = "k_lowtier"
 
 
 def run_headline(args, gb, synth, torch, barrier, dist, rank, world, local):
@@ -896,7 +904,58 @@ def run_headline(args, gb, synth, torch, barrier, dist, rank, world, local):
     ms_all, flops_all = ranks.job_timing(ms_m, acc_m["flops"], dist, "cuda")
     value = flops_all / (ms_all * 1e-3) / 1e12
 
-    # the plain FP64 iteration of the same H
+    fp64 = low_correction = c2 = None
+    de_vs_fp64 = speedup = None
+    if not args.main_only:
+        fp64, low_correction, de_vs_fp64, speedup = headline_side_legs(args, gb, torch, barrier, H, h, w,
+                                                                       side_steps, peak, peak_info, rm, ms_all)
+
+    # end to end through the public API: H from pinned host memory each step, P exported to pinned
+    # host memory each step (row pointers, block columns, values), the report read back
+    e2e = None
+    if not args.no_e2e:
+        e2e = headline_e2e(args, gb, torch, barrier, stream, h, w, rm)
+
+    # the 1,024-water configuration beside it: FP64 (eps 1e-7, tol 1e-9) and the mixed ladder
+    if not args.main_only:
+        c2 = headline_sign1024(gb, synth, torch, barrier, stream, side_steps, peak, peak_info)
+
+    f_roof = fp64_roofline(acc_m, ms_m, args.steps, peak, peak_info)
+    l_roof = low_roofline(acc_m, ms_m, args.steps)
+    dominant = f_roof if f_roof["kernel_share_of_step"] >= (l_roof["kernel_share_of_step"] or 0.0) else l_roof
+    out = {"metric": HEADLINE_METRIC, "value": value, "unit": "TFLOP/s",
+           "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_all / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3+f64",
+           "data": "synthetic",
+           "config": {"workload": "sign-4096h2o-23-7-mixed-vs-fp64", "n_mol": w.n_mol, "N": w.n,
+                      "blocks": {"O": w.basis[0], "H": w.basis[1]}, "eps_filter": w.eps_filter, "tol": w.tol,
+                      "switch": w.switch, "mu": h.mu,
+                      "l2": "inputs larger than L2 (H alone is %.0f MB; 129 MB L2)" % (h.H.data.nbytes / 1e6),
+                      "parallelism": f"replicas x{world}"},
+           "time_to_p_ms": ms_all / args.steps, "iterations": rm.report.iterations,
+           "fp64_from_step": rm.report.fp64_from, "converged": bool(rm.report.converged),
+           "stalled": bool(rm.report.stalled), "residual": rm.report.residual, "trace_p": rm.report.trace_p,
+           "n_occ": h.n_occ, "e_band": rm.report.e_band, "e_band_both_spins": 2.0 * rm.report.e_band,
+           "de_band_per_atom_vs_fp64": de_vs_fp64, "speedup_vs_fp64": speedup,
+           "ms_per_step_phases": {k: acc_m[k] / args.steps for k in ("ms_low", "ms_multiply", "ms_symbolic",
+                                                                      "ms_filter")},
+           "gpu_launches": launches, "clocks": clk, "roofline": dominant,
+           "fp64_tail_roofline": f_roof, "low_tier_roofline": l_roof,
+           "fp64": fp64, "low_correction": low_correction, "e2e": e2e, "sign_1024h2o": c2, "tuning": tuning}
+    if rank == 0 and world == 1 and not args.no_cpu:
+        smp = RowsSample(h, w, CPU_ROWS_FRAC)
+        f, dt, cores = smp.run()
+        out["cpu_baseline"] = {"value": f / dt / 1e12, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+                               "sample": smp.text(f, dt)}
+    if rank == 0:
+        print(json.dumps(out))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def headline_side_legs(args, gb, torch, barrier, H, h, w, side_steps, peak, peak_info, rm, ms_all):
+    """The plain FP64 iteration of the headline H and the low-correction option beside the mixed leg."""
     rf, ms_f, acc_f = sign_leg(gb, torch, barrier, H, h, w, side_steps, 1, gb.DBCSR_FP64)
     ms_f_all, flops_f_all = ranks.job_timing(ms_f, acc_f["flops"], dist, "cuda")
     fp64 = {"time_to_p_ms": ms_f_all / side_steps, "value": flops_f_all / (ms_f_all * 1e-3) / 1e12,
@@ -913,47 +972,52 @@ def run_headline(args, gb, synth, torch, barrier, dist, rank, world, local):
                       "de_band_per_atom_vs_fp64": abs(rc.report.e_band - rf.report.e_band) / h.n_atoms,
                       "note": "DBCSR_SIGN_LOW_CORRECTION: X*X, residual, test, filter and traces in FP64; "
                               "the update's correction product in split BF16"}
+    return fp64, low_correction, abs(rm.report.e_band - rf.report.e_band) / h.n_atoms, \
+        fp64["time_to_p_ms"] / (ms_all / args.steps)
 
-    # end to end through the public API: H from pinned host memory each step, P exported to pinned
-    # host memory each step (row pointers, block columns, values), the report read back
-    e2e = None
-    if not args.no_e2e:
-        e2e_steps = max(1, min(args.steps, args.e2e_steps))
-        data_pin = torch.from_numpy(np.ascontiguousarray(h.H.data)).pin_memory()
-        rows_pin = torch.from_numpy(np.ascontiguousarray(
-            np.repeat(np.arange(h.H.blk_size.shape[0], dtype=np.int32), np.diff(h.H.row_ptr)))).pin_memory()
-        cols_pin = torch.from_numpy(np.ascontiguousarray(h.H.col, dtype=np.int32)).pin_memory()
-        nb, nzp, nep = rm.P.info()
-        cap_z, cap_e = int(nzp * 1.25) + 1024, int(nep * 1.25) + 65536
-        p_rp = torch.empty(nb + 1, dtype=torch.int64).pin_memory()
-        p_col = torch.empty(cap_z, dtype=torch.int32).pin_memory()
-        p_dat = torch.empty(cap_e, dtype=torch.float64).pin_memory()
-        h2d = int(data_pin.numel() * 8 + rows_pin.numel() * 4 + cols_pin.numel() * 4)
-        barrier()
-        f0 = time.perf_counter()
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-        ev[0].record(stream)
-        fl, d2h = 0.0, 0
-        for _ in range(e2e_steps):
-            Hs = gb.Matrix.from_pinned(h.H.blk_size, rows_pin.data_ptr(), cols_pin.data_ptr(), cols_pin.numel(),
-                                       data_pin.data_ptr(), stream=stream.cuda_stream)
-            rr = gb.sign_iterate(Hs, h.mu, w.eps_filter, w.tol, prec=gb.DBCSR_MIXED, switch_tol=w.switch)
-            d2h += rr.P.export_to(p_rp.data_ptr(), p_col.data_ptr(), cap_z, p_dat.data_ptr(), cap_e)
-            fl += rr.report.flops
-            d2h += 3 * 8                                                # trace, band energy, residual
-            _ = (float(rr.report.e_band), float(rr.report.trace_p), float(rr.report.residual))
-            rr.P.close()
-            Hs.close()
-        ev[1].record(stream)
-        torch.cuda.synchronize()
-        ms2 = ev[0].elapsed_time(ev[1])
-        e2e = {"value": fl / (ms2 * 1e-3) / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h // e2e_steps, "ms_per_step": ms2 / e2e_steps, "steps": e2e_steps,
-               "wall_s": time.perf_counter() - f0,
-               "note": "dbcsr_put_blocks + dbcsr_finalize from pinned host buffers, the mixed sign iteration, "
-                       "dbcsr_export of P into pinned host buffers"}
 
-    # the 1,024-water configuration beside it: FP64 (eps 1e-7, tol 1e-9) and the mixed ladder
+def headline_e2e(args, gb, torch, barrier, stream, h, w, rm):
+    """The mixed sign iteration end to end: H from pinned host memory, P exported to pinned host memory."""
+    import numpy as np
+    e2e_steps = max(1, min(args.steps, args.e2e_steps))
+    data_pin = torch.from_numpy(np.ascontiguousarray(h.H.data)).pin_memory()
+    rows_pin = torch.from_numpy(np.ascontiguousarray(
+        np.repeat(np.arange(h.H.blk_size.shape[0], dtype=np.int32), np.diff(h.H.row_ptr)))).pin_memory()
+    cols_pin = torch.from_numpy(np.ascontiguousarray(h.H.col, dtype=np.int32)).pin_memory()
+    nb, nzp, nep = rm.P.info()
+    cap_z, cap_e = int(nzp * 1.25) + 1024, int(nep * 1.25) + 65536
+    p_rp = torch.empty(nb + 1, dtype=torch.int64).pin_memory()
+    p_col = torch.empty(cap_z, dtype=torch.int32).pin_memory()
+    p_dat = torch.empty(cap_e, dtype=torch.float64).pin_memory()
+    h2d = int(data_pin.numel() * 8 + rows_pin.numel() * 4 + cols_pin.numel() * 4)
+    barrier()
+    f0 = time.perf_counter()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record(stream)
+    fl, d2h = 0.0, 0
+    for _ in range(e2e_steps):
+        Hs = gb.Matrix.from_pinned(h.H.blk_size, rows_pin.data_ptr(), cols_pin.data_ptr(), cols_pin.numel(),
+                                   data_pin.data_ptr(), stream=stream.cuda_stream)
+        rr = gb.sign_iterate(Hs, h.mu, w.eps_filter, w.tol, prec=gb.DBCSR_MIXED, switch_tol=w.switch)
+        d2h += rr.P.export_to(p_rp.data_ptr(), p_col.data_ptr(), cap_z, p_dat.data_ptr(), cap_e)
+        fl += rr.report.flops
+        d2h += 3 * 8                                                # trace, band energy, residual
+        _ = (float(rr.report.e_band), float(rr.report.trace_p), float(rr.report.residual))
+        rr.P.close()
+        Hs.close()
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    ms2 = ev[0].elapsed_time(ev[1])
+    e2e = {"value": fl / (ms2 * 1e-3) / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": d2h // e2e_steps, "ms_per_step": ms2 / e2e_steps, "steps": e2e_steps,
+           "wall_s": time.perf_counter() - f0,
+           "note": "dbcsr_put_blocks + dbcsr_finalize from pinned host buffers, the mixed sign iteration, "
+                   "dbcsr_export of P into pinned host buffers"}
+    return e2e
+
+
+def headline_sign1024(gb, synth, torch, barrier, stream, side_steps, peak, peak_info):
+    """The 1,024-water configuration (13/5): FP64 and the mixed ladder."""
     w2 = synth.SIGN_1024
     h2 = synth.build_hamiltonian(w2)
     H2 = gb.Matrix.of(h2.H, stream=stream.cuda_stream)
@@ -974,40 +1038,7 @@ def run_headline(args, gb, synth, torch, barrier, dist, rank, world, local):
                     "low_tier_roofline": low_roofline(acc2m, ms2m, side_steps)},
           "unit": "TFLOP/s", "unit_time": "ms"}
     H2.close()
-
-    f_roof = fp64_roofline(acc_m, ms_m, args.steps, peak, peak_info)
-    l_roof = low_roofline(acc_m, ms_m, args.steps)
-    dominant = f_roof if f_roof["kernel_share_of_step"] >= (l_roof["kernel_share_of_step"] or 0.0) else l_roof
-    out = {"metric": HEADLINE_METRIC, "value": value, "unit": "TFLOP/s",
-           "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_all / args.steps,
-           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3+f64",
-           "data": "synthetic",
-           "config": {"workload": "sign-4096h2o-23-7-mixed-vs-fp64", "n_mol": w.n_mol, "N": w.n,
-                      "blocks": {"O": w.basis[0], "H": w.basis[1]}, "eps_filter": w.eps_filter, "tol": w.tol,
-                      "switch": w.switch, "mu": h.mu,
-                      "l2": "inputs larger than L2 (H alone is %.0f MB; 129 MB L2)" % (h.H.data.nbytes / 1e6),
-                      "parallelism": f"replicas x{world}"},
-           "time_to_p_ms": ms_all / args.steps, "iterations": rm.report.iterations,
-           "fp64_from_step": rm.report.fp64_from, "converged": bool(rm.report.converged),
-           "stalled": bool(rm.report.stalled), "residual": rm.report.residual, "trace_p": rm.report.trace_p,
-           "n_occ": h.n_occ, "e_band": rm.report.e_band, "e_band_both_spins": 2.0 * rm.report.e_band,
-           "de_band_per_atom_vs_fp64": abs(rm.report.e_band - rf.report.e_band) / h.n_atoms,
-           "speedup_vs_fp64": fp64["time_to_p_ms"] / (ms_all / args.steps),
-           "ms_per_step_phases": {k: acc_m[k] / args.steps for k in ("ms_low", "ms_multiply", "ms_symbolic",
-                                                                      "ms_filter")},
-           "gpu_launches": launches, "clocks": clk, "roofline": dominant,
-           "fp64_tail_roofline": f_roof, "low_tier_roofline": l_roof,
-           "fp64": fp64, "low_correction": low_correction, "e2e": e2e, "sign_1024h2o": c2, "tuning": tuning}
-    if rank == 0 and world == 1 and not args.no_cpu:
-        smp = RowsSample(h, w, CPU_ROWS_FRAC)
-        f, dt, cores = smp.run()
-        out["cpu_baseline"] = {"value": f / dt / 1e12, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
-                               "sample": smp.text(f, dt)}
-    if rank == 0:
-        print(json.dumps(out))
-    if dist:
-        dist.destroy_process_group()
-    return 0
+    return c2
 
 
 def main():
@@ -1024,6 +1055,9 @@ def main():
     ap.add_argument("--side-steps", type=int, default=3, help="timed steps of the side legs of the default run")
     ap.add_argument("--e2e-steps", type=int, default=5, help="timed steps of the end-to-end leg")
     ap.add_argument("--no-tune", action="store_true", help="default run: skip the autotuning of the block shapes")
+    ap.add_argument("--main-only", action="store_true",
+                    help="default run: the mixed leg alone (no FP64, low-correction or 1,024-water legs), "
+                         "for launch lists whose kernel shares match the headline step")
     ap.add_argument("--workload", default="sign-4096h2o-mixed",
                     choices=["sign-4096h2o-mixed", "sign-1024h2o", "sign-512h2o", "sign-512h2o-23-7", "sign-4096h2o", "batch-64", "batch-64-small",
                              "sign-20736h2o-mlp", "mult-32h2o", "sign-1024h2o-orders", "sign-4096h2o-orders",
@@ -1155,7 +1189,7 @@ def main():
             m0, m1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             m0.record(stream)
             acc = {"flops": 0.0, "flops_low": 0.0, "ms_low": 0.0, "ms_multiply": 0.0, "ms_symbolic": 0.0,
-                   "ms_filter": 0.0}
+                   "ms_filter": 0.0, "flops_tensor": 0.0, "bytes_tensor": 0.0}
             for _ in range(args.steps):
                 rm = one()
                 for k in acc:
@@ -1166,8 +1200,6 @@ def main():
             return rm, m0.elapsed_time(m1), acc
 
         rm, mms, acc = time_mixed(gb.DBCSR_BF16X3)
-        bpk, bpk_src = bf16_peak()
-        low_alg = acc["flops_low"] / (acc["ms_low"] * 1e-3) / 1e12 if acc["ms_low"] > 0 else 0.0
         mixed = {"time_to_p_ms": mms / args.steps, "value": acc["flops"] / (mms * 1e-3) / 1e12, "unit": "TFLOP/s",
                  "speedup_vs_fp64": (ms_all / args.steps) / (mms / args.steps),
                  "iterations": rm.report.iterations, "fp64_from_step": rm.report.fp64_from,
@@ -1177,12 +1209,7 @@ def main():
                  "switch": 1e-4,
                  "dtype": "bf16x3 (split bf16 hi+lo operands, fp32 accumulate), then f64",
                  "ms_per_step": {k: acc[k] / args.steps for k in ("ms_low", "ms_multiply", "ms_symbolic", "ms_filter")},
-                 "low_tier_roofline": {"bound": "tensor", "kernel": "k_smm_bf16<MT,NT,split>",
-                                       "achieved": 3 * low_alg, "unit": "TFLOP/s", "peak": bpk,
-                                       "frac": 3 * low_alg / bpk, "peak_source": bpk_src,
-                                       "algorithmic_tflops": low_alg,
-                                       "note": "achieved counts the three bf16 products (hi*hi, hi*lo, lo*hi) "
-                                               "of every unpadded 2mnk block product"}}
+                 "low_tier_roofline": low_roofline(acc, mms, args.steps)}
         rp_, mps, _ = time_mixed(gb.DBCSR_BF16)
         mixed["plain_bf16"] = {"time_to_p_ms": mps / args.steps, "iterations": rp_.report.iterations,
                                "fp64_from_step": rp_.report.fp64_from,

@@ -43,8 +43,13 @@ constexpr int kRunMax = 2;                     // K steps per stage (one bulk co
 constexpr int kStageBytesMax = kRunMax * 2 * 2 * 2 * kGroupRows * 16;   // 28 KB
 constexpr int kStages = 5;
 constexpr int kOutStride = kTileRows - 15;     // 113 floats per staged output row (odd: no bank conflicts)
-constexpr int kLtThreads = 192;                // producer, MMA, 4 epilogue warps
-constexpr int kTmemCols = 256;                 // two accumulators of up to 128 columns
+constexpr int kEpiWarps = 8;                   // two per TMEM lane quadrant
+constexpr int kEpiThreads = 32 * kEpiWarps;
+constexpr int kLoaderWarp = 2 + kEpiWarps;     // fetches the epilogue's tables one tile ahead
+constexpr int kLtThreads = 64 + kEpiThreads + 32;   // producer, MMA, epilogue warps, table loader
+constexpr int kAccs = 4;                       // TMEM accumulators of up to 128 columns
+constexpr int kTmemCols = 128 * kAccs;
+constexpr int kEpiBatch = 8;                   // C-input loads a lane issues before its first store
 constexpr long long kWaitLimit = 4000000000ll; // about 2 s at 2 GHz
 
 // ------------------------------------------------------------------ groups (host)
@@ -525,21 +530,28 @@ struct LtArgs {
     int* err;                                // 1: a wait ran out
 };
 
+// What the epilogue needs of one C tile: the atom blocks it writes and where.
+struct LtTables {
+    int64_t koff[kGroupMembers][kGroupMembers];   // element offset of the formed block
+    int64_t kcin[kGroupMembers][kGroupMembers];   // element offset of its C input, -1 without
+    int32_t tbl[kGroupMembers][kGroupMembers];    // formed block of (row member, column member) or -1
+    int32_t rowblk[kGroupMembers], colblk[kGroupMembers];
+    int32_t rowrec[kGroupMembers], colrec[kGroupMembers];   // first row | rows << 8
+    int32_t nm, nn, wc, live;
+};
+
 struct LtShared {
     alignas(1024) uint8_t stage[kStages][kStageBytesMax];
     float out[kTileRows][kOutStride];        // the finished accumulator, staged for coalesced writes
-    int32_t tbl[kGroupMembers][kGroupMembers];
-    int64_t koff[kGroupMembers][kGroupMembers];   // element offset of the formed block
-    int64_t kcin[kGroupMembers][kGroupMembers];   // element offset of its C input, -1 without
-    int32_t rowblk[kGroupMembers], colblk[kGroupMembers];
-    int32_t rowrec[kGroupMembers], colrec[kGroupMembers];   // first row | rows << 8
-    uint64_t full[kStages], empty[kStages], acc_full[2], acc_empty[2], fin;
+    LtTables T[2];                           // filled by the loader warp, one tile ahead
+    uint64_t full[kStages], empty[kStages], acc_full[kAccs], acc_empty[kAccs], fin;
+    uint64_t tbl_full[2], tbl_empty[2];
     uint32_t tmem_base;
     int abort;                               // set once by a role whose wait ran out
     int epi_stop;                            // the epilogue's snapshot of abort
 };
 
-__device__ __forceinline__ void lt_epi_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+__device__ __forceinline__ void lt_epi_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kEpiThreads) : "memory"); }
 
 __device__ __forceinline__ int lt_aborted(const LtShared& S) { return *(volatile const int*)&S.abort; }
 
@@ -566,9 +578,13 @@ __global__ void __launch_bounds__(kLtThreads, 1) k_lowtier(LtArgs A) {
             tc::mbar_init(&S.full[i], 1);
             tc::mbar_init(&S.empty[i], 1);
         }
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < kAccs; ++i) {
             tc::mbar_init(&S.acc_full[i], 1);
-            tc::mbar_init(&S.acc_empty[i], 128);
+            tc::mbar_init(&S.acc_empty[i], kEpiThreads);
+        }
+        for (int i = 0; i < 2; ++i) {
+            tc::mbar_init(&S.tbl_full[i], 32);
+            tc::mbar_init(&S.tbl_empty[i], 1);
         }
         tc::mbar_init(&S.fin, 1);
         S.abort = 0;
@@ -649,8 +665,8 @@ __global__ void __launch_bounds__(kLtThreads, 1) k_lowtier(LtArgs A) {
         int it = 0;
         bool stop = false;
         for (int64_t t = blockIdx.x; t < A.ntiles && !stop; t += gridDim.x, ++it) {
-            const int acc = it & 1;
-            const uint32_t acc_phase = (uint32_t)(it >> 1) & 1u;
+            const int acc = it % kAccs;
+            const uint32_t acc_phase = (uint32_t)(it / kAccs) & 1u;
             const int wc = A.g.g_w[A.c_tcol[t]];
             const int ra = lt_rows(A.g.g_w[A.c_trow[t]]), rb = lt_rows(wc);
             const int sa_bytes = np * 2 * ra * 16, sb_bytes = np * 2 * rb * 16;
@@ -710,52 +726,88 @@ __global__ void __launch_bounds__(kLtThreads, 1) k_lowtier(LtArgs A) {
             tc::mma_commit(&S.fin);
             if (!tc::mbar_wait(&S.fin, 0, kWaitLimit)) lt_fail(A, S);
         }
+    } else if (warp == kLoaderWarp) {
+        // ---------------- table loader: the tables of the epilogue's next tile, while it writes
+        // the current one (every lane fetches 8 of the 256 member pairs, loads batched by level)
+        constexpr int kPer = kGroupMembers * kGroupMembers / 32;
+        int it = 0;
+        for (int64_t t = blockIdx.x; t < A.ntiles; t += gridDim.x, ++it) {
+            const int b = it & 1;
+            const uint32_t ph = (uint32_t)(it >> 1) & 1u;
+            int ok = 1;
+            if (lane == 0) {
+                ok = tc::mbar_wait(&S.tbl_empty[b], ph ^ 1u, kWaitLimit) ? 1 : 0;
+                if (!ok) lt_fail(A, S);
+            }
+            if (!__shfl_sync(0xffffffffu, ok, 0) || __shfl_sync(0xffffffffu, lt_aborted(S), 0)) break;
+            LtTables& T = S.T[b];
+            const int32_t G = __ldg(A.c_trow + t), Gc = __ldg(A.c_tcol + t);
+            int32_t k[kPer];
+#pragma unroll
+            for (int u = 0; u < kPer; ++u) k[u] = __ldg(A.c_tbl + t * (kGroupMembers * kGroupMembers) + 32 * u + lane);
+            const int32_t m0 = __ldg(A.g.g_ptr + G), nm = __ldg(A.g.g_ptr + G + 1) - m0;
+            const int32_t n0 = __ldg(A.g.g_ptr + Gc), nn = __ldg(A.g.g_ptr + Gc + 1) - n0;
+            int64_t off[kPer], ci[kPer];
+#pragma unroll
+            for (int u = 0; u < kPer; ++u) {
+                off[u] = k[u] >= 0 ? __ldg(A.f_off + k[u]) : 0;
+                ci[u] = (k[u] >= 0 && A.f_cin) ? __ldg(A.f_cin + k[u]) : -1;
+            }
+            if (lane < nm) {
+                T.rowblk[lane] = __ldg(A.g.g_mem + m0 + lane);
+                T.rowrec[lane] = __ldg(A.g_mrec + m0 + lane);
+            }
+            if (lane < nn) {
+                T.colblk[lane] = __ldg(A.g.g_mem + n0 + lane);
+                T.colrec[lane] = __ldg(A.g_mrec + n0 + lane);
+            }
+#pragma unroll
+            for (int u = 0; u < kPer; ++u) {
+                const int p = 32 * u + lane;
+                T.tbl[p >> 4][p & 15] = k[u];
+                T.koff[p >> 4][p & 15] = off[u];
+                T.kcin[p >> 4][p & 15] = ci[u] >= 0 ? __ldg(A.ci_off + ci[u]) : -1;
+            }
+            if (lane == 0) {
+                T.nm = nm;
+                T.nn = nn;
+                T.wc = __ldg(A.g.g_w + Gc);
+                T.live = __ldg(A.t_live + t);
+            }
+            tc::mbar_arrive(&S.tbl_full[b]);     // release: the stores above are visible to the waiters
+        }
     } else {
-        // ---------------- epilogue: warps 2..5.  The accumulator (TMEM lanes 32 * (warp % 4) ..)
-        // is staged in shared memory, the TMEM released, then each formed atom block is written
-        // by one warp, lanes over its contiguous elements, with its norm summed in a fixed order.
-        const int et = threadIdx.x - 64;                          // 0..127
-        const int q = warp & 3, ew = et >> 5;
+        // ---------------- epilogue: warps 2..9.  The accumulator is staged in shared memory (a
+        // warp reads TMEM lanes 32 * (warp % 4) .. and every other 16-column chunk), the TMEM
+        // released, then each formed atom block is written by one warp, lanes over its contiguous
+        // elements, with its norm summed in a fixed order.
+        const int et = threadIdx.x - 64;                          // 0 .. kEpiThreads - 1
+        const int q = warp & 3, ew = et >> 5, half = ew >> 2;
         const int r = 32 * q + lane;                              // tile row of this thread
         int it = 0;
         for (int64_t t = blockIdx.x; t < A.ntiles; t += gridDim.x, ++it) {
             if (et == 0) S.epi_stop = lt_aborted(S);
             lt_epi_sync();
             if (S.epi_stop) break;
-            const int acc = it & 1;
-            const uint32_t acc_phase = (uint32_t)(it >> 1) & 1u;
-            const int32_t G = A.c_trow[t], Gc = A.c_tcol[t];
-            const int32_t m0 = A.g.g_ptr[G], nm = A.g.g_ptr[G + 1] - m0;
-            const int32_t n0 = A.g.g_ptr[Gc], nn = A.g.g_ptr[Gc + 1] - n0;
-            const int wc = A.g.g_w[Gc];
-            // the atom blocks of the tile this product writes (tables of the symbolic phase)
-            for (int p = et; p < kGroupMembers * kGroupMembers; p += 128) {
-                const int a = p >> 4, b = p & 15;
-                const int32_t k = A.c_tbl[t * (kGroupMembers * kGroupMembers) + p];
-                S.tbl[a][b] = k;
-                if (k >= 0) {
-                    S.koff[a][b] = A.f_off[k];
-                    const int64_t ci = A.f_cin ? A.f_cin[k] : -1;
-                    S.kcin[a][b] = ci >= 0 ? A.ci_off[ci] : -1;
-                }
-            }
-            if (et < nm) {
-                S.rowblk[et] = A.g.g_mem[m0 + et];
-                S.rowrec[et] = A.g_mrec[m0 + et];
-            }
-            if (et < nn) {
-                S.colblk[et] = A.g.g_mem[n0 + et];
-                S.colrec[et] = A.g_mrec[n0 + et];
-            }
+            const int acc = it % kAccs;
+            const uint32_t acc_phase = (uint32_t)(it / kAccs) & 1u;
+            const int tb = it & 1;
+            // the tile's tables (loader warp); a warp that did not see them complete skips the
+            // tile's work but keeps to the barriers
+            const bool tok = __all_sync(0xffffffffu, tc::mbar_wait(&S.tbl_full[tb], (uint32_t)(it >> 1) & 1u,
+                                                                   kWaitLimit));
+            if (!tok) lt_fail(A, S);
+            const LtTables& T = S.T[tb];
+            const int nm = tok ? T.nm : 0, nn = tok ? T.nn : 0;
             // every tile's accumulator phase completes (a tile without products commits no MMA
             // and is written as zeros, but its phase is still waited for); the TMEM loads are
             // warp-collective: a warp reads only if all its lanes saw the phase
-            const bool empty = !A.t_live[t];
-            const bool ok = __all_sync(0xffffffffu, tc::mbar_wait(&S.acc_full[acc], acc_phase, kWaitLimit));
+            const bool empty = !tok || !T.live;
+            const bool ok = __all_sync(0xffffffffu, tc::mbar_wait(&S.acc_full[acc], acc_phase, kWaitLimit)) && tok;
             if (!ok) lt_fail(A, S);
             tc::fence_after_sync();
-            const int ncol = ((wc + 15) >> 4) << 4;
-            for (int c0 = 0; c0 < ncol; c0 += 16) {
+            const int ncol = tok ? ((T.wc + 15) >> 4) << 4 : 0;
+            for (int c0 = 16 * half; c0 < ncol; c0 += 32) {
                 float v[16];
                 if (!empty && ok) {
                     tc::tmem_ld16(tmem + (uint32_t)(acc * 128 + c0) + ((uint32_t)(32 * q) << 16), v);
@@ -772,23 +824,41 @@ __global__ void __launch_bounds__(kLtThreads, 1) k_lowtier(LtArgs A) {
             lt_epi_sync();
             tc::mbar_arrive(&S.acc_empty[acc]);
             if (ok) {
-                for (int p = ew; p < nm * nn; p += 4) {
+                for (int p = ew; p < nm * nn; p += kEpiWarps) {
                     const int a = p / nn, b = p - a * nn;
-                    if (S.tbl[a][b] < 0) continue;
-                    const int ra0 = S.rowrec[a] & 255, m = S.rowrec[a] >> 8;
-                    const int cb0 = S.colrec[b] & 255, n = S.colrec[b] >> 8;
-                    const bool diag = S.rowblk[a] == S.colblk[b];
-                    double* out = A.c_data + S.koff[a][b];
-                    const int64_t ci = S.kcin[a][b];
+                    if (T.tbl[a][b] < 0) continue;
+                    const int ra0 = T.rowrec[a] & 255, m = T.rowrec[a] >> 8;
+                    const int cb0 = T.colrec[b] & 255, n = T.colrec[b] >> 8;
+                    const bool diag = T.rowblk[a] == T.colblk[b];
+                    double* __restrict__ out = A.c_data + T.koff[a][b];
+                    const int64_t ci = T.kcin[a][b];
+                    const double* __restrict__ cin = A.ci_data + (ci >= 0 ? ci : 0);
+                    // (e + 1/2) / n is at least 1 / (2 n) away from an integer; the float
+                    // product errs by far less for e < 2^14, so its truncation is e / n
+                    const float rn = 1.0f / (float)n;
+                    const int mn = m * n;
                     double sq = 0.0, d2 = 0.0;
-                    for (int e = lane; e < m * n; e += 32) {
-                        const int i = e / n, j = e - i * n;
-                        double val = A.alpha * (double)S.out[ra0 + i][cb0 + j];
-                        if (ci >= 0) val = val + A.beta * A.ci_data[ci + e];
-                        out[e] = val;
-                        sq = fma(val, val, sq);
-                        const double w = (diag && i == j) ? val - 1.0 : val;
-                        d2 = fma(w, w, d2);
+                    for (int e0 = 0; e0 < mn; e0 += 32 * kEpiBatch) {
+                        // the batch's C-input loads are all in flight before its first store
+                        double c[kEpiBatch];
+#pragma unroll
+                        for (int u = 0; u < kEpiBatch; ++u) {
+                            const int e = e0 + 32 * u + lane;
+                            c[u] = (ci >= 0 && e < mn) ? __ldg(cin + e) : 0.0;
+                        }
+#pragma unroll
+                        for (int u = 0; u < kEpiBatch; ++u) {
+                            const int e = e0 + 32 * u + lane;
+                            if (e < mn) {
+                                const int i = (int)(((float)e + 0.5f) * rn), j = e - i * n;
+                                double val = A.alpha * (double)S.out[ra0 + i][cb0 + j];
+                                if (ci >= 0) val = val + A.beta * c[u];
+                                out[e] = val;
+                                sq = fma(val, val, sq);
+                                const double w = (diag && i == j) ? val - 1.0 : val;
+                                d2 = fma(w, w, d2);
+                            }
+                        }
                     }
 #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) {
@@ -796,13 +866,14 @@ __global__ void __launch_bounds__(kLtThreads, 1) k_lowtier(LtArgs A) {
                         d2 += __shfl_xor_sync(0xffffffffu, d2, o);
                     }
                     if (lane == 0) {
-                        const int32_t k = S.tbl[a][b];
+                        const int32_t k = T.tbl[a][b];
                         A.c_norm[k] = sqrt(sq);
                         A.c_dev2[k] = d2;
                     }
                 }
             }
             lt_epi_sync();
+            if (et == 0) tc::mbar_arrive(&S.tbl_empty[tb]);      // the loader may refill these tables
         }
     }
     // wind down: every role is done; MMAs issued are complete (the epilogue waited on them)
@@ -1080,7 +1151,10 @@ void lowtier_check(LowTierPlan& L, cudaStream_t s) {
 }
 
 int64_t lowtier_tiles(const LowTierPlan& L) { return L.ntiles; }
-double lowtier_tensor_flops(const LowTierPlan& L) { return 2.0 * kTileRows * 16.0 * (double)L.ksteps_n * L.nparts; }
+// split operands: three MMAs per K step (hi*hi, hi*lo, lo*hi); plain BF16: one
+double lowtier_tensor_flops(const LowTierPlan& L) {
+    return 2.0 * kTileRows * 16.0 * (double)L.ksteps_n * (L.nparts == 2 ? 3 : 1);
+}
 double lowtier_copy_bytes(const LowTierPlan& L) { return (double)L.ksteps_rows * L.nparts * 2 * 16; }
 
 }  // namespace dbg

@@ -68,6 +68,7 @@ def test_bf16_product_matches_rounded_oracle(gb, si, density):
     exact = bsr.multiply(1.0, Ao, Bo)
     assert np.abs(data - exact.data).max() > 1e-6 * np.abs(exact.data).max()
     assert st.flops == bsr.multiply(1.0, Ao, Bo, info=True)[1].flops
+    assert st.flops_tensor >= st.flops
 
 
 def _split_reference(Ao, Bo):
@@ -108,6 +109,8 @@ def test_bf16x3_product_matches_split_oracle(gb, si, density):
     exact = bsr.multiply(1.0, Ao, Bo)
     assert np.all(np.abs(data - exact.data) <= (3 * 2.0 ** -16 + 2 * kmax * U32) * mag.data + 1e-300)
     assert st.flops == bsr.multiply(1.0, Ao, Bo, info=True)[1].flops
+    # three MMAs per K step; group tiles and the 128-row MMA only add padded work
+    assert st.flops_tensor >= 3 * st.flops
 
 
 def test_bf16x3_filtered_product_keeps_the_split_oracle_pattern(gb):
