@@ -907,7 +907,7 @@ def run_headline(args, gb, synth, torch, barrier, dist, rank, world, local):
     fp64 = low_correction = c2 = None
     de_vs_fp64 = speedup = None
     if not args.main_only:
-        fp64, low_correction, de_vs_fp64, speedup = headline_side_legs(args, gb, torch, barrier, H, h, w,
+        fp64, low_correction, de_vs_fp64, speedup = headline_side_legs(args, gb, torch, barrier, dist, H, h, w,
                                                                        side_steps, peak, peak_info, rm, ms_all)
 
     # end to end through the public API: H from pinned host memory each step, P exported to pinned
@@ -954,8 +954,9 @@ def run_headline(args, gb, synth, torch, barrier, dist, rank, world, local):
     return 0
 
 
-def headline_side_legs(args, gb, torch, barrier, H, h, w, side_steps, peak, peak_info, rm, ms_all):
+def headline_side_legs(args, gb, torch, barrier, dist, H, h, w, side_steps, peak, peak_info, rm, ms_all):
     """The plain FP64 iteration of the headline H and the low-correction option beside the mixed leg."""
+    from paper_2003_03868_gb300 import ranks
     rf, ms_f, acc_f = sign_leg(gb, torch, barrier, H, h, w, side_steps, 1, gb.DBCSR_FP64)
     ms_f_all, flops_f_all = ranks.job_timing(ms_f, acc_f["flops"], dist, "cuda")
     fp64 = {"time_to_p_ms": ms_f_all / side_steps, "value": flops_f_all / (ms_f_all * 1e-3) / 1e12,
