@@ -25,8 +25,10 @@ namespace {
 constexpr int kDM = 128;                 // M of the MMA and rows of an A tile
 constexpr int kDNMax = 256;              // rows of the widest B tile (N of the MMA)
 constexpr int kDStepK = 8;               // TF32 elements per MMA K step (32 bytes)
-constexpr int kDRun = 2;                 // K steps per stage
+constexpr int kDRunParts = 2;            // K steps x parts per stage: two steps plain, one step split
 constexpr int kDStages = 4;
+constexpr int kDStageBytes = kDRunParts * 2 * (kDM + kDNMax) * 16;   // 24 KB: two CTAs fit an SM
+constexpr int kDEpiCols = 64;            // accumulator columns staged per pass of the epilogue
 constexpr int kDThreads = 128;
 constexpr long long kDWaitLimit = 4000000000ll;
 
@@ -82,12 +84,12 @@ struct DenseArgs {
 };
 
 struct DenseShared {
-    alignas(1024) uint8_t stage[kDStages][kDRun * 2 * 2 * (kDM + kDNMax) * 16];
+    alignas(1024) uint8_t stage[kDStages][kDStageBytes];   // after the K loop: the epilogue's staging
     uint64_t full[kDStages], empty[kDStages], done;
     uint32_t tmem_base;
 };
 
-__global__ void __launch_bounds__(kDThreads, 1) k_dense_tf32(DenseArgs D) {
+__global__ void __launch_bounds__(kDThreads, 2) k_dense_tf32(DenseArgs D) {
     extern __shared__ __align__(1024) uint8_t d_dyn[];
     DenseShared& S = *reinterpret_cast<DenseShared*>((reinterpret_cast<uintptr_t>(d_dyn) + 1023) & ~(uintptr_t)1023);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -112,7 +114,8 @@ __global__ void __launch_bounds__(kDThreads, 1) k_dense_tf32(DenseArgs D) {
     const int np = D.np, NT = D.NT;
     const int64_t sa_step = (int64_t)np * 2 * kDM * 16, sb_step = (int64_t)np * 2 * NT * 16;
     const int nk = D.kpad / kDStepK;
-    const int nstage = (nk + kDRun - 1) / kDRun;
+    const int run = kDRunParts / np;                      // K steps per stage
+    const int nstage = (nk + run - 1) / run;
     const uint8_t* pa = D.a_pack + (b * D.ntm + tm) * (int64_t)nk * sa_step;
     const uint8_t* pb = D.b_pack + (b * D.ntn + tn) * (int64_t)nk * sb_step;
     bool ok = true;
@@ -123,7 +126,7 @@ __global__ void __launch_bounds__(kDThreads, 1) k_dense_tf32(DenseArgs D) {
         auto issue = [&](int s) {
             const int slot = s % kDStages;
             issued = s + 1;
-            const int k0 = s * kDRun, len = min(kDRun, nk - k0);
+            const int k0 = s * run, len = min(run, nk - k0);
             tc::mbar_arrive_expect_tx(&S.full[slot], (uint32_t)(len * (sa_step + sb_step)));
             tc::bulk_g2s(S.stage[slot], pa + k0 * sa_step, (uint32_t)(len * sa_step), &S.full[slot]);
             tc::bulk_g2s(S.stage[slot] + len * sa_step, pb + k0 * sb_step, (uint32_t)(len * sb_step), &S.full[slot]);
@@ -139,7 +142,7 @@ __global__ void __launch_bounds__(kDThreads, 1) k_dense_tf32(DenseArgs D) {
                 break;
             }
             tc::fence_after_sync();
-            const int len = min(kDRun, nk - s * kDRun);
+            const int len = min(run, nk - s * run);
             const uint32_t s0 = tc::smem_u32(S.stage[slot]);
             for (int j = 0; j < len; ++j) {
                 const uint32_t sa = s0 + (uint32_t)(j * sa_step), sb = s0 + (uint32_t)(len * sa_step + j * sb_step);
@@ -177,20 +180,34 @@ __global__ void __launch_bounds__(kDThreads, 1) k_dense_tf32(DenseArgs D) {
     }
     __syncthreads();
     tc::fence_after_sync();
-    // epilogue: thread r owns row r of the tile (TMEM lane r)
-    const int row = tm * kDM + threadIdx.x;
-    for (int c0 = 0; c0 < NT; c0 += 16) {
-        float v[16];
-        tc::tmem_ld16(tmem + (uint32_t)c0 + ((uint32_t)(32 * warp) << 16), v);
-        const int col0 = tn * NT + c0;
-        if (row < D.n) {
-            float* out = D.C + b * D.n * D.n + (int64_t)row * D.n;
+    // epilogue, kDEpiCols columns per pass: thread r reads row r of the accumulator (TMEM lane
+    // r) into shared memory (the stage ring is idle now: every copy landed and every MMA
+    // completed), then each warp writes whole row segments, lanes over consecutive columns
+    float* T = reinterpret_cast<float*>(S.stage[0]);
+    constexpr int kTS = kDEpiCols + 1;                    // odd stride: no bank conflicts
+    float* Cb = D.C + b * D.n * D.n;
+    const int r0 = tm * kDM;
+    for (int c0 = 0; c0 < NT; c0 += kDEpiCols) {
+        const int cw = min(kDEpiCols, NT - c0);
+        for (int c = 0; c < cw; c += 16) {
+            float v[16];
+            tc::tmem_ld16(tmem + (uint32_t)(c0 + c) + ((uint32_t)(32 * warp) << 16), v);
 #pragma unroll
-            for (int x = 0; x < 16; ++x) {
-                const int col = col0 + x;
-                if (col < D.n) out[col] = D.beta == 0.f ? D.alpha * v[x] : D.alpha * v[x] + D.beta * out[col];
+            for (int x = 0; x < 16; ++x) T[threadIdx.x * kTS + c + x] = v[x];
+        }
+        __syncthreads();
+        const int col0 = tn * NT + c0;
+        const int ncol = min(cw, D.n - col0);
+        for (int r = warp; r < kDM; r += kDThreads / 32) {
+            const int row = r0 + r;
+            if (row >= D.n) break;
+            float* out = Cb + (int64_t)row * D.n + col0;
+            for (int c = lane; c < ncol; c += 32) {
+                const float v = D.alpha * T[r * kTS + c];
+                out[c] = D.beta == 0.f ? v : v + D.beta * out[c];
             }
         }
+        __syncthreads();
     }
     tc::fence_before_sync();
     __syncthreads();
