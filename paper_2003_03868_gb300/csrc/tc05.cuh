@@ -74,6 +74,24 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
         : "memory");
 }
 
+// A box of a 3-D tensor map (global, described on the host by cuTensorMapEncodeTiled) at
+// coordinates (c0 innermost, c1, c2) into shared memory; c0 times the element size must be a
+// multiple of 16 bytes.  Coordinates past the tensor's end read zeros.  Completion is
+// signalled on bar as transaction bytes (the whole box).
+__device__ __forceinline__ void tma_load3d(void* dst, const void* tmap, int c0, int c1, int c2, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(smem_u32(dst)),
+        "l"(tmap), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Shared-memory writes of this thread become visible to the async proxy (tensor cores, bulk
+// copies) once it has passed this fence.
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
 // ---------------------------------------------------------------- tensor memory
 // One full warp allocates ncols columns (a power of two >= 32) of TMEM; the base address
 // is written to *slot (shared memory).
@@ -119,6 +137,20 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo_bytes
     d |= (uint64_t)((sbo_bytes >> 4) & 0x3FFFu) << 32;
     d |= (uint64_t)1 << 46;                     // descriptor version of the sm_100 family
     return d;                                   // base offset 0, layout 0 = no swizzle
+}
+
+// K-major operand in the 64-byte swizzled layout that a tensor-map load with
+// CU_TENSOR_MAP_SWIZZLE_64B writes: rows of 64 bytes, 8-row atoms of 512 bytes (the stride
+// between 8-row groups); saddr inside a 512-byte aligned atom row (the K offset in bytes
+// within the 64-byte row is added to the start address).
+__device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;                     // leading byte offset: unused for swizzled K-major
+    d |= (uint64_t)(512u >> 4) << 32;           // stride byte offset: 8 rows x 64 bytes
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)4 << 61;                     // layout: 64-byte swizzle
+    return d;
 }
 
 // Instruction descriptor of kind::f16 (ab_fmt 1: BF16 operands) or kind::tf32 (ab_fmt 2),
