@@ -9,6 +9,8 @@
 #include <array>
 #include <mutex>
 #include <numeric>
+#include <thread>
+#include <vector>
 
 #include <cstdio>
 #include <cstring>
@@ -568,19 +570,51 @@ dbcsr_status dbcsr_put_values(dbcsr_matrix m, const double* data, int on_device)
     });
 }
 
+// Runs f(chunk, begin, end) over [0, n) in up to 16 contiguous chunks on host threads (one
+// chunk below 2^18 items); chunk c always covers the same range, so results are deterministic.
+extern "C++" {
+template <class F>
+int host_chunks(int64_t n, F&& f) {
+    const int hw = (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    const int nt = n < (1 << 18) ? 1 : hw;
+    const int64_t per = (n + nt - 1) / nt;
+    std::vector<std::thread> th;
+    for (int c = 1; c < nt; ++c) th.emplace_back([&, c] { f(c, std::min(n, c * per), std::min(n, (c + 1) * per)); });
+    f(0, 0, std::min(n, per));
+    for (auto& t : th) t.join();
+    return nt;
+}
+}
+
 // Every staged block is copied at once into a device staging pool (host sources
-// through one cudaMemcpyAsync, so pinned host buffers move by DMA).
+// through one cudaMemcpyAsync, so pinned host buffers move by DMA); the host-side records of
+// the blocks are written while that copy runs.
 static void stage(dbcsr_matrix m, int64_t n, const int32_t* rows, const int32_t* cols, const double* packed,
                   int on_device) {
     if (!m) fail(DBCSR_EINVAL, "null matrix handle");
     dbg::check_unplanned(m, "put_block");
     if (m->finalized) fail(DBCSR_ESTATE, "put_block: matrix already finalized");
     if (n < 0 || (n > 0 && (!rows || !cols || !packed))) fail(DBCSR_EINVAL, "put_blocks: null argument");
+    const int32_t nblk = m->nblk;
+    const int32_t* bs = m->h_bs.data();
+    // per chunk: elements of its blocks (0 if an index is out of range) and a validity flag
+    std::array<int64_t, 16> part{};
+    std::array<int, 16> bad{};
+    const int nt = host_chunks(n, [&](int c, int64_t b, int64_t e) {
+        int64_t t = 0;
+        bool x = false;
+        for (int64_t i = b; i < e; ++i) {
+            const int32_t r = rows[i], cl = cols[i];
+            x |= (uint32_t)r >= (uint32_t)nblk || (uint32_t)cl >= (uint32_t)nblk;
+            if (!x) t += (int64_t)bs[r] * bs[cl];
+        }
+        part[c] = t;
+        bad[c] = x;
+    });
     int64_t total = 0;
-    for (int64_t i = 0; i < n; ++i) {
-        if (rows[i] < 0 || rows[i] >= m->nblk || cols[i] < 0 || cols[i] >= m->nblk)
-            fail(DBCSR_EINVAL, "put_block: block index out of range");
-        total += (int64_t)m->h_bs[rows[i]] * m->h_bs[cols[i]];
+    for (int c = 0; c < nt; ++c) {
+        if (bad[c]) fail(DBCSR_EINVAL, "put_block: block index out of range");
+        total += part[c];
     }
     if (m->st_dev_used + total > m->st_dev.n) {
         const int64_t cap = std::max<int64_t>(m->st_dev.n + m->st_dev.n / 2, m->st_dev_used + total);
@@ -594,15 +628,29 @@ static void stage(dbcsr_matrix m, int64_t n, const int32_t* rows, const int32_t*
     if (total)
         DBG_CK(cudaMemcpyAsync(m->st_dev.p + m->st_dev_used, packed, sizeof(double) * total,
                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, m->stream));
-    DBG_CK(cudaStreamSynchronize(m->stream));
-    int64_t at = m->st_dev_used;
-    for (int64_t i = 0; i < n; ++i) {
-        m->st_row.push_back(rows[i]);
-        m->st_col.push_back(cols[i]);
-        m->st_src.push_back(at);
-        at += (int64_t)m->h_bs[rows[i]] * m->h_bs[cols[i]];
+    const size_t base = m->st_row.size();
+    m->st_row.resize(base + n);
+    m->st_col.resize(base + n);
+    m->st_src.resize(base + n);
+    std::array<int64_t, 16> start{};
+    {
+        int64_t acc = m->st_dev_used;
+        for (int c = 0; c < nt; ++c) {
+            start[c] = acc;
+            acc += part[c];
+        }
     }
-    m->st_dev_used = at;
+    host_chunks(n, [&](int c, int64_t b, int64_t e) {
+        int64_t at = start[c];
+        for (int64_t i = b; i < e; ++i) {
+            m->st_row[base + i] = rows[i];
+            m->st_col[base + i] = cols[i];
+            m->st_src[base + i] = at;
+            at += (int64_t)bs[rows[i]] * bs[cols[i]];
+        }
+    });
+    m->st_dev_used += total;
+    DBG_CK(cudaStreamSynchronize(m->stream));   // the caller may reuse its buffers on return
 }
 
 dbcsr_status dbcsr_put_block(dbcsr_matrix m, int32_t row, int32_t col, const double* data, int on_device) {
@@ -619,32 +667,59 @@ dbcsr_status dbcsr_finalize(dbcsr_matrix m) {
         if (!m) fail(DBCSR_EINVAL, "null matrix handle");
         if (m->finalized) fail(DBCSR_ESTATE, "finalize: already finalized");
         const int64_t nb = (int64_t)m->st_row.size();
-        std::vector<int64_t> order(nb);
-        std::iota(order.begin(), order.end(), 0);
+        const std::vector<int32_t>& sr = m->st_row;
+        const std::vector<int32_t>& sc = m->st_col;
+        // staged in strictly increasing (row, column) order: then no block repeats
+        std::array<int, 16> unsorted{};
+        host_chunks(nb, [&](int c, int64_t b, int64_t e) {
+            bool u = false;
+            for (int64_t i = std::max<int64_t>(b, 1); i < e && !u; ++i)
+                u = !(sr[i - 1] < sr[i] || (sr[i - 1] == sr[i] && sc[i - 1] < sc[i]));
+            unsorted[c] = u;
+        });
         bool sorted = true;
-        for (int64_t i = 1; i < nb && sorted; ++i)
-            sorted = (m->st_row[i - 1] < m->st_row[i]) ||
-                     (m->st_row[i - 1] == m->st_row[i] && m->st_col[i - 1] < m->st_col[i]);
-        if (!sorted)
+        for (int c = 0; c < 16; ++c) sorted = sorted && !unsorted[c];
+        std::vector<int64_t> order;
+        if (!sorted) {
+            order.resize(nb);
+            std::iota(order.begin(), order.end(), 0);
             std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) {
-                return m->st_row[a] != m->st_row[b] ? m->st_row[a] < m->st_row[b] : m->st_col[a] < m->st_col[b];
+                return sr[a] != sr[b] ? sr[a] < sr[b] : sc[a] < sc[b];
             });
-        for (int64_t i = 1; i < nb; ++i) {
-            const int64_t a = order[i - 1], b = order[i];
-            if (m->st_row[a] == m->st_row[b] && m->st_col[a] == m->st_col[b])
-                fail(DBCSR_EINVAL, "finalize: duplicate block (" + std::to_string(m->st_row[a]) + ", " +
-                                       std::to_string(m->st_col[a]) + ")");
+            for (int64_t i = 1; i < nb; ++i) {
+                const int64_t a = order[i - 1], b = order[i];
+                if (sr[a] == sr[b] && sc[a] == sc[b])
+                    fail(DBCSR_EINVAL, "finalize: duplicate block (" + std::to_string(sr[a]) + ", " +
+                                           std::to_string(sc[a]) + ")");
+            }
         }
         std::vector<int64_t> rp(m->nblk + 1, 0), off(nb + 1, 0), src(nb);
         std::vector<int32_t> col(nb), row(nb);
-        for (int64_t i = 0; i < nb; ++i) {
-            const int64_t o = order[i];
-            row[i] = m->st_row[o];
-            col[i] = m->st_col[o];
-            src[i] = m->st_src[o];
-            rp[row[i] + 1]++;
-            off[i + 1] = off[i] + (int64_t)m->h_bs[row[i]] * m->h_bs[col[i]];
-        }
+        // blocks in order, then their element offsets: per-chunk sums, then a fill from each
+        // chunk's start
+        std::array<int64_t, 16> part{};
+        const int nt = host_chunks(nb, [&](int c, int64_t b, int64_t e) {
+            int64_t t = 0;
+            for (int64_t i = b; i < e; ++i) {
+                const int64_t o = sorted ? i : order[i];
+                row[i] = sr[o];
+                col[i] = sc[o];
+                src[i] = m->st_src[o];
+                t += (int64_t)m->h_bs[row[i]] * m->h_bs[col[i]];
+            }
+            part[c] = t;
+        });
+        std::array<int64_t, 16> start{};
+        for (int c = 1; c < nt; ++c) start[c] = start[c - 1] + part[c - 1];
+        host_chunks(nb, [&](int c, int64_t b, int64_t e) {
+            int64_t at = start[c];
+            for (int64_t i = b; i < e; ++i) {
+                off[i] = at;
+                at += (int64_t)m->h_bs[row[i]] * m->h_bs[col[i]];
+            }
+        });
+        off[nb] = nb ? start[nt - 1] + part[nt - 1] : 0;
+        for (int64_t i = 0; i < nb; ++i) rp[row[i] + 1]++;
         for (int32_t I = 0; I < m->nblk; ++I) rp[I + 1] += rp[I];
         cudaStream_t s = m->stream;
         m->nnzb = nb;
@@ -659,8 +734,15 @@ dbcsr_status dbcsr_finalize(dbcsr_matrix m) {
         if (nb) {
             DBG_CK(cudaMemcpyAsync(m->col.p, col.data(), sizeof(int32_t) * nb, cudaMemcpyHostToDevice, s));
             DBG_CK(cudaMemcpyAsync(m->row.p, row.data(), sizeof(int32_t) * nb, cudaMemcpyHostToDevice, s));
+            std::array<int, 16> moved{};
+            if (sorted)
+                host_chunks(nb, [&](int c, int64_t b, int64_t e) {
+                    bool x = false;
+                    for (int64_t i = b; i < e && !x; ++i) x = src[i] != off[i];
+                    moved[c] = x;
+                });
             bool direct = sorted;
-            for (int64_t i = 0; i < nb && direct; ++i) direct = (src[i] == off[i]);
+            for (int c = 0; c < 16; ++c) direct = direct && !moved[c];
             if (direct && m->st_dev_used == m->nel) {
                 // staged in block-CSR order: the staging pool is the data
                 m->data = std::move(m->st_dev);
