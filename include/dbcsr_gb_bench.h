@@ -30,6 +30,15 @@ double dbcsr_bench_peak(int32_t kind, int32_t iters, int32_t blocks, int32_t thr
 /* Number of kernels this library has launched in this process so far. */
 int64_t dbcsr_launch_count(void);
 
+/*
+ * Device memory of the library's stream-ordered pool on the current device: bytes in use
+ * now (*used_now) and the most in use at once since the last reset (*used_high); either
+ * pointer may be NULL.  reset_high != 0 then restarts the high-water mark at the current
+ * use.  Lets a caller check that a call allocated nothing (allocation-free entry points).
+ * Returns 0, or a dbcsr_status code on a CUDA error.
+ */
+int32_t dbcsr_pool_usage(int64_t* used_now, int64_t* used_high, int32_t reset_high);
+
 #ifdef __cplusplus
 }
 #endif

@@ -264,6 +264,14 @@ def trace_product(A: Matrix, B: Matrix) -> float:
     return out.value
 
 
+def pool_usage(reset_high: bool = False) -> tuple[int, int]:
+    """Bytes of the library's device memory pool in use now and at most since the last reset
+    (dbcsr_pool_usage); reset_high restarts the high-water mark afterwards."""
+    now, high = C.c_int64(), C.c_int64()
+    _check(lib().dbcsr_pool_usage(C.byref(now), C.byref(high), 1 if reset_high else 0), "pool_usage")
+    return int(now.value), int(high.value)
+
+
 def trace_product_noalloc(A: Matrix, B: Matrix, out_dev_ptr: int) -> None:
     """Queues Tr(A*B) into the caller's device double at ``out_dev_ptr`` without any
     device allocation (see dbcsr_trace_product_noalloc); does not synchronise."""

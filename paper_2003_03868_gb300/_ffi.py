@@ -133,6 +133,7 @@ SIGNATURES = [
     ("dbcsr_halo_rows", C.c_int, [C.c_int32, P, P, P, C.c_int32, P, C.c_int32, C.POINTER(C.c_int32)]),
     ("dbcsr_bench_peak", C.c_double, [C.c_int32, C.c_int32, C.c_int32, C.c_int32]),
     ("dbcsr_launch_count", C.c_int64, []),
+    ("dbcsr_pool_usage", C.c_int32, [C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.c_int32]),
 ]
 
 _lib = None

@@ -92,4 +92,28 @@ double dbcsr_bench_peak(int32_t kind, int32_t iters, int32_t blocks, int32_t thr
 
 int64_t dbcsr_launch_count(void) { return dbg::g_launches.load(); }
 
+int32_t dbcsr_pool_usage(int64_t* used_now, int64_t* used_high, int32_t reset_high) {
+    try {
+        cudaMemPool_t pool = dbg::library_pool();
+        uint64_t v = 0;
+        if (used_now) {
+            DBG_CK(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &v));
+            *used_now = (int64_t)v;
+        }
+        if (used_high) {
+            DBG_CK(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &v));
+            *used_high = (int64_t)v;
+        }
+        if (reset_high) {
+            uint64_t zero = 0;
+            DBG_CK(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &zero));
+        }
+        dbg::set_last_error("");
+        return DBCSR_OK;
+    } catch (const dbg::Error& e) {
+        dbg::set_last_error(e.what());
+        return e.code;
+    }
+}
+
 }  // extern "C"

@@ -68,3 +68,43 @@ def test_rejects_more_blocks_than_the_scratch_holds(gb):
     assert e.value.status == 3                     # DBCSR_ECAPACITY
     assert "1048576" in str(e.value)
     assert out.item() == 0.0                       # nothing was launched
+
+
+def test_allocates_nothing_and_replays_in_a_cuda_graph(gb):
+    # the stated purpose: no pool allocation during a call (the high-water mark of the
+    # library's pool stays at its use before the call), and a call recorded in a CUDA graph
+    # replays with the values A holds at replay time
+    import torch
+    s = torch.cuda.Stream()
+    bs = [13, 5, 5] * 12
+    a = synth.random_block_matrix(bs, 0.5, 7011)
+    b = synth.random_block_matrix(bs, 0.5, 7012)
+    A = gb.Matrix.of(a, stream=s.cuda_stream)
+    B = gb.Matrix.of(b, stream=s.cuda_stream)
+    out = torch.full((1,), float("nan"), dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    gb.trace_product_noalloc(A, B, out.data_ptr())          # warm-up (module load)
+    s.synchronize()
+    now0, _ = gb.pool_usage(reset_high=True)
+    gb.trace_product_noalloc(A, B, out.data_ptr())
+    s.synchronize()
+    now1, high1 = gb.pool_usage()
+    assert now1 == now0 and high1 == now0
+    assert float(out.item()) == pytest.approx(gb.trace_product(A, B), rel=1e-12, abs=1e-12)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        gb.trace_product_noalloc(A, B, out.data_ptr())
+    rng = np.random.default_rng(7013)
+    for _ in range(2):
+        vals = rng.uniform(-1.0, 1.0, a.data.shape[0])
+        A.put_values(vals)
+        s.synchronize()
+        gb.pool_usage(reset_high=True)
+        out.fill_(float("nan"))
+        torch.cuda.synchronize()
+        g.replay()
+        s.synchronize()
+        torch.cuda.synchronize()
+        _, high = gb.pool_usage()
+        assert high == now0
+        assert float(out.item()) == pytest.approx(gb.trace_product(A, B), rel=1e-12, abs=1e-12)
