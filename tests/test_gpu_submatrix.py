@@ -102,3 +102,26 @@ def test_dense_products_match_fp64_reference(gb, n, nb):
             gb.dense_multiply(prec, nb, n, 1.0, a.data_ptr(), b.data_ptr(), 0.0, c.data_ptr())
             errs.append(np.abs(c.double().cpu().numpy() - np.einsum("bij,bjk->bik", A, B)).max())
         assert errs[0] > 30 * errs[1]
+
+
+@pytest.mark.parametrize("n,nb", [(4, 3), (8, 1), (20, 5), (252, 1), (256, 2), (268, 1)])
+def test_dense_tf32_edge_sizes(gb, n, nb):
+    # sizes at the edges of the tensor-map path (n a multiple of 4): a single 16-column stage
+    # partly past n, one or two 256-row tiles of B^T, N tiles of 16 rows; products against
+    # float64 with the truncation bound (2^-9 plain, 2^-18 split) plus FP32 summation
+    import torch
+    rng = np.random.default_rng(1000 + n)
+    A = rng.uniform(-1, 1, (nb, n, n))
+    B = rng.uniform(-1, 1, (nb, n, n))
+    a = torch.tensor(A, dtype=torch.float32, device="cuda")
+    b = torch.tensor(B, dtype=torch.float32, device="cuda")
+    A32, B32 = a.double().cpu().numpy(), b.double().cpu().numpy()
+    ref = np.einsum("bij,bjk->bik", A32, B32)
+    mag = np.einsum("bij,bjk->bik", np.abs(A32), np.abs(B32))
+    for prec, tol in ((gb.DBCSR_TF32, 2.0 ** -9), (gb.DBCSR_TF32X3, 2.0 ** -18)):
+        c = torch.full((nb, n, n), float("nan"), dtype=torch.float32, device="cuda")
+        gb.dense_multiply(prec, nb, n, 1.0, a.data_ptr(), b.data_ptr(), 0.0, c.data_ptr())
+        torch.cuda.synchronize()
+        got = c.double().cpu().numpy()
+        assert np.all(np.isfinite(got)), prec
+        assert np.all(np.abs(got - ref) <= (tol + n * 2.0 ** -24) * mag + 1e-30), prec
