@@ -942,6 +942,13 @@ def run_headline(args, gb, synth, torch, barrier, dist, rank, world, local):
            "gpu_launches": launches, "clocks": clk, "roofline": dominant,
            "fp64_tail_roofline": f_roof, "low_tier_roofline": l_roof,
            "fp64": fp64, "low_correction": low_correction, "e2e": e2e, "sign_1024h2o": c2, "tuning": tuning}
+    if not args.main_only:
+        shapes = [(23, 23, 23), (23, 7, 23), (7, 23, 23), (7, 7, 23)]
+        out["vendor_small_gemm"] = {
+            "fp64": vendor_small_gemm(torch, shapes, torch.float64),
+            "bf16": vendor_small_gemm(torch, shapes, torch.bfloat16),
+            "note": "torch.bmm (cuBLAS) on 131,072 independent products per block shape, untimed by the step; "
+                    "compare k_smm_f64 (roofline.achieved) and k_lowtier (low_tier_roofline.algorithmic_tflops)"}
     if rank == 0 and world == 1 and not args.no_cpu:
         smp = RowsSample(h, w, CPU_ROWS_FRAC)
         f, dt, cores = smp.run()
@@ -952,6 +959,30 @@ def run_headline(args, gb, synth, torch, barrier, dist, rank, world, local):
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def vendor_small_gemm(torch, shapes, dtype, nprod=131072, reps=5):
+    """Context for the block-product kernels: the vendor library's batched GEMM (torch.bmm, which
+    calls cuBLAS) on independent products of the block shapes, nprod per batch, timed with CUDA
+    events after a warm-up.  Not the same work as a block-sparse product (no accumulation of a
+    stack into one C block, no prescreen): a rate for the small shapes, nothing more."""
+    out = []
+    for (m, n, k) in shapes:
+        a = torch.rand(nprod, m, k, dtype=dtype, device="cuda")
+        b = torch.rand(nprod, k, n, dtype=dtype, device="cuda")
+        c = torch.empty(nprod, m, n, dtype=dtype, device="cuda")
+        torch.bmm(a, b, out=c)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            torch.bmm(a, b, out=c)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        out.append({"mnk": [m, n, k], "tflops": 2.0 * m * n * k * nprod / (ms * 1e-3) / 1e12, "ms": ms})
+        del a, b, c
+    return out
 
 
 def headline_side_legs(args, gb, torch, barrier, dist, H, h, w, side_steps, peak, peak_info, rm, ms_all):
