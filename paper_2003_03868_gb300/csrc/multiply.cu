@@ -778,6 +778,16 @@ __global__ void __launch_bounds__(256) k_smm_f64_ks(int64_t nlist, const int64_t
         smm_block_ks<EF, R>(list[w], S, lane);
 }
 
+// The five-slot class (23 x 7 and 7 x 23: m n = 32 x 5 + 1) with registers capped for three
+// CTAs of 256 threads per SM (80 registers, no spills): at the uncapped 98 registers only two
+// fit, and the operand loads' latency showed (FP64 pipe 72% busy).
+__global__ void __launch_bounds__(256, 3) k_smm_f64_ks5(int64_t nlist, const int64_t* __restrict__ list, SmmArgs S) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < nlist; w += warps)
+        smm_block_ks<5, 1>(list[w], S, lane);
+}
+
 // One launch for every block shape of a product: the warps take C blocks from one work queue
 // (the shape lists one after another) in chunks of kQueueChunk with an atomic counter, and
 // each runs the single-warp body of its block's class (the K-split one where m n = 32 EF + 1).
@@ -860,6 +870,7 @@ template <int... Es>
 struct SmmKsTable {
     static SmmKernel get(int ef) {
         SmmKernel t[] = {nullptr, &k_smm_f64_ks<Es, 1>...};
+        if (ef == 5) return &k_smm_f64_ks5;
         return (ef >= 1 && ef <= (int)sizeof...(Es)) ? t[ef] : nullptr;
     }
 };
