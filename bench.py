@@ -39,10 +39,10 @@ FALLBACK_BF16_BURST, FALLBACK_BF16_SUSTAINED = 1900.0, 1700.0
 # DRAM bytes per flop of the FP64 block-product kernels: dram__bytes_read.sum +
 # dram__bytes_write.sum over three captured launches (7x7, 23x7 and 7x23 classes of one product
 # of the 512-water 23/7 case) divided by their executed DFMA flops (2 x
-# sm__sass_thread_inst_executed_op_dfma_pred_on.sum): 2.494 GB / 21.63 GFLOP.  A full launch's
+# sm__sass_thread_inst_executed_op_dfma_pred_on.sum): 2.680 GB / 21.63 GFLOP.  A full launch's
 # traffic is this ratio times its flops (the larger systems are assumed to re-read operands at the
 # same rate per flop).  Reset to None whenever the kernel changes.
-SMM_F64_BYTES_PER_FLOP = 0.1153
+SMM_F64_BYTES_PER_FLOP = 0.1239
 
 
 def bf16_peak():
