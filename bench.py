@@ -735,7 +735,7 @@ def run_predictor(args, gb, synth, torch, barrier):
     stream = torch.cuda.current_stream()
     H = gb.Matrix.of(h.H, stream=stream.cuda_stream)
 
-    # the prediction judged by measured time, with the exhaustive search as its fallback
+    # the prediction checked by measured time, with the exhaustive search as its fallback
     gb.tune_clear()
     t0 = time.time()
     fallback = {k: gb.tune_predicted(models[k], target, p, stack_len=args.tune_stack, reps=3, tolerance=0.02)

@@ -640,8 +640,8 @@ dbcsr_status dbcsr_predictor_data(const char* tune_records, int32_t prec, float*
 dbcsr_status dbcsr_predictor_params(int32_t prec, float* params);
 
 /*
- * The prediction with the exhaustive autotune as its fallback and measured time as the
- * judge (section "Batched execution": the model fills in the untuned kernels; the tuner
+ * The prediction with the exhaustive autotune as its fallback and measured time deciding
+ * (section "Batched execution": the model fills in the untuned kernels; the tuner
  * stays the reference).  For each triple mnk[3t..3t+2]:
  *   - the MLP (params, as for dbcsr_mlp_predict_best) picks a configuration;
  *   - the prediction and the default configuration are timed on the synthetic stack

@@ -289,7 +289,7 @@ dbcsr_status dbcsr_tune_predicted(int32_t prec, const float* params, const int32
         for (int32_t t = 0; t < ntriples; ++t) {
             const int m = mnk[3 * t], n = mnk[3 * t + 1], k = mnk[3 * t + 2];
             dbg::SynthStack st(m, n, k, stack_len, s);
-            // measured time judges the prediction: kept if within tolerance of the default,
+            // measured time decides on the prediction: kept if within tolerance of the default,
             // otherwise the exhaustive search over the space decides
             dbg::TuneCfg chosen = from_c(pred[t]);
             const double tp = st.time(chosen, reps, s);
