@@ -39,6 +39,15 @@ int64_t dbcsr_launch_count(void);
  */
 int32_t dbcsr_pool_usage(int64_t* used_now, int64_t* used_high, int32_t reset_high);
 
+/*
+ * Self-test of the bounded device-side waits every persistent kernel of the library uses:
+ * one CTA waits on an mbarrier for at most limit_cycles SM clock cycles (limit_cycles >= 0).
+ * arrive != 0: a thread of the CTA arrives first, so the wait completes (DBCSR_OK);
+ * arrive == 0: nothing ever arrives, the wait runs out and the call returns DBCSR_ETIMEOUT,
+ * the context staying usable.  *waited (nullable) receives the cycles the wait took.
+ */
+int32_t dbcsr_wait_selftest(int64_t limit_cycles, int32_t arrive, int64_t* waited);
+
 #ifdef __cplusplus
 }
 #endif

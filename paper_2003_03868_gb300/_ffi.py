@@ -134,6 +134,7 @@ SIGNATURES = [
     ("dbcsr_bench_peak", C.c_double, [C.c_int32, C.c_int32, C.c_int32, C.c_int32]),
     ("dbcsr_launch_count", C.c_int64, []),
     ("dbcsr_pool_usage", C.c_int32, [C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.c_int32]),
+    ("dbcsr_wait_selftest", C.c_int32, [C.c_int64, C.c_int32, C.POINTER(C.c_int64)]),
 ]
 
 _lib = None

@@ -1,9 +1,11 @@
 // FP64 rate microbenchmarks (no counterpart in the paper; they measure the
-// pipes that bound the FP64 block products) and the launch counter.
+// pipes that bound the FP64 block products), the launch counter, and the self-test of the
+// bounded device-side waits.
 #include <atomic>
 
 #include "common.cuh"
 #include "dbcsr_gb_bench.h"
+#include "tc05.cuh"
 
 namespace dbg {
 
@@ -78,6 +80,26 @@ double bench_peak(int kind, int iters, int blocks, int threads) {
     return ops / (ms * 1e-3) * 1e-9;
 }
 
+// One warp: an mbarrier of count 1, thread 0 arrives first when `arrive`, then every lane
+// waits (bounded, as the library's kernels do) for the first phase.  out[0] = 1 if the wait
+// completed, out[1] = the cycles lane 0 waited.  No asynchronous copy or TMEM is involved,
+// so giving up leaves nothing in flight.
+__global__ void k_wait_selftest(long long limit, int arrive, int64_t* out) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        tc::mbar_init(&bar, 1);
+        tc::fence_barrier_init();
+    }
+    __syncthreads();
+    if (arrive && threadIdx.x == 0) tc::mbar_arrive(&bar);
+    const long long t0 = clock64();
+    const bool ok = __all_sync(0xffffffffu, tc::mbar_wait(&bar, 0, limit));
+    if (threadIdx.x == 0) {
+        out[0] = ok ? 1 : 0;
+        out[1] = clock64() - t0;
+    }
+}
+
 }  // namespace dbg
 
 extern "C" {
@@ -91,6 +113,28 @@ double dbcsr_bench_peak(int32_t kind, int32_t iters, int32_t blocks, int32_t thr
 }
 
 int64_t dbcsr_launch_count(void) { return dbg::g_launches.load(); }
+
+int32_t dbcsr_wait_selftest(int64_t limit_cycles, int32_t arrive, int64_t* waited) {
+    try {
+        if (limit_cycles < 0) dbg::fail(DBCSR_EINVAL, "wait_selftest: negative limit");
+        int64_t* d = nullptr;
+        DBG_CK(cudaMalloc(&d, 2 * sizeof(int64_t)));
+        dbg::k_wait_selftest<<<1, 32>>>((long long)limit_cycles, arrive, d);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        int64_t h[2] = {0, 0};
+        if (e == cudaSuccess) e = cudaMemcpy(h, d, sizeof h, cudaMemcpyDeviceToHost);
+        cudaFree(d);
+        DBG_CK(e);
+        if (waited) *waited = h[1];
+        if (!h[0]) dbg::fail(DBCSR_ETIMEOUT, "wait_selftest: the wait ran out");
+        dbg::set_last_error("");
+        return DBCSR_OK;
+    } catch (const dbg::Error& e) {
+        dbg::set_last_error(e.what());
+        return e.code;
+    }
+}
 
 int32_t dbcsr_pool_usage(int64_t* used_now, int64_t* used_high, int32_t reset_high) {
     try {

@@ -99,12 +99,12 @@ def test_allocates_nothing_and_replays_in_a_cuda_graph(gb):
         vals = rng.uniform(-1.0, 1.0, a.data.shape[0])
         A.put_values(vals)
         s.synchronize()
-        gb.pool_usage(reset_high=True)
         out.fill_(float("nan"))
         torch.cuda.synchronize()
+        now_r, _ = gb.pool_usage(reset_high=True)
         g.replay()
         s.synchronize()
         torch.cuda.synchronize()
-        _, high = gb.pool_usage()
-        assert high == now0
+        now_a, high = gb.pool_usage()
+        assert now_a == now_r and high == now_r            # the replay allocated nothing
         assert float(out.item()) == pytest.approx(gb.trace_product(A, B), rel=1e-12, abs=1e-12)
