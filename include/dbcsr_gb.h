@@ -123,6 +123,10 @@ typedef struct {
  * and the traces stay FP64.  Off by default: the default FP64 tier computes both
  * products in FP64.  Order 2 only (EINVAL with a higher order). */
 #define DBCSR_SIGN_LOW_CORRECTION 4
+/* The iteration's state instead of the density matrix: P_out receives X as it stands when the
+ * iteration stops (for a checkpoint: dbcsr_save it, and continue later with
+ * dbcsr_sign_iterate_resume); rep->trace_p and rep->e_band are NaN. */
+#define DBCSR_SIGN_RETURN_X 8
 
 #define DBCSR_MAX_HISTORY 128
 
@@ -374,6 +378,23 @@ dbcsr_status dbcsr_gershgorin(dbcsr_matrix A, double mu, double* out);
  */
 dbcsr_status dbcsr_sign_iterate(dbcsr_matrix H, double mu, const dbcsr_sign_opts* opts, dbcsr_matrix P_out,
                                 dbcsr_sign_report* rep);
+
+/*
+ * Checkpoint / resume of the sign iteration (no counterpart in the paper).  The state of
+ * the iteration after k steps is (X_k, k, the tier of the next product): X from a run with
+ * DBCSR_SIGN_RETURN_X that max_iter = k stopped (possibly written with dbcsr_save and read
+ * back with dbcsr_load), k and the switch step from that run's report `prev`.  The call
+ * continues the iteration from there with opts (the same options as the first run, max_iter
+ * counting all steps), the stall test looking back into prev's residual history, and fills
+ * P_out and rep as dbcsr_sign_iterate would (rep continues prev's histories and totals).
+ * An FP64 iteration, and a mixed one resumed after its switch to FP64, take exactly the
+ * products of the uninterrupted run: the resumed P equals its P bit for bit.  Resumed inside
+ * a split-BF16 tier, the tensor-core tier regroups the blocks of X, so the products agree to
+ * rounding.  X is not modified.  Errors: EINVAL (null arguments, block sizes of X or P_out
+ * not those of H, a report with a negative or too long history); as dbcsr_sign_iterate.
+ */
+dbcsr_status dbcsr_sign_iterate_resume(dbcsr_matrix H, dbcsr_matrix X, const dbcsr_sign_report* prev,
+                                       const dbcsr_sign_opts* opts, dbcsr_matrix P_out, dbcsr_sign_report* rep);
 
 /*
  * S^(-1/2) and S^(1/2) of a symmetric positive definite S (section "Sign-Method": the

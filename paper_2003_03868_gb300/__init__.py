@@ -301,12 +301,13 @@ class SignResult:
         return [self.report.residual_history[i] for i in range(n)]
 
 
-def _sign_flags(full_products: bool, low: int, low_correction: bool = False) -> int:
+def _sign_flags(full_products: bool, low: int, low_correction: bool = False, return_x: bool = False) -> int:
     if low not in (DBCSR_BF16, DBCSR_BF16X3):
         raise ValueError("low must be DBCSR_BF16 or DBCSR_BF16X3")
     return ((_ffi.DBCSR_SIGN_FULL_PRODUCTS if full_products else 0)
             | (_ffi.DBCSR_SIGN_PLAIN_BF16 if low == DBCSR_BF16 else 0)
-            | (_ffi.DBCSR_SIGN_LOW_CORRECTION if low_correction else 0))
+            | (_ffi.DBCSR_SIGN_LOW_CORRECTION if low_correction else 0)
+            | (_ffi.DBCSR_SIGN_RETURN_X if return_x else 0))
 
 
 DBCSR_SCHEDULE_PER_SHAPE, DBCSR_SCHEDULE_QUEUE = 0, 1
@@ -341,20 +342,40 @@ def sign_iterate(H: Matrix, mu: float, eps_filter: float, tol: float, max_iter: 
                  prec: int = DBCSR_FP64, switch_tol: float = 1e-4, stall_ratio: float = 0.5,
                  P: Matrix | None = None, verbose: bool = False, raise_on_notconv: bool = False,
                  full_products: bool = False, low: int = DBCSR_BF16X3, low_correction: bool = False,
-                 order: int = 2) -> SignResult:
+                 order: int = 2, return_x: bool = False) -> SignResult:
     """Density matrix P = (1 - sign(H - mu 1)) / 2 by the sign iteration of the given order
     (2: Newton-Schulz; 3 to 7: the polynomial Pade steps, see dbcsr_sign_iterate).
 
     With prec=DBCSR_MIXED, `low` picks the product of the low-precision tier:
     the split DBCSR_BF16X3 (default) or plain DBCSR_BF16; low_correction takes the
-    FP64 tier's update correction X (X^2 - 1) in split BF16 (DBCSR_SIGN_LOW_CORRECTION)."""
+    FP64 tier's update correction X (X^2 - 1) in split BF16 (DBCSR_SIGN_LOW_CORRECTION).
+    return_x: the result holds the iteration's X instead of P (a checkpoint for
+    sign_iterate_resume, DBCSR_SIGN_RETURN_X)."""
     P = Matrix(H.blk_size, H.stream) if P is None else P
     o = SignOpts(float(eps_filter), float(tol), int(max_iter), int(prec), float(switch_tol), float(stall_ratio),
-                 1 if verbose else 0, _sign_flags(full_products, low, low_correction), int(order), 0)
+                 1 if verbose else 0, _sign_flags(full_products, low, low_correction, return_x), int(order), 0)
     rep = SignReport()
     st = lib().dbcsr_sign_iterate(H.handle, float(mu), C.byref(o), P.handle, C.byref(rep))
     if st != _ffi.DBCSR_OK and (st != _ffi.DBCSR_ENOTCONV or raise_on_notconv):
         _check(st, "sign_iterate")
+    return SignResult(P=P, report=rep, status=st)
+
+
+def sign_iterate_resume(H: Matrix, X: Matrix, prev: SignReport, eps_filter: float, tol: float,
+                        max_iter: int = 100, prec: int = DBCSR_FP64, switch_tol: float = 1e-4,
+                        stall_ratio: float = 0.5, P: Matrix | None = None, verbose: bool = False,
+                        raise_on_notconv: bool = False, full_products: bool = False, low: int = DBCSR_BF16X3,
+                        low_correction: bool = False, order: int = 2, return_x: bool = False) -> SignResult:
+    """Continue a sign iteration from its checkpoint: X (a run with return_x=True that
+    max_iter stopped, perhaps saved and loaded) and that run's report (dbcsr_sign_iterate_resume).
+    The options are those of the first run; max_iter counts every step."""
+    P = Matrix(H.blk_size, H.stream) if P is None else P
+    o = SignOpts(float(eps_filter), float(tol), int(max_iter), int(prec), float(switch_tol), float(stall_ratio),
+                 1 if verbose else 0, _sign_flags(full_products, low, low_correction, return_x), int(order), 0)
+    rep = SignReport()
+    st = lib().dbcsr_sign_iterate_resume(H.handle, X.handle, C.byref(prev), C.byref(o), P.handle, C.byref(rep))
+    if st != _ffi.DBCSR_OK and (st != _ffi.DBCSR_ENOTCONV or raise_on_notconv):
+        _check(st, "sign_iterate_resume")
     return SignResult(P=P, report=rep, status=st)
 
 

@@ -11,7 +11,7 @@ DBCSR_OK, DBCSR_EINVAL, DBCSR_ENOMEM, DBCSR_ECAPACITY, DBCSR_ECUDA = 0, 1, 2, 3,
 DBCSR_ENAN, DBCSR_ENOTCONV, DBCSR_ETIMEOUT, DBCSR_ESTATE = 5, 6, 7, 8
 DBCSR_FP64, DBCSR_BF16, DBCSR_MIXED, DBCSR_BF16X3, DBCSR_TF32, DBCSR_TF32X3 = 0, 2, 3, 4, 5, 6
 DBCSR_PURIFY_TC2, DBCSR_PURIFY_TRS4 = 1, 2
-DBCSR_SIGN_FULL_PRODUCTS, DBCSR_SIGN_PLAIN_BF16, DBCSR_SIGN_LOW_CORRECTION = 1, 2, 4
+DBCSR_SIGN_FULL_PRODUCTS, DBCSR_SIGN_PLAIN_BF16, DBCSR_SIGN_LOW_CORRECTION, DBCSR_SIGN_RETURN_X = 1, 2, 4, 8
 MAX_HISTORY = 128
 
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECAPACITY", 4: "ECUDA", 5: "ENAN", 6: "ENOTCONV",
@@ -98,6 +98,8 @@ SIGNATURES = [
     ("dbcsr_trace_product_noalloc", C.c_int, [P, P, P]),
     ("dbcsr_gershgorin", C.c_int, [P, C.c_double, C.POINTER(C.c_double)]),
     ("dbcsr_sign_iterate", C.c_int, [P, C.c_double, C.POINTER(SignOpts), P, C.POINTER(SignReport)]),
+    ("dbcsr_sign_iterate_resume", C.c_int, [P, P, C.POINTER(SignReport), C.POINTER(SignOpts), P,
+                                            C.POINTER(SignReport)]),
     ("dbcsr_inverse_hotelling", C.c_int, [P, C.POINTER(SignOpts), P, C.POINTER(SignReport)]),
     ("dbcsr_inverse_sqrt", C.c_int, [P, C.POINTER(SignOpts), P, P, C.POINTER(SignReport)]),
     ("dbcsr_submatrix_sign", C.c_int, [P, C.c_double, C.POINTER(SignOpts), P, C.POINTER(SignReport)]),

@@ -324,6 +324,8 @@ std::unique_ptr<dbcsr_matrix_> step_polynomial(dbcsr_matrix_* Y, int order, doub
 // Y is overwritten (with 1 - Y for orders above 2, with Y - 1 in order 2's correction form).
 void sign_update(dbcsr_matrix_* X, dbcsr_matrix_* Y, int order, bool correction, double eps, int tier, int sym,
                  const std::function<void(const dbcsr_mult_stats&, int)>& account);
+dbcsr_status sign_iterate_resume(dbcsr_matrix_* H, dbcsr_matrix_* X0, const dbcsr_sign_report* prev,
+                                 const dbcsr_sign_opts* opts, dbcsr_matrix_* P, dbcsr_sign_report* rep);
 dbcsr_status sign_iterate(dbcsr_matrix_* H, double mu, const dbcsr_sign_opts* opts, dbcsr_matrix_* P,
                           dbcsr_sign_report* rep);
 

@@ -872,6 +872,15 @@ dbcsr_status dbcsr_sign_iterate(dbcsr_matrix H, double mu, const dbcsr_sign_opts
     return st;
 }
 
+dbcsr_status dbcsr_sign_iterate_resume(dbcsr_matrix H, dbcsr_matrix X, const dbcsr_sign_report* prev,
+                                       const dbcsr_sign_opts* opts, dbcsr_matrix P_out, dbcsr_sign_report* rep) {
+    dbcsr_status st = DBCSR_OK;
+    dbcsr_status g = guarded([&] { st = dbg::sign_iterate_resume(H, X, prev, opts, P_out, rep); });
+    if (g != DBCSR_OK) return g;
+    if (st != DBCSR_OK) g_last_error = "sign iteration did not reach the tolerance";
+    return st;
+}
+
 dbcsr_status dbcsr_inverse_sqrt(dbcsr_matrix S, const dbcsr_sign_opts* opts, dbcsr_matrix S_invsqrt,
                                 dbcsr_matrix S_sqrt, dbcsr_sign_report* rep) {
     dbcsr_status st = DBCSR_OK;

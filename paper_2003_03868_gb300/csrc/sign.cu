@@ -125,12 +125,18 @@ void sign_update(dbcsr_matrix_* X, dbcsr_matrix_* Y, int order, bool correction,
     account(st, tier);
 }
 
-dbcsr_status sign_iterate(dbcsr_matrix_* H, double mu, const dbcsr_sign_opts* opts, dbcsr_matrix_* P,
-                          dbcsr_sign_report* rep) {
-    check_finalized(H);
-    if (!P) fail(DBCSR_EINVAL, "sign_iterate: null P_out");
-    if (P->h_bs != H->h_bs) fail(DBCSR_EINVAL, "sign_iterate: P_out block sizes differ from H");
+namespace {
+
+// Options with their defaults filled in and checked, and what they imply.
+struct SignSetup {
     dbcsr_sign_opts o{};
+    bool full = false, full_mixed = false, correction = false, return_x = false;
+    int low = DBCSR_BF16X3;
+};
+
+SignSetup sign_setup(const dbcsr_sign_opts* opts) {
+    SignSetup S;
+    dbcsr_sign_opts& o = S.o;
     o.eps_filter = 0.0;
     o.tol = 1e-9;
     o.max_iter = 100;
@@ -151,31 +157,27 @@ dbcsr_status sign_iterate(dbcsr_matrix_* H, double mu, const dbcsr_sign_opts* op
     // triangles as computed: a BF16 X2 commutes with X only to about 1e-3, so mirrored BF16
     // products would steer X towards a different matrix; a mixed run with a plain BF16 tier
     // therefore forms full products throughout and takes X's symmetric part at the end.
-    const bool full = (o.flags & DBCSR_SIGN_FULL_PRODUCTS) != 0;
-    const int low = (o.flags & DBCSR_SIGN_PLAIN_BF16) ? DBCSR_BF16 : DBCSR_BF16X3;
-    const bool full_mixed = o.prec == DBCSR_MIXED && low == DBCSR_BF16;
-    const bool correction = o.prec == DBCSR_MIXED && (o.flags & DBCSR_SIGN_LOW_CORRECTION) != 0;
+    S.full = (o.flags & DBCSR_SIGN_FULL_PRODUCTS) != 0;
+    S.low = (o.flags & DBCSR_SIGN_PLAIN_BF16) ? DBCSR_BF16 : DBCSR_BF16X3;
+    S.full_mixed = o.prec == DBCSR_MIXED && S.low == DBCSR_BF16;
+    S.correction = o.prec == DBCSR_MIXED && (o.flags & DBCSR_SIGN_LOW_CORRECTION) != 0;
+    S.return_x = (o.flags & DBCSR_SIGN_RETURN_X) != 0;
+    return S;
+}
 
-    const auto t0 = std::chrono::steady_clock::now();
+// The iteration from the scaled X after `it` steps, the next X*X in `tier`, the switch to
+// FP64 at step first_fp64 (0: not yet), with r holding the report so far (histories of the
+// steps taken); fills P (or X itself with DBCSR_SIGN_RETURN_X) and the report.
+dbcsr_status sign_run(dbcsr_matrix_* H, std::unique_ptr<dbcsr_matrix_> X, const SignSetup& S, int it, int tier,
+                      int first_fp64, dbcsr_sign_report r, dbcsr_matrix_* P, dbcsr_sign_report* rep,
+                      std::chrono::steady_clock::time_point t0) {
+    const dbcsr_sign_opts& o = S.o;
     cudaStream_t s = H->stream;
     const double N = (double)H->n;
-    const double alpha = gershgorin(H, mu);
-    if (!(alpha > 0) || !std::isfinite(alpha)) fail(DBCSR_EINVAL, "sign_iterate: Gershgorin bound is zero or not finite");
-
-    auto X = make_like(H, s);
     auto X2 = make_like(H, s);
-    copy_matrix(X.get(), H);
-    scale_shift(X.get(), 1.0 / alpha, -mu / alpha);
-
-    dbcsr_sign_report r{};
-    r.alpha = alpha;
-    int it = 0;
     bool converged = false, stalled = false;
-    double res = 0.0;
-    // precision ladder: BF16 operands / FP32 accumulation while r >= switch_tol, then FP64
-    int tier = (o.prec == DBCSR_MIXED) ? low : DBCSR_FP64;
-    int first_fp64 = (tier == DBCSR_FP64) ? 1 : 0;
-    const int sym = (full || full_mixed) ? kSymNone : kSymMirror;
+    double res = it > 0 && it - 1 < DBCSR_MAX_HISTORY ? r.residual_history[it - 1] : 0.0;
+    const int sym = (S.full || S.full_mixed) ? kSymNone : kSymMirror;
     auto account = [&](const dbcsr_mult_stats& st, int tier_of_product) {
         r.flops += st.flops;
         r.n_products += st.n_products;
@@ -228,17 +230,24 @@ dbcsr_status sign_iterate(dbcsr_matrix_* H, double mu, const dbcsr_sign_opts* op
                 break;
             }
         }
-        sign_update(X.get(), X2.get(), o.order, correction, o.eps_filter, tier, sym, account);
+        sign_update(X.get(), X2.get(), o.order, S.correction, o.eps_filter, tier, sym, account);
         if (it - 1 < DBCSR_MAX_HISTORY) r.nnzb_history[it - 1] = X->nnzb;
     }
-    // X of a mixed run with a plain BF16 tier (both triangles formed) is symmetric only to that
-    // tier's accuracy, so it is replaced by its symmetric part before P is formed; mirrored
-    // products keep X exactly symmetric
-    if (full_mixed && !full) symmetrize(X.get());
-    copy_matrix(P, X.get());
-    scale_shift(P, -0.5, 0.5);
-    r.trace_p = trace(P);
-    r.e_band = trace_product(P, H);
+    if (S.return_x) {
+        // the iteration's state for a later dbcsr_sign_iterate_resume: X as it stands
+        copy_matrix(P, X.get());
+        r.trace_p = std::nan("");
+        r.e_band = std::nan("");
+    } else {
+        // X of a mixed run with a plain BF16 tier (both triangles formed) is symmetric only to
+        // that tier's accuracy, so it is replaced by its symmetric part before P is formed;
+        // mirrored products keep X exactly symmetric
+        if (S.full_mixed && !S.full) symmetrize(X.get());
+        copy_matrix(P, X.get());
+        scale_shift(P, -0.5, 0.5);
+        r.trace_p = trace(P);
+        r.e_band = trace_product(P, H);
+    }
     DBG_CK(cudaStreamSynchronize(s));
     DBG_CK(cudaStreamSynchronize(P->stream));
     r.iterations = it;
@@ -250,6 +259,51 @@ dbcsr_status sign_iterate(dbcsr_matrix_* H, double mu, const dbcsr_sign_opts* op
     r.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     if (rep) *rep = r;
     return converged ? DBCSR_OK : DBCSR_ENOTCONV;
+}
+
+}  // namespace
+
+dbcsr_status sign_iterate(dbcsr_matrix_* H, double mu, const dbcsr_sign_opts* opts, dbcsr_matrix_* P,
+                          dbcsr_sign_report* rep) {
+    check_finalized(H);
+    if (!P) fail(DBCSR_EINVAL, "sign_iterate: null P_out");
+    if (P->h_bs != H->h_bs) fail(DBCSR_EINVAL, "sign_iterate: P_out block sizes differ from H");
+    const SignSetup S = sign_setup(opts);
+    const auto t0 = std::chrono::steady_clock::now();
+    const double alpha = gershgorin(H, mu);
+    if (!(alpha > 0) || !std::isfinite(alpha)) fail(DBCSR_EINVAL, "sign_iterate: Gershgorin bound is zero or not finite");
+    auto X = make_like(H, H->stream);
+    copy_matrix(X.get(), H);
+    scale_shift(X.get(), 1.0 / alpha, -mu / alpha);
+    dbcsr_sign_report r{};
+    r.alpha = alpha;
+    // precision ladder: BF16 operands / FP32 accumulation while r >= switch_tol, then FP64
+    const int tier = (S.o.prec == DBCSR_MIXED) ? S.low : DBCSR_FP64;
+    return sign_run(H, std::move(X), S, 0, tier, tier == DBCSR_FP64 ? 1 : 0, r, P, rep, t0);
+}
+
+dbcsr_status sign_iterate_resume(dbcsr_matrix_* H, dbcsr_matrix_* X0, const dbcsr_sign_report* prev,
+                                 const dbcsr_sign_opts* opts, dbcsr_matrix_* P, dbcsr_sign_report* rep) {
+    check_finalized(H);
+    check_finalized(X0);
+    if (!P || !prev) fail(DBCSR_EINVAL, "sign_iterate_resume: null P_out or report");
+    if (P->h_bs != H->h_bs || X0->h_bs != H->h_bs)
+        fail(DBCSR_EINVAL, "sign_iterate_resume: block sizes of X or P_out differ from H");
+    if (prev->iterations < 0 || prev->iterations > DBCSR_MAX_HISTORY || prev->fp64_from < 0)
+        fail(DBCSR_EINVAL, "sign_iterate_resume: the report is not one of a sign iteration");
+    const SignSetup S = sign_setup(opts);
+    const auto t0 = std::chrono::steady_clock::now();
+    auto X = make_like(H, H->stream);
+    copy_matrix(X.get(), X0);
+    const int it = prev->iterations;
+    int first_fp64 = prev->fp64_from;
+    if (S.o.prec == DBCSR_FP64) first_fp64 = std::max(1, first_fp64 ? first_fp64 : 1);
+    // the step after `it` multiplies in FP64 once the switch has come (at or before it)
+    const bool fp64_now = S.o.prec == DBCSR_FP64 || (first_fp64 > 0 && first_fp64 <= it + 1);
+    dbcsr_sign_report r = *prev;
+    r.ms_total = 0.0;
+    return sign_run(H, std::move(X), S, it, fp64_now ? DBCSR_FP64 : S.low, fp64_now ? first_fp64 : 0, r, P, rep,
+                    t0);
 }
 
 }  // namespace dbg
