@@ -300,6 +300,32 @@ class SignResult:
         n = min(self.report.iterations, _ffi.MAX_HISTORY)
         return [self.report.residual_history[i] for i in range(n)]
 
+    def log_jsonl(self, path: str, low_tier: str = "bf16x3") -> None:
+        """Appends the iteration's log to a JSON-lines file: one record per step (step k,
+        the tier of its X*X product, residual r_k = ||X_k^2 - 1||_F / N, blocks of X after
+        the step) and a closing record with the totals of the report."""
+        write_sign_log(self.report, path, low_tier)
+
+
+def write_sign_log(rep, path: str, low_tier: str = "bf16x3") -> None:
+    """The per-step log of a dbcsr_sign_report (see SignResult.log_jsonl)."""
+    import json
+    n = min(int(rep.iterations), _ffi.MAX_HISTORY)
+    f64 = int(rep.fp64_from)
+    with open(path, "a") as fh:
+        for i in range(n):
+            k = i + 1
+            tier = "fp64" if (f64 and k >= f64) else low_tier
+            fh.write(json.dumps({"step": k, "tier": tier, "residual": float(rep.residual_history[i]),
+                                 "nnzb_x": int(rep.nnzb_history[i])}) + "\n")
+        fh.write(json.dumps({"summary": True, "iterations": int(rep.iterations), "converged": bool(rep.converged),
+                             "stalled": bool(rep.stalled), "fp64_from": f64, "residual": float(rep.residual),
+                             "trace_p": float(rep.trace_p), "e_band": float(rep.e_band),
+                             "flops": float(rep.flops), "flops_low": float(rep.flops_low),
+                             "ms_total": float(rep.ms_total), "ms_multiply": float(rep.ms_multiply),
+                             "ms_low": float(rep.ms_low), "ms_symbolic": float(rep.ms_symbolic),
+                             "ms_filter": float(rep.ms_filter)}) + "\n")
+
 
 def _sign_flags(full_products: bool, low: int, low_correction: bool = False, return_x: bool = False) -> int:
     if low not in (DBCSR_BF16, DBCSR_BF16X3):
