@@ -12,6 +12,7 @@
 #include <memory>
 #include <stdexcept>
 #include <string>
+#include <thread>
 #include <utility>
 #include <vector>
 
@@ -21,6 +22,22 @@ namespace dbg {
 
 // Largest block edge the kernels accept (atom blocks of the workloads are <= 23).
 constexpr int kMaxBlock = 32;
+
+// Host work split over threads: f(chunk, begin, end) over [0, n) in up to 16 contiguous chunks
+// (one chunk below 2^18 items); chunk c always covers the same range for a given n, so
+// results that are combined in chunk order are deterministic.  Returns the chunk count.
+template <class F>
+int host_chunks(int64_t n, F&& f) {
+    const int hw = (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    const int nt = n < (1 << 18) ? 1 : hw;
+    const int64_t per = (n + nt - 1) / nt;
+    std::vector<std::thread> th;
+    for (int c = 1; c < nt; ++c)
+        th.emplace_back([&, c] { f(c, std::min(n, c * per), std::min(n, (c + 1) * per)); });
+    f(0, 0, std::min(n, per));
+    for (auto& t : th) t.join();
+    return nt;
+}
 
 struct Error : std::runtime_error {
     dbcsr_status code;

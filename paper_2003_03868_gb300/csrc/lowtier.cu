@@ -86,20 +86,27 @@ std::shared_ptr<Groups> build_groups(dbcsr_matrix_* M) {
         double w;
         int32_t a, b;
     };
+    // block rows in chunks on host threads; the chunks' edges joined in chunk order
+    std::vector<std::vector<Edge>> part(16);
+    const int nch = host_chunks(nb, [&](int c, int64_t b, int64_t e) {
+        std::vector<std::pair<double, int32_t>> row;
+        std::vector<Edge>& out = part[c];
+        out.reserve((size_t)(e - b) * kTop);
+        for (int32_t i = (int32_t)b; i < (int32_t)e; ++i) {
+            row.clear();
+            for (int64_t q = rp[i]; q < rp[i + 1]; ++q)
+                if (col[q] != i) row.push_back({nrm[q], col[q]});
+            const size_t t = std::min<size_t>(kTop, row.size());
+            std::partial_sort(row.begin(), row.begin() + t, row.end(), [](const auto& x, const auto& y) {
+                return x.first > y.first || (x.first == y.first && x.second < y.second);
+            });
+            for (size_t k = 0; k < t; ++k)
+                out.push_back({row[k].first, std::min(i, row[k].second), std::max(i, row[k].second)});
+        }
+    });
     std::vector<Edge> edges;
     edges.reserve((size_t)nb * kTop);
-    std::vector<std::pair<double, int32_t>> row;
-    for (int32_t i = 0; i < nb; ++i) {
-        row.clear();
-        for (int64_t q = rp[i]; q < rp[i + 1]; ++q)
-            if (col[q] != i) row.push_back({nrm[q], col[q]});
-        const size_t t = std::min<size_t>(kTop, row.size());
-        std::partial_sort(row.begin(), row.begin() + t, row.end(), [](const auto& x, const auto& y) {
-            return x.first > y.first || (x.first == y.first && x.second < y.second);
-        });
-        for (size_t e = 0; e < t; ++e)
-            edges.push_back({row[e].first, std::min(i, row[e].second), std::max(i, row[e].second)});
-    }
+    for (int c = 0; c < nch; ++c) edges.insert(edges.end(), part[c].begin(), part[c].end());
     std::sort(edges.begin(), edges.end(), [](const Edge& x, const Edge& y) {
         if (x.w != y.w) return x.w > y.w;
         if (x.a != y.a) return x.a < y.a;

@@ -570,22 +570,6 @@ dbcsr_status dbcsr_put_values(dbcsr_matrix m, const double* data, int on_device)
     });
 }
 
-// Runs f(chunk, begin, end) over [0, n) in up to 16 contiguous chunks on host threads (one
-// chunk below 2^18 items); chunk c always covers the same range, so results are deterministic.
-extern "C++" {
-template <class F>
-int host_chunks(int64_t n, F&& f) {
-    const int hw = (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
-    const int nt = n < (1 << 18) ? 1 : hw;
-    const int64_t per = (n + nt - 1) / nt;
-    std::vector<std::thread> th;
-    for (int c = 1; c < nt; ++c) th.emplace_back([&, c] { f(c, std::min(n, c * per), std::min(n, (c + 1) * per)); });
-    f(0, 0, std::min(n, per));
-    for (auto& t : th) t.join();
-    return nt;
-}
-}
-
 // Every staged block is copied at once into a device staging pool (host sources
 // through one cudaMemcpyAsync, so pinned host buffers move by DMA); the host-side records of
 // the blocks are written while that copy runs.
@@ -600,7 +584,7 @@ static void stage(dbcsr_matrix m, int64_t n, const int32_t* rows, const int32_t*
     // per chunk: elements of its blocks (0 if an index is out of range) and a validity flag
     std::array<int64_t, 16> part{};
     std::array<int, 16> bad{};
-    const int nt = host_chunks(n, [&](int c, int64_t b, int64_t e) {
+    const int nt = dbg::host_chunks(n, [&](int c, int64_t b, int64_t e) {
         int64_t t = 0;
         bool x = false;
         for (int64_t i = b; i < e; ++i) {
@@ -640,7 +624,7 @@ static void stage(dbcsr_matrix m, int64_t n, const int32_t* rows, const int32_t*
             acc += part[c];
         }
     }
-    host_chunks(n, [&](int c, int64_t b, int64_t e) {
+    dbg::host_chunks(n, [&](int c, int64_t b, int64_t e) {
         int64_t at = start[c];
         for (int64_t i = b; i < e; ++i) {
             m->st_row[base + i] = rows[i];
@@ -671,7 +655,7 @@ dbcsr_status dbcsr_finalize(dbcsr_matrix m) {
         const std::vector<int32_t>& sc = m->st_col;
         // staged in strictly increasing (row, column) order: then no block repeats
         std::array<int, 16> unsorted{};
-        host_chunks(nb, [&](int c, int64_t b, int64_t e) {
+        dbg::host_chunks(nb, [&](int c, int64_t b, int64_t e) {
             bool u = false;
             for (int64_t i = std::max<int64_t>(b, 1); i < e && !u; ++i)
                 u = !(sr[i - 1] < sr[i] || (sr[i - 1] == sr[i] && sc[i - 1] < sc[i]));
@@ -698,7 +682,7 @@ dbcsr_status dbcsr_finalize(dbcsr_matrix m) {
         // blocks in order, then their element offsets: per-chunk sums, then a fill from each
         // chunk's start
         std::array<int64_t, 16> part{};
-        const int nt = host_chunks(nb, [&](int c, int64_t b, int64_t e) {
+        const int nt = dbg::host_chunks(nb, [&](int c, int64_t b, int64_t e) {
             int64_t t = 0;
             for (int64_t i = b; i < e; ++i) {
                 const int64_t o = sorted ? i : order[i];
@@ -711,7 +695,7 @@ dbcsr_status dbcsr_finalize(dbcsr_matrix m) {
         });
         std::array<int64_t, 16> start{};
         for (int c = 1; c < nt; ++c) start[c] = start[c - 1] + part[c - 1];
-        host_chunks(nb, [&](int c, int64_t b, int64_t e) {
+        dbg::host_chunks(nb, [&](int c, int64_t b, int64_t e) {
             int64_t at = start[c];
             for (int64_t i = b; i < e; ++i) {
                 off[i] = at;
@@ -736,7 +720,7 @@ dbcsr_status dbcsr_finalize(dbcsr_matrix m) {
             DBG_CK(cudaMemcpyAsync(m->row.p, row.data(), sizeof(int32_t) * nb, cudaMemcpyHostToDevice, s));
             std::array<int, 16> moved{};
             if (sorted)
-                host_chunks(nb, [&](int c, int64_t b, int64_t e) {
+                dbg::host_chunks(nb, [&](int c, int64_t b, int64_t e) {
                     bool x = false;
                     for (int64_t i = b; i < e && !x; ++i) x = src[i] != off[i];
                     moved[c] = x;
