@@ -187,9 +187,26 @@ class RowsSample:
                 f"candidate block, no prescreen)")
 
 
+def one_core_sample(h, w):
+    """The oracle's rows sample of the first product on one host thread (the thread count is
+    restored afterwards)."""
+    from oracle import bsr
+    n0 = bsr.num_threads()
+    bsr.set_num_threads(1)
+    try:
+        smp = RowsSample(h, w, CPU_1CORE_ROWS_FRAC)
+        f, dt, cores = smp.run()
+    finally:
+        bsr.set_num_threads(n0)
+    return {"value": f / dt / 1e12, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+            "sample": smp.text(f, dt)}
+
+
 # block rows of the 4,096-water X0 in one oracle sample: a reference-arm step (about 5 s on 16
 # host cores) and the CPU baseline of the main line (about 10 s)
 REF_ROWS_FRAC, CPU_ROWS_FRAC = 1.0 / 8, 1.0 / 4
+# the same sample on one host core: block rows of X0 in that sample (about 10 s)
+CPU_1CORE_ROWS_FRAC = 1.0 / 64
 HEADLINE_METRIC = "block-GEMM TFLOP/s & time-to-P at 1e-6 Ha/atom, mixed vs FP64 on GB300"
 
 
@@ -953,7 +970,7 @@ def run_headline(args, gb, synth, torch, barrier, dist, rank, world, local):
         smp = RowsSample(h, w, CPU_ROWS_FRAC)
         f, dt, cores = smp.run()
         out["cpu_baseline"] = {"value": f / dt / 1e12, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
-                               "sample": smp.text(f, dt)}
+                               "sample": smp.text(f, dt), "single_core": one_core_sample(h, w)}
     if rank == 0:
         print(json.dumps(out))
     if dist:

@@ -46,6 +46,8 @@ def lib():
         L.oracle_trace_product.restype = C.c_double
         L.oracle_abs_row_sums.argtypes = [C.c_int32, p, p, p, p, p, p, C.c_double, p]
         L.oracle_num_threads.restype = C.c_int
+        L.oracle_set_num_threads.argtypes = [C.c_int]
+        L.oracle_set_num_threads.restype = None
         L.oracle_mm_block.argtypes = [C.c_int32, C.c_int32, p, C.c_double] + [p] * 8 + [C.c_double, p, p]
         _lib = L
     return _lib
@@ -303,6 +305,12 @@ def add(alpha: float, A: Mat, beta: float, B: Mat) -> Mat:
 
 def num_threads() -> int:
     return int(lib().oracle_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    """Threads of the oracle's parallel loops from now on (timing on fewer cores; no effect on
+    the results, which do not depend on the thread count)."""
+    lib().oracle_set_num_threads(int(n))
 
 
 def os_threads() -> int:

@@ -323,6 +323,15 @@ int oracle_num_threads(void) {
 #endif
 }
 
+/* Threads of the parallel loops that follow (n >= 1); for timing the oracle on one core. */
+void oracle_set_num_threads(int n) {
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 /*
  * One block of the product: out = alpha * sum_K A_IK * B_KJ (ascending K, then k)
  * + beta * ci (ci may be NULL).  Used to check single outputs of large products.

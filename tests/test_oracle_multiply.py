@@ -180,6 +180,20 @@ def test_thread_count_does_not_change_results(monkeypatch):
     assert outs[0] == outs[1]
 
 
+def test_set_num_threads_gives_the_same_product():
+    A = bsr.Mat.of(synth.build_decay(synth.DECAY_32))
+    n0 = bsr.num_threads()
+    try:
+        bsr.set_num_threads(1)
+        assert bsr.num_threads() == 1
+        C1 = bsr.multiply(1.0, A, A, eps=1e-6)
+        bsr.set_num_threads(max(2, n0))
+        C2 = bsr.multiply(1.0, A, A, eps=1e-6)
+    finally:
+        bsr.set_num_threads(n0)
+    assert np.array_equal(C1.col, C2.col) and np.array_equal(C1.data, C2.data)
+
+
 def _dense_block(D, roff, I, J):
     return D[roff[I]:roff[I + 1], roff[J]:roff[J + 1]]
 
