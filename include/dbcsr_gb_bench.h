@@ -10,6 +10,8 @@
 
 #include <stdint.h>
 
+#include "dbcsr_gb.h"
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -47,6 +49,18 @@ int32_t dbcsr_pool_usage(int64_t* used_now, int64_t* used_high, int32_t reset_hi
  * the context staying usable.  *waited (nullable) receives the cycles the wait took.
  */
 int32_t dbcsr_wait_selftest(int64_t limit_cycles, int32_t arrive, int64_t* waited);
+
+/*
+ * The block groups of the tensor-core tier, built now from m's block norms (a BF16 product with
+ * m as A builds the same groups when m carries none): the block rows are merged along their
+ * strongest couplings -- every row's 12 largest off-diagonal block norms, ties to the lower
+ * column, taken in decreasing norm (then lower row, then lower column) -- as long as a group
+ * keeps at most 112 rows and 16 blocks.  Host outputs, each nullable: g_of[nblk] the group of
+ * every block row (groups numbered in the order of their first block), norms[nnzb] the FP64
+ * block Frobenius norms the couplings were ranked by (m's block order), *ngrp the number of
+ * groups.  m is not changed.  Errors: DBCSR_ESTATE if m is not finalized; DBCSR_ECUDA.
+ */
+int32_t dbcsr_matrix_groups(dbcsr_matrix m, int32_t* g_of, double* norms, int32_t* ngrp);
 
 #ifdef __cplusplus
 }

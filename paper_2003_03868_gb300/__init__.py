@@ -133,6 +133,16 @@ class Matrix:
     def nnzb(self) -> int:
         return self.info()[1]
 
+    def groups(self):
+        """The tensor-core tier's block groups for this matrix (dbcsr_matrix_groups): the group
+        of every block row and the FP64 block norms they were formed from."""
+        nb, nz, _ = self.info()
+        g_of = np.empty(nb, dtype=np.int32)
+        norms = np.empty(max(nz, 1), dtype=np.float64)
+        ng = C.c_int32()
+        _check(lib().dbcsr_matrix_groups(self.handle, _ptr(g_of), _ptr(norms), C.byref(ng)), "matrix_groups")
+        return g_of, norms[:nz], ng.value
+
     def get_block(self, row: int, col: int):
         m, n = int(self.blk_size[row]), int(self.blk_size[col])
         out = np.empty((m, n))

@@ -137,6 +137,7 @@ SIGNATURES = [
     ("dbcsr_launch_count", C.c_int64, []),
     ("dbcsr_pool_usage", C.c_int32, [C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.c_int32]),
     ("dbcsr_wait_selftest", C.c_int32, [C.c_int64, C.c_int32, C.POINTER(C.c_int64)]),
+    ("dbcsr_matrix_groups", C.c_int32, [P, P, P, C.POINTER(C.c_int32)]),
 ]
 
 _lib = None

@@ -52,7 +52,7 @@ constexpr int kTmemCols = 128 * kAccs;
 constexpr int kEpiBatch = 8;                   // C-input loads a lane issues before its first store
 constexpr long long kWaitLimit = 4000000000ll; // about 2 s at 2 GHz
 
-// ------------------------------------------------------------------ groups (host)
+// ------------------------------------------------------------------ groups
 struct Dsu {
     std::vector<int32_t> p, w, n;
     int32_t find(int32_t x) {
@@ -64,6 +64,82 @@ struct Dsu {
     }
 };
 
+// The kTop strongest off-diagonal couplings of every block row: one warp per row.  Every lane
+// keeps the best kTop entries of its strided share (sorted by norm, descending, then column,
+// ascending), then kTop rounds of a warp arg-max pop the row's best.  Slots the row cannot fill
+// get a = -1.
+constexpr int kTop = 12;
+struct alignas(16) Coupling {
+    double w;
+    int32_t a, b;
+};
+
+__device__ __forceinline__ bool stronger(double w1, int32_t c1, double w2, int32_t c2) {
+    return w1 > w2 || (w1 == w2 && c1 < c2);
+}
+
+__global__ void __launch_bounds__(256) k_top_couplings(int32_t nb, const int64_t* __restrict__ rp,
+                                                       const int32_t* __restrict__ col,
+                                                       const double* __restrict__ nrm, Coupling* __restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const int32_t i = (int32_t)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5));
+    if (i >= nb) return;
+    constexpr int32_t kNone = 0x7fffffff;
+    double w[kTop];
+    int32_t c[kTop];
+#pragma unroll
+    for (int k = 0; k < kTop; ++k) {
+        w[k] = -1.0;                     // below every norm
+        c[k] = kNone;
+    }
+    const int64_t q1 = rp[i + 1];
+    for (int64_t q = rp[i] + lane; q < q1; q += 32) {
+        int32_t nc = col[q];
+        if (nc == i) continue;
+        double nw = nrm[q];
+        if (!stronger(nw, nc, w[kTop - 1], c[kTop - 1])) continue;
+#pragma unroll
+        for (int k = 0; k < kTop; ++k) {  // insertion: the displaced entry moves down
+            if (stronger(nw, nc, w[k], c[k])) {
+                const double tw = w[k];
+                const int32_t tc = c[k];
+                w[k] = nw;
+                c[k] = nc;
+                nw = tw;
+                nc = tc;
+            }
+        }
+    }
+    Coupling* o = out + (size_t)i * kTop;
+    int r = 0;
+    for (; r < kTop; ++r) {
+        double bw = w[0];
+        int32_t bc = c[0];
+#pragma unroll
+        for (int sh = 16; sh; sh >>= 1) {
+            const double ow = __shfl_xor_sync(0xffffffffu, bw, sh);
+            const int32_t oc = __shfl_xor_sync(0xffffffffu, bc, sh);
+            if (stronger(ow, oc, bw, bc)) {
+                bw = ow;
+                bc = oc;
+            }
+        }
+        if (bc == kNone) break;          // the same on every lane
+        if (lane == 0) o[r] = Coupling{bw, min(i, bc), max(i, bc)};
+        if (c[0] == bc) {                // the one lane that held it (columns are unique in a row)
+#pragma unroll
+            for (int k = 0; k + 1 < kTop; ++k) {
+                w[k] = w[k + 1];
+                c[k] = c[k + 1];
+            }
+            w[kTop - 1] = -1.0;
+            c[kTop - 1] = kNone;
+        }
+    }
+    if (lane == 0)
+        for (; r < kTop; ++r) o[r] = Coupling{0.0, -1, -1};
+}
+
 }  // namespace
 
 std::shared_ptr<Groups> build_groups(dbcsr_matrix_* M) {
@@ -71,43 +147,22 @@ std::shared_ptr<Groups> build_groups(dbcsr_matrix_* M) {
     ensure_norms(M);
     cudaStream_t s = M->stream;
     const int32_t nb = M->nblk;
-    std::vector<int64_t> rp(nb + 1);
-    std::vector<int32_t> col(std::max<int64_t>(M->nnzb, 1));
-    std::vector<double> nrm(std::max<int64_t>(M->nnzb, 1));
-    DBG_CK(cudaMemcpyAsync(rp.data(), M->rp.p, sizeof(int64_t) * (nb + 1), cudaMemcpyDeviceToHost, s));
-    if (M->nnzb) {
-        DBG_CK(cudaMemcpyAsync(col.data(), M->col.p, sizeof(int32_t) * M->nnzb, cudaMemcpyDeviceToHost, s));
-        DBG_CK(cudaMemcpyAsync(nrm.data(), M->norms.p, sizeof(double) * M->nnzb, cudaMemcpyDeviceToHost, s));
+    // candidate merges: the kTop strongest off-diagonal couplings of every block row, selected on
+    // the device; only the selected couplings come to the host
+    std::vector<Coupling> top((size_t)nb * kTop);
+    if (nb > 0) {
+        DBuf<Coupling> d_top;
+        d_top.alloc((int64_t)nb * kTop, s);
+        k_top_couplings<<<grid_for(nb, 8), 256, 0, s>>>(nb, M->rp.p, M->col.p, M->norms.p, d_top.p);
+        DBG_LAUNCH_CK();
+        DBG_CK(cudaMemcpyAsync(top.data(), d_top.p, sizeof(Coupling) * top.size(), cudaMemcpyDeviceToHost, s));
+        DBG_CK(cudaStreamSynchronize(s));
     }
-    DBG_CK(cudaStreamSynchronize(s));
-    // candidate merges: the kTop strongest off-diagonal couplings of every block row
-    constexpr int kTop = 12;
-    struct Edge {
-        double w;
-        int32_t a, b;
-    };
-    // block rows in chunks on host threads; the chunks' edges joined in chunk order
-    std::vector<std::vector<Edge>> part(16);
-    const int nch = host_chunks(nb, [&](int c, int64_t b, int64_t e) {
-        std::vector<std::pair<double, int32_t>> row;
-        std::vector<Edge>& out = part[c];
-        out.reserve((size_t)(e - b) * kTop);
-        for (int32_t i = (int32_t)b; i < (int32_t)e; ++i) {
-            row.clear();
-            for (int64_t q = rp[i]; q < rp[i + 1]; ++q)
-                if (col[q] != i) row.push_back({nrm[q], col[q]});
-            const size_t t = std::min<size_t>(kTop, row.size());
-            std::partial_sort(row.begin(), row.begin() + t, row.end(), [](const auto& x, const auto& y) {
-                return x.first > y.first || (x.first == y.first && x.second < y.second);
-            });
-            for (size_t k = 0; k < t; ++k)
-                out.push_back({row[k].first, std::min(i, row[k].second), std::max(i, row[k].second)});
-        }
-    });
-    std::vector<Edge> edges;
-    edges.reserve((size_t)nb * kTop);
-    for (int c = 0; c < nch; ++c) edges.insert(edges.end(), part[c].begin(), part[c].end());
-    std::sort(edges.begin(), edges.end(), [](const Edge& x, const Edge& y) {
+    std::vector<Coupling> edges;
+    edges.reserve(top.size());
+    for (const Coupling& e : top)
+        if (e.a >= 0) edges.push_back(e);
+    std::sort(edges.begin(), edges.end(), [](const Coupling& x, const Coupling& y) {
         if (x.w != y.w) return x.w > y.w;
         if (x.a != y.a) return x.a < y.a;
         return x.b < y.b;
@@ -118,7 +173,7 @@ std::shared_ptr<Groups> build_groups(dbcsr_matrix_* M) {
     d.n.assign(nb, 1);
     std::iota(d.p.begin(), d.p.end(), 0);
     for (int32_t i = 0; i < nb; ++i) d.w[i] = M->h_bs[i];
-    for (const Edge& e : edges) {
+    for (const Coupling& e : edges) {
         int32_t a = d.find(e.a), b = d.find(e.b);
         if (a == b || d.w[a] + d.w[b] > kGroupWidth || d.n[a] + d.n[b] > kGroupMembers) continue;
         if (b < a) std::swap(a, b);

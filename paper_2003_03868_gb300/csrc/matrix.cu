@@ -16,6 +16,7 @@
 #include <cstring>
 
 #include "common.cuh"
+#include "dbcsr_gb_bench.h"
 
 namespace dbg {
 
@@ -547,6 +548,19 @@ dbcsr_status dbcsr_create(dbcsr_matrix* out, int32_t nblk, const int32_t* blk_si
             throw;
         }
         *out = m;
+    });
+}
+
+int32_t dbcsr_matrix_groups(dbcsr_matrix m, int32_t* g_of, double* norms, int32_t* ngrp) {
+    return guarded([&] {
+        dbg::check_finalized(m);
+        std::shared_ptr<dbg::Groups> g = dbg::build_groups(m);
+        if (g_of && m->nblk)
+            DBG_CK(cudaMemcpyAsync(g_of, g->g_of.p, sizeof(int32_t) * m->nblk, cudaMemcpyDeviceToHost, m->stream));
+        if (norms && m->nnzb)
+            DBG_CK(cudaMemcpyAsync(norms, m->norms.p, sizeof(double) * m->nnzb, cudaMemcpyDeviceToHost, m->stream));
+        DBG_CK(cudaStreamSynchronize(m->stream));
+        if (ngrp) *ngrp = g->ngrp;
     });
 }
 
