@@ -726,7 +726,6 @@ dbcsr_status dbcsr_finalize(dbcsr_matrix m) {
         m->col.alloc(std::max<int64_t>(nb, 1), s);
         m->row.alloc(std::max<int64_t>(nb, 1), s);
         m->off.alloc(nb + 1, s);
-        m->data.alloc(std::max<int64_t>(m->nel, 1), s);
         DBG_CK(cudaMemcpyAsync(m->rp.p, rp.data(), sizeof(int64_t) * (m->nblk + 1), cudaMemcpyHostToDevice, s));
         DBG_CK(cudaMemcpyAsync(m->off.p, off.data(), sizeof(int64_t) * (nb + 1), cudaMemcpyHostToDevice, s));
         if (nb) {
@@ -745,6 +744,7 @@ dbcsr_status dbcsr_finalize(dbcsr_matrix m) {
                 // staged in block-CSR order: the staging pool is the data
                 m->data = std::move(m->st_dev);
             } else {
+                m->data.alloc(std::max<int64_t>(m->nel, 1), s);
                 dbg::DBuf<int64_t> dsrc;
                 dsrc.alloc(nb, s);
                 DBG_CK(cudaMemcpyAsync(dsrc.p, src.data(), sizeof(int64_t) * nb, cudaMemcpyHostToDevice, s));
@@ -754,6 +754,7 @@ dbcsr_status dbcsr_finalize(dbcsr_matrix m) {
                 DBG_CK(cudaStreamSynchronize(s));
             }
         }
+        if (!m->data.p) m->data.alloc(1, s);    // no block: a one-element buffer, as for every matrix
         DBG_CK(cudaStreamSynchronize(s));
         m->st_row.clear(); m->st_row.shrink_to_fit();
         m->st_col.clear(); m->st_col.shrink_to_fit();
