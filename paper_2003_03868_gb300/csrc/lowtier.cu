@@ -30,6 +30,7 @@
 #include <numeric>
 #include <vector>
 
+#include "bf16split.cuh"
 #include "common.cuh"
 #include "tc05.cuh"
 
@@ -376,33 +377,6 @@ __global__ void k_gt_transpose(int64_t nt, const int32_t* __restrict__ t_row, co
 }
 
 // ------------------------------------------------------------------ packing
-// FP64 -> BF16, round to nearest even, from the IEEE-754 encodings (binary32 range; values
-// below its normal range become signed zero).
-__device__ __forceinline__ uint16_t lt_bf16_bits(double x) {
-    const uint64_t u = (uint64_t)__double_as_longlong(x);
-    const uint16_t sign = (uint16_t)((u >> 48) & 0x8000u);
-    const int e = (int)((u >> 52) & 0x7ff);
-    if (e == 0x7ff) return (uint16_t)(sign | 0x7f80u | ((u & 0xfffffffffffffull) ? 0x40u : 0u));
-    const int eb = e - 1023 + 127;               // biased binary32 exponent
-    if (eb < 1) return sign;                     // below the normal range
-    uint64_t mant = u & 0xfffffffffffffull;      // 52 bits; keep 7
-    const uint64_t keep = mant >> 45, rest = mant & ((1ull << 45) - 1);
-    const uint64_t half = 1ull << 44;
-    uint32_t m7 = (uint32_t)keep;
-    int ex = eb;
-    if (rest > half || (rest == half && (m7 & 1u))) {
-        if (++m7 == 128u) {
-            m7 = 0;
-            ++ex;
-        }
-    }
-    if (ex >= 255) return (uint16_t)(sign | 0x7f80u);
-    return (uint16_t)(sign | ((uint32_t)ex << 7) | m7);
-}
-__device__ __forceinline__ double lt_bf16_value(uint16_t b) {
-    return (double)__uint_as_float((uint32_t)b << 16);
-}
-
 struct PackArgs {
     int64_t nb;
     const int32_t* row; const int32_t* col; const int64_t* off; const double* data; const int32_t* bs;
@@ -429,15 +403,28 @@ __global__ void k_gt_pack(PackArgs P) {
         uint8_t* base = P.pack + P.t_off[t];
         const int R = lt_rows(P.g_w[P.g_of[P.transpose ? J : I]]);
         const int slab = P.nparts * 2 * R * 16;
+        // (i, j) of element e = i n + j, stepped by 32 elements without a division per element
+        const int di = 32 / n, dj = 32 - di * n;
+        int i = lane / n, j = lane - i * n;
         for (int e = lane; e < m * n; e += 32) {
-            const int i = e / n, j = e - i * n;
             const int r = P.transpose ? pj + j : pi + i;
             const int kc = P.transpose ? pi + i : pj + j;
             const double x = src[e];
-            const uint16_t hi = lt_bf16_bits(x);
             uint8_t* p = base + (int64_t)(kc >> 4) * slab + ((kc >> 3) & 1) * (R * 16) + r * 16 + (kc & 7) * 2;
-            *(uint16_t*)p = hi;
-            if (P.nparts == 2) *(uint16_t*)(p + 2 * R * 16) = lt_bf16_bits(x - lt_bf16_value(hi));
+            if (P.nparts == 2) {
+                uint16_t hi, lo;
+                bf16_split(x, hi, lo);
+                *(uint16_t*)p = hi;
+                *(uint16_t*)(p + 2 * R * 16) = lo;
+            } else {
+                *(uint16_t*)p = bf16_bits(x);
+            }
+            i += di;
+            j += dj;
+            if (j >= n) {
+                j -= n;
+                ++i;
+            }
         }
     }
 }

@@ -166,16 +166,29 @@ __global__ void k_block_norms(int64_t nb, const int32_t* __restrict__ row, const
         const int n = bs[J], area = bs[I] * n;
         const double* x = data + off[b];
         double s = 0.0, d = 0.0;
-        for (int e = lane; e < area; e += 32) {
-            const double v = x[e];
-            s = fma(v, v, s);
-            const double w = (I == J && (e / n) == (e % n)) ? v - 1.0 : v;
-            d = fma(w, w, d);
-        }
+        if (I != J) {
+            // off the diagonal the distance to 1 is the norm: one FMA chain (the FP64 rate,
+            // not the memory, bounds this loop)
+            for (int e = lane; e < area; e += 32) {
+                const double v = x[e];
+                s = fma(v, v, s);
+            }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            s += __shfl_xor_sync(0xffffffffu, s, o);
-            d += __shfl_xor_sync(0xffffffffu, d, o);
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            d = s;
+        } else {
+            // element e = i n + j of a square block is diagonal when e is a multiple of n + 1
+            for (int e = lane; e < area; e += 32) {
+                const double v = x[e];
+                s = fma(v, v, s);
+                const double w = (e % (n + 1) == 0) ? v - 1.0 : v;
+                d = fma(w, w, d);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                s += __shfl_xor_sync(0xffffffffu, s, o);
+                d += __shfl_xor_sync(0xffffffffu, d, o);
+            }
         }
         if (lane == 0) {
             if (norms) norms[b] = sqrt(s);
@@ -193,10 +206,14 @@ __global__ void k_scale_shift(int64_t nb, const int32_t* __restrict__ row, const
         const int I = row[b], J = col[b];
         const int n = bs[J], area = bs[I] * n;
         double* x = data + off[b];
-        for (int e = lane; e < area; e += 32) {
-            double v = scale * x[e];
-            if (I == J && (e / n) == (e % n)) v += shift;
-            x[e] = v;
+        if (I != J) {
+            for (int e = lane; e < area; e += 32) x[e] = scale * x[e];
+        } else {
+            for (int e = lane; e < area; e += 32) {
+                double v = scale * x[e];
+                if (e % (n + 1) == 0) v += shift;     // the diagonal of a square block
+                x[e] = v;
+            }
         }
     }
 }

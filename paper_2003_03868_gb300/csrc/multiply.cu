@@ -409,6 +409,12 @@ __global__ void k_form_stats(int64_t nform, const int32_t* __restrict__ f_row, c
                              unsigned long long* __restrict__ flops, unsigned long long* __restrict__ nprod,
                              unsigned long long* __restrict__ shape_cnt, uint8_t* __restrict__ comp,
                              const int32_t* __restrict__ grp) {
+    // the shape histogram is gathered per CTA in shared memory (a few shapes take every block,
+    // so global atomics per block would serialise on them) and added once per nonzero bin
+    constexpr int kBins = (kMaxBlock + 1) * (kMaxBlock + 1);
+    __shared__ unsigned int hist[kBins];
+    for (int t = threadIdx.x; t < kBins; t += blockDim.x) hist[t] = 0;
+    __syncthreads();
     unsigned long long lf = 0, lp = 0;
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nform; k += (int64_t)gridDim.x * blockDim.x) {
         const bool computed = block_role(sym, f_row[k], f_col[k], mirror[k], grp) == 0;
@@ -420,8 +426,11 @@ __global__ void k_form_stats(int64_t nform, const int32_t* __restrict__ f_row, c
         const int m = bs[f_row[k]], n = bs[f_col[k]];
         lf += 2ull * (unsigned long long)m * (unsigned long long)n * (unsigned long long)f_ksum[k];
         lp += (unsigned long long)f_np[k];
-        atomicAdd(shape_cnt + m * (kMaxBlock + 1) + n, 1ull);
+        atomicAdd(&hist[m * (kMaxBlock + 1) + n], 1u);
     }
+    __syncthreads();
+    for (int t = threadIdx.x; t < kBins; t += blockDim.x)
+        if (hist[t]) atomicAdd(shape_cnt + t, (unsigned long long)hist[t]);
     for (int o = 16; o > 0; o >>= 1) {
         lf += __shfl_xor_sync(0xffffffffu, lf, o);
         lp += __shfl_xor_sync(0xffffffffu, lp, o);
@@ -457,11 +466,19 @@ __global__ void k_mirror_copy(int64_t nform, int sym, const int64_t* __restrict_
         const double* S = c_data + f_off[src];
         double* D = c_data + f_off[k];
         double sq = 0.0;
+        // (i, j) of element e = i n + j, stepped by 32 elements without a division per element
+        const int di = 32 / n, dj = 32 - di * n;
+        int i = lane / n, j = lane - i * n;
         for (int e = lane; e < m * n; e += 32) {
-            const int i = e / n, j = e - i * n;
             const double v = S[j * m + i];
             D[e] = v;
             sq = fma(v, v, sq);
+            i += di;
+            j += dj;
+            if (j >= n) {
+                j -= n;
+                ++i;
+            }
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
@@ -1152,7 +1169,7 @@ void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbc
         } else {
             DBG_CK(cudaMemsetAsync(mirror.p, 0xff, sizeof(int64_t) * nform, s));   // -1 (unused without sym)
         }
-        k_form_stats<<<grid_for(nform, 256), 256, 0, s>>>(nform, f_row.p, f_col.p, f_np.p, f_ksum.p, mirror.p,
+        k_form_stats<<<grid_for(nform, 256, (int64_t)num_sms() * 8), 256, 0, s>>>(nform, f_row.p, f_col.p, f_np.p, f_ksum.p, mirror.p,
                                                           sym_result, A->bs.p,
                                                           (unsigned long long*)flops.p,
                                                           (unsigned long long*)nprod_exec.p,

@@ -58,14 +58,18 @@ __global__ void k_trace_product_blocks(int64_t nb, const int32_t* __restrict__ b
     }
 }
 
-// One thread per matrix row i of block row I: sum_j |(A - mu 1)_ij|; the maximum
-// over rows is taken with an integer atomicMax on the bits of the non-negative sum.
-__global__ void k_gershgorin(int32_t nblk, const int32_t* __restrict__ bs, const int64_t* __restrict__ rp,
-                             const int32_t* __restrict__ col, const int64_t* __restrict__ off,
-                             const double* __restrict__ data, double mu, unsigned long long* __restrict__ maxbits) {
-    const int32_t I = blockIdx.x;
+// One warp per block row I (eight per CTA), one lane per matrix row i of it: sum_j |(A - mu 1)_ij|
+// in ascending column order; the maximum over rows is taken with an integer atomicMax on the
+// bits of the non-negative sum.
+constexpr int kGershWarps = 8;
+__global__ void __launch_bounds__(32 * kGershWarps)
+    k_gershgorin(int32_t nblk, const int32_t* __restrict__ bs, const int64_t* __restrict__ rp,
+                 const int32_t* __restrict__ col, const int64_t* __restrict__ off,
+                 const double* __restrict__ data, double mu, unsigned long long* __restrict__ maxbits) {
+    const int32_t I = (int32_t)(blockIdx.x * kGershWarps + (threadIdx.x >> 5));
+    if (I >= nblk) return;
     const int m = bs[I];
-    const int i = threadIdx.x;
+    const int i = threadIdx.x & 31;
     if (i >= m) return;
     double s = 0.0;
     bool has_diag = false;
@@ -124,7 +128,7 @@ double gershgorin(dbcsr_matrix_* m, double mu) {
     DBuf<double> out;
     out.alloc(1, s);
     out.zero();
-    k_gershgorin<<<m->nblk, kMaxBlock, 0, s>>>(m->nblk, m->bs.p, m->rp.p, m->col.p, m->off.p, m->data.p, mu,
+    k_gershgorin<<<(unsigned)ceil_div(m->nblk, kGershWarps), 32 * kGershWarps, 0, s>>>(m->nblk, m->bs.p, m->rp.p, m->col.p, m->off.p, m->data.p, mu,
                                                (unsigned long long*)out.p);
     DBG_LAUNCH_CK();
     return read_f64(out.p, s);
