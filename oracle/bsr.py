@@ -46,6 +46,9 @@ def lib():
         L.oracle_trace_product.restype = C.c_double
         L.oracle_abs_row_sums.argtypes = [C.c_int32, p, p, p, p, p, p, C.c_double, p]
         L.oracle_num_threads.restype = C.c_int
+        L.oracle_prescreen.argtypes = [C.c_int32, C.c_double, p, p, p, p, p, p, C.c_double, p, p, p, p, p,
+                                       C.c_double, p]
+        L.oracle_prescreen.restype = C.c_int
         L.oracle_set_num_threads.argtypes = [C.c_int]
         L.oracle_set_num_threads.restype = None
         L.oracle_mm_block.argtypes = [C.c_int32, C.c_int32, p, C.c_double] + [p] * 8 + [C.c_double, p, p]
@@ -139,7 +142,7 @@ def from_dense(D: np.ndarray, bs, pattern=None) -> Mat:
 
 @dataclasses.dataclass
 class MultInfo:
-    unfiltered: Mat         # alpha*A*B + beta*C_in on the full product pattern
+    unfiltered: Mat         # alpha*A*B + beta*C_in on the full product pattern (prescreened: the formed blocks)
     norms: np.ndarray       # Frobenius norm of each unfiltered block
     keep: np.ndarray        # bool mask of the blocks that survive the filter
     dev2: float             # ||filtered - 1||_F^2 (the residual the sign iteration tests)
@@ -196,12 +199,45 @@ def filter_blocks(M: Mat, eps: float) -> Mat:
     return select_blocks(M, keep_mask(M, norms, eps))
 
 
+# a candidate is kept when its bound reaches eps (1 - 1e-12): the margin covers the rounding of
+# the bound's sum, so that no block whose computed norm reaches eps is left out
+PRESCREEN_MARGIN = 1.0 - 1e-12
+
+
+def prescreen_mask(alpha: float, A: Mat, B: Mat, beta: float, Cin: Mat | None, rp, col, eps: float):
+    """keep[q] for the candidates (rp, col) of alpha*A*B + beta*C_in: I == J, or the norm bound
+    |alpha| sum_K ||A_IK|| ||B_KJ|| (+ |beta| ||C_in,IJ||) at least eps (1 - 1e-12)."""
+    na, _ = block_norms(A)
+    nb, _ = block_norms(B)
+    use_c = Cin is not None and beta != 0.0
+    nc = block_norms(Cin)[0] if use_c else None
+    keep = np.zeros(max(int(rp[-1]), 1), dtype=np.int32)
+    err = lib().oracle_prescreen(A.nblk, abs(float(alpha)), _p(A.rp), _p(A.col), _p(na), _p(B.rp), _p(B.col),
+                                 _p(nb), abs(float(beta)), _p(Cin.rp) if use_c else None,
+                                 _p(Cin.col) if use_c else None, _p(nc) if use_c else None,
+                                 _p(np.ascontiguousarray(rp, dtype=np.int64)),
+                                 _p(np.ascontiguousarray(col, dtype=np.int32)), float(eps) * PRESCREEN_MARGIN, _p(keep))
+    if err:
+        raise MemoryError("oracle_prescreen")
+    return keep[:int(rp[-1])].astype(bool)
+
+
 def multiply(alpha: float, A: Mat, B: Mat, beta: float = 0.0, Cin: Mat | None = None,
-             eps: float = 0.0, info: bool = False):
-    """C = filter(alpha*A*B + beta*C_in, eps).  Returns C (and a MultInfo if ``info``)."""
+             eps: float = 0.0, info: bool = False, prescreen: bool = False):
+    """C = filter(alpha*A*B + beta*C_in, eps).  Returns C (and a MultInfo if ``info``).
+
+    prescreen: form only the candidate blocks whose norm bound reaches eps (and the diagonal
+    ones); the others would be filtered anyway, so C is the same, bit for bit, with fewer block
+    products (``MultInfo.unfiltered`` then holds the formed blocks)."""
     if not (np.array_equal(A.bs, B.bs) and (Cin is None or np.array_equal(A.bs, Cin.bs))):
         raise ValueError("block sizes differ")
     rp, col = product_pattern(A, B, Cin if (Cin is not None and beta != 0.0) else None)
+    if prescreen and eps > 0.0:
+        keep0 = prescreen_mask(alpha, A, B, beta, Cin, rp, col, eps)
+        cnt = np.bincount(np.repeat(np.arange(A.nblk), np.diff(rp))[keep0], minlength=A.nblk)
+        rp = np.zeros(A.nblk + 1, dtype=np.int64)
+        np.cumsum(cnt, out=rp[1:])
+        col = np.ascontiguousarray(col[keep0])
     rows = np.repeat(np.arange(A.nblk, dtype=np.int32), np.diff(rp))
     area = A.bs[rows].astype(np.int64) * A.bs[col].astype(np.int64)
     data = np.zeros(int(area.sum()))

@@ -132,6 +132,7 @@ int oracle_mm_numeric(int32_t nblk, const int32_t* bs,
 #pragma omp atomic write
             err = 1;
         } else {
+            for (int32_t J = 0; J <= nblk; ++J) pos[J] = -1;    /* not in C's pattern */
 #pragma omp for schedule(dynamic, 8)
             for (int32_t I = 0; I < nblk; ++I) {
                 const int64_t m = bs[I];
@@ -160,6 +161,7 @@ int oracle_mm_numeric(int32_t nblk, const int32_t* bs,
                     const double* a = a_data + a_boff[p];
                     for (int64_t q = b_rp[K]; q < b_rp[K + 1]; ++q) {
                         const int32_t J = b_col[q];
+                        if (pos[J] < 0) continue;   /* a candidate the caller left out (prescreen) */
                         const int64_t n = bs[J];
                         const double* b = b_data + b_boff[q];
                         double* c = acc + pos[J];
@@ -189,6 +191,7 @@ int oracle_mm_numeric(int32_t nblk, const int32_t* bs,
                         for (int64_t e = 0; e < area; ++e) out[e] = alpha * s[e];
                     }
                 }
+                for (int64_t q = c_rp[I]; q < c_rp[I + 1]; ++q) pos[c_col[q]] = -1;
             }
         }
         free(pos);
@@ -196,6 +199,59 @@ int oracle_mm_numeric(int32_t nblk, const int32_t* bs,
     }
     out_stats[0] = nprod;
     out_stats[1] = nflop;
+    return err;
+}
+
+/*
+ * The norm-bound prescreen of a product, for every candidate block (I, J) of a pattern of
+ * alpha*A*B + beta*C_in (c_rp, c_col): bound = |alpha| sum_K ||A_IK|| ||B_KJ|| in ascending K,
+ * plus |beta| ||C_in,IJ|| where C_in has the block; keep[q] = 1 if I == J or bound >= eps_lo.
+ * By the triangle inequality and ||XY||_F <= ||X||_F ||Y||_F the block's norm is at most its
+ * bound, so a block left out has norm below eps_lo and the filter would drop it.
+ */
+int oracle_prescreen(int32_t nblk, double abs_alpha,
+                     const int64_t* a_rp, const int32_t* a_col, const double* a_norm,
+                     const int64_t* b_rp, const int32_t* b_col, const double* b_norm,
+                     double abs_beta, const int64_t* ci_rp, const int32_t* ci_col, const double* ci_norm,
+                     const int64_t* c_rp, const int32_t* c_col, double eps_lo, int32_t* keep) {
+    int err = 0;
+#pragma omp parallel
+    {
+        int64_t* pos = (int64_t*)malloc(sizeof(int64_t) * ((size_t)nblk + 1));
+        double* bound = (double*)malloc(sizeof(double) * ((size_t)nblk + 1));
+        if (!pos || !bound) {
+#pragma omp atomic write
+            err = 1;
+        } else {
+            for (int32_t J = 0; J <= nblk; ++J) pos[J] = -1;
+#pragma omp for schedule(dynamic, 8)
+            for (int32_t I = 0; I < nblk; ++I) {
+                for (int64_t q = c_rp[I]; q < c_rp[I + 1]; ++q) {
+                    pos[c_col[q]] = q - c_rp[I];
+                    bound[q - c_rp[I]] = 0.0;
+                }
+                for (int64_t p = a_rp[I]; p < a_rp[I + 1]; ++p) {
+                    const int32_t K = a_col[p];
+                    const double na = abs_alpha * a_norm[p];
+                    for (int64_t q = b_rp[K]; q < b_rp[K + 1]; ++q) {
+                        const int64_t t = pos[b_col[q]];
+                        if (t >= 0) bound[t] = bound[t] + na * b_norm[q];
+                    }
+                }
+                if (ci_rp)
+                    for (int64_t r = ci_rp[I]; r < ci_rp[I + 1]; ++r) {
+                        const int64_t t = pos[ci_col[r]];
+                        if (t >= 0) bound[t] = bound[t] + abs_beta * ci_norm[r];
+                    }
+                for (int64_t q = c_rp[I]; q < c_rp[I + 1]; ++q) {
+                    keep[q] = (c_col[q] == I || bound[q - c_rp[I]] >= eps_lo) ? 1 : 0;
+                    pos[c_col[q]] = -1;
+                }
+            }
+        }
+        free(pos);
+        free(bound);
+    }
     return err;
 }
 

@@ -244,3 +244,49 @@ def test_product_block_wrong_b_block_fails_the_pin():
     bad_err = max(np.abs(bsr.product_block(I, J, 1.0, A, Bbad) - _dense_block(ref, roff, I, J)).max()
                   for I, J in itertools.product(range(len(bs)), repeat=2))
     assert bad_err > 1e-2
+
+
+def _dense_pattern(M, weights=None):
+    D = np.zeros((M.nblk, M.nblk))
+    D[M.rows, M.col] = 1.0 if weights is None else weights
+    return D
+
+
+@pytest.mark.parametrize("eps", [1e-2, 1e-1, 1.0])          # the 32-water box screens from about 1e-2
+@pytest.mark.parametrize("alpha,beta", [(1.0, 0.0), (-0.5, 1.5)])
+def test_prescreen_leaves_the_filtered_product_unchanged(eps, alpha, beta):
+    A = bsr.Mat.of(synth.build_decay(synth.DECAY_32))
+    Cin = _mat(A.bs, 0.2, 31)
+    full, fi = bsr.multiply(alpha, A, A, beta, Cin, eps=eps, info=True)
+    pre, pi = bsr.multiply(alpha, A, A, beta, Cin, eps=eps, info=True, prescreen=True)
+    assert np.array_equal(full.rp, pre.rp) and np.array_equal(full.col, pre.col)
+    assert np.array_equal(full.data, pre.data)                 # the same loops on the kept blocks
+    assert pi.dev2 == fi.dev2
+    assert pi.unfiltered.nnzb < fi.unfiltered.nnzb and pi.n_products < fi.n_products
+    # without a threshold nothing is screened
+    _, zi = bsr.multiply(alpha, A, A, beta, Cin, eps=0.0, info=True, prescreen=True)
+    assert zi.n_products == bsr.multiply(alpha, A, A, beta, Cin, info=True)[1].n_products
+
+
+def test_prescreen_forms_the_blocks_whose_bound_reaches_eps():
+    # brute force on dense block-norm matrices: formed <=> diagonal or |alpha| (NA NB)_IJ >= eps
+    # (candidates within 1e-9 of eps, where the summation order could decide, are not judged);
+    # product and flop counts over the formed blocks
+    A = bsr.Mat.of(synth.build_decay(synth.DECAY_32))
+    eps, alpha = 0.1, -0.75
+    _, fi = bsr.multiply(alpha, A, A, info=True)
+    _, pi = bsr.multiply(alpha, A, A, eps=eps, info=True, prescreen=True)
+    na, _ = bsr.block_norms(A)
+    bound = abs(alpha) * (_dense_pattern(A, na) @ _dense_pattern(A, na))
+    cand = _dense_pattern(fi.unfiltered) > 0
+    formed = _dense_pattern(pi.unfiltered) > 0
+    assert not np.any(formed & ~cand)
+    want = cand & ((bound >= eps) | np.eye(A.nblk, dtype=bool))
+    clear = np.abs(bound / eps - 1.0) > 1e-9
+    assert np.array_equal(formed[clear], want[clear])
+    assert 0 < formed.sum() < cand.sum()
+    PA = _dense_pattern(A)
+    assert pi.n_products == int((PA @ PA)[formed].sum())
+    m = A.bs.astype(np.float64)
+    flops = 2.0 * m[:, None] * ((PA * m[None, :]) @ PA) * m[None, :]
+    assert pi.flops == int(round(flops[formed].sum()))
