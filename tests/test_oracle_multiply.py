@@ -270,7 +270,7 @@ def test_prescreen_leaves_the_filtered_product_unchanged(eps, alpha, beta):
 
 def test_prescreen_forms_the_blocks_whose_bound_reaches_eps():
     # brute force on dense block-norm matrices: formed <=> diagonal or |alpha| (NA NB)_IJ >= eps
-    # (candidates within 1e-9 of eps, where the summation order could decide, are not judged);
+    # (candidates within 1e-9 of eps, where the summation order could decide, are left out);
     # product and flop counts over the formed blocks
     A = bsr.Mat.of(synth.build_decay(synth.DECAY_32))
     eps, alpha = 0.1, -0.75
