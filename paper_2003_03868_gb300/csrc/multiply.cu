@@ -143,7 +143,15 @@ struct BoundArgs {
     int32_t* keep;
     int use_smem;
     int use_fast;            // FP32 upper bound with atomics (needs use_smem and < 4096 terms per candidate)
+    const float* b_norm_ru;  // use_fast: B's norms rounded up to FP32, once per block
 };
+
+// B's block norms rounded up to FP32 for the fast bound: one conversion per block instead of one
+// per (K, J) term (the FP64 pipe that converts runs at a few operations per clock per SM).
+__global__ void k_norms_f32_ru(int64_t n, const double* __restrict__ in, float* __restrict__ out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = __double2float_ru(in[i]);
+}
 
 // The norm bound is accumulated in FP32 with shared-memory atomics, in any order, so the
 // K loop needs no barrier.  Each term is scaled up by (1 + 2^-10) before it is added; with
@@ -195,7 +203,7 @@ __global__ void k_cand_bound(int32_t nblk, RowPattern P, int nwords, BoundArgs B
                 const int kk = B.bs[K];
                 for (int64_t q = P.b_rp[K] + lane; q < P.b_rp[K + 1]; q += 32) {
                     const int r = rank_of(bm, wpre, P.b_col[q]);
-                    atomicAdd(&fb[r], __fmul_ru(na, __double2float_ru(B.b_norm[q])));
+                    atomicAdd(&fb[r], __fmul_ru(na, B.b_norm_ru[q]));
                     atomicAdd(&pc[r], 1);
                     atomicAdd(&ks[r], kk);
                 }
@@ -1119,10 +1127,16 @@ void multiply(double alpha, dbcsr_matrix_* A, dbcsr_matrix_* B, double beta, dbc
     const bool fast_bound = acc_smem && max_arow < 4096;
     if (!acc_smem) bound.alloc(nc1, s);
     if (ncand) {
+        DBuf<float> b_norm_ru;
+        if (fast_bound && B->nnzb) {
+            b_norm_ru.alloc(B->nnzb, s);
+            k_norms_f32_ru<<<grid_for(B->nnzb, 256), 256, 0, s>>>(B->nnzb, B->norms.p, b_norm_ru.p);
+            DBG_LAUNCH_CK();
+        }
         BoundArgs ba{std::fabs(alpha), std::fabs(beta), eps * (1.0 - 1e-12), A->norms.p, B->norms.p,
                      use_c ? C->norms.p : nullptr, A->bs.p, coff.p, cand_row.p, cand_col.p,
                      bound.p, pcnt.p, ksum.p, use_c ? cin.p : nullptr, keep.p, acc_smem ? 1 : 0,
-                     fast_bound ? 1 : 0};
+                     fast_bound ? 1 : 0, b_norm_ru.p};
         const size_t sm = acc_smem ? sm_acc : sm_rank;
         allow_dyn_smem(k_cand_bound, sm);
         k_cand_bound<<<sym_grid(nblk), kSymThreads, sm, s>>>(nblk, P, nwords, ba);
