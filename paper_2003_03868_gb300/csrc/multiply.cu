@@ -449,9 +449,9 @@ __global__ void k_form_stats(int64_t nform, const int32_t* __restrict__ f_row, c
     }
 }
 
-// Copied blocks: C_IJ = C_JI^T (after every computed block is written), with their
-// norm and distance to 1 (never diagonal); dropped blocks get norm -1 so that the
-// filter removes them.
+// Copied blocks: C_IJ = C_JI^T (after every computed block is written), with their twin's
+// norm and distance to 1 (never diagonal); dropped blocks get norm -1 so that the filter
+// removes them.
 __global__ void k_mirror_copy(int64_t nform, int sym, const int64_t* __restrict__ mirror,
                               const int32_t* __restrict__ f_row, const int32_t* __restrict__ f_col,
                               const int64_t* __restrict__ f_off, const int32_t* __restrict__ bs,
@@ -473,14 +473,11 @@ __global__ void k_mirror_copy(int64_t nform, int sym, const int64_t* __restrict_
         const int m = bs[f_row[k]], n = bs[f_col[k]];
         const double* S = c_data + f_off[src];
         double* D = c_data + f_off[k];
-        double sq = 0.0;
         // (i, j) of element e = i n + j, stepped by 32 elements without a division per element
         const int di = 32 / n, dj = 32 - di * n;
         int i = lane / n, j = lane - i * n;
         for (int e = lane; e < m * n; e += 32) {
-            const double v = S[j * m + i];
-            D[e] = v;
-            sq = fma(v, v, sq);
+            D[e] = S[j * m + i];
             i += di;
             j += dj;
             if (j >= n) {
@@ -488,11 +485,11 @@ __global__ void k_mirror_copy(int64_t nform, int sym, const int64_t* __restrict_
                 ++i;
             }
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+        // the transpose has its twin's norm and (off the diagonal) distance to 1: taken over, so
+        // that the pair is kept or dropped together and no FP64 arithmetic bounds the copy
         if (lane == 0) {
-            c_norm[k] = sqrt(sq);
-            c_dev2[k] = sq;
+            c_norm[k] = c_norm[src];
+            c_dev2[k] = c_dev2[src];
         }
     }
 }
