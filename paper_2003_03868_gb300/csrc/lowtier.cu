@@ -904,15 +904,22 @@ __global__ void __launch_bounds__(kLtThreads, 1) k_lowtier(LtArgs A) {
                                 if (ci >= 0) val = val + A.beta * c[u];
                                 out[e] = val;
                                 sq = fma(val, val, sq);
-                                const double w = (diag && i == j) ? val - 1.0 : val;
-                                d2 = fma(w, w, d2);
+                                // off the diagonal the distance to 1 is the norm (summed once
+                                // below): the FP64 pipe, not the stores, would bound this loop
+                                if (diag) {
+                                    const double w = (i == j) ? val - 1.0 : val;
+                                    d2 = fma(w, w, d2);
+                                }
                             }
                         }
                     }
 #pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) {
-                        sq += __shfl_xor_sync(0xffffffffu, sq, o);
-                        d2 += __shfl_xor_sync(0xffffffffu, d2, o);
+                    for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+                    if (diag) {
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) d2 += __shfl_xor_sync(0xffffffffu, d2, o);
+                    } else {
+                        d2 = sq;
                     }
                     if (lane == 0) {
                         const int32_t k = T.tbl[a][b];
