@@ -76,3 +76,24 @@ def test_products_per_iteration_match_the_oracle():
         r = sign.sign_iterate(H, 0.0, 1e-7, 1e-9, order=order)
         assert r.converged or r.stalled
         assert r.multiplies == k * (r.iterations - 1) + 1, order
+
+
+def test_oracle_samples_time_the_prescreened_product():
+    # the CPU-baseline and reference-arm samples run the oracle's prescreened product (the
+    # library's product list): the same filtered rows as the full product, fewer flops; the
+    # one-core sample leaves the oracle's thread count as it found it
+    import numpy as np
+    import synth
+    from oracle import bsr
+    w = synth.small(48, basis=(23, 7), seed=8501, eps=1e-4)
+    h = synth.build_hamiltonian(w)
+    smp = bench.RowsSample(h, w, 0.5)
+    flops, dt, cores = smp.run()
+    full, info = bsr.multiply(1.0, smp.A, smp.X0, eps=smp.eps, info=True)
+    pre = bsr.multiply(1.0, smp.A, smp.X0, eps=smp.eps, prescreen=True)
+    assert np.array_equal(full.col, pre.col) and np.array_equal(full.data, pre.data)
+    assert 0 < flops < info.flops and dt > 0 and cores >= 1
+    assert "prescreen" in smp.text(flops, dt)
+    n0 = bsr.num_threads()
+    one = bench.one_core_sample(h, w)
+    assert one["cores"] == 1 and one["value"] > 0 and bsr.num_threads() == n0
