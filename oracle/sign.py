@@ -150,28 +150,31 @@ def _step_polynomial(Y: bsr.Mat, order: int, eps: float, mult) -> bsr.Mat:
 class _Work:
     """Counts the filtered products of an iteration."""
 
-    def __init__(self, eps: float):
+    def __init__(self, eps: float, prescreen: bool = False):
         self.eps, self.flops, self.n_products, self.multiplies = eps, 0, 0, 0
+        self.prescreen = prescreen
 
     def __call__(self, alpha, A, B, beta=0.0, Cin=None, info=False):
-        C, inf = bsr.multiply(alpha, A, B, beta, Cin, eps=self.eps, info=True)
+        C, inf = bsr.multiply(alpha, A, B, beta, Cin, eps=self.eps, info=True, prescreen=self.prescreen)
         self.flops += inf.flops
         self.n_products += inf.n_products
         self.multiplies += 1
         return (C, inf) if info else C
 
 
-def _higher_order_update(X: bsr.Mat, Y: bsr.Mat, order: int, eps: float):
+def _higher_order_update(X: bsr.Mat, Y: bsr.Mat, order: int, eps: float, prescreen: bool = False):
     """X p_n(Y) for Y = filter(X X), by the four-product scheme of the module header.
     Returns the new X and the (flops, block products, matrix products) it took."""
-    w = _Work(eps)
+    w = _Work(eps, prescreen)
     U = _step_polynomial(Y, order, eps, w)
     Xn = w(1.0, X, U)
     return Xn, (w.flops, w.n_products, w.multiplies)
 
 
 def sign_iterate(H: bsr.Mat, mu: float, eps: float, tol: float, max_iter: int = 100,
-                 stall_ratio: float = 0.5, order: int = 2) -> SignResult:
+                 stall_ratio: float = 0.5, order: int = 2, prescreen: bool = False) -> SignResult:
+    """prescreen: every product forms only the blocks whose norm bound reaches eps
+    (bsr.multiply); the iteration is the same bit for bit, with fewer block products."""
     t0 = time.perf_counter()
     n = H.n
     alpha = gershgorin(H, mu)
@@ -183,7 +186,7 @@ def sign_iterate(H: bsr.Mat, mu: float, eps: float, tol: float, max_iter: int = 
     converged = stalled = False
     it = 0
     while it < max_iter:
-        X2, info = bsr.multiply(1.0, X, X, eps=eps, info=True)
+        X2, info = bsr.multiply(1.0, X, X, eps=eps, info=True, prescreen=prescreen)
         mults += 1
         it += 1
         flops += info.flops
@@ -198,12 +201,12 @@ def sign_iterate(H: bsr.Mat, mu: float, eps: float, tol: float, max_iter: int = 
             break
         if order == 2:
             T = bsr.add_identity(X2, -1.0, 3.0)                    # 3 1 - X^2
-            X, info = bsr.multiply(0.5, X, T, eps=eps, info=True)  # X (3 1 - X^2) / 2
+            X, info = bsr.multiply(0.5, X, T, eps=eps, info=True, prescreen=prescreen)  # X (3 1 - X^2) / 2
             flops += info.flops
             nprod += info.n_products
             mults += 1
         else:
-            X, (f, npr, nm) = _higher_order_update(X, X2, order, eps)
+            X, (f, npr, nm) = _higher_order_update(X, X2, order, eps, prescreen)
             flops += f
             nprod += npr
             mults += nm

@@ -130,3 +130,17 @@ def test_stall_is_reported():
     r = sign.sign_iterate(H, 0.0, eps=0.05, tol=1e-14, max_iter=60)
     assert not r.converged
     assert r.stalled or r.iterations == 60
+
+
+@pytest.mark.parametrize("order", [2, 3])
+def test_prescreened_iteration_is_the_same_bit_for_bit(order):
+    # the prescreen leaves every filtered product unchanged, so the whole iteration too, with
+    # fewer block products
+    h = synth.build_hamiltonian(synth.small(32, basis=(23, 7), seed=8601, eps=1e-4, tol=1e-7))
+    H = bsr.Mat.of(h.H)
+    a = sign.sign_iterate(H, h.mu, 1e-4, 1e-7, order=order)
+    b = sign.sign_iterate(H, h.mu, 1e-4, 1e-7, order=order, prescreen=True)
+    assert a.residuals == b.residuals and a.iterations == b.iterations
+    assert np.array_equal(a.P.col, b.P.col) and np.array_equal(a.P.data, b.P.data)
+    assert a.e_band == b.e_band
+    assert b.n_products < a.n_products and b.flops < a.flops
